@@ -1,0 +1,499 @@
+/*
+ * CPU oracle for spin-orbit tracking through a ring lattice.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file: only the tests, the package's smoke check and the bench's
+ * CPU-baseline / reference leg do.  It shares no code, header or constant with
+ * the CUDA library.
+ *
+ * It is a plain, slow, step-by-step transcription of the method of
+ *   Abell, Meiser, Ranjbar, Barber, "Accurate and efficient spin integration
+ *   for particle accelerators" (arXiv:1501.03450),
+ * in the paper's order and notation, with no blocking, fusion or reordering:
+ *
+ *   Sec. 2.1  canonical variables z = (X, Px, Y, Py, T, Pt), Eqs. (1)-(3)
+ *   Sec. 2.2  Thomas-BMT precession vector in s, Eq. (6b)
+ *   Sec. 3.1  exact sector-bend map, Eqs. (7)-(10)       ("bend-kick")
+ *   Sec. 3.3  quadrupole matrix-kick split, Eqs. (21)-(27)
+ *   Sec. 3.4  multipole drift-kick split, Eqs. (28)-(29)
+ *   Sec. 4.1  piece-wise constant spin rotations composed as quaternions,
+ *             later slices on the left, Eq. (37)
+ *   Sec. 4.3  trapezoid-weighted edge rotations, sub-sampled levels Q(h/2^k),
+ *             Romberg table and normalisation per element, Eqs. (38)-(39)
+ *   Sec. 5    thin Siberian snakes (orbit-transparent spin rotators)
+ *
+ * Readings where the paper is silent (recorded in the design notes):
+ *   - quaternions are Hamilton, scalar first; the spin is rotated actively,
+ *     S' = Q S conj(Q); a rotation vector w gives q = (cos|w|/2, sin|w|/2 w^);
+ *   - "Romberg order k" is the number of Romberg iterations, result Q_kk;
+ *   - the DKD slice is half-drift, kick, half-drift; slice edges are the
+ *     states between slices, edge 0 the element entrance;
+ *   - the sector-bend vector-potential term of Eq. (7) already contains the
+ *     metric factor (1 + hX) of Eq. (3);
+ *   - the particle's own gamma = gamma0 (1 + beta0 Pt) enters Eq. (6b);
+ *   - elements whose precession vector vanishes identically (drifts) carry no
+ *     spin step;
+ *   - a particle whose longitudinal momentum becomes imaginary (Ps^2 <= 0) is
+ *     lost: it keeps the state it had at the entrance of that element and is
+ *     not tracked further.
+ *
+ * The scalar type `real` is double for the oracle proper.  The same source is
+ * also compiled with long double (an extended-precision copy used only to
+ * measure the oracle's own rounding noise) and with double complex (complex-
+ * step derivatives for exact Jacobians in the symplecticity tests).
+ * <tgmath.h> makes sqrt/sin/... dispatch on the argument type.
+ */
+#include <tgmath.h>
+#include <complex.h>
+#include <stdint.h>
+#include <string.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef ORACLE_REAL
+#define ORACLE_REAL double
+#endif
+typedef ORACLE_REAL real;
+
+/* Real part, used for branch decisions only (identity for real builds). */
+#define RE(x) ((double)creal(x))
+
+/* Element kinds (own numbering; the CUDA library has its own). */
+enum { ORC_DRIFT = 0, ORC_MULT = 1, ORC_QUAD_MK = 2, ORC_SBEND = 3, ORC_SNAKE = 4 };
+
+typedef struct {
+    int32_t type;
+    int32_t n_slices;
+    double L, k1, k2, angle, eta, snake_phi, snake_mu;
+} orc_element;
+
+typedef struct {
+    double G, Ggamma0, gamma0, beta0;
+} orc_ref;
+
+typedef struct {
+    real X, Px, Y, Py, T, Pt;
+} orc_orbit;
+
+static orc_ref make_ref(double G, double Ggamma0) {
+    orc_ref r;
+    r.G = G;
+    r.Ggamma0 = Ggamma0;
+    r.gamma0 = Ggamma0 / G;
+    r.beta0 = sqrt(1.0 - 1.0 / (r.gamma0 * r.gamma0));
+    return r;
+}
+
+/* Square of the scaled total momentum, 1 + 2 Pt/beta0 + Pt^2 (Eq. (22)). */
+static real momentum_sq(const orc_ref* r, real Pt) {
+    return 1.0 + 2.0 * Pt / r->beta0 + Pt * Pt;
+}
+
+/* ---------------------------------------------------------------------- */
+/* orbit maps                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Exact drift: the flow of H_drift = -Ps + Pt/beta0 (Eq. (29b)),
+ * dX/ds = Px/Ps, dY/ds = Py/Ps, dT/ds = 1/beta0 - (1/beta0 + Pt)/Ps. */
+static int drift(const orc_ref* r, orc_orbit* z, double s) {
+    real ps2 = momentum_sq(r, z->Pt) - z->Px * z->Px - z->Py * z->Py;
+    if (!(RE(ps2) > 0.0)) return 1;
+    real Ps = sqrt(ps2);
+    z->X += s * z->Px / Ps;
+    z->Y += s * z->Py / Ps;
+    z->T += s * (1.0 / r->beta0 - (1.0 / r->beta0 + z->Pt) / Ps);
+    return 0;
+}
+
+/* Normal multipole coefficients of Eq. (28) for a combined quadrupole and
+ * sextupole: H_m = Re[ sum_m (b_m/(m B rho)) (X + iY)^m ] with
+ * b_2/(B rho) = k1 and b_3/(B rho) = k2/2 (MAD k2 = B''/(B rho)).
+ * The field b = B/(B rho) follows from B_y + i B_x = sum_m c_m (X+iY)^(m-1). */
+static void mult_field(double k1, double k2, real X, real Y, real* bx, real* by) {
+    /* (X + iY)^1 and (X + iY)^2 written out in real arithmetic so that the
+     * complex-step build can use the same code */
+    real w1r = X, w1i = Y;
+    real w2r = X * X - Y * Y, w2i = 2.0 * X * Y;
+    real c2 = k1, c3 = 0.5 * k2;
+    *by = c2 * w1r + c3 * w2r;
+    *bx = c2 * w1i + c3 * w2i;
+}
+
+/* Kick generated by H_m over a length ds: dPx/ds = -dH_m/dX = -b_y,
+ * dPy/ds = -dH_m/dY = +b_x (Sec. 3.4). */
+static void mult_kick(orc_orbit* z, double k1, double k2, double ds) {
+    real bx, by;
+    mult_field(k1, k2, z->X, z->Y, &bx, &by);
+    z->Px -= ds * by;
+    z->Py += ds * bx;
+}
+
+/* Exact sector-bend map over a length s, Eq. (10) with P_alpha of Eq. (8) and
+ * eta of Eq. (9).  h is the fixed curvature of the magnet. */
+static int sbend_map(const orc_ref* r, orc_orbit* z, double h, double eta, double s) {
+    real Pa2 = momentum_sq(r, z->Pt) - z->Py * z->Py;           /* Eq. (8) squared */
+    real Xi = z->X, Pxi = z->Px;
+    real ri2 = Pa2 - Pxi * Pxi;
+    if (!(RE(ri2) > 0.0)) return 1;
+    real Pa = sqrt(Pa2);
+    real root_i = sqrt(ri2);
+    double c = cos(h * s), sn = sin(h * s);
+    real Pxf = Pxi * c + (root_i - eta * (1.0 + h * Xi)) * sn;               /* Eq. (10b) */
+    real dPxf = -h * Pxi * sn + h * (root_i - eta * (1.0 + h * Xi)) * c;     /* d Px / ds */
+    real rf2 = Pa2 - Pxf * Pxf;
+    if (!(RE(rf2) > 0.0)) return 1;
+    real Xf = (1.0 / h) * ((1.0 / eta) * (sqrt(rf2) - dPxf / h) - 1.0);     /* Eq. (10a) */
+    real dasin = asin(Pxi / Pa) - asin(Pxf / Pa);
+    z->Y = z->Y + (1.0 / eta) * z->Py * s + (1.0 / (eta * h)) * z->Py * dasin;   /* Eq. (10c) */
+    z->T = z->T - (1.0 / eta) * z->Pt * s
+           - (1.0 / (eta * h)) * (1.0 / r->beta0 + z->Pt) * dasin
+           + (1.0 - 1.0 / eta) * s / r->beta0;                                /* Eq. (10e) */
+    z->X = Xf;
+    z->Px = Pxf;
+    return 0;
+}
+
+static real sinc_(real x) { return (RE(x) == 0.0 && cimag(x) == 0.0) ? (real)1.0 : sin(x) / x; }
+static real sinhc_(real x) { return (RE(x) == 0.0 && cimag(x) == 0.0) ? (real)1.0 : sinh(x) / x; }
+static real sin2c_(real x) { return (RE(x) == 0.0 && cimag(x) == 0.0) ? (real)0.0 : sin(x) * sin(x) / x; }
+static real sinh2c_(real x) { return (RE(x) == 0.0 && cimag(x) == 0.0) ? (real)0.0 : sinh(x) * sinh(x) / x; }
+
+/* Flow of the linear quadrupole Hamiltonian H_qL (Eq. (21b)) over a length
+ * s for a focusing gradient k1 = b2/(B rho) >= 0: Eq. (24) with P of Eq. (22)
+ * and kappa of Eq. (23). */
+static void quad_linear_focusing(const orc_ref* r, orc_orbit* z, double k1, double s) {
+    real P = sqrt(momentum_sq(r, z->Pt));
+    real kap = sqrt(k1 / P);
+    real ks = kap * s;
+    real X = z->X, Px = z->Px, Y = z->Y, Py = z->Py;
+    real Xf = X * cos(ks) + s * (Px / P) * sinc_(ks);
+    real Pxf = Px * cos(ks) - kap * P * X * sin(ks);
+    real Yf = Y * cosh(ks) + s * (Py / P) * sinhc_(ks);
+    real Pyf = Py * cosh(ks) + kap * P * Y * sinh(ks);
+    real brace =
+        (s / 4.0) * ((Px * Px + Py * Py) / (P * P) + kap * kap * (X * X - Y * Y))
+        + (s / 4.0) * ((Px / P) * (Px / P) - (kap * X) * (kap * X)) * sinc_(2.0 * ks)
+        + (s / 4.0) * ((Py / P) * (Py / P) + (kap * Y) * (kap * Y)) * sinhc_(2.0 * ks)
+        - (ks / 2.0) * (X * (Px / P) * sin2c_(ks) - Y * (Py / P) * sinh2c_(ks));
+    z->T = z->T - (1.0 / P) * (1.0 / r->beta0 + z->Pt) * brace;
+    z->X = Xf;
+    z->Px = Pxf;
+    z->Y = Yf;
+    z->Py = Pyf;
+}
+
+/* For a defocusing gradient (k1 < 0) the paper rotates the transverse frame
+ * about the longitudinal axis so that the magnet focuses in the first plane
+ * (Sec. 3.3): a 90 degree rotation maps (X, Px, Y, Py) -> (Y, Py, -X, -Px)
+ * and turns the gradient k1 into -k1. */
+static void quad_linear(const orc_ref* r, orc_orbit* z, double k1, double s) {
+    if (k1 >= 0.0) {
+        quad_linear_focusing(r, z, k1, s);
+        return;
+    }
+    orc_orbit w = *z;
+    w.X = z->Y;
+    w.Px = z->Py;
+    w.Y = -z->X;
+    w.Py = -z->Px;
+    quad_linear_focusing(r, &w, -k1, s);
+    z->X = -w.Y;
+    z->Px = -w.Py;
+    z->Y = w.X;
+    z->Py = w.Px;
+    z->T = w.T;
+}
+
+/* Flow of the nonlinear quadrupole remainder H_qNL (Eq. (21c)) over s,
+ * Eq. (25). */
+static int quad_nonlinear(const orc_ref* r, orc_orbit* z, double s) {
+    real P2 = momentum_sq(r, z->Pt);
+    real P = sqrt(P2);
+    real ps2 = P2 - z->Px * z->Px - z->Py * z->Py;
+    if (!(RE(ps2) > 0.0)) return 1;
+    real Ps = sqrt(ps2);
+    real Px = z->Px, Py = z->Py;
+    z->X = z->X + s * Px * (1.0 / Ps - 1.0 / P);
+    z->Y = z->Y + s * Py * (1.0 / Ps - 1.0 / P);
+    z->T = z->T - s * (1.0 / r->beta0 + z->Pt) * (1.0 / Ps - (1.0 / P) * (Px * Px + Py * Py) / (2.0 * P2))
+           + s / r->beta0;
+    return 0;
+}
+
+/* One integration slice of length ds of a spin-carrying element. */
+static int slice_map(const orc_ref* r, const orc_element* e, orc_orbit* z, double ds) {
+    switch (e->type) {
+    case ORC_MULT:   /* drift-kick-drift, Sec. 3.4 with the symmetric form of Eq. (27) */
+        if (drift(r, z, 0.5 * ds)) return 1;
+        mult_kick(z, e->k1, e->k2, ds);
+        return drift(r, z, 0.5 * ds);
+    case ORC_QUAD_MK: /* matrix-kick, Eq. (27) */
+        quad_linear(r, z, e->k1, 0.5 * ds);
+        if (quad_nonlinear(r, z, ds)) return 1;
+        quad_linear(r, z, e->k1, 0.5 * ds);
+        return 0;
+    case ORC_SBEND:   /* exact bend, Eq. (10) */
+        return sbend_map(r, z, e->angle / e->L, e->eta, ds);
+    default:
+        return 1;
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* spin                                                                   */
+/* ---------------------------------------------------------------------- */
+
+/* Thomas-BMT precession vector in s, Eq. (6b):
+ *   Omega = -(1 + hX)/(B rho Ps) [ (1 + G gamma) B - G (gamma - 1)(u.B) u ] + h y^
+ * with u the unit vector along (Px, Py, Ps) and gamma the particle's own
+ * Lorentz factor, gamma = gamma0 (1 + beta0 Pt) from Eq. (2). */
+static int omega(const orc_ref* r, const orc_element* e, const orc_orbit* z, real out[3]) {
+    real P2 = momentum_sq(r, z->Pt);
+    real P = sqrt(P2);
+    real ps2 = P2 - z->Px * z->Px - z->Py * z->Py;
+    if (!(RE(ps2) > 0.0)) return 1;
+    real Ps = sqrt(ps2);
+    real gamma = r->gamma0 * (1.0 + r->beta0 * z->Pt);
+    real b[3] = {0.0, 0.0, 0.0};
+    double h = 0.0;
+    if (e->type == ORC_SBEND) {
+        h = e->angle / e->L;
+        b[1] = e->eta * h;             /* b1/(B rho) = eta h, Eq. (9) */
+    } else {
+        mult_field(e->k1, e->k2, z->X, z->Y, &b[0], &b[1]);
+    }
+    real u[3] = {z->Px / P, z->Py / P, Ps / P};
+    real ub = u[0] * b[0] + u[1] * b[1] + u[2] * b[2];
+    real pre = -(1.0 + h * z->X) / Ps;
+    for (int i = 0; i < 3; ++i)
+        out[i] = pre * ((1.0 + r->G * gamma) * b[i] - r->G * (gamma - 1.0) * ub * u[i]);
+    out[1] += h;
+    return 0;
+}
+
+/* Hamilton product a (x) b, scalar first. */
+static void qmul(const real a[4], const real b[4], real out[4]) {
+    real o0 = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    real o1 = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    real o2 = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    real o3 = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    out[0] = o0; out[1] = o1; out[2] = o2; out[3] = o3;
+}
+
+/* Unit quaternion of the rotation about w^ by the angle |w|. */
+static void quat_from_rotation_vector(const real w[3], real q[4]) {
+    real th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    if (RE(th2) == 0.0 && cimag(th2) == 0.0) {
+        q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
+        return;
+    }
+    real th = sqrt(th2);
+    real f = sin(0.5 * th) / th;
+    q[0] = cos(0.5 * th);
+    q[1] = f * w[0];
+    q[2] = f * w[1];
+    q[3] = f * w[2];
+}
+
+/* S <- Q S conj(Q), computed as quaternion products. */
+static void rotate_spin(const real Q[4], real S[3]) {
+    real s4[4] = {0.0, S[0], S[1], S[2]};
+    real qc[4] = {Q[0], -Q[1], -Q[2], -Q[3]};
+    real t[4], o[4];
+    qmul(Q, s4, t);
+    qmul(t, qc, o);
+    S[0] = o[1]; S[1] = o[2]; S[2] = o[3];
+}
+
+#define ORC_MAX_ORDER 6
+
+/* Net element rotation from the precession vectors recorded at the N+1
+ * slice edges (Sec. 4.3): for every level k = 0..K the edges are sub-sampled
+ * with stride 2^(K-k), the step is stride*ds, the two end edges get half a
+ * step (trapezoid rule), and the edge rotations are multiplied with later
+ * edges on the left (Eq. (37b)); this gives Q_0k = Q(h/2^k) of Eqs. (38),
+ * (39a).  The Romberg rule Eq. (39b) then builds the table Eq. (39c) and the
+ * bottom-right entry Q_KK is normalised.  levels (may be NULL) receives
+ * Q_00..Q_0K. */
+static void romberg_element_rotation(const real (*Om)[3], int N, double ds, int K,
+                                     real Q[4], real* levels) {
+    real Tab[ORC_MAX_ORDER + 1][ORC_MAX_ORDER + 1][4];
+    for (int k = 0; k <= K; ++k) {
+        int stride = 1 << (K - k);
+        double step = stride * ds;
+        real acc[4] = {1.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i <= N; i += stride) {
+            double wgt = (i == 0 || i == N) ? 0.5 * step : step;
+            real w[3] = {wgt * Om[i][0], wgt * Om[i][1], wgt * Om[i][2]};
+            real q[4];
+            quat_from_rotation_vector(w, q);
+            qmul(q, acc, acc);
+        }
+        for (int c = 0; c < 4; ++c) {
+            Tab[0][k][c] = acc[c];
+            if (levels) levels[4 * k + c] = acc[c];
+        }
+    }
+    for (int j = 0; j < K; ++j) {
+        double f = 1.0;
+        for (int p = 0; p <= j; ++p) f *= 4.0;        /* 4^(j+1) */
+        for (int k = j + 1; k <= K; ++k)
+            for (int c = 0; c < 4; ++c)
+                Tab[j + 1][k][c] = (f * Tab[j][k][c] - Tab[j][k - 1][c]) / (f - 1.0);
+    }
+    real n = sqrt(Tab[K][K][0] * Tab[K][K][0] + Tab[K][K][1] * Tab[K][K][1] +
+                  Tab[K][K][2] * Tab[K][K][2] + Tab[K][K][3] * Tab[K][K][3]);
+    for (int c = 0; c < 4; ++c) Q[c] = Tab[K][K][c] / n;
+}
+
+/* Track one particle through one element; the spin S is rotated by the
+ * element's net rotation.  Returns 0, or 1 if the particle is lost. */
+static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, real S[3],
+                         int K, real* levels_out, real* Q_out) {
+    if (e->type == ORC_DRIFT)
+        return drift(r, z, e->L);
+    if (e->type == ORC_SNAKE) {
+        /* orbit-transparent rotation by snake_mu about (sin phi, 0, cos phi) */
+        real Q[4] = {cos(0.5 * e->snake_mu), sin(0.5 * e->snake_mu) * sin(e->snake_phi), 0.0,
+                     sin(0.5 * e->snake_mu) * cos(e->snake_phi)};
+        rotate_spin(Q, S);
+        if (Q_out) memcpy(Q_out, Q, sizeof(Q));
+        return 0;
+    }
+    int N = e->n_slices;
+    double ds = e->L / N;
+    real (*Om)[3] = malloc(sizeof(real[3]) * (size_t)(N + 1));
+    if (!Om) return 2;
+    int lost = omega(r, e, z, Om[0]);
+    for (int i = 1; i <= N && !lost; ++i) {
+        lost = slice_map(r, e, z, ds);
+        if (!lost) lost = omega(r, e, z, Om[i]);
+    }
+    if (!lost) {
+        real Q[4];
+        romberg_element_rotation((const real(*)[3])Om, N, ds, K, Q, levels_out);
+        rotate_spin(Q, S);
+        if (Q_out) memcpy(Q_out, Q, sizeof(Q));
+    }
+    free(Om);
+    return lost;
+}
+
+/* ---------------------------------------------------------------------- */
+/* exported entry points                                                  */
+/* ---------------------------------------------------------------------- */
+
+int orc_real_size(void) { return (int)sizeof(real); }
+
+/* Validate a lattice as the tracker reads it: Romberg order k needs every
+ * spin-carrying element's slice count divisible by 2^k. */
+int orc_check_lattice(const orc_element* els, int n_el, int K) {
+    if (K < 0 || K > ORC_MAX_ORDER) return -1;
+    for (int i = 0; i < n_el; ++i) {
+        const orc_element* e = &els[i];
+        if (e->type < 0 || e->type > ORC_SNAKE) return -1;
+        if (e->type == ORC_MULT || e->type == ORC_QUAD_MK || e->type == ORC_SBEND) {
+            if (e->n_slices < 1 || (e->n_slices % (1 << K)) != 0) return -1;
+            if (e->L == 0.0) return -1;
+        }
+        if (e->type == ORC_SBEND && (e->angle == 0.0 || e->eta == 0.0)) return -1;
+    }
+    return 0;
+}
+
+/* Track n particles for n_turns turns.  z is [6][n] (X, Px, Y, Py, T, Pt),
+ * S is [3][n]; lost[n] flags (input and output).  Returns 0, or -1 for an
+ * invalid lattice. */
+int orc_track(const orc_element* els, int n_el, double G, double Ggamma0, long n,
+              real* z, real* S, uint8_t* lost, int n_turns, int K, int n_threads) {
+    if (orc_check_lattice(els, n_el, K)) return -1;
+    orc_ref r = make_ref(G, Ggamma0);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (long p = 0; p < n; ++p) {
+        if (lost[p]) continue;
+        orc_orbit o = {z[0 * n + p], z[1 * n + p], z[2 * n + p], z[3 * n + p], z[4 * n + p], z[5 * n + p]};
+        real s[3] = {S[0 * n + p], S[1 * n + p], S[2 * n + p]};
+        int is_lost = 0;
+        for (int t = 0; t < n_turns && !is_lost; ++t) {
+            for (int i = 0; i < n_el; ++i) {
+                orc_orbit o0 = o;
+                real s0[3] = {s[0], s[1], s[2]};
+                if (track_element(&r, &els[i], &o, s, K, NULL, NULL)) {
+                    o = o0;
+                    s[0] = s0[0]; s[1] = s0[1]; s[2] = s0[2];
+                    is_lost = 1;
+                    break;
+                }
+            }
+        }
+        z[0 * n + p] = o.X; z[1 * n + p] = o.Px; z[2 * n + p] = o.Y;
+        z[3 * n + p] = o.Py; z[4 * n + p] = o.T; z[5 * n + p] = o.Pt;
+        S[0 * n + p] = s[0]; S[1 * n + p] = s[1]; S[2 * n + p] = s[2];
+        lost[p] = (uint8_t)is_lost;
+    }
+    return 0;
+}
+
+/* One particle (z6 in/out, S3 in/out) through one element, also returning the
+ * trapezoid levels Q_00..Q_0K ([K+1][4], may be NULL) and the normalised
+ * element rotation ([4], may be NULL).  Returns 0, 1 (lost) or -1. */
+int orc_element_detail(const orc_element* e, double G, double Ggamma0, real* z6, real* S3,
+                       int K, real* levels, real* Q) {
+    if (orc_check_lattice(e, 1, K)) return -1;
+    orc_ref r = make_ref(G, Ggamma0);
+    orc_orbit o = {z6[0], z6[1], z6[2], z6[3], z6[4], z6[5]};
+    int rc = track_element(&r, e, &o, S3, K, levels, Q);
+    z6[0] = o.X; z6[1] = o.Px; z6[2] = o.Y; z6[3] = o.Py; z6[4] = o.T; z6[5] = o.Pt;
+    return rc;
+}
+
+/* Orbit-only map of one element over its full length with its slicing
+ * (n_slices slices; a negative L runs the map backwards).  Returns 0 / 1. */
+int orc_orbit_map(const orc_element* e, double G, double Ggamma0, real* z6) {
+    orc_ref r = make_ref(G, Ggamma0);
+    orc_orbit o = {z6[0], z6[1], z6[2], z6[3], z6[4], z6[5]};
+    int rc = 0;
+    if (e->type == ORC_DRIFT) {
+        rc = drift(&r, &o, e->L);
+    } else if (e->type == ORC_SNAKE) {
+        rc = 0;
+    } else {
+        if (e->n_slices < 1) return -1;
+        double ds = e->L / e->n_slices;
+        for (int i = 0; i < e->n_slices && !rc; ++i) rc = slice_map(&r, e, &o, ds);
+    }
+    z6[0] = o.X; z6[1] = o.Px; z6[2] = o.Y; z6[3] = o.Py; z6[4] = o.T; z6[5] = o.Pt;
+    return rc;
+}
+
+/* Individual sub-flows, for the tests that pin them one by one:
+ * which = 0 drift, 1 multipole kick, 2 quadrupole linear flow H_qL,
+ *         3 quadrupole nonlinear flow H_qNL, 4 sector bend. */
+int orc_subflow(int which, double G, double Ggamma0, real* z6, double s, double k1, double k2,
+                double h, double eta) {
+    orc_ref r = make_ref(G, Ggamma0);
+    orc_orbit o = {z6[0], z6[1], z6[2], z6[3], z6[4], z6[5]};
+    int rc = 0;
+    switch (which) {
+    case 0: rc = drift(&r, &o, s); break;
+    case 1: mult_kick(&o, k1, k2, s); break;
+    case 2: quad_linear(&r, &o, k1, s); break;
+    case 3: rc = quad_nonlinear(&r, &o, s); break;
+    case 4: rc = sbend_map(&r, &o, h, eta, s); break;
+    default: return -1;
+    }
+    z6[0] = o.X; z6[1] = o.Px; z6[2] = o.Y; z6[3] = o.Py; z6[4] = o.T; z6[5] = o.Pt;
+    return rc;
+}
+
+/* Precession vector Omega of Eq. (6b) at state z6 inside element e. */
+int orc_omega(const orc_element* e, double G, double Ggamma0, const real* z6, real* out3) {
+    orc_ref r = make_ref(G, Ggamma0);
+    orc_orbit o = {z6[0], z6[1], z6[2], z6[3], z6[4], z6[5]};
+    return omega(&r, e, &o, out3);
+}

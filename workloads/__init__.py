@@ -1,0 +1,257 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the bench.
+
+This module only *describes* inputs: ring lattices as lists of element dicts
+and particle ensembles as float64 arrays.  It holds none of the tracking
+arithmetic (no orbit map, no precession vector, no quaternion); both the CPU
+oracle and the CUDA library receive exactly the same element list and the same
+uploaded doubles.
+
+Element dict keys (all lengths in m, strengths in the paper's normalised form
+b/(B rho), Sec. 2.1 and Sec. 3):
+
+    type       "drift" | "mult" (drift-kick-drift multipole, Sec. 3.4)
+               | "quad_mk" (matrix-kick quadrupole, Sec. 3.3)
+               | "sbend" (exact bend-kick sector bend, Sec. 3.1)
+               | "snake" (thin spin rotator, Sec. 5)
+    L          length
+    n_slices   number of integration slices (spin-carrying elements)
+    k1         quadrupole gradient b2/(B rho)            [m^-2]
+    k2         sextupole strength  B''/(B rho) (MAD k2)  [m^-3]
+    angle      bend angle h*L of a sector bend           [rad]
+    eta        field ratio eta = b1/(h B rho), Eq. (9)
+    snake_phi  snake axis angle from the longitudinal axis, in the x-s plane
+    snake_mu   snake rotation angle
+
+The ring description dict: {"G", "Ggamma0", "elements": [...], "name"}.
+
+Particle ensembles follow the Gaussian recipe of the toy proton ring: sigma_x =
+sigma_y = 1 mm, sigma_px = sigma_py = 0.1 mrad, sigma_T = 1 cm, sigma_delta =
+1e-3 (relative momentum deviation), spins along y.  The energy coordinate Pt of
+Eq. (2) is obtained from delta through the definition of Pt and of the scale
+momentum p0 (input preparation, not part of the tracked map).
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, List
+
+import numpy as np
+
+G_PROTON = 1.7928
+
+ELEMENT_TYPES = ("drift", "mult", "quad_mk", "sbend", "snake")
+SPIN_TYPES = ("mult", "quad_mk", "sbend")
+
+
+def element(type: str, L: float = 0.0, n_slices: int = 1, k1: float = 0.0,
+            k2: float = 0.0, angle: float = 0.0, eta: float = 1.0,
+            snake_phi: float = 0.0, snake_mu: float = 0.0, name: str = "") -> Dict:
+    if type not in ELEMENT_TYPES:
+        raise ValueError(f"unknown element type {type!r}")
+    return dict(type=type, L=float(L), n_slices=int(n_slices), k1=float(k1),
+                k2=float(k2), angle=float(angle), eta=float(eta),
+                snake_phi=float(snake_phi), snake_mu=float(snake_mu),
+                name=name or type)
+
+
+def slices_for_order(base: int, spin_order: int) -> int:
+    """Smallest multiple of 2**spin_order that is >= base (Romberg needs the
+    slice count divisible by 2**k, Sec. 4.3)."""
+    m = 1 << spin_order
+    return max(m, ((base + m - 1) // m) * m)
+
+
+def with_spin_order(ring: Dict, spin_order: int) -> Dict:
+    """Copy of `ring` whose spin-carrying elements have slice counts valid for
+    Romberg order `spin_order`."""
+    out = dict(ring)
+    out["elements"] = []
+    for e in ring["elements"]:
+        e = dict(e)
+        if e["type"] in SPIN_TYPES:
+            e["n_slices"] = slices_for_order(e["n_slices"], spin_order)
+        out["elements"].append(e)
+    return out
+
+
+def reference(Ggamma0: float, G: float = G_PROTON):
+    """(gamma0, beta0) of the scale momentum for a given naive spin tune."""
+    gamma0 = Ggamma0 / G
+    beta0 = math.sqrt(1.0 - 1.0 / (gamma0 * gamma0))
+    return gamma0, beta0
+
+
+# ---------------------------------------------------------------------------
+# rings
+# ---------------------------------------------------------------------------
+
+def toy_ring(Ggamma0: float = 45.5, n_cells: int = 8, k1: float = 0.05,
+             quad_slices: int = 4, bend_slices: int = 4) -> Dict:
+    """Toy proton ring: 8 FODO cells of QF(1 m, k1=+0.05, DKD) D(2) B(3 m,
+    2pi/16, BK) D(2) QD(1 m, k1=-0.05, DKD) D(2) B D(2); 64 elements, 128 m."""
+    ang = 2.0 * math.pi / (2 * n_cells)
+    els = []
+    for c in range(n_cells):
+        els += [
+            element("mult", L=1.0, n_slices=quad_slices, k1=+k1, name=f"QF{c}"),
+            element("drift", L=2.0, name=f"D{c}a"),
+            element("sbend", L=3.0, n_slices=bend_slices, angle=ang, name=f"B{c}a"),
+            element("drift", L=2.0, name=f"D{c}b"),
+            element("mult", L=1.0, n_slices=quad_slices, k1=-k1, name=f"QD{c}"),
+            element("drift", L=2.0, name=f"D{c}c"),
+            element("sbend", L=3.0, n_slices=bend_slices, angle=ang, name=f"B{c}b"),
+            element("drift", L=2.0, name=f"D{c}d"),
+        ]
+    return dict(name="toy_proton_ring", G=G_PROTON, Ggamma0=float(Ggamma0), elements=els)
+
+
+def rhic_like_ring(Ggamma0: float = 45.5, n_cells: int = 108, k1: float = 0.03,
+                   k2: float = 0.5, base_slices: int = 4, sext_slices: int = 2,
+                   snakes: bool = True, quad_type: str = "quad_mk") -> Dict:
+    """RHIC-scale synthetic ring: n_cells FODO cells of
+    QF(1, +k1, MK) SF(0.2, +k2, DKD) D(1.8) B(3) D(2) B(3) D(2)
+    QD(1, -k1, MK) SD(0.2, -k2, DKD) D(1.8) B(3) D(2) B(3) D(2),
+    26 m per cell, 4*n_cells sector dipoles of angle 2pi/(4 n_cells), and two
+    ideal Siberian snakes (pi rotations about horizontal axes at +-45 deg from
+    the longitudinal axis): one at s=0, one after cell n_cells/2 - 1."""
+    ang = 2.0 * math.pi / (4 * n_cells)
+    els = []
+    half = n_cells // 2
+    if snakes:
+        els.append(element("snake", snake_phi=+math.pi / 4, snake_mu=math.pi, name="SNK1"))
+    for c in range(n_cells):
+        els += [
+            element(quad_type, L=1.0, n_slices=base_slices, k1=+k1, name=f"QF{c}"),
+            element("mult", L=0.2, n_slices=sext_slices, k2=+k2, name=f"SF{c}"),
+            element("drift", L=1.8, name=f"D{c}a"),
+            element("sbend", L=3.0, n_slices=base_slices, angle=ang, name=f"B{c}a"),
+            element("drift", L=2.0, name=f"D{c}b"),
+            element("sbend", L=3.0, n_slices=base_slices, angle=ang, name=f"B{c}b"),
+            element("drift", L=2.0, name=f"D{c}c"),
+            element(quad_type, L=1.0, n_slices=base_slices, k1=-k1, name=f"QD{c}"),
+            element("mult", L=0.2, n_slices=sext_slices, k2=-k2, name=f"SD{c}"),
+            element("drift", L=1.8, name=f"D{c}d"),
+            element("sbend", L=3.0, n_slices=base_slices, angle=ang, name=f"B{c}c"),
+            element("drift", L=2.0, name=f"D{c}e"),
+            element("sbend", L=3.0, n_slices=base_slices, angle=ang, name=f"B{c}d"),
+            element("drift", L=2.0, name=f"D{c}f"),
+        ]
+        if snakes and c == half - 1:
+            els.append(element("snake", snake_phi=-math.pi / 4, snake_mu=math.pi, name="SNK2"))
+    return dict(name=f"rhic_like_{n_cells}cells", G=G_PROTON, Ggamma0=float(Ggamma0), elements=els)
+
+
+def batched_jobs(n_jobs: int = 64, seed: int = 20240603, turns: int = 500,
+                 min_cells: int = 8, max_cells: int = 108,
+                 min_particles: int = 1000, max_particles: int = 100000) -> List[Dict]:
+    """Uneven batch: rings with U{min_cells..max_cells} cells (the RHIC-like
+    layout scaled to the cell count, snakes only for an even cell count),
+    G*gamma0 ~ U[45.5, 487], particle counts log-uniform in
+    [min_particles, max_particles], every job `turns` turns."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for j in range(n_jobs):
+        cells = int(rng.integers(min_cells, max_cells + 1))
+        gg = float(rng.uniform(45.5, 487.0))
+        n = int(round(10.0 ** rng.uniform(math.log10(min_particles), math.log10(max_particles))))
+        ring = rhic_like_ring(Ggamma0=gg, n_cells=cells, snakes=(cells % 2 == 0))
+        jobs.append(dict(ring=ring, n_particles=n, turns=turns, seed=seed * 1000 + j))
+    return jobs
+
+
+def single_element_ring(el: Dict, Ggamma0: float, G: float = G_PROTON) -> Dict:
+    return dict(name="single_" + el["type"], G=G, Ggamma0=float(Ggamma0), elements=[dict(el)])
+
+
+def count_passes(ring: Dict, n_particles: int, n_turns: int) -> int:
+    """Particle-element passes: one particle through one element (drifts and
+    snakes included)."""
+    return len(ring["elements"]) * n_particles * n_turns
+
+
+# ---------------------------------------------------------------------------
+# particles
+# ---------------------------------------------------------------------------
+
+def delta_to_pt(delta: np.ndarray, Ggamma0: float, G: float = G_PROTON) -> np.ndarray:
+    """Energy coordinate Pt of Eq. (2) for relative momentum deviation delta:
+    with P = p/p0 = 1 + delta and m c^2/(p0 c) = 1/(beta0 gamma0),
+    Pt = sqrt(P^2 + 1/(beta0 gamma0)^2) - 1/beta0."""
+    gamma0, beta0 = reference(Ggamma0, G)
+    inv_bg = 1.0 / (beta0 * gamma0)
+    return np.sqrt((1.0 + delta) ** 2 + inv_bg * inv_bg) - 1.0 / beta0
+
+
+DEFAULT_SIGMAS = dict(x=1e-3, px=1e-4, y=1e-3, py=1e-4, t=1e-2, delta=1e-3)
+
+
+def gaussian_particles(n: int, Ggamma0: float, seed: int, sigmas: Dict = None,
+                       G: float = G_PROTON, spin=(0.0, 1.0, 0.0), cut: float = None):
+    """6D Gaussian ensemble.  Returns (z, S): z is float64 [6, n] in the order
+    (X, Px, Y, Py, T, Pt) of Eq. (1); S is float64 [3, n] (x, y, s components).
+    `cut` truncates each normal deviate at +-cut sigma (resampling)."""
+    s = dict(DEFAULT_SIGMAS)
+    if sigmas:
+        s.update(sigmas)
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((6, n))
+    if cut is not None:
+        bad = np.abs(g) > cut
+        while bad.any():
+            g[bad] = rng.standard_normal(int(bad.sum()))
+            bad = np.abs(g) > cut
+    z = np.empty((6, n), dtype=np.float64)
+    z[0] = s["x"] * g[0]
+    z[1] = s["px"] * g[1]
+    z[2] = s["y"] * g[2]
+    z[3] = s["py"] * g[3]
+    z[4] = s["t"] * g[4]
+    z[5] = delta_to_pt(s["delta"] * g[5], Ggamma0, G)
+    S = np.zeros((3, n), dtype=np.float64)
+    S[0], S[1], S[2] = spin
+    return z, S
+
+
+def cap_spins(n: int, alpha: float, seed: int) -> np.ndarray:
+    """Unit spins uniformly distributed on the cap of opening angle alpha about
+    the vertical y axis (quasi-random cap sampling used for the quadrupole
+    spin-error maps of Sec. 5.2).  Uses the area-uniform parametrisation
+    cos(theta) ~ U[cos(alpha), 1]."""
+    rng = np.random.default_rng(seed)
+    ct = rng.uniform(math.cos(alpha), 1.0, n)
+    ph = rng.uniform(0.0, 2.0 * math.pi, n)
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    S = np.empty((3, n))
+    S[0] = st * np.cos(ph)
+    S[1] = ct
+    S[2] = st * np.sin(ph)
+    return S
+
+
+# The paper's single-particle test case (Sec. 5.2, footnote on the
+# single-element error study): X = 1 mm, Px = 0.1 mrad, Py = -0.2 mrad,
+# delta = 1e-3, Y = T = 0, spin ~ (0.1952, 0.9759, 0.0976).
+def footnote_particle(Ggamma0: float, G: float = G_PROTON):
+    z = np.array([[1e-3], [1e-4], [0.0], [-2e-4], [0.0],
+                  [float(delta_to_pt(np.array(1e-3), Ggamma0, G))]])
+    s = np.array([0.1952, 0.9759, 0.0976])
+    s = s / np.linalg.norm(s)
+    return z, s.reshape(3, 1)
+
+
+# Named workloads (the five benchmark configurations, by what they are).
+def workload(name: str, spin_order: int = 2, Ggamma0: float = None):
+    """Returns dict(ring, n_particles, turns, spin_order, seed)."""
+    if name == "toy_ring_1024":
+        ring = toy_ring(45.5 if Ggamma0 is None else Ggamma0)
+        return dict(ring=with_spin_order(ring, spin_order), n_particles=1024,
+                    turns=100, spin_order=spin_order, seed=1501)
+    if name == "rhic_like_1e5":
+        ring = rhic_like_ring(45.5 if Ggamma0 is None else Ggamma0)
+        return dict(ring=with_spin_order(ring, spin_order), n_particles=100000,
+                    turns=1000, spin_order=spin_order, seed=3450)
+    if name == "rhic_like_1e6_mixed":
+        ring = rhic_like_ring(45.5 if Ggamma0 is None else Ggamma0)
+        return dict(ring=with_spin_order(ring, spin_order), n_particles=1000000,
+                    turns=1000, spin_order=spin_order, seed=3451)
+    raise KeyError(name)
