@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Throughput benchmark: particle-element passes per second of the spin-orbit
+tracker on the RHIC-scale synthetic ring (108 FODO cells, 432 sector bends,
+matrix-kick quadrupoles, drift-kick sextupoles, two Siberian snakes; 1514
+elements per turn), 10^5 Gaussian protons per GPU, G*gamma0 = 45.5,
+Romberg order 2.
+
+One step = one turn of the whole ensemble through the ring (every element,
+all slices, the spin step included).  `value` is measured with the particle
+state resident in HBM; `e2e` includes, every step, the upload of the state
+from pinned host memory through the C ABI and the download of spins, orbit
+and lost flags.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py --impl reference ...     # the CPU oracle, timed on host cores
+
+For N > 1 (torchrun) each rank tracks its own 10^5 particles (weak scaling,
+no data-path collective); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "rhic_like_1e5"
+L2_BYTES = 126 * 1024 * 1024
+
+# FP64 floating-point operations the FP64 tracker executes per particle-element
+# pass on this workload (2 per DFMA, 1 per DADD/DMUL), from the thread-level
+# instruction counters of one ncu capture (profiles/track_fp64_rhic_like_ncu.md).
+# None until measured for the current kernel.
+FP64_FLOPS_PER_PASS = None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--spin-order", type=int, default=2)
+    ap.add_argument("--ggamma", type=float, default=45.5)
+    ap.add_argument("--particles", type=int, default=None, help="override particles per GPU")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu_index)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(ring, z, S, spin_order, seconds_target=10.0):
+    """Time the FP64 oracle on a bounded sample of the workload; returns
+    (passes/s, sample description, threads)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    n_el = len(ring["elements"])
+    probe_n = min(z.shape[1], 4 * threads)
+    t0 = time.perf_counter()
+    oracle.track(ring, z[:, :probe_n], S[:, :probe_n], 1, spin_order, n_threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    rate = probe_n * n_el / dt
+    n = int(min(z.shape[1], max(threads, rate * seconds_target / n_el)))
+    t0 = time.perf_counter()
+    oracle.track(ring, z[:, :n], S[:, :n], 1, spin_order, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return n * n_el / dt, f"{n} particles x 1 turn of the {n_el}-element ring ({dt:.1f} s)", threads, n
+
+
+def run_reference(args):
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return 0
+    w = W.workload(WORKLOAD, spin_order=args.spin_order, Ggamma0=args.ggamma)
+    ring = w["ring"]
+    n_el = len(ring["elements"])
+    npart = args.particles or w["n_particles"]
+    z, S = W.gaussian_particles(npart, args.ggamma, seed=w["seed"])
+    import oracle
+    threads = os.cpu_count() or 1
+    # size each step for about 10 s of host work, so K + W steps stay within minutes
+    _, _, _, n_step = oracle_rate(ring, z, S, args.spin_order, seconds_target=min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle.track(ring, z[:, :n_step], S[:, :n_step], 1, args.spin_order, n_threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.track(ring, z[:, :n_step], S[:, :n_step], 1, args.spin_order, n_threads=threads)
+    dt = time.perf_counter() - t0
+    value = n_step * n_el * args.steps / dt
+    sample = f"{n_step} of {npart} particles x 1 turn per step ({n_el} elements)"
+    out = {
+        "impl": "reference", "metric": "particle-element passes/s", "value": value,
+        "unit": "passes/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: 108-cell RHIC-like ring, Ggamma={args.ggamma}, "
+                   f"Romberg order {args.spin_order}", "particles_per_gpu": npart,
+                   "elements_per_turn": n_el, "precision": "fp64", "parallelism": f"replicas{args.gpus}"},
+        "cpu_baseline": {"value": value, "unit": "passes/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "passes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1501_03450_b300 as st
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    w = W.workload(WORKLOAD, spin_order=args.spin_order, Ggamma0=args.ggamma)
+    ring = w["ring"]
+    n_el = len(ring["elements"])
+    npart = args.particles or w["n_particles"]
+    z, S = W.gaussian_particles(npart, args.ggamma, seed=w["seed"] + rank)
+    K = args.spin_order
+
+    stream = torch.cuda.Stream()
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, npart, args.precision, stream=stream.cuda_stream)
+    tr.set_launch(block_threads=128, turns_per_launch=1)
+    tr.upload(z, S)
+    fp64_peak, fp32_peak = st.st_measure_peaks()
+
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    launches_per_step = 1
+
+    # warm-up
+    for _ in range(args.warmup):
+        tr.track(1, K)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local_rank
+    sampler = ClockSampler(gpu_index)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()                      # evict L2 between steps (outside the timed events)
+            starts[i].record(stream)
+            tr.track(1, K)
+            ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_sum = sum(step_ms) * 1e-3
+    if dist:
+        tt = torch.tensor([t_sum], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_sum = float(tt.item())
+    passes_per_rank = npart * n_el * args.steps
+    value = passes_per_rank * world / t_sum
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        zh = torch.from_numpy(z).pin_memory()
+        Sh = torch.from_numpy(S).pin_memory()
+        zo = torch.empty_like(zh).pin_memory()
+        So = torch.empty_like(Sh).pin_memory()
+        lo = torch.empty(npart, dtype=torch.uint8).pin_memory()
+        e2e_steps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            st.st_particles_upload(tr.handle, zh.data_ptr(), Sh.data_ptr(), 0)
+            tr.track(1, K)
+            st.st_spins_download(tr.handle, So.data_ptr(), zo.data_ptr(), lo.data_ptr(), 0)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": npart * n_el * e2e_steps * world / te, "unit": "passes/s",
+               "h2d_bytes_per_step": 9 * 8 * npart, "d2h_bytes_per_step": 9 * 8 * npart + npart}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the tracking kernel ---------------------------------
+    peak = fp64_peak if args.precision == "fp64" else fp32_peak
+    avg_launch_s = t_sum / (args.steps * launches_per_step)
+    if args.precision == "fp64" and FP64_FLOPS_PER_PASS:
+        achieved = FP64_FLOPS_PER_PASS * npart * n_el / avg_launch_s / 1e12
+    else:
+        achieved = None
+    roofline = {"bound": "alu", "pipe": "fp64" if args.precision == "fp64" else "fp32",
+                "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": (achieved / (peak / 1e12)) if achieved else None, "traffic": None,
+                "peak_source": "measured by st_measure_peaks (independent FMA chains) at run time"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, sample, threads, _ = oracle_rate(ring, z, S, K)
+        cpu = {"value": rate, "unit": "passes/s", "cores": threads, "kind": "oracle", "sample": sample}
+
+    out = {
+        "metric": "particle-element passes/s", "value": value, "unit": "passes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: 108-cell RHIC-like ring (1514 elements/turn), "
+                   f"{npart} Gaussian protons per GPU, Ggamma={args.ggamma}, Romberg order {K}, 1 turn per step",
+                   "particles_per_gpu": npart, "elements_per_turn": n_el, "precision": args.precision,
+                   "spin_order": K, "turns_per_step": 1, "parallelism": f"replicas{world}",
+                   "l2": "flushed between steps (2x L2 buffer written outside the timed events)"},
+        "e2e": e2e,
+        "gpu_launches": args.steps * launches_per_step,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "wall_s_timed": wall,
+        "peaks_measured": {"fp64_tflops": fp64_peak / 1e12, "fp32_tflops": fp32_peak / 1e12},
+    }
+    print(json.dumps(out))
+    tr.close()
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,153 @@
+/*
+ * spintrack -- spin-orbit tracking of a particle ensemble through a ring
+ * lattice on one NVIDIA B300 (sm_103a).
+ *
+ * The tracked method is that of Abell, Meiser, Ranjbar, Barber, "Accurate and
+ * efficient spin integration for particle accelerators" (arXiv:1501.03450):
+ *   - orbit in the canonical variables z = (X, Px, Y, Py, T, Pt) of Sec. 2.1,
+ *     Eqs. (1)-(3): X, Y, T in metres, Px, Py, Pt scaled by the reference
+ *     momentum p0 (Pt by p0 c);
+ *   - exact sector bends ("bend-kick", Sec. 3.1, Eq. (10)), matrix-kick
+ *     quadrupoles (Sec. 3.3, Eqs. (21)-(27)), drift-kick-drift multipoles
+ *     (Sec. 3.4, Eqs. (28)-(29)), exact drifts, thin Siberian snakes (Sec. 5);
+ *   - spin precession from the Thomas-BMT equation in s (Sec. 2.2, Eq. (6b)),
+ *     integrated per element by trapezoid-weighted edge rotations composed as
+ *     unit quaternions, later slices on the left (Sec. 4.1, Eq. (37)), at the
+ *     2^k sub-sampled step sizes of Eq. (38), extrapolated with the Romberg
+ *     table of Eq. (39) and normalised per element (Sec. 4.3).
+ *
+ * Conventions of this library (the paper leaves them open):
+ *   - quaternions are Hamilton, scalar first; the spin is rotated actively;
+ *   - "spin_order" k is the number of Romberg iterations (result Q_kk);
+ *   - the drift-kick-drift slice is half drift, kick, half drift; slice edges
+ *     are the states between slices, edge 0 the element entrance;
+ *   - particle gamma = gamma0 (1 + beta0 Pt) enters Eq. (6b);
+ *   - a particle whose longitudinal momentum becomes imaginary is lost: its
+ *     state is frozen at the entrance of that element and its lost flag set.
+ *
+ * All functions return ST_OK (0) or a negative error code; st_last_error()
+ * gives a message for the calling thread.  No function throws.  One process,
+ * one GPU; the library owns every device buffer it allocates.
+ */
+#ifndef SPINTRACK_H
+#define SPINTRACK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define ST_OK        0
+#define ST_EINVAL   -1   /* invalid argument or lattice                          */
+#define ST_ENOMEM   -2   /* device or host allocation failed                     */
+#define ST_ECUDA    -3   /* CUDA runtime error (message in st_last_error)        */
+#define ST_ETIMEOUT -4   /* a bounded device-side wait gave up (status word set) */
+#define ST_ESTATE   -5   /* call out of order (e.g. track before upload)         */
+
+/* ---- element kinds --------------------------------------------------- */
+#define ST_DRIFT    0   /* exact drift, flow of H_drift (Eq. (29b)); no spin step      */
+#define ST_MULT     1   /* normal quadrupole k1 + sextupole k2, drift-kick-drift slices
+                           (Sec. 3.4); field b = (k1 Y + k2 X Y, k1 X + k2 (X^2-Y^2)/2)  */
+#define ST_QUAD_MK  2   /* quadrupole k1, matrix-kick slices H_qL/2 H_qNL H_qL/2 (Eq. (27)) */
+#define ST_SBEND    3   /* sector bend of curvature h = angle/L and field ratio eta
+                           (Eq. (9)), exact map Eq. (10) per slice                       */
+#define ST_SNAKE    4   /* thin, orbit-transparent spin rotation by snake_mu about the
+                           horizontal axis (sin snake_phi, 0, cos snake_phi)            */
+
+/* ---- precision of a tracking context ---------------------------------- */
+#define ST_FP64   0   /* all arithmetic in IEEE double                                 */
+#define ST_MIXED  1   /* FP32 slice arithmetic with compensated coordinates, FP64
+                         per-turn spin composition (see st_ctx_create)                 */
+
+typedef struct st_lattice st_lattice;   /* opaque; immutable after creation          */
+typedef struct st_ctx st_ctx;           /* opaque; particle state on the device      */
+
+/* One beamline element.  Units: metres, radians; k1 = b2/(B rho) [m^-2],
+ * k2 = B''/(B rho) [m^-3] (MAD convention).  n_slices is the number of
+ * integration slices of a spin-carrying element (ST_MULT, ST_QUAD_MK,
+ * ST_SBEND) and must be a multiple of 2^spin_order at st_track time. */
+typedef struct {
+    int32_t type;
+    int32_t n_slices;
+    double L;
+    double k1;
+    double k2;
+    double angle;
+    double eta;
+    double snake_phi;
+    double snake_mu;
+} st_element;
+
+/* Reference particle: anomaly G and naive spin tune G*gamma0 of the scale
+ * momentum p0 (gamma0 = Ggamma0/G, beta0 = sqrt(1 - 1/gamma0^2)); protons,
+ * positive rigidity. */
+typedef struct {
+    double G;
+    double Ggamma0;
+} st_reference;
+
+/* Build a lattice from n >= 1 elements (host array, copied).  Element tables
+ * are deduplicated and packed with per-element constants, then copied to the
+ * current CUDA device.  Errors: ST_EINVAL (n < 1, unknown type, L <= 0 or
+ * n_slices < 1 for a spin-carrying element, angle == 0 or eta == 0 for a bend,
+ * G*gamma0 <= G), ST_ENOMEM, ST_ECUDA.  *out is set only on success. */
+int st_lattice_create(const st_element* elems, int32_t n, const st_reference* ref,
+                      st_lattice** out);
+int st_lattice_destroy(st_lattice* lat);
+
+/* Create a tracking context for n_particles >= 1 particles on the current
+ * device.  precision is ST_FP64 or ST_MIXED.  cuda_stream is a cudaStream_t
+ * (e.g. torch.cuda.current_stream().cuda_stream) or NULL for a stream owned by
+ * the context.  Allocates the device state (orbit as (X,Px), (Y,Py), (T,Pt)
+ * double2 arrays, spin, lost flags) and a staging buffer.  The lattice must
+ * outlive the context. */
+int st_ctx_create(const st_lattice* lat, int64_t n_particles, int32_t precision,
+                  void* cuda_stream, st_ctx** out);
+int st_ctx_destroy(st_ctx* ctx);
+
+/* Load particle state.  z_soa is [6][n] doubles (X, Px, Y, Py, T, Pt rows);
+ * spin_soa is [3][n] doubles (x, y, s components of unit spins).  Pointers are
+ * host memory (src_is_device = 0; read during the call) or device memory of
+ * the current device (src_is_device = 1; read asynchronously on the context
+ * stream).  Clears the lost flags.  Errors: ST_EINVAL for NULL pointers. */
+int st_particles_upload(st_ctx* ctx, const double* z_soa, const double* spin_soa,
+                        int32_t src_is_device);
+
+/* Track every particle for n_turns >= 0 turns with Romberg order spin_order
+ * (0..4).  Asynchronous on the context stream.  Errors: ST_ESTATE before the
+ * first upload, ST_EINVAL for n_turns < 0, spin_order outside 0..4 or a
+ * spin-carrying element whose n_slices is not a multiple of 2^spin_order,
+ * ST_ECUDA on a launch failure. */
+int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order);
+
+/* Copy the tracked state out: spin_soa [3][n] (required), z_soa [6][n] and
+ * lost [n] (each may be NULL), to host (dst_is_device = 0) or device memory.
+ * Synchronises the context stream.  Returns ST_ETIMEOUT if a kernel reported
+ * a bounded-wait failure, ST_ECUDA on an asynchronous CUDA error. */
+int st_spins_download(st_ctx* ctx, double* spin_soa, double* z_soa, uint8_t* lost,
+                      int32_t dst_is_device);
+
+/* Launch shape used by st_track: threads per block (32..1024, multiple of 32)
+ * and turns per kernel launch (>= 1).  0 keeps the current value.  These are
+ * the knobs the autotuner sweeps. */
+int st_ctx_set_launch(st_ctx* ctx, int32_t block_threads, int32_t turns_per_launch);
+
+/* Measure the current device's sustained fused-multiply-add throughput in
+ * FP64 and in FP32 (flop/s, two flops per FMA) with independent FMA chains
+ * timed by CUDA events (about 0.2 s).  These are the denominators of the
+ * trackers' arithmetic roofline.  Errors: ST_EINVAL (NULL), ST_ECUDA. */
+int st_measure_peaks(double* fp64_flops, double* fp32_flops);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* st_last_error(void);
+
+/* Library version string. */
+const char* st_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPINTRACK_H */

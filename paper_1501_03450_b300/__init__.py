@@ -1,0 +1,230 @@
+"""Python binding of the spintrack C ABI (include/spintrack.h).
+
+Argument marshalling only: every step of the tracking runs in the CUDA
+library `libspintrack.so` built in-tree for sm_103a.  If the library is
+missing the import of the binding functions fails loudly; there is no CPU
+fallback.  PyTorch is used by callers only for device memory and streams
+(pass `tensor.data_ptr()` with `*_is_device=1` and
+`torch.cuda.current_stream().cuda_stream`).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ESTATE = 0, -1, -2, -3, -4, -5
+ST_DRIFT, ST_MULT, ST_QUAD_MK, ST_SBEND, ST_SNAKE = 0, 1, 2, 3, 4
+ST_FP64, ST_MIXED = 0, 1
+
+TYPE_CODES = {"drift": ST_DRIFT, "mult": ST_MULT, "quad_mk": ST_QUAD_MK, "sbend": ST_SBEND, "snake": ST_SNAKE}
+PRECISIONS = {"fp64": ST_FP64, "mixed": ST_MIXED}
+
+
+class StElement(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("n_slices", ctypes.c_int32), ("L", ctypes.c_double),
+                ("k1", ctypes.c_double), ("k2", ctypes.c_double), ("angle", ctypes.c_double),
+                ("eta", ctypes.c_double), ("snake_phi", ctypes.c_double), ("snake_mu", ctypes.c_double)]
+
+
+class StReference(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_double), ("Ggamma0", ctypes.c_double)]
+
+
+class SpinTrackError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"spintrack error {code}: {msg}")
+        self.code = code
+
+
+# Every symbol declared in include/spintrack.h, with its ctypes signature.
+_VP = ctypes.c_void_p
+SIGNATURES = {
+    "st_lattice_create": ([ctypes.POINTER(StElement), ctypes.c_int32, ctypes.POINTER(StReference),
+                           ctypes.POINTER(_VP)], ctypes.c_int),
+    "st_lattice_destroy": ([_VP], ctypes.c_int),
+    "st_ctx_create": ([_VP, ctypes.c_int64, ctypes.c_int32, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "st_ctx_destroy": ([_VP], ctypes.c_int),
+    "st_particles_upload": ([_VP, _VP, _VP, ctypes.c_int32], ctypes.c_int),
+    "st_track": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "st_spins_download": ([_VP, _VP, _VP, _VP, ctypes.c_int32], ctypes.c_int),
+    "st_ctx_set_launch": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "st_measure_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "st_last_error": ([], ctypes.c_char_p),
+    "st_version": ([], ctypes.c_char_p),
+}
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libspintrack.so (building it with nvcc if it is missing or stale
+    and `build_if_missing`).  Raises if the library cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"spintrack CUDA library not found at {LIB_PATH}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != ST_OK:
+        raise SpinTrackError(rc, load().st_last_error().decode())
+    return rc
+
+
+def last_error() -> str:
+    return load().st_last_error().decode()
+
+
+def elements_array(elements: List[Dict]):
+    arr = (StElement * len(elements))()
+    for i, e in enumerate(elements):
+        arr[i] = StElement(TYPE_CODES[e["type"]], int(e["n_slices"]), e["L"], e["k1"], e["k2"], e["angle"],
+                           e["eta"], e["snake_phi"], e["snake_mu"])
+    return arr
+
+
+# ---- thin wrappers with the C names --------------------------------------
+
+def st_lattice_create(elements: List[Dict], G: float, Ggamma0: float) -> int:
+    lib = load()
+    arr = elements_array(elements)
+    ref = StReference(G, Ggamma0)
+    out = _VP()
+    _check(lib.st_lattice_create(arr, len(elements), ctypes.byref(ref), ctypes.byref(out)))
+    return out.value
+
+
+def st_lattice_destroy(lat: int) -> None:
+    _check(load().st_lattice_destroy(lat))
+
+
+def st_ctx_create(lat: int, n_particles: int, precision: int = ST_FP64, stream: Optional[int] = None) -> int:
+    out = _VP()
+    _check(load().st_ctx_create(lat, int(n_particles), int(precision), stream, ctypes.byref(out)))
+    return out.value
+
+
+def st_ctx_destroy(ctx: int) -> None:
+    _check(load().st_ctx_destroy(ctx))
+
+
+def st_particles_upload(ctx: int, z_ptr: int, s_ptr: int, src_is_device: int) -> None:
+    _check(load().st_particles_upload(ctx, z_ptr, s_ptr, int(src_is_device)))
+
+
+def st_track(ctx: int, n_turns: int, spin_order: int) -> None:
+    _check(load().st_track(ctx, int(n_turns), int(spin_order)))
+
+
+def st_spins_download(ctx: int, s_ptr: int, z_ptr: Optional[int], lost_ptr: Optional[int],
+                      dst_is_device: int) -> None:
+    _check(load().st_spins_download(ctx, s_ptr, z_ptr, lost_ptr, int(dst_is_device)))
+
+
+def st_ctx_set_launch(ctx: int, block_threads: int = 0, turns_per_launch: int = 0) -> None:
+    _check(load().st_ctx_set_launch(ctx, int(block_threads), int(turns_per_launch)))
+
+
+def st_measure_peaks():
+    """(fp64_flops, fp32_flops) of the current device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().st_measure_peaks(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+# ---- convenience object layer (still only marshalling) --------------------
+
+class Lattice:
+    def __init__(self, ring: Dict):
+        self.ring = ring
+        self.handle = st_lattice_create(ring["elements"], ring["G"], ring["Ggamma0"])
+        self.n_elements = len(ring["elements"])
+
+    def close(self):
+        if self.handle:
+            st_lattice_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tracker:
+    """Tracking context for one particle ensemble on the current device."""
+
+    def __init__(self, lattice: Lattice, n_particles: int, precision: str = "fp64", stream: Optional[int] = None):
+        self.lattice = lattice
+        self.n = int(n_particles)
+        self.handle = st_ctx_create(lattice.handle, self.n, PRECISIONS[precision], stream)
+
+    def set_launch(self, block_threads: int = 0, turns_per_launch: int = 0):
+        st_ctx_set_launch(self.handle, block_threads, turns_per_launch)
+
+    def upload(self, z: np.ndarray, S: np.ndarray):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        assert z.shape == (6, self.n) and S.shape == (3, self.n)
+        st_particles_upload(self.handle, z.ctypes.data, S.ctypes.data, 0)
+
+    def upload_device(self, z_ptr: int, s_ptr: int):
+        st_particles_upload(self.handle, z_ptr, s_ptr, 1)
+
+    def track(self, n_turns: int, spin_order: int):
+        st_track(self.handle, n_turns, spin_order)
+
+    def download(self):
+        z = np.empty((6, self.n), np.float64)
+        S = np.empty((3, self.n), np.float64)
+        lost = np.empty(self.n, np.uint8)
+        st_spins_download(self.handle, S.ctypes.data, z.ctypes.data, lost.ctypes.data, 0)
+        return z, S, lost
+
+    def download_device(self, s_ptr: int, z_ptr: Optional[int] = None, lost_ptr: Optional[int] = None):
+        st_spins_download(self.handle, s_ptr, z_ptr, lost_ptr, 1)
+
+    def close(self):
+        if self.handle:
+            st_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def track(ring: Dict, z: np.ndarray, S: np.ndarray, n_turns: int, spin_order: int, precision: str = "fp64",
+          block_threads: int = 0, turns_per_launch: int = 0):
+    """One-shot helper: host arrays in, host arrays out (z, S, lost)."""
+    lat = Lattice(ring)
+    tr = Tracker(lat, z.shape[1], precision)
+    try:
+        if block_threads or turns_per_launch:
+            tr.set_launch(block_threads, turns_per_launch)
+        tr.upload(z, S)
+        tr.track(n_turns, spin_order)
+        return tr.download()
+    finally:
+        tr.close()
+        lat.close()

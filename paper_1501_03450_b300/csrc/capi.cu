@@ -1,0 +1,387 @@
+// C ABI of the spintrack library: lattice packing, contexts, state upload and
+// download, and dispatch of the tracking kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "st_internal.cuh"
+
+namespace st {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return ST_ECUDA;
+}
+
+static bool is_spin_type(int t) { return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND; }
+
+// Precompute the per-element constants the kernels use (all in FP64).
+static DevElem pack_element(const st_element& e) {
+    DevElem d;
+    memset(&d, 0, sizeof(d));
+    d.type = e.type;
+    d.n_slices = is_spin_type(e.type) ? e.n_slices : 1;
+    switch (e.type) {
+    case ST_DRIFT:
+        d.ds = e.L;
+        break;
+    case ST_MULT:
+        d.ds = e.L / e.n_slices;
+        d.a[0] = e.k1;
+        d.a[1] = e.k2;
+        break;
+    case ST_QUAD_MK:
+        d.ds = e.L / e.n_slices;
+        d.a[0] = e.k1;
+        d.a[1] = std::fabs(e.k1);
+        break;
+    case ST_SBEND: {
+        d.ds = e.L / e.n_slices;
+        double h = e.angle / e.L;
+        d.a[0] = h;
+        d.a[1] = e.eta;
+        d.a[2] = std::cos(h * d.ds);
+        d.a[3] = std::sin(h * d.ds);
+        d.a[4] = 1.0 / (e.eta * h);
+        d.a[5] = 1.0 / e.eta;
+        break;
+    }
+    case ST_SNAKE: {
+        double c = std::cos(0.5 * e.snake_mu), s = std::sin(0.5 * e.snake_mu);
+        d.a[0] = c;
+        d.a[1] = s * std::sin(e.snake_phi);
+        d.a[2] = 0.0;
+        d.a[3] = s * std::cos(e.snake_phi);
+        break;
+    }
+    }
+    return d;
+}
+
+static bool same_elem(const DevElem& a, const DevElem& b) { return memcmp(&a, &b, sizeof(DevElem)) == 0; }
+
+}  // namespace st
+
+using namespace st;
+
+extern "C" {
+
+const char* st_last_error(void) { return g_err; }
+
+const char* st_version(void) { return "spintrack 0.1 (sm_103a)"; }
+
+int st_lattice_create(const st_element* elems, int32_t n, const st_reference* ref, st_lattice** out) {
+    if (!elems || !ref || !out || n < 1) {
+        set_error("st_lattice_create: null pointer or n < 1");
+        return ST_EINVAL;
+    }
+    if (n > 65535) {
+        set_error("st_lattice_create: at most 65535 elements per turn (got %d)", n);
+        return ST_EINVAL;
+    }
+    if (!(ref->G > 0.0) || !(ref->Ggamma0 > ref->G)) {
+        set_error("st_lattice_create: need G > 0 and Ggamma0 > G (gamma0 > 1)");
+        return ST_EINVAL;
+    }
+    for (int i = 0; i < n; ++i) {
+        const st_element& e = elems[i];
+        if (e.type < ST_DRIFT || e.type > ST_SNAKE) {
+            set_error("element %d: unknown type %d", i, e.type);
+            return ST_EINVAL;
+        }
+        if (is_spin_type(e.type) && (!(e.L > 0.0) || e.n_slices < 1 || e.n_slices > 4096)) {
+            set_error("element %d: spin-carrying element needs L > 0 and 1 <= n_slices <= 4096", i);
+            return ST_EINVAL;
+        }
+        if (e.type == ST_DRIFT && !(e.L >= 0.0)) {
+            set_error("element %d: drift needs L >= 0", i);
+            return ST_EINVAL;
+        }
+        if (e.type == ST_SBEND && (e.angle == 0.0 || e.eta == 0.0 || !std::isfinite(e.angle / e.L))) {
+            set_error("element %d: sector bend needs angle != 0 and eta != 0", i);
+            return ST_EINVAL;
+        }
+    }
+    st_lattice* lat = new (std::nothrow) st_lattice();
+    if (!lat) {
+        set_error("st_lattice_create: host allocation failed");
+        return ST_ENOMEM;
+    }
+    LatticeImpl& L = lat->impl;
+    L.ref.G = ref->G;
+    L.ref.gamma0 = ref->Ggamma0 / ref->G;
+    L.ref.beta0 = std::sqrt(1.0 - 1.0 / (L.ref.gamma0 * L.ref.gamma0));
+    L.ref.inv_beta0 = 1.0 / L.ref.beta0;
+    L.n_elements = n;
+
+    std::vector<DevElem> uniq;
+    std::vector<uint16_t> seq(n);
+    int max_slices = 1;
+    int min_pow2 = 30;
+    for (int i = 0; i < n; ++i) {
+        DevElem d = pack_element(elems[i]);
+        int idx = -1;
+        for (size_t u = 0; u < uniq.size(); ++u)
+            if (same_elem(uniq[u], d)) { idx = (int)u; break; }
+        if (idx < 0) {
+            idx = (int)uniq.size();
+            uniq.push_back(d);
+        }
+        seq[i] = (uint16_t)idx;
+        if (is_spin_type(d.type)) {
+            max_slices = std::max(max_slices, d.n_slices);
+            int p = 0;
+            while (((d.n_slices >> p) & 1) == 0 && p < 30) ++p;
+            min_pow2 = std::min(min_pow2, p);
+        }
+    }
+    if (uniq.size() > 2048) {
+        delete lat;
+        set_error("st_lattice_create: more than 2048 distinct elements");
+        return ST_EINVAL;
+    }
+    L.n_unique = (int)uniq.size();
+    L.max_slices = max_slices;
+    L.min_spin_slices_pow2 = min_pow2;
+    L.table_bytes = uniq.size() * sizeof(DevElem);
+    L.seq_offset = L.table_bytes;
+    size_t seq_bytes = ((size_t)n * sizeof(uint16_t) + 15) & ~(size_t)15;
+    L.blob_bytes = L.table_bytes + seq_bytes;
+    std::vector<unsigned char> blob(L.blob_bytes, 0);
+    memcpy(blob.data(), uniq.data(), L.table_bytes);
+    memcpy(blob.data() + L.seq_offset, seq.data(), (size_t)n * sizeof(uint16_t));
+    L.h_table = (DevElem*)malloc(L.table_bytes);
+    L.h_seq = (uint16_t*)malloc((size_t)n * sizeof(uint16_t));
+    if (!L.h_table || !L.h_seq) {
+        free(L.h_table);
+        free(L.h_seq);
+        delete lat;
+        set_error("st_lattice_create: host allocation failed");
+        return ST_ENOMEM;
+    }
+    memcpy(L.h_table, uniq.data(), L.table_bytes);
+    memcpy(L.h_seq, seq.data(), (size_t)n * sizeof(uint16_t));
+    cudaError_t e = cudaMalloc(&L.d_blob, L.blob_bytes);
+    if (e != cudaSuccess) {
+        free(L.h_table);
+        free(L.h_seq);
+        delete lat;
+        return cuda_fail(e, "st_lattice_create: cudaMalloc");
+    }
+    e = cudaMemcpy(L.d_blob, blob.data(), L.blob_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(L.d_blob);
+        free(L.h_table);
+        free(L.h_seq);
+        delete lat;
+        return cuda_fail(e, "st_lattice_create: cudaMemcpy");
+    }
+    *out = lat;
+    return ST_OK;
+}
+
+int st_lattice_destroy(st_lattice* lat) {
+    if (!lat) return ST_OK;
+    cudaFree(lat->impl.d_blob);
+    free(lat->impl.h_table);
+    free(lat->impl.h_seq);
+    delete lat;
+    return ST_OK;
+}
+
+static void free_ctx(st_ctx* c) {
+    cudaFree(c->xpx);
+    cudaFree(c->ypy);
+    cudaFree(c->tpt);
+    cudaFree(c->sxy);
+    cudaFree(c->sz);
+    cudaFree(c->lost);
+    cudaFree(c->staging);
+    cudaFree(c->status);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int st_ctx_create(const st_lattice* lat, int64_t n_particles, int32_t precision, void* cuda_stream,
+                  st_ctx** out) {
+    if (!lat || !out || n_particles < 1) {
+        set_error("st_ctx_create: null pointer or n_particles < 1");
+        return ST_EINVAL;
+    }
+    if (precision != ST_FP64 && precision != ST_MIXED) {
+        set_error("st_ctx_create: precision must be ST_FP64 or ST_MIXED");
+        return ST_EINVAL;
+    }
+    if (n_particles > (int64_t)1 << 31) {
+        set_error("st_ctx_create: at most 2^31 particles");
+        return ST_EINVAL;
+    }
+    st_ctx* c = new (std::nothrow) st_ctx();
+    if (!c) {
+        set_error("st_ctx_create: host allocation failed");
+        return ST_ENOMEM;
+    }
+    c->lat = lat;
+    c->n = n_particles;
+    c->precision = precision;
+    size_t n = (size_t)n_particles;
+    cudaError_t e = cudaSuccess;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(e, "st_ctx_create: stream");
+        }
+        c->own_stream = true;
+    }
+#define ST_ALLOC(ptr, bytes)                                      \
+    e = cudaMalloc((void**)&(ptr), (bytes));                      \
+    if (e != cudaSuccess) {                                       \
+        free_ctx(c);                                              \
+        set_error("st_ctx_create: cudaMalloc of %zu bytes failed: %s", (size_t)(bytes), cudaGetErrorString(e)); \
+        return ST_ENOMEM;                                         \
+    }
+    ST_ALLOC(c->xpx, n * sizeof(double2));
+    ST_ALLOC(c->ypy, n * sizeof(double2));
+    ST_ALLOC(c->tpt, n * sizeof(double2));
+    ST_ALLOC(c->sxy, n * sizeof(double2));
+    ST_ALLOC(c->sz, n * sizeof(double));
+    ST_ALLOC(c->lost, n);
+    ST_ALLOC(c->staging, 9 * n * sizeof(double));
+    ST_ALLOC(c->status, sizeof(int32_t));
+#undef ST_ALLOC
+    e = cudaMemsetAsync(c->status, 0, sizeof(int32_t), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->lost, 0, n, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return cuda_fail(e, "st_ctx_create: init");
+    }
+    *out = c;
+    return ST_OK;
+}
+
+int st_ctx_destroy(st_ctx* ctx) {
+    if (!ctx) return ST_OK;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+    return ST_OK;
+}
+
+int st_ctx_set_launch(st_ctx* ctx, int32_t block_threads, int32_t turns_per_launch) {
+    if (!ctx) {
+        set_error("st_ctx_set_launch: null context");
+        return ST_EINVAL;
+    }
+    if (block_threads != 0 && (block_threads < 32 || block_threads > 1024 || block_threads % 32)) {
+        set_error("st_ctx_set_launch: block_threads must be a multiple of 32 in [32, 1024]");
+        return ST_EINVAL;
+    }
+    if (turns_per_launch < 0) {
+        set_error("st_ctx_set_launch: turns_per_launch must be >= 1 (0 keeps)");
+        return ST_EINVAL;
+    }
+    if (block_threads) ctx->block_threads = block_threads;
+    if (turns_per_launch) ctx->turns_per_launch = turns_per_launch;
+    return ST_OK;
+}
+
+int st_particles_upload(st_ctx* ctx, const double* z_soa, const double* spin_soa, int32_t src_is_device) {
+    if (!ctx || !z_soa || !spin_soa) {
+        set_error("st_particles_upload: null pointer");
+        return ST_EINVAL;
+    }
+    size_t n = (size_t)ctx->n;
+    cudaError_t e;
+    const double* dz = z_soa;
+    const double* ds = spin_soa;
+    if (!src_is_device) {
+        e = cudaMemcpyAsync(ctx->staging, z_soa, 6 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->staging + 6 * n, spin_soa, 3 * n * sizeof(double), cudaMemcpyHostToDevice,
+                                ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "st_particles_upload: copy");
+        dz = ctx->staging;
+        ds = ctx->staging + 6 * n;
+    }
+    int rc = launch_pack(ctx, dz, ds);
+    if (rc) return rc;
+    e = cudaMemsetAsync(ctx->lost, 0, n, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "st_particles_upload: lost flags");
+    if (!src_is_device) {
+        // host buffers are only guaranteed valid during the call
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "st_particles_upload: sync");
+    }
+    ctx->uploaded = true;
+    return ST_OK;
+}
+
+int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order) {
+    if (!ctx) {
+        set_error("st_track: null context");
+        return ST_EINVAL;
+    }
+    if (!ctx->uploaded) {
+        set_error("st_track: no particles uploaded");
+        return ST_ESTATE;
+    }
+    if (n_turns < 0 || spin_order < 0 || spin_order > 4) {
+        set_error("st_track: need n_turns >= 0 and 0 <= spin_order <= 4");
+        return ST_EINVAL;
+    }
+    if (spin_order > ctx->lat->impl.min_spin_slices_pow2) {
+        set_error("st_track: spin_order %d needs every spin-carrying element's n_slices divisible by %d",
+                  spin_order, 1 << spin_order);
+        return ST_EINVAL;
+    }
+    if (n_turns == 0) return ST_OK;
+    if (ctx->precision == ST_FP64) return launch_track_fp64(ctx, n_turns, spin_order);
+    set_error("st_track: precision not available in this build");
+    return ST_EINVAL;
+}
+
+int st_spins_download(st_ctx* ctx, double* spin_soa, double* z_soa, uint8_t* lost, int32_t dst_is_device) {
+    if (!ctx || !spin_soa) {
+        set_error("st_spins_download: null pointer");
+        return ST_EINVAL;
+    }
+    if (!ctx->uploaded) {
+        set_error("st_spins_download: no particles uploaded");
+        return ST_ESTATE;
+    }
+    size_t n = (size_t)ctx->n;
+    int rc = launch_unpack(ctx, ctx->staging, ctx->staging + 6 * n);
+    if (rc) return rc;
+    cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpyAsync(spin_soa, ctx->staging + 6 * n, 3 * n * sizeof(double), kind, ctx->stream);
+    if (e == cudaSuccess && z_soa)
+        e = cudaMemcpyAsync(z_soa, ctx->staging, 6 * n * sizeof(double), kind, ctx->stream);
+    if (e == cudaSuccess && lost) e = cudaMemcpyAsync(lost, ctx->lost, n, kind, ctx->stream);
+    int32_t status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "st_spins_download");
+    if (status != STATUS_OK) {
+        set_error("st_spins_download: a tracking kernel reported status %d (bounded wait expired)", status);
+        return ST_ETIMEOUT;
+    }
+    return ST_OK;
+}
+
+}  // extern "C"

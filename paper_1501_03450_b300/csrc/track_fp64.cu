@@ -1,0 +1,410 @@
+// FP64 spin-orbit tracker: one persistent thread per particle holds the orbit
+// (X, Px, Y, Py, T; Pt is a constant of the motion in every element here), the
+// spin and the Romberg level products in registers for all turns of a launch.
+// The deduplicated lattice table and the element sequence sit in shared
+// memory (one bulk TMA copy per block); every element is uniform across the
+// block, so the element switch never diverges.
+//
+// Per element (Sec. 3 orbit maps, Sec. 4.3 spin):
+//   edge 0 = entrance: Omega (Eq. (6b)) -> edge rotation -> level products
+//   for each slice: orbit slice map, Omega at the new edge, edge rotation
+//   level products: the finest level K multiplies every edge rotation; level
+//   K-m every 2^m-th one, whose rotation by 2^m times the angle is obtained by
+//   squaring the edge quaternion m times; end edges start from half the
+//   angle (trapezoid weights of Eq. (38))
+//   Romberg table (Eq. (39)) in place over the K+1 level products, normalise,
+//   compose into the turn quaternion (later elements on the left).
+// The spin is rotated once per turn by the composed turn quaternion.
+#include <cstdio>
+
+#include "device_common.cuh"
+
+namespace st {
+
+struct Particle {
+    double X, Px, Y, Py, T;
+};
+
+struct PConst {
+    double Pt, P2, P, invP, b0pt, a, c;   // b0pt = 1/beta0 + Pt, a = 1 + G gamma, c = G (gamma - 1)
+};
+
+// Cached matrix-kick coefficients of the linear quadrupole flow over a half
+// slice for one (|k1|, s): trig plane and hyperbolic plane.
+struct QuadCache {
+    double key_k, key_s;
+    double C1, S1, al1, be1, ga1;   // cos plane
+    double C2, S2, al2, be2, ga2;   // cosh plane
+};
+
+__device__ __forceinline__ void quad_coeffs(QuadCache& qc, const PConst& pc, double absk1, double s) {
+    qc.key_k = absk1;
+    qc.key_s = s;
+    double w = sqrt(absk1 * pc.invP);
+    double ws = w * s;
+    if (w > 0.0) {
+        double sn, cs;
+        sincos(ws, &sn, &cs);
+        double e = exp(ws);
+        double ei = 1.0 / e;
+        double ch = 0.5 * (e + ei), sh = 0.5 * (e - ei);
+        double iw = 1.0 / w;
+        qc.C1 = cs;
+        qc.S1 = sn * iw;
+        qc.C2 = ch;
+        qc.S2 = sh * iw;
+    } else {
+        qc.C1 = qc.C2 = 1.0;
+        qc.S1 = qc.S2 = s;
+    }
+    // integrals over the half slice of C^2, S^2 (/2) used by the T update
+    qc.al1 = 0.5 * (s + qc.C1 * qc.S1);
+    qc.be1 = qc.S1 * qc.S1;
+    qc.ga1 = 0.5 * (s - qc.C1 * qc.S1);
+    qc.al2 = 0.5 * (s + qc.C2 * qc.S2);
+    qc.be2 = qc.S2 * qc.S2;
+    qc.ga2 = 0.5 * (s - qc.C2 * qc.S2);
+}
+
+// Linear quadrupole flow H_qL over s (Eq. (24)); per plane with focusing
+// constant K_u = +-k1/P: u' = u C + (pu/P) S, pu' = pu C - P K_u u S, and
+// T' = T - (1/beta0 + Pt)/(2 P^3) * sum_u [pu^2 (s + C S)/2 - P K_u u pu S^2
+//                                          + P^2 K_u u^2 (s - C S)/2].
+__device__ __forceinline__ void quad_linear(Particle& p, const PConst& pc, const QuadCache& qc, double k1) {
+    const bool foc = k1 >= 0.0;
+    const double Cx = foc ? qc.C1 : qc.C2, Sx = foc ? qc.S1 : qc.S2;
+    const double Cy = foc ? qc.C2 : qc.C1, Sy = foc ? qc.S2 : qc.S1;
+    const double alx = foc ? qc.al1 : qc.al2, bex = foc ? qc.be1 : qc.be2, gax = foc ? qc.ga1 : qc.ga2;
+    const double aly = foc ? qc.al2 : qc.al1, bey = foc ? qc.be2 : qc.be1, gay = foc ? qc.ga2 : qc.ga1;
+    double X = p.X, Px = p.Px, Y = p.Y, Py = p.Py;
+    double Pk = pc.P * k1;   // P^2 K_x = P k1
+    double tsum = Px * Px * alx - k1 * X * Px * bex + Pk * X * X * gax
+                + Py * Py * aly + k1 * Y * Py * bey - Pk * Y * Y * gay;
+    double f = 0.5 * pc.b0pt * pc.invP * pc.invP * pc.invP;
+    p.T -= f * tsum;
+    p.X = X * Cx + Px * pc.invP * Sx;
+    p.Px = Px * Cx - k1 * X * Sx;
+    p.Y = Y * Cy + Py * pc.invP * Sy;
+    p.Py = Py * Cy + k1 * Y * Sy;
+}
+
+// Precession vector Omega (Eq. (6b)) for a transverse field b = (bx, by, 0),
+// frame curvature h; ips = 1/Ps, Ps = longitudinal momentum.
+__device__ __forceinline__ void precession(const Particle& p, const PConst& pc, double bx, double by, double h,
+                                           double ips, double Ps, double& ox, double& oy, double& os) {
+    double ub = (p.Px * bx + p.Py * by) * pc.invP;   // u . b
+    double pre = -(1.0 + h * p.X) * ips;
+    double cu = pc.c * ub * pc.invP;                 // G (gamma-1) (u.b) / P
+    ox = pre * (pc.a * bx - cu * p.Px);
+    oy = pre * (pc.a * by - cu * p.Py) + h;
+    os = -pre * cu * Ps;
+}
+
+template <int K>
+struct LevelProducts {
+    Quat q[K + 1];
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int k = 0; k <= K; ++k) q[k] = Quat{1.0, 0.0, 0.0, 0.0};
+    }
+    // edge i of N (N divisible by 2^K): multiply the edge rotation into every
+    // level that samples this edge
+    __device__ __forceinline__ void add_edge(int i, int N, double ds, double ox, double oy, double os) {
+        double w = (i == 0 || i == N) ? 0.5 * ds : ds;
+        Quat e = quat_from_rotvec(w * ox, w * oy, w * os);
+        q[K] = qmul(e, q[K]);
+#pragma unroll
+        for (int m = 1; m <= K; ++m) {
+            if (i & ((1 << m) - 1)) break;
+            e = qsquare(e);
+            q[K - m] = qmul(e, q[K - m]);
+        }
+    }
+    // Romberg table, Eq. (39b), in place (column j -> j+1), then normalise
+    __device__ __forceinline__ Quat romberg() {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const double f = (double)(1 << (2 * (j + 1)));
+            const double inv = 1.0 / (f - 1.0);
+#pragma unroll
+            for (int k = K; k >= j + 1; --k) {
+                q[k].w = (f * q[k].w - q[k - 1].w) * inv;
+                q[k].x = (f * q[k].x - q[k - 1].x) * inv;
+                q[k].y = (f * q[k].y - q[k - 1].y) * inv;
+                q[k].z = (f * q[k].z - q[k - 1].z) * inv;
+            }
+        }
+        return qnormalize(q[K]);
+    }
+};
+
+template <int K>
+__global__ void __launch_bounds__(128) track_fp64_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
+                                                         uint32_t seq_offset, int n_seq, RefConst ref,
+                                                         double2* __restrict__ xpx, double2* __restrict__ ypy,
+                                                         double2* __restrict__ tpt, double2* __restrict__ sxy,
+                                                         double* __restrict__ szp, uint8_t* __restrict__ lost,
+                                                         int n, int n_turns, int32_t* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t bar;
+    if (!stage_to_smem(smem, blob, blob_bytes, &bar, status)) return;
+    const DevElem* table = (const DevElem*)smem;
+    const uint16_t* seq = (const uint16_t*)(smem + seq_offset);
+
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || lost[i]) return;
+
+    Particle p;
+    double2 v = xpx[i];
+    p.X = v.x;
+    p.Px = v.y;
+    v = ypy[i];
+    p.Y = v.x;
+    p.Py = v.y;
+    v = tpt[i];
+    p.T = v.x;
+    PConst pc;
+    pc.Pt = v.y;
+    pc.P2 = 1.0 + 2.0 * pc.Pt * ref.inv_beta0 + pc.Pt * pc.Pt;
+    pc.invP = rsqrt(pc.P2);
+    pc.P = pc.P2 * pc.invP;
+    pc.b0pt = ref.inv_beta0 + pc.Pt;
+    const double gamma = ref.gamma0 * (1.0 + ref.beta0 * pc.Pt);
+    pc.a = 1.0 + ref.G * gamma;
+    pc.c = ref.G * (gamma - 1.0);
+    v = sxy[i];
+    double sx = v.x, sy = v.y, sz = szp[i];
+
+    QuadCache qc;
+    qc.key_k = -1.0;
+    qc.key_s = 0.0;
+    LevelProducts<K> lv;
+    bool is_lost = false;
+
+    for (int turn = 0; turn < n_turns && !is_lost; ++turn) {
+        Quat qt{1.0, 0.0, 0.0, 0.0};
+        for (int e = 0; e < n_seq; ++e) {
+            const DevElem& el = table[seq[e]];
+            const int type = el.type;
+            if (type == ST_SNAKE) {
+                qt = qmul(Quat{el.a[0], el.a[1], el.a[2], el.a[3]}, qt);
+                continue;
+            }
+            const Particle p0 = p;
+            if (type == ST_DRIFT) {
+                double L = el.ds;
+                double ips = rsqrt(pc.P2 - p.Px * p.Px - p.Py * p.Py);
+                p.X += L * p.Px * ips;
+                p.Y += L * p.Py * ips;
+                p.T += L * (ref.inv_beta0 - pc.b0pt * ips);
+                if (!isfinite(p.X + p.Y + p.T)) {
+                    p = p0;
+                    is_lost = true;
+                    break;
+                }
+                continue;
+            }
+            // spin-carrying element
+            const int N = el.n_slices;
+            const double ds = el.ds;
+            lv.reset();
+            double ox, oy, os;
+            if (type == ST_SBEND) {
+                const double h = el.a[0], eta = el.a[1], cb = el.a[2], sb = el.a[3], ieh = el.a[4],
+                             ieta = el.a[5];
+                const double Pa2 = pc.P2 - p.Py * p.Py;
+                const double iPa = rsqrt(Pa2);
+                double ps2 = Pa2 - p.Px * p.Px;
+                double ips = rsqrt(ps2);
+                double Ps = ps2 * ips;
+                double psi = asin(p.Px * iPa);
+                const double by = eta * h;
+                precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
+                lv.add_edge(0, N, ds, ox, oy, os);
+                const double dY = ieta * p.Py * ds;
+                const double dT = -ieta * pc.Pt * ds + (1.0 - ieta) * ds * ref.inv_beta0;
+                for (int s = 1; s <= N; ++s) {
+                    // exact sector-bend map over ds, Eq. (10): (Px, A = Ps - eta(1+hX))
+                    // rotates by h ds; X follows from Ps - A = eta (1 + hX)
+                    double A = Ps - eta * (1.0 + h * p.X);
+                    double Pxf = p.Px * cb + A * sb;
+                    double Af = A * cb - p.Px * sb;
+                    ps2 = Pa2 - Pxf * Pxf;
+                    ips = rsqrt(ps2);
+                    Ps = ps2 * ips;
+                    p.X = (Ps - Af - eta) * ieh;
+                    p.Px = Pxf;
+                    double psif = asin(Pxf * iPa);
+                    double dpsi = psi - psif;
+                    psi = psif;
+                    p.Y += dY + ieh * p.Py * dpsi;
+                    p.T += dT - ieh * pc.b0pt * dpsi;
+                    precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
+                    lv.add_edge(s, N, ds, ox, oy, os);
+                }
+            } else if (type == ST_MULT) {
+                const double k1 = el.a[0], k2 = el.a[1];
+                const double half = 0.5 * ds;
+                double ips = rsqrt(pc.P2 - p.Px * p.Px - p.Py * p.Py);
+                double Ps = (pc.P2 - p.Px * p.Px - p.Py * p.Py) * ips;
+                double bx = k1 * p.Y + k2 * p.X * p.Y;
+                double by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
+                precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
+                lv.add_edge(0, N, ds, ox, oy, os);
+                for (int s = 1; s <= N; ++s) {
+                    p.X += half * p.Px * ips;
+                    p.Y += half * p.Py * ips;
+                    p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
+                    by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
+                    bx = k1 * p.Y + k2 * p.X * p.Y;
+                    p.Px -= ds * by;
+                    p.Py += ds * bx;
+                    double ps2 = pc.P2 - p.Px * p.Px - p.Py * p.Py;
+                    ips = rsqrt(ps2);
+                    Ps = ps2 * ips;
+                    p.X += half * p.Px * ips;
+                    p.Y += half * p.Py * ips;
+                    p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
+                    bx = k1 * p.Y + k2 * p.X * p.Y;
+                    by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
+                    precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
+                    lv.add_edge(s, N, ds, ox, oy, os);
+                }
+            } else {   // ST_QUAD_MK
+                const double k1 = el.a[0], absk = el.a[1];
+                const double half = 0.5 * ds;
+                if (qc.key_k != absk || qc.key_s != half) quad_coeffs(qc, pc, absk, half);
+                double ps2 = pc.P2 - p.Px * p.Px - p.Py * p.Py;
+                double ips = rsqrt(ps2);
+                double Ps = ps2 * ips;
+                precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
+                lv.add_edge(0, N, ds, ox, oy, os);
+                for (int s = 1; s <= N; ++s) {
+                    quad_linear(p, pc, qc, k1);
+                    // nonlinear remainder H_qNL over ds, Eq. (25)
+                    double pp = p.Px * p.Px + p.Py * p.Py;
+                    ps2 = pc.P2 - pp;
+                    ips = rsqrt(ps2);
+                    double d = ips - pc.invP;
+                    p.X += ds * p.Px * d;
+                    p.Y += ds * p.Py * d;
+                    p.T += -ds * pc.b0pt * (ips - pc.invP * pp / (2.0 * pc.P2)) + ds * ref.inv_beta0;
+                    quad_linear(p, pc, qc, k1);
+                    ps2 = pc.P2 - p.Px * p.Px - p.Py * p.Py;
+                    ips = rsqrt(ps2);
+                    Ps = ps2 * ips;
+                    precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
+                    lv.add_edge(s, N, ds, ox, oy, os);
+                }
+            }
+            Quat qe = lv.romberg();
+            if (!isfinite(p.X + p.Px + p.Y + p.Py + p.T + qe.w + qe.x + qe.y + qe.z)) {
+                p = p0;
+                is_lost = true;
+                break;
+            }
+            qt = qmul(qe, qt);
+        }
+        qt = qnormalize(qt);
+        rotate_vec(qt, sx, sy, sz);
+    }
+    xpx[i] = make_double2(p.X, p.Px);
+    ypy[i] = make_double2(p.Y, p.Py);
+    tpt[i].x = p.T;
+    sxy[i] = make_double2(sx, sy);
+    szp[i] = sz;
+    if (is_lost) lost[i] = 1;
+}
+
+__global__ void pack_kernel(const double* __restrict__ z, const double* __restrict__ s, double2* xpx, double2* ypy,
+                            double2* tpt, double2* sxy, double* sz, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    xpx[i] = make_double2(z[i], z[n + i]);
+    ypy[i] = make_double2(z[2 * n + i], z[3 * n + i]);
+    tpt[i] = make_double2(z[4 * n + i], z[5 * n + i]);
+    sxy[i] = make_double2(s[i], s[n + i]);
+    sz[i] = s[2 * n + i];
+}
+
+__global__ void unpack_kernel(double* __restrict__ z, double* __restrict__ s, const double2* xpx, const double2* ypy,
+                              const double2* tpt, const double2* sxy, const double* sz, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 a = xpx[i], b = ypy[i], c = tpt[i], d = sxy[i];
+    z[i] = a.x;
+    z[n + i] = a.y;
+    z[2 * n + i] = b.x;
+    z[3 * n + i] = b.y;
+    z[4 * n + i] = c.x;
+    z[5 * n + i] = c.y;
+    s[i] = d.x;
+    s[n + i] = d.y;
+    s[2 * n + i] = sz[i];
+}
+
+int launch_pack(st_ctx* ctx, const double* z, const double* s) {
+    int64_t n = ctx->n;
+    int threads = 256;
+    unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    pack_kernel<<<blocks, threads, 0, ctx->stream>>>(z, s, ctx->xpx, ctx->ypy, ctx->tpt, ctx->sxy, ctx->sz, n);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "pack kernel launch");
+}
+
+int launch_unpack(st_ctx* ctx, double* z, double* s) {
+    int64_t n = ctx->n;
+    int threads = 256;
+    unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    unpack_kernel<<<blocks, threads, 0, ctx->stream>>>(z, s, ctx->xpx, ctx->ypy, ctx->tpt, ctx->sxy, ctx->sz, n);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "unpack kernel launch");
+}
+
+template <int K>
+static int launch_k(st_ctx* ctx, int n_turns) {
+    const LatticeImpl& L = ctx->lat->impl;
+    const int threads = ctx->block_threads;
+    const unsigned blocks = (unsigned)((ctx->n + threads - 1) / threads);
+    const size_t smem = L.blob_bytes;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(track_fp64_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fp64 tracker)");
+        attr_set = true;
+    }
+    const int tpl = ctx->turns_per_launch;
+    for (int t = 0; t < n_turns; t += tpl) {
+        int nt = n_turns - t < tpl ? n_turns - t : tpl;
+        track_fp64_kernel<K><<<blocks, threads, smem, ctx->stream>>>(
+            L.d_blob, (uint32_t)L.blob_bytes, (uint32_t)L.seq_offset, L.n_elements, L.ref, ctx->xpx, ctx->ypy,
+            ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "fp64 tracker launch");
+    }
+    return ST_OK;
+}
+
+int launch_track_fp64(st_ctx* ctx, int n_turns, int spin_order) {
+    if (ctx->lat->impl.blob_bytes > 200 * 1024) {
+        set_error("lattice table of %zu bytes exceeds the 200 KiB shared-memory budget",
+                  ctx->lat->impl.blob_bytes);
+        return ST_EINVAL;
+    }
+    if (ctx->block_threads > 128) {
+        set_error("fp64 tracker: block_threads must be <= 128");
+        return ST_EINVAL;
+    }
+    switch (spin_order) {
+    case 0: return launch_k<0>(ctx, n_turns);
+    case 1: return launch_k<1>(ctx, n_turns);
+    case 2: return launch_k<2>(ctx, n_turns);
+    case 3: return launch_k<3>(ctx, n_turns);
+    case 4: return launch_k<4>(ctx, n_turns);
+    }
+    set_error("spin_order out of range");
+    return ST_EINVAL;
+}
+
+}  // namespace st

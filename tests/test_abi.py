@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI (no GPU needed): the shared library builds,
+loads, and exports every function include/spintrack.h declares; argument
+validation that happens before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1501_03450_b300 as st
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if not fn.endswith(".h"):
+            continue
+        txt = open(os.path.join(inc, fn)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(st_\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("st_lattice_create", "st_particles_upload", "st_track", "st_spins_download"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = st.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in st.SIGNATURES, f"binding lacks a signature for {name}"
+
+
+def test_version_and_error_string():
+    lib = st.load()
+    assert b"sm_103a" in lib.st_version()
+    assert isinstance(lib.st_last_error(), bytes)
+
+
+def test_lattice_validation_happens_on_host():
+    lib = st.load()
+    out = ctypes.c_void_p()
+    ref = st.StReference(1.7928, 45.5)
+    # n < 1
+    assert lib.st_lattice_create(None, 0, ctypes.byref(ref), ctypes.byref(out)) == st.ST_EINVAL
+    # unknown type
+    arr = st.elements_array([dict(type="drift", L=1.0, n_slices=1, k1=0, k2=0, angle=0, eta=1,
+                                  snake_phi=0, snake_mu=0)])
+    arr[0].type = 9
+    assert lib.st_lattice_create(arr, 1, ctypes.byref(ref), ctypes.byref(out)) == st.ST_EINVAL
+    assert b"unknown type" in lib.st_last_error()
+    # bend with zero angle
+    arr = st.elements_array([dict(type="sbend", L=1.0, n_slices=4, k1=0, k2=0, angle=0.0, eta=1,
+                                  snake_phi=0, snake_mu=0)])
+    assert lib.st_lattice_create(arr, 1, ctypes.byref(ref), ctypes.byref(out)) == st.ST_EINVAL
+    # gamma0 <= 1
+    bad = st.StReference(1.7928, 1.0)
+    arr = st.elements_array([dict(type="drift", L=1.0, n_slices=1, k1=0, k2=0, angle=0, eta=1,
+                                  snake_phi=0, snake_mu=0)])
+    assert lib.st_lattice_create(arr, 1, ctypes.byref(bad), ctypes.byref(out)) == st.ST_EINVAL
+    assert out.value is None
+
+
+def test_null_context_calls_are_rejected():
+    lib = st.load()
+    assert lib.st_track(None, 1, 2) == st.ST_EINVAL
+    assert lib.st_particles_upload(None, None, None, 0) == st.ST_EINVAL
+    assert lib.st_spins_download(None, None, None, None, 0) == st.ST_EINVAL
+    assert lib.st_ctx_set_launch(None, 64, 1) == st.ST_EINVAL
+    assert lib.st_ctx_destroy(None) == st.ST_OK
+    assert lib.st_lattice_destroy(None) == st.ST_OK
