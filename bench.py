@@ -43,7 +43,7 @@ L2_BYTES = 126 * 1024 * 1024
 # pass on this workload (2 per DFMA, 1 per DADD/DMUL), from the thread-level
 # instruction counters of one ncu capture (profiles/track_fp64_rhic_like_ncu.md).
 # None until measured for the current kernel.
-FP64_FLOPS_PER_PASS = None
+FP64_FLOPS_PER_PASS = 662.3
 
 
 def parse_args():
