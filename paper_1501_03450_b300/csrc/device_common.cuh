@@ -124,8 +124,8 @@ __device__ __forceinline__ Quat qnormalize(const Quat& a) {
     return Quat{a.w * r, a.x * r, a.y * r, a.z * r};
 }
 
-// Unit quaternion of the rotation by |w| about w^.
-__device__ __forceinline__ Quat quat_from_rotvec(double wx, double wy, double wz) {
+// Unit quaternion of the rotation by |w| about w^, with library sincos.
+__device__ __forceinline__ Quat quat_from_rotvec_lib(double wx, double wy, double wz) {
     double th2 = wx * wx + wy * wy + wz * wz;
     if (th2 > 0.0) {
         double r = rsqrt(th2);
@@ -136,6 +136,67 @@ __device__ __forceinline__ Quat quat_from_rotvec(double wx, double wy, double wz
         return Quat{c, f * wx, f * wy, f * wz};
     }
     return Quat{1.0, 0.0, 0.0, 0.0};
+}
+
+// Taylor coefficients of cos(t/2) and sin(t/2)/t as power series in u = t^2:
+//   cos(t/2)   = sum_n (-1)^n u^n / (4^n (2n)!)
+//   sin(t/2)/t = sum_n (-1)^n u^n / (2 4^n (2n+1)!)
+// (exact rationals, fixed at compile time by template recursion).
+template <int N> struct Fact { static constexpr double v = (double)N * Fact<N - 1>::v; };
+template <> struct Fact<0> { static constexpr double v = 1.0; };
+template <int N> struct Pow4 { static constexpr double v = 4.0 * Pow4<N - 1>::v; };
+template <> struct Pow4<0> { static constexpr double v = 1.0; };
+template <int N> struct HalfCosCoef {
+    static constexpr double v = (N % 2 ? -1.0 : 1.0) / (Pow4<N>::v * Fact<2 * N>::v);
+};
+template <int N> struct HalfSincCoef {
+    static constexpr double v = (N % 2 ? -1.0 : 1.0) / (2.0 * Pow4<N>::v * Fact<2 * N + 1>::v);
+};
+
+template <int N>
+struct HalfAngleHorner {   // continues Horner's rule from degree N down to 0
+    static __device__ __forceinline__ void step(double u, double& c, double& f) {
+        c = fma(c, u, HalfCosCoef<N>::v);
+        f = fma(f, u, HalfSincCoef<N>::v);
+        HalfAngleHorner<N - 1>::step(u, c, f);
+    }
+};
+template <>
+struct HalfAngleHorner<-1> {
+    static __device__ __forceinline__ void step(double, double&, double&) {}
+};
+
+template <int DEG>
+__device__ __forceinline__ void half_angle_series(double u, double& c, double& f) {
+    c = HalfCosCoef<DEG>::v;
+    f = HalfSincCoef<DEG>::v;
+    HalfAngleHorner<DEG - 1>::step(u, c, f);
+}
+
+// Unit quaternion of the rotation by |w| about w^ without library calls:
+// q = (cos(t/2), sin(t/2)/t * w) with t^2 = w.w, both even functions of t
+// evaluated as truncated Taylor series in u = t^2 (degree 5 for u <= 0.04,
+// degree 11 for u <= 4; truncation below 1e-20 relative).  Larger angles are
+// halved until u <= 4 and the quaternion squared back.
+__device__ __forceinline__ Quat quat_from_rotvec(double wx, double wy, double wz) {
+    double u = wx * wx + wy * wy + wz * wz;
+    double c, f;
+    if (u <= 0.04) {
+        half_angle_series<5>(u, c, f);
+        return Quat{c, f * wx, f * wy, f * wz};
+    }
+    int m = 0;
+    double scale = 1.0;
+    while (u > 4.0 && m < 60) {
+        u *= 0.25;
+        scale *= 0.5;
+        ++m;
+    }
+    half_angle_series<11>(u, c, f);
+    f *= scale;
+    Quat q{c, f * wx, f * wy, f * wz};
+    for (int k = 0; k < m; ++k) q = qsquare(q);
+    return q;
 }
 
 // S <- Q S conj(Q) for a unit quaternion Q.

@@ -139,7 +139,7 @@ struct LevelProducts {
 };
 
 template <int K>
-__global__ void __launch_bounds__(128) track_fp64_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
+__global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
                                                          uint32_t seq_offset, int n_seq, RefConst ref,
                                                          double2* __restrict__ xpx, double2* __restrict__ ypy,
                                                          double2* __restrict__ tpt, double2* __restrict__ sxy,
@@ -151,8 +151,17 @@ __global__ void __launch_bounds__(128) track_fp64_kernel(const void* __restrict_
     const DevElem* table = (const DevElem*)smem;
     const uint16_t* seq = (const uint16_t*)(smem + seq_offset);
 
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || lost[i]) return;
+    // Every block owns a contiguous, equal share of whole warps of particles;
+    // the grid is (#SMs x resident blocks per SM), so every SM gets the same
+    // amount of FP64 work.
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int64_t n_warps = ((int64_t)n + 31) / 32;
+    const int64_t w_begin = (int64_t)blockIdx.x * n_warps / gridDim.x;
+    const int64_t w_end = (int64_t)(blockIdx.x + 1) * n_warps / gridDim.x;
+    for (int64_t wi = w_begin + (threadIdx.x >> 5); wi < w_end; wi += wpb) {
+    const int64_t i = wi * 32 + lane;
+    if (i >= n || lost[i]) continue;
 
     Particle p;
     double2 v = xpx[i];
@@ -213,11 +222,10 @@ __global__ void __launch_bounds__(128) track_fp64_kernel(const void* __restrict_
                 const double h = el.a[0], eta = el.a[1], cb = el.a[2], sb = el.a[3], ieh = el.a[4],
                              ieta = el.a[5];
                 const double Pa2 = pc.P2 - p.Py * p.Py;
-                const double iPa = rsqrt(Pa2);
+                const double iPa2 = 1.0 / Pa2;
                 double ps2 = Pa2 - p.Px * p.Px;
                 double ips = rsqrt(ps2);
                 double Ps = ps2 * ips;
-                double psi = asin(p.Px * iPa);
                 const double by = eta * h;
                 precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
                 lv.add_edge(0, N, ds, ox, oy, os);
@@ -226,17 +234,26 @@ __global__ void __launch_bounds__(128) track_fp64_kernel(const void* __restrict_
                 for (int s = 1; s <= N; ++s) {
                     // exact sector-bend map over ds, Eq. (10): (Px, A = Ps - eta(1+hX))
                     // rotates by h ds; X follows from Ps - A = eta (1 + hX)
+                    const double Pxi = p.Px, Psi = Ps;
                     double A = Ps - eta * (1.0 + h * p.X);
-                    double Pxf = p.Px * cb + A * sb;
-                    double Af = A * cb - p.Px * sb;
+                    double Pxf = Pxi * cb + A * sb;
+                    double Af = A * cb - Pxi * sb;
                     ps2 = Pa2 - Pxf * Pxf;
                     ips = rsqrt(ps2);
                     Ps = ps2 * ips;
                     p.X = (Ps - Af - eta) * ieh;
                     p.Px = Pxf;
-                    double psif = asin(Pxf * iPa);
-                    double dpsi = psi - psif;
-                    psi = psif;
+                    // asin(Px_i/P_a) - asin(Px_f/P_a) = asin(sin of the difference),
+                    // sin(psi_i - psi_f) = (Px_i Ps_f - Px_f Ps_i) / P_a^2
+                    const double sd = (Pxi * Ps - Pxf * Psi) * iPa2;
+                    double dpsi;
+                    if (fabs(sd) < 1e-2) {
+                        const double x2 = sd * sd;   // Taylor series of asin, truncation < 1e-21 relative
+                        dpsi = sd * fma(x2, fma(x2, fma(x2, fma(x2, 35.0 / 1152.0, 5.0 / 112.0), 3.0 / 40.0),
+                                                1.0 / 6.0), 1.0);
+                    } else {
+                        dpsi = asin(sd);
+                    }
                     p.Y += dY + ieh * p.Py * dpsi;
                     p.T += dT - ieh * pc.b0pt * dpsi;
                     precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
@@ -314,6 +331,7 @@ __global__ void __launch_bounds__(128) track_fp64_kernel(const void* __restrict_
     sxy[i] = make_double2(sx, sy);
     szp[i] = sz;
     if (is_lost) lost[i] = 1;
+    }  // particle loop
 }
 
 __global__ void pack_kernel(const double* __restrict__ z, const double* __restrict__ s, double2* xpx, double2* ypy,
@@ -365,7 +383,6 @@ template <int K>
 static int launch_k(st_ctx* ctx, int n_turns) {
     const LatticeImpl& L = ctx->lat->impl;
     const int threads = ctx->block_threads;
-    const unsigned blocks = (unsigned)((ctx->n + threads - 1) / threads);
     const size_t smem = L.blob_bytes;
     static bool attr_set = false;
     if (!attr_set) {
@@ -374,13 +391,28 @@ static int launch_k(st_ctx* ctx, int n_turns) {
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fp64 tracker)");
         attr_set = true;
     }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_fp64_kernel<K>, threads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "fp64 tracker occupancy query");
+    if (per_sm < 1) {
+        set_error("fp64 tracker: block of %d threads with %zu B shared memory does not fit on an SM", threads,
+                  smem);
+        return ST_EINVAL;
+    }
+    // never more blocks than warps of particles
+    const int64_t n_warps = (ctx->n + 31) / 32;
+    int64_t grid = (int64_t)sms * per_sm;
+    if (grid > n_warps) grid = n_warps;
     const int tpl = ctx->turns_per_launch;
     for (int t = 0; t < n_turns; t += tpl) {
         int nt = n_turns - t < tpl ? n_turns - t : tpl;
-        track_fp64_kernel<K><<<blocks, threads, smem, ctx->stream>>>(
+        track_fp64_kernel<K><<<(unsigned)grid, threads, smem, ctx->stream>>>(
             L.d_blob, (uint32_t)L.blob_bytes, (uint32_t)L.seq_offset, L.n_elements, L.ref, ctx->xpx, ctx->ypy,
             ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status);
-        cudaError_t e = cudaGetLastError();
+        e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "fp64 tracker launch");
     }
     return ST_OK;

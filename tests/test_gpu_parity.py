@@ -128,3 +128,33 @@ def test_device_pointers_and_torch_stream():
     assert np.abs(So.cpu().numpy() - Sr).max() < TOL
     tr.close()
     lat.close()
+
+
+@pytest.mark.parametrize("gg", [1.9, 10.0, 45.5, 150.0, 487.0, 2000.0])
+def test_edge_rotation_angle_sweep(gg):
+    """Edge rotations from 0.05 rad to 200 rad per slice (every branch of the
+    edge-quaternion series, including halving and squaring back) against the
+    oracle's library sin/cos; on-axis also against the closed form."""
+    el = W.element("sbend", L=3.0, n_slices=4, angle=0.4)
+    ring = W.single_element_ring(el, gg)
+    z, S = W.gaussian_particles(64, gg, seed=21, sigmas=dict(x=5e-3, px=5e-4))
+    z[:, 0] = 0.0
+    S = W.cap_spins(64, math.pi, seed=22)
+    zg, Sg, _ = st.track(ring, z, S, 1, 2)
+    zo, So, _ = oracle.track(ring, z, S, 1, 2)
+    tol = 1e-15 * (20 + gg * 0.4)
+    assert np.abs(Sg - So).max() < tol
+    assert np.abs(zg - zo).max() < 1e-13
+    a = -gg * 0.4                    # on axis: rotation by -G gamma theta about y
+    s0 = S[:, 0]
+    exp = np.array([s0[0] * math.cos(a) + s0[2] * math.sin(a), s0[1], -s0[0] * math.sin(a) + s0[2] * math.cos(a)])
+    assert np.abs(Sg[:, 0] - exp).max() < tol
+
+
+def test_strong_bend_large_deflections():
+    """Large transverse momenta in a strongly bending magnet exercise the
+    library-asin branch of the bend's angle difference."""
+    el = W.element("sbend", L=1.0, n_slices=8, angle=1.2, eta=1.05)
+    ring = W.with_spin_order(W.single_element_ring(el, 45.5), 3)
+    z, S = W.gaussian_particles(128, 45.5, seed=8, sigmas=dict(x=0.05, px=0.08, y=0.01, py=0.02, delta=0.02))
+    compare(ring, z, S, 1, 3, tol=1e-12)
