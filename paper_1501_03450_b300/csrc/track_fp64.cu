@@ -26,22 +26,29 @@ struct Particle {
 };
 
 struct PConst {
-    double Pt, P2, P, invP, b0pt, a, c;   // b0pt = 1/beta0 + Pt, a = 1 + G gamma, c = G (gamma - 1)
+    double Pt, P2, P, invP, invP2, b0pt, a, c;   // b0pt = 1/beta0 + Pt, a = 1 + G gamma, c = G (gamma - 1)
 };
 
 // Cached matrix-kick coefficients of the linear quadrupole flow over a half
-// slice for one (|k1|, s): trig plane and hyperbolic plane.
+// slice for one (|k1|, s): trig plane (C1, S1, al1, be1, ga1) and hyperbolic
+// plane (C2, ...).  They depend only on the particle's P, so they are kept per
+// thread in shared memory (column threadIdx.x of a [10][blockDim] array) and
+// recomputed only when the (|k1|, s) key changes.
 struct QuadCache {
     double key_k, key_s;
-    double C1, S1, al1, be1, ga1;   // cos plane
-    double C2, S2, al2, be2, ga2;   // cosh plane
+    double* col;      // &smem[0][threadIdx.x]
+    int stride;       // blockDim.x
+    __device__ __forceinline__ double get(int f) const { return col[f * stride]; }
+    __device__ __forceinline__ void set(int f, double v) { col[f * stride] = v; }
 };
+enum { QC_C1, QC_S1, QC_AL1, QC_BE1, QC_GA1, QC_C2, QC_S2, QC_AL2, QC_BE2, QC_GA2, QC_N };
 
 __device__ __forceinline__ void quad_coeffs(QuadCache& qc, const PConst& pc, double absk1, double s) {
     qc.key_k = absk1;
     qc.key_s = s;
     double w = sqrt(absk1 * pc.invP);
     double ws = w * s;
+    double C1, S1, C2, S2;
     if (w > 0.0) {
         double sn, cs;
         sincos(ws, &sn, &cs);
@@ -49,21 +56,25 @@ __device__ __forceinline__ void quad_coeffs(QuadCache& qc, const PConst& pc, dou
         double ei = 1.0 / e;
         double ch = 0.5 * (e + ei), sh = 0.5 * (e - ei);
         double iw = 1.0 / w;
-        qc.C1 = cs;
-        qc.S1 = sn * iw;
-        qc.C2 = ch;
-        qc.S2 = sh * iw;
+        C1 = cs;
+        S1 = sn * iw;
+        C2 = ch;
+        S2 = sh * iw;
     } else {
-        qc.C1 = qc.C2 = 1.0;
-        qc.S1 = qc.S2 = s;
+        C1 = C2 = 1.0;
+        S1 = S2 = s;
     }
-    // integrals over the half slice of C^2, S^2 (/2) used by the T update
-    qc.al1 = 0.5 * (s + qc.C1 * qc.S1);
-    qc.be1 = qc.S1 * qc.S1;
-    qc.ga1 = 0.5 * (s - qc.C1 * qc.S1);
-    qc.al2 = 0.5 * (s + qc.C2 * qc.S2);
-    qc.be2 = qc.S2 * qc.S2;
-    qc.ga2 = 0.5 * (s - qc.C2 * qc.S2);
+    // integrals over the half slice used by the T update: (s + C S)/2, S^2, (s - C S)/2
+    qc.set(QC_C1, C1);
+    qc.set(QC_S1, S1);
+    qc.set(QC_AL1, 0.5 * (s + C1 * S1));
+    qc.set(QC_BE1, S1 * S1);
+    qc.set(QC_GA1, 0.5 * (s - C1 * S1));
+    qc.set(QC_C2, C2);
+    qc.set(QC_S2, S2);
+    qc.set(QC_AL2, 0.5 * (s + C2 * S2));
+    qc.set(QC_BE2, S2 * S2);
+    qc.set(QC_GA2, 0.5 * (s - C2 * S2));
 }
 
 // Linear quadrupole flow H_qL over s (Eq. (24)); per plane with focusing
@@ -72,10 +83,11 @@ __device__ __forceinline__ void quad_coeffs(QuadCache& qc, const PConst& pc, dou
 //                                          + P^2 K_u u^2 (s - C S)/2].
 __device__ __forceinline__ void quad_linear(Particle& p, const PConst& pc, const QuadCache& qc, double k1) {
     const bool foc = k1 >= 0.0;
-    const double Cx = foc ? qc.C1 : qc.C2, Sx = foc ? qc.S1 : qc.S2;
-    const double Cy = foc ? qc.C2 : qc.C1, Sy = foc ? qc.S2 : qc.S1;
-    const double alx = foc ? qc.al1 : qc.al2, bex = foc ? qc.be1 : qc.be2, gax = foc ? qc.ga1 : qc.ga2;
-    const double aly = foc ? qc.al2 : qc.al1, bey = foc ? qc.be2 : qc.be1, gay = foc ? qc.ga2 : qc.ga1;
+    const int ox_ = foc ? 0 : 5, oy_ = foc ? 5 : 0;   // field offsets of the x and y planes
+    const double Cx = qc.get(QC_C1 + ox_), Sx = qc.get(QC_S1 + ox_);
+    const double Cy = qc.get(QC_C1 + oy_), Sy = qc.get(QC_S1 + oy_);
+    const double alx = qc.get(QC_AL1 + ox_), bex = qc.get(QC_BE1 + ox_), gax = qc.get(QC_GA1 + ox_);
+    const double aly = qc.get(QC_AL1 + oy_), bey = qc.get(QC_BE1 + oy_), gay = qc.get(QC_GA1 + oy_);
     double X = p.X, Px = p.Px, Y = p.Y, Py = p.Py;
     double Pk = pc.P * k1;   // P^2 K_x = P k1
     double tsum = Px * Px * alx - k1 * X * Px * bex + Pk * X * X * gax
@@ -86,6 +98,16 @@ __device__ __forceinline__ void quad_linear(Particle& p, const PConst& pc, const
     p.Px = Px * Cx - k1 * X * Sx;
     p.Y = Y * Cy + Py * pc.invP * Sy;
     p.Py = Py * Cy + k1 * Y * Sy;
+}
+
+// 1/sqrt(a2 - p2) given ia = 1/sqrt(a2), ia2 = 1/a2 and p2 >= 0.  Near the
+// paraxial limit (e = p2/a2 < 1e-6) the binomial series
+// (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + ... (truncation < 4e-19) replaces the
+// library reciprocal square root.
+__device__ __forceinline__ double inv_sqrt_diff(double a2, double ia, double ia2, double p2) {
+    const double e = p2 * ia2;
+    if (e < 1e-6) return ia * fma(e, fma(e, 0.375, 0.5), 1.0);
+    return rsqrt(a2 - p2);
 }
 
 // Precession vector Omega (Eq. (6b)) for a transverse field b = (bx, by, 0),
@@ -103,15 +125,20 @@ __device__ __forceinline__ void precession(const Particle& p, const PConst& pc, 
 template <int K>
 struct LevelProducts {
     Quat q[K + 1];
-    __device__ __forceinline__ void reset() {
-#pragma unroll
-        for (int k = 0; k <= K; ++k) q[k] = Quat{1.0, 0.0, 0.0, 0.0};
-    }
     // edge i of N (N divisible by 2^K): multiply the edge rotation into every
-    // level that samples this edge
+    // level that samples this edge (the entrance edge starts every level)
     __device__ __forceinline__ void add_edge(int i, int N, double ds, double ox, double oy, double os) {
         double w = (i == 0 || i == N) ? 0.5 * ds : ds;
         Quat e = quat_from_rotvec(w * ox, w * oy, w * os);
+        if (i == 0) {
+            q[K] = e;
+#pragma unroll
+            for (int m = 1; m <= K; ++m) {
+                e = qsquare(e);
+                q[K - m] = e;
+            }
+            return;
+        }
         q[K] = qmul(e, q[K]);
 #pragma unroll
         for (int m = 1; m <= K; ++m) {
@@ -139,7 +166,7 @@ struct LevelProducts {
 };
 
 template <int K>
-__global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
+__global__ void __launch_bounds__(128, 3) track_fp64_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
                                                          uint32_t seq_offset, int n_seq, RefConst ref,
                                                          double2* __restrict__ xpx, double2* __restrict__ ypy,
                                                          double2* __restrict__ tpt, double2* __restrict__ sxy,
@@ -147,6 +174,7 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
                                                          int n, int n_turns, int32_t* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
+    __shared__ double qcache[QC_N * 128];
     if (!stage_to_smem(smem, blob, blob_bytes, &bar, status)) return;
     const DevElem* table = (const DevElem*)smem;
     const uint16_t* seq = (const uint16_t*)(smem + seq_offset);
@@ -177,6 +205,7 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
     pc.P2 = 1.0 + 2.0 * pc.Pt * ref.inv_beta0 + pc.Pt * pc.Pt;
     pc.invP = rsqrt(pc.P2);
     pc.P = pc.P2 * pc.invP;
+    pc.invP2 = pc.invP * pc.invP;
     pc.b0pt = ref.inv_beta0 + pc.Pt;
     const double gamma = ref.gamma0 * (1.0 + ref.beta0 * pc.Pt);
     pc.a = 1.0 + ref.G * gamma;
@@ -187,6 +216,8 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
     QuadCache qc;
     qc.key_k = -1.0;
     qc.key_s = 0.0;
+    qc.col = &qcache[threadIdx.x];
+    qc.stride = blockDim.x;
     LevelProducts<K> lv;
     bool is_lost = false;
 
@@ -202,7 +233,7 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
             const Particle p0 = p;
             if (type == ST_DRIFT) {
                 double L = el.ds;
-                double ips = rsqrt(pc.P2 - p.Px * p.Px - p.Py * p.Py);
+                double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Px * p.Px + p.Py * p.Py);
                 p.X += L * p.Px * ips;
                 p.Y += L * p.Py * ips;
                 p.T += L * (ref.inv_beta0 - pc.b0pt * ips);
@@ -216,15 +247,15 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
             // spin-carrying element
             const int N = el.n_slices;
             const double ds = el.ds;
-            lv.reset();
             double ox, oy, os;
             if (type == ST_SBEND) {
                 const double h = el.a[0], eta = el.a[1], cb = el.a[2], sb = el.a[3], ieh = el.a[4],
                              ieta = el.a[5];
                 const double Pa2 = pc.P2 - p.Py * p.Py;
-                const double iPa2 = 1.0 / Pa2;
+                const double iPa = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Py * p.Py);
+                const double iPa2 = iPa * iPa;
                 double ps2 = Pa2 - p.Px * p.Px;
-                double ips = rsqrt(ps2);
+                double ips = inv_sqrt_diff(Pa2, iPa, iPa2, p.Px * p.Px);
                 double Ps = ps2 * ips;
                 const double by = eta * h;
                 precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
@@ -239,7 +270,7 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
                     double Pxf = Pxi * cb + A * sb;
                     double Af = A * cb - Pxi * sb;
                     ps2 = Pa2 - Pxf * Pxf;
-                    ips = rsqrt(ps2);
+                    ips = inv_sqrt_diff(Pa2, iPa, iPa2, Pxf * Pxf);
                     Ps = ps2 * ips;
                     p.X = (Ps - Af - eta) * ieh;
                     p.Px = Pxf;
@@ -262,8 +293,9 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
             } else if (type == ST_MULT) {
                 const double k1 = el.a[0], k2 = el.a[1];
                 const double half = 0.5 * ds;
-                double ips = rsqrt(pc.P2 - p.Px * p.Px - p.Py * p.Py);
-                double Ps = (pc.P2 - p.Px * p.Px - p.Py * p.Py) * ips;
+                double pp = p.Px * p.Px + p.Py * p.Py;
+                double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                double Ps = (pc.P2 - pp) * ips;
                 double bx = k1 * p.Y + k2 * p.X * p.Y;
                 double by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
                 precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
@@ -276,9 +308,9 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
                     bx = k1 * p.Y + k2 * p.X * p.Y;
                     p.Px -= ds * by;
                     p.Py += ds * bx;
-                    double ps2 = pc.P2 - p.Px * p.Px - p.Py * p.Py;
-                    ips = rsqrt(ps2);
-                    Ps = ps2 * ips;
+                    pp = p.Px * p.Px + p.Py * p.Py;
+                    ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                    Ps = (pc.P2 - pp) * ips;
                     p.X += half * p.Px * ips;
                     p.Y += half * p.Py * ips;
                     p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
@@ -291,25 +323,24 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
                 const double k1 = el.a[0], absk = el.a[1];
                 const double half = 0.5 * ds;
                 if (qc.key_k != absk || qc.key_s != half) quad_coeffs(qc, pc, absk, half);
-                double ps2 = pc.P2 - p.Px * p.Px - p.Py * p.Py;
-                double ips = rsqrt(ps2);
-                double Ps = ps2 * ips;
+                double pp = p.Px * p.Px + p.Py * p.Py;
+                double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                double Ps = (pc.P2 - pp) * ips;
                 precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
                 lv.add_edge(0, N, ds, ox, oy, os);
                 for (int s = 1; s <= N; ++s) {
                     quad_linear(p, pc, qc, k1);
                     // nonlinear remainder H_qNL over ds, Eq. (25)
-                    double pp = p.Px * p.Px + p.Py * p.Py;
-                    ps2 = pc.P2 - pp;
-                    ips = rsqrt(ps2);
+                    pp = p.Px * p.Px + p.Py * p.Py;
+                    ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
                     double d = ips - pc.invP;
                     p.X += ds * p.Px * d;
                     p.Y += ds * p.Py * d;
-                    p.T += -ds * pc.b0pt * (ips - pc.invP * pp / (2.0 * pc.P2)) + ds * ref.inv_beta0;
+                    p.T += -ds * pc.b0pt * (ips - pc.invP * pp * 0.5 * pc.invP2) + ds * ref.inv_beta0;
                     quad_linear(p, pc, qc, k1);
-                    ps2 = pc.P2 - p.Px * p.Px - p.Py * p.Py;
-                    ips = rsqrt(ps2);
-                    Ps = ps2 * ips;
+                    pp = p.Px * p.Px + p.Py * p.Py;
+                    ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                    Ps = (pc.P2 - pp) * ips;
                     precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
                     lv.add_edge(s, N, ds, ox, oy, os);
                 }
