@@ -43,7 +43,11 @@ L2_BYTES = 126 * 1024 * 1024
 # pass on this workload (2 per DFMA, 1 per DADD/DMUL), from the thread-level
 # instruction counters of one ncu capture (profiles/track_fp64_rhic_like_ncu.md).
 # None until measured for the current kernel.
-FP64_FLOPS_PER_PASS = 662.3
+FP64_FLOPS_PER_PASS = 501.5
+# DRAM bytes (read + write) per particle per launch of the FP64 tracker, from
+# dram__bytes_read.sum + dram__bytes_write.sum of the same capture (2e4
+# particles: 1.595 MB + 0 B), scaled linearly with the particle count.
+FP64_DRAM_BYTES_PER_PARTICLE = 79.8
 
 
 def parse_args():
@@ -287,7 +291,8 @@ def main():
         achieved = None
     roofline = {"bound": "alu", "pipe": "fp64" if args.precision == "fp64" else "fp32",
                 "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": (achieved / (peak / 1e12)) if achieved else None, "traffic": None,
+                "frac": (achieved / (peak / 1e12)) if achieved else None,
+                "traffic": FP64_DRAM_BYTES_PER_PARTICLE * npart if args.precision == "fp64" else None,
                 "peak_source": "measured by st_measure_peaks (independent FMA chains) at run time"}
 
     cpu = None
