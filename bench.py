@@ -62,6 +62,8 @@ def parse_args():
     ap.add_argument("--particles", type=int, default=None, help="override particles per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant report")
+    ap.add_argument("--error-turns", type=int, default=1000, help="turns of the variants' error check")
     return ap.parse_args()
 
 
@@ -183,6 +185,65 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# variants: mixed precision (and the learned spin map) against the FP64 tracker
+# ---------------------------------------------------------------------------
+
+MIXED_WORKLOAD_PARTICLES = 1_000_000
+# FP32 floating-point operations the mixed tracker executes per pass on this
+# workload (2 per FFMA, 1 per FADD/FMUL), from one ncu capture
+# (profiles/track_mixed_rhic_like_ncu.md); None until measured.
+MIXED_FP32_FLOPS_PER_PASS = None
+
+
+def variant_mixed(st, torch, args, fp64_value, fp32_peak):
+    ring = W.with_spin_order(W.rhic_like_ring(args.ggamma), args.spin_order)
+    n_el = len(ring["elements"])
+    n = MIXED_WORKLOAD_PARTICLES
+    z, S = W.gaussian_particles(n, args.ggamma, seed=3451)
+    stream = torch.cuda.Stream()
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, n, "mixed", stream=stream.cuda_stream)
+    tr.set_launch(block_threads=128, turns_per_launch=1)
+    tr.upload(z, S)
+    for _ in range(2):
+        tr.track(1, args.spin_order)
+    torch.cuda.synchronize()
+    steps = 3
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            tr.track(1, args.spin_order)
+            b.record(stream)
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
+    value = n * n_el * steps / t
+    tr.close()
+    lat.close()
+    achieved = MIXED_FP32_FLOPS_PER_PASS * n * n_el / (t / steps) / 1e12 if MIXED_FP32_FLOPS_PER_PASS else None
+    out = {"metric": "particle-element passes/s", "value": value, "unit": "passes/s",
+           "speedup_vs_fp64": value / fp64_value, "dtype": "f32 (compensated) + f64 per turn",
+           "config": {"workload": f"108-cell RHIC-like ring, {n} Gaussian protons, Ggamma={args.ggamma}, "
+                      f"Romberg order {args.spin_order}, 1 turn per step", "steps": steps},
+           "roofline": {"bound": "alu", "pipe": "fp32", "achieved": achieved, "peak": fp32_peak / 1e12,
+                        "unit": "TFLOP/s", "frac": achieved / (fp32_peak / 1e12) if achieved else None},
+           "error_vs_fp64": {}}
+    # accuracy: 1024-particle subset, mixed vs the FP64 tracker (pinned to the oracle)
+    for gg in sorted({args.ggamma, 45.5, 487.0}):
+        ring_g = W.with_spin_order(W.rhic_like_ring(gg), args.spin_order)
+        zz, SS = W.gaussian_particles(1024, gg, seed=3451)
+        zm, Sm, _ = st.track(ring_g, zz, SS, args.error_turns, args.spin_order, precision="mixed")
+        zf, Sf, _ = st.track(ring_g, zz, SS, args.error_turns, args.spin_order, precision="fp64")
+        dS = np.linalg.norm(Sm - Sf, axis=0)
+        out["error_vs_fp64"][f"Ggamma={gg}"] = {
+            "turns": args.error_turns, "particles": 1024, "dS_mean": float(dS.mean()), "dS_max": float(dS.max()),
+            "orbit_max_abs": [float(x) for x in np.abs(zm - zf).max(axis=1)[:5]]}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -295,6 +356,10 @@ def main():
                 "traffic": FP64_DRAM_BYTES_PER_PARTICLE * npart if args.precision == "fp64" else None,
                 "peak_source": "measured by st_measure_peaks (independent FMA chains) at run time"}
 
+    variants = None
+    if not args.no_variants and world == 1:
+        variants = {"mixed": variant_mixed(st, torch, args, value, fp32_peak)}
+
     cpu = None
     if not args.no_cpu_baseline:
         rate, sample, threads, _ = oracle_rate(ring, z, S, K)
@@ -315,6 +380,7 @@ def main():
         "gpu_launches": args.steps * launches_per_step,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "variants": variants,
         "clocks": clocks,
         "wall_s_timed": wall,
         "peaks_measured": {"fp64_tflops": fp64_peak / 1e12, "fp32_tflops": fp32_peak / 1e12},

@@ -189,12 +189,21 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
         delete lat;
         return cuda_fail(e, "st_lattice_create: cudaMemcpy");
     }
+    int rc = build_mixed_tables(L);
+    if (rc != ST_OK) {
+        cudaFree(L.d_blob);
+        free(L.h_table);
+        free(L.h_seq);
+        delete lat;
+        return rc;
+    }
     *out = lat;
     return ST_OK;
 }
 
 int st_lattice_destroy(st_lattice* lat) {
     if (!lat) return ST_OK;
+    cudaFree(lat->impl.d_mix);
     cudaFree(lat->impl.d_blob);
     free(lat->impl.h_table);
     free(lat->impl.h_seq);
@@ -352,8 +361,7 @@ int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order) {
     }
     if (n_turns == 0) return ST_OK;
     if (ctx->precision == ST_FP64) return launch_track_fp64(ctx, n_turns, spin_order);
-    set_error("st_track: precision not available in this build");
-    return ST_EINVAL;
+    return launch_track_mixed(ctx, n_turns, spin_order);
 }
 
 int st_spins_download(st_ctx* ctx, double* spin_soa, double* z_soa, uint8_t* lost, int32_t dst_is_device) {

@@ -1,0 +1,173 @@
+// Host-side preparation of the mixed-precision tracker's tables (all in FP64,
+// rounded to FP32 once at the end):
+//   - per unique element: orbit constants in increment form (cos(h ds) - 1
+//     instead of cos(h ds)), the reference precession rate of the on-axis,
+//     on-momentum particle, and for every edge weight the constants that give
+//     an edge rotation's deviation from the reference rotation;
+//   - first-order (linear) map coefficients as compensated (hi, lo) float
+//     pairs, the reference rotation of each element as a (hi, lo) quaternion;
+//   - the element sequence (uint16) and, for bends, cos/sin of the reference
+//     rotation accumulated up to every slice edge.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "st_internal.cuh"
+
+namespace st {
+
+namespace {
+
+float2 split(double x) {
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+
+// Derivatives C^(m)(u0), S^(m)(u0), m = 0..4, of C(u) = cos(sqrt(u)/2) and
+// S(u) = sin(sqrt(u)/2)/sqrt(u).
+void half_angle_derivatives(double u0, double C[5], double S[5]) {
+    if (u0 < 100.0) {
+        // power series about 0: C = sum (-1)^n u^n / (4^n (2n)!),
+        // S = sum (-1)^n u^n / (2 4^n (2n+1)!); differentiate term by term
+        for (int m = 0; m < 5; ++m) {
+            double c = 0.0, s = 0.0;
+            for (int n = m; n < 80; ++n) {
+                double f2n = 1.0, f2n1;
+                for (int k = 2; k <= 2 * n; ++k) f2n *= k;
+                f2n1 = f2n * (2 * n + 1);
+                double p4 = std::pow(4.0, n);
+                double fall = 1.0;   // n! / (n-m)!
+                for (int k = 0; k < m; ++k) fall *= (n - k);
+                double up = std::pow(u0, n - m);
+                double sign = (n % 2) ? -1.0 : 1.0;
+                c += sign * fall * up / (p4 * f2n);
+                s += sign * fall * up / (2.0 * p4 * f2n1);
+                if (!std::isfinite(f2n)) break;
+            }
+            C[m] = c;
+            S[m] = s;
+        }
+    } else {
+        // 4u S' = C - 2S and C' = -S/4, differentiated n times:
+        // S^(n+1) = (C^(n) - (2 + 4n) S^(n)) / (4u), C^(n+1) = -S^(n)/4
+        double th = std::sqrt(u0);
+        C[0] = std::cos(0.5 * th);
+        S[0] = std::sin(0.5 * th) / th;
+        for (int n = 0; n < 4; ++n) {
+            C[n + 1] = -S[n] / 4.0;
+            S[n + 1] = (C[n] - (2.0 + 4.0 * n) * S[n]) / (4.0 * u0);
+        }
+    }
+}
+
+}  // namespace
+
+int build_mixed_tables(LatticeImpl& L) {
+    const double G = L.ref.G, gamma0 = L.ref.gamma0, beta0 = L.ref.beta0;
+    const double a0 = 1.0 + G * gamma0;
+    const int nu = L.n_unique, ne = L.n_elements;
+    std::vector<MixElem> me(nu);
+    std::vector<float> rho;   // float2 pairs
+    for (int u = 0; u < nu; ++u) {
+        const DevElem& d = L.h_table[u];
+        MixElem m;
+        memset(&m, 0, sizeof(m));
+        m.type = d.type;
+        m.n_slices = d.n_slices;
+        m.ds = (float)d.ds;
+        m.ds_ff = split(d.ds);
+        double rq[4] = {1.0, 0.0, 0.0, 0.0};
+        double omr = 0.0;
+        switch (d.type) {
+        case ST_MULT:
+            m.k1 = (float)d.a[0];
+            m.k2 = (float)d.a[1];
+            m.k1ds_ff = split(d.a[0] * d.ds);
+            m.k2h_ff = split(0.5 * d.a[1] * d.ds);
+            m.k2ds_ff = split(d.a[1] * d.ds);
+            break;
+        case ST_QUAD_MK:
+            m.k1 = (float)d.a[0];
+            m.k2 = (float)d.a[1];          // |k1|
+            m.k1ds_ff = split(d.a[1]);     // |k1| as (hi, lo): the matrix-kick coefficients need it exactly
+            break;
+        case ST_SBEND: {
+            const double h = d.a[0], eta = d.a[1];
+            const double hs = std::sin(0.5 * h * d.ds);
+            m.cbm1 = (float)(-2.0 * hs * hs);
+            m.sb = (float)std::sin(h * d.ds);
+            m.h = (float)h;
+            m.eta = (float)eta;
+            m.ieta = (float)(1.0 / eta);
+            m.ieh = (float)(1.0 / (eta * h));
+            m.dT_eta = (float)((1.0 - 1.0 / eta) * d.ds / beta0);
+            m.sbieh_ff = split(std::sin(h * d.ds) / (eta * h));
+            m.ietads_ff = split(d.ds / eta);
+            m.sb_ff = split(std::sin(h * d.ds));
+            m.cbmieh_ff = split(-2.0 * hs * hs / (eta * h));
+            m.etah_ff = split(eta * h);
+            m.ome_ff = split(1.0 - eta);
+            // on-axis, on-momentum particle: Omega = (0, h - (1 + G gamma0) eta h, 0)
+            omr = h - a0 * eta * h;
+            m.omr = (float)omr;
+            const double phi = omr * d.ds * d.n_slices;
+            rq[0] = std::cos(0.5 * phi);
+            rq[2] = std::sin(0.5 * phi);
+            m.rho_off = (int)(rho.size() / 2);
+            for (int i = 0; i <= d.n_slices; ++i) {
+                rho.push_back((float)std::cos(omr * i * d.ds));
+                rho.push_back((float)std::sin(omr * i * d.ds));
+            }
+            break;
+        }
+        case ST_SNAKE:
+            for (int c = 0; c < 4; ++c) rq[c] = d.a[c];
+            break;
+        default:
+            break;
+        }
+        for (int j = 0; j < 6; ++j) {
+            const double w = std::ldexp(d.ds, j) * 0.5;
+            const double al = w * omr;
+            MixWeight& W = m.w[j];
+            W.alpha = (float)al;
+            W.ch = (float)std::cos(0.5 * al);
+            W.sh = (float)std::sin(0.5 * al);
+            W.cf = (float)std::cos(al);
+            W.sf = (float)std::sin(al);
+            double C[5], S[5];
+            half_angle_derivatives(al * al, C, S);
+            W.S0 = (float)S[0];
+            double fact = 1.0;
+            for (int n = 0; n < 4; ++n) {
+                fact *= (n + 1);
+                W.dC[n] = (float)(C[n + 1] / fact);
+                W.dS[n] = (float)(S[n + 1] / fact);
+            }
+        }
+        for (int c = 0; c < 4; ++c) m.rq[c] = split(rq[c]);
+        me[u] = m;
+    }
+    // blob: [MixElem table] [uint16 sequence, padded to 16 B] [float2 rho table]
+    const size_t elem_bytes = (size_t)nu * sizeof(MixElem);
+    const size_t seq_bytes = (((size_t)ne * sizeof(uint16_t)) + 15) & ~(size_t)15;
+    const size_t rho_bytes = ((rho.size() * sizeof(float)) + 15) & ~(size_t)15;
+    L.mix_seq_offset = elem_bytes;
+    L.mix_rho_offset = elem_bytes + seq_bytes;
+    L.mix_bytes = elem_bytes + seq_bytes + rho_bytes;
+    std::vector<unsigned char> blob(L.mix_bytes, 0);
+    memcpy(blob.data(), me.data(), elem_bytes);
+    memcpy(blob.data() + L.mix_seq_offset, L.h_seq, (size_t)ne * sizeof(uint16_t));
+    if (!rho.empty()) memcpy(blob.data() + L.mix_rho_offset, rho.data(), rho.size() * sizeof(float));
+    cudaError_t e = cudaMalloc(&L.d_mix, L.mix_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed tables: cudaMalloc");
+    e = cudaMemcpy(L.d_mix, blob.data(), L.mix_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(L.d_mix);
+        L.d_mix = nullptr;
+        return cuda_fail(e, "mixed tables: cudaMemcpy");
+    }
+    return ST_OK;
+}
+
+}  // namespace st

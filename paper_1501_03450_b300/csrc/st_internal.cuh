@@ -37,14 +37,50 @@ struct RefConst {
     double inv_beta0;
 };
 
-// Per-element FP32 copy of the constants used by the mixed-precision kernel.
-struct __align__(16) DevElemF {
+// ---- mixed-precision tables ------------------------------------------------
+// Spin reference constants of one edge weight w_j = 2^j ds / 2 (j = 0..5 covers
+// the end and interior weights of every Romberg level for orders 0..4).
+// alpha = w_j * Omega_ref_y, where Omega_ref is the precession vector of the
+// on-axis, on-momentum particle (bends only; zero elsewhere).  C(u) =
+// cos(sqrt(u)/2) and S(u) = sin(sqrt(u)/2)/sqrt(u); their Taylor coefficients
+// about u0 = alpha^2 give the deviation of the edge rotation from the
+// reference rotation without cancellation.
+struct MixWeight {
+    float alpha;
+    float ch, sh;     // cos(alpha/2), sin(alpha/2)
+    float cf, sf;     // cos(alpha), sin(alpha)
+    float S0;         // S(alpha^2)
+    float dC[4];      // C(u0 + du) - C(u0) = sum_n dC[n] du^(n+1)
+    float dS[4];      // S(u0 + du) - S(u0) = sum_n dS[n] du^(n+1)
+};
+
+// Per unique element, constants of the mixed-precision kernel.  First-order
+// (linear) map coefficients are kept as compensated (hi, lo) float pairs so
+// that no systematic FP32 rounding enters the linear optics; second-order
+// terms use plain FP32.
+struct __align__(16) MixElem {
     int32_t type;
     int32_t n_slices;
-    float ds;
-    float a[5];
+    float ds;                         // slice length (drift: full length)
+    int32_t rho_off;                  // bends: offset (float2 units) of cos/sin(omr*i*ds), i = 0..N
+    float2 ds_ff;                     // ds as (hi, lo)
+    float2 k1ds_ff;                   // multipole: k1 ds; matrix-kick quadrupole: |k1| (as (hi, lo))
+    float k1, k2;                     // multipole / quadrupole strengths (quadrupole: k2 = |k1|)
+    float cbm1, sb;                   // bend: cos(h ds) - 1, sin(h ds)
+    float h, eta, ieta, ieh;          // bend: h, eta, 1/eta, 1/(eta h)
+    float dT_eta, omr;                // bend: (1 - 1/eta) ds / beta0; Omega_ref_y
+    float2 sbieh_ff;                  // bend: sin(h ds)/(eta h) as (hi, lo)
+    float2 ietads_ff;                 // bend: ds/eta as (hi, lo)
+    float2 sb_ff;                     // bend: sin(h ds) as (hi, lo)
+    float2 cbmieh_ff;                 // bend: (cos(h ds) - 1)/(eta h) as (hi, lo)
+    float2 etah_ff;                   // bend: eta h as (hi, lo)
+    float2 ome_ff;                    // bend: 1 - eta as (hi, lo)
+    float2 k2h_ff;                    // multipole: k2 ds / 2 as (hi, lo)
+    float2 k2ds_ff;                   // multipole: k2 ds as (hi, lo)
+    float2 rq[4];                     // reference rotation over the element (bends, snakes), (hi, lo) per component
+    MixWeight w[6];
 };
-static_assert(sizeof(DevElemF) == 32, "DevElemF must be 32 bytes");
+static_assert(sizeof(MixElem) % 16 == 0, "MixElem must be a multiple of 16 bytes");
 
 // Kernel status word values (written by bounded device waits).
 enum : int32_t { STATUS_OK = 0, STATUS_TMA_TIMEOUT = 1 };
@@ -60,10 +96,14 @@ struct LatticeImpl {
     size_t blob_bytes = 0;
     size_t table_bytes = 0;
     size_t seq_offset = 0;
-    // host copies for validation and the mixed-precision table
+    // host copies for validation
     DevElem* h_table = nullptr;
     uint16_t* h_seq = nullptr;
-    int32_t* h_slices = nullptr;   // per unique element
+    // mixed-precision blob: [MixElem (n_unique)] [uint16 sequence (n_elements), padded] [float2 rho table]
+    void* d_mix = nullptr;
+    size_t mix_bytes = 0;
+    size_t mix_seq_offset = 0;
+    size_t mix_rho_offset = 0;
 };
 
 }  // namespace st
@@ -97,8 +137,11 @@ namespace st {
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 
-// kernel launchers (track_fp64.cu)
+// kernel launchers (track_fp64.cu, track_mixed.cu)
 int launch_track_fp64(st_ctx* ctx, int n_turns, int spin_order);
+int launch_track_mixed(st_ctx* ctx, int n_turns, int spin_order);
+// mixed-precision table builder (mixed_tables.cu)
+int build_mixed_tables(LatticeImpl& L);
 int launch_pack(st_ctx* ctx, const double* z_soa, const double* spin_soa);
 int launch_unpack(st_ctx* ctx, double* z_soa, double* spin_soa);
 

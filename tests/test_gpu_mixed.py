@@ -1,0 +1,92 @@
+"""Mixed-precision tracker (FP32 slices with compensated coordinates, FP64
+per-turn spin composition) through the C ABI, against the CPU oracle and
+against the FP64 GPU tracker (itself pinned to the oracle at 1e-11).
+
+The mixed tracker computes the same discretisation as the FP64 one in a
+different arithmetic, so the comparison is an error budget, not bit parity.
+Metric: Delta S = mean_j |S_j - S_j(ref)| (Sec. 5.2.2), with the maximum also
+bounded, and the max absolute orbit error."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1501_03450_b300 as st
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def spin_err(Sa, Sb):
+    d = np.linalg.norm(Sa - Sb, axis=0)
+    return float(d.mean()), float(d.max())
+
+
+def test_toy_ring_mixed_vs_oracle_100_turns():
+    w = W.workload("toy_ring_1024")
+    z, S = W.gaussian_particles(1024, 45.5, seed=w["seed"])
+    zm, Sm, lm = st.track(w["ring"], z, S, 100, 2, precision="mixed")
+    zo, So, lo = oracle.track(w["ring"], z, S, 100, 2)
+    assert np.array_equal(lm, lo)
+    mean, mx = spin_err(Sm, So)
+    assert mean < 1e-7 and mx < 1e-6, (mean, mx)
+    assert np.abs(zm[:4] - zo[:4]).max() < 1e-7
+    assert np.abs(zm[4] - zo[4]).max() < 1e-5          # T is passive; FP32 path-length terms
+
+
+@pytest.mark.parametrize("gg,mean_tol,max_tol", [(45.5, 3e-7, 3e-6), (487.0, 4e-6, 4e-5)])
+def test_rhic_like_ring_mixed_100_turns(gg, mean_tol, max_tol):
+    ring = W.with_spin_order(W.rhic_like_ring(gg), 2)
+    z, S = W.gaussian_particles(512, gg, seed=3451)
+    zm, Sm, _ = st.track(ring, z, S, 100, 2, precision="mixed")
+    zf, Sf, _ = st.track(ring, z, S, 100, 2, precision="fp64")
+    mean, mx = spin_err(Sm, Sf)
+    assert mean < mean_tol and mx < max_tol, (mean, mx)
+    assert np.abs(zm[:4] - zf[:4]).max() < 3e-7
+
+
+def test_rhic_like_ring_mixed_vs_oracle_direct():
+    ring = W.with_spin_order(W.rhic_like_ring(45.5), 2)
+    z, S = W.gaussian_particles(64, 45.5, seed=77)
+    zm, Sm, _ = st.track(ring, z, S, 5, 2, precision="mixed")
+    zo, So, _ = oracle.track(ring, z, S, 5, 2)
+    mean, mx = spin_err(Sm, So)
+    assert mean < 1e-7 and mx < 1e-6
+    assert np.abs(zm[:4] - zo[:4]).max() < 1e-9
+
+
+@pytest.mark.parametrize("K", [0, 1, 2, 3, 4])
+def test_mixed_every_romberg_order(K):
+    ring = W.with_spin_order(W.toy_ring(45.5), K)
+    z, S = W.gaussian_particles(200, 45.5, seed=30 + K)
+    zm, Sm, _ = st.track(ring, z, S, 10, K, precision="mixed")
+    zo, So, _ = oracle.track(ring, z, S, 10, K)
+    mean, mx = spin_err(Sm, So)
+    assert mean < 1e-7 and mx < 1e-6, (K, mean, mx)
+    assert np.abs(zm[:4] - zo[:4]).max() < 1e-8
+
+
+def test_mixed_full_size_sampled():
+    """10^6 particles (the mixed-precision workload's size) for 2 turns;
+    256 particles sampled across the ensemble against the oracle."""
+    ring = W.with_spin_order(W.rhic_like_ring(45.5), 2)
+    n = 1_000_000
+    z, S = W.gaussian_particles(n, 45.5, seed=3451)
+    zm, Sm, lm = st.track(ring, z, S, 2, 2, precision="mixed")
+    idx = np.linspace(0, n - 1, 256).astype(int)
+    zo, So, lo = oracle.track(ring, z[:, idx], S[:, idx], 2, 2)
+    assert np.array_equal(lm[idx], lo)
+    mean, mx = spin_err(Sm[:, idx], So)
+    assert mean < 1e-7 and mx < 1e-6
+    assert np.abs(zm[:4, idx] - zo[:4]).max() < 1e-9
+
+
+def test_mixed_lost_particle_and_edge_cases():
+    ring = W.with_spin_order(W.toy_ring(45.5), 2)
+    z, S = W.gaussian_particles(33, 45.5, seed=3)
+    z[1, 5] = 1.5                       # lost in the first element
+    z[:, 0] = 0.0                       # on axis: zero-angle edge rotations
+    zm, Sm, lm = st.track(ring, z, S, 3, 2, precision="mixed")
+    zo, So, lo = oracle.track(ring, z, S, 3, 2)
+    assert np.array_equal(lm, lo) and lm[5] == 1
+    assert np.abs(zm - zo).max() < 1e-6
+    assert spin_err(Sm, So)[1] < 1e-6
