@@ -176,9 +176,9 @@ struct MQuad {
     float al[2], be[2], ga[2];
 };
 
-__device__ __forceinline__ void mquad_coeffs(MQuad& q, double invP, double absk, double s) {
-    q.key_k = (float)absk;
-    q.key_s = (float)s;
+__device__ __forceinline__ void mquad_coeffs(MQuad& q, double invP, double absk, double s, float key_k, float key_s) {
+    q.key_k = key_k;
+    q.key_s = key_s;
     const double w = sqrt(absk * invP);
     const double ds = s;
     const double ws = w * ds;
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(128, 4) track_mixed_kernel(const void* __restr
                     const float half = 0.5f * ds;
                     if (mq.key_k != absk || mq.key_s != half)
                         mquad_coeffs(mq, invP64, (double)el.k1ds_ff.x + (double)el.k1ds_ff.y,
-                                     0.5 * ((double)el.ds_ff.x + (double)el.ds_ff.y));
+                                     0.5 * ((double)el.ds_ff.x + (double)el.ds_ff.y), absk, half);
                     FF ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                     float ips = ips_ff.hi, Ps = (k.P2 - pp) * ips;
                     omega_straight(k, z.Px.hi, z.Py.hi, k1 * z.Y.hi, k1 * z.X.hi, ips, Ps, ox, oy, os);
