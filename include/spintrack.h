@@ -140,6 +140,31 @@ int st_ctx_set_launch(st_ctx* ctx, int32_t block_threads, int32_t turns_per_laun
  * trackers' arithmetic roofline.  Errors: ST_EINVAL (NULL), ST_ECUDA. */
 int st_measure_peaks(double* fp64_flops, double* fp32_flops);
 
+/* Allocation-free FP64 tracking.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory (code running
+ * inside an allocator or memory pool that owns the device memory, host
+ * processes that forbid further allocations, latency-critical loops where a
+ * cudaMalloc would stall).  It calls no cudaMalloc/cudaFree and no allocating
+ * library routine: the packed lattice (at most 64 KiB: <= 512 distinct
+ * elements, <= 16384 elements per turn) and the kernel status word live in
+ * one file-scope device array of about 64 KiB that every GPU loading the
+ * library holds until the process exits.
+ *   elems, n_elems, ref: the lattice as for st_lattice_create (host memory).
+ *   state: device buffer of 9 n doubles, updated in place, laid out as the
+ *          tracker's native pairs: (X,Px)[n], (Y,Py)[n], (T,Pt)[n], (Sx,Sy)[n],
+ *          then Sz[n];  lost: device buffer of n flags (0 = tracked; set to 1
+ *          when a particle is lost; particles flagged on entry are skipped).
+ *   n_turns >= 0, spin_order 0..4 (every spin-carrying element's n_slices a
+ *   multiple of 2^spin_order); cuda_stream may be NULL (legacy stream).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the scratch and rewrites it;
+ * calls that overlap on the GPU race.  The call synchronises the stream.
+ * Errors: ST_EINVAL (arguments, lattice too large), ST_ECUDA, ST_ETIMEOUT. */
+int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, const st_reference* ref,
+                          double* state, uint8_t* lost, int64_t n_particles, int32_t n_turns,
+                          int32_t spin_order, void* cuda_stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char* st_last_error(void);
 

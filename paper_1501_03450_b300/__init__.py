@@ -56,6 +56,8 @@ SIGNATURES = {
     "st_spins_download": ([_VP, _VP, _VP, _VP, ctypes.c_int32], ctypes.c_int),
     "st_ctx_set_launch": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "st_measure_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "st_track_fp64_noalloc": ([ctypes.POINTER(StElement), ctypes.c_int32, ctypes.POINTER(StReference), _VP, _VP,
+                               ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _VP], ctypes.c_int),
     "st_last_error": ([], ctypes.c_char_p),
     "st_version": ([], ctypes.c_char_p),
 }
@@ -147,6 +149,40 @@ def st_measure_peaks():
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load().st_measure_peaks(ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def st_track_fp64_noalloc(elements: List[Dict], G: float, Ggamma0: float, state_ptr: int, lost_ptr: int,
+                          n_particles: int, n_turns: int, spin_order: int, stream: Optional[int] = None) -> None:
+    """Allocation-free FP64 tracking on caller-owned device buffers (see the
+    header for the state layout)."""
+    arr = elements_array(elements)
+    ref = StReference(G, Ggamma0)
+    _check(load().st_track_fp64_noalloc(arr, len(elements), ctypes.byref(ref), state_ptr, lost_ptr,
+                                        int(n_particles), int(n_turns), int(spin_order), stream))
+
+
+def pairs_from_soa(z: np.ndarray, S: np.ndarray) -> np.ndarray:
+    """[6][n] orbit + [3][n] spin -> the tracker's native 9n-double layout
+    (X,Px)(Y,Py)(T,Pt)(Sx,Sy) pairs, then Sz."""
+    n = z.shape[1]
+    out = np.empty(9 * n, np.float64)
+    for k, (a, b) in enumerate(((z[0], z[1]), (z[2], z[3]), (z[4], z[5]), (S[0], S[1]))):
+        out[2 * k * n:2 * (k + 1) * n:2] = a
+        out[2 * k * n + 1:2 * (k + 1) * n:2] = b
+    out[8 * n:] = S[2]
+    return out
+
+
+def soa_from_pairs(state: np.ndarray, n: int):
+    z = np.empty((6, n))
+    S = np.empty((3, n))
+    for k in range(3):
+        z[2 * k] = state[2 * k * n:2 * (k + 1) * n:2]
+        z[2 * k + 1] = state[2 * k * n + 1:2 * (k + 1) * n:2]
+    S[0] = state[6 * n:8 * n:2]
+    S[1] = state[6 * n + 1:8 * n:2]
+    S[2] = state[8 * n:]
+    return z, S
 
 
 # ---- convenience object layer (still only marshalling) --------------------

@@ -26,10 +26,10 @@ int cuda_fail(cudaError_t e, const char* what) {
     return ST_ECUDA;
 }
 
-static bool is_spin_type(int t) { return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND; }
+bool is_spin_type(int t) { return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND; }
 
 // Precompute the per-element constants the kernels use (all in FP64).
-static DevElem pack_element(const st_element& e) {
+DevElem pack_element(const st_element& e) {
     DevElem d;
     memset(&d, 0, sizeof(d));
     d.type = e.type;

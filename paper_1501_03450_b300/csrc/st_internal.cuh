@@ -136,6 +136,8 @@ namespace st {
 
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
+bool is_spin_type(int t);
+DevElem pack_element(const st_element& e);
 
 // kernel launchers (track_fp64.cu, track_mixed.cu)
 int launch_track_fp64(st_ctx* ctx, int n_turns, int spin_order);
