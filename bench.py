@@ -243,6 +243,56 @@ def variant_mixed(st, torch, args, fp64_value, fp32_peak):
     return out
 
 
+def variant_batched(st, torch, args, turns=3):
+    """64 uneven jobs (8-108 cells, G*gamma0 in [45.5, 487], 10^3-10^5
+    particles) in one persistent launch per chunk of turns, against tracking
+    the same jobs one after another with the single-job entry point."""
+    jobs = W.batched_jobs(n_jobs=64, seed=20240603)
+    for j in jobs:
+        j["ring"] = W.with_spin_order(j["ring"], args.spin_order)
+    passes_per_turn = sum(len(j["ring"]["elements"]) * j["n_particles"] for j in jobs)
+    inputs = [W.gaussian_particles(j["n_particles"], j["ring"]["Ggamma0"], seed=j["seed"]) for j in jobs]
+    out = {"config": {"workload": "64 seeded rings, 8-108 FODO cells, Ggamma U[45.5, 487], particles log-U[1e3, 1e5]",
+                      "jobs": len(jobs), "particles": sum(j["n_particles"] for j in jobs),
+                      "passes_per_turn": passes_per_turn, "turns_timed": turns}}
+    for prec in ("fp64", "mixed"):
+        b = st.Batch([j["ring"] for j in jobs], [j["n_particles"] for j in jobs], prec)
+        for k in range(len(jobs)):
+            b.upload(k, *inputs[k])
+        tuned = b.autotune(args.spin_order, trial_turns=1) if prec == "mixed" else None
+        b.track(turns, args.spin_order)            # warm-up and graph capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.track(turns, args.spin_order)
+        b.download(0)                              # synchronises the batch stream
+        dt = time.perf_counter() - t0
+        b.close()
+        # the same jobs tracked one after another (single-job contexts)
+        lats, trs = [], []
+        for k, j in enumerate(jobs):
+            lat = st.Lattice(j["ring"])
+            tr = st.Tracker(lat, j["n_particles"], prec)
+            tr.set_launch(128, turns)
+            tr.upload(*inputs[k])
+            lats.append(lat)
+            trs.append(tr)
+        for tr in trs:
+            tr.track(1, args.spin_order)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for tr in trs:
+            tr.track(turns, args.spin_order)
+        torch.cuda.synchronize()
+        ds = time.perf_counter() - t0
+        for tr, lat in zip(trs, lats):
+            tr.close()
+            lat.close()
+        out[prec] = {"value": passes_per_turn * turns / dt, "unit": "passes/s",
+                     "sequential_single_job_value": passes_per_turn * turns / ds,
+                     "speedup_vs_sequential": ds / dt, "autotuned_shape": tuned}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -358,7 +408,8 @@ def main():
 
     variants = None
     if not args.no_variants and world == 1:
-        variants = {"mixed": variant_mixed(st, torch, args, value, fp32_peak)}
+        variants = {"mixed": variant_mixed(st, torch, args, value, fp32_peak),
+                    "batched": variant_batched(st, torch, args)}
 
     cpu = None
     if not args.no_cpu_baseline:

@@ -134,6 +134,45 @@ int st_spins_download(st_ctx* ctx, double* spin_soa, double* z_soa, uint8_t* los
  * the knobs the autotuner sweeps. */
 int st_ctx_set_launch(st_ctx* ctx, int32_t block_threads, int32_t turns_per_launch);
 
+/* ---- batched jobs ----------------------------------------------------
+ * Many independent tracking jobs (each its own lattice, particle count and
+ * reference energy) tracked together by one persistent launch per chunk of
+ * turns: work items of one block's worth of particles are ordered by cost
+ * (largest first) and popped from a device work queue; each item's lattice is
+ * staged into shared memory; every particle is tracked with the same
+ * integrator as st_track, so results equal tracking each job alone.  The turn
+ * loop is captured into a CUDA graph (per n_turns, spin order and launch
+ * shape) and replayed. */
+typedef struct st_batch st_batch;
+
+/* n_jobs >= 1 jobs: lattices[j] (must outlive the batch) and n_particles[j]
+ * (1..2^30).  precision ST_FP64 or ST_MIXED; cuda_stream as st_ctx_create.
+ * Errors: ST_EINVAL, ST_ENOMEM, ST_ECUDA. */
+int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particles, int32_t n_jobs,
+                    int32_t precision, void* cuda_stream, st_batch** out);
+int st_batch_destroy(st_batch* batch);
+/* Load job `job`'s particles ([6][n] orbit, [3][n] spins, as
+ * st_particles_upload); synchronises the batch stream. */
+int st_batch_upload(st_batch* batch, int32_t job, const double* z_soa, const double* spin_soa,
+                    int32_t src_is_device);
+/* Track every job for n_turns with Romberg order spin_order (asynchronous).
+ * Errors: ST_ESTATE if a job has no particles, ST_EINVAL as st_track. */
+int st_batch_track(st_batch* batch, int32_t n_turns, int32_t spin_order);
+/* Copy job `job`'s state out (as st_spins_download); synchronises. */
+int st_batch_download(st_batch* batch, int32_t job, double* spin_soa, double* z_soa, uint8_t* lost,
+                      int32_t dst_is_device);
+/* Launch shape: threads per block (32..128, multiple of 32; 0 keeps), turns
+ * per launch (0 keeps), CUDA graph on/off (-1 keeps), register-budget
+ * variant 0 (larger budget, fewer resident blocks) or 1 (-1 keeps). */
+int st_batch_set_launch(st_batch* batch, int32_t block_threads, int32_t turns_per_launch, int32_t use_graph,
+                        int32_t variant);
+/* Autotuner: times block size {64, 96, 128} x turns per launch {1,
+ * trial_turns} x register variant {0, 1} on trial_turns turns of the live
+ * state (restored after every trial), keeps the fastest shape and returns it
+ * (any output pointer may be NULL).  Allocates a temporary backup buffer. */
+int st_batch_autotune(st_batch* batch, int32_t spin_order, int32_t trial_turns, int32_t* best_block,
+                      int32_t* best_tpl, int32_t* best_variant, float* best_ms);
+
 /* Measure the current device's sustained fused-multiply-add throughput in
  * FP64 and in FP32 (flop/s, two flops per FMA) with independent FMA chains
  * timed by CUDA events (about 0.2 s).  These are the denominators of the

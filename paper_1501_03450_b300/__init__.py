@@ -58,6 +58,16 @@ SIGNATURES = {
     "st_measure_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "st_track_fp64_noalloc": ([ctypes.POINTER(StElement), ctypes.c_int32, ctypes.POINTER(StReference), _VP, _VP,
                                ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _VP], ctypes.c_int),
+    "st_batch_create": ([ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.c_int32, _VP,
+                         ctypes.POINTER(_VP)], ctypes.c_int),
+    "st_batch_destroy": ([_VP], ctypes.c_int),
+    "st_batch_upload": ([_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int32], ctypes.c_int),
+    "st_batch_track": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "st_batch_download": ([_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int32], ctypes.c_int),
+    "st_batch_set_launch": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "st_batch_autotune": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "st_last_error": ([], ctypes.c_char_p),
     "st_version": ([], ctypes.c_char_p),
 }
@@ -159,6 +169,91 @@ def st_track_fp64_noalloc(elements: List[Dict], G: float, Ggamma0: float, state_
     ref = StReference(G, Ggamma0)
     _check(load().st_track_fp64_noalloc(arr, len(elements), ctypes.byref(ref), state_ptr, lost_ptr,
                                         int(n_particles), int(n_turns), int(spin_order), stream))
+
+
+def st_batch_create(lattice_handles: List[int], n_particles: List[int], precision: int = ST_FP64,
+                    stream: Optional[int] = None) -> int:
+    n = len(lattice_handles)
+    lats = (_VP * n)(*lattice_handles)
+    ns = (ctypes.c_int64 * n)(*[int(x) for x in n_particles])
+    out = _VP()
+    _check(load().st_batch_create(lats, ns, n, int(precision), stream, ctypes.byref(out)))
+    return out.value
+
+
+def st_batch_destroy(b: int) -> None:
+    _check(load().st_batch_destroy(b))
+
+
+def st_batch_upload(b: int, job: int, z_ptr: int, s_ptr: int, src_is_device: int) -> None:
+    _check(load().st_batch_upload(b, int(job), z_ptr, s_ptr, int(src_is_device)))
+
+
+def st_batch_track(b: int, n_turns: int, spin_order: int) -> None:
+    _check(load().st_batch_track(b, int(n_turns), int(spin_order)))
+
+
+def st_batch_download(b: int, job: int, s_ptr: int, z_ptr: Optional[int], lost_ptr: Optional[int],
+                      dst_is_device: int) -> None:
+    _check(load().st_batch_download(b, int(job), s_ptr, z_ptr, lost_ptr, int(dst_is_device)))
+
+
+def st_batch_set_launch(b: int, block_threads: int = 0, turns_per_launch: int = 0, use_graph: int = -1,
+                        variant: int = -1) -> None:
+    _check(load().st_batch_set_launch(b, int(block_threads), int(turns_per_launch), int(use_graph), int(variant)))
+
+
+def st_batch_autotune(b: int, spin_order: int, trial_turns: int = 2):
+    blk, tpl, var, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load().st_batch_autotune(b, int(spin_order), int(trial_turns), ctypes.byref(blk), ctypes.byref(tpl),
+                                    ctypes.byref(var), ctypes.byref(ms)))
+    return dict(block_threads=blk.value, turns_per_launch=tpl.value, variant=var.value, ms=ms.value)
+
+
+class Batch:
+    """Many independent tracking jobs tracked by one persistent launch."""
+
+    def __init__(self, rings: List[Dict], n_particles: List[int], precision: str = "fp64",
+                 stream: Optional[int] = None):
+        self.lattices = [Lattice(r) for r in rings]
+        self.n = [int(x) for x in n_particles]
+        self.handle = st_batch_create([l.handle for l in self.lattices], self.n, PRECISIONS[precision], stream)
+
+    def upload(self, job: int, z: np.ndarray, S: np.ndarray):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        assert z.shape == (6, self.n[job]) and S.shape == (3, self.n[job])
+        st_batch_upload(self.handle, job, z.ctypes.data, S.ctypes.data, 0)
+
+    def track(self, n_turns: int, spin_order: int):
+        st_batch_track(self.handle, n_turns, spin_order)
+
+    def download(self, job: int):
+        n = self.n[job]
+        z = np.empty((6, n))
+        S = np.empty((3, n))
+        lost = np.empty(n, np.uint8)
+        st_batch_download(self.handle, job, S.ctypes.data, z.ctypes.data, lost.ctypes.data, 0)
+        return z, S, lost
+
+    def set_launch(self, block_threads=0, turns_per_launch=0, use_graph=-1, variant=-1):
+        st_batch_set_launch(self.handle, block_threads, turns_per_launch, use_graph, variant)
+
+    def autotune(self, spin_order: int, trial_turns: int = 2):
+        return st_batch_autotune(self.handle, spin_order, trial_turns)
+
+    def close(self):
+        if self.handle:
+            st_batch_destroy(self.handle)
+            self.handle = None
+        for l in self.lattices:
+            l.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pairs_from_soa(z: np.ndarray, S: np.ndarray) -> np.ndarray:

@@ -53,12 +53,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait (about `limit_ns` of wall time) on phase 0 of `bar`.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint64_t limit_ns) {
+// Bounded wait (about `limit_ns` of wall time) for the phase with the given
+// parity of `bar` to complete.
+__device__ __forceinline__ bool mbar_wait_bounded_parity(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
     uint64_t t0 = global_timer_ns();
     for (uint32_t it = 0;; ++it) {
-        if (mbar_try_wait(bar, 0)) return true;
+        if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 63u && global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint64_t limit_ns) {
+    return mbar_wait_bounded_parity(bar, 0, limit_ns);
+}
+
+// Issue the bulk copies of `bytes` (multiple of 16) into shared memory on an
+// already initialised barrier (one thread calls this).
+__device__ __forceinline__ void issue_bulk_stage(void* smem, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+    mbar_arrive_expect_tx(bar, bytes);
+    const char* s = (const char*)gsrc;
+    char* d = (char*)smem;
+    uint32_t off = 0;
+    while (off < bytes) {
+        uint32_t c = bytes - off < 65536u ? bytes - off : 65536u;
+        bulk_copy_g2s(d + off, s + off, c, bar);
+        off += c;
     }
 }
 

@@ -146,5 +146,9 @@ int launch_track_mixed(st_ctx* ctx, int n_turns, int spin_order);
 int build_mixed_tables(LatticeImpl& L);
 int launch_pack(st_ctx* ctx, const double* z_soa, const double* spin_soa);
 int launch_unpack(st_ctx* ctx, double* z_soa, double* spin_soa);
+__global__ void pack_kernel(const double* __restrict__ z, const double* __restrict__ s, double2* xpx, double2* ypy,
+                            double2* tpt, double2* sxy, double* sz, int64_t n);
+__global__ void unpack_kernel(double* __restrict__ z, double* __restrict__ s, const double2* xpx, const double2* ypy,
+                              const double2* tpt, const double2* sxy, const double* sz, int64_t n);
 
 }  // namespace st

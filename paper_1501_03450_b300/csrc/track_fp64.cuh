@@ -1,0 +1,351 @@
+// FP64 spin-orbit tracker: one persistent thread per particle holds the orbit
+// (X, Px, Y, Py, T; Pt is a constant of the motion in every element here), the
+// spin and the Romberg level products in registers for all turns of a launch.
+// The deduplicated lattice table and the element sequence sit in shared
+// memory (one bulk TMA copy per block); every element is uniform across the
+// block, so the element switch never diverges.
+//
+// Per element (Sec. 3 orbit maps, Sec. 4.3 spin):
+//   edge 0 = entrance: Omega (Eq. (6b)) -> edge rotation -> level products
+//   for each slice: orbit slice map, Omega at the new edge, edge rotation
+//   level products: the finest level K multiplies every edge rotation; level
+//   K-m every 2^m-th one, whose rotation by 2^m times the angle is obtained by
+//   squaring the edge quaternion m times; end edges start from half the
+//   angle (trapezoid weights of Eq. (38))
+//   Romberg table (Eq. (39)) in place over the K+1 level products, normalise,
+//   compose into the turn quaternion (later elements on the left).
+// The spin is rotated once per turn by the composed turn quaternion.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace st {
+
+struct Particle {
+    double X, Px, Y, Py, T;
+};
+
+struct PConst {
+    double Pt, P2, P, invP, invP2, b0pt, a, c;   // b0pt = 1/beta0 + Pt, a = 1 + G gamma, c = G (gamma - 1)
+};
+
+// Cached matrix-kick coefficients of the linear quadrupole flow over a half
+// slice for one (|k1|, s): trig plane (C1, S1, al1, be1, ga1) and hyperbolic
+// plane (C2, ...).  They depend only on the particle's P, so they are kept per
+// thread in shared memory (column threadIdx.x of a [10][blockDim] array) and
+// recomputed only when the (|k1|, s) key changes.
+struct QuadCache {
+    double key_k, key_s;
+    double* col;      // &smem[0][threadIdx.x]
+    int stride;       // blockDim.x
+    __device__ __forceinline__ double get(int f) const { return col[f * stride]; }
+    __device__ __forceinline__ void set(int f, double v) { col[f * stride] = v; }
+};
+enum { QC_C1, QC_S1, QC_AL1, QC_BE1, QC_GA1, QC_C2, QC_S2, QC_AL2, QC_BE2, QC_GA2, QC_N };
+
+__device__ __forceinline__ void quad_coeffs(QuadCache& qc, const PConst& pc, double absk1, double s) {
+    qc.key_k = absk1;
+    qc.key_s = s;
+    double w = sqrt(absk1 * pc.invP);
+    double ws = w * s;
+    double C1, S1, C2, S2;
+    if (w > 0.0) {
+        double sn, cs;
+        sincos(ws, &sn, &cs);
+        double e = exp(ws);
+        double ei = 1.0 / e;
+        double ch = 0.5 * (e + ei), sh = 0.5 * (e - ei);
+        double iw = 1.0 / w;
+        C1 = cs;
+        S1 = sn * iw;
+        C2 = ch;
+        S2 = sh * iw;
+    } else {
+        C1 = C2 = 1.0;
+        S1 = S2 = s;
+    }
+    // integrals over the half slice used by the T update: (s + C S)/2, S^2, (s - C S)/2
+    qc.set(QC_C1, C1);
+    qc.set(QC_S1, S1);
+    qc.set(QC_AL1, 0.5 * (s + C1 * S1));
+    qc.set(QC_BE1, S1 * S1);
+    qc.set(QC_GA1, 0.5 * (s - C1 * S1));
+    qc.set(QC_C2, C2);
+    qc.set(QC_S2, S2);
+    qc.set(QC_AL2, 0.5 * (s + C2 * S2));
+    qc.set(QC_BE2, S2 * S2);
+    qc.set(QC_GA2, 0.5 * (s - C2 * S2));
+}
+
+// Linear quadrupole flow H_qL over s (Eq. (24)); per plane with focusing
+// constant K_u = +-k1/P: u' = u C + (pu/P) S, pu' = pu C - P K_u u S, and
+// T' = T - (1/beta0 + Pt)/(2 P^3) * sum_u [pu^2 (s + C S)/2 - P K_u u pu S^2
+//                                          + P^2 K_u u^2 (s - C S)/2].
+__device__ __forceinline__ void quad_linear(Particle& p, const PConst& pc, const QuadCache& qc, double k1) {
+    const bool foc = k1 >= 0.0;
+    const int ox_ = foc ? 0 : 5, oy_ = foc ? 5 : 0;   // field offsets of the x and y planes
+    const double Cx = qc.get(QC_C1 + ox_), Sx = qc.get(QC_S1 + ox_);
+    const double Cy = qc.get(QC_C1 + oy_), Sy = qc.get(QC_S1 + oy_);
+    const double alx = qc.get(QC_AL1 + ox_), bex = qc.get(QC_BE1 + ox_), gax = qc.get(QC_GA1 + ox_);
+    const double aly = qc.get(QC_AL1 + oy_), bey = qc.get(QC_BE1 + oy_), gay = qc.get(QC_GA1 + oy_);
+    double X = p.X, Px = p.Px, Y = p.Y, Py = p.Py;
+    double Pk = pc.P * k1;   // P^2 K_x = P k1
+    double tsum = Px * Px * alx - k1 * X * Px * bex + Pk * X * X * gax
+                + Py * Py * aly + k1 * Y * Py * bey - Pk * Y * Y * gay;
+    double f = 0.5 * pc.b0pt * pc.invP * pc.invP * pc.invP;
+    p.T -= f * tsum;
+    p.X = X * Cx + Px * pc.invP * Sx;
+    p.Px = Px * Cx - k1 * X * Sx;
+    p.Y = Y * Cy + Py * pc.invP * Sy;
+    p.Py = Py * Cy + k1 * Y * Sy;
+}
+
+// 1/sqrt(a2 - p2) given ia = 1/sqrt(a2), ia2 = 1/a2 and p2 >= 0.  Near the
+// paraxial limit (e = p2/a2 < 1e-6) the binomial series
+// (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + ... (truncation < 4e-19) replaces the
+// library reciprocal square root.
+__device__ __forceinline__ double inv_sqrt_diff(double a2, double ia, double ia2, double p2) {
+    const double e = p2 * ia2;
+    if (e < 1e-6) return ia * fma(e, fma(e, 0.375, 0.5), 1.0);
+    return rsqrt(a2 - p2);
+}
+
+// Precession vector Omega (Eq. (6b)) for a transverse field b = (bx, by, 0),
+// frame curvature h; ips = 1/Ps, Ps = longitudinal momentum.
+__device__ __forceinline__ void precession(const Particle& p, const PConst& pc, double bx, double by, double h,
+                                           double ips, double Ps, double& ox, double& oy, double& os) {
+    double ub = (p.Px * bx + p.Py * by) * pc.invP;   // u . b
+    double pre = -(1.0 + h * p.X) * ips;
+    double cu = pc.c * ub * pc.invP;                 // G (gamma-1) (u.b) / P
+    ox = pre * (pc.a * bx - cu * p.Px);
+    oy = pre * (pc.a * by - cu * p.Py) + h;
+    os = -pre * cu * Ps;
+}
+
+template <int K>
+struct LevelProducts {
+    Quat q[K + 1];
+    // edge i of N (N divisible by 2^K): multiply the edge rotation into every
+    // level that samples this edge (the entrance edge starts every level)
+    __device__ __forceinline__ void add_edge(int i, int N, double ds, double ox, double oy, double os) {
+        double w = (i == 0 || i == N) ? 0.5 * ds : ds;
+        Quat e = quat_from_rotvec(w * ox, w * oy, w * os);
+        if (i == 0) {
+            q[K] = e;
+#pragma unroll
+            for (int m = 1; m <= K; ++m) {
+                e = qsquare(e);
+                q[K - m] = e;
+            }
+            return;
+        }
+        q[K] = qmul(e, q[K]);
+#pragma unroll
+        for (int m = 1; m <= K; ++m) {
+            if (i & ((1 << m) - 1)) break;
+            e = qsquare(e);
+            q[K - m] = qmul(e, q[K - m]);
+        }
+    }
+    // Romberg table, Eq. (39b), in place (column j -> j+1), then normalise
+    __device__ __forceinline__ Quat romberg() {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const double f = (double)(1 << (2 * (j + 1)));
+            const double inv = 1.0 / (f - 1.0);
+#pragma unroll
+            for (int k = K; k >= j + 1; --k) {
+                q[k].w = (f * q[k].w - q[k - 1].w) * inv;
+                q[k].x = (f * q[k].x - q[k - 1].x) * inv;
+                q[k].y = (f * q[k].y - q[k - 1].y) * inv;
+                q[k].z = (f * q[k].z - q[k - 1].z) * inv;
+            }
+        }
+        return qnormalize(q[K]);
+    }
+};
+
+// Track particle i for n_turns turns through the lattice in shared memory
+// (table, seq); state in the pair-SoA arrays; qcache is the block's
+// [QC_N][blockDim] shared-memory cache of matrix-kick coefficients.
+template <int K>
+__device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ table, const uint16_t* __restrict__ seq,
+                                                    int n_seq, const RefConst& ref, double2* __restrict__ xpx,
+                                                    double2* __restrict__ ypy, double2* __restrict__ tpt,
+                                                    double2* __restrict__ sxy, double* __restrict__ szp,
+                                                    uint8_t* __restrict__ lost, int64_t i, int n_turns,
+                                                    double* qcache) {
+    Particle p;
+    double2 v = xpx[i];
+    p.X = v.x;
+    p.Px = v.y;
+    v = ypy[i];
+    p.Y = v.x;
+    p.Py = v.y;
+    v = tpt[i];
+    p.T = v.x;
+    PConst pc;
+    pc.Pt = v.y;
+    pc.P2 = 1.0 + 2.0 * pc.Pt * ref.inv_beta0 + pc.Pt * pc.Pt;
+    pc.invP = rsqrt(pc.P2);
+    pc.P = pc.P2 * pc.invP;
+    pc.invP2 = pc.invP * pc.invP;
+    pc.b0pt = ref.inv_beta0 + pc.Pt;
+    const double gamma = ref.gamma0 * (1.0 + ref.beta0 * pc.Pt);
+    pc.a = 1.0 + ref.G * gamma;
+    pc.c = ref.G * (gamma - 1.0);
+    v = sxy[i];
+    double sx = v.x, sy = v.y, sz = szp[i];
+
+    QuadCache qc;
+    qc.key_k = -1.0;
+    qc.key_s = 0.0;
+    qc.col = &qcache[threadIdx.x];
+    qc.stride = blockDim.x;
+    LevelProducts<K> lv;
+    bool is_lost = false;
+
+    for (int turn = 0; turn < n_turns && !is_lost; ++turn) {
+        Quat qt{1.0, 0.0, 0.0, 0.0};
+        for (int e = 0; e < n_seq; ++e) {
+            const DevElem& el = table[seq[e]];
+            const int type = el.type;
+            if (type == ST_SNAKE) {
+                qt = qmul(Quat{el.a[0], el.a[1], el.a[2], el.a[3]}, qt);
+                continue;
+            }
+            const Particle p0 = p;
+            if (type == ST_DRIFT) {
+                double L = el.ds;
+                double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Px * p.Px + p.Py * p.Py);
+                p.X += L * p.Px * ips;
+                p.Y += L * p.Py * ips;
+                p.T += L * (ref.inv_beta0 - pc.b0pt * ips);
+                if (!isfinite(p.X + p.Y + p.T)) {
+                    p = p0;
+                    is_lost = true;
+                    break;
+                }
+                continue;
+            }
+            // spin-carrying element
+            const int N = el.n_slices;
+            const double ds = el.ds;
+            double ox, oy, os;
+            if (type == ST_SBEND) {
+                const double h = el.a[0], eta = el.a[1], cb = el.a[2], sb = el.a[3], ieh = el.a[4],
+                             ieta = el.a[5];
+                const double Pa2 = pc.P2 - p.Py * p.Py;
+                const double iPa = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Py * p.Py);
+                const double iPa2 = iPa * iPa;
+                double ps2 = Pa2 - p.Px * p.Px;
+                double ips = inv_sqrt_diff(Pa2, iPa, iPa2, p.Px * p.Px);
+                double Ps = ps2 * ips;
+                const double by = eta * h;
+                precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
+                lv.add_edge(0, N, ds, ox, oy, os);
+                const double dY = ieta * p.Py * ds;
+                const double dT = -ieta * pc.Pt * ds + (1.0 - ieta) * ds * ref.inv_beta0;
+                for (int s = 1; s <= N; ++s) {
+                    // exact sector-bend map over ds, Eq. (10): (Px, A = Ps - eta(1+hX))
+                    // rotates by h ds; X follows from Ps - A = eta (1 + hX)
+                    const double Pxi = p.Px, Psi = Ps;
+                    double A = Ps - eta * (1.0 + h * p.X);
+                    double Pxf = Pxi * cb + A * sb;
+                    double Af = A * cb - Pxi * sb;
+                    ps2 = Pa2 - Pxf * Pxf;
+                    ips = inv_sqrt_diff(Pa2, iPa, iPa2, Pxf * Pxf);
+                    Ps = ps2 * ips;
+                    p.X = (Ps - Af - eta) * ieh;
+                    p.Px = Pxf;
+                    // asin(Px_i/P_a) - asin(Px_f/P_a) = asin(sin of the difference),
+                    // sin(psi_i - psi_f) = (Px_i Ps_f - Px_f Ps_i) / P_a^2
+                    const double sd = (Pxi * Ps - Pxf * Psi) * iPa2;
+                    double dpsi;
+                    if (fabs(sd) < 1e-2) {
+                        const double x2 = sd * sd;   // Taylor series of asin, truncation < 1e-21 relative
+                        dpsi = sd * fma(x2, fma(x2, fma(x2, fma(x2, 35.0 / 1152.0, 5.0 / 112.0), 3.0 / 40.0),
+                                                1.0 / 6.0), 1.0);
+                    } else {
+                        dpsi = asin(sd);
+                    }
+                    p.Y += dY + ieh * p.Py * dpsi;
+                    p.T += dT - ieh * pc.b0pt * dpsi;
+                    precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
+                    lv.add_edge(s, N, ds, ox, oy, os);
+                }
+            } else if (type == ST_MULT) {
+                const double k1 = el.a[0], k2 = el.a[1];
+                const double half = 0.5 * ds;
+                double pp = p.Px * p.Px + p.Py * p.Py;
+                double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                double Ps = (pc.P2 - pp) * ips;
+                double bx = k1 * p.Y + k2 * p.X * p.Y;
+                double by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
+                precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
+                lv.add_edge(0, N, ds, ox, oy, os);
+                for (int s = 1; s <= N; ++s) {
+                    p.X += half * p.Px * ips;
+                    p.Y += half * p.Py * ips;
+                    p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
+                    by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
+                    bx = k1 * p.Y + k2 * p.X * p.Y;
+                    p.Px -= ds * by;
+                    p.Py += ds * bx;
+                    pp = p.Px * p.Px + p.Py * p.Py;
+                    ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                    Ps = (pc.P2 - pp) * ips;
+                    p.X += half * p.Px * ips;
+                    p.Y += half * p.Py * ips;
+                    p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
+                    bx = k1 * p.Y + k2 * p.X * p.Y;
+                    by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
+                    precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
+                    lv.add_edge(s, N, ds, ox, oy, os);
+                }
+            } else {   // ST_QUAD_MK
+                const double k1 = el.a[0], absk = el.a[1];
+                const double half = 0.5 * ds;
+                if (qc.key_k != absk || qc.key_s != half) quad_coeffs(qc, pc, absk, half);
+                double pp = p.Px * p.Px + p.Py * p.Py;
+                double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                double Ps = (pc.P2 - pp) * ips;
+                precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
+                lv.add_edge(0, N, ds, ox, oy, os);
+                for (int s = 1; s <= N; ++s) {
+                    quad_linear(p, pc, qc, k1);
+                    // nonlinear remainder H_qNL over ds, Eq. (25)
+                    pp = p.Px * p.Px + p.Py * p.Py;
+                    ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                    double d = ips - pc.invP;
+                    p.X += ds * p.Px * d;
+                    p.Y += ds * p.Py * d;
+                    p.T += -ds * pc.b0pt * (ips - pc.invP * pp * 0.5 * pc.invP2) + ds * ref.inv_beta0;
+                    quad_linear(p, pc, qc, k1);
+                    pp = p.Px * p.Px + p.Py * p.Py;
+                    ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                    Ps = (pc.P2 - pp) * ips;
+                    precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
+                    lv.add_edge(s, N, ds, ox, oy, os);
+                }
+            }
+            Quat qe = lv.romberg();
+            if (!isfinite(p.X + p.Px + p.Y + p.Py + p.T + qe.w + qe.x + qe.y + qe.z)) {
+                p = p0;
+                is_lost = true;
+                break;
+            }
+            qt = qmul(qe, qt);
+        }
+        qt = qnormalize(qt);
+        rotate_vec(qt, sx, sy, sz);
+    }
+    xpx[i] = make_double2(p.X, p.Px);
+    ypy[i] = make_double2(p.Y, p.Py);
+    tpt[i].x = p.T;
+    sxy[i] = make_double2(sx, sy);
+    szp[i] = sz;
+    if (is_lost) lost[i] = 1;
+}
+
+}  // namespace st

@@ -1,301 +1,9 @@
-// Mixed-precision spin-orbit tracker: FP32 slice arithmetic, FP64 once per
-// turn.  Same method and discretisation as the FP64 tracker (Sec. 3 orbit
-// maps, Sec. 4.3 trapezoid levels and Romberg table), rearranged so that
-// plain FP32 only carries small quantities:
-//
-// Orbit: every map is written as an increment (cos(h ds) - 1 instead of
-//   cos(h ds), 1/Ps - 1/P instead of 1/Ps, Ps - 1 from (P^2 - 1 - p^2)/(Ps + 1),
-//   ...).  Coordinates are compensated (hi, lo) float pairs; first-order
-//   (linear) terms multiply compensated coordinates by compensated constants
-//   with error-free FMA products and are accumulated with two-sums, so the
-//   linear optics carry no FP32 rounding bias (no systematic tune error);
-//   second-order terms are plain FP32.
-// Spin: an edge rotation q(w Omega) is split exactly into the on-axis,
-//   on-momentum reference rotation r = q(w Omega_ref) (about the vertical in
-//   bends, identity in multipoles) and the small deviation e = r^-1 q, which
-//   is evaluated in FP32 from the deviation of Omega with Taylor coefficients
-//   of cos(t/2) and sin(t/2)/t about the reference angle.  Because every
-//   Romberg level's trapezoid weights add up to the element length, every
-//   level product equals R_L E_k with the same reference rotation R_L, so the
-//   Romberg table and the normalisation act on the near-identity deviations
-//   E_k (scalar part stored minus one) in FP32.  The element rotation R_L D is
-//   multiplied into a compensated (hi, lo) turn quaternion; once per turn it
-//   is composed and renormalised in FP64 and the spin rotated in FP64.
-#include "device_common.cuh"
-#include "ff.cuh"
+// Mixed-precision tracker kernel over one particle ensemble and its
+// launcher; the per-particle integrator is mixed_track_particle in
+// track_mixed.cuh.
+#include "track_mixed.cuh"
 
 namespace st {
-
-// ---- near-identity quaternions (w holds scalar - 1) -------------------------
-struct NQ {
-    float w, x, y, z;
-};
-
-__device__ __forceinline__ NQ nq_mul(const NQ& a, const NQ& b) {
-    NQ o;
-    o.w = a.w + b.w + (a.w * b.w - (a.x * b.x + a.y * b.y + a.z * b.z));
-    o.x = a.x + b.x + (a.w * b.x + b.w * a.x + (a.y * b.z - a.z * b.y));
-    o.y = a.y + b.y + (a.w * b.y + b.w * a.y + (a.z * b.x - a.x * b.z));
-    o.z = a.z + b.z + (a.w * b.z + b.w * a.z + (a.x * b.y - a.y * b.x));
-    return o;
-}
-
-__device__ __forceinline__ NQ nq_square(const NQ& a) {
-    const float t = 2.0f * (1.0f + a.w);
-    NQ o;
-    o.w = 2.0f * a.w + (a.w * a.w - (a.x * a.x + a.y * a.y + a.z * a.z));
-    o.x = t * a.x;
-    o.y = t * a.y;
-    o.z = t * a.z;
-    return o;
-}
-
-__device__ __forceinline__ NQ nq_normalize(const NQ& a) {
-    const float eps = 2.0f * a.w + (a.w * a.w + a.x * a.x + a.y * a.y + a.z * a.z);   // |q|^2 - 1
-    float g;   // (1 + eps)^(-1/2) - 1
-    if (fabsf(eps) < 1e-3f)
-        g = eps * fmaf(eps, fmaf(eps, -0.3125f, 0.375f), -0.5f);
-    else
-        g = rsqrtf(1.0f + eps) - 1.0f;
-    return NQ{a.w + g * (1.0f + a.w), a.x + g * a.x, a.y + g * a.y, a.z + g * a.z};
-}
-
-// Rotation q(b) of a small rotation vector b as a near-identity quaternion:
-// (cos(t/2) - 1, sin(t/2)/t b), t = |b|, Taylor series in u = t^2.
-__device__ __forceinline__ NQ nq_from_small_rotvec(float bx, float by, float bz) {
-    const float u = bx * bx + by * by + bz * bz;
-    float cm1, S;
-    if (u < 0.01f) {
-        cm1 = u * fmaf(u, fmaf(u, -1.0f / 46080.0f, 1.0f / 384.0f), -0.125f);
-        S = fmaf(u, fmaf(u, fmaf(u, -1.0f / 645120.0f, 1.0f / 3840.0f), -1.0f / 48.0f), 0.5f);
-    } else {
-        const float t = sqrtf(u);
-        float sq, cq;
-        sincosf(0.25f * t, &sq, &cq);
-        cm1 = -2.0f * sq * sq;                 // cos(t/2) - 1
-        S = 2.0f * sq * cq / t;                // sin(t/2) / t
-    }
-    return NQ{cm1, S * bx, S * by, S * bz};
-}
-
-// Deviation e = r^-1 q(a + b) of the edge rotation from the reference
-// rotation r = q(a), a = alpha y^, for a small deviation vector b:
-//   e_w = c C + s S (alpha + b_y),  e_v = c S (a + b) - C s y^ - s S y^ x (a + b)
-// with c, s = cos, sin(alpha/2), C = cos(|a+b|/2), S = sin(|a+b|/2)/|a+b|,
-// written in the differences C - c and S - S(alpha^2).
-__device__ __forceinline__ NQ nq_deviation(const MixWeight& W, float bx, float by, float bz) {
-    const float du = fmaf(2.0f * W.alpha, by, bx * bx + by * by + bz * bz);   // |a+b|^2 - alpha^2
-    const float dC = du * fmaf(du, fmaf(du, fmaf(du, W.dC[3], W.dC[2]), W.dC[1]), W.dC[0]);
-    const float dS = du * fmaf(du, fmaf(du, fmaf(du, W.dS[3], W.dS[2]), W.dS[1]), W.dS[0]);
-    const float S = W.S0 + dS;
-    NQ e;
-    e.w = W.ch * dC + W.sh * (W.alpha * dS + S * by);
-    e.x = S * (W.ch * bx - W.sh * bz);
-    e.y = W.ch * (W.alpha * dS + S * by) - W.sh * dC;
-    e.z = S * (W.ch * bz + W.sh * bx);
-    return e;
-}
-
-// ---- compensated turn quaternion -----------------------------------------------
-struct FQ {
-    FF w, x, y, z;
-};
-
-// Q <- (1 + D) Q for a near-identity D: Q + D Q, the correction D Q in FP32
-__device__ __forceinline__ void fq_premul_nq(FQ& q, const NQ& d) {
-    const float qw = q.w.hi, qx = q.x.hi, qy = q.y.hi, qz = q.z.hi;
-    const float cw = d.w * qw - (d.x * qx + d.y * qy + d.z * qz);
-    const float cx = d.w * qx + qw * d.x + (d.y * qz - d.z * qy);
-    const float cy = d.w * qy + qw * d.y + (d.z * qx - d.x * qz);
-    const float cz = d.w * qz + qw * d.z + (d.x * qy - d.y * qx);
-    q.w = ff_add_f(q.w, cw);
-    q.x = ff_add_f(q.x, cx);
-    q.y = ff_add_f(q.y, cy);
-    q.z = ff_add_f(q.z, cz);
-}
-
-// Q <- R Q for a compensated reference rotation R
-__device__ __forceinline__ void fq_premul_ref(FQ& q, const float2* rq) {
-    const FF a0{rq[0].x, rq[0].y}, a1{rq[1].x, rq[1].y}, a2{rq[2].x, rq[2].y}, a3{rq[3].x, rq[3].y};
-    FQ o;
-    o.w = ff_add(ff_add(ff_mul(a0, q.w), ff_neg(ff_mul(a1, q.x))), ff_neg(ff_add(ff_mul(a2, q.y), ff_mul(a3, q.z))));
-    o.x = ff_add(ff_add(ff_mul(a0, q.x), ff_mul(a1, q.w)), ff_add(ff_mul(a2, q.z), ff_neg(ff_mul(a3, q.y))));
-    o.y = ff_add(ff_add(ff_mul(a0, q.y), ff_neg(ff_mul(a1, q.z))), ff_add(ff_mul(a2, q.w), ff_mul(a3, q.x)));
-    o.z = ff_add(ff_add(ff_mul(a0, q.z), ff_mul(a1, q.y)), ff_add(ff_neg(ff_mul(a2, q.x)), ff_mul(a3, q.w)));
-    q = o;
-}
-
-// ---- per-particle constants ---------------------------------------------------
-struct MConst {
-    FF invP, tau, PM1;                     // 1/P; 1/beta0 - (1/beta0 + Pt)/P; P - 1
-    float Pt, P2, P2m1, invPf, P, b0pt, a, c, da, f3, a0;
-};
-
-struct MState {
-    FF X, Px, Y, Py, T;
-};
-
-// 1/Ps as a compensated value and d = 1/Ps - 1/P in FP32, from the
-// transverse momenta: 1/Ps = (1/P)(1 - e)^(-1/2), e = p^2/P^2.
-__device__ __forceinline__ FF inv_ps(const MConst& k, float px, float py, float& d, float& pp) {
-    pp = px * px + py * py;
-    const float e = pp * k.invPf * k.invPf;
-    if (e < 1e-4f) {
-        d = k.invPf * e * fmaf(e, fmaf(e, 0.3125f, 0.375f), 0.5f);
-    } else {
-        const float ips = rsqrtf(k.P2 - pp);
-        d = pp * k.invPf * ips / (k.P + (k.P2 - pp) * ips);
-    }
-    return ff_add_f(k.invP, d);
-}
-
-__device__ __forceinline__ void drift_inc(MState& z, const MConst& k, const FF& L, const FF& ips, float d) {
-    const FF Lips = ff_mul(L, ips);
-    z.X = ff_add(z.X, ff_mul(Lips, z.Px));
-    z.Y = ff_add(z.Y, ff_mul(Lips, z.Py));
-    z.T = ff_add(z.T, ff_mul(L, ff_add_f(k.tau, -k.b0pt * d)));
-}
-
-// precession vector for a straight element with field b = (bx, by, 0)
-__device__ __forceinline__ void omega_straight(const MConst& k, float px, float py, float bx, float by, float ips,
-                                               float Ps, float& ox, float& oy, float& os) {
-    const float ub = (px * bx + py * by) * k.invPf;
-    const float cu = k.c * ub * k.invPf;
-    ox = -ips * (k.a * bx - cu * px);
-    oy = -ips * (k.a * by - cu * py);
-    os = ips * cu * Ps;
-}
-
-// cached matrix-kick coefficients of the half-slice linear flow (computed in
-// FP64 when the (|k1|, s) key changes): for the cos plane (1) and the cosh
-// plane (2): C - 1, S/P and |k1| S as compensated pairs, and the FP32 time
-// coefficients (s + C S)/2, S^2, (s - C S)/2.
-struct MQuad {
-    float key_k, key_s;
-    FF Cm1[2], SP[2], kS[2];
-    float al[2], be[2], ga[2];
-};
-
-__device__ __forceinline__ void mquad_coeffs(MQuad& q, double invP, double absk, double s, float key_k, float key_s) {
-    q.key_k = key_k;
-    q.key_s = key_s;
-    const double w = sqrt(absk * invP);
-    const double ds = s;
-    const double ws = w * ds;
-    double Cm1[2], S[2];
-    if (w > 0.0) {
-        double sh, ch;
-        sincos(0.5 * ws, &sh, &ch);
-        Cm1[0] = -2.0 * sh * sh;
-        S[0] = 2.0 * sh * ch / w;
-        const double e = exp(0.5 * ws), ei = 1.0 / e;
-        const double shh = 0.5 * (e - ei), chh = 0.5 * (e + ei);
-        Cm1[1] = 2.0 * shh * shh;
-        S[1] = 2.0 * shh * chh / w;
-    } else {
-        Cm1[0] = Cm1[1] = 0.0;
-        S[0] = S[1] = ds;
-    }
-    for (int p = 0; p < 2; ++p) {
-        const double C = 1.0 + Cm1[p];
-        q.Cm1[p] = ff_make(Cm1[p]);
-        q.SP[p] = ff_make(S[p] * invP);
-        q.kS[p] = ff_make(absk * S[p]);
-        q.al[p] = (float)(0.5 * (ds + C * S[p]));
-        q.be[p] = (float)(S[p] * S[p]);
-        q.ga[p] = (float)(0.5 * (ds - C * S[p]));
-    }
-}
-
-// linear quadrupole flow H_qL over a half slice, Eq. (24), in increment form:
-// dU = U (C-1) + Pu (S/P),  dPu = Pu (C-1) -/+ k1 U S
-__device__ __forceinline__ void quad_linear_inc(MState& z, const MConst& k, const MQuad& q, float k1) {
-    const int px_ = k1 >= 0.0f ? 0 : 1, py_ = 1 - px_;
-    const float sgn = k1 >= 0.0f ? 1.0f : -1.0f;
-    const float X = z.X.hi, Px = z.Px.hi, Y = z.Y.hi, Py = z.Py.hi;
-    const float Pk = k.P * k1;
-    const float tsum = Px * Px * q.al[px_] - k1 * X * Px * q.be[px_] + Pk * X * X * q.ga[px_] +
-                       Py * Py * q.al[py_] + k1 * Y * Py * q.be[py_] - Pk * Y * Y * q.ga[py_];
-    const FF dX = ff_add(ff_mul(z.X, q.Cm1[px_]), ff_mul(z.Px, q.SP[px_]));
-    const FF dPx = ff_add(ff_mul(z.Px, q.Cm1[px_]), ff_neg(ff_mul_f(ff_mul(z.X, q.kS[px_]), sgn)));
-    const FF dY = ff_add(ff_mul(z.Y, q.Cm1[py_]), ff_mul(z.Py, q.SP[py_]));
-    const FF dPy = ff_add(ff_mul(z.Py, q.Cm1[py_]), ff_mul_f(ff_mul(z.Y, q.kS[py_]), sgn));
-    z.X = ff_add(z.X, dX);
-    z.Px = ff_add(z.Px, dPx);
-    z.Y = ff_add(z.Y, dY);
-    z.Py = ff_add(z.Py, dPy);
-    z.T = ff_add_f(z.T, -k.f3 * tsum);
-}
-
-template <int K>
-struct MixLevels {
-    NQ q[K + 1];
-
-    // straight elements (no reference rotation): levels by squaring
-    __device__ __forceinline__ void add_straight(int i, int N, float ds, float ox, float oy, float os) {
-        const float w = (i == 0 || i == N) ? 0.5f * ds : ds;
-        NQ e = nq_from_small_rotvec(w * ox, w * oy, w * os);
-        if (i == 0) {
-            q[K] = e;
-#pragma unroll
-            for (int m = 1; m <= K; ++m) {
-                e = nq_square(e);
-                q[K - m] = e;
-            }
-            return;
-        }
-        q[K] = nq_mul(e, q[K]);
-#pragma unroll
-        for (int m = 1; m <= K; ++m) {
-            if (i & ((1 << m) - 1)) break;
-            e = nq_square(e);
-            q[K - m] = nq_mul(e, q[K - m]);
-        }
-    }
-
-    // bends: for every level sampling edge i, the deviation of the level's edge
-    // rotation from its reference rotation, conjugated by the reference
-    // rotation accumulated over the level's earlier edges (angle
-    // omr i ds - alpha_m, the trapezoid end weight alpha_m = omr 2^m ds / 2)
-    __device__ __forceinline__ void add_bend(int i, int N, const MixElem& el, float rc, float rs, float dox,
-                                             float doy, float dos) {
-#pragma unroll
-        for (int m = 0; m <= K; ++m) {
-            if (m > 0 && (i & ((1 << m) - 1))) break;
-            const int j = (i == 0 || i == N) ? m : m + 1;
-            const float w = ldexpf(el.ds, j) * 0.5f;
-            NQ e = nq_deviation(el.w[j], w * dox, w * doy, w * dos);
-            if (i == 0) {
-                q[K - m] = e;
-                continue;
-            }
-            const MixWeight& Wm = el.w[m];
-            const float cphi = rc * Wm.cf + rs * Wm.sf;
-            const float sphi = rs * Wm.cf - rc * Wm.sf;
-            const float ex = e.x * cphi - e.z * sphi;
-            const float ez = e.x * sphi + e.z * cphi;
-            e.x = ex;
-            e.z = ez;
-            q[K - m] = nq_mul(e, q[K - m]);
-        }
-    }
-
-    __device__ __forceinline__ NQ romberg() {
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const float f = (float)(1 << (2 * (j + 1)));
-            const float inv = 1.0f / (f - 1.0f);
-#pragma unroll
-            for (int k = K; k >= j + 1; --k) {
-                q[k].w = (f * q[k].w - q[k - 1].w) * inv;
-                q[k].x = (f * q[k].x - q[k - 1].x) * inv;
-                q[k].y = (f * q[k].y - q[k - 1].y) * inv;
-                q[k].z = (f * q[k].z - q[k - 1].z) * inv;
-            }
-        }
-        return nq_normalize(q[K]);
-    }
-};
 
 template <int K>
 __global__ void __launch_bounds__(128, 4) track_mixed_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
@@ -321,233 +29,7 @@ __global__ void __launch_bounds__(128, 4) track_mixed_kernel(const void* __restr
         const int64_t i = wi * 32 + lane;
         if (i >= n || lost[i]) continue;
 
-        // state and per-particle constants (FP64 -> compensated FP32)
-        MState z;
-        double2 v = xpx[i];
-        z.X = ff_make(v.x);
-        z.Px = ff_make(v.y);
-        v = ypy[i];
-        z.Y = ff_make(v.x);
-        z.Py = ff_make(v.y);
-        v = tpt[i];
-        z.T = ff_make(v.x);
-        const double Pt = v.y;
-        MConst k;
-        double invP64;
-        {
-            const double P2m1 = 2.0 * Pt * ref.inv_beta0 + Pt * Pt;
-            const double P2 = 1.0 + P2m1;
-            invP64 = rsqrt(P2);
-            const double P = P2 * invP64;
-            const double b0pt = ref.inv_beta0 + Pt;
-            const double gamma = ref.gamma0 * (1.0 + ref.beta0 * Pt);
-            k.invP = ff_make(invP64);
-            k.PM1 = ff_make(P2m1 / (P + 1.0));
-            // 1/beta0 - (1/beta0 + Pt)/P = ((P - 1) - beta0 Pt) / (beta0 P)
-            k.tau = ff_make((P2m1 / (P + 1.0) - ref.beta0 * Pt) * ref.inv_beta0 * invP64);
-            k.Pt = (float)Pt;
-            k.P2 = (float)P2;
-            k.P2m1 = (float)P2m1;
-            k.invPf = (float)invP64;
-            k.P = (float)P;
-            k.b0pt = (float)b0pt;
-            k.a = (float)(1.0 + ref.G * gamma);
-            k.c = (float)(ref.G * (gamma - 1.0));
-            k.da = (float)(ref.G * ref.gamma0 * ref.beta0 * Pt);
-            k.f3 = (float)(0.5 * b0pt * invP64 * invP64 * invP64);
-            k.a0 = (float)(1.0 + ref.G * ref.gamma0);
-        }
-        v = sxy[i];
-        double sx = v.x, sy = v.y, sz = szp[i];
-
-        MQuad mq;
-        mq.key_k = -1.0f;
-        mq.key_s = 0.0f;
-        MixLevels<K> lv;
-        bool is_lost = false;
-
-        for (int turn = 0; turn < n_turns && !is_lost; ++turn) {
-            FQ qt{FF{1.0f, 0.0f}, FF{0.0f, 0.0f}, FF{0.0f, 0.0f}, FF{0.0f, 0.0f}};
-            for (int e = 0; e < n_seq; ++e) {
-                const MixElem& el = table[seq[e]];
-                const int type = el.type;
-                if (type == ST_SNAKE) {
-                    fq_premul_ref(qt, el.rq);
-                    continue;
-                }
-                const MState z0 = z;
-                float d, pp;
-                if (type == ST_DRIFT) {
-                    const FF ips = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-                    drift_inc(z, k, FF{el.ds_ff.x, el.ds_ff.y}, ips, d);
-                    if (!isfinite(z.X.hi + z.Y.hi + z.T.hi)) {
-                        z = z0;
-                        is_lost = true;
-                        break;
-                    }
-                    continue;
-                }
-                const int N = el.n_slices;
-                const float ds = el.ds;
-                float ox, oy, os;
-                if (type == ST_SBEND) {
-                    const float h = el.h, eta = el.eta;
-                    const float py = z.Py.hi;
-                    const float Pa2 = k.P2 - py * py;
-                    const float iPa2 = 1.0f / Pa2;
-                    float px = z.Px.hi;
-                    float ps2 = Pa2 - px * px;
-                    float ips = rsqrtf(ps2);
-                    float Ps = ps2 * ips;
-                    // Ps - 1 = (P - 1) + (Ps - P), the second term -p^2/(Ps + P) second order
-                    FF PsM1 = ff_add_f(k.PM1, -(px * px + py * py) / (Ps + k.P));
-                    const float etah = eta * h;
-                    const float cu = k.c * py * etah * k.invPf * k.invPf;     // G(gamma-1)(u.b)/P, u.b = Py eta h / P
-                    const FF ietads{el.ietads_ff.x, el.ietads_ff.y};
-                    const FF sbieh{el.sbieh_ff.x, el.sbieh_ff.y};
-                    const FF sbff{el.sb_ff.x, el.sb_ff.y};
-                    const FF cbmieh{el.cbmieh_ff.x, el.cbmieh_ff.y};
-                    const FF etahff{el.etah_ff.x, el.etah_ff.y};
-                    const FF omeff{el.ome_ff.x, el.ome_ff.y};
-                    const float dT0 = -el.ieta * k.Pt * ds + el.dT_eta;
-                    // deviation of Omega (Eq. (6b)) from the on-axis reference:
-                    //   dOy = eta h [a0 (Ps - 1 - hX) - (1 + hX) (a - a0)] / Ps + (1 + hX) cu Py / Ps
-                    //   dOx = (1 + hX) cu Px / Ps,  dOs = (1 + hX) cu
-                    auto dev_omega = [&](float X, float Pxv, float Psv, float PsM1v, float ipsv, float& dx, float& dy,
-                                         float& dz) {
-                        const float hX = h * X;
-                        const float g = (1.0f + hX) * ipsv;
-                        dy = etah * (k.a0 * (PsM1v - hX) * ipsv - g * k.da) + g * cu * py;
-                        dx = g * cu * Pxv;
-                        dz = g * cu * Psv;
-                    };
-                    dev_omega(z.X.hi, px, Ps, PsM1.hi, ips, ox, oy, os);
-                    const float2* rh = rho + el.rho_off;
-                    lv.add_bend(0, N, el, 1.0f, 0.0f, ox, oy, os);
-                    for (int s = 1; s <= N; ++s) {
-                        // exact bend over ds, Eq. (10): (Px, A = Ps - eta(1+hX)) rotates by h ds;
-                        // dX = (dPs - dA)/(eta h) with dA = A (cos - 1) - Px sin
-                        // A = (Ps - 1) + (1 - eta) - eta h X, compensated (first order in the
-                        // momentum deviation and in X)
-                        const FF Aff = ff_add(ff_add(PsM1, omeff), ff_neg(ff_mul(etahff, z.X)));
-                        const float A = Aff.hi;
-                        const FF dPxff = ff_add_f(ff_mul(Aff, sbff), px * el.cbm1);
-                        const float dPx = dPxff.hi;
-                        const float pxf = px + dPx;
-                        const float ps2f = Pa2 - pxf * pxf;
-                        const float ipsf = rsqrtf(ps2f);
-                        const float Psf = ps2f * ipsf;
-                        const float dPs = -dPx * (px + pxf) / (Ps + Psf);
-                        const float sd = (px * dPs - dPx * Ps) * iPa2;   // sin(psi_i - psi_f)
-                        float dpsi;
-                        if (fabsf(sd) < 1e-2f) {
-                            const float x2 = sd * sd;
-                            dpsi = sd * fmaf(x2, fmaf(x2, 3.0f / 40.0f, 1.0f / 6.0f), 1.0f);
-                        } else {
-                            dpsi = asinf(sd);
-                        }
-                        // dX = (dPs - dA)/(eta h), dA = A (cos - 1) - Px sin
-                        const FF dX = ff_add_f(ff_add(ff_mul(z.Px, sbieh), ff_neg(ff_mul(Aff, cbmieh))), dPs * el.ieh);
-                        const FF dY = ff_add_f(ff_mul(z.Py, ietads), el.ieh * py * dpsi);
-                        z.X = ff_add(z.X, dX);
-                        z.Px = ff_add(z.Px, dPxff);
-                        z.Y = ff_add(z.Y, dY);
-                        z.T = ff_add_f(z.T, dT0 - el.ieh * k.b0pt * dpsi);
-                        (void)A;
-                        px = z.Px.hi;
-                        ps2 = Pa2 - px * px;
-                        ips = rsqrtf(ps2);
-                        Ps = ps2 * ips;
-                        PsM1 = ff_add_f(k.PM1, -(px * px + py * py) / (Ps + k.P));
-                        dev_omega(z.X.hi, px, Ps, PsM1.hi, ips, ox, oy, os);
-                        const float2 r = rh[s];
-                        lv.add_bend(s, N, el, r.x, r.y, ox, oy, os);
-                    }
-                } else if (type == ST_MULT) {
-                    const float k1 = el.k1, k2 = el.k2;
-                    const FF half{0.5f * el.ds_ff.x, 0.5f * el.ds_ff.y};
-                    const FF k1ds{el.k1ds_ff.x, el.k1ds_ff.y};
-                    const FF k2h{el.k2h_ff.x, el.k2h_ff.y};
-                    const FF k2ds{el.k2ds_ff.x, el.k2ds_ff.y};
-                    FF ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-                    float ips = ips_ff.hi, Ps = (k.P2 - pp) * ips;
-                    {
-                        const float X = z.X.hi, Y = z.Y.hi;
-                        const float bx = k1 * Y + k2 * X * Y;
-                        const float by = k1 * X + 0.5f * k2 * (X * X - Y * Y);
-                        omega_straight(k, z.Px.hi, z.Py.hi, bx, by, ips, Ps, ox, oy, os);
-                    }
-                    lv.add_straight(0, N, ds, ox, oy, os);
-                    for (int s = 1; s <= N; ++s) {
-                        drift_inc(z, k, half, ips_ff, d);
-                        {
-                            // kick of H_m over ds, compensated (the sextupole kick is first order
-                            // in the betatron offset around a dispersive orbit)
-                            const FF x2my2 = ff_add(ff_mul(z.X, z.X), ff_neg(ff_mul(z.Y, z.Y)));
-                            const FF kx = ff_add(ff_mul(z.X, k1ds), ff_mul(x2my2, k2h));
-                            const FF ky = ff_add(ff_mul(z.Y, k1ds), ff_mul(ff_mul(z.X, z.Y), k2ds));
-                            z.Px = ff_add(z.Px, ff_neg(kx));
-                            z.Py = ff_add(z.Py, ky);
-                        }
-                        ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-                        ips = ips_ff.hi;
-                        Ps = (k.P2 - pp) * ips;
-                        drift_inc(z, k, half, ips_ff, d);
-                        const float X = z.X.hi, Y = z.Y.hi;
-                        const float bx = k1 * Y + k2 * X * Y;
-                        const float by = k1 * X + 0.5f * k2 * (X * X - Y * Y);
-                        omega_straight(k, z.Px.hi, z.Py.hi, bx, by, ips, Ps, ox, oy, os);
-                        lv.add_straight(s, N, ds, ox, oy, os);
-                    }
-                } else {   // ST_QUAD_MK
-                    const float k1 = el.k1, absk = el.k2;
-                    const float half = 0.5f * ds;
-                    if (mq.key_k != absk || mq.key_s != half)
-                        mquad_coeffs(mq, invP64, (double)el.k1ds_ff.x + (double)el.k1ds_ff.y,
-                                     0.5 * ((double)el.ds_ff.x + (double)el.ds_ff.y), absk, half);
-                    FF ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-                    float ips = ips_ff.hi, Ps = (k.P2 - pp) * ips;
-                    omega_straight(k, z.Px.hi, z.Py.hi, k1 * z.Y.hi, k1 * z.X.hi, ips, Ps, ox, oy, os);
-                    lv.add_straight(0, N, ds, ox, oy, os);
-                    const FF dsff{el.ds_ff.x, el.ds_ff.y};
-                    for (int s = 1; s <= N; ++s) {
-                        quad_linear_inc(z, k, mq, k1);
-                        inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-                        // H_qNL over ds, Eq. (25), in increment form:
-                        // dX = ds Px (1/Ps - 1/P); dT = ds [tau - (1/beta0+Pt)(d - p^2/(2P^3))]
-                        z.X = ff_add_f(z.X, ds * z.Px.hi * d);
-                        z.Y = ff_add_f(z.Y, ds * z.Py.hi * d);
-                        z.T = ff_add(z.T, ff_mul(dsff, ff_add_f(k.tau, -k.b0pt * (d - 0.5f * pp * k.invPf * k.invPf * k.invPf))));
-                        quad_linear_inc(z, k, mq, k1);
-                        ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-                        ips = ips_ff.hi;
-                        Ps = (k.P2 - pp) * ips;
-                        omega_straight(k, z.Px.hi, z.Py.hi, k1 * z.Y.hi, k1 * z.X.hi, ips, Ps, ox, oy, os);
-                        lv.add_straight(s, N, ds, ox, oy, os);
-                    }
-                }
-                const NQ dq = lv.romberg();
-                if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi + dq.w + dq.x + dq.y + dq.z)) {
-                    z = z0;
-                    is_lost = true;
-                    break;
-                }
-                // element rotation R_L (1 + D) into the compensated turn quaternion
-                fq_premul_nq(qt, dq);
-                if (type == ST_SBEND) fq_premul_ref(qt, el.rq);
-            }
-            // FP64 once per turn: compose, renormalise, rotate the spin (a particle lost
-            // inside the turn gets the rotation up to the element where it was lost)
-            Quat q64{ff_to_double(qt.w), ff_to_double(qt.x), ff_to_double(qt.y), ff_to_double(qt.z)};
-            q64 = qnormalize(q64);
-            rotate_vec(q64, sx, sy, sz);
-        }
-        xpx[i] = make_double2(ff_to_double(z.X), ff_to_double(z.Px));
-        ypy[i] = make_double2(ff_to_double(z.Y), ff_to_double(z.Py));
-        tpt[i].x = ff_to_double(z.T);
-        sxy[i] = make_double2(sx, sy);
-        szp[i] = sz;
-        if (is_lost) lost[i] = 1;
+        mixed_track_particle<K>(table, seq, rho, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns);
     }
 }
 

@@ -1,0 +1,94 @@
+"""Batched uneven jobs in one persistent launch (work queue, CUDA-graph turn
+loop, autotuner) through the C ABI: every job's result must equal tracking
+that job alone with the single-job entry point (same integrator), and the
+FP64 batch must match the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1501_03450_b300 as st
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+def small_jobs(n_jobs=6, seed=5):
+    jobs = W.batched_jobs(n_jobs=n_jobs, seed=seed, turns=3, min_cells=2, max_cells=14, min_particles=20,
+                          max_particles=700)
+    for j in jobs:
+        j["ring"] = W.with_spin_order(j["ring"], 2)
+    return jobs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_batch_equals_single_job_tracking(precision, use_graph):
+    jobs = small_jobs()
+    b = st.Batch([j["ring"] for j in jobs], [j["n_particles"] for j in jobs], precision)
+    b.set_launch(use_graph=use_graph, turns_per_launch=2)
+    inputs = []
+    for k, j in enumerate(jobs):
+        gg = j["ring"]["Ggamma0"]
+        z, S = W.gaussian_particles(j["n_particles"], gg, seed=j["seed"])
+        if k == 1:
+            z[1, 3] = 1.5                      # a lost particle in one job
+        inputs.append((z, S))
+        b.upload(k, z, S)
+    b.track(3, 2)
+    for k, j in enumerate(jobs):
+        zb, Sb, lb = b.download(k)
+        zs, Ss, ls = st.track(j["ring"], *inputs[k], 3, 2, precision=precision)
+        assert np.array_equal(lb, ls)
+        assert np.abs(zb - zs).max() < TOL and np.abs(Sb - Ss).max() < TOL, (k, precision)
+    b.close()
+
+
+def test_batch_fp64_matches_oracle_and_graph_replay():
+    jobs = small_jobs(n_jobs=4, seed=9)
+    b = st.Batch([j["ring"] for j in jobs], [j["n_particles"] for j in jobs], "fp64")
+    inputs = []
+    for k, j in enumerate(jobs):
+        z, S = W.gaussian_particles(j["n_particles"], j["ring"]["Ggamma0"], seed=j["seed"])
+        inputs.append((z, S))
+        b.upload(k, z, S)
+    b.track(2, 2)
+    b.track(2, 2)                              # replays the captured graph
+    for k, j in enumerate(jobs):
+        zb, Sb, lb = b.download(k)
+        zo, So, lo = oracle.track(j["ring"], *inputs[k], 4, 2)
+        assert np.array_equal(lb, lo)
+        assert np.abs(zb - zo).max() < TOL and np.abs(Sb - So).max() < TOL
+    b.close()
+
+
+def test_batch_autotune_keeps_state_and_results():
+    jobs = small_jobs(n_jobs=5, seed=13)
+    b = st.Batch([j["ring"] for j in jobs], [j["n_particles"] for j in jobs], "fp64")
+    inputs = []
+    for k, j in enumerate(jobs):
+        z, S = W.gaussian_particles(j["n_particles"], j["ring"]["Ggamma0"], seed=j["seed"])
+        inputs.append((z, S))
+        b.upload(k, z, S)
+    best = b.autotune(2, trial_turns=1)
+    assert best["block_threads"] in (64, 96, 128) and best["turns_per_launch"] in (1,) and best["ms"] > 0
+    z0, S0, _ = b.download(0)                  # state restored after the trials
+    assert np.array_equal(z0, inputs[0][0]) and np.array_equal(S0, inputs[0][1])
+    b.track(2, 2)
+    for k, j in enumerate(jobs):
+        zb, Sb, _ = b.download(k)
+        zs, Ss, _ = st.track(j["ring"], *inputs[k], 2, 2)
+        assert np.abs(zb - zs).max() < TOL and np.abs(Sb - Ss).max() < TOL
+    b.close()
+
+
+def test_batch_errors():
+    jobs = small_jobs(n_jobs=2, seed=1)
+    b = st.Batch([j["ring"] for j in jobs], [j["n_particles"] for j in jobs], "fp64")
+    with pytest.raises(st.SpinTrackError) as e:
+        b.track(1, 2)                          # nothing uploaded
+    assert e.value.code == st.ST_ESTATE
+    with pytest.raises(st.SpinTrackError):
+        b.set_launch(block_threads=256)
+    b.close()
