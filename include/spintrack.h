@@ -204,6 +204,16 @@ int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, const st_ref
                           double* state, uint8_t* lost, int64_t n_particles, int32_t n_turns,
                           int32_t spin_order, void* cuda_stream);
 
+/* BF16 tensor-core GEMM (tcgen05, TMA-fed, FP32 accumulation in tensor
+ * memory): D[M][N] = A[M][K] . B[N][K]^T (+ bias[N] if bias != NULL).  All
+ * pointers are device memory: A, B bf16 row-major, D and bias FP32; M a
+ * multiple of 128, K of 64, N of 16; A and B 16-byte aligned.  Asynchronous on
+ * cuda_stream; *status (device int32, caller-cleared) becomes nonzero if a
+ * bounded wait expired.  This is the building block of the learned spin map's
+ * kernels.  Errors: ST_EINVAL (shapes, alignment), ST_ECUDA. */
+int st_gemm_bf16(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K, const float* bias,
+                 int32_t* status, void* cuda_stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char* st_last_error(void);
 

@@ -68,6 +68,7 @@ SIGNATURES = {
     "st_batch_autotune": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "st_gemm_bf16": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
     "st_last_error": ([], ctypes.c_char_p),
     "st_version": ([], ctypes.c_char_p),
 }
@@ -254,6 +255,11 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def st_gemm_bf16(A_ptr: int, B_ptr: int, D_ptr: int, M: int, N: int, K: int, bias_ptr: Optional[int],
+                 status_ptr: int, stream: Optional[int] = None) -> None:
+    _check(load().st_gemm_bf16(A_ptr, B_ptr, D_ptr, int(M), int(N), int(K), bias_ptr, status_ptr, stream))
 
 
 def pairs_from_soa(z: np.ndarray, S: np.ndarray) -> np.ndarray:

@@ -1,0 +1,267 @@
+// BF16 tensor-core GEMM on the 5th-generation tensor cores (tcgen05), written
+// directly in PTX:  D[M x N] = A[M x K] . B[N x K]^T  (+ fused epilogue),
+// A and B bf16 row-major (K contiguous, "K-major" for both operands), FP32
+// accumulation in tensor memory (TMEM).
+//
+// One CTA of 128 threads computes a 128 x BN tile:
+//   thread 0   : TMA producer -- 2D tensor-map loads of 64-wide K blocks of A
+//                and B into a 4-stage shared-memory ring, 128-byte swizzle
+//                (the canonical K-major SW128 layout the MMA reads directly);
+//   thread 32  : MMA issuer -- 4 x tcgen05.mma (K = 16 each) per K block,
+//                tcgen05.commit to the stage's "empty" barrier, and to the
+//                "done" barrier after the last block;
+//   all 4 warps: epilogue -- tcgen05.ld of their 32 TMEM lanes (= rows),
+//                bias / SiLU / SiLU-derivative, FP32 or BF16 stores (row-major
+//                and, for backward passes, transposed).
+// Every mbarrier wait is bounded (about one second); on expiry the CTA sets
+// the status word, waits once more for work in flight, frees its TMEM and
+// returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "device_common.cuh"
+
+namespace st {
+
+enum GemmEpiMode : int32_t { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_SILU = 2, EPI_DSILU = 3 };
+
+struct GemmEpi {
+    int32_t mode;
+    int32_t n_valid;                 // columns >= n_valid are written as zero to the bf16 outputs
+    float* out_f32;                  // [M][ld_f32]
+    int32_t ld_f32;
+    const float* bias;               // [N]
+    __nv_bfloat16* out_bf16;         // [M][ld_bf16]
+    int32_t ld_bf16;
+    __nv_bfloat16* out_bf16_t;       // [N][ld_bf16_t] (transposed)
+    int32_t ld_bf16_t;
+    const float* z_in;               // [M][ld_z] pre-activations (EPI_DSILU)
+    int32_t ld_z;
+    float* z_out;                    // [M][ld_zo] pre-activations (EPI_BIAS_SILU)
+    int32_t ld_zo;
+};
+
+enum { STATUS_MMA_TIMEOUT = 2 };
+
+// ---- tcgen05 / TMA primitives ---------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(tm), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
+// swizzled layout: rows of 128 bytes (64 bf16 along K), 8-row atoms of 1024
+// bytes (stride byte offset 1024), start address in 16-byte units, version 1,
+// layout type 2 = 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
+    const uint64_t addr = smem_u32(p);
+    uint64_t d = (addr & 0x3FFFFull) >> 4;
+    d |= 1ull << 16;                       // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;      // stride byte offset
+    d |= 1ull << 46;                       // descriptor version
+    d |= 2ull << 61;                       // swizzle mode: 128 B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M x N.
+template <int M, int N>
+__host__ __device__ constexpr uint32_t idesc_bf16_f32() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int NC>
+__device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float* v);
+
+template <>
+__device__ __forceinline__ void tmem_load_cols<32>(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_load_cols<16>(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+    const float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+template <int BN>
+struct GemmCfg {
+    static constexpr int BM = 128, BK = 64, STAGES = 4;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + alignment slack
+    static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN;        // power of two >= 32
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                              const __grid_constant__ CUtensorMap tmB, int K,
+                                                              GemmEpi epi, int32_t* status) {
+    using C = GemmCfg<BN>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full_bar[C::STAGES], empty_bar[C::STAGES], done_bar;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int32_t abort_s;
+    const int warp = threadIdx.x >> 5;
+    const int m0 = blockIdx.x * C::BM;
+    const int n0 = blockIdx.y * BN;
+    const int kblocks = K / C::BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        abort_s = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base_s, C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+    const uint64_t limit = 1000000000ull;
+
+    if (threadIdx.x == 0) {
+        // TMA producer
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int s = kb % C::STAGES;
+            if (kb >= C::STAGES) {
+                if (!mbar_wait_bounded_parity(&empty_bar[s], ((kb / C::STAGES) - 1) & 1, limit)) {
+                    atomicExch(&abort_s, 1);
+                    break;
+                }
+            }
+            unsigned char* a = smem + s * C::STAGE_BYTES;
+            unsigned char* b = a + C::A_BYTES;
+            mbar_arrive_expect_tx(&full_bar[s], C::STAGE_BYTES);
+            tma_load_2d(a, &tmA, kb * C::BK, m0, &full_bar[s]);
+            tma_load_2d(b, &tmB, kb * C::BK, n0, &full_bar[s]);
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_bf16_f32<128, BN>();
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int s = kb % C::STAGES;
+            if (!mbar_wait_bounded_parity(&full_bar[s], (kb / C::STAGES) & 1, limit)) {
+                atomicExch(&abort_s, 1);
+                break;
+            }
+            tc_fence_after();
+            const unsigned char* a = smem + s * C::STAGE_BYTES;
+            const unsigned char* b = a + C::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < C::BK / 16; ++kk)
+                tc_mma_bf16(tmem, smem_desc_sw128(a + kk * 32), smem_desc_sw128(b + kk * 32), idesc,
+                            (kb > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(&empty_bar[s]);
+        }
+        tc_commit(&done_bar);
+    }
+    // epilogue: every thread owns TMEM lane (= row) threadIdx.x
+    const bool done_ok = mbar_wait_bounded_parity(&done_bar, 0, limit);
+    tc_fence_after();
+    __syncthreads();
+    if (!done_ok || abort_s) {
+        if (threadIdx.x == 0) atomicExch(status, STATUS_MMA_TIMEOUT);
+        if (!done_ok) mbar_wait_bounded_parity(&done_bar, 0, limit);   // let work in flight drain
+    } else {
+        const int row = m0 + threadIdx.x;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        constexpr int CH = BN < 32 ? BN : 32;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += CH) {
+            float v[CH];
+            tmem_load_cols<CH>(lane_addr + c0, v);
+            const int nb = n0 + c0;
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+                const int col = nb + j;
+                float x = v[j];
+                if (epi.mode == EPI_F32) {
+                    epi.out_f32[(size_t)row * epi.ld_f32 + col] = x;
+                } else if (epi.mode == EPI_BIAS_F32) {
+                    epi.out_f32[(size_t)row * epi.ld_f32 + col] = x + epi.bias[col];
+                } else {
+                    float y;
+                    if (epi.mode == EPI_BIAS_SILU) {
+                        const float z = x + epi.bias[col];
+                        if (epi.z_out) epi.z_out[(size_t)row * epi.ld_zo + col] = z;
+                        y = silu_f(z);
+                    } else {   // EPI_DSILU
+                        y = x * dsilu_f(epi.z_in[(size_t)row * epi.ld_z + col]);
+                    }
+                    if (col >= epi.n_valid) y = 0.0f;
+                    const __nv_bfloat16 yb = __float2bfloat16_rn(y);
+                    if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ld_bf16 + col] = yb;
+                    if (epi.out_bf16_t) epi.out_bf16_t[(size_t)col * epi.ld_bf16_t + row] = yb;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+}  // namespace st
