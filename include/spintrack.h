@@ -122,6 +122,29 @@ int st_particles_upload(st_ctx* ctx, const double* z_soa, const double* spin_soa
  * ST_ECUDA on a launch failure. */
 int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order);
 
+/* Track the orbits only (FP64 maps of st_track without the spin step; spins
+ * are left untouched) for n_turns >= 0 turns.  Used by the learned spin map,
+ * which supplies the spin rotation per turn.  Asynchronous.  Errors as
+ * st_track. */
+int st_track_orbit(st_ctx* ctx, int32_t n_turns);
+
+/* Track one turn (as st_track with n_turns = 1) and write every particle's
+ * one-turn spin rotation -- the element rotations of the turn composed and
+ * renormalised, a unit quaternion (scalar first) -- to q_out (device double
+ * [4][n]), with its sign chosen so that q . q_ref >= 0 (q_ref: host double[4]).
+ * These are the (orbit at s = 0, one-turn map) pairs of the learned spin map.
+ * Entries of particles already flagged lost are left unchanged; a particle
+ * lost during the turn gets the rotation up to the element that lost it.
+ * FP64 contexts only; spin_order as for st_track.  Asynchronous. */
+int st_track_one_turn_map(st_ctx* ctx, int32_t spin_order, const double* q_ref, double* q_out);
+
+/* Stroboscopic spin average: as st_track, and after every turn each
+ * particle's spin at the start of the lattice (the fixed azimuth s = 0) is
+ * added to spin_sum (device double [3][n], accumulated, not cleared), so that
+ * spin_sum / n_turns is the turn-averaged spin <S>.  FP64 contexts only.
+ * Asynchronous. */
+int st_track_average(st_ctx* ctx, int32_t n_turns, int32_t spin_order, double* spin_sum);
+
 /* Copy the tracked state out: spin_soa [3][n] (required), z_soa [6][n] and
  * lost [n] (each may be NULL), to host (dst_is_device = 0) or device memory.
  * Synchronises the context stream.  Returns ST_ETIMEOUT if a kernel reported
@@ -213,6 +236,58 @@ int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, const st_ref
  * kernels.  Errors: ST_EINVAL (shapes, alignment), ST_ECUDA. */
 int st_gemm_bf16(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K, const float* bias,
                  int32_t* status, void* cuda_stream);
+
+/* ---- learned one-turn spin map ------------------------------------------
+ * A multilayer perceptron 6 -> 256 -> 256 -> 256 -> 256 -> 4 with SiLU
+ * activations maps a particle's orbit z = (X, Px, Y, Py, T, Pt) at the fixed
+ * azimuth s = 0 to its one-turn spin rotation: q = normalise(q0 + L x + s y),
+ * x = z scaled per coordinate, y the network output, q0 the closed-orbit
+ * one-turn quaternion and L an optional linear term.  Weights and
+ * activations are bf16 on the tensor cores (st_gemm_bf16's kernel) with FP32
+ * accumulation; master weights and Adam moments are FP32.  All x / q arrays
+ * below are device memory, row-major float [B][6] / [B][4].  The parameter
+ * vector (host, float[st_mlp_param_count()]) is W1[256][6], b1, W2[256][256],
+ * b2, W3, b3, W4, b4, W5[4][256], b5. */
+typedef struct st_mlp st_mlp;
+int64_t st_mlp_param_count(void);
+/* Buffers for batches of up to max_batch rows (padded to 128); parameters
+ * start at zero.  cuda_stream as st_ctx_create. */
+int st_mlp_create(int32_t max_batch, void* cuda_stream, st_mlp** out);
+int st_mlp_destroy(st_mlp* mlp);
+int st_mlp_set_params(st_mlp* mlp, const float* params);     /* host; resets Adam */
+int st_mlp_get_params(st_mlp* mlp, float* params);           /* host */
+/* Head: q0[4], lin[4][6] (NULL = zero), out_scale > 0, in_scale[6]. */
+int st_mlp_set_head(st_mlp* mlp, const double* q0, const double* lin, double out_scale, const double* in_scale);
+/* Training pairs in the network's layout: z_soa (device double [6][n], the
+ * orbits at s = 0 before the turn) and q_soa (device double [4][n], their
+ * one-turn quaternions from st_track_one_turn_map) to x_rows (device float
+ * [n][6]) and q_rows (device float [n][4]).  Asynchronous on cuda_stream. */
+int st_mlp_pack_pairs(const double* z_soa, const double* q_soa, int64_t n, float* x_rows, float* q_rows,
+                      void* cuda_stream);
+/* FP64 least-squares fit q - q0 ~ c + L x over n pairs (z_soa, q_soa as for
+ * st_mlp_pack_pairs; lost: device flags, may be NULL, flagged pairs are left
+ * out), with q0 and the input scales of the head last set; x = in_scale * z.
+ * The moments are summed on the device in FP64 and the normal equations
+ * (7x7, coordinates with in_scale 0 dropped) solved on the host by Cholesky.
+ * Writes L to lin_out (host double [4][6]; pass it to st_mlp_set_head).
+ * Synchronises the network's stream.  Errors: ST_EINVAL (singular fit). */
+int st_mlp_fit_linear(st_mlp* mlp, const double* z_soa, const double* q_soa, const uint8_t* lost, int64_t n,
+                      double* lin_out);
+/* Inference: q[B][4] unit quaternions for x[B][6].  Asynchronous. */
+int st_mlp_forward(st_mlp* mlp, const float* x, int32_t B, float* q_out);
+/* Loss L = mean_b |q_b - q_target_b|^2 and its gradient with respect to all
+ * parameters (kept on the device for st_mlp_adam_step).  If loss / grads
+ * (host, may be NULL) are given they are filled and the call synchronises. */
+int st_mlp_loss_grad(st_mlp* mlp, const float* x, const float* q_target, int32_t B, float* loss, float* grads);
+/* One Adam update with the last gradients; refreshes the bf16 weights. */
+int st_mlp_adam_step(st_mlp* mlp, float lr, float beta1, float beta2, float eps);
+/* Stroboscopic spin tracking with the learned map: per turn, the network
+ * gives each particle's one-turn rotation from its orbit at s = 0, the spin
+ * is rotated by it (FP64), and the orbit is tracked exactly for one turn
+ * (st_track_orbit).  spin_sum (device double [3][n], may be NULL) accumulates
+ * S after every turn.  Needs an FP64 context with n <= max_batch.
+ * Asynchronous on the context stream. */
+int st_track_surrogate(st_ctx* ctx, st_mlp* mlp, int32_t n_turns, double* spin_sum);
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char* st_last_error(void);

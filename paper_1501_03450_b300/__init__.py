@@ -54,6 +54,11 @@ SIGNATURES = {
     "st_particles_upload": ([_VP, _VP, _VP, ctypes.c_int32], ctypes.c_int),
     "st_track": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "st_spins_download": ([_VP, _VP, _VP, _VP, ctypes.c_int32], ctypes.c_int),
+    "st_track_orbit": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "st_track_one_turn_map": ([_VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
+    "st_track_average": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP], ctypes.c_int),
+    "st_mlp_pack_pairs": ([_VP, _VP, ctypes.c_int64, _VP, _VP, _VP], ctypes.c_int),
+    "st_mlp_fit_linear": ([_VP, _VP, _VP, _VP, ctypes.c_int64, _VP], ctypes.c_int),
     "st_ctx_set_launch": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "st_measure_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "st_track_fp64_noalloc": ([ctypes.POINTER(StElement), ctypes.c_int32, ctypes.POINTER(StReference), _VP, _VP,
@@ -69,6 +74,16 @@ SIGNATURES = {
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "st_gemm_bf16": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
+    "st_mlp_param_count": ([], ctypes.c_int64),
+    "st_mlp_create": ([ctypes.c_int32, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "st_mlp_destroy": ([_VP], ctypes.c_int),
+    "st_mlp_set_params": ([_VP, _VP], ctypes.c_int),
+    "st_mlp_get_params": ([_VP, _VP], ctypes.c_int),
+    "st_mlp_set_head": ([_VP, _VP, _VP, ctypes.c_double, _VP], ctypes.c_int),
+    "st_mlp_forward": ([_VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
+    "st_mlp_loss_grad": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), _VP], ctypes.c_int),
+    "st_mlp_adam_step": ([_VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], ctypes.c_int),
+    "st_track_surrogate": ([_VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
     "st_last_error": ([], ctypes.c_char_p),
     "st_version": ([], ctypes.c_char_p),
 }
@@ -144,6 +159,19 @@ def st_particles_upload(ctx: int, z_ptr: int, s_ptr: int, src_is_device: int) ->
 
 def st_track(ctx: int, n_turns: int, spin_order: int) -> None:
     _check(load().st_track(ctx, int(n_turns), int(spin_order)))
+
+
+def st_track_orbit(ctx: int, n_turns: int) -> None:
+    _check(load().st_track_orbit(ctx, int(n_turns)))
+
+
+def st_track_one_turn_map(ctx: int, spin_order: int, q_ref, q_out_ptr: int) -> None:
+    qr = np.ascontiguousarray(q_ref, dtype=np.float64)
+    _check(load().st_track_one_turn_map(ctx, int(spin_order), qr.ctypes.data, q_out_ptr))
+
+
+def st_track_average(ctx: int, n_turns: int, spin_order: int, spin_sum_ptr: int) -> None:
+    _check(load().st_track_average(ctx, int(n_turns), int(spin_order), spin_sum_ptr))
 
 
 def st_spins_download(ctx: int, s_ptr: int, z_ptr: Optional[int], lost_ptr: Optional[int],
@@ -262,6 +290,77 @@ def st_gemm_bf16(A_ptr: int, B_ptr: int, D_ptr: int, M: int, N: int, K: int, bia
     _check(load().st_gemm_bf16(A_ptr, B_ptr, D_ptr, int(M), int(N), int(K), bias_ptr, status_ptr, stream))
 
 
+class MLP:
+    """The learned one-turn spin map (device-resident parameters)."""
+
+    def __init__(self, max_batch: int, stream: Optional[int] = None):
+        out = _VP()
+        _check(load().st_mlp_create(int(max_batch), stream, ctypes.byref(out)))
+        self.handle = out.value
+        self.n_params = int(load().st_mlp_param_count())
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.shape == (self.n_params,)
+        _check(load().st_mlp_set_params(self.handle, p.ctypes.data))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.n_params, np.float32)
+        _check(load().st_mlp_get_params(self.handle, p.ctypes.data))
+        return p
+
+    def set_head(self, q0, lin, out_scale: float, in_scale):
+        q0 = np.ascontiguousarray(q0, dtype=np.float64)
+        ins = np.ascontiguousarray(in_scale, dtype=np.float64)
+        lp = None
+        if lin is not None:
+            lin = np.ascontiguousarray(lin, dtype=np.float64).reshape(4, 6)
+            lp = lin.ctypes.data
+        self._head_keep = (q0, ins, lin)
+        _check(load().st_mlp_set_head(self.handle, q0.ctypes.data, lp, float(out_scale), ins.ctypes.data))
+
+    def forward(self, x_ptr: int, B: int, q_ptr: int):
+        _check(load().st_mlp_forward(self.handle, x_ptr, int(B), q_ptr))
+
+    def fit_linear(self, z_ptr: int, q_ptr: int, n: int, lost_ptr: Optional[int] = None) -> np.ndarray:
+        lin = np.empty((4, 6), np.float64)
+        _check(load().st_mlp_fit_linear(self.handle, z_ptr, q_ptr, lost_ptr, int(n), lin.ctypes.data))
+        return lin
+
+    def loss_grad(self, x_ptr: int, qt_ptr: int, B: int, want_grads: bool = False):
+        loss = ctypes.c_float()
+        g = np.empty(self.n_params, np.float32) if want_grads else None
+        _check(load().st_mlp_loss_grad(self.handle, x_ptr, qt_ptr, int(B), ctypes.byref(loss),
+                                       g.ctypes.data if g is not None else None))
+        return loss.value, g
+
+    def loss_grad_async(self, x_ptr: int, qt_ptr: int, B: int):
+        _check(load().st_mlp_loss_grad(self.handle, x_ptr, qt_ptr, int(B), None, None))
+
+    def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        _check(load().st_mlp_adam_step(self.handle, float(lr), float(beta1), float(beta2), float(eps)))
+
+    def close(self):
+        if self.handle:
+            _check(load().st_mlp_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def st_mlp_pack_pairs(z_ptr: int, q_ptr: int, n: int, x_rows_ptr: int, q_rows_ptr: int,
+                      stream: Optional[int] = None) -> None:
+    _check(load().st_mlp_pack_pairs(z_ptr, q_ptr, int(n), x_rows_ptr, q_rows_ptr, stream))
+
+
+def st_track_surrogate(ctx: int, mlp: int, n_turns: int, spin_sum_ptr: Optional[int] = None) -> None:
+    _check(load().st_track_surrogate(ctx, mlp, int(n_turns), spin_sum_ptr))
+
+
 def pairs_from_soa(z: np.ndarray, S: np.ndarray) -> np.ndarray:
     """[6][n] orbit + [3][n] spin -> the tracker's native 9n-double layout
     (X,Px)(Y,Py)(T,Pt)(Sx,Sy) pairs, then Sz."""
@@ -328,6 +427,9 @@ class Tracker:
 
     def track(self, n_turns: int, spin_order: int):
         st_track(self.handle, n_turns, spin_order)
+
+    def track_orbit(self, n_turns: int):
+        st_track_orbit(self.handle, n_turns)
 
     def download(self):
         z = np.empty((6, self.n), np.float64)

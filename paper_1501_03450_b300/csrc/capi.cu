@@ -364,6 +364,58 @@ int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order) {
     return launch_track_mixed(ctx, n_turns, spin_order);
 }
 
+int st_track_orbit(st_ctx* ctx, int32_t n_turns) {
+    if (!ctx) {
+        set_error("st_track_orbit: null context");
+        return ST_EINVAL;
+    }
+    if (!ctx->uploaded) {
+        set_error("st_track_orbit: no particles uploaded");
+        return ST_ESTATE;
+    }
+    if (n_turns < 0) {
+        set_error("st_track_orbit: need n_turns >= 0");
+        return ST_EINVAL;
+    }
+    if (n_turns == 0) return ST_OK;
+    return launch_track_orbit(ctx, n_turns);
+}
+
+int st_track_one_turn_map(st_ctx* ctx, int32_t spin_order, const double* q_ref, double* q_out) {
+    if (!ctx || !q_ref || !q_out) {
+        set_error("st_track_one_turn_map: null pointer");
+        return ST_EINVAL;
+    }
+    if (!ctx->uploaded) {
+        set_error("st_track_one_turn_map: no particles uploaded");
+        return ST_ESTATE;
+    }
+    if (ctx->precision != ST_FP64 || spin_order < 0 || spin_order > 4 ||
+        spin_order > ctx->lat->impl.min_spin_slices_pow2) {
+        set_error("st_track_one_turn_map: needs an FP64 context and a valid spin_order");
+        return ST_EINVAL;
+    }
+    return launch_track_turn_map(ctx, spin_order, q_out, q_ref);
+}
+
+int st_track_average(st_ctx* ctx, int32_t n_turns, int32_t spin_order, double* spin_sum) {
+    if (!ctx || !spin_sum) {
+        set_error("st_track_average: null pointer");
+        return ST_EINVAL;
+    }
+    if (!ctx->uploaded) {
+        set_error("st_track_average: no particles uploaded");
+        return ST_ESTATE;
+    }
+    if (ctx->precision != ST_FP64 || n_turns < 0 || spin_order < 0 || spin_order > 4 ||
+        spin_order > ctx->lat->impl.min_spin_slices_pow2) {
+        set_error("st_track_average: needs an FP64 context, n_turns >= 0 and a valid spin_order");
+        return ST_EINVAL;
+    }
+    if (n_turns == 0) return ST_OK;
+    return launch_track_average(ctx, n_turns, spin_order, spin_sum);
+}
+
 int st_spins_download(st_ctx* ctx, double* spin_soa, double* z_soa, uint8_t* lost, int32_t dst_is_device) {
     if (!ctx || !spin_soa) {
         set_error("st_spins_download: null pointer");

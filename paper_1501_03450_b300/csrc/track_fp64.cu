@@ -7,13 +7,14 @@
 
 namespace st {
 
-template <int K>
+template <int K, bool SPIN = true>
 __global__ void __launch_bounds__(128, 3) track_fp64_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
                                                          uint32_t seq_offset, int n_seq, RefConst ref,
                                                          double2* __restrict__ xpx, double2* __restrict__ ypy,
                                                          double2* __restrict__ tpt, double2* __restrict__ sxy,
                                                          double* __restrict__ szp, uint8_t* __restrict__ lost,
-                                                         int n, int n_turns, int32_t* __restrict__ status) {
+                                                         int n, int n_turns, int32_t* __restrict__ status,
+                                                         TurnOut tq) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
     __shared__ double qcache[QC_N * 128];
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(128, 3) track_fp64_kernel(const void* __restri
     const int64_t i = wi * 32 + lane;
     if (i >= n || lost[i]) continue;
 
-    fp64_track_particle<K>(table, seq, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns, qcache);
+    fp64_track_particle<K, SPIN>(table, seq, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns, qcache, tq);
     }  // particle loop
 }
 
@@ -82,14 +83,14 @@ int launch_unpack(st_ctx* ctx, double* z, double* s) {
     return e == cudaSuccess ? ST_OK : cuda_fail(e, "unpack kernel launch");
 }
 
-template <int K>
-static int launch_k(st_ctx* ctx, int n_turns) {
+template <int K, bool SPIN = true>
+static int launch_k(st_ctx* ctx, int n_turns, const TurnOut& tq) {
     const LatticeImpl& L = ctx->lat->impl;
     const int threads = ctx->block_threads;
     const size_t smem = L.blob_bytes;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(track_fp64_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(track_fp64_kernel<K, SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fp64 tracker)");
         attr_set = true;
@@ -98,7 +99,7 @@ static int launch_k(st_ctx* ctx, int n_turns) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_fp64_kernel<K>, threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_fp64_kernel<K, SPIN>, threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "fp64 tracker occupancy query");
     if (per_sm < 1) {
         set_error("fp64 tracker: block of %d threads with %zu B shared memory does not fit on an SM", threads,
@@ -112,16 +113,31 @@ static int launch_k(st_ctx* ctx, int n_turns) {
     const int tpl = ctx->turns_per_launch;
     for (int t = 0; t < n_turns; t += tpl) {
         int nt = n_turns - t < tpl ? n_turns - t : tpl;
-        track_fp64_kernel<K><<<(unsigned)grid, threads, smem, ctx->stream>>>(
+        track_fp64_kernel<K, SPIN><<<(unsigned)grid, threads, smem, ctx->stream>>>(
             L.d_blob, (uint32_t)L.blob_bytes, (uint32_t)L.seq_offset, L.n_elements, L.ref, ctx->xpx, ctx->ypy,
-            ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status);
+            ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status, tq);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "fp64 tracker launch");
     }
     return ST_OK;
 }
 
-int launch_track_fp64(st_ctx* ctx, int n_turns, int spin_order) {
+// Orbit only (spins untouched): the orbit maps of the FP64 tracker without the
+// precession, level products and spin rotation.
+int launch_track_orbit(st_ctx* ctx, int n_turns) {
+    if (ctx->lat->impl.blob_bytes > 200 * 1024) {
+        set_error("lattice table of %zu bytes exceeds the 200 KiB shared-memory budget",
+                  ctx->lat->impl.blob_bytes);
+        return ST_EINVAL;
+    }
+    if (ctx->block_threads > 128) {
+        set_error("orbit tracker: block_threads must be <= 128");
+        return ST_EINVAL;
+    }
+    return launch_k<0, false>(ctx, n_turns, TurnOut{nullptr, nullptr, 0, {}});
+}
+
+int launch_track_fp64(st_ctx* ctx, int n_turns, int spin_order, const TurnOut& out) {
     if (ctx->lat->impl.blob_bytes > 200 * 1024) {
         set_error("lattice table of %zu bytes exceeds the 200 KiB shared-memory budget",
                   ctx->lat->impl.blob_bytes);
@@ -132,14 +148,30 @@ int launch_track_fp64(st_ctx* ctx, int n_turns, int spin_order) {
         return ST_EINVAL;
     }
     switch (spin_order) {
-    case 0: return launch_k<0>(ctx, n_turns);
-    case 1: return launch_k<1>(ctx, n_turns);
-    case 2: return launch_k<2>(ctx, n_turns);
-    case 3: return launch_k<3>(ctx, n_turns);
-    case 4: return launch_k<4>(ctx, n_turns);
+    case 0: return launch_k<0>(ctx, n_turns, out);
+    case 1: return launch_k<1>(ctx, n_turns, out);
+    case 2: return launch_k<2>(ctx, n_turns, out);
+    case 3: return launch_k<3>(ctx, n_turns, out);
+    case 4: return launch_k<4>(ctx, n_turns, out);
     }
     set_error("spin_order out of range");
     return ST_EINVAL;
+}
+
+int launch_track_fp64(st_ctx* ctx, int n_turns, int spin_order) {
+    return launch_track_fp64(ctx, n_turns, spin_order, TurnOut{nullptr, nullptr, 0, {}});
+}
+
+// One turn, storing every particle's one-turn quaternion (sign-aligned with q_ref).
+int launch_track_turn_map(st_ctx* ctx, int spin_order, double* q_out, const double* q_ref) {
+    TurnOut out{q_out, nullptr, ctx->n, {q_ref[0], q_ref[1], q_ref[2], q_ref[3]}};
+    return launch_track_fp64(ctx, 1, spin_order, out);
+}
+
+// n_turns with the spin at the start of the lattice summed after every turn.
+int launch_track_average(st_ctx* ctx, int n_turns, int spin_order, double* spin_sum) {
+    TurnOut out{nullptr, spin_sum, ctx->n, {1.0, 0.0, 0.0, 0.0}};
+    return launch_track_fp64(ctx, n_turns, spin_order, out);
 }
 
 }  // namespace st

@@ -168,13 +168,24 @@ struct LevelProducts {
 // Track particle i for n_turns turns through the lattice in shared memory
 // (table, seq); state in the pair-SoA arrays; qcache is the block's
 // [QC_N][blockDim] shared-memory cache of matrix-kick coefficients.
-template <int K>
+// Optional per-turn outputs: each particle's composed one-turn quaternion of
+// the last tracked turn, sign-aligned with ref (q: [4][n] or nullptr), and a
+// running sum of the spin at the start of the lattice after every turn
+// (sum: [3][n] or nullptr).
+struct TurnOut {
+    double* q;
+    double* sum;
+    int64_t n;
+    double ref[4];
+};
+
+template <int K, bool SPIN = true>
 __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ table, const uint16_t* __restrict__ seq,
                                                     int n_seq, const RefConst& ref, double2* __restrict__ xpx,
                                                     double2* __restrict__ ypy, double2* __restrict__ tpt,
                                                     double2* __restrict__ sxy, double* __restrict__ szp,
                                                     uint8_t* __restrict__ lost, int64_t i, int n_turns,
-                                                    double* qcache) {
+                                                    double* qcache, const TurnOut& tq = TurnOut{nullptr, nullptr, 0, {}}) {
     Particle p;
     double2 v = xpx[i];
     p.X = v.x;
@@ -211,7 +222,7 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
             const DevElem& el = table[seq[e]];
             const int type = el.type;
             if (type == ST_SNAKE) {
-                qt = qmul(Quat{el.a[0], el.a[1], el.a[2], el.a[3]}, qt);
+                if constexpr (SPIN) qt = qmul(Quat{el.a[0], el.a[1], el.a[2], el.a[3]}, qt);
                 continue;
             }
             const Particle p0 = p;
@@ -242,8 +253,10 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 double ips = inv_sqrt_diff(Pa2, iPa, iPa2, p.Px * p.Px);
                 double Ps = ps2 * ips;
                 const double by = eta * h;
-                precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
-                lv.add_edge(0, N, ds, ox, oy, os);
+                if constexpr (SPIN) {
+                    precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
+                    lv.add_edge(0, N, ds, ox, oy, os);
+                }
                 const double dY = ieta * p.Py * ds;
                 const double dT = -ieta * pc.Pt * ds + (1.0 - ieta) * ds * ref.inv_beta0;
                 for (int s = 1; s <= N; ++s) {
@@ -271,8 +284,10 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     }
                     p.Y += dY + ieh * p.Py * dpsi;
                     p.T += dT - ieh * pc.b0pt * dpsi;
-                    precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
-                    lv.add_edge(s, N, ds, ox, oy, os);
+                    if constexpr (SPIN) {
+                        precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
+                        lv.add_edge(s, N, ds, ox, oy, os);
+                    }
                 }
             } else if (type == ST_MULT) {
                 const double k1 = el.a[0], k2 = el.a[1];
@@ -282,8 +297,10 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 double Ps = (pc.P2 - pp) * ips;
                 double bx = k1 * p.Y + k2 * p.X * p.Y;
                 double by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
-                precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
-                lv.add_edge(0, N, ds, ox, oy, os);
+                if constexpr (SPIN) {
+                    precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
+                    lv.add_edge(0, N, ds, ox, oy, os);
+                }
                 for (int s = 1; s <= N; ++s) {
                     p.X += half * p.Px * ips;
                     p.Y += half * p.Py * ips;
@@ -300,8 +317,10 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
                     bx = k1 * p.Y + k2 * p.X * p.Y;
                     by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
-                    precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
-                    lv.add_edge(s, N, ds, ox, oy, os);
+                    if constexpr (SPIN) {
+                        precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
+                        lv.add_edge(s, N, ds, ox, oy, os);
+                    }
                 }
             } else {   // ST_QUAD_MK
                 const double k1 = el.a[0], absk = el.a[1];
@@ -310,8 +329,10 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 double pp = p.Px * p.Px + p.Py * p.Py;
                 double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
                 double Ps = (pc.P2 - pp) * ips;
-                precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
-                lv.add_edge(0, N, ds, ox, oy, os);
+                if constexpr (SPIN) {
+                    precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
+                    lv.add_edge(0, N, ds, ox, oy, os);
+                }
                 for (int s = 1; s <= N; ++s) {
                     quad_linear(p, pc, qc, k1);
                     // nonlinear remainder H_qNL over ds, Eq. (25)
@@ -325,20 +346,38 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     pp = p.Px * p.Px + p.Py * p.Py;
                     ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
                     Ps = (pc.P2 - pp) * ips;
-                    precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
-                    lv.add_edge(s, N, ds, ox, oy, os);
+                    if constexpr (SPIN) {
+                        precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
+                        lv.add_edge(s, N, ds, ox, oy, os);
+                    }
                 }
             }
-            Quat qe = lv.romberg();
+            Quat qe{1.0, 0.0, 0.0, 0.0};
+            if constexpr (SPIN) qe = lv.romberg();
             if (!isfinite(p.X + p.Px + p.Y + p.Py + p.T + qe.w + qe.x + qe.y + qe.z)) {
                 p = p0;
                 is_lost = true;
                 break;
             }
-            qt = qmul(qe, qt);
+            if constexpr (SPIN) qt = qmul(qe, qt);
         }
-        qt = qnormalize(qt);
-        rotate_vec(qt, sx, sy, sz);
+        if constexpr (SPIN) {
+            qt = qnormalize(qt);
+            rotate_vec(qt, sx, sy, sz);
+            if (tq.q) {
+                const double sgn =
+                    (qt.w * tq.ref[0] + qt.x * tq.ref[1] + qt.y * tq.ref[2] + qt.z * tq.ref[3]) < 0.0 ? -1.0 : 1.0;
+                tq.q[i] = sgn * qt.w;
+                tq.q[tq.n + i] = sgn * qt.x;
+                tq.q[2 * tq.n + i] = sgn * qt.y;
+                tq.q[3 * tq.n + i] = sgn * qt.z;
+            }
+            if (tq.sum) {
+                tq.sum[i] += sx;
+                tq.sum[tq.n + i] += sy;
+                tq.sum[2 * tq.n + i] += sz;
+            }
+        }
     }
     xpx[i] = make_double2(p.X, p.Px);
     ypy[i] = make_double2(p.Y, p.Py);

@@ -1,0 +1,317 @@
+"""Learned one-turn spin map: training pairs from the FP64 tracker, training
+by the network's own tensor-core kernels, and stroboscopic spin tracking with
+the map while the orbit is tracked exactly.
+
+The map sends a particle's orbit z = (X, Px, Y, Py, T, Pt) at the start of the
+lattice (the fixed azimuth s = 0) to the unit quaternion of its spin rotation
+over one turn (the composed element rotations of Sec. 4, Eqs. (37)-(39)):
+
+    q(z) = normalise(q0 + L x + s y(x)),   x = in_scale * z,
+
+q0 the one-turn quaternion of the on-axis particle, L a linear term fitted in
+FP64 on the tracked pairs, y the 6 -> 256 x 4 -> 4 SiLU network (bf16 weights
+and activations, FP32 accumulation) and s an output scale.  T enters with
+scale 0: no element of these rings depends on the arrival time (no RF), so the
+one-turn map does not depend on T.
+
+Every per-sample step runs in the CUDA library (pair tracking, layout, the
+linear fit's moments, forward, backward, Adam, the surrogate turn loop).  The
+host does the bookkeeping: the 4x4 linear optics of the sampling domain from
+a handful of tracked particles, the input generator, the batch schedule.
+PyTorch provides device memory and the stream.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, Optional
+
+import numpy as np
+import torch
+
+from . import (MLP, Lattice, Tracker, st_mlp_pack_pairs, st_track_average, st_track_one_turn_map,
+               st_track_surrogate)
+
+LAYERS = [(256, 6), (256, 256), (256, 256), (256, 256), (4, 256)]
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def init_params(seed: int, gain: float = 1.0, last_scale: float = 0.1) -> np.ndarray:
+    """Initial network weights, flattened W1, b1, ..., W5, b5: normal with std
+    gain * sqrt(2 / fan_in) (the output layer scaled by last_scale), biases 0."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l, (r, c) in enumerate(LAYERS):
+        std = gain * math.sqrt(2.0 / c) * (last_scale if l == len(LAYERS) - 1 else 1.0)
+        parts.append(rng.standard_normal(r * c) * std)
+        parts.append(np.zeros(r))
+    return np.concatenate(parts)
+
+
+def action_angle_points(n: int, seed: int, twiss_x: Dict, twiss_y: Dict, D: float, Dp: float,
+                        Jx_max: float, Jy_max: float, pt_max: float) -> np.ndarray:
+    """Orbits z [6, n] at s = 0 with betatron actions uniform in [0, J_max]
+    (uniform over the phase-space ellipse), uniform random phases, Pt uniform
+    in [-pt_max, pt_max], the dispersive offset (D, Dp) * Pt added, T = 0.
+    twiss_*: dict(beta, alpha); J = (gamma u^2 + 2 alpha u u' + beta u'^2) / 2."""
+    rng = np.random.default_rng(seed)
+    z = np.zeros((6, n))
+    pt = rng.uniform(-pt_max, pt_max, n)
+    for (i, tw, jm) in ((0, twiss_x, Jx_max), (2, twiss_y, Jy_max)):
+        J = jm * rng.uniform(0.0, 1.0, n)
+        ph = rng.uniform(0.0, 2.0 * math.pi, n)
+        z[i] = np.sqrt(2.0 * J * tw["beta"]) * np.cos(ph)
+        z[i + 1] = -np.sqrt(2.0 * J / tw["beta"]) * (np.sin(ph) + tw["alpha"] * np.cos(ph))
+    z[0] += D * pt
+    z[1] += Dp * pt
+    z[5] = pt
+    return z
+
+
+class SpinMapSurrogate:
+    """Learned one-turn spin map of one ring at one reference energy."""
+
+    def __init__(self, ring: Dict, spin_order: int = 2, max_batch: int = 65536, seed: int = 1501):
+        if not torch.cuda.is_available():
+            raise RuntimeError("SpinMapSurrogate needs a CUDA device")
+        self.ring = ring
+        self.spin_order = int(spin_order)
+        self.stream = torch.cuda.Stream()
+        self.sp = self.stream.cuda_stream
+        self.lattice = Lattice(ring)
+        self.max_batch = int(max_batch)
+        self.mlp = MLP(self.max_batch, self.sp)
+        self.seed = int(seed)
+        self.q0 = self.closed_orbit_quaternion()
+        self.optics = None
+        self.in_scale = None
+        self.lin = None
+        self.out_scale = 1.0
+        self.history = []
+
+    # ---------------------------------------------------------------- tracking
+    def _tracker(self, n: int) -> Tracker:
+        return Tracker(self.lattice, n, "fp64", self.sp)
+
+    def one_turn_maps(self, z: np.ndarray, q_ref) -> np.ndarray:
+        """One-turn quaternions [4, n] of the orbits z [6, n] (host)."""
+        n = z.shape[1]
+        tr = self._tracker(n)
+        try:
+            S = np.zeros((3, n))
+            S[1] = 1.0
+            tr.upload(z, S)
+            with torch.cuda.stream(self.stream):
+                q = torch.empty((4, n), dtype=torch.float64, device="cuda")
+            st_track_one_turn_map(tr.handle, self.spin_order, q_ref, _ptr(q))
+            self.stream.synchronize()
+            return q.cpu().numpy()
+        finally:
+            tr.close()
+
+    def closed_orbit_quaternion(self) -> np.ndarray:
+        """q0: the one-turn quaternion of the on-axis particle (scalar part >= 0)."""
+        return self.one_turn_maps(np.zeros((6, 1)), [1.0, 0.0, 0.0, 0.0])[:, 0].copy()
+
+    def linear_optics(self, eps=(1e-7, 1e-8, 1e-7, 1e-8, 0.0, 1e-7)) -> Dict:
+        """Twiss parameters and dispersion at s = 0 from the one-turn orbit map,
+        linearised by central differences of tracked orbits."""
+        cols = [j for j in range(6) if eps[j] > 0]
+        z = np.zeros((6, 2 * len(cols)))
+        for k, j in enumerate(cols):
+            z[j, 2 * k] = eps[j]
+            z[j, 2 * k + 1] = -eps[j]
+        tr = self._tracker(z.shape[1])
+        try:
+            tr.upload(z, np.tile([[0.0], [1.0], [0.0]], (1, z.shape[1])))
+            tr.track_orbit(1)
+            z1, _, lost = tr.download()
+        finally:
+            tr.close()
+        if lost.any():
+            raise RuntimeError("linear_optics: a probe particle was lost")
+        Mx = np.zeros((6, 6))
+        for k, j in enumerate(cols):
+            Mx[:, j] = (z1[:, 2 * k] - z1[:, 2 * k + 1]) / (2 * eps[j])
+        out = {}
+        for plane, (a, b) in (("x", (0, 1)), ("y", (2, 3))):
+            m = Mx[np.ix_([a, b], [a, b])]
+            c = 0.5 * (m[0, 0] + m[1, 1])
+            if not abs(c) < 1.0:
+                raise RuntimeError(f"linear_optics: plane {plane} is not stable (cos mu = {c})")
+            s = math.copysign(math.sqrt(1.0 - c * c), m[0, 1])
+            beta = m[0, 1] / s
+            alpha = (m[0, 0] - m[1, 1]) / (2 * s)
+            out[plane] = dict(beta=beta, alpha=alpha, gamma=(1 + alpha * alpha) / beta,
+                              tune=math.atan2(s, c) / (2 * math.pi) % 1.0)
+        # periodic dispersion per unit Pt: (I - M_xx) d = M_x,pt
+        m = Mx[np.ix_([0, 1], [0, 1])]
+        d = np.linalg.solve(np.eye(2) - m, Mx[[0, 1], 5])
+        out["D"], out["Dp"] = float(d[0]), float(d[1])
+        out["M"] = Mx
+        self.optics = out
+        return out
+
+    # ------------------------------------------------------------ training set
+    def action_bounds(self, sigmas: Dict, cut: float, margin: float):
+        """Largest betatron action per plane of a particle whose coordinates lie
+        within cut sigma (each coordinate, as the truncated Gaussian use
+        distribution), and the Pt bound; margin scales the amplitudes.
+        sigmas: x, px, y, py and pt_max (the largest |Pt| of the use ensemble)."""
+        o = self.optics or self.linear_optics()
+        pt_max = float(sigmas["pt_max"])
+        bounds = {}
+        for plane, (su, sp) in (("x", (sigmas["x"], sigmas["px"])), ("y", (sigmas["y"], sigmas["py"]))):
+            t = o[plane]
+
+            def J(u, p):
+                return 0.5 * (t["gamma"] * u * u + 2 * t["alpha"] * u * p + t["beta"] * p * p)
+
+            jb = max(J(cut * su * a, cut * sp * b) for a in (-1, 1) for b in (-1, 1))
+            amp = math.sqrt(jb)
+            if plane == "x":   # the dispersive offset D Pt adds to the betatron amplitude
+                amp += pt_max * math.sqrt(J(o["D"], o["Dp"]))
+            bounds[plane] = (margin * amp) ** 2
+        return bounds, margin * pt_max
+
+    def training_points(self, n: int, sigmas: Dict, cut: float = 3.0, margin: float = 1.1, seed: int = None):
+        """Orbits at s = 0 uniform in betatron action up to the bounds of
+        action_bounds, with uniform random phases and uniform Pt."""
+        bounds, pt_max = self.action_bounds(sigmas, cut, margin)
+        o = self.optics
+        return action_angle_points(n, self.seed if seed is None else seed, o["x"], o["y"], o["D"], o["Dp"],
+                                   bounds["x"], bounds["y"], pt_max)
+
+    def make_pairs(self, n: int, sigmas: Dict, cut: float = 3.0, margin: float = 1.1, seed: int = None):
+        """Tracks the training orbits one turn (FP64, spin order of the
+        surrogate) and keeps (z, q) on the device: z64 [6, n], q64 [4, n] and
+        the network's rows x [n, 6], q [n, 4] (float)."""
+        z = self.training_points(n, sigmas, cut, margin, seed)
+        tr = self._tracker(n)
+        try:
+            with torch.cuda.stream(self.stream):
+                z64 = torch.from_numpy(z).to("cuda", non_blocking=False)
+                q64 = torch.empty((4, n), dtype=torch.float64, device="cuda")
+                lost = torch.zeros(n, dtype=torch.uint8, device="cuda")
+                x_rows = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+                q_rows = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+                s_dummy = torch.empty((3, n), dtype=torch.float64, device="cuda")
+            S = np.zeros((3, n))
+            S[1] = 1.0
+            tr.upload(z, S)
+            st_track_one_turn_map(tr.handle, self.spin_order, self.q0, _ptr(q64))
+            tr.download_device(_ptr(s_dummy), None, _ptr(lost))
+            st_mlp_pack_pairs(_ptr(z64), _ptr(q64), n, _ptr(x_rows), _ptr(q_rows), self.sp)
+            self.stream.synchronize()
+        finally:
+            tr.close()
+        n_lost = int(lost.sum().item())
+        if n_lost:
+            raise RuntimeError(f"make_pairs: {n_lost} training orbits were lost in one turn")
+        self.pairs = dict(z64=z64, q64=q64, x=x_rows, q=q_rows, n=n, lost=lost)
+        return self.pairs
+
+    def fit_head(self, in_scale=None):
+        """Input scales (1 / RMS of each coordinate over the pairs, 0 for T),
+        the FP64 linear term L, and the output scale s (RMS of the residual
+        q - q0 - L x over a sample)."""
+        P = self.pairs
+        z = P["z64"]
+        if in_scale is None:
+            rms = torch.sqrt(torch.mean(z * z, dim=1)).cpu().numpy()
+            in_scale = np.where(rms > 0, 1.0 / np.where(rms > 0, rms, 1.0), 0.0)
+            in_scale[4] = 0.0
+        self.in_scale = np.asarray(in_scale, dtype=np.float64)
+        self.mlp.set_head(self.q0, None, 1.0, self.in_scale)
+        self.lin = self.mlp.fit_linear(_ptr(z), _ptr(P["q64"]), P["n"], _ptr(P["lost"]))
+        m = min(P["n"], 16384)
+        zs = z[:, :m].cpu().numpy() * self.in_scale[:, None]
+        r = P["q64"][:, :m].cpu().numpy() - self.q0[:, None] - self.lin @ zs
+        self.out_scale = float(np.sqrt(np.mean(r * r)) * 2.0) or 1.0
+        self.mlp.set_head(self.q0, self.lin, self.out_scale, self.in_scale)
+        return self.in_scale, self.lin, self.out_scale
+
+    def train(self, steps: int, batch: int = 16384, lr: float = 1e-3, lr_final: float = 1e-5,
+              log_every: int = 200, init_seed: int = None, warmup: int = 100):
+        """Adam on mean |q - q_t|^2 over contiguous batches of the (randomly
+        ordered) pairs; the learning rate decays as a cosine from lr to lr_final."""
+        P = self.pairs
+        n = P["n"]
+        batch = min(int(batch), self.max_batch, n)
+        self.mlp.set_params(init_params(self.seed if init_seed is None else init_seed))
+        rng = np.random.default_rng(self.seed + 1)
+        start = int(rng.integers(0, batch))
+        xb, qb = P["x"], P["q"]
+        for k in range(steps):
+            if start + batch > n:
+                start = int(rng.integers(0, batch))
+            xp = _ptr(xb) + start * 6 * 4
+            qp = _ptr(qb) + start * 4 * 4
+            start += batch
+            if log_every and (k % log_every == 0 or k == steps - 1):
+                loss, _ = self.mlp.loss_grad(xp, qp, batch)
+                self.history.append((k, loss))
+            else:
+                self.mlp.loss_grad_async(xp, qp, batch)
+            f = min(1.0, (k + 1) / warmup) if warmup else 1.0
+            c = 0.5 * (1 + math.cos(math.pi * k / max(1, steps - 1)))
+            self.mlp.adam_step(f * (lr_final + (lr - lr_final) * c))
+        self.stream.synchronize()
+        return self.history
+
+    def eval_loss(self, x: torch.Tensor, q: torch.Tensor) -> float:
+        """Mean |q - q_t|^2 of the current network over the given rows."""
+        n = x.shape[0]
+        tot, k = 0.0, 0
+        while k < n:
+            b = min(self.max_batch, n - k)
+            loss, _ = self.mlp.loss_grad(_ptr(x) + k * 24, _ptr(q) + k * 16, b)
+            tot += loss * b
+            k += b
+        return tot / n
+
+    # ------------------------------------------------------------------- use
+    def track(self, z: np.ndarray, S: np.ndarray, n_turns: int, average: bool = True, timed: bool = False):
+        """Stroboscopic tracking with the learned map: returns (z, S, lost,
+        <S> or None, ms)."""
+        return _run(self, z, S, n_turns, average, timed, surrogate=True)
+
+    def track_plain(self, z: np.ndarray, S: np.ndarray, n_turns: int, average: bool = True,
+                    timed: bool = False):
+        """The same with plain FP64 spin tracking (the judge of the map)."""
+        return _run(self, z, S, n_turns, average, timed, surrogate=False)
+
+    def close(self):
+        self.mlp.close()
+        self.lattice.close()
+
+
+def _run(sg: SpinMapSurrogate, z, S, n_turns, average, timed, surrogate):
+    n = z.shape[1]
+    if surrogate and n > sg.max_batch:
+        raise ValueError("more particles than the network's max_batch")
+    tr = sg._tracker(n)
+    try:
+        with torch.cuda.stream(sg.stream):
+            ssum = torch.zeros((3, n), dtype=torch.float64, device="cuda") if average else None
+        tr.upload(z, S)
+        sg.stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sg.stream)
+        if surrogate:
+            st_track_surrogate(tr.handle, sg.mlp.handle, n_turns, _ptr(ssum) if average else None)
+        elif average:
+            st_track_average(tr.handle, n_turns, sg.spin_order, _ptr(ssum))
+        else:
+            tr.track(n_turns, sg.spin_order)
+        e1.record(sg.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        z1, S1, lost = tr.download()
+        avg = (ssum.cpu().numpy() / max(1, n_turns)) if average else None
+        return z1, S1, lost, avg, ms
+    finally:
+        tr.close()

@@ -1,0 +1,317 @@
+"""GPU tests of the learned one-turn spin map through the C ABI: the network's
+forward pass, loss gradient and Adam step against the FP64 NumPy reference
+(oracle/mlp.py) with bf16 storage emulated, the tracker's one-turn quaternions
+and stroboscopic sums against the CPU oracle, the FP64 linear head fit against
+least squares, and the surrogate turn loop against closed forms."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1501_03450_b300 as st
+import workloads as W
+from oracle import mlp as M
+from test_oracle_mlp import random_params
+
+pytestmark = pytest.mark.gpu
+
+IN_SCALE = np.array([1e3, 1e4, 1e3, 1e4, 0.0, 1e3])
+
+
+def dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(dtype)).cuda()
+
+
+def rand_x(B, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((B, 6)) * np.array([1e-3, 1e-4, 1e-3, 1e-4, 1e-2, 1e-3])
+
+
+def unit(v):
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def make_net(p, head, max_batch=4096):
+    net = st.MLP(max_batch, torch.cuda.current_stream().cuda_stream)
+    net.set_params(p.astype(np.float32))
+    net.set_head(head["q0"], head["lin"], head["scale"], head["in_scale"])
+    return net
+
+
+def f32_params(p):
+    return p.astype(np.float32).astype(np.float64)
+
+
+def head_for(seed, scale=0.05, lin=True):
+    rng = np.random.default_rng(seed)
+    return dict(q0=unit(rng.standard_normal(4)), lin=(0.01 * rng.standard_normal((4, 6)) if lin else None),
+                scale=scale, in_scale=IN_SCALE)
+
+
+def f32_head(h):
+    """The head as the kernels hold it (float)."""
+    return dict(q0=h["q0"].astype(np.float32).astype(np.float64),
+                lin=None if h["lin"] is None else h["lin"].astype(np.float32).astype(np.float64),
+                scale=float(np.float32(h["scale"])), in_scale=h["in_scale"].astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("B", [1, 128, 300, 2048])
+def test_forward_matches_reference(B):
+    """Inference against the reference with the weights, scaled inputs and
+    activations rounded to bf16.  The kernels accumulate in FP32 and round
+    FP32 sums to bf16, the reference FP64 sums: a rounding decision differs
+    only when the two sums straddle a bf16 rounding boundary, which moves one
+    activation by one bf16 step (2^-8 relative); over the 256-wide layers that
+    bounds |dy| well below 1e-3 |y| and |dq| below 1e-3 s.  Without the bf16
+    emulation the difference is an order of magnitude larger."""
+    p = random_params(21, last_scale=1.0)
+    h = head_for(3)
+    x = rand_x(B, 4)
+    net = make_net(p, h)
+    xd = dev(x, np.float32)
+    q = torch.empty((B, 4), dtype=torch.float32, device="cuda")
+    net.forward(xd.data_ptr(), B, q.data_ptr())
+    qg = q.cpu().numpy().astype(np.float64)
+    x32 = x.astype(np.float32).astype(np.float64)
+    qo, _ = M.forward(f32_params(p), x32, f32_head(h), bf16=True)
+    qf, _ = M.forward(p, x, h, bf16=False)
+    err = np.abs(qg - qo).max()
+    assert err < 1e-3 * h["scale"], err
+    assert np.abs(np.linalg.norm(qg, axis=1) - 1).max() < 1e-6
+    if B >= 128:
+        assert err < 0.2 * np.abs(qg - qf).max()
+    net.close()
+
+
+def test_loss_and_gradient_match_reference():
+    """Loss and all 200196 gradient entries against the reference (bf16
+    storage emulated, FP64 arithmetic).  The kernels also round the
+    back-propagated dL/dy and dL/dz to bf16 (relative 2^-9 each), so every
+    parameter block agrees to a relative L2 error of a few 1e-3."""
+    B = 1000
+    p = random_params(7, last_scale=1.0)
+    h = head_for(5)
+    x = rand_x(B, 8)
+    qo, _ = M.forward(f32_params(p), x, f32_head(h), bf16=True)
+    rng = np.random.default_rng(9)
+    qt = unit(qo + 0.02 * rng.standard_normal(qo.shape))
+    net = make_net(p, h)
+    loss, g = net.loss_grad(dev(x, np.float32).data_ptr(), dev(qt, np.float32).data_ptr(), B, want_grads=True)
+    x32 = x.astype(np.float32).astype(np.float64)
+    qt32 = qt.astype(np.float32).astype(np.float64)
+    lo, go = M.loss_grad(f32_params(p), x32, qt32, f32_head(h), bf16=True)
+    assert loss == pytest.approx(lo, rel=2e-3)
+    offs = np.cumsum([0] + [r * c + r for r, c in M.LAYERS])
+    for l, (r, c) in enumerate(M.LAYERS):
+        for a, b in ((offs[l], offs[l] + r * c), (offs[l] + r * c, offs[l + 1])):
+            gg, gr = g[a:b].astype(np.float64), go[a:b]
+            rel = np.linalg.norm(gg - gr) / np.linalg.norm(gr)
+            assert rel < 2e-2, (l, a, rel)
+            assert np.dot(gg, gr) / (np.linalg.norm(gg) * np.linalg.norm(gr)) > 0.9995
+    net.close()
+
+
+def test_adam_steps_match_reference():
+    """Two Adam steps on the kernels' own gradients against Adam in FP64."""
+    B = 512
+    p = random_params(17, last_scale=1.0).astype(np.float32)
+    h = head_for(2)
+    x = dev(rand_x(B, 1), np.float32)
+    qt = dev(unit(np.random.default_rng(3).standard_normal((B, 4))), np.float32)
+    net = make_net(p.astype(np.float64), h)
+    pe = p.astype(np.float64)
+    m = np.zeros_like(pe)
+    v = np.zeros_like(pe)
+    for t in (1, 2):
+        _, g = net.loss_grad(x.data_ptr(), qt.data_ptr(), B, want_grads=True)
+        net.adam_step(1e-3, 0.9, 0.999, 1e-8)
+        pe, m, v = M.adam_step(pe, m, v, g.astype(np.float64), t, 1e-3, 0.9, 0.999, 1e-8)
+        pg = net.get_params().astype(np.float64)
+        np.testing.assert_allclose(pg, pe, rtol=0, atol=2e-7 * np.abs(pe).max() + 1e-9)
+        pe = pg
+    net.close()
+
+
+def test_training_reduces_loss_on_a_smooth_map():
+    """Adam on a smooth synthetic map (q0 + 0.01 sin(A x)) lowers the loss
+    by more than an order of magnitude in 400 steps."""
+    B = 4096
+    rng = np.random.default_rng(31)
+    x = rand_x(B, 30)
+    A = rng.standard_normal((4, 6)) * IN_SCALE
+    q0 = unit(np.array([0.1, 0.2, 0.9, 0.1]))
+    qt = unit(q0 + 0.01 * np.sin(x @ A.T))
+    net = st.MLP(B, torch.cuda.current_stream().cuda_stream)
+    from paper_1501_03450_b300.surrogate import init_params
+    net.set_params(init_params(1).astype(np.float32))
+    net.set_head(q0, None, 0.01, IN_SCALE)
+    xd, qd = dev(x, np.float32), dev(qt, np.float32)
+    l0, _ = net.loss_grad(xd.data_ptr(), qd.data_ptr(), B)
+    for k in range(400):
+        net.loss_grad_async(xd.data_ptr(), qd.data_ptr(), B)
+        net.adam_step(2e-3 if k < 300 else 5e-4)
+    l1, _ = net.loss_grad(xd.data_ptr(), qd.data_ptr(), B)
+    assert l1 < 0.05 * l0, (l0, l1)
+    net.close()
+
+
+def test_pack_pairs_layout():
+    n = 777
+    rng = np.random.default_rng(4)
+    z = rng.standard_normal((6, n))
+    q = rng.standard_normal((4, n))
+    x_rows = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+    q_rows = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    st.st_mlp_pack_pairs(dev(z, np.float64).data_ptr(), dev(q, np.float64).data_ptr(), n, x_rows.data_ptr(),
+                         q_rows.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(x_rows.cpu().numpy(), z.T.astype(np.float32))
+    np.testing.assert_array_equal(q_rows.cpu().numpy(), q.T.astype(np.float32))
+
+
+def test_fit_linear_is_least_squares():
+    """The FP64 head fit against numpy's least squares with an intercept;
+    coordinates with input scale 0 get a zero column; lost pairs are left out."""
+    n = 50000
+    rng = np.random.default_rng(12)
+    z = rng.standard_normal((6, n)) * np.array([1e-3, 1e-4, 1e-3, 1e-4, 1e-2, 1e-3])[:, None]
+    q0 = unit(rng.standard_normal(4))
+    Lt = rng.standard_normal((4, 6)) * 1e-2
+    xs = z * IN_SCALE[:, None]
+    q = q0[:, None] + Lt @ xs + 1e-3 + 1e-4 * np.sin(3 * xs[0] * xs[2])[None, :] + 1e-5 * rng.standard_normal((4, n))
+    lost = np.zeros(n, np.uint8)
+    lost[::7] = 1
+    q[:, ::7] = 1e3                                    # garbage in lost rows
+    net = st.MLP(128, torch.cuda.current_stream().cuda_stream)
+    net.set_head(q0, None, 1.0, IN_SCALE)
+    L = net.fit_linear(dev(z, np.float64).data_ptr(), dev(q, np.float64).data_ptr(), n,
+                       dev(lost, np.uint8).data_ptr())
+    keep = lost == 0
+    F = np.concatenate([np.ones((1, keep.sum())), xs[[0, 1, 2, 3, 5]][:, keep]]).T
+    sol, *_ = np.linalg.lstsq(F, (q[:, keep] - q0[:, None]).T, rcond=None)
+    ref = np.zeros((4, 6))
+    ref[:, [0, 1, 2, 3, 5]] = sol[1:].T
+    np.testing.assert_allclose(L, ref, rtol=0, atol=1e-10)
+    assert np.all(L[:, 4] == 0.0)
+    net.close()
+
+
+def _oracle_turn_quats(ring, z, K):
+    n = z.shape[1]
+    ex = np.zeros((3, n)); ex[0] = 1.0
+    ey = np.zeros((3, n)); ey[1] = 1.0
+    _, Sx, _ = oracle.track(ring, z, ex, 1, K)
+    _, Sy, _ = oracle.track(ring, z, ey, 1, K)
+    return M.quat_from_images(Sx, Sy)
+
+
+@pytest.mark.parametrize("gg", [45.5, 487.0])
+def test_one_turn_quaternions_match_oracle(gg):
+    """The tracker's composed one-turn quaternions against the rotation the
+    oracle's tracked spins define (images of x^ and y^), up to the sign fixed
+    by the reference hemisphere; spins and orbits equal those of st_track."""
+    ring = W.with_spin_order(W.rhic_like_ring(gg, n_cells=12), 2)
+    z, S = W.gaussian_particles(261, gg, seed=40)
+    qo = _oracle_turn_quats(ring, z, 2)
+    q_ref = np.array([0.3, -0.2, 0.9, 0.1])
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, z.shape[1])
+    tr.upload(z, S)
+    q = torch.full((4, z.shape[1]), 7.0, dtype=torch.float64, device="cuda")
+    st.st_track_one_turn_map(tr.handle, 2, q_ref, q.data_ptr())
+    zg, Sg, lg = tr.download()
+    qg = q.cpu().numpy().T
+    assert np.all(qg @ q_ref >= 0.0)
+    sgn = np.sign(np.sum(qg * qo, axis=1))[:, None]
+    assert np.abs(qg - sgn * qo).max() < 1e-12
+    z1, S1, _ = st.track(ring, z, S, 1, 2)
+    np.testing.assert_array_equal(zg, z1)
+    np.testing.assert_array_equal(Sg, S1)
+    tr.close()
+    lat.close()
+
+
+def test_one_turn_quaternions_skip_lost_particles():
+    ring = W.with_spin_order(W.toy_ring(45.5), 2)
+    z, S = W.gaussian_particles(40, 45.5, seed=2)
+    z[1, 5] = 1.5                                      # lost in the first element
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, 40)
+    tr.upload(z, S)
+    q = torch.full((4, 40), 7.0, dtype=torch.float64, device="cuda")
+    st.st_track_one_turn_map(tr.handle, 2, [1.0, 0, 0, 0], q.data_ptr())
+    _, _, lost = tr.download()
+    assert lost[5] == 1 and lost.sum() == 1
+    q2 = torch.full((4, 40), 7.0, dtype=torch.float64, device="cuda")
+    st.st_track_one_turn_map(tr.handle, 2, [1.0, 0, 0, 0], q2.data_ptr())
+    torch.cuda.synchronize()
+    assert np.all(q2.cpu().numpy()[:, 5] == 7.0)       # already lost: untouched
+    tr.close()
+    lat.close()
+
+
+def test_stroboscopic_sum_matches_oracle():
+    """st_track_average: the spin at s = 0 summed after every turn, against
+    the oracle tracked turn by turn."""
+    ring = W.with_spin_order(W.toy_ring(45.5), 2)
+    z, S = W.gaussian_particles(100, 45.5, seed=6)
+    S = W.cap_spins(100, 0.3, seed=6)
+    turns = 12
+    zo, So = z.copy(), S.copy()
+    acc = np.zeros_like(S)
+    for _ in range(turns):
+        zo, So, _ = oracle.track(ring, zo, So, 1, 2)
+        acc += So
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, 100)
+    tr.set_launch(0, 5)                                # several turns per launch
+    tr.upload(z, S)
+    ssum = torch.zeros((3, 100), dtype=torch.float64, device="cuda")
+    st.st_track_average(tr.handle, turns, 2, ssum.data_ptr())
+    zg, Sg, _ = tr.download()
+    assert np.abs(ssum.cpu().numpy() - acc).max() < 1e-11 * turns
+    assert np.abs(Sg - So).max() < 1e-11 and np.abs(zg - zo).max() < 1e-11
+    tr.close()
+    lat.close()
+
+
+def test_surrogate_with_zero_network_is_the_closed_form():
+    """With zero weights and no linear term the learned map is the constant
+    rotation q0: S_t = R(q0)^t S_0 for every particle, the orbit is the
+    orbit-only tracker's, and the stroboscopic sum is the sum of the S_t."""
+    ring = W.with_spin_order(W.toy_ring(45.5), 2)
+    n, turns = 300, 25
+    z, S = W.gaussian_particles(n, 45.5, seed=8)
+    S = W.cap_spins(n, 0.4, seed=8)
+    th = 0.7
+    axis = unit(np.array([0.2, 1.0, -0.3]))
+    q0 = np.array([math.cos(th / 2), *(axis * math.sin(th / 2))])
+    net = st.MLP(512, None)
+    net.set_params(np.zeros(net.n_params, np.float32))
+    net.set_head(q0, None, 1.0, IN_SCALE)
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, n)
+    tr.upload(z, S)
+    ssum = torch.zeros((3, n), dtype=torch.float64, device="cuda")
+    st.st_track_surrogate(tr.handle, net.handle, turns, ssum.data_ptr())
+    zg, Sg, lg = tr.download()
+    qf = unit(q0.astype(np.float32).astype(np.float64))
+    Se = S.copy()
+    acc = np.zeros_like(S)
+    for _ in range(turns):
+        Se = M.rotate(np.tile(qf, (n, 1)), Se)
+        acc += Se
+    assert np.abs(Sg - Se).max() < 1e-12 * turns
+    assert np.abs(ssum.cpu().numpy() - acc).max() < 1e-12 * turns * turns
+    tr2 = st.Tracker(lat, n)
+    tr2.upload(z, S)
+    tr2.track_orbit(turns)
+    z2, S2, l2 = tr2.download()
+    np.testing.assert_array_equal(zg, z2)
+    np.testing.assert_array_equal(S2, S)               # orbit-only leaves spins alone
+    tr.close()
+    tr2.close()
+    lat.close()
+    net.close()

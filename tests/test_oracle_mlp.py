@@ -1,0 +1,155 @@
+"""Pins of the FP64 reference of the learned one-turn spin map (oracle/mlp.py)
+against facts that do not come from it: central finite differences of its own
+loss (gradient), library routines (torch's bfloat16 cast, scipy's logistic
+function), Rodrigues' rotation formula, closed forms of Adam's first step and
+of a network with zero weights."""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy.special import expit
+
+from oracle import mlp as M
+
+HEAD = dict(q0=np.array([0.05, 0.1, 0.99, -0.02]), lin=None, scale=0.3,
+            in_scale=np.array([1e3, 1e4, 1e3, 1e4, 0.0, 1e3]))
+
+
+def _inputs(B, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((B, 6)) * np.array([1e-3, 1e-4, 1e-3, 1e-4, 1e-2, 1e-3])
+    qt = rng.standard_normal((B, 4))
+    qt /= np.linalg.norm(qt, axis=1, keepdims=True)
+    return x, qt
+
+
+def random_params(seed, last_scale=1.0):
+    """Random network weights (He-normal), biases small random."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l, (r, c) in enumerate(M.LAYERS):
+        parts.append(rng.standard_normal(r * c) * np.sqrt(2.0 / c) * (last_scale if l == 4 else 1.0))
+        parts.append(0.01 * rng.standard_normal(r))
+    return np.concatenate(parts)
+
+
+def test_param_layout():
+    assert M.param_count() == 6 * 256 + 256 + 3 * (256 * 256 + 256) + 4 * 256 + 4 == 200196
+    p = np.arange(M.param_count(), dtype=np.float64)
+    layers = M.unpack(p)
+    assert layers[0][0].shape == (256, 6) and layers[0][0][0, 1] == 1.0
+    assert layers[0][1][0] == 1536.0
+    assert layers[4][0].shape == (4, 256) and layers[4][1][-1] == M.param_count() - 1
+
+
+def test_round_bf16_ties_and_library_cast():
+    u = 2.0 ** -7                                    # bf16 spacing at 1
+    assert M.round_bf16(np.array([1.0]))[0] == 1.0
+    assert M.round_bf16(np.array([1.0 + u / 2]))[0] == 1.0             # tie -> even
+    assert M.round_bf16(np.array([1.0 + 1.5 * u]))[0] == 1.0 + 2 * u   # tie -> even
+    assert M.round_bf16(np.array([1.0 + 0.51 * u]))[0] == 1.0 + u
+    assert M.round_bf16(np.array([-3.0 - 0.49 * 2 * u]))[0] == -3.0
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal(20000) * 10.0 ** rng.integers(-6, 6, 20000)
+    ref = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(M.round_bf16(a), ref)
+
+
+def test_silu_and_derivative():
+    z = np.linspace(-12, 12, 97)
+    np.testing.assert_allclose(M.silu(z), z * expit(z), rtol=1e-14, atol=1e-300)
+    h = 1e-6
+    fd = (M.silu(z + h) - M.silu(z - h)) / (2 * h)
+    np.testing.assert_allclose(M.dsilu(z), fd, rtol=1e-8, atol=1e-9)
+
+
+@pytest.mark.parametrize("with_lin", [False, True])
+def test_gradient_central_differences(with_lin):
+    rng = np.random.default_rng(11)
+    p = random_params(5)
+    head = dict(HEAD)
+    if with_lin:
+        head["lin"] = 0.01 * rng.standard_normal((4, 6))
+    x, qt = _inputs(7, 12)
+    loss, g = M.loss_grad(p, x, qt, head)
+    # indices in every parameter block (weights and biases of all 5 layers)
+    offs = np.cumsum([0] + [r * c + r for r, c in M.LAYERS])
+    idx = []
+    for l, (r, c) in enumerate(M.LAYERS):
+        idx += list(offs[l] + rng.integers(0, r * c, 8))
+        idx += list(offs[l] + r * c + rng.integers(0, r, 4))
+    # fourth-order central differences: truncation O(h^4), rounding ~ eps L / h
+    h = 1e-4
+
+    def f(i, d):
+        pd = p.copy()
+        pd[i] += d
+        return M.loss_grad(pd, x, qt, head)[0]
+
+    for i in idx:
+        fd = (8 * (f(i, h) - f(i, -h)) - (f(i, 2 * h) - f(i, -2 * h))) / (12 * h)
+        assert abs(g[i] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max()), (i, g[i], fd)
+    # the loss the gradient belongs to is the one defined: mean |q - qt|^2
+    q, _ = M.forward(p, x, head)
+    assert loss == pytest.approx(np.mean(np.sum((q - qt) ** 2, axis=1)), rel=1e-14)
+    np.testing.assert_allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-15)
+
+
+def test_zero_network_is_the_head():
+    p = np.zeros(M.param_count())
+    x, qt = _inputs(9, 4)
+    lin = np.random.default_rng(2).standard_normal((4, 6)) * 1e-2
+    head = dict(HEAD, lin=lin)
+    q, _ = M.forward(p, x, head)
+    xs = x * HEAD["in_scale"]
+    u = HEAD["q0"] + xs @ lin.T
+    np.testing.assert_allclose(q, u / np.linalg.norm(u, axis=1, keepdims=True), atol=1e-15)
+    # with zero weights only the output bias has a gradient
+    _, g = M.loss_grad(p, x, qt, head)
+    assert np.all(g[:-4] == 0.0) and np.any(g[-4:] != 0.0)
+
+
+def test_rotate_matches_rodrigues():
+    rng = np.random.default_rng(8)
+    for _ in range(20):
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        th = rng.uniform(-math.pi, math.pi)
+        v = rng.standard_normal(3)
+        q = np.array([[math.cos(th / 2), *(n * math.sin(th / 2))]])
+        rod = v * math.cos(th) + np.cross(n, v) * math.sin(th) + n * np.dot(n, v) * (1 - math.cos(th))
+        np.testing.assert_allclose(M.rotate(q, v[:, None])[:, 0], rod, atol=1e-14)
+
+
+def test_quat_from_images_all_branches():
+    rng = np.random.default_rng(9)
+    qs = [rng.standard_normal(4) for _ in range(40)]
+    # rotations by ~pi about each axis exercise the branches with trace <= 0
+    for ax in range(3):
+        e = np.zeros(4)
+        e[0] = 1e-3
+        e[1 + ax] = 1.0
+        qs.append(e)
+        qs.append(-e)
+    q = np.array(qs)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    ex = M.rotate(q, np.tile(np.array([[1.0], [0.0], [0.0]]), (1, len(q))))
+    ey = M.rotate(q, np.tile(np.array([[0.0], [1.0], [0.0]]), (1, len(q))))
+    r = M.quat_from_images(ex, ey)
+    sgn = np.sign(np.sum(r * q, axis=1))[:, None]
+    np.testing.assert_allclose(r * sgn, q, atol=1e-13)
+
+
+def test_adam_first_step_closed_form():
+    # first step: m^ = g, v^ = g^2, so every coordinate moves by lr g / (|g| + eps)
+    rng = np.random.default_rng(1)
+    p = rng.standard_normal(50)
+    g = rng.standard_normal(50)
+    p1, m, v = M.adam_step(p, np.zeros(50), np.zeros(50), g, 1, lr=1e-3, eps=1e-8)
+    np.testing.assert_allclose(p1, p - 1e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    # a constant gradient keeps m^ = g, v^ = g^2 at every step
+    for t in range(2, 6):
+        p2, m, v = M.adam_step(p1, m, v, g, t, lr=1e-3, eps=0.0)
+        np.testing.assert_allclose(p2 - p1, -1e-3 * np.sign(g), atol=1e-14)
+        p1 = p2

@@ -250,8 +250,15 @@ def workload(name: str, spin_order: int = 2, Ggamma0: float = None):
         ring = rhic_like_ring(45.5 if Ggamma0 is None else Ggamma0)
         return dict(ring=with_spin_order(ring, spin_order), n_particles=100000,
                     turns=1000, spin_order=spin_order, seed=3450)
+    if name == "rhic_like_spin_map":
+        # learned one-turn spin map: 2e6 training pairs, 1e4 particles x 1e4
+        # turns of stroboscopic averaging (errors judged at turn 1000)
+        ring = rhic_like_ring(45.5 if Ggamma0 is None else Ggamma0)
+        return dict(ring=with_spin_order(ring, spin_order), n_particles=10000,
+                    turns=10000, spin_order=spin_order, seed=3452, n_pairs=2000000, cut=3.0)
     if name == "rhic_like_1e6_mixed":
         ring = rhic_like_ring(45.5 if Ggamma0 is None else Ggamma0)
         return dict(ring=with_spin_order(ring, spin_order), n_particles=1000000,
                     turns=1000, spin_order=spin_order, seed=3451)
     raise KeyError(name)
+
