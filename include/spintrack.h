@@ -240,53 +240,74 @@ int st_gemm_bf16(const void* A, const void* B, float* D, int32_t M, int32_t N, i
 /* ---- learned one-turn spin map ------------------------------------------
  * A multilayer perceptron 6 -> 256 -> 256 -> 256 -> 256 -> 4 with SiLU
  * activations maps a particle's orbit z = (X, Px, Y, Py, T, Pt) at the fixed
- * azimuth s = 0 to its one-turn spin rotation: q = normalise(q0 + L x + s y),
- * x = z scaled per coordinate, y the network output, q0 the closed-orbit
- * one-turn quaternion and L an optional linear term.  Weights and
- * activations are bf16 on the tensor cores (st_gemm_bf16's kernel) with FP32
- * accumulation; master weights and Adam moments are FP32.  All x / q arrays
- * below are device memory, row-major float [B][6] / [B][4].  The parameter
- * vector (host, float[st_mlp_param_count()]) is W1[256][6], b1, W2[256][256],
- * b2, W3, b3, W4, b4, W5[4][256], b5. */
+ * azimuth s = 0 to its one-turn spin rotation (the composed element rotations
+ * of Sec. 4, Eqs. (37)-(39)) through an FP64 head
+ *     u = q0 + P(x) + s y,   q = u / |u|,   x = in_scale * z,
+ * q0 the closed-orbit one-turn quaternion, P a polynomial in x (degree <= 3,
+ * fitted by st_mlp_fit_head; st_mlp_set_head installs a linear one), s the
+ * output scales (one per component, s y componentwise) and y the network's
+ * output.  Weights and activations are bf16
+ * on the tensor cores (st_gemm_bf16's kernel) with FP32 accumulation; each
+ * scaled input enters the first layer as two bf16 numbers (hi, and the bf16
+ * rounding of x - hi) multiplying the same weight, so inputs are resolved to
+ * about 2^-16.  Master weights and Adam moments are FP32.  All x / q / r
+ * arrays below are device memory, row-major float [B][6] / [B][4].  The
+ * parameter vector (host, float[st_mlp_param_count()]) is W1[256][6], b1,
+ * W2[256][256], b2, W3, b3, W4, b4, W5[4][256], b5.
+ * Monomials of P, in order: 1; x_0..x_5; x_i x_j (0 <= i <= j < 6, i the
+ * outer loop); x_i x_j x_k (i <= j <= k) -- 1, 7, 28 or 84 terms for degree
+ * 0..3. */
 typedef struct st_mlp st_mlp;
 int64_t st_mlp_param_count(void);
 /* Buffers for batches of up to max_batch rows (padded to 128); parameters
- * start at zero.  cuda_stream as st_ctx_create. */
+ * start at zero; head q0 = (1,0,0,0), P = 0, s = 1, unit input scales.
+ * cuda_stream as st_ctx_create. */
 int st_mlp_create(int32_t max_batch, void* cuda_stream, st_mlp** out);
 int st_mlp_destroy(st_mlp* mlp);
 int st_mlp_set_params(st_mlp* mlp, const float* params);     /* host; resets Adam */
 int st_mlp_get_params(st_mlp* mlp, float* params);           /* host */
-/* Head: q0[4], lin[4][6] (NULL = zero), out_scale > 0, in_scale[6]. */
+/* Head: q0[4], P(x) = lin x with lin[4][6] (NULL = zero), out_scale > 0,
+ * in_scale[6] >= 0 (0 removes a coordinate from P and from the network). */
 int st_mlp_set_head(st_mlp* mlp, const double* q0, const double* lin, double out_scale, const double* in_scale);
-/* Training pairs in the network's layout: z_soa (device double [6][n], the
- * orbits at s = 0 before the turn) and q_soa (device double [4][n], their
- * one-turn quaternions from st_track_one_turn_map) to x_rows (device float
- * [n][6]) and q_rows (device float [n][4]).  Asynchronous on cuda_stream. */
-int st_mlp_pack_pairs(const double* z_soa, const double* q_soa, int64_t n, float* x_rows, float* q_rows,
-                      void* cuda_stream);
-/* FP64 least-squares fit q - q0 ~ c + L x over n pairs (z_soa, q_soa as for
- * st_mlp_pack_pairs; lost: device flags, may be NULL, flagged pairs are left
- * out), with q0 and the input scales of the head last set; x = in_scale * z.
- * The moments are summed on the device in FP64 and the normal equations
- * (7x7, coordinates with in_scale 0 dropped) solved on the host by Cholesky.
- * Writes L to lin_out (host double [4][6]; pass it to st_mlp_set_head).
- * Synchronises the network's stream.  Errors: ST_EINVAL (singular fit). */
-int st_mlp_fit_linear(st_mlp* mlp, const double* z_soa, const double* q_soa, const uint8_t* lost, int64_t n,
-                      double* lin_out);
+/* Output scales s only, one per quaternion component: out_scale[4] > 0. */
+int st_mlp_set_scale(st_mlp* mlp, const double* out_scale);
+/* FP64 least-squares fit of q - q0 by P of the given degree (0..3) over n
+ * tracked pairs: z_soa (device double [6][n], orbits at s = 0), q_soa (device
+ * double [4][n], their one-turn quaternions from st_track_one_turn_map), lost
+ * (device flags, may be NULL; flagged pairs are left out); q0 and in_scale as
+ * last set.  The moments are summed on the device in FP64 and the normal
+ * equations (monomials of coordinates with in_scale 0 dropped) solved on the
+ * host by Cholesky.  Installs P in the head; writes its coefficients to
+ * coef_out (host double [4][n_terms], may be NULL) and the RMS of each
+ * residual component to rms_out (host double [4], may be NULL).  Synchronises
+ * the network's stream.  Errors: ST_EINVAL (arguments, singular fit). */
+int st_mlp_fit_head(st_mlp* mlp, int32_t degree, const double* z_soa, const double* q_soa, const uint8_t* lost,
+                    int64_t n, double* coef_out, double* rms_out);
+/* Training rows from tracked pairs (z_soa, q_soa as for st_mlp_fit_head):
+ * x_rows = z (float [n][6]) and the residual targets
+ * r_rows = (q - q0 - P(x)) / s (computed in FP64, float [n][4]) with the
+ * current head.  Asynchronous. */
+int st_mlp_make_targets(st_mlp* mlp, const double* z_soa, const double* q_soa, int64_t n, float* x_rows,
+                        float* r_rows);
 /* Inference: q[B][4] unit quaternions for x[B][6].  Asynchronous. */
 int st_mlp_forward(st_mlp* mlp, const float* x, int32_t B, float* q_out);
-/* Loss L = mean_b |q_b - q_target_b|^2 and its gradient with respect to all
- * parameters (kept on the device for st_mlp_adam_step).  If loss / grads
- * (host, may be NULL) are given they are filled and the call synchronises. */
+/* Loss L = mean_b |q_b - q_target_b|^2 of the normalised head output and its
+ * gradient with respect to all parameters (kept on the device for
+ * st_mlp_adam_step).  If loss / grads (host, may be NULL) are given they are
+ * filled and the call synchronises. */
 int st_mlp_loss_grad(st_mlp* mlp, const float* x, const float* q_target, int32_t B, float* loss, float* grads);
+/* The same for the residual regression L = mean_b |y_b - r_b|^2 on the raw
+ * network outputs y, with targets from st_mlp_make_targets. */
+int st_mlp_loss_grad_residual(st_mlp* mlp, const float* x, const float* r_target, int32_t B, float* loss,
+                              float* grads);
 /* One Adam update with the last gradients; refreshes the bf16 weights. */
 int st_mlp_adam_step(st_mlp* mlp, float lr, float beta1, float beta2, float eps);
 /* Stroboscopic spin tracking with the learned map: per turn, the network
- * gives each particle's one-turn rotation from its orbit at s = 0, the spin
- * is rotated by it (FP64), and the orbit is tracked exactly for one turn
- * (st_track_orbit).  spin_sum (device double [3][n], may be NULL) accumulates
- * S after every turn.  Needs an FP64 context with n <= max_batch.
- * Asynchronous on the context stream. */
+ * gives each particle's one-turn rotation from its FP64 orbit at s = 0 (head
+ * in FP64), the spin is rotated by it (FP64), and the orbit is tracked
+ * exactly for one turn (st_track_orbit).  spin_sum (device double [3][n], may
+ * be NULL) accumulates S after every turn.  Needs an FP64 context with
+ * n <= max_batch.  Asynchronous on the context stream. */
 int st_track_surrogate(st_ctx* ctx, st_mlp* mlp, int32_t n_turns, double* spin_sum);
 
 /* Message describing the last error on the calling thread ("" if none). */

@@ -2,13 +2,16 @@
 INFRASTRUCTURE ONLY (tests, smoke and the bench's reference leg).
 
 Network: 6 -> 256 -> 256 -> 256 -> 256 -> 4, SiLU activations, head
-q = normalise(q0 + L x + s y) with x the per-coordinate scaled input and y the
-network output; loss mean_b |q_b - q_target_b|^2.  Flattened parameter order:
+q = normalise(q0 + P(x) + s y) with x the per-coordinate scaled input, P a
+polynomial (a linear term L x, or monomials with coefficients) and y the
+network output; losses mean_b |q_b - q_target_b|^2 (quaternion) and
+mean_b |y_b - r_b|^2 (residual regression).  Flattened parameter order:
 W1[256][6], b1, W2[256][256], b2, W3, b3, W4, b4, W5[4][256], b5.
 
-`bf16=True` rounds the weights, the scaled input and every hidden activation
-to bfloat16 (round to nearest even) while keeping FP64 arithmetic, i.e. the
-storage precision of the GPU kernels without their FP32 accumulation order.
+`bf16=True` rounds the weights and every hidden activation to bfloat16 (round
+to nearest even) and represents the scaled input as the two-term bf16 split of
+its float32 value, keeping FP64 arithmetic: the storage precision of the GPU
+kernels without their FP32 accumulation order.
 """
 from __future__ import annotations
 
@@ -50,12 +53,28 @@ def dsilu(z):
     return s * (1.0 + z * (1.0 - s))
 
 
-def forward(p, x, head, bf16=False):
-    """Returns (q [B,4], cache).  head: dict(q0[4], lin[4,6] or None, scale, in_scale[6])."""
+def split_bf16(v):
+    """Two-term bf16 representation of float32 values: hi = bf16(v),
+    lo = bf16(v - hi); returns hi + lo (exact in float64)."""
+    v = np.asarray(v, dtype=np.float32)
+    hi = round_bf16(v).astype(np.float32)
+    lo = round_bf16(v - hi)
+    return hi.astype(np.float64) + lo
+
+
+def scaled_input(x, in_scale, bf16):
+    """The first layer's input.  With bf16 the kernels' representation: the
+    float32 product x * in_scale split into bf16 hi + lo; else FP64 x * in_scale."""
+    if bf16:
+        return split_bf16(np.asarray(x, np.float32) * np.asarray(in_scale, np.float32))
+    return np.asarray(x, dtype=np.float64) * np.asarray(in_scale, dtype=np.float64)
+
+
+def network(p, a0, bf16=False):
+    """The five layers from the scaled input a0 [B, 6]: y [B, 4] and the cache."""
     layers = unpack(np.asarray(p, dtype=np.float64))
     rd = round_bf16 if bf16 else (lambda a: a)
-    xs = np.asarray(x, dtype=np.float64) * np.asarray(head["in_scale"], dtype=np.float64)
-    a = rd(xs)
+    a = a0
     acts, zs = [a], []
     for l in range(4):
         W, b = layers[l]
@@ -65,24 +84,11 @@ def forward(p, x, head, bf16=False):
         acts.append(a)
     W5, b5 = layers[4]
     y = a @ rd(W5).T + b5
-    lin = head.get("lin")
-    u = np.asarray(head["q0"], dtype=np.float64)[None, :] + head["scale"] * y
-    if lin is not None:
-        u = u + xs @ np.asarray(lin, dtype=np.float64).T
-    nrm = np.linalg.norm(u, axis=1, keepdims=True)
-    q = u / nrm
-    return q, dict(layers=layers, acts=acts, zs=zs, u=u, nrm=nrm, q=q, rd=rd)
+    return y, dict(layers=layers, acts=acts, zs=zs, rd=rd)
 
 
-def loss_grad(p, x, qt, head, bf16=False):
-    """Loss and gradient (flattened, same order as the parameters)."""
-    q, c = forward(p, x, head, bf16)
-    B = q.shape[0]
-    d = q - qt
-    loss = float((d * d).sum() / B)
-    gq = 2.0 * d / B
-    gu = (gq - q * (q * gq).sum(axis=1, keepdims=True)) / c["nrm"]
-    gy = head["scale"] * gu
+def backward(c, gy):
+    """Gradient (flattened, parameter order) from dL/dy [B, 4]."""
     rd = c["rd"]
     grads = [None] * 5
     W5, _ = c["layers"][4]
@@ -93,8 +99,59 @@ def loss_grad(p, x, qt, head, bf16=False):
         W, _ = c["layers"][l]
         grads[l] = (gz.T @ c["acts"][l], gz.sum(axis=0))
         ga = gz @ rd(W)
-    flat = np.concatenate([np.concatenate([g[0].ravel(), g[1]]) for g in grads])
-    return loss, flat
+    return np.concatenate([np.concatenate([g[0].ravel(), g[1]]) for g in grads])
+
+
+def poly(terms, coef, xs):
+    """P(x) [B, 4] = sum_f coef[:, f] prod_{i in terms[f]} x_i."""
+    out = np.zeros((xs.shape[0], 4))
+    for f, t in enumerate(terms):
+        m = np.ones(xs.shape[0])
+        for i in t:
+            m = m * xs[:, i]
+        out += m[:, None] * np.asarray(coef)[:, f][None, :]
+    return out
+
+
+def head_polynomial(head, xs):
+    """P(x) of a head: 'lin' [4, 6] (linear term) or 'poly' = (terms, coef)."""
+    if head.get("poly") is not None:
+        terms, coef = head["poly"]
+        return poly(terms, coef, xs)
+    if head.get("lin") is not None:
+        return xs @ np.asarray(head["lin"], dtype=np.float64).T
+    return np.zeros((xs.shape[0], 4))
+
+
+def forward(p, x, head, bf16=False):
+    """q [B, 4] = normalise(q0 + P(x) + s y) and the cache.
+    head: dict(q0[4], lin[4, 6] or poly=(terms, coef) or neither, scale, in_scale[6])."""
+    y, c = network(p, scaled_input(x, head["in_scale"], bf16), bf16)
+    xs = np.asarray(x, dtype=np.float64) * np.asarray(head["in_scale"], dtype=np.float64)
+    u = np.asarray(head["q0"], dtype=np.float64)[None, :] + head_polynomial(head, xs) + head["scale"] * y
+    nrm = np.linalg.norm(u, axis=1, keepdims=True)
+    q = u / nrm
+    c.update(u=u, nrm=nrm, q=q, y=y)
+    return q, c
+
+
+def loss_grad(p, x, qt, head, bf16=False):
+    """Loss mean_b |q_b - qt_b|^2 and its gradient (flattened, parameter order)."""
+    q, c = forward(p, x, head, bf16)
+    B = q.shape[0]
+    d = q - qt
+    loss = float((d * d).sum() / B)
+    gq = 2.0 * d / B
+    gu = (gq - q * (q * gq).sum(axis=1, keepdims=True)) / c["nrm"]
+    return loss, backward(c, head["scale"] * gu)
+
+
+def residual_loss_grad(p, x, r, in_scale, bf16=False):
+    """Regression of the raw outputs: loss mean_b |y_b - r_b|^2 and its gradient."""
+    y, c = network(p, scaled_input(x, in_scale, bf16), bf16)
+    B = y.shape[0]
+    d = y - r
+    return float((d * d).sum() / B), backward(c, 2.0 * d / B)
 
 
 def quat_from_images(ex, ey):

@@ -57,8 +57,6 @@ SIGNATURES = {
     "st_track_orbit": ([_VP, ctypes.c_int32], ctypes.c_int),
     "st_track_one_turn_map": ([_VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
     "st_track_average": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP], ctypes.c_int),
-    "st_mlp_pack_pairs": ([_VP, _VP, ctypes.c_int64, _VP, _VP, _VP], ctypes.c_int),
-    "st_mlp_fit_linear": ([_VP, _VP, _VP, _VP, ctypes.c_int64, _VP], ctypes.c_int),
     "st_ctx_set_launch": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "st_measure_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "st_track_fp64_noalloc": ([ctypes.POINTER(StElement), ctypes.c_int32, ctypes.POINTER(StReference), _VP, _VP,
@@ -80,8 +78,13 @@ SIGNATURES = {
     "st_mlp_set_params": ([_VP, _VP], ctypes.c_int),
     "st_mlp_get_params": ([_VP, _VP], ctypes.c_int),
     "st_mlp_set_head": ([_VP, _VP, _VP, ctypes.c_double, _VP], ctypes.c_int),
+    "st_mlp_set_scale": ([_VP, _VP], ctypes.c_int),
+    "st_mlp_fit_head": ([_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int64, _VP, _VP], ctypes.c_int),
+    "st_mlp_make_targets": ([_VP, _VP, _VP, ctypes.c_int64, _VP, _VP], ctypes.c_int),
     "st_mlp_forward": ([_VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
     "st_mlp_loss_grad": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), _VP], ctypes.c_int),
+    "st_mlp_loss_grad_residual": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), _VP],
+                                  ctypes.c_int),
     "st_mlp_adam_step": ([_VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], ctypes.c_int),
     "st_track_surrogate": ([_VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
     "st_last_error": ([], ctypes.c_char_p),
@@ -322,10 +325,30 @@ class MLP:
     def forward(self, x_ptr: int, B: int, q_ptr: int):
         _check(load().st_mlp_forward(self.handle, x_ptr, int(B), q_ptr))
 
-    def fit_linear(self, z_ptr: int, q_ptr: int, n: int, lost_ptr: Optional[int] = None) -> np.ndarray:
-        lin = np.empty((4, 6), np.float64)
-        _check(load().st_mlp_fit_linear(self.handle, z_ptr, q_ptr, lost_ptr, int(n), lin.ctypes.data))
-        return lin
+    def set_scale(self, out_scale):
+        """Output scales: a number (all components) or four numbers."""
+        sc = np.ascontiguousarray(np.broadcast_to(np.asarray(out_scale, dtype=np.float64), (4,)))
+        _check(load().st_mlp_set_scale(self.handle, sc.ctypes.data))
+
+    def fit_head(self, degree: int, z_ptr: int, q_ptr: int, n: int, lost_ptr: Optional[int] = None):
+        """Returns (coef [4, n_terms], rms [4])."""
+        nt = poly_term_count(degree)
+        coef = np.empty((4, nt), np.float64)
+        rms = np.empty(4, np.float64)
+        _check(load().st_mlp_fit_head(self.handle, int(degree), z_ptr, q_ptr, lost_ptr, int(n), coef.ctypes.data,
+                                      rms.ctypes.data))
+        return coef, rms
+
+    def make_targets(self, z_ptr: int, q_ptr: int, n: int, x_rows_ptr: int, r_rows_ptr: int):
+        _check(load().st_mlp_make_targets(self.handle, z_ptr, q_ptr, int(n), x_rows_ptr, r_rows_ptr))
+
+    def loss_grad_residual(self, x_ptr: int, r_ptr: int, B: int, want_loss: bool = True, want_grads: bool = False):
+        loss = ctypes.c_float()
+        g = np.empty(self.n_params, np.float32) if want_grads else None
+        _check(load().st_mlp_loss_grad_residual(self.handle, x_ptr, r_ptr, int(B),
+                                                ctypes.byref(loss) if want_loss else None,
+                                                g.ctypes.data if g is not None else None))
+        return (loss.value if want_loss else None), g
 
     def loss_grad(self, x_ptr: int, qt_ptr: int, B: int, want_grads: bool = False):
         loss = ctypes.c_float()
@@ -352,9 +375,22 @@ class MLP:
             pass
 
 
-def st_mlp_pack_pairs(z_ptr: int, q_ptr: int, n: int, x_rows_ptr: int, q_rows_ptr: int,
-                      stream: Optional[int] = None) -> None:
-    _check(load().st_mlp_pack_pairs(z_ptr, q_ptr, int(n), x_rows_ptr, q_rows_ptr, stream))
+def poly_term_count(degree: int) -> int:
+    """Number of monomials of the 6 inputs up to the degree (1, 7, 28, 84)."""
+    return [1, 7, 28, 84][int(degree)]
+
+
+def poly_terms(degree: int):
+    """The head polynomial's monomials in the library's order, each a tuple of
+    input indices (empty for the constant)."""
+    t = [()]
+    if degree >= 1:
+        t += [(i,) for i in range(6)]
+    if degree >= 2:
+        t += [(i, j) for i in range(6) for j in range(i, 6)]
+    if degree >= 3:
+        t += [(i, j, k) for i in range(6) for j in range(i, 6) for k in range(j, 6)]
+    return t
 
 
 def st_track_surrogate(ctx: int, mlp: int, n_turns: int, spin_sum_ptr: Optional[int] = None) -> None:

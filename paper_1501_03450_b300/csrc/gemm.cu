@@ -1,0 +1,105 @@
+// Host side of the tcgen05 BF16 GEMM: tensor-map encoding (driver entry
+// point, no libcuda link), tile-width dispatch, and the C-ABI entry point
+// st_gemm_bf16.  The learned one-turn spin map builds on gemm_bf16_tn.
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "st_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace st {
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int get_encoder() {
+    if (g_encode) return ST_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        set_error("cuTensorMapEncodeTiled unavailable from the driver");
+        return ST_ECUDA;
+    }
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return ST_OK;
+}
+
+// 2D bf16 row-major matrix [rows][cols], box = box_rows x 64 columns,
+// 128-byte swizzle.
+static int make_tmap(CUtensorMap* tm, const void* base, int rows, int cols, int box_rows) {
+    int rc = get_encoder();
+    if (rc) return rc;
+    if (((uintptr_t)base & 15) || (cols * 2) % 16) {
+        set_error("gemm: operand base must be 16-byte aligned and rows a multiple of 16 bytes");
+        return ST_EINVAL;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return ST_ECUDA;
+    }
+    return ST_OK;
+}
+
+template <int BN>
+static int launch_gemm_bn(const void* A, const void* B, int M, int N, int K, const GemmEpi& epi, int32_t* status,
+                          cudaStream_t stream) {
+    using Cf = GemmCfg<BN>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Cf::SMEM_BYTES);
+        if (e != cudaSuccess) return cuda_fail(e, "gemm: cudaFuncSetAttribute");
+        attr = true;
+    }
+    CUtensorMap ta, tb;
+    int rc = make_tmap(&ta, A, M, K, 128);
+    if (rc == ST_OK) rc = make_tmap(&tb, B, N, K, BN);
+    if (rc) return rc;
+    dim3 grid(M / 128, N / BN);
+    gemm_bf16_tn_kernel<BN><<<grid, 128, Cf::SMEM_BYTES, stream>>>(ta, tb, K, epi, status);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "gemm launch");
+}
+
+// D = A B^T with the epilogue; M % 128 == 0, K % 64 == 0, N % 16 == 0.
+int gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const GemmEpi& epi, int32_t* status,
+                 cudaStream_t stream) {
+    if (M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64 || N % 16) {
+        set_error("gemm: need M %% 128 == 0, K %% 64 == 0, N %% 16 == 0 (got %d, %d, %d)", M, N, K);
+        return ST_EINVAL;
+    }
+    if (N % 256 == 0) return launch_gemm_bn<256>(A, B, M, N, K, epi, status, stream);
+    if (N % 128 == 0) return launch_gemm_bn<128>(A, B, M, N, K, epi, status, stream);
+    if (N % 64 == 0) return launch_gemm_bn<64>(A, B, M, N, K, epi, status, stream);
+    if (N % 32 == 0) return launch_gemm_bn<32>(A, B, M, N, K, epi, status, stream);
+    return launch_gemm_bn<16>(A, B, M, N, K, epi, status, stream);
+}
+
+}  // namespace st
+
+using namespace st;
+
+extern "C" int st_gemm_bf16(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K,
+                            const float* bias, int32_t* status, void* cuda_stream) {
+    if (!A || !B || !D || !status) {
+        set_error("st_gemm_bf16: null pointer");
+        return ST_EINVAL;
+    }
+    GemmEpi epi;
+    memset(&epi, 0, sizeof(epi));
+    epi.mode = bias ? EPI_BIAS_F32 : EPI_F32;
+    epi.n_valid = N;
+    epi.out_f32 = D;
+    epi.ld_f32 = N;
+    epi.bias = bias;
+    return gemm_bf16_tn(A, B, M, N, K, epi, status, (cudaStream_t)cuda_stream);
+}
+

@@ -1,0 +1,1023 @@
+// Learned one-turn spin map: a multilayer perceptron 6 -> 256 -> 256 -> 256 ->
+// 256 -> 4 with SiLU activations whose layers run on the tcgen05 BF16 GEMM
+// (gemm_bf16_tn: bf16 weights and activations, FP32 accumulation in tensor
+// memory), FP32 master weights and Adam moments, and an FP64 head:
+//
+//     u = q0 + P(x) + s y,   q = u / |u|,   x = in_scale * z,
+//
+// q0 the closed-orbit one-turn quaternion, P a polynomial of degree <= 3 in x
+// fitted by FP64 least squares over tracked pairs (degree 1 = a linear term),
+// s the output scales (one per component) and y the network's 4 outputs.  The
+// network learns the residual (q - q0 - P(x)) / s, component by component.
+//
+// The scaled input is handed to the first layer as two bf16 numbers (hi and
+// the bf16 rounding of x - hi) multiplying the same weight column, so the
+// network sees x to about 2^-16 relative although every operand is bf16; the
+// first layer's K = 64 padding has room for both at no extra cost.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "st_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace st {
+
+constexpr int MLP_IN = 6, MLP_H = 256, MLP_OUT = 4, MLP_KIN = 64, MLP_NOUT = 16;
+constexpr int POLY_MAX_DEG = 3, POLY_MAX = 84;   // monomials of 6 inputs up to degree 3
+
+// flattened FP32 parameter layout: W1 [256][6], b1, W2 [256][256], b2, W3, b3,
+// W4, b4, W5 [4][256], b5
+__host__ __device__ constexpr int64_t mlp_w_off(int l) {
+    return l == 0 ? 0 : l == 1 ? 1792 : l == 2 ? 67584 : l == 3 ? 133376 : 199168;
+}
+__host__ __device__ constexpr int64_t mlp_b_off(int l) {
+    return l == 0 ? 1536 : l == 1 ? 67328 : l == 2 ? 133120 : l == 3 ? 198912 : 200192;
+}
+constexpr int64_t MLP_PARAMS = 200196;
+static_assert(mlp_b_off(0) == MLP_H * MLP_IN && mlp_w_off(1) == mlp_b_off(0) + MLP_H &&
+                  mlp_b_off(1) == mlp_w_off(1) + MLP_H * MLP_H && mlp_w_off(2) == mlp_b_off(1) + MLP_H &&
+                  mlp_b_off(2) == mlp_w_off(2) + MLP_H * MLP_H && mlp_w_off(3) == mlp_b_off(2) + MLP_H &&
+                  mlp_b_off(3) == mlp_w_off(3) + MLP_H * MLP_H && mlp_w_off(4) == mlp_b_off(3) + MLP_H &&
+                  mlp_b_off(4) == mlp_w_off(4) + MLP_OUT * MLP_H && MLP_PARAMS == mlp_b_off(4) + MLP_OUT,
+              "parameter layout");
+
+// Monomials of the 6 inputs up to a degree, graded: 1; x0..x5; x_i x_j
+// (i <= j, i outer); x_i x_j x_k (i <= j <= k).  Each is three input indices,
+// 6 standing for "none".  Returns the count (1, 7, 28 or 84).
+static int build_terms(int degree, uint8_t terms[POLY_MAX][3]) {
+    int f = 0;
+    terms[f][0] = terms[f][1] = terms[f][2] = MLP_IN;
+    ++f;
+    if (degree >= 1)
+        for (int i = 0; i < MLP_IN; ++i, ++f) {
+            terms[f][0] = (uint8_t)i;
+            terms[f][1] = terms[f][2] = MLP_IN;
+        }
+    if (degree >= 2)
+        for (int i = 0; i < MLP_IN; ++i)
+            for (int j = i; j < MLP_IN; ++j, ++f) {
+                terms[f][0] = (uint8_t)i;
+                terms[f][1] = (uint8_t)j;
+                terms[f][2] = MLP_IN;
+            }
+    if (degree >= 3)
+        for (int i = 0; i < MLP_IN; ++i)
+            for (int j = i; j < MLP_IN; ++j)
+                for (int k = j; k < MLP_IN; ++k, ++f) {
+                    terms[f][0] = (uint8_t)i;
+                    terms[f][1] = (uint8_t)j;
+                    terms[f][2] = (uint8_t)k;
+                }
+    return f;
+}
+
+// The FP64 head.  terms / coef point to device memory: terms [n_terms][3],
+// coef [4][POLY_MAX]; one output scale per quaternion component.
+struct PolyHead {
+    double q0[4];
+    double scale[4];
+    double in_scale[MLP_IN];
+    int32_t n_terms;
+    const uint8_t* terms;
+    const double* coef;
+};
+
+// input scales for the layout kernels
+struct InScale {
+    float s[MLP_IN];
+};
+
+}  // namespace st
+
+struct st_mlp {
+    int32_t max_batch = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+    __nv_bfloat16 *W1p = nullptr, *W2 = nullptr, *W3 = nullptr, *W4 = nullptr, *W5p = nullptr;
+    __nv_bfloat16 *W2T = nullptr, *W3T = nullptr, *W4T = nullptr, *W5Tp = nullptr;
+    __nv_bfloat16 *X0 = nullptr, *X0T = nullptr;            // [Bp][64] / [64][Bp]: hi, lo, zero
+    __nv_bfloat16* A[4] = {nullptr, nullptr, nullptr, nullptr};
+    __nv_bfloat16* AT[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* Z[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* Y = nullptr;                                     // [Bp][16]
+    __nv_bfloat16 *dYp = nullptr, *dYT = nullptr;
+    __nv_bfloat16* dZ[2] = {nullptr, nullptr};
+    __nv_bfloat16* dZT[2] = {nullptr, nullptr};
+    float* dWtmp = nullptr;                                 // [256][64]
+    float* b5p = nullptr;                                   // [16] output bias, zero padded
+    double* loss = nullptr;
+    int32_t* status = nullptr;
+    uint8_t* d_terms = nullptr;                             // [POLY_MAX][3]
+    double* d_coef = nullptr;                               // [4][POLY_MAX]
+    double h_coef[4][st::POLY_MAX];
+    uint8_t h_terms[st::POLY_MAX][3];
+    int32_t degree = 1;
+    st::PolyHead head;
+    st::InScale in_scale;
+    int64_t step = 0;
+    bool have_grads = false;
+};
+
+namespace st {
+
+__device__ __forceinline__ void poly_eval(const PolyHead& h, const double* xs, double* out) {
+    for (int k = 0; k < 4; ++k) out[k] = 0.0;
+    for (int f = 0; f < h.n_terms; ++f) {
+        double mono = 1.0;
+        for (int j = 0; j < 3; ++j) {
+            const int c = h.terms[3 * f + j];
+            if (c < MLP_IN) mono *= xs[c];
+        }
+        for (int k = 0; k < 4; ++k) out[k] = fma(h.coef[k * POLY_MAX + f], mono, out[k]);
+    }
+}
+
+// u = q0 + P(x) + s y in FP64
+__device__ __forceinline__ void head_u(const PolyHead& h, const double* xs, const float* y, double* u) {
+    double pv[4];
+    poly_eval(h, xs, pv);
+    for (int k = 0; k < 4; ++k) u[k] = h.q0[k] + pv[k] + h.scale[k] * (double)y[k];
+}
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));   // v - hi is exact in FP32
+}
+
+// one row of the first layer's input: hi parts in columns 0..5, lo parts in
+// 6..11, zeros after
+__device__ __forceinline__ void write_input_row(const float* xs, int r, int Bp, __nv_bfloat16* __restrict__ X0,
+                                                __nv_bfloat16* __restrict__ X0T) {
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+    for (int c = 0; c < MLP_KIN; ++c) {
+        __nv_bfloat16 b = zero;
+        if (c < 2 * MLP_IN) {
+            __nv_bfloat16 hi, lo;
+            split_bf16(xs[c % MLP_IN], hi, lo);
+            b = c < MLP_IN ? hi : lo;
+        }
+        X0[(size_t)r * MLP_KIN + c] = b;
+        if (X0T) X0T[(size_t)c * Bp + r] = b;
+    }
+}
+
+__global__ void mlp_pack_x(const float* __restrict__ x, int B, int Bp, InScale is, __nv_bfloat16* __restrict__ X0,
+                           __nv_bfloat16* __restrict__ X0T) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= Bp) return;
+    float xs[MLP_IN];
+    for (int c = 0; c < MLP_IN; ++c) xs[c] = r < B ? x[(size_t)r * MLP_IN + c] * is.s[c] : 0.0f;
+    write_input_row(xs, r, Bp, X0, X0T);
+}
+
+// the same from the tracker's FP64 pair-SoA state (coordinates X..Pt)
+__global__ void mlp_pack_state(const double2* __restrict__ xpx, const double2* __restrict__ ypy,
+                               const double2* __restrict__ tpt, int B, int Bp, PolyHead h,
+                               __nv_bfloat16* __restrict__ X0) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= Bp) return;
+    float xs[MLP_IN] = {0, 0, 0, 0, 0, 0};
+    if (r < B) {
+        const double2 a = xpx[r], b = ypy[r], c = tpt[r];
+        const double z[MLP_IN] = {a.x, a.y, b.x, b.y, c.x, c.y};
+        for (int k = 0; k < MLP_IN; ++k) xs[k] = (float)(z[k] * h.in_scale[k]);
+    }
+    write_input_row(xs, r, Bp, X0, nullptr);
+}
+
+// writes dL/dy (bf16, zero padded) row-major [Bp][64] and transposed [16][Bp]
+__device__ __forceinline__ void write_dy(const float* gy, int r, int Bp, __nv_bfloat16* __restrict__ dYp,
+                                         __nv_bfloat16* __restrict__ dYT) {
+    for (int c = 0; c < MLP_KIN; ++c) dYp[(size_t)r * MLP_KIN + c] = __float2bfloat16_rn(c < 4 ? gy[c] : 0.0f);
+    for (int c = 0; c < MLP_NOUT; ++c) dYT[(size_t)c * Bp + r] = __float2bfloat16_rn(c < 4 ? gy[c] : 0.0f);
+}
+
+// block sum of l, one double atomic per block
+__device__ __forceinline__ void block_loss_add(double l, double* loss) {
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(loss, t);
+    }
+}
+
+// Quaternion head: q = u / |u|; with targets the loss mean_b |q_b - qt_b|^2 and
+// dL/dy = s (I - q q^T) (2 (q - qt) / B) / |u|.
+__global__ void mlp_head_quat(const float* __restrict__ Y, const float* __restrict__ x, int B, int Bp, PolyHead h,
+                              const float* __restrict__ qt, float* __restrict__ q_out, double* __restrict__ loss,
+                              __nv_bfloat16* __restrict__ dYp, __nv_bfloat16* __restrict__ dYT) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (r < Bp) {
+        float gy[4] = {0, 0, 0, 0};
+        if (r < B) {
+            double xs[MLP_IN], u[4];
+            for (int c = 0; c < MLP_IN; ++c) xs[c] = (double)x[(size_t)r * MLP_IN + c] * h.in_scale[c];
+            head_u(h, xs, Y + (size_t)r * MLP_NOUT, u);
+            const double nu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + u[3] * u[3]);
+            double q[4];
+            for (int k = 0; k < 4; ++k) q[k] = u[k] / nu;
+            if (q_out)
+                for (int k = 0; k < 4; ++k) q_out[(size_t)r * 4 + k] = (float)q[k];
+            if (qt) {
+                double d[4], dq = 0.0;
+                for (int k = 0; k < 4; ++k) {
+                    d[k] = q[k] - (double)qt[(size_t)r * 4 + k];
+                    l += d[k] * d[k];
+                    dq += q[k] * d[k];
+                }
+                for (int k = 0; k < 4; ++k) gy[k] = (float)(h.scale[k] * (2.0 / B) * (d[k] - q[k] * dq) / nu);
+            }
+        }
+        if (dYp) write_dy(gy, r, Bp, dYp, dYT);
+    }
+    if (loss) block_loss_add(l / B, loss);
+}
+
+// Residual head: loss mean_b |y_b - r_b|^2, dL/dy = 2 (y - r) / B.
+__global__ void mlp_head_resid(const float* __restrict__ Y, const float* __restrict__ rt, int B, int Bp,
+                               double* __restrict__ loss, __nv_bfloat16* __restrict__ dYp,
+                               __nv_bfloat16* __restrict__ dYT) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (r < Bp) {
+        float gy[4] = {0, 0, 0, 0};
+        if (r < B) {
+            for (int k = 0; k < 4; ++k) {
+                const float d = Y[(size_t)r * MLP_NOUT + k] - rt[(size_t)r * 4 + k];
+                l += (double)d * d;
+                gy[k] = (2.0f / B) * d;
+            }
+        }
+        write_dy(gy, r, Bp, dYp, dYT);
+    }
+    block_loss_add(l / B, loss);
+}
+
+// row sums of a [rows][Bp] bf16 matrix (bias gradients), one warp per row
+__global__ void mlp_rowsum(const __nv_bfloat16* __restrict__ M, int rows, int Bp, float* __restrict__ out) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    float s = 0.0f;
+    for (int c = threadIdx.x & 31; c < Bp; c += 32) s += __bfloat162float(M[(size_t)row * Bp + c]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) out[row] = s;
+}
+
+// dW1 [256][6] from dWtmp [256][64]: the hi and lo input columns share W1
+__global__ void mlp_gather_w1(const float* __restrict__ tmp, float* __restrict__ g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= MLP_H * MLP_IN) return;
+    const int r = i / MLP_IN, c = i % MLP_IN;
+    g[i] = tmp[r * MLP_KIN + c] + tmp[r * MLP_KIN + MLP_IN + c];
+}
+// dW5 [4][256] from D' [256][16] (transposed)
+__global__ void mlp_gather_w5(const float* __restrict__ tmp, float* __restrict__ g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= MLP_OUT * MLP_H) return;
+    const int o = i / MLP_H, in = i % MLP_H;
+    g[i] = tmp[in * MLP_NOUT + o];
+}
+
+// Refresh the bf16 weight copies (padded, and transposed for the backward
+// pass) from the FP32 master parameters.
+__global__ void mlp_cast_weights(const float* __restrict__ p, __nv_bfloat16* W1p, __nv_bfloat16* W2,
+                                 __nv_bfloat16* W3, __nv_bfloat16* W4, __nv_bfloat16* W5p, __nv_bfloat16* W2T,
+                                 __nv_bfloat16* W3T, __nv_bfloat16* W4T, __nv_bfloat16* W5Tp, float* b5p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < MLP_NOUT) b5p[i] = i < MLP_OUT ? p[mlp_b_off(4) + i] : 0.0f;
+    // W1p [256][64]: W1 in columns 0..5 (hi inputs) and again in 6..11 (lo inputs)
+    if (i < MLP_H * MLP_KIN) {
+        const int r = i / MLP_KIN, c = i % MLP_KIN;
+        W1p[i] = __float2bfloat16_rn(c < 2 * MLP_IN ? p[mlp_w_off(0) + r * MLP_IN + c % MLP_IN] : 0.0f);
+    }
+    if (i < MLP_H * MLP_H) {
+        const int r = i / MLP_H, c = i % MLP_H;
+        __nv_bfloat16* Ws[3] = {W2, W3, W4};
+        __nv_bfloat16* WTs[3] = {W2T, W3T, W4T};
+        for (int l = 0; l < 3; ++l) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(p[mlp_w_off(l + 1) + i]);
+            Ws[l][i] = b;
+            WTs[l][(size_t)c * MLP_H + r] = b;
+        }
+    }
+    // W5p [16][256]
+    if (i < MLP_NOUT * MLP_H) {
+        const int r = i / MLP_H, c = i % MLP_H;
+        W5p[i] = __float2bfloat16_rn(r < MLP_OUT ? p[mlp_w_off(4) + r * MLP_H + c] : 0.0f);
+    }
+    // W5Tp [256][64]
+    if (i < MLP_H * MLP_KIN) {
+        const int r = i / MLP_KIN, c = i % MLP_KIN;
+        W5Tp[i] = __float2bfloat16_rn(c < MLP_OUT ? p[mlp_w_off(4) + c * MLP_H + r] : 0.0f);
+    }
+}
+
+__global__ void mlp_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                         const float* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                         float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+// Spin step of the learned map: q = normalise(q0 + P(x) + s y) in FP64 from
+// the FP64 orbit at s = 0 and the FP32 network output, S <- q S conj(q);
+// optional running sum of S.
+__global__ void surrogate_apply(const float* __restrict__ Y, int B, PolyHead h, const double2* __restrict__ xpx,
+                                const double2* __restrict__ ypy, const double2* __restrict__ tpt,
+                                double2* __restrict__ sxy, double* __restrict__ szp, const uint8_t* __restrict__ lost,
+                                double* __restrict__ sum) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= B || lost[r]) return;
+    const double2 a = xpx[r], b = ypy[r], c = tpt[r];
+    const double z[MLP_IN] = {a.x, a.y, b.x, b.y, c.x, c.y};
+    double xs[MLP_IN], u[4];
+    for (int k = 0; k < MLP_IN; ++k) xs[k] = z[k] * h.in_scale[k];
+    head_u(h, xs, Y + (size_t)r * MLP_NOUT, u);
+    Quat q = qnormalize(Quat{u[0], u[1], u[2], u[3]});
+    const double2 s2 = sxy[r];
+    double sx = s2.x, sy = s2.y, sz = szp[r];
+    rotate_vec(q, sx, sy, sz);
+    sxy[r] = make_double2(sx, sy);
+    szp[r] = sz;
+    if (sum) {
+        sum[r] += sx;
+        sum[(size_t)B + r] += sy;
+        sum[2 * (size_t)B + r] += sz;
+    }
+}
+
+// Training rows from the tracker's SoA FP64 pairs (z [6][n] before the turn,
+// q [4][n] its one-turn quaternion): x_rows = z (float), r_rows = the residual
+// target (q - q0 - P(x)) / s (computed in FP64, stored as float).
+__global__ void mlp_make_targets(const double* __restrict__ z, const double* __restrict__ q, int64_t n, PolyHead h,
+                                 float* __restrict__ x_rows, float* __restrict__ r_rows) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double xs[MLP_IN], pv[4];
+    for (int c = 0; c < MLP_IN; ++c) {
+        const double zc = z[c * n + i];
+        x_rows[i * MLP_IN + c] = (float)zc;
+        xs[c] = zc * h.in_scale[c];
+    }
+    poly_eval(h, xs, pv);
+    for (int k = 0; k < 4; ++k) r_rows[i * 4 + k] = (float)((q[k * n + i] - h.q0[k] - pv[k]) / h.scale[k]);
+}
+
+// FP64 moments of the least-squares fit q - q0 ~ P(x): with features f (the
+// n_terms monomials) and responses e = q - q0, the products f_a f_b (a <= b),
+// f_a e_k and e_k e_k summed over the pairs, one value per entry of the pair
+// table (pa, pb index the row [f, e]).  Rows are staged 32 at a time in shared
+// memory; each thread owns up to FIT_PER_THREAD table entries.
+constexpr int FIT_ROWS = 32, FIT_THREADS = 256, FIT_PER_THREAD = 16;
+constexpr int FIT_W = POLY_MAX + 4;
+
+__global__ void __launch_bounds__(FIT_THREADS) mlp_fit_moments(const double* __restrict__ z,
+                                                               const double* __restrict__ q,
+                                                               const uint8_t* __restrict__ lost, int64_t n,
+                                                               PolyHead h, const uint8_t* __restrict__ pa,
+                                                               const uint8_t* __restrict__ pb, int n_entries,
+                                                               double* __restrict__ mom) {
+    __shared__ double rows[FIT_ROWS][FIT_W];
+    const int F = h.n_terms, W = F + 4;
+    double acc[FIT_PER_THREAD];
+    int ea[FIT_PER_THREAD], eb[FIT_PER_THREAD];
+#pragma unroll
+    for (int o = 0; o < FIT_PER_THREAD; ++o) {
+        acc[o] = 0.0;
+        const int t = threadIdx.x + o * FIT_THREADS;
+        ea[o] = t < n_entries ? pa[t] : 0;
+        eb[o] = t < n_entries ? pb[t] : 0;
+    }
+    const int64_t n_chunks = (n + FIT_ROWS - 1) / FIT_ROWS;
+    for (int64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        for (int e = threadIdx.x; e < FIT_ROWS * W; e += FIT_THREADS) {
+            const int row = e / W, col = e % W;
+            const int64_t i = ch * FIT_ROWS + row;
+            double val = 0.0;
+            if (i < n && !(lost && lost[i])) {
+                if (col < F) {
+                    val = 1.0;
+                    for (int j = 0; j < 3; ++j) {
+                        const int c = h.terms[3 * col + j];
+                        if (c < MLP_IN) val *= z[c * n + i] * h.in_scale[c];
+                    }
+                } else {
+                    val = q[(col - F) * n + i] - h.q0[col - F];
+                }
+            }
+            rows[row][col] = val;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int o = 0; o < FIT_PER_THREAD; ++o) {
+            if (threadIdx.x + o * FIT_THREADS < n_entries) {
+                double s = acc[o];
+                for (int row = 0; row < FIT_ROWS; ++row) s = fma(rows[row][ea[o]], rows[row][eb[o]], s);
+                acc[o] = s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 0; o < FIT_PER_THREAD; ++o) {
+        const int t = threadIdx.x + o * FIT_THREADS;
+        if (t < n_entries) atomicAdd(&mom[t], acc[o]);
+    }
+}
+
+static GemmEpi epi_base() {
+    GemmEpi e;
+    memset(&e, 0, sizeof(e));
+    return e;
+}
+
+static int mlp_refresh_weights(st_mlp* n) {
+    const int total = MLP_H * MLP_H;
+    mlp_cast_weights<<<(total + 255) / 256, 256, 0, n->stream>>>(n->p, n->W1p, n->W2, n->W3, n->W4, n->W5p, n->W2T,
+                                                                 n->W3T, n->W4T, n->W5Tp, n->b5p);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "mlp: weight cast");
+}
+
+static int upload_head(st_mlp* n) {
+    cudaError_t e = cudaMemcpyAsync(n->d_coef, n->h_coef, sizeof(n->h_coef), cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(n->d_terms, n->h_terms, sizeof(n->h_terms), cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "mlp: head upload");
+}
+
+// forward through the five layers from X0 (rows Bp); keep_t writes the
+// transposed activations and pre-activations for a following backward pass
+static int mlp_forward_layers(st_mlp* n, int Bp, bool keep_t) {
+    int rc;
+    GemmEpi e = epi_base();
+    const __nv_bfloat16* Win[4] = {n->W1p, n->W2, n->W3, n->W4};
+    const __nv_bfloat16* in = n->X0;
+    int K = MLP_KIN;
+    for (int l = 0; l < 4; ++l) {
+        e = epi_base();
+        e.mode = EPI_BIAS_SILU;
+        e.n_valid = MLP_H;
+        e.bias = n->p + mlp_b_off(l);
+        e.out_bf16 = n->A[l];
+        e.ld_bf16 = MLP_H;
+        e.out_bf16_t = keep_t ? n->AT[l] : nullptr;
+        e.ld_bf16_t = Bp;
+        e.z_out = keep_t ? n->Z[l] : nullptr;
+        e.ld_zo = MLP_H;
+        rc = gemm_bf16_tn(in, Win[l], Bp, MLP_H, K, e, n->status, n->stream);
+        if (rc) return rc;
+        in = n->A[l];
+        K = MLP_H;
+    }
+    e = epi_base();
+    e.mode = EPI_BIAS_F32;
+    e.n_valid = MLP_NOUT;
+    e.out_f32 = n->Y;
+    e.ld_f32 = MLP_NOUT;
+    // bias of the padded output layer: b5 for the first 4 columns, 0 after
+    e.bias = n->b5p;
+    return gemm_bf16_tn(in, n->W5p, Bp, MLP_NOUT, MLP_H, e, n->status, n->stream);
+}
+
+// Backward pass from dL/dy (dYp, dYT written by a head kernel) into the
+// gradient buffer g, using the activations kept by the forward pass.
+static int mlp_backward(st_mlp* n, int Bp) {
+    float* g = n->g;
+    // layer 5: dW5^T = A4^T . dY  (D'[256][16]), db5 = sum dY, dZ4 = (dY W5) * silu'(Z4)
+    GemmEpi ep = epi_base();
+    ep.mode = EPI_F32;
+    ep.n_valid = MLP_NOUT;
+    ep.out_f32 = n->dWtmp;
+    ep.ld_f32 = MLP_NOUT;
+    int rc = gemm_bf16_tn(n->AT[3], n->dYT, MLP_H, MLP_NOUT, Bp, ep, n->status, n->stream);
+    if (rc) return rc;
+    mlp_gather_w5<<<(MLP_OUT * MLP_H + 255) / 256, 256, 0, n->stream>>>(n->dWtmp, g + mlp_w_off(4));
+    mlp_rowsum<<<1, 128, 0, n->stream>>>(n->dYT, MLP_OUT, Bp, g + mlp_b_off(4));
+    ep = epi_base();
+    ep.mode = EPI_DSILU;
+    ep.n_valid = MLP_H;
+    ep.z_in = n->Z[3];
+    ep.ld_z = MLP_H;
+    ep.out_bf16 = n->dZ[0];
+    ep.ld_bf16 = MLP_H;
+    ep.out_bf16_t = n->dZT[0];
+    ep.ld_bf16_t = Bp;
+    rc = gemm_bf16_tn(n->dYp, n->W5Tp, Bp, MLP_H, MLP_KIN, ep, n->status, n->stream);
+    if (rc) return rc;
+    // hidden layers l = 3, 2, 1 (0-based weights W[l], activations A[l-1])
+    const __nv_bfloat16* WT[4] = {nullptr, n->W2T, n->W3T, n->W4T};
+    int cur = 0;
+    for (int l = 3; l >= 1; --l) {
+        // dW_l = dZ_l^T . A_{l-1}  ->  [256 out][256 in], straight into the gradient buffer
+        ep = epi_base();
+        ep.mode = EPI_F32;
+        ep.n_valid = MLP_H;
+        ep.out_f32 = g + mlp_w_off(l);
+        ep.ld_f32 = MLP_H;
+        rc = gemm_bf16_tn(n->dZT[cur], n->AT[l - 1], MLP_H, MLP_H, Bp, ep, n->status, n->stream);
+        if (rc) return rc;
+        mlp_rowsum<<<MLP_H / 4, 128, 0, n->stream>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(l));
+        // dZ_{l-1} = (dZ_l W_l) * silu'(Z_{l-1})
+        ep = epi_base();
+        ep.mode = EPI_DSILU;
+        ep.n_valid = MLP_H;
+        ep.z_in = n->Z[l - 1];
+        ep.ld_z = MLP_H;
+        ep.out_bf16 = n->dZ[1 - cur];
+        ep.ld_bf16 = MLP_H;
+        ep.out_bf16_t = n->dZT[1 - cur];
+        ep.ld_bf16_t = Bp;
+        rc = gemm_bf16_tn(n->dZ[cur], WT[l], Bp, MLP_H, MLP_H, ep, n->status, n->stream);
+        if (rc) return rc;
+        cur = 1 - cur;
+    }
+    // layer 1: dW1 = dZ1^T . X0 -> [256][64] -> [256][6] (hi + lo columns); db1
+    ep = epi_base();
+    ep.mode = EPI_F32;
+    ep.n_valid = MLP_KIN;
+    ep.out_f32 = n->dWtmp;
+    ep.ld_f32 = MLP_KIN;
+    rc = gemm_bf16_tn(n->dZT[cur], n->X0T, MLP_H, MLP_KIN, Bp, ep, n->status, n->stream);
+    if (rc) return rc;
+    mlp_gather_w1<<<(MLP_H * MLP_IN + 255) / 256, 256, 0, n->stream>>>(n->dWtmp, g + mlp_w_off(0));
+    mlp_rowsum<<<MLP_H / 4, 128, 0, n->stream>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(0));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mlp: backward");
+    n->have_grads = true;
+    return ST_OK;
+}
+
+static int check_status(st_mlp* n, const char* what) {
+    int32_t st_h = 0;
+    cudaError_t e = cudaMemcpyAsync(&st_h, n->status, sizeof(int32_t), cudaMemcpyDeviceToHost, n->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (st_h) {
+        set_error("%s: a tensor-core kernel reported status %d (bounded wait expired)", what, st_h);
+        return ST_ETIMEOUT;
+    }
+    return ST_OK;
+}
+
+// loss / gradient copies to the host (optional), then the status check
+static int finish_loss_grad(st_mlp* n, float* loss, float* grads, const char* what) {
+    if (!loss && !grads) return ST_OK;
+    double lh = 0.0;
+    cudaError_t e = cudaSuccess;
+    if (loss) e = cudaMemcpyAsync(&lh, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream);
+    if (e == cudaSuccess && grads)
+        e = cudaMemcpyAsync(grads, n->g, (size_t)MLP_PARAMS * 4, cudaMemcpyDeviceToHost, n->stream);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    int rc = check_status(n, what);
+    if (rc) return rc;
+    if (loss) *loss = (float)lh;
+    return ST_OK;
+}
+
+static int check_batch(st_mlp* n, const void* x, const void* t, int32_t B, const char* what) {
+    if (!n || !x || !t || B < 1 || B > n->max_batch) {
+        set_error("%s: null pointer or batch outside 1..max_batch", what);
+        return ST_EINVAL;
+    }
+    return ST_OK;
+}
+
+}  // namespace st
+
+using namespace st;
+
+extern "C" {
+
+int64_t st_mlp_param_count(void) { return MLP_PARAMS; }
+
+int st_mlp_destroy(st_mlp* n) {
+    if (!n) return ST_OK;
+    cudaStreamSynchronize(n->stream);
+    void* ptrs[] = {n->p,   n->m,   n->v,   n->g,   n->W1p, n->W2,  n->W3,   n->W4,      n->W5p,  n->W2T,
+                    n->W3T, n->W4T, n->W5Tp, n->X0, n->X0T, n->Y,   n->dYp,  n->dYT,     n->dWtmp, n->b5p,
+                    n->loss, n->status, n->d_terms, n->d_coef};
+    for (void* q : ptrs) cudaFree(q);
+    for (int l = 0; l < 4; ++l) {
+        cudaFree(n->A[l]);
+        cudaFree(n->AT[l]);
+        cudaFree(n->Z[l]);
+    }
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(n->dZ[k]);
+        cudaFree(n->dZT[k]);
+    }
+    if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
+    delete n;
+    return ST_OK;
+}
+
+int st_mlp_create(int32_t max_batch, void* cuda_stream, st_mlp** out) {
+    if (!out || max_batch < 1 || max_batch > (1 << 22)) {
+        set_error("st_mlp_create: need 1 <= max_batch <= 2^22");
+        return ST_EINVAL;
+    }
+    st_mlp* n = new (std::nothrow) st_mlp();
+    if (!n) {
+        set_error("st_mlp_create: host allocation failed");
+        return ST_ENOMEM;
+    }
+    const int Bp = ((max_batch + 127) / 128) * 128;
+    n->max_batch = Bp;
+    cudaError_t e = cudaSuccess;
+    if (cuda_stream) {
+        n->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete n;
+            return cuda_fail(e, "st_mlp_create: stream");
+        }
+        n->own_stream = true;
+    }
+    const size_t P = (size_t)MLP_PARAMS;
+    const size_t bf = sizeof(__nv_bfloat16);
+#define ST_MALLOC(ptr, bytes)                                                                                   \
+    e = cudaMalloc((void**)&(ptr), (bytes));                                                                    \
+    if (e != cudaSuccess) {                                                                                     \
+        st_mlp_destroy(n);                                                                                      \
+        set_error("st_mlp_create: cudaMalloc of %zu bytes failed: %s", (size_t)(bytes), cudaGetErrorString(e)); \
+        return ST_ENOMEM;                                                                                       \
+    }
+    ST_MALLOC(n->p, P * 4);
+    ST_MALLOC(n->m, P * 4);
+    ST_MALLOC(n->v, P * 4);
+    ST_MALLOC(n->g, P * 4);
+    ST_MALLOC(n->W1p, (size_t)MLP_H * MLP_KIN * bf);
+    ST_MALLOC(n->W2, (size_t)MLP_H * MLP_H * bf);
+    ST_MALLOC(n->W3, (size_t)MLP_H * MLP_H * bf);
+    ST_MALLOC(n->W4, (size_t)MLP_H * MLP_H * bf);
+    ST_MALLOC(n->W5p, (size_t)MLP_NOUT * MLP_H * bf);
+    ST_MALLOC(n->W2T, (size_t)MLP_H * MLP_H * bf);
+    ST_MALLOC(n->W3T, (size_t)MLP_H * MLP_H * bf);
+    ST_MALLOC(n->W4T, (size_t)MLP_H * MLP_H * bf);
+    ST_MALLOC(n->W5Tp, (size_t)MLP_H * MLP_KIN * bf);
+    ST_MALLOC(n->X0, (size_t)Bp * MLP_KIN * bf);
+    ST_MALLOC(n->X0T, (size_t)Bp * MLP_KIN * bf);
+    for (int l = 0; l < 4; ++l) {
+        ST_MALLOC(n->A[l], (size_t)Bp * MLP_H * bf);
+        ST_MALLOC(n->AT[l], (size_t)Bp * MLP_H * bf);
+        ST_MALLOC(n->Z[l], (size_t)Bp * MLP_H * 4);
+    }
+    ST_MALLOC(n->Y, (size_t)Bp * MLP_NOUT * 4);
+    ST_MALLOC(n->dYp, (size_t)Bp * MLP_KIN * bf);
+    ST_MALLOC(n->dYT, (size_t)Bp * MLP_NOUT * bf);
+    for (int k = 0; k < 2; ++k) {
+        ST_MALLOC(n->dZ[k], (size_t)Bp * MLP_H * bf);
+        ST_MALLOC(n->dZT[k], (size_t)Bp * MLP_H * bf);
+    }
+    ST_MALLOC(n->dWtmp, (size_t)MLP_H * MLP_KIN * 4);
+    ST_MALLOC(n->b5p, MLP_NOUT * 4);
+    ST_MALLOC(n->loss, sizeof(double));
+    ST_MALLOC(n->status, sizeof(int32_t));
+    ST_MALLOC(n->d_terms, sizeof(n->h_terms));
+    ST_MALLOC(n->d_coef, sizeof(n->h_coef));
+#undef ST_MALLOC
+    e = cudaMemset(n->p, 0, P * 4);
+    if (e == cudaSuccess) e = cudaMemset(n->m, 0, P * 4);
+    if (e == cudaSuccess) e = cudaMemset(n->v, 0, P * 4);
+    if (e == cudaSuccess) e = cudaMemset(n->g, 0, P * 4);
+    if (e == cudaSuccess) e = cudaMemset(n->status, 0, sizeof(int32_t));
+    if (e != cudaSuccess) {
+        st_mlp_destroy(n);
+        return cuda_fail(e, "st_mlp_create: init");
+    }
+    // head: q0 = 1, no polynomial, s = 1, unit input scales
+    memset(n->h_coef, 0, sizeof(n->h_coef));
+    memset(&n->head, 0, sizeof(n->head));
+    n->degree = 1;
+    n->head.n_terms = build_terms(1, n->h_terms);
+    n->head.q0[0] = 1.0;
+    for (int k = 0; k < 4; ++k) n->head.scale[k] = 1.0;
+    for (int c = 0; c < MLP_IN; ++c) {
+        n->head.in_scale[c] = 1.0;
+        n->in_scale.s[c] = 1.0f;
+    }
+    n->head.terms = n->d_terms;
+    n->head.coef = n->d_coef;
+    int rc = upload_head(n);
+    if (rc == ST_OK) rc = mlp_refresh_weights(n);
+    if (rc) {
+        st_mlp_destroy(n);
+        return rc;
+    }
+    *out = n;
+    return ST_OK;
+}
+
+int st_mlp_set_params(st_mlp* n, const float* params) {
+    if (!n || !params) {
+        set_error("st_mlp_set_params: null pointer");
+        return ST_EINVAL;
+    }
+    cudaError_t e = cudaMemcpyAsync(n->p, params, (size_t)MLP_PARAMS * 4, cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, (size_t)MLP_PARAMS * 4, n->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, (size_t)MLP_PARAMS * 4, n->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "st_mlp_set_params");
+    n->step = 0;
+    int rc = mlp_refresh_weights(n);
+    if (rc) return rc;
+    e = cudaStreamSynchronize(n->stream);
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "st_mlp_set_params: sync");
+}
+
+int st_mlp_get_params(st_mlp* n, float* params) {
+    if (!n || !params) {
+        set_error("st_mlp_get_params: null pointer");
+        return ST_EINVAL;
+    }
+    cudaError_t e = cudaMemcpyAsync(params, n->p, (size_t)MLP_PARAMS * 4, cudaMemcpyDeviceToHost, n->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "st_mlp_get_params");
+}
+
+int st_mlp_set_head(st_mlp* n, const double* q0, const double* lin, double out_scale, const double* in_scale) {
+    if (!n || !q0 || !in_scale || !(out_scale > 0.0)) {
+        set_error("st_mlp_set_head: null pointer or out_scale <= 0");
+        return ST_EINVAL;
+    }
+    for (int c = 0; c < MLP_IN; ++c)
+        if (!(in_scale[c] >= 0.0) || !std::isfinite(in_scale[c])) {
+            set_error("st_mlp_set_head: input scales must be finite and >= 0");
+            return ST_EINVAL;
+        }
+    memset(n->h_coef, 0, sizeof(n->h_coef));
+    n->degree = 1;
+    n->head.n_terms = build_terms(1, n->h_terms);
+    for (int k = 0; k < 4; ++k) {
+        n->head.q0[k] = q0[k];
+        for (int c = 0; c < MLP_IN; ++c) n->h_coef[k][1 + c] = lin ? lin[k * MLP_IN + c] : 0.0;
+    }
+    for (int k = 0; k < 4; ++k) n->head.scale[k] = out_scale;
+    for (int c = 0; c < MLP_IN; ++c) {
+        n->head.in_scale[c] = in_scale[c];
+        n->in_scale.s[c] = (float)in_scale[c];
+    }
+    return upload_head(n);
+}
+
+int st_mlp_set_scale(st_mlp* n, const double* out_scale) {
+    if (!n || !out_scale) {
+        set_error("st_mlp_set_scale: null pointer");
+        return ST_EINVAL;
+    }
+    for (int k = 0; k < 4; ++k)
+        if (!(out_scale[k] > 0.0) || !std::isfinite(out_scale[k])) {
+            set_error("st_mlp_set_scale: need finite output scales > 0");
+            return ST_EINVAL;
+        }
+    for (int k = 0; k < 4; ++k) n->head.scale[k] = out_scale[k];
+    return ST_OK;
+}
+
+int st_mlp_fit_head(st_mlp* nw, int32_t degree, const double* z_soa, const double* q_soa, const uint8_t* lost,
+                    int64_t n, double* coef_out, double* rms_out) {
+    if (!nw || !z_soa || !q_soa || n < 1 || degree < 0 || degree > POLY_MAX_DEG) {
+        set_error("st_mlp_fit_head: null pointer, n < 1 or degree outside 0..3");
+        return ST_EINVAL;
+    }
+    uint8_t terms[POLY_MAX][3];
+    const int F = build_terms(degree, terms);
+    // table of products: f_a f_b (a <= b), f_a e_k, e_k e_k
+    static_assert(POLY_MAX * (POLY_MAX + 1) / 2 + 4 * POLY_MAX + 4 <= FIT_THREADS * FIT_PER_THREAD, "fit table");
+    uint8_t pa[FIT_THREADS * FIT_PER_THREAD], pb[FIT_THREADS * FIT_PER_THREAD];
+    int T = 0;
+    for (int a = 0; a < F; ++a)
+        for (int b = a; b < F; ++b, ++T) {
+            pa[T] = (uint8_t)a;
+            pb[T] = (uint8_t)b;
+        }
+    const int h_off = T;
+    for (int a = 0; a < F; ++a)
+        for (int k = 0; k < 4; ++k, ++T) {
+            pa[T] = (uint8_t)a;
+            pb[T] = (uint8_t)(F + k);
+        }
+    const int r_off = T;
+    for (int k = 0; k < 4; ++k, ++T) pa[T] = pb[T] = (uint8_t)(F + k);
+
+    memcpy(nw->h_terms, terms, sizeof(terms));
+    nw->head.n_terms = F;
+    int rc = upload_head(nw);   // the kernel reads the new monomial table
+    if (rc) return rc;
+    uint8_t* d_tab = nullptr;
+    double* d_mom = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&d_tab, 2 * (size_t)T, nw->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_mom, (size_t)T * sizeof(double), nw->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, pa, T, cudaMemcpyHostToDevice, nw->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab + T, pb, T, cudaMemcpyHostToDevice, nw->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_mom, 0, (size_t)T * sizeof(double), nw->stream);
+    std::vector<double> mom(FIT_THREADS * FIT_PER_THREAD, 0.0);
+    if (e == cudaSuccess) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int64_t blocks = (n + FIT_ROWS - 1) / FIT_ROWS;
+        if (blocks > 4 * sms) blocks = 4 * sms;
+        mlp_fit_moments<<<(unsigned)blocks, FIT_THREADS, 0, nw->stream>>>(z_soa, q_soa, lost, n, nw->head, d_tab,
+                                                                         d_tab + T, T, d_mom);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mom.data(), d_mom, (size_t)T * sizeof(double), cudaMemcpyDeviceToHost, nw->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nw->stream);
+    cudaFreeAsync(d_tab, nw->stream);
+    cudaFreeAsync(d_mom, nw->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "st_mlp_fit_head");
+
+    // Normal equations over the monomials with nonzero sum of squares (an
+    // input scale of 0 removes every monomial of its coordinate), solved by
+    // Cholesky in FP64.
+    std::vector<double> Gv((size_t)F * F), Cv((size_t)F * F, 0.0);
+    auto G = [&](int a, int b) -> double& { return Gv[(size_t)a * F + b]; };
+    auto C = [&](int a, int b) -> double& { return Cv[(size_t)a * F + b]; };
+    int t = 0;
+    for (int a = 0; a < F; ++a)
+        for (int b = a; b < F; ++b, ++t) G(a, b) = G(b, a) = mom[t];
+    int idx[POLY_MAX], m = 0;
+    for (int a = 0; a < F; ++a)
+        if (G(a, a) > 0.0) idx[m++] = a;
+    for (int a = 0; a < m; ++a) {
+        for (int b = 0; b <= a; ++b) {
+            double s = G(idx[a], idx[b]);
+            for (int c = 0; c < b; ++c) s -= C(a, c) * C(b, c);
+            if (a == b) {
+                if (!(s > 1e-300)) {
+                    set_error("st_mlp_fit_head: singular normal equations (too few distinct pairs?)");
+                    return ST_EINVAL;
+                }
+                C(a, a) = sqrt(s);
+            } else {
+                C(a, b) = s / C(b, b);
+            }
+        }
+    }
+    const double count = G(0, 0);
+    double coef[4][POLY_MAX];
+    memset(coef, 0, sizeof(coef));
+    for (int k = 0; k < 4; ++k) {
+        double y[POLY_MAX], sol[POLY_MAX];
+        for (int a = 0; a < m; ++a) {
+            double s = mom[h_off + idx[a] * 4 + k];
+            for (int c = 0; c < a; ++c) s -= C(a, c) * y[c];
+            y[a] = s / C(a, a);
+        }
+        for (int a = m - 1; a >= 0; --a) {
+            double s = y[a];
+            for (int c = a + 1; c < m; ++c) s -= C(c, a) * sol[c];
+            sol[a] = s / C(a, a);
+        }
+        double rss = mom[r_off + k];
+        for (int a = 0; a < m; ++a) {
+            coef[k][idx[a]] = sol[a];
+            rss -= sol[a] * mom[h_off + idx[a] * 4 + k];
+        }
+        if (rms_out) rms_out[k] = sqrt(rss > 0.0 ? rss / count : 0.0);
+    }
+    memset(nw->h_coef, 0, sizeof(nw->h_coef));
+    for (int k = 0; k < 4; ++k)
+        for (int f = 0; f < F; ++f) {
+            nw->h_coef[k][f] = coef[k][f];
+            if (coef_out) coef_out[k * F + f] = coef[k][f];
+        }
+    nw->degree = degree;
+    return upload_head(nw);
+}
+
+int st_mlp_make_targets(st_mlp* nw, const double* z_soa, const double* q_soa, int64_t n, float* x_rows,
+                        float* r_rows) {
+    if (!nw || !z_soa || !q_soa || !x_rows || !r_rows || n < 1) {
+        set_error("st_mlp_make_targets: null pointer or n < 1");
+        return ST_EINVAL;
+    }
+    mlp_make_targets<<<(unsigned)((n + 255) / 256), 256, 0, nw->stream>>>(z_soa, q_soa, n, nw->head, x_rows, r_rows);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "st_mlp_make_targets");
+}
+
+int st_mlp_forward(st_mlp* n, const float* x, int32_t B, float* q_out) {
+    int rc = check_batch(n, x, q_out, B, "st_mlp_forward");
+    if (rc) return rc;
+    const int Bp = ((B + 127) / 128) * 128;
+    mlp_pack_x<<<(Bp + 127) / 128, 128, 0, n->stream>>>(x, B, Bp, n->in_scale, n->X0, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "st_mlp_forward: pack");
+    rc = mlp_forward_layers(n, Bp, false);
+    if (rc) return rc;
+    mlp_head_quat<<<(Bp + 127) / 128, 128, 0, n->stream>>>(n->Y, x, B, Bp, n->head, nullptr, q_out, nullptr, nullptr,
+                                                           nullptr);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "st_mlp_forward: head");
+}
+
+int st_mlp_loss_grad(st_mlp* n, const float* x, const float* q_target, int32_t B, float* loss, float* grads) {
+    int rc = check_batch(n, x, q_target, B, "st_mlp_loss_grad");
+    if (rc) return rc;
+    const int Bp = ((B + 127) / 128) * 128;
+    cudaError_t e = cudaMemsetAsync(n->loss, 0, sizeof(double), n->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "st_mlp_loss_grad: reset");
+    mlp_pack_x<<<(Bp + 127) / 128, 128, 0, n->stream>>>(x, B, Bp, n->in_scale, n->X0, n->X0T);
+    rc = mlp_forward_layers(n, Bp, true);
+    if (rc) return rc;
+    mlp_head_quat<<<(Bp + 127) / 128, 128, 0, n->stream>>>(n->Y, x, B, Bp, n->head, q_target, nullptr, n->loss,
+                                                           n->dYp, n->dYT);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "st_mlp_loss_grad: head");
+    rc = mlp_backward(n, Bp);
+    if (rc) return rc;
+    return finish_loss_grad(n, loss, grads, "st_mlp_loss_grad");
+}
+
+int st_mlp_loss_grad_residual(st_mlp* n, const float* x, const float* r_target, int32_t B, float* loss,
+                              float* grads) {
+    int rc = check_batch(n, x, r_target, B, "st_mlp_loss_grad_residual");
+    if (rc) return rc;
+    const int Bp = ((B + 127) / 128) * 128;
+    cudaError_t e = cudaMemsetAsync(n->loss, 0, sizeof(double), n->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "st_mlp_loss_grad_residual: reset");
+    mlp_pack_x<<<(Bp + 127) / 128, 128, 0, n->stream>>>(x, B, Bp, n->in_scale, n->X0, n->X0T);
+    rc = mlp_forward_layers(n, Bp, true);
+    if (rc) return rc;
+    mlp_head_resid<<<(Bp + 127) / 128, 128, 0, n->stream>>>(n->Y, r_target, B, Bp, n->loss, n->dYp, n->dYT);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "st_mlp_loss_grad_residual: head");
+    rc = mlp_backward(n, Bp);
+    if (rc) return rc;
+    return finish_loss_grad(n, loss, grads, "st_mlp_loss_grad_residual");
+}
+
+int st_mlp_adam_step(st_mlp* n, float lr, float beta1, float beta2, float eps) {
+    if (!n || !n->have_grads || !(lr > 0.0f)) {
+        set_error("st_mlp_adam_step: no gradients or lr <= 0");
+        return ST_EINVAL;
+    }
+    n->step += 1;
+    const float c1 = 1.0f / (1.0f - powf(beta1, (float)n->step));
+    const float c2 = 1.0f / (1.0f - powf(beta2, (float)n->step));
+    const int64_t P = MLP_PARAMS;
+    mlp_adam<<<(unsigned)((P + 255) / 256), 256, 0, n->stream>>>(n->p, n->m, n->v, n->g, P, lr, beta1, beta2, eps, c1,
+                                                                 c2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "st_mlp_adam_step");
+    return mlp_refresh_weights(n);
+}
+
+int st_track_surrogate(st_ctx* ctx, st_mlp* n, int32_t n_turns, double* spin_sum) {
+    if (!ctx || !n) {
+        set_error("st_track_surrogate: null pointer");
+        return ST_EINVAL;
+    }
+    if (!ctx->uploaded) {
+        set_error("st_track_surrogate: no particles uploaded");
+        return ST_ESTATE;
+    }
+    if (n_turns < 0 || ctx->n > n->max_batch || ctx->precision != ST_FP64) {
+        set_error("st_track_surrogate: need n_turns >= 0, n_particles <= the network's max_batch, FP64 context");
+        return ST_EINVAL;
+    }
+    const int B = (int)ctx->n;
+    const int Bp = ((B + 127) / 128) * 128;
+    // the network runs on the context's stream
+    cudaStream_t keep = n->stream;
+    n->stream = ctx->stream;
+    int rc = ST_OK;
+    cudaError_t e = cudaMemsetAsync(n->status, 0, sizeof(int32_t), n->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "st_track_surrogate: status");
+    for (int t = 0; t < n_turns && rc == ST_OK; ++t) {
+        // one-turn map from the orbit at the fixed azimuth (start of the turn)
+        mlp_pack_state<<<(Bp + 127) / 128, 128, 0, n->stream>>>(ctx->xpx, ctx->ypy, ctx->tpt, B, Bp, n->head, n->X0);
+        rc = mlp_forward_layers(n, Bp, false);
+        if (rc) break;
+        surrogate_apply<<<(B + 127) / 128, 128, 0, n->stream>>>(n->Y, B, n->head, ctx->xpx, ctx->ypy, ctx->tpt,
+                                                                ctx->sxy, ctx->sz, ctx->lost, spin_sum);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "st_track_surrogate: spin step");
+            break;
+        }
+        rc = launch_track_orbit(ctx, 1);
+    }
+    n->stream = keep;
+    return rc;
+}
+
+}  // extern "C"

@@ -45,6 +45,11 @@ struct GemmEpi {
 
 enum { STATUS_MMA_TIMEOUT = 2 };
 
+// D = A B^T with the epilogue (host launcher, gemm.cu); M % 128 == 0,
+// K % 64 == 0, N % 16 == 0.
+int gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const GemmEpi& epi, int32_t* status,
+                 cudaStream_t stream);
+
 // ---- tcgen05 / TMA primitives ---------------------------------------------
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)

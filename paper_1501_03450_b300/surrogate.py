@@ -6,19 +6,21 @@ The map sends a particle's orbit z = (X, Px, Y, Py, T, Pt) at the start of the
 lattice (the fixed azimuth s = 0) to the unit quaternion of its spin rotation
 over one turn (the composed element rotations of Sec. 4, Eqs. (37)-(39)):
 
-    q(z) = normalise(q0 + L x + s y(x)),   x = in_scale * z,
+    q(z) = normalise(q0 + P(x) + s y(x)),   x = in_scale * z,
 
-q0 the one-turn quaternion of the on-axis particle, L a linear term fitted in
-FP64 on the tracked pairs, y the 6 -> 256 x 4 -> 4 SiLU network (bf16 weights
-and activations, FP32 accumulation) and s an output scale.  T enters with
+q0 the one-turn quaternion of the on-axis particle, P a polynomial (degree
+<= 3) fitted by FP64 least squares on the tracked pairs, y the 6 -> 256 x 4 ->
+4 SiLU network (bf16 weights and activations, FP32 accumulation) trained on
+the residual (q - q0 - P(x)) / s, and s the residual's RMS.  T enters with
 scale 0: no element of these rings depends on the arrival time (no RF), so the
 one-turn map does not depend on T.
 
-Every per-sample step runs in the CUDA library (pair tracking, layout, the
-linear fit's moments, forward, backward, Adam, the surrogate turn loop).  The
-host does the bookkeeping: the 4x4 linear optics of the sampling domain from
-a handful of tracked particles, the input generator, the batch schedule.
-PyTorch provides device memory and the stream.
+Every per-sample step runs in the CUDA library (pair tracking, the fit's
+moments, the residual targets, forward, backward, Adam, the surrogate turn
+loop).  The host does the bookkeeping: the 4x4 linear optics of the sampling
+domain from a handful of tracked particles, the input generator, the normal
+equations of the fit (inside the library), the batch schedule.  PyTorch
+provides device memory and the stream.
 """
 from __future__ import annotations
 
@@ -28,8 +30,7 @@ from typing import Dict, Optional
 import numpy as np
 import torch
 
-from . import (MLP, Lattice, Tracker, st_mlp_pack_pairs, st_track_average, st_track_one_turn_map,
-               st_track_surrogate)
+from . import MLP, Lattice, Tracker, st_track_average, st_track_one_turn_map, st_track_surrogate
 
 LAYERS = [(256, 6), (256, 256), (256, 256), (256, 256), (4, 256)]
 
@@ -87,8 +88,9 @@ class SpinMapSurrogate:
         self.q0 = self.closed_orbit_quaternion()
         self.optics = None
         self.in_scale = None
-        self.lin = None
-        self.out_scale = 1.0
+        self.coef = None
+        self.degree = None
+        self.out_scale = np.ones(4)
         self.history = []
 
     # ---------------------------------------------------------------- tracking
@@ -185,89 +187,128 @@ class SpinMapSurrogate:
                                    bounds["x"], bounds["y"], pt_max)
 
     def make_pairs(self, n: int, sigmas: Dict, cut: float = 3.0, margin: float = 1.1, seed: int = None):
-        """Tracks the training orbits one turn (FP64, spin order of the
-        surrogate) and keeps (z, q) on the device: z64 [6, n], q64 [4, n] and
-        the network's rows x [n, 6], q [n, 4] (float)."""
+        """Tracks the training orbits one turn (FP64, the surrogate's spin
+        order) and keeps the pairs on the device: z64 [6, n] (orbit at s = 0)
+        and q64 [4, n] (its one-turn quaternion in q0's hemisphere)."""
         z = self.training_points(n, sigmas, cut, margin, seed)
         tr = self._tracker(n)
         try:
             with torch.cuda.stream(self.stream):
-                z64 = torch.from_numpy(z).to("cuda", non_blocking=False)
+                z64 = torch.from_numpy(z).to("cuda")
                 q64 = torch.empty((4, n), dtype=torch.float64, device="cuda")
-                lost = torch.zeros(n, dtype=torch.uint8, device="cuda")
-                x_rows = torch.empty((n, 6), dtype=torch.float32, device="cuda")
-                q_rows = torch.empty((n, 4), dtype=torch.float32, device="cuda")
-                s_dummy = torch.empty((3, n), dtype=torch.float64, device="cuda")
+                lost = torch.empty(n, dtype=torch.uint8, device="cuda")
+                s_out = torch.empty((3, n), dtype=torch.float64, device="cuda")
             S = np.zeros((3, n))
             S[1] = 1.0
             tr.upload(z, S)
             st_track_one_turn_map(tr.handle, self.spin_order, self.q0, _ptr(q64))
-            tr.download_device(_ptr(s_dummy), None, _ptr(lost))
-            st_mlp_pack_pairs(_ptr(z64), _ptr(q64), n, _ptr(x_rows), _ptr(q_rows), self.sp)
+            tr.download_device(_ptr(s_out), None, _ptr(lost))
             self.stream.synchronize()
         finally:
             tr.close()
-        n_lost = int(lost.sum().item())
+        n_lost = int(lost.cpu().numpy().sum())
         if n_lost:
             raise RuntimeError(f"make_pairs: {n_lost} training orbits were lost in one turn")
-        self.pairs = dict(z64=z64, q64=q64, x=x_rows, q=q_rows, n=n, lost=lost)
-        return self.pairs
+        return dict(z=z, z64=z64, q64=q64, lost=lost, n=n)
 
-    def fit_head(self, in_scale=None):
-        """Input scales (1 / RMS of each coordinate over the pairs, 0 for T),
-        the FP64 linear term L, and the output scale s (RMS of the residual
-        q - q0 - L x over a sample)."""
-        P = self.pairs
-        z = P["z64"]
+    def make_pairs_from_orbits(self, z0: np.ndarray, n_turns: int, S0: Optional[np.ndarray] = None):
+        """Pairs along tracked orbits: the ensemble z0 [6, m] is tracked for
+        n_turns (FP64) and every turn contributes (z at s = 0, one-turn
+        quaternion) for every particle, so that the pairs sample the region
+        of phase space the orbits of such an ensemble visit.  Pairs are
+        ordered turn by turn; m * n_turns in all."""
+        m = z0.shape[1]
+        n = m * int(n_turns)
+        tr = self._tracker(m)
+        try:
+            with torch.cuda.stream(self.stream):
+                z64 = torch.empty((6, n), dtype=torch.float64, device="cuda")
+                q64 = torch.empty((4, n), dtype=torch.float64, device="cuda")
+                zt = torch.empty((6, m), dtype=torch.float64, device="cuda")
+                qt = torch.empty((4, m), dtype=torch.float64, device="cuda")
+                st_ = torch.empty((3, m), dtype=torch.float64, device="cuda")
+                lost = torch.empty(m, dtype=torch.uint8, device="cuda")
+            S = np.zeros((3, m))
+            S[1] = 1.0
+            tr.upload(z0, S if S0 is None else S0)
+            for t in range(int(n_turns)):
+                tr.download_device(_ptr(st_), _ptr(zt), None)
+                st_track_one_turn_map(tr.handle, self.spin_order, self.q0, _ptr(qt))
+                with torch.cuda.stream(self.stream):
+                    z64[:, t * m:(t + 1) * m].copy_(zt)
+                    q64[:, t * m:(t + 1) * m].copy_(qt)
+            tr.download_device(_ptr(st_), None, _ptr(lost))
+            self.stream.synchronize()
+        finally:
+            tr.close()
+        n_lost = int(lost.cpu().numpy().sum())
+        if n_lost:
+            raise RuntimeError(f"make_pairs_from_orbits: {n_lost} orbits were lost")
+        return dict(z=z64.cpu().numpy(), z64=z64, q64=q64, lost=torch.zeros(n, dtype=torch.uint8, device="cuda"),
+                    n=n)
+
+    def fit_head(self, pairs: Dict, degree: int = 3, in_scale=None):
+        """Input scales (1 / RMS of each coordinate over the pairs; 0 for T),
+        the FP64 least-squares polynomial P of the given degree, and the output
+        scales s_k = RMS of each component of the residual q - q0 - P(x), so
+        that the network's targets are O(1) in every component."""
         if in_scale is None:
-            rms = torch.sqrt(torch.mean(z * z, dim=1)).cpu().numpy()
+            rms = np.sqrt(np.mean(pairs["z"] ** 2, axis=1))
             in_scale = np.where(rms > 0, 1.0 / np.where(rms > 0, rms, 1.0), 0.0)
             in_scale[4] = 0.0
         self.in_scale = np.asarray(in_scale, dtype=np.float64)
+        self.degree = int(degree)
         self.mlp.set_head(self.q0, None, 1.0, self.in_scale)
-        self.lin = self.mlp.fit_linear(_ptr(z), _ptr(P["q64"]), P["n"], _ptr(P["lost"]))
-        m = min(P["n"], 16384)
-        zs = z[:, :m].cpu().numpy() * self.in_scale[:, None]
-        r = P["q64"][:, :m].cpu().numpy() - self.q0[:, None] - self.lin @ zs
-        self.out_scale = float(np.sqrt(np.mean(r * r)) * 2.0) or 1.0
-        self.mlp.set_head(self.q0, self.lin, self.out_scale, self.in_scale)
-        return self.in_scale, self.lin, self.out_scale
+        self.coef, self.fit_rms = self.mlp.fit_head(self.degree, _ptr(pairs["z64"]), _ptr(pairs["q64"]),
+                                                    pairs["n"], _ptr(pairs["lost"]))
+        self.out_scale = np.where(self.fit_rms > 0, self.fit_rms, 1.0)
+        self.mlp.set_scale(self.out_scale)
+        return self.in_scale, self.coef, self.out_scale
 
-    def train(self, steps: int, batch: int = 16384, lr: float = 1e-3, lr_final: float = 1e-5,
-              log_every: int = 200, init_seed: int = None, warmup: int = 100):
-        """Adam on mean |q - q_t|^2 over contiguous batches of the (randomly
-        ordered) pairs; the learning rate decays as a cosine from lr to lr_final."""
-        P = self.pairs
-        n = P["n"]
+    def targets(self, pairs: Dict):
+        """The network's training rows for the pairs with the current head:
+        x [n, 6] (float orbit) and r [n, 4] = (q - q0 - P(x)) / s."""
+        n = pairs["n"]
+        with torch.cuda.stream(self.stream):
+            x = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+            r = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        self.mlp.make_targets(_ptr(pairs["z64"]), _ptr(pairs["q64"]), n, _ptr(x), _ptr(r))
+        self.stream.synchronize()
+        return x, r
+
+    def train(self, x: torch.Tensor, r: torch.Tensor, steps: int, batch: int = 16384, lr: float = 1e-3,
+              lr_final: float = 1e-6, log_every: int = 500, init_seed: int = None, warmup: int = 200):
+        """Adam on the residual regression mean |y - r|^2 over contiguous
+        batches of the (randomly ordered) rows; the learning rate warms up
+        linearly and then decays as a cosine from lr to lr_final."""
+        n = x.shape[0]
         batch = min(int(batch), self.max_batch, n)
         self.mlp.set_params(init_params(self.seed if init_seed is None else init_seed))
         rng = np.random.default_rng(self.seed + 1)
-        start = int(rng.integers(0, batch))
-        xb, qb = P["x"], P["q"]
+        start = int(rng.integers(0, n - batch + 1))
         for k in range(steps):
             if start + batch > n:
-                start = int(rng.integers(0, batch))
-            xp = _ptr(xb) + start * 6 * 4
-            qp = _ptr(qb) + start * 4 * 4
+                start = int(rng.integers(0, batch)) if n >= 2 * batch else 0
+            xp = _ptr(x) + start * 6 * 4
+            rp = _ptr(r) + start * 4 * 4
             start += batch
-            if log_every and (k % log_every == 0 or k == steps - 1):
-                loss, _ = self.mlp.loss_grad(xp, qp, batch)
+            log = bool(log_every) and (k % log_every == 0 or k == steps - 1)
+            loss, _ = self.mlp.loss_grad_residual(xp, rp, batch, want_loss=log)
+            if log:
                 self.history.append((k, loss))
-            else:
-                self.mlp.loss_grad_async(xp, qp, batch)
             f = min(1.0, (k + 1) / warmup) if warmup else 1.0
             c = 0.5 * (1 + math.cos(math.pi * k / max(1, steps - 1)))
             self.mlp.adam_step(f * (lr_final + (lr - lr_final) * c))
         self.stream.synchronize()
         return self.history
 
-    def eval_loss(self, x: torch.Tensor, q: torch.Tensor) -> float:
-        """Mean |q - q_t|^2 of the current network over the given rows."""
+    def eval_loss(self, x: torch.Tensor, r: torch.Tensor) -> float:
+        """Mean |y - r|^2 of the current network over the given rows."""
         n = x.shape[0]
         tot, k = 0.0, 0
         while k < n:
             b = min(self.max_batch, n - k)
-            loss, _ = self.mlp.loss_grad(_ptr(x) + k * 24, _ptr(q) + k * 16, b)
+            loss, _ = self.mlp.loss_grad_residual(_ptr(x) + k * 24, _ptr(r) + k * 16, b)
             tot += loss * b
             k += b
         return tot / n

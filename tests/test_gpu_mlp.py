@@ -17,6 +17,21 @@ from test_oracle_mlp import random_params
 
 pytestmark = pytest.mark.gpu
 
+
+@pytest.fixture(autouse=True)
+def side_stream():
+    """Every test runs on one non-default stream shared by torch's copies and
+    the library calls, so that their order is the program order."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        yield s
+    s.synchronize()
+
+
+def cur():
+    return torch.cuda.current_stream().cuda_stream
+
+
 IN_SCALE = np.array([1e3, 1e4, 1e3, 1e4, 0.0, 1e3])
 
 
@@ -34,7 +49,7 @@ def unit(v):
 
 
 def make_net(p, head, max_batch=4096):
-    net = st.MLP(max_batch, torch.cuda.current_stream().cuda_stream)
+    net = st.MLP(max_batch, cur())
     net.set_params(p.astype(np.float32))
     net.set_head(head["q0"], head["lin"], head["scale"], head["in_scale"])
     return net
@@ -50,22 +65,19 @@ def head_for(seed, scale=0.05, lin=True):
                 scale=scale, in_scale=IN_SCALE)
 
 
-def f32_head(h):
-    """The head as the kernels hold it (float)."""
-    return dict(q0=h["q0"].astype(np.float32).astype(np.float64),
-                lin=None if h["lin"] is None else h["lin"].astype(np.float32).astype(np.float64),
-                scale=float(np.float32(h["scale"])), in_scale=h["in_scale"].astype(np.float32).astype(np.float64))
 
 
 @pytest.mark.parametrize("B", [1, 128, 300, 2048])
 def test_forward_matches_reference(B):
-    """Inference against the reference with the weights, scaled inputs and
-    activations rounded to bf16.  The kernels accumulate in FP32 and round
-    FP32 sums to bf16, the reference FP64 sums: a rounding decision differs
-    only when the two sums straddle a bf16 rounding boundary, which moves one
-    activation by one bf16 step (2^-8 relative); over the 256-wide layers that
-    bounds |dy| well below 1e-3 |y| and |dq| below 1e-3 s.  Without the bf16
-    emulation the difference is an order of magnitude larger."""
+    """Inference against the reference with the weights and activations
+    rounded to bf16 and the input split into bf16 hi + lo.  The kernels
+    accumulate in FP32 and round FP32 sums to bf16, the reference rounds FP64
+    sums: a rounding decision differs only where the two sums straddle a bf16
+    rounding boundary (probability ~ 2^-24 sqrt(256) / 2^-8 per activation),
+    which moves that activation by one bf16 step (2^-8 relative) and the next
+    layer's sums by |w| 2^-8 |a|.  Rows hit by such flips differ by up to about
+    one bf16 step of y (|dq| <= 1e-2 s), the average row far less; without the
+    bf16 emulation every row differs by ~2^-9 |y|."""
     p = random_params(21, last_scale=1.0)
     h = head_for(3)
     x = rand_x(B, 4)
@@ -73,15 +85,16 @@ def test_forward_matches_reference(B):
     xd = dev(x, np.float32)
     q = torch.empty((B, 4), dtype=torch.float32, device="cuda")
     net.forward(xd.data_ptr(), B, q.data_ptr())
-    qg = q.cpu().numpy().astype(np.float64)
+    qg = q.cpu().numpy().astype(np.float64)        # same stream: ordered after the forward pass
     x32 = x.astype(np.float32).astype(np.float64)
-    qo, _ = M.forward(f32_params(p), x32, f32_head(h), bf16=True)
+    qo, _ = M.forward(f32_params(p), x32, h, bf16=True)
     qf, _ = M.forward(p, x, h, bf16=False)
-    err = np.abs(qg - qo).max()
-    assert err < 1e-3 * h["scale"], err
+    err = np.abs(qg - qo)
+    assert err.max() < 1e-2 * h["scale"], err.max()
+    assert err.mean() < 5e-4 * h["scale"], err.mean()
     assert np.abs(np.linalg.norm(qg, axis=1) - 1).max() < 1e-6
     if B >= 128:
-        assert err < 0.2 * np.abs(qg - qf).max()
+        assert err.mean() < 0.2 * np.abs(qg - qf).mean()
     net.close()
 
 
@@ -94,14 +107,15 @@ def test_loss_and_gradient_match_reference():
     p = random_params(7, last_scale=1.0)
     h = head_for(5)
     x = rand_x(B, 8)
-    qo, _ = M.forward(f32_params(p), x, f32_head(h), bf16=True)
+    qo, _ = M.forward(f32_params(p), x.astype(np.float32).astype(np.float64), h, bf16=True)
     rng = np.random.default_rng(9)
     qt = unit(qo + 0.02 * rng.standard_normal(qo.shape))
     net = make_net(p, h)
-    loss, g = net.loss_grad(dev(x, np.float32).data_ptr(), dev(qt, np.float32).data_ptr(), B, want_grads=True)
+    xd, qd = dev(x, np.float32), dev(qt, np.float32)      # held: the library reads them
+    loss, g = net.loss_grad(xd.data_ptr(), qd.data_ptr(), B, want_grads=True)
     x32 = x.astype(np.float32).astype(np.float64)
     qt32 = qt.astype(np.float32).astype(np.float64)
-    lo, go = M.loss_grad(f32_params(p), x32, qt32, f32_head(h), bf16=True)
+    lo, go = M.loss_grad(f32_params(p), x32, qt32, h, bf16=True)
     assert loss == pytest.approx(lo, rel=2e-3)
     offs = np.cumsum([0] + [r * c + r for r, c in M.LAYERS])
     for l, (r, c) in enumerate(M.LAYERS):
@@ -143,7 +157,7 @@ def test_training_reduces_loss_on_a_smooth_map():
     A = rng.standard_normal((4, 6)) * IN_SCALE
     q0 = unit(np.array([0.1, 0.2, 0.9, 0.1]))
     qt = unit(q0 + 0.01 * np.sin(x @ A.T))
-    net = st.MLP(B, torch.cuda.current_stream().cuda_stream)
+    net = st.MLP(B, cur())
     from paper_1501_03450_b300.surrogate import init_params
     net.set_params(init_params(1).astype(np.float32))
     net.set_head(q0, None, 0.01, IN_SCALE)
@@ -157,44 +171,73 @@ def test_training_reduces_loss_on_a_smooth_map():
     net.close()
 
 
-def test_pack_pairs_layout():
-    n = 777
-    rng = np.random.default_rng(4)
-    z = rng.standard_normal((6, n))
-    q = rng.standard_normal((4, n))
-    x_rows = torch.empty((n, 6), dtype=torch.float32, device="cuda")
-    q_rows = torch.empty((n, 4), dtype=torch.float32, device="cuda")
-    st.st_mlp_pack_pairs(dev(z, np.float64).data_ptr(), dev(q, np.float64).data_ptr(), n, x_rows.data_ptr(),
-                         q_rows.data_ptr(), torch.cuda.current_stream().cuda_stream)
-    torch.cuda.synchronize()
-    np.testing.assert_array_equal(x_rows.cpu().numpy(), z.T.astype(np.float32))
-    np.testing.assert_array_equal(q_rows.cpu().numpy(), q.T.astype(np.float32))
+def test_residual_loss_and_gradient_match_reference():
+    B = 700
+    p = random_params(8, last_scale=1.0)
+    x = rand_x(B, 2)
+    r = np.random.default_rng(4).standard_normal((B, 4))
+    net = make_net(p, head_for(1))
+    xd, rd = dev(x, np.float32), dev(r, np.float32)
+    loss, g = net.loss_grad_residual(xd.data_ptr(), rd.data_ptr(), B, want_grads=True)
+    x32 = x.astype(np.float32).astype(np.float64)
+    r32 = r.astype(np.float32).astype(np.float64)
+    lo, go = M.residual_loss_grad(f32_params(p), x32, r32, IN_SCALE, bf16=True)
+    assert loss == pytest.approx(lo, rel=2e-3)
+    offs = np.cumsum([0] + [a * b + a for a, b in M.LAYERS])
+    for l, (a, b) in enumerate(M.LAYERS):
+        gg, gr = g[offs[l]:offs[l + 1]].astype(np.float64), go[offs[l]:offs[l + 1]]
+        assert np.linalg.norm(gg - gr) / np.linalg.norm(gr) < 2e-2, l
+    net.close()
 
 
-def test_fit_linear_is_least_squares():
-    """The FP64 head fit against numpy's least squares with an intercept;
-    coordinates with input scale 0 get a zero column; lost pairs are left out."""
-    n = 50000
-    rng = np.random.default_rng(12)
+def _features(xs, degree):
+    cols = []
+    for t in st.poly_terms(degree):
+        m = np.ones(xs.shape[1])
+        for i in t:
+            m = m * xs[i]
+        cols.append(m)
+    return np.array(cols).T
+
+
+@pytest.mark.parametrize("degree", [0, 1, 2, 3])
+def test_fit_head_is_least_squares(degree):
+    """The FP64 polynomial fit against numpy's least squares over the same
+    monomials; coordinates with input scale 0 drop out; lost pairs are left
+    out; the reported RMS is the residual's."""
+    n = 60000
+    rng = np.random.default_rng(12 + degree)
     z = rng.standard_normal((6, n)) * np.array([1e-3, 1e-4, 1e-3, 1e-4, 1e-2, 1e-3])[:, None]
     q0 = unit(rng.standard_normal(4))
-    Lt = rng.standard_normal((4, 6)) * 1e-2
     xs = z * IN_SCALE[:, None]
-    q = q0[:, None] + Lt @ xs + 1e-3 + 1e-4 * np.sin(3 * xs[0] * xs[2])[None, :] + 1e-5 * rng.standard_normal((4, n))
+    q = (q0[:, None] + 1e-2 * np.sin(xs[[0, 1, 2, 3]] + xs[5]) + 1e-3 * xs[0] * xs[2] * xs[3]
+         + 1e-5 * rng.standard_normal((4, n)))
     lost = np.zeros(n, np.uint8)
     lost[::7] = 1
     q[:, ::7] = 1e3                                    # garbage in lost rows
-    net = st.MLP(128, torch.cuda.current_stream().cuda_stream)
+    net = st.MLP(128, cur())
     net.set_head(q0, None, 1.0, IN_SCALE)
-    L = net.fit_linear(dev(z, np.float64).data_ptr(), dev(q, np.float64).data_ptr(), n,
-                       dev(lost, np.uint8).data_ptr())
+    zd, qd, ld = dev(z, np.float64), dev(q, np.float64), dev(lost, np.uint8)
+    coef, rms = net.fit_head(degree, zd.data_ptr(), qd.data_ptr(), n, ld.data_ptr())
     keep = lost == 0
-    F = np.concatenate([np.ones((1, keep.sum())), xs[[0, 1, 2, 3, 5]][:, keep]]).T
-    sol, *_ = np.linalg.lstsq(F, (q[:, keep] - q0[:, None]).T, rcond=None)
-    ref = np.zeros((4, 6))
-    ref[:, [0, 1, 2, 3, 5]] = sol[1:].T
-    np.testing.assert_allclose(L, ref, rtol=0, atol=1e-10)
-    assert np.all(L[:, 4] == 0.0)
+    F = _features(xs[:, keep], degree)
+    live = np.array([4 not in t for t in st.poly_terms(degree)])
+    sol, *_ = np.linalg.lstsq(F[:, live], (q[:, keep] - q0[:, None]).T, rcond=None)
+    ref = np.zeros((4, len(live)))
+    ref[:, live] = sol.T
+    assert np.all(coef[:, ~live] == 0.0)
+    np.testing.assert_allclose(coef, ref, rtol=0, atol=1e-8 * np.abs(ref).max())
+    res = (q[:, keep] - q0[:, None]) - ref @ F.T
+    np.testing.assert_allclose(rms, np.sqrt(np.mean(res * res, axis=1)), rtol=1e-6)
+    # the installed head: residual targets (q - q0 - P(x)) / s, and x rows
+    sc = np.array([0.25, 0.5, 1e-3, 2.0])
+    net.set_scale(sc)
+    xr = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+    rr = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    net.make_targets(zd.data_ptr(), qd.data_ptr(), n, xr.data_ptr(), rr.data_ptr())
+    np.testing.assert_array_equal(xr.cpu().numpy(), z.T.astype(np.float32))
+    r_ref = ((q - q0[:, None] - coef @ _features(xs, degree).T) / sc[:, None]).T
+    np.testing.assert_allclose(rr.cpu().numpy(), r_ref.astype(np.float32), rtol=2e-7, atol=1e-9)
     net.close()
 
 
@@ -217,7 +260,7 @@ def test_one_turn_quaternions_match_oracle(gg):
     qo = _oracle_turn_quats(ring, z, 2)
     q_ref = np.array([0.3, -0.2, 0.9, 0.1])
     lat = st.Lattice(ring)
-    tr = st.Tracker(lat, z.shape[1])
+    tr = st.Tracker(lat, z.shape[1], "fp64", cur())
     tr.upload(z, S)
     q = torch.full((4, z.shape[1]), 7.0, dtype=torch.float64, device="cuda")
     st.st_track_one_turn_map(tr.handle, 2, q_ref, q.data_ptr())
@@ -225,7 +268,7 @@ def test_one_turn_quaternions_match_oracle(gg):
     qg = q.cpu().numpy().T
     assert np.all(qg @ q_ref >= 0.0)
     sgn = np.sign(np.sum(qg * qo, axis=1))[:, None]
-    assert np.abs(qg - sgn * qo).max() < 1e-12
+    assert np.abs(qg - sgn * qo).max() < 1e-11
     z1, S1, _ = st.track(ring, z, S, 1, 2)
     np.testing.assert_array_equal(zg, z1)
     np.testing.assert_array_equal(Sg, S1)
@@ -238,7 +281,7 @@ def test_one_turn_quaternions_skip_lost_particles():
     z, S = W.gaussian_particles(40, 45.5, seed=2)
     z[1, 5] = 1.5                                      # lost in the first element
     lat = st.Lattice(ring)
-    tr = st.Tracker(lat, 40)
+    tr = st.Tracker(lat, 40, "fp64", cur())
     tr.upload(z, S)
     q = torch.full((4, 40), 7.0, dtype=torch.float64, device="cuda")
     st.st_track_one_turn_map(tr.handle, 2, [1.0, 0, 0, 0], q.data_ptr())
@@ -265,7 +308,7 @@ def test_stroboscopic_sum_matches_oracle():
         zo, So, _ = oracle.track(ring, zo, So, 1, 2)
         acc += So
     lat = st.Lattice(ring)
-    tr = st.Tracker(lat, 100)
+    tr = st.Tracker(lat, 100, "fp64", cur())
     tr.set_launch(0, 5)                                # several turns per launch
     tr.upload(z, S)
     ssum = torch.zeros((3, 100), dtype=torch.float64, device="cuda")
@@ -288,16 +331,16 @@ def test_surrogate_with_zero_network_is_the_closed_form():
     th = 0.7
     axis = unit(np.array([0.2, 1.0, -0.3]))
     q0 = np.array([math.cos(th / 2), *(axis * math.sin(th / 2))])
-    net = st.MLP(512, None)
+    net = st.MLP(512, cur())
     net.set_params(np.zeros(net.n_params, np.float32))
     net.set_head(q0, None, 1.0, IN_SCALE)
     lat = st.Lattice(ring)
-    tr = st.Tracker(lat, n)
+    tr = st.Tracker(lat, n, "fp64", cur())
     tr.upload(z, S)
     ssum = torch.zeros((3, n), dtype=torch.float64, device="cuda")
     st.st_track_surrogate(tr.handle, net.handle, turns, ssum.data_ptr())
     zg, Sg, lg = tr.download()
-    qf = unit(q0.astype(np.float32).astype(np.float64))
+    qf = unit(q0)                                      # the head is FP64
     Se = S.copy()
     acc = np.zeros_like(S)
     for _ in range(turns):
@@ -305,7 +348,7 @@ def test_surrogate_with_zero_network_is_the_closed_form():
         acc += Se
     assert np.abs(Sg - Se).max() < 1e-12 * turns
     assert np.abs(ssum.cpu().numpy() - acc).max() < 1e-12 * turns * turns
-    tr2 = st.Tracker(lat, n)
+    tr2 = st.Tracker(lat, n, "fp64", cur())
     tr2.upload(z, S)
     tr2.track_orbit(turns)
     z2, S2, l2 = tr2.download()

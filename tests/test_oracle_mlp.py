@@ -153,3 +153,48 @@ def test_adam_first_step_closed_form():
         p2, m, v = M.adam_step(p1, m, v, g, t, lr=1e-3, eps=0.0)
         np.testing.assert_allclose(p2 - p1, -1e-3 * np.sign(g), atol=1e-14)
         p1 = p2
+
+
+def test_residual_gradient_central_differences():
+    rng = np.random.default_rng(21)
+    p = random_params(6)
+    x, _ = _inputs(6, 22)
+    r = rng.standard_normal((6, 4))
+    loss, g = M.residual_loss_grad(p, x, r, HEAD["in_scale"])
+    offs = np.cumsum([0] + [a * b + a for a, b in M.LAYERS])
+    h = 1e-4
+
+    def f(i, d):
+        pd = p.copy()
+        pd[i] += d
+        return M.residual_loss_grad(pd, x, r, HEAD["in_scale"])[0]
+
+    for l, (a, b) in enumerate(M.LAYERS):
+        for i in list(offs[l] + rng.integers(0, a * b, 6)) + list(offs[l] + a * b + rng.integers(0, a, 3)):
+            fd = (8 * (f(i, h) - f(i, -h)) - (f(i, 2 * h) - f(i, -2 * h))) / (12 * h)
+            assert abs(g[i] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max()), (i, g[i], fd)
+    y, _ = M.network(p, x * HEAD["in_scale"])
+    assert loss == pytest.approx(np.mean(np.sum((y - r) ** 2, axis=1)), rel=1e-14)
+
+
+def test_split_bf16_resolution():
+    """hi = bf16(v) exactly, and hi + lo resolves v to 2^-17 relative
+    (two 8-bit significands)."""
+    rng = np.random.default_rng(5)
+    v = (rng.standard_normal(50000) * 10.0 ** rng.integers(-3, 3, 50000)).astype(np.float32)
+    s = M.split_bf16(v)
+    vv = v.astype(np.float64)
+    assert np.all(np.abs(s - vv) <= 2.0 ** -17 * np.abs(vv))
+    hi = M.round_bf16(v)
+    assert np.all(np.abs(s - hi) <= 2.0 ** -8 * np.abs(vv))
+    assert np.abs(s - vv).max() > 0                  # not the identity
+
+
+def test_polynomial_head_terms():
+    rng = np.random.default_rng(2)
+    xs = rng.standard_normal((5, 6))
+    terms = [(), (0,), (1, 2), (3, 3, 5)]
+    coef = rng.standard_normal((4, 4))
+    ref = (coef[:, 0][None, :] + np.outer(xs[:, 0], coef[:, 1]) + np.outer(xs[:, 1] * xs[:, 2], coef[:, 2])
+           + np.outer(xs[:, 3] ** 2 * xs[:, 5], coef[:, 3]))
+    np.testing.assert_allclose(M.poly(terms, coef, xs), ref, rtol=1e-14, atol=1e-14)
