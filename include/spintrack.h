@@ -230,7 +230,7 @@ int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, const st_ref
 /* BF16 tensor-core GEMM (tcgen05, TMA-fed, FP32 accumulation in tensor
  * memory): D[M][N] = A[M][K] . B[N][K]^T (+ bias[N] if bias != NULL).  All
  * pointers are device memory: A, B bf16 row-major, D and bias FP32; M a
- * multiple of 128, K of 64, N of 16; A and B 16-byte aligned.  Asynchronous on
+ * multiple of 128, K of 64, N of 16; A, B and D 16-byte aligned.  Asynchronous on
  * cuda_stream; *status (device int32, caller-cleared) becomes nonzero if a
  * bounded wait expired.  This is the building block of the learned spin map's
  * kernels.  Errors: ST_EINVAL (shapes, alignment), ST_ECUDA. */

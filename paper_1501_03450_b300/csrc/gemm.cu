@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstring>
+#include <mutex>
 
 #include "st_internal.cuh"
 #include "tc_gemm.cuh"
@@ -48,9 +49,46 @@ static int make_tmap(CUtensorMap* tm, const void* base, int rows, int cols, int 
     return ST_OK;
 }
 
+// Tensor maps depend only on (base, rows, cols, box rows) -- the data is read
+// at run time -- so a map stays valid for any buffer at that address with that
+// shape.  The network's buffers are fixed: their maps are encoded once.
+struct TmapKey {
+    const void* base;
+    int rows, cols, box_rows;
+};
+struct TmapEntry {
+    TmapKey key;
+    CUtensorMap map;
+    bool used;
+};
+static TmapEntry g_tmaps[256];
+static std::mutex g_tmap_mu;
+
+static int get_tmap(CUtensorMap* out, const void* base, int rows, int cols, int box_rows) {
+    std::lock_guard<std::mutex> lock(g_tmap_mu);
+    const size_t h = ((uintptr_t)base >> 8) ^ ((size_t)rows * 131) ^ ((size_t)cols * 7919) ^ (size_t)box_rows;
+    for (int probe = 0; probe < 8; ++probe) {
+        TmapEntry& e = g_tmaps[(h + probe) & 255];
+        if (e.used && e.key.base == base && e.key.rows == rows && e.key.cols == cols && e.key.box_rows == box_rows) {
+            *out = e.map;
+            return ST_OK;
+        }
+        if (!e.used) {
+            int rc = make_tmap(&e.map, base, rows, cols, box_rows);
+            if (rc) return rc;
+            e.key = TmapKey{base, rows, cols, box_rows};
+            e.used = true;
+            *out = e.map;
+            return ST_OK;
+        }
+    }
+    // probe window full: encode without caching
+    return make_tmap(out, base, rows, cols, box_rows);
+}
+
 template <int BN>
 static int launch_gemm_bn(const void* A, const void* B, int M, int N, int K, const GemmEpi& epi, int32_t* status,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, int splits) {
     using Cf = GemmCfg<BN>;
     static bool attr = false;
     if (!attr) {
@@ -60,27 +98,61 @@ static int launch_gemm_bn(const void* A, const void* B, int M, int N, int K, con
         attr = true;
     }
     CUtensorMap ta, tb;
-    int rc = make_tmap(&ta, A, M, K, 128);
-    if (rc == ST_OK) rc = make_tmap(&tb, B, N, K, BN);
+    int rc = get_tmap(&ta, A, M, K, 128);
+    if (rc == ST_OK) rc = get_tmap(&tb, B, N, K, BN);
     if (rc) return rc;
-    dim3 grid(M / 128, N / BN);
-    gemm_bf16_tn_kernel<BN><<<grid, 128, Cf::SMEM_BYTES, stream>>>(ta, tb, K, epi, status);
+    const int kblocks = K / 64;
+    const int per = (kblocks + splits - 1) / splits;
+    dim3 grid(M / 128, N / BN, (kblocks + per - 1) / per);
+    gemm_bf16_tn_kernel<BN><<<grid, 128, Cf::SMEM_BYTES, stream>>>(ta, tb, K, per, epi, status);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ST_OK : cuda_fail(e, "gemm launch");
 }
 
 // D = A B^T with the epilogue; M % 128 == 0, K % 64 == 0, N % 16 == 0.
 int gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const GemmEpi& epi, int32_t* status,
-                 cudaStream_t stream) {
+                 cudaStream_t stream, int splits) {
     if (M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64 || N % 16) {
         set_error("gemm: need M %% 128 == 0, K %% 64 == 0, N %% 16 == 0 (got %d, %d, %d)", M, N, K);
         return ST_EINVAL;
     }
-    if (N % 256 == 0) return launch_gemm_bn<256>(A, B, M, N, K, epi, status, stream);
-    if (N % 128 == 0) return launch_gemm_bn<128>(A, B, M, N, K, epi, status, stream);
-    if (N % 64 == 0) return launch_gemm_bn<64>(A, B, M, N, K, epi, status, stream);
-    if (N % 32 == 0) return launch_gemm_bn<32>(A, B, M, N, K, epi, status, stream);
-    return launch_gemm_bn<16>(A, B, M, N, K, epi, status, stream);
+    splits = gemm_split_count(K, splits);
+    if (splits > 1 && epi.mode != EPI_F32) {
+        set_error("gemm: split-K needs the plain FP32 epilogue");
+        return ST_EINVAL;
+    }
+    if (N % 256 == 0) return launch_gemm_bn<256>(A, B, M, N, K, epi, status, stream, splits);
+    if (N % 128 == 0) return launch_gemm_bn<128>(A, B, M, N, K, epi, status, stream, splits);
+    if (N % 64 == 0) return launch_gemm_bn<64>(A, B, M, N, K, epi, status, stream, splits);
+    if (N % 32 == 0) return launch_gemm_bn<32>(A, B, M, N, K, epi, status, stream, splits);
+    return launch_gemm_bn<16>(A, B, M, N, K, epi, status, stream, splits);
+}
+
+__global__ void split_reduce_kernel(const float4* __restrict__ ws, int splits, int64_t stride4, int64_t count4,
+                                    float4* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count4) return;
+    float4 a = ws[i];
+    for (int z = 1; z < splits; ++z) {
+        const float4 b = ws[(int64_t)z * stride4 + i];
+        a.x += b.x;
+        a.y += b.y;
+        a.z += b.z;
+        a.w += b.w;
+    }
+    out[i] = a;
+}
+
+int gemm_split_reduce(const float* ws, int splits, int64_t stride, int64_t count, float* out, cudaStream_t stream) {
+    if ((count & 3) || (stride & 3) || ((uintptr_t)ws & 15) || ((uintptr_t)out & 15)) {
+        set_error("gemm_split_reduce: counts and pointers must be multiples of 4 floats");
+        return ST_EINVAL;
+    }
+    const int64_t c4 = count / 4;
+    split_reduce_kernel<<<(unsigned)((c4 + 255) / 256), 256, 0, stream>>>((const float4*)ws, splits, stride / 4, c4,
+                                                                          (float4*)out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "gemm_split_reduce");
 }
 
 }  // namespace st
@@ -91,6 +163,10 @@ extern "C" int st_gemm_bf16(const void* A, const void* B, float* D, int32_t M, i
                             const float* bias, int32_t* status, void* cuda_stream) {
     if (!A || !B || !D || !status) {
         set_error("st_gemm_bf16: null pointer");
+        return ST_EINVAL;
+    }
+    if ((uintptr_t)D & 15) {
+        set_error("st_gemm_bf16: D must be 16-byte aligned");
         return ST_EINVAL;
     }
     GemmEpi epi;

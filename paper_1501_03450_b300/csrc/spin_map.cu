@@ -26,6 +26,7 @@ namespace st {
 
 constexpr int MLP_IN = 6, MLP_H = 256, MLP_OUT = 4, MLP_KIN = 64, MLP_NOUT = 16;
 constexpr int POLY_MAX_DEG = 3, POLY_MAX = 84;   // monomials of 6 inputs up to degree 3
+constexpr int WG_MAX_SPLITS = 64;                 // split-K pieces of the weight-gradient GEMMs
 
 // flattened FP32 parameter layout: W1 [256][6], b1, W2 [256][256], b2, W3, b3,
 // W4, b4, W5 [4][256], b5
@@ -107,6 +108,7 @@ struct st_mlp {
     __nv_bfloat16* dZ[2] = {nullptr, nullptr};
     __nv_bfloat16* dZT[2] = {nullptr, nullptr};
     float* dWtmp = nullptr;                                 // [256][64]
+    float* ws = nullptr;                                    // split-K partial sums [64][256][256]
     float* b5p = nullptr;                                   // [16] output bias, zero padded
     double* loss = nullptr;
     int32_t* status = nullptr;
@@ -148,20 +150,20 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
 }
 
 // one row of the first layer's input: hi parts in columns 0..5, lo parts in
-// 6..11, zeros after
+// 6..11, zeros after; the row-major copy is written as 16-byte vectors
 __device__ __forceinline__ void write_input_row(const float* xs, int r, int Bp, __nv_bfloat16* __restrict__ X0,
                                                 __nv_bfloat16* __restrict__ X0T) {
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-    for (int c = 0; c < MLP_KIN; ++c) {
-        __nv_bfloat16 b = zero;
-        if (c < 2 * MLP_IN) {
-            __nv_bfloat16 hi, lo;
-            split_bf16(xs[c % MLP_IN], hi, lo);
-            b = c < MLP_IN ? hi : lo;
-        }
-        X0[(size_t)r * MLP_KIN + c] = b;
-        if (X0T) X0T[(size_t)c * Bp + r] = b;
-    }
+    __align__(16) __nv_bfloat16 row[16];
+    for (int c = 0; c < MLP_IN; ++c) split_bf16(xs[c], row[c], row[MLP_IN + c]);
+    row[12] = row[13] = row[14] = row[15] = __float2bfloat16_rn(0.0f);
+    uint4* dst = reinterpret_cast<uint4*>(X0 + (size_t)r * MLP_KIN);
+    dst[0] = *reinterpret_cast<const uint4*>(&row[0]);
+    dst[1] = *reinterpret_cast<const uint4*>(&row[8]);
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    for (int k = 2; k < MLP_KIN / 8; ++k) dst[k] = zero4;
+    if (X0T)
+        for (int c = 0; c < MLP_KIN; ++c)
+            X0T[(size_t)c * Bp + r] = c < 16 ? row[c] : __float2bfloat16_rn(0.0f);
 }
 
 __global__ void mlp_pack_x(const float* __restrict__ x, int B, int Bp, InScale is, __nv_bfloat16* __restrict__ X0,
@@ -191,7 +193,11 @@ __global__ void mlp_pack_state(const double2* __restrict__ xpx, const double2* _
 // writes dL/dy (bf16, zero padded) row-major [Bp][64] and transposed [16][Bp]
 __device__ __forceinline__ void write_dy(const float* gy, int r, int Bp, __nv_bfloat16* __restrict__ dYp,
                                          __nv_bfloat16* __restrict__ dYT) {
-    for (int c = 0; c < MLP_KIN; ++c) dYp[(size_t)r * MLP_KIN + c] = __float2bfloat16_rn(c < 4 ? gy[c] : 0.0f);
+    const __nv_bfloat162 a = __floats2bfloat162_rn(gy[0], gy[1]);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(gy[2], gy[3]);
+    uint4* dst = reinterpret_cast<uint4*>(dYp + (size_t)r * MLP_KIN);
+    dst[0] = make_uint4(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b), 0u, 0u);
+    for (int k = 1; k < MLP_KIN / 8; ++k) dst[k] = make_uint4(0u, 0u, 0u, 0u);
     for (int c = 0; c < MLP_NOUT; ++c) dYT[(size_t)c * Bp + r] = __float2bfloat16_rn(c < 4 ? gy[c] : 0.0f);
 }
 
@@ -495,18 +501,34 @@ static int mlp_forward_layers(st_mlp* n, int Bp, bool keep_t) {
     return gemm_bf16_tn(in, n->W5p, Bp, MLP_NOUT, MLP_H, e, n->status, n->stream);
 }
 
+// Weight gradient out[M][N] = A . B^T with the batch as K (K = Bp): few
+// output tiles and a long K, so K is split across CTAs and the partial sums
+// reduced (deterministic order).
+static int wgrad_gemm(st_mlp* n, const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int Bp, float* out) {
+    GemmEpi ep = epi_base();
+    ep.mode = EPI_F32;
+    ep.n_valid = N;
+    ep.ld_f32 = N;
+    const int splits = gemm_split_count(Bp, WG_MAX_SPLITS);
+    if (splits == 1) {
+        ep.out_f32 = out;
+        return gemm_bf16_tn(A, B, M, N, Bp, ep, n->status, n->stream);
+    }
+    ep.out_f32 = n->ws;
+    ep.split_stride = (int64_t)M * N;
+    int rc = gemm_bf16_tn(A, B, M, N, Bp, ep, n->status, n->stream, splits);
+    if (rc) return rc;
+    return gemm_split_reduce(n->ws, splits, (int64_t)M * N, (int64_t)M * N, out, n->stream);
+}
+
 // Backward pass from dL/dy (dYp, dYT written by a head kernel) into the
 // gradient buffer g, using the activations kept by the forward pass.
 static int mlp_backward(st_mlp* n, int Bp) {
     float* g = n->g;
     // layer 5: dW5^T = A4^T . dY  (D'[256][16]), db5 = sum dY, dZ4 = (dY W5) * silu'(Z4)
-    GemmEpi ep = epi_base();
-    ep.mode = EPI_F32;
-    ep.n_valid = MLP_NOUT;
-    ep.out_f32 = n->dWtmp;
-    ep.ld_f32 = MLP_NOUT;
-    int rc = gemm_bf16_tn(n->AT[3], n->dYT, MLP_H, MLP_NOUT, Bp, ep, n->status, n->stream);
+    int rc = wgrad_gemm(n, n->AT[3], n->dYT, MLP_H, MLP_NOUT, Bp, n->dWtmp);
     if (rc) return rc;
+    GemmEpi ep;
     mlp_gather_w5<<<(MLP_OUT * MLP_H + 255) / 256, 256, 0, n->stream>>>(n->dWtmp, g + mlp_w_off(4));
     mlp_rowsum<<<1, 128, 0, n->stream>>>(n->dYT, MLP_OUT, Bp, g + mlp_b_off(4));
     ep = epi_base();
@@ -524,13 +546,8 @@ static int mlp_backward(st_mlp* n, int Bp) {
     const __nv_bfloat16* WT[4] = {nullptr, n->W2T, n->W3T, n->W4T};
     int cur = 0;
     for (int l = 3; l >= 1; --l) {
-        // dW_l = dZ_l^T . A_{l-1}  ->  [256 out][256 in], straight into the gradient buffer
-        ep = epi_base();
-        ep.mode = EPI_F32;
-        ep.n_valid = MLP_H;
-        ep.out_f32 = g + mlp_w_off(l);
-        ep.ld_f32 = MLP_H;
-        rc = gemm_bf16_tn(n->dZT[cur], n->AT[l - 1], MLP_H, MLP_H, Bp, ep, n->status, n->stream);
+        // dW_l = dZ_l^T . A_{l-1}  ->  [256 out][256 in], into the gradient buffer
+        rc = wgrad_gemm(n, n->dZT[cur], n->AT[l - 1], MLP_H, MLP_H, Bp, g + mlp_w_off(l));
         if (rc) return rc;
         mlp_rowsum<<<MLP_H / 4, 128, 0, n->stream>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(l));
         // dZ_{l-1} = (dZ_l W_l) * silu'(Z_{l-1})
@@ -548,12 +565,7 @@ static int mlp_backward(st_mlp* n, int Bp) {
         cur = 1 - cur;
     }
     // layer 1: dW1 = dZ1^T . X0 -> [256][64] -> [256][6] (hi + lo columns); db1
-    ep = epi_base();
-    ep.mode = EPI_F32;
-    ep.n_valid = MLP_KIN;
-    ep.out_f32 = n->dWtmp;
-    ep.ld_f32 = MLP_KIN;
-    rc = gemm_bf16_tn(n->dZT[cur], n->X0T, MLP_H, MLP_KIN, Bp, ep, n->status, n->stream);
+    rc = wgrad_gemm(n, n->dZT[cur], n->X0T, MLP_H, MLP_KIN, Bp, n->dWtmp);
     if (rc) return rc;
     mlp_gather_w1<<<(MLP_H * MLP_IN + 255) / 256, 256, 0, n->stream>>>(n->dWtmp, g + mlp_w_off(0));
     mlp_rowsum<<<MLP_H / 4, 128, 0, n->stream>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(0));
@@ -610,7 +622,7 @@ int st_mlp_destroy(st_mlp* n) {
     if (!n) return ST_OK;
     cudaStreamSynchronize(n->stream);
     void* ptrs[] = {n->p,   n->m,   n->v,   n->g,   n->W1p, n->W2,  n->W3,   n->W4,      n->W5p,  n->W2T,
-                    n->W3T, n->W4T, n->W5Tp, n->X0, n->X0T, n->Y,   n->dYp,  n->dYT,     n->dWtmp, n->b5p,
+                    n->W3T, n->W4T, n->W5Tp, n->X0, n->X0T, n->Y,   n->dYp,  n->dYT,     n->dWtmp, n->ws, n->b5p,
                     n->loss, n->status, n->d_terms, n->d_coef};
     for (void* q : ptrs) cudaFree(q);
     for (int l = 0; l < 4; ++l) {
@@ -687,6 +699,7 @@ int st_mlp_create(int32_t max_batch, void* cuda_stream, st_mlp** out) {
         ST_MALLOC(n->dZT[k], (size_t)Bp * MLP_H * bf);
     }
     ST_MALLOC(n->dWtmp, (size_t)MLP_H * MLP_KIN * 4);
+    ST_MALLOC(n->ws, (size_t)WG_MAX_SPLITS * MLP_H * MLP_H * 4);
     ST_MALLOC(n->b5p, MLP_NOUT * 4);
     ST_MALLOC(n->loss, sizeof(double));
     ST_MALLOC(n->status, sizeof(int32_t));

@@ -41,14 +41,27 @@ struct GemmEpi {
     int32_t ld_z;
     float* z_out;                    // [M][ld_zo] pre-activations (EPI_BIAS_SILU)
     int32_t ld_zo;
+    int64_t split_stride;            // split-K (EPI_F32): split z writes out_f32 + z * split_stride
 };
 
 enum { STATUS_MMA_TIMEOUT = 2 };
 
 // D = A B^T with the epilogue (host launcher, gemm.cu); M % 128 == 0,
-// K % 64 == 0, N % 16 == 0.
+// K % 64 == 0, N % 16 == 0.  With splits > 1 (EPI_F32 only) the K range is
+// cut into that many pieces, piece z written to out_f32 + z * split_stride,
+// and the caller reduces them (gemm_split_reduce).
 int gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const GemmEpi& epi, int32_t* status,
-                 cudaStream_t stream);
+                 cudaStream_t stream, int splits = 1);
+// out[i] = sum_z ws[z * stride + i], i < count
+int gemm_split_reduce(const float* ws, int splits, int64_t stride, int64_t count, float* out, cudaStream_t stream);
+// K blocks per split for a requested split count (every split gets >= 1 block)
+inline int gemm_split_count(int K, int want) {
+    const int kblocks = K / 64;
+    if (want < 1) want = 1;
+    if (want > kblocks) want = kblocks;
+    const int per = (kblocks + want - 1) / want;
+    return (kblocks + per - 1) / per;
+}
 
 // ---- tcgen05 / TMA primitives ---------------------------------------------
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
@@ -156,7 +169,7 @@ struct GemmCfg {
 template <int BN>
 __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB, int K,
-                                                              GemmEpi epi, int32_t* status) {
+                                                              int kb_per_split, GemmEpi epi, int32_t* status) {
     using C = GemmCfg<BN>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -166,7 +179,10 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_const
     const int warp = threadIdx.x >> 5;
     const int m0 = blockIdx.x * C::BM;
     const int n0 = blockIdx.y * BN;
-    const int kblocks = K / C::BK;
+    // this CTA's K blocks: [kb0, kb0 + kblocks)
+    const int kb0 = blockIdx.z * kb_per_split;
+    const int kb_all = K / C::BK;
+    const int kblocks = (kb_all - kb0) < kb_per_split ? (kb_all - kb0) : kb_per_split;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -200,8 +216,8 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_const
             unsigned char* a = smem + s * C::STAGE_BYTES;
             unsigned char* b = a + C::A_BYTES;
             mbar_arrive_expect_tx(&full_bar[s], C::STAGE_BYTES);
-            tma_load_2d(a, &tmA, kb * C::BK, m0, &full_bar[s]);
-            tma_load_2d(b, &tmB, kb * C::BK, n0, &full_bar[s]);
+            tma_load_2d(a, &tmA, (kb0 + kb) * C::BK, m0, &full_bar[s]);
+            tma_load_2d(b, &tmB, (kb0 + kb) * C::BK, n0, &full_bar[s]);
         }
     } else if (threadIdx.x == 32) {
         // MMA issuer
@@ -239,27 +255,68 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_const
             float v[CH];
             tmem_load_cols<CH>(lane_addr + c0, v);
             const int nb = n0 + c0;
+            // Row-major outputs are written as 16-byte vectors of the thread's
+            // row (CH consecutive columns); the transposed bf16 output is
+            // coalesced across the warp's 32 consecutive rows.
+            if (epi.mode == EPI_F32 || epi.mode == EPI_BIAS_F32) {
+                float* dst = epi.out_f32 + (size_t)blockIdx.z * epi.split_stride + (size_t)row * epi.ld_f32 + nb;
 #pragma unroll
-            for (int j = 0; j < CH; ++j) {
-                const int col = nb + j;
-                float x = v[j];
-                if (epi.mode == EPI_F32) {
-                    epi.out_f32[(size_t)row * epi.ld_f32 + col] = x;
-                } else if (epi.mode == EPI_BIAS_F32) {
-                    epi.out_f32[(size_t)row * epi.ld_f32 + col] = x + epi.bias[col];
-                } else {
-                    float y;
-                    if (epi.mode == EPI_BIAS_SILU) {
-                        const float z = x + epi.bias[col];
-                        if (epi.z_out) epi.z_out[(size_t)row * epi.ld_zo + col] = z;
-                        y = silu_f(z);
-                    } else {   // EPI_DSILU
-                        y = x * dsilu_f(epi.z_in[(size_t)row * epi.ld_z + col]);
+                for (int j = 0; j < CH; j += 4) {
+                    float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    if (epi.mode == EPI_BIAS_F32) {
+                        o.x += epi.bias[nb + j];
+                        o.y += epi.bias[nb + j + 1];
+                        o.z += epi.bias[nb + j + 2];
+                        o.w += epi.bias[nb + j + 3];
                     }
-                    if (col >= epi.n_valid) y = 0.0f;
-                    const __nv_bfloat16 yb = __float2bfloat16_rn(y);
-                    if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ld_bf16 + col] = yb;
-                    if (epi.out_bf16_t) epi.out_bf16_t[(size_t)col * epi.ld_bf16_t + row] = yb;
+                    *reinterpret_cast<float4*>(dst + j) = o;
+                }
+            } else {
+                if (epi.mode == EPI_BIAS_SILU) {
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) v[j] += epi.bias[nb + j];
+                    if (epi.z_out) {
+                        float* zd = epi.z_out + (size_t)row * epi.ld_zo + nb;
+#pragma unroll
+                        for (int j = 0; j < CH; j += 4)
+                            *reinterpret_cast<float4*>(zd + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) v[j] = silu_f(v[j]);
+                } else {   // EPI_DSILU
+                    const float* zs = epi.z_in + (size_t)row * epi.ld_z + nb;
+#pragma unroll
+                    for (int j = 0; j < CH; j += 4) {
+                        const float4 zz = *reinterpret_cast<const float4*>(zs + j);
+                        v[j] *= dsilu_f(zz.x);
+                        v[j + 1] *= dsilu_f(zz.y);
+                        v[j + 2] *= dsilu_f(zz.z);
+                        v[j + 3] *= dsilu_f(zz.w);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < CH; ++j)
+                    if (nb + j >= epi.n_valid) v[j] = 0.0f;
+                if (epi.out_bf16) {
+                    __nv_bfloat16* bd = epi.out_bf16 + (size_t)row * epi.ld_bf16 + nb;
+#pragma unroll
+                    for (int j = 0; j < CH; j += 8) {
+                        uint4 pk;
+                        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[j], v[j + 1]);
+                        __nv_bfloat162 h1 = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[j + 4], v[j + 5]);
+                        __nv_bfloat162 h3 = __floats2bfloat162_rn(v[j + 6], v[j + 7]);
+                        pk.x = *reinterpret_cast<uint32_t*>(&h0);
+                        pk.y = *reinterpret_cast<uint32_t*>(&h1);
+                        pk.z = *reinterpret_cast<uint32_t*>(&h2);
+                        pk.w = *reinterpret_cast<uint32_t*>(&h3);
+                        *reinterpret_cast<uint4*>(bd + j) = pk;
+                    }
+                }
+                if (epi.out_bf16_t) {
+#pragma unroll
+                    for (int j = 0; j < CH; ++j)
+                        epi.out_bf16_t[(size_t)(nb + j) * epi.ld_bf16_t + row] = __float2bfloat16_rn(v[j]);
                 }
             }
         }

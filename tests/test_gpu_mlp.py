@@ -171,12 +171,14 @@ def test_training_reduces_loss_on_a_smooth_map():
     net.close()
 
 
-def test_residual_loss_and_gradient_match_reference():
-    B = 700
+@pytest.mark.parametrize("B", [700, 8192])
+def test_residual_loss_and_gradient_match_reference(B):
+    """As the quaternion loss; B = 8192 runs the weight gradients as split-K
+    GEMMs (64 K pieces, reduced in a fixed order)."""
     p = random_params(8, last_scale=1.0)
     x = rand_x(B, 2)
     r = np.random.default_rng(4).standard_normal((B, 4))
-    net = make_net(p, head_for(1))
+    net = make_net(p, head_for(1), max_batch=max(B, 4096))
     xd, rd = dev(x, np.float32), dev(r, np.float32)
     loss, g = net.loss_grad_residual(xd.data_ptr(), rd.data_ptr(), B, want_grads=True)
     x32 = x.astype(np.float32).astype(np.float64)
