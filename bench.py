@@ -293,6 +293,59 @@ def variant_batched(st, torch, args, turns=3):
     return out
 
 
+def variant_surrogate(st, torch, args, fp64_value, throughput_turns=30):
+    """The learned one-turn spin map: trained here (pairs along tracked orbits,
+    FP64 polynomial head, network on its own tensor-core kernels), then used
+    for stroboscopic spin tracking with the orbit tracked exactly.  Error
+    against plain FP64 spin tracking on 1024 particles after --error-turns
+    turns; throughput on the 10^4-particle averaging ensemble against plain
+    FP64 tracking with the same stroboscopic sum."""
+    from paper_1501_03450_b300.surrogate import train_spin_map
+    w = W.workload("rhic_like_spin_map", spin_order=args.spin_order)
+    ring = w["ring"]
+    gg = ring["Ggamma0"]
+    n_el = len(ring["elements"])
+    z_train, _ = W.gaussian_particles(w["train_particles"], gg, seed=w["train_seed"], cut=w["cut"])
+    sg = train_spin_map(ring, z_train, w["train_turns"], w["spin_order"], degree=w["degree"], steps=w["steps"],
+                        batch=w["batch"], lr=w["lr"])
+    out = {"config": {"workload": f"108-cell RHIC-like ring, Ggamma={gg}, Romberg order {args.spin_order}; "
+                      f"use: {w['n_particles']} Gaussian protons (cut {w['cut']} sigma), stroboscopic <S> at s=0",
+                      "training": dict(sg.timings, degree=w["degree"], lr=w["lr"],
+                                       pairs_from=f"{w['train_particles']} particles x {w['train_turns']} turns"),
+                      "network": "6-256-256-256-256-4 SiLU, bf16 weights/activations, fp32 accumulation"}}
+    # accuracy against plain FP64 tracking
+    z, S = W.gaussian_particles(w["eval_particles"], gg, seed=w["seed"], cut=w["cut"])
+    T = args.error_turns
+    zs, Ss, _, avs, _ = sg.track(z, S, T)
+    zp, Sp, _, avp, _ = sg.track_plain(z, S, T)
+    p = sg.mlp.get_params()
+    sg.mlp.set_params(np.zeros_like(p))
+    _, Sl, _, avl, _ = sg.track(z, S, T)
+    sg.mlp.set_params(p)
+    dS = np.linalg.norm(Ss - Sp, axis=0)
+    dA = np.linalg.norm(avs - avp, axis=0)
+    dL = np.linalg.norm(Sl - Sp, axis=0)
+    out["error_vs_fp64"] = {"turns": T, "particles": int(z.shape[1]), "dS_mean": float(dS.mean()),
+                            "dS_median": float(np.median(dS)), "dS_max": float(dS.max()),
+                            "d_avgS_mean": float(dA.mean()), "d_avgS_max": float(dA.max()),
+                            "polynomial_head_only_dS_mean": float(dL.mean()),
+                            "orbit_max_abs_diff": float(np.abs(zs - zp).max())}
+    # throughput on the averaging ensemble (a bounded number of turns)
+    z, S = W.gaussian_particles(w["n_particles"], gg, seed=w["seed"] + 1, cut=w["cut"])
+    sg.track(z, S, 2)
+    _, _, _, _, ms_s = sg.track(z, S, throughput_turns)
+    _, _, _, _, ms_p = sg.track_plain(z, S, throughput_turns)
+    passes = w["n_particles"] * n_el * throughput_turns
+    out.update({"metric": "particle-element passes/s", "value": passes / (ms_s * 1e-3), "unit": "passes/s",
+                "plain_fp64_same_ensemble": passes / (ms_p * 1e-3),
+                "speedup_vs_plain_fp64_same_ensemble": ms_p / ms_s,
+                "speedup_vs_fp64_headline": passes / (ms_s * 1e-3) / fp64_value,
+                "turns_timed": throughput_turns, "ms_per_turn": ms_s / throughput_turns,
+                "dtype": "f64 orbit + bf16/fp32 network + f64 head"})
+    sg.close()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -409,7 +462,8 @@ def main():
     variants = None
     if not args.no_variants and world == 1:
         variants = {"mixed": variant_mixed(st, torch, args, value, fp32_peak),
-                    "batched": variant_batched(st, torch, args)}
+                    "batched": variant_batched(st, torch, args),
+                    "surrogate": variant_surrogate(st, torch, args, value)}
 
     cpu = None
     if not args.no_cpu_baseline:

@@ -356,3 +356,27 @@ def _run(sg: SpinMapSurrogate, z, S, n_turns, average, timed, surrogate):
         return z1, S1, lost, avg, ms
     finally:
         tr.close()
+
+
+def train_spin_map(ring: Dict, z_train: np.ndarray, sample_turns: int, spin_order: int = 2, degree: int = 3,
+                   steps: int = 20000, batch: int = 32768, lr: float = 1e-3, seed: int = 1501,
+                   max_batch: int = 65536) -> SpinMapSurrogate:
+    """The whole training recipe: pairs along the orbits of the ensemble
+    z_train [6, m] over sample_turns turns (m * sample_turns pairs), the FP64
+    polynomial head of the given degree, and `steps` Adam steps of the
+    network on the residual.  Returns the trained surrogate; its `timings`
+    holds the seconds spent on pairs, fit and training."""
+    import time
+    sg = SpinMapSurrogate(ring, spin_order, max_batch=max_batch, seed=seed)
+    t0 = time.perf_counter()
+    pairs = sg.make_pairs_from_orbits(z_train, sample_turns)
+    t1 = time.perf_counter()
+    sg.fit_head(pairs, degree)
+    x, r = sg.targets(pairs)
+    t2 = time.perf_counter()
+    sg.train(x, r, steps, batch=batch, lr=lr)
+    t3 = time.perf_counter()
+    sg.timings = dict(pairs_s=t1 - t0, fit_s=t2 - t1, train_s=t3 - t2, n_pairs=pairs["n"], steps=steps,
+                      batch=min(batch, max_batch, pairs["n"]))
+    del pairs, x, r
+    return sg

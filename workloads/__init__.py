@@ -251,11 +251,15 @@ def workload(name: str, spin_order: int = 2, Ggamma0: float = None):
         return dict(ring=with_spin_order(ring, spin_order), n_particles=100000,
                     turns=1000, spin_order=spin_order, seed=3450)
     if name == "rhic_like_spin_map":
-        # learned one-turn spin map: 2e6 training pairs, 1e4 particles x 1e4
-        # turns of stroboscopic averaging (errors judged at turn 1000)
+        # learned one-turn spin map: training pairs along the orbits of 4e4
+        # Gaussian particles (cut at 3 sigma) over 100 turns (4e6 pairs);
+        # use on 1e4 particles x 1e4 turns of stroboscopic averaging; errors
+        # judged on 1024 particles at turn 1000
         ring = rhic_like_ring(45.5 if Ggamma0 is None else Ggamma0)
         return dict(ring=with_spin_order(ring, spin_order), n_particles=10000,
-                    turns=10000, spin_order=spin_order, seed=3452, n_pairs=2000000, cut=3.0)
+                    turns=10000, spin_order=spin_order, seed=3452, cut=3.0,
+                    train_particles=40000, train_turns=100, train_seed=777,
+                    steps=30000, batch=32768, lr=2e-3, degree=3, eval_particles=1024, eval_turns=1000)
     if name == "rhic_like_1e6_mixed":
         ring = rhic_like_ring(45.5 if Ggamma0 is None else Ggamma0)
         return dict(ring=with_spin_order(ring, spin_order), n_particles=1000000,
