@@ -46,8 +46,8 @@ L2_BYTES = 126 * 1024 * 1024
 FP64_FLOPS_PER_PASS = 501.5
 # DRAM bytes (read + write) per particle per launch of the FP64 tracker, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the same capture (2e4
-# particles: 1.595 MB + 0 B), scaled linearly with the particle count.
-FP64_DRAM_BYTES_PER_PARTICLE = 79.8
+# particles: 1.618 MB + 0 B), scaled linearly with the particle count.
+FP64_DRAM_BYTES_PER_PARTICLE = 80.9
 
 
 def parse_args():
@@ -64,7 +64,33 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant report")
     ap.add_argument("--error-turns", type=int, default=1000, help="turns of the variants' error check")
+    ap.add_argument("--profile-train", type=int, default=0, metavar="STEPS",
+                    help="profiling mode: only train the spin-map network for STEPS steps on 32768-row batches "
+                         "(pairs from 4000 particles x 10 turns) and print the step time")
     return ap.parse_args()
+
+
+def profile_train(args):
+    """A short, self-contained run of the network's training kernels (for ncu)."""
+    import torch
+    import paper_1501_03450_b300 as st
+    from paper_1501_03450_b300.surrogate import SpinMapSurrogate
+    w = W.workload("rhic_like_spin_map", spin_order=args.spin_order)
+    gg = w["ring"]["Ggamma0"]
+    sg = SpinMapSurrogate(w["ring"], w["spin_order"], max_batch=w["batch"])
+    z0, _ = W.gaussian_particles(4000, gg, seed=w["train_seed"], cut=w["cut"])
+    pairs = sg.make_pairs_from_orbits(z0, 10)
+    sg.fit_head(pairs, w["degree"])
+    x, r = sg.targets(pairs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(sg.stream)
+    sg.train(x, r, args.profile_train, batch=w["batch"], lr=w["lr"], log_every=0)
+    e1.record(sg.stream)
+    e1.synchronize()
+    print(json.dumps({"profile_train_steps": args.profile_train, "batch": w["batch"],
+                      "ms_per_step": e0.elapsed_time(e1) / max(1, args.profile_train),
+                      "library": st.LIB_PATH}))
+    sg.close()
 
 
 def dist_env():
@@ -352,6 +378,8 @@ def variant_surrogate(st, torch, args, fp64_value, throughput_turns=30):
 
 def main():
     args = parse_args()
+    if args.profile_train:
+        return profile_train(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch
