@@ -53,6 +53,34 @@ __device__ __forceinline__ FF ff_add_f(const FF& a, float b) {
 
 __device__ __forceinline__ FF ff_neg(const FF& a) { return FF{-a.hi, -a.lo}; }
 
+// Lazy sum for results that feed straight into ff_mul / ff_add (which read lo
+// in full and renormalise): the rounding error goes into lo unnormalised.
+__device__ __forceinline__ FF ff_add_lazy(const FF& a, const FF& b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return FF{s, e + (a.lo + b.lo)};
+}
+// a + b for a b proportional to a and much smaller (a relative correction):
+// folded into lo; hi keeps carrying the value
+__device__ __forceinline__ FF ff_addlo(const FF& a, float b) { return FF{a.hi, a.lo + b}; }
+// a + b for a b small against ulp-scale of a.hi, or possibly larger when a
+// nearly vanishes: folded into lo and renormalised, so that hi carries the
+// value in every case (exact when |a.hi| >= |a.lo + b|)
+__device__ __forceinline__ FF ff_addn(const FF& a, float b) {
+    FF r;
+    fast_two_sum(a.hi, a.lo + b, r.hi, r.lo);
+    return r;
+}
+// a + b + c, c a small float term, renormalised once
+__device__ __forceinline__ FF ff_add3(const FF& a, const FF& b, float c) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += (a.lo + b.lo) + c;
+    FF r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+
 __device__ __forceinline__ FF ff_mul(const FF& a, const FF& b) {
     const float p = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -p);

@@ -23,13 +23,13 @@ float2 split(double x) {
     return make_float2(hi, (float)(x - (double)hi));
 }
 
-// Derivatives C^(m)(u0), S^(m)(u0), m = 0..4, of C(u) = cos(sqrt(u)/2) and
-// S(u) = sin(sqrt(u)/2)/sqrt(u).
-void half_angle_derivatives(double u0, double C[5], double S[5]) {
+// Derivatives C^(m)(u0), S^(m)(u0), m = 0..MIX_TAYLOR, of C(u) = cos(sqrt(u)/2)
+// and S(u) = sin(sqrt(u)/2)/sqrt(u).
+void half_angle_derivatives(double u0, double C[MIX_TAYLOR + 1], double S[MIX_TAYLOR + 1]) {
     if (u0 < 100.0) {
         // power series about 0: C = sum (-1)^n u^n / (4^n (2n)!),
         // S = sum (-1)^n u^n / (2 4^n (2n+1)!); differentiate term by term
-        for (int m = 0; m < 5; ++m) {
+        for (int m = 0; m <= MIX_TAYLOR; ++m) {
             double c = 0.0, s = 0.0;
             for (int n = m; n < 80; ++n) {
                 double f2n = 1.0, f2n1;
@@ -53,7 +53,7 @@ void half_angle_derivatives(double u0, double C[5], double S[5]) {
         double th = std::sqrt(u0);
         C[0] = std::cos(0.5 * th);
         S[0] = std::sin(0.5 * th) / th;
-        for (int n = 0; n < 4; ++n) {
+        for (int n = 0; n < MIX_TAYLOR; ++n) {
             C[n + 1] = -S[n] / 4.0;
             S[n + 1] = (C[n] - (2.0 + 4.0 * n) * S[n]) / (4.0 * u0);
         }
@@ -107,6 +107,9 @@ int build_mixed_tables(LatticeImpl& L) {
             m.cbmieh_ff = split(-2.0 * hs * hs / (eta * h));
             m.etah_ff = split(eta * h);
             m.ome_ff = split(1.0 - eta);
+            m.eh2_ff = split(eta * h * h);
+            m.cbm1_ff = split(-2.0 * hs * hs);
+            m.dTeta_ff = split((1.0 - 1.0 / eta) * d.ds / beta0);
             // on-axis, on-momentum particle: Omega = (0, h - (1 + G gamma0) eta h, 0)
             omr = h - a0 * eta * h;
             m.omr = (float)omr;
@@ -135,15 +138,23 @@ int build_mixed_tables(LatticeImpl& L) {
             W.sh = (float)std::sin(0.5 * al);
             W.cf = (float)std::cos(al);
             W.sf = (float)std::sin(al);
-            double C[5], S[5];
+            double C[MIX_TAYLOR + 1], S[MIX_TAYLOR + 1];
             half_angle_derivatives(al * al, C, S);
             W.S0 = (float)S[0];
             double fact = 1.0;
-            for (int n = 0; n < 4; ++n) {
+            for (int n = 0; n < MIX_TAYLOR; ++n) {
                 fact *= (n + 1);
                 W.dC[n] = (float)(C[n + 1] / fact);
                 W.dS[n] = (float)(S[n + 1] / fact);
             }
+            // e_y = ch (alpha dS + S b_y) - sh dC with du = 2 alpha b_y + |b|^2:
+            // its first-order coefficient Ky = ch S0 + 2 alpha Kq, where
+            // Kq = ch alpha S'(u0) - sh C'(u0) also multiplies |b|^2
+            const double ch = std::cos(0.5 * al), sh = std::sin(0.5 * al);
+            const double kq = ch * al * S[1] - sh * C[1];
+            W.Ky = split(ch * S[0] + 2.0 * al * kq);
+            W.Kq = (float)kq;
+            W.pad_ = 0.0f;
         }
         for (int c = 0; c < 4; ++c) m.rq[c] = split(rq[c]);
         me[u] = m;

@@ -45,13 +45,21 @@ struct RefConst {
 // cos(sqrt(u)/2) and S(u) = sin(sqrt(u)/2)/sqrt(u); their Taylor coefficients
 // about u0 = alpha^2 give the deviation of the edge rotation from the
 // reference rotation without cancellation.
+// Taylor terms of the edge-deviation functions: the n-th term is about
+// (b_y/2)^n / n! for a deviation angle b_y, so 8 terms keep strong bends at
+// high G gamma (b_y up to ~0.5 at the coarsest Romberg level) below 1e-12.
+constexpr int MIX_TAYLOR = 8;
+
 struct MixWeight {
     float alpha;
     float ch, sh;     // cos(alpha/2), sin(alpha/2)
     float cf, sf;     // cos(alpha), sin(alpha)
     float S0;         // S(alpha^2)
-    float dC[4];      // C(u0 + du) - C(u0) = sum_n dC[n] du^(n+1)
-    float dS[4];      // S(u0 + du) - S(u0) = sum_n dS[n] du^(n+1)
+    float dC[MIX_TAYLOR];   // C(u0 + du) - C(u0) = sum_n dC[n] du^(n+1)
+    float dS[MIX_TAYLOR];   // S(u0 + du) - S(u0) = sum_n dS[n] du^(n+1)
+    float2 Ky;        // d e_y / d b_y at b = 0 (first-order coefficient), as (hi, lo)
+    float Kq;         // coefficient of du in e_y beyond Ky: ch alpha dS[0] - sh dC[0]
+    float pad_;
 };
 
 // Per unique element, constants of the mixed-precision kernel.  First-order
@@ -77,6 +85,9 @@ struct __align__(16) MixElem {
     float2 ome_ff;                    // bend: 1 - eta as (hi, lo)
     float2 k2h_ff;                    // multipole: k2 ds / 2 as (hi, lo)
     float2 k2ds_ff;                   // multipole: k2 ds as (hi, lo)
+    float2 eh2_ff;                    // bend: eta h^2 as (hi, lo)
+    float2 cbm1_ff;                   // bend: cos(h ds) - 1 as (hi, lo)
+    float2 dTeta_ff;                  // bend: (1 - 1/eta) ds / beta0 as (hi, lo)
     float2 rq[4];                     // reference rotation over the element (bends, snakes), (hi, lo) per component
     MixWeight w[6];
 };

@@ -6,7 +6,7 @@
 namespace st {
 
 template <int K>
-__global__ void __launch_bounds__(128, 4) track_mixed_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
+__global__ void __launch_bounds__(128, 3) track_mixed_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
                                                             uint32_t seq_offset, uint32_t rho_offset, int n_seq,
                                                             RefConst ref, double2* __restrict__ xpx,
                                                             double2* __restrict__ ypy, double2* __restrict__ tpt,

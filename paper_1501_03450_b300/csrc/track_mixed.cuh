@@ -18,9 +18,16 @@
 //   Romberg level's trapezoid weights add up to the element length, every
 //   level product equals R_L E_k with the same reference rotation R_L, so the
 //   Romberg table and the normalisation act on the near-identity deviations
-//   E_k (scalar part stored minus one) in FP32.  The element rotation R_L D is
-//   multiplied into a compensated (hi, lo) turn quaternion; once per turn it
-//   is composed and renormalised in FP64 and the spin rotated in FP64.
+//   E_k (scalar part minus one in FP32, vector part compensated).  The
+//   first-order parts of the spin rotations -- the deviation of Omega linear in
+//   the coordinates (quadrupole fields, the bend's dispersive and energy
+//   terms), the rotation vectors, their sums in the level products, the
+//   Romberg combinations and the composition into the turn -- are carried as
+//   compensated (hi, lo) pairs like the orbit's linear terms, so that FP32
+//   rounding of rotations of order 1e-2 per element (G gamma ~ 500) does not
+//   accumulate; second-order parts are plain FP32.  The element rotation
+//   R_L D is multiplied into a compensated (hi, lo) turn quaternion; once per
+//   turn it is composed and renormalised in FP64 and the spin rotated in FP64.
 #pragma once
 
 #include "device_common.cuh"
@@ -32,35 +39,6 @@ namespace st {
 struct NQ {
     float w, x, y, z;
 };
-
-__device__ __forceinline__ NQ nq_mul(const NQ& a, const NQ& b) {
-    NQ o;
-    o.w = a.w + b.w + (a.w * b.w - (a.x * b.x + a.y * b.y + a.z * b.z));
-    o.x = a.x + b.x + (a.w * b.x + b.w * a.x + (a.y * b.z - a.z * b.y));
-    o.y = a.y + b.y + (a.w * b.y + b.w * a.y + (a.z * b.x - a.x * b.z));
-    o.z = a.z + b.z + (a.w * b.z + b.w * a.z + (a.x * b.y - a.y * b.x));
-    return o;
-}
-
-__device__ __forceinline__ NQ nq_square(const NQ& a) {
-    const float t = 2.0f * (1.0f + a.w);
-    NQ o;
-    o.w = 2.0f * a.w + (a.w * a.w - (a.x * a.x + a.y * a.y + a.z * a.z));
-    o.x = t * a.x;
-    o.y = t * a.y;
-    o.z = t * a.z;
-    return o;
-}
-
-__device__ __forceinline__ NQ nq_normalize(const NQ& a) {
-    const float eps = 2.0f * a.w + (a.w * a.w + a.x * a.x + a.y * a.y + a.z * a.z);   // |q|^2 - 1
-    float g;   // (1 + eps)^(-1/2) - 1
-    if (fabsf(eps) < 1e-3f)
-        g = eps * fmaf(eps, fmaf(eps, -0.3125f, 0.375f), -0.5f);
-    else
-        g = rsqrtf(1.0f + eps) - 1.0f;
-    return NQ{a.w + g * (1.0f + a.w), a.x + g * a.x, a.y + g * a.y, a.z + g * a.z};
-}
 
 // Rotation q(b) of a small rotation vector b as a near-identity quaternion:
 // (cos(t/2) - 1, sin(t/2)/t b), t = |b|, Taylor series in u = t^2.
@@ -80,21 +58,97 @@ __device__ __forceinline__ NQ nq_from_small_rotvec(float bx, float by, float bz)
     return NQ{cm1, S * bx, S * by, S * bz};
 }
 
-// Deviation e = r^-1 q(a + b) of the edge rotation from the reference
-// rotation r = q(a), a = alpha y^, for a small deviation vector b:
+// ---- near-identity quaternions with a compensated vector part ---------------
+// w = scalar - 1 (second order) in FP32; x, y, z as (hi, lo).
+struct CNQ {
+    float w;
+    FF x, y, z;
+};
+
+__device__ __forceinline__ FF ff_scale2(const FF& a, float p2) { return FF{a.hi * p2, a.lo * p2}; }   // p2 a power of 2
+
+// later rotation a on the left: a b; first-order sums a.v + b.v compensated,
+// second-order terms in FP32
+__device__ __forceinline__ CNQ cnq_mul(const CNQ& a, const CNQ& b) {
+    const float ax = a.x.hi, ay = a.y.hi, az = a.z.hi, bx = b.x.hi, by = b.y.hi, bz = b.z.hi;
+    CNQ o;
+    o.w = a.w + b.w + (a.w * b.w - (ax * bx + ay * by + az * bz));
+    o.x = ff_add3(a.x, b.x, a.w * bx + b.w * ax + (ay * bz - az * by));
+    o.y = ff_add3(a.y, b.y, a.w * by + b.w * ay + (az * bx - ax * bz));
+    o.z = ff_add3(a.z, b.z, a.w * bz + b.w * az + (ax * by - ay * bx));
+    return o;
+}
+
+__device__ __forceinline__ CNQ cnq_square(const CNQ& a) {
+    const float ax = a.x.hi, ay = a.y.hi, az = a.z.hi;
+    CNQ o;
+    o.w = 2.0f * a.w + (a.w * a.w - (ax * ax + ay * ay + az * az));
+    const float t = 2.0f * a.w;
+    o.x = ff_add_f(ff_scale2(a.x, 2.0f), t * ax);
+    o.y = ff_add_f(ff_scale2(a.y, 2.0f), t * ay);
+    o.z = ff_add_f(ff_scale2(a.z, 2.0f), t * az);
+    return o;
+}
+
+__device__ __forceinline__ CNQ cnq_normalize(const CNQ& a) {
+    const float ax = a.x.hi, ay = a.y.hi, az = a.z.hi;
+    const float eps = 2.0f * a.w + (a.w * a.w + ax * ax + ay * ay + az * az);   // |q|^2 - 1
+    float g;   // (1 + eps)^(-1/2) - 1
+    if (fabsf(eps) < 1e-3f)
+        g = eps * fmaf(eps, fmaf(eps, -0.3125f, 0.375f), -0.5f);
+    else
+        g = rsqrtf(1.0f + eps) - 1.0f;
+    return CNQ{a.w + g * (1.0f + a.w), ff_add_f(a.x, g * ax), ff_add_f(a.y, g * ay), ff_add_f(a.z, g * az)};
+}
+
+// q(b) for a small rotation vector b: (cos(t/2) - 1, S b), S = sin(t/2)/t =
+// 1/2 + O(t^2): the first-order part b/2 exact, the rest in FP32
+__device__ __forceinline__ CNQ cnq_from_rotvec(const FF& bx, const FF& by, float bz) {
+    const NQ e = nq_from_small_rotvec(bx.hi, by.hi, bz);
+    const float u = bx.hi * bx.hi + by.hi * by.hi + bz * bz;
+    // S - 1/2 from the same series (u is tiny for these edges)
+    const float Sm = u * fmaf(u, fmaf(u, -1.0f / 645120.0f, 1.0f / 3840.0f), -1.0f / 48.0f);
+    CNQ o;
+    o.w = e.w;
+    if (u < 0.01f) {
+        o.x = ff_add_f(ff_scale2(bx, 0.5f), Sm * bx.hi);
+        o.y = ff_add_f(ff_scale2(by, 0.5f), Sm * by.hi);
+    } else {
+        o.x = FF{e.x, 0.0f};
+        o.y = FF{e.y, 0.0f};
+    }
+    o.z = FF{e.z, 0.0f};
+    return o;
+}
+
+// Deviation e = r^-1 q(a + b) of an edge rotation from the reference rotation
+// r = q(a), a = alpha y^, for a small deviation vector b:
 //   e_w = c C + s S (alpha + b_y),  e_v = c S (a + b) - C s y^ - s S y^ x (a + b)
 // with c, s = cos, sin(alpha/2), C = cos(|a+b|/2), S = sin(|a+b|/2)/|a+b|,
-// written in the differences C - c and S - S(alpha^2).
-__device__ __forceinline__ NQ nq_deviation(const MixWeight& W, float bx, float by, float bz) {
-    const float du = fmaf(2.0f * W.alpha, by, bx * bx + by * by + bz * bz);   // |a+b|^2 - alpha^2
-    const float dC = du * fmaf(du, fmaf(du, fmaf(du, W.dC[3], W.dC[2]), W.dC[1]), W.dC[0]);
-    const float dS = du * fmaf(du, fmaf(du, fmaf(du, W.dS[3], W.dS[2]), W.dS[1]), W.dS[0]);
+// written in the differences C - c and S - S(alpha^2) (Taylor series in
+// du = |a+b|^2 - alpha^2, MIX_TAYLOR terms); e_y = Ky b_y compensated + the
+// terms of second and higher order in b (FP32).
+__device__ __forceinline__ CNQ cnq_deviation(const MixWeight& W, float bx, const FF& byf, float bz) {
+    const float by = byf.hi;
+    const float bb = bx * bx + by * by + bz * bz;
+    const float du = fmaf(2.0f * W.alpha, by, bb);   // |a+b|^2 - alpha^2
+    // dC = du (dC0 + du tC), dS = du (dS0 + du tS), tails by Horner
+    float tC = W.dC[MIX_TAYLOR - 1], tS = W.dS[MIX_TAYLOR - 1];
+#pragma unroll
+    for (int n = MIX_TAYLOR - 2; n >= 1; --n) {
+        tC = fmaf(du, tC, W.dC[n]);
+        tS = fmaf(du, tS, W.dS[n]);
+    }
+    const float dC = du * fmaf(du, tC, W.dC[0]);
+    const float dS = du * fmaf(du, tS, W.dS[0]);
     const float S = W.S0 + dS;
-    NQ e;
+    CNQ e;
     e.w = W.ch * dC + W.sh * (W.alpha * dS + S * by);
-    e.x = S * (W.ch * bx - W.sh * bz);
-    e.y = W.ch * (W.alpha * dS + S * by) - W.sh * dC;
-    e.z = S * (W.ch * bz + W.sh * bx);
+    // e_y = Ky b_y + Kq |b|^2 + du^2 (ch alpha tS - sh tC) + ch dS b_y
+    const float rest = fmaf(W.Kq, bb, fmaf(du * du, W.ch * W.alpha * tS - W.sh * tC, W.ch * dS * by));
+    e.y = ff_addn(ff_mul(FF{W.Ky.x, W.Ky.y}, byf), rest);
+    e.x = FF{S * (W.ch * bx - W.sh * bz), 0.0f};
+    e.z = FF{S * (W.ch * bz + W.sh * bx), 0.0f};
     return e;
 }
 
@@ -103,17 +157,18 @@ struct FQ {
     FF w, x, y, z;
 };
 
-// Q <- (1 + D) Q for a near-identity D: Q + D Q, the correction D Q in FP32
-__device__ __forceinline__ void fq_premul_nq(FQ& q, const NQ& d) {
+// Q <- (1 + D) Q for a near-identity D with compensated vector part: the
+// first-order products D.v Q compensated, D.w Q (second order) in FP32
+__device__ __forceinline__ void fq_premul_cnq(FQ& q, const CNQ& d) {
     const float qw = q.w.hi, qx = q.x.hi, qy = q.y.hi, qz = q.z.hi;
-    const float cw = d.w * qw - (d.x * qx + d.y * qy + d.z * qz);
-    const float cx = d.w * qx + qw * d.x + (d.y * qz - d.z * qy);
-    const float cy = d.w * qy + qw * d.y + (d.z * qx - d.x * qz);
-    const float cz = d.w * qz + qw * d.z + (d.x * qy - d.y * qx);
-    q.w = ff_add_f(q.w, cw);
-    q.x = ff_add_f(q.x, cx);
-    q.y = ff_add_f(q.y, cy);
-    q.z = ff_add_f(q.z, cz);
+    const FF cw = ff_addlo(ff_neg(ff_add_lazy(ff_add_lazy(ff_mul(d.x, q.x), ff_mul(d.y, q.y)), ff_mul(d.z, q.z))), d.w * qw);
+    const FF cx = ff_addlo(ff_add_lazy(ff_add_lazy(ff_mul(d.x, q.w), ff_mul(d.y, q.z)), ff_neg(ff_mul(d.z, q.y))), d.w * qx);
+    const FF cy = ff_addlo(ff_add_lazy(ff_add_lazy(ff_mul(d.y, q.w), ff_mul(d.z, q.x)), ff_neg(ff_mul(d.x, q.z))), d.w * qy);
+    const FF cz = ff_addlo(ff_add_lazy(ff_add_lazy(ff_mul(d.z, q.w), ff_mul(d.x, q.y)), ff_neg(ff_mul(d.y, q.x))), d.w * qz);
+    q.w = ff_add(q.w, cw);
+    q.x = ff_add(q.x, cx);
+    q.y = ff_add(q.y, cy);
+    q.z = ff_add(q.z, cz);
 }
 
 // Q <- R Q for a compensated reference rotation R
@@ -130,7 +185,9 @@ __device__ __forceinline__ void fq_premul_ref(FQ& q, const float2* rq) {
 // ---- per-particle constants ---------------------------------------------------
 struct MConst {
     FF invP, tau, PM1;                     // 1/P; 1/beta0 - (1/beta0 + Pt)/P; P - 1
-    float Pt, P2, P2m1, invPf, P, b0pt, a, c, da, f3, a0;
+    FF aP, a0P, c1P;                       // a/P, a0/P, c1/P (spin: first-order coefficients)
+    FF invP2, Ptf, b0ptf;                  // 1/P^2, Pt, 1/beta0 + Pt
+    float Pt, P2, P2m1, invPf, P, b0pt, a, c, da, f3, a0, c1;
 };
 
 struct MState {
@@ -158,14 +215,23 @@ __device__ __forceinline__ void drift_inc(MState& z, const MConst& k, const FF& 
     z.T = ff_add(z.T, ff_mul(L, ff_add_f(k.tau, -k.b0pt * d)));
 }
 
-// precession vector for a straight element with field b = (bx, by, 0)
-__device__ __forceinline__ void omega_straight(const MConst& k, float px, float py, float bx, float by, float ips,
-                                               float Ps, float& ox, float& oy, float& os) {
-    const float ub = (px * bx + py * by) * k.invPf;
-    const float cu = k.c * ub * k.invPf;
-    ox = -ips * (k.a * bx - cu * px);
-    oy = -ips * (k.a * by - cu * py);
-    os = ips * cu * Ps;
+// Edge rotation vector b = w Omega (Eq. (6b)) in a straight element with field
+// b = (k1 Y + k2 X Y, k1 X + k2 (X^2 - Y^2)/2, 0): the quadrupole part of the
+// first order, -w (a/P) k1 (Y, X), compensated (Aw = w (a/P) k1); the rest,
+// -w [(a/P) b_sext + a (1/Ps - 1/P) b - (c (u.b)/P) p / Ps], in FP32;
+// d = 1/Ps - 1/P.
+__device__ __forceinline__ void straight_edge(const MConst& k, const MState& z, float k1, float k2, const FF& Aw,
+                                              float w, float d, float ips, float Ps, FF& bx, FF& by, float& bz) {
+    const float X = z.X.hi, Y = z.Y.hi, px = z.Px.hi, py = z.Py.hi;
+    const float sx = k2 * X * Y, sy = 0.5f * k2 * (X * X - Y * Y);
+    const float fbx = k1 * Y + sx, fby = k1 * X + sy;
+    const float cu = k.c * ((px * fbx + py * fby) * k.invPf) * k.invPf;
+    const float aPf = k.aP.hi;
+    const float remx = -aPf * sx - d * k.a * fbx + ips * cu * px;
+    const float remy = -aPf * sy - d * k.a * fby + ips * cu * py;
+    bx = ff_addn(ff_neg(ff_mul(Aw, z.Y)), w * remx);
+    by = ff_addn(ff_neg(ff_mul(Aw, z.X)), w * remy);
+    bz = w * ips * cu * Ps;
 }
 
 // cached matrix-kick coefficients of the half-slice linear flow (computed in
@@ -231,42 +297,44 @@ __device__ __forceinline__ void quad_linear_inc(MState& z, const MConst& k, cons
 
 template <int K>
 struct MixLevels {
-    NQ q[K + 1];
+    CNQ q[K + 1];
 
-    // straight elements (no reference rotation): levels by squaring
-    __device__ __forceinline__ void add_straight(int i, int N, float ds, float ox, float oy, float os) {
-        const float w = (i == 0 || i == N) ? 0.5f * ds : ds;
-        NQ e = nq_from_small_rotvec(w * ox, w * oy, w * os);
+    // straight elements (no reference rotation): edge rotation vector b of the
+    // finest level (x, y compensated); coarser levels by squaring
+    __device__ __forceinline__ void add_straight(int i, const FF& bx, const FF& by, float bz) {
+        CNQ e = cnq_from_rotvec(bx, by, bz);
         if (i == 0) {
             q[K] = e;
 #pragma unroll
             for (int m = 1; m <= K; ++m) {
-                e = nq_square(e);
+                e = cnq_square(e);
                 q[K - m] = e;
             }
             return;
         }
-        q[K] = nq_mul(e, q[K]);
+        q[K] = cnq_mul(e, q[K]);
 #pragma unroll
         for (int m = 1; m <= K; ++m) {
             if (i & ((1 << m) - 1)) break;
-            e = nq_square(e);
-            q[K - m] = nq_mul(e, q[K - m]);
+            e = cnq_square(e);
+            q[K - m] = cnq_mul(e, q[K - m]);
         }
     }
 
     // bends: for every level sampling edge i, the deviation of the level's edge
     // rotation from its reference rotation, conjugated by the reference
     // rotation accumulated over the level's earlier edges (angle
-    // omr i ds - alpha_m, the trapezoid end weight alpha_m = omr 2^m ds / 2)
+    // omr i ds - alpha_m, the trapezoid end weight alpha_m = omr 2^m ds / 2);
+    // the deviation of Omega is (dox, doy, dos) with doy compensated
     __device__ __forceinline__ void add_bend(int i, int N, const MixElem& el, float rc, float rs, float dox,
-                                             float doy, float dos) {
+                                             const FF& doy, float dos) {
 #pragma unroll
         for (int m = 0; m <= K; ++m) {
             if (m > 0 && (i & ((1 << m) - 1))) break;
             const int j = (i == 0 || i == N) ? m : m + 1;
             const float w = ldexpf(el.ds, j) * 0.5f;
-            NQ e = nq_deviation(el.w[j], w * dox, w * doy, w * dos);
+            const FF wf{ldexpf(el.ds_ff.x, j - 1), ldexpf(el.ds_ff.y, j - 1)};
+            CNQ e = cnq_deviation(el.w[j], w * dox, ff_mul(wf, doy), w * dos);
             if (i == 0) {
                 q[K - m] = e;
                 continue;
@@ -274,35 +342,37 @@ struct MixLevels {
             const MixWeight& Wm = el.w[m];
             const float cphi = rc * Wm.cf + rs * Wm.sf;
             const float sphi = rs * Wm.cf - rc * Wm.sf;
-            const float ex = e.x * cphi - e.z * sphi;
-            const float ez = e.x * sphi + e.z * cphi;
-            e.x = ex;
-            e.z = ez;
-            q[K - m] = nq_mul(e, q[K - m]);
+            const float ex = e.x.hi * cphi - e.z.hi * sphi;
+            const float ez = e.x.hi * sphi + e.z.hi * cphi;
+            e.x = FF{ex, 0.0f};
+            e.z = FF{ez, 0.0f};
+            q[K - m] = cnq_mul(e, q[K - m]);
         }
     }
 
-    __device__ __forceinline__ NQ romberg() {
+    // Romberg table on the deviations (Eq. (39)): q_k <- (4^j q_k - q_{k-1}) / (4^j - 1)
+    __device__ __forceinline__ CNQ romberg() {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const float f = (float)(1 << (2 * (j + 1)));
             const float inv = 1.0f / (f - 1.0f);
+            const FF invf{inv, fmaf(-inv, f - 1.0f, 1.0f) * inv};   // 1/(f-1) to ~2^-46
 #pragma unroll
             for (int k = K; k >= j + 1; --k) {
                 q[k].w = (f * q[k].w - q[k - 1].w) * inv;
-                q[k].x = (f * q[k].x - q[k - 1].x) * inv;
-                q[k].y = (f * q[k].y - q[k - 1].y) * inv;
-                q[k].z = (f * q[k].z - q[k - 1].z) * inv;
+                q[k].x = ff_mul(ff_add_lazy(ff_scale2(q[k].x, f), ff_neg(q[k - 1].x)), invf);
+                q[k].y = ff_mul(ff_add_lazy(ff_scale2(q[k].y, f), ff_neg(q[k - 1].y)), invf);
+                q[k].z = ff_mul(ff_add_lazy(ff_scale2(q[k].z, f), ff_neg(q[k - 1].z)), invf);
             }
         }
-        return nq_normalize(q[K]);
+        return cnq_normalize(q[K]);
     }
 };
 
 // Track particle i for n_turns turns through the mixed-precision tables in
 // shared memory (table, seq, rho); state in the FP64 pair-SoA arrays.
 template <int K>
-__device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__ table,
+__device__ __noinline__ void mixed_track_particle(const MixElem* __restrict__ table,
                                                      const uint16_t* __restrict__ seq,
                                                      const float2* __restrict__ rho, int n_seq, const RefConst& ref,
                                                      double2* __restrict__ xpx, double2* __restrict__ ypy,
@@ -344,6 +414,17 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
         k.da = (float)(ref.G * ref.gamma0 * ref.beta0 * Pt);
         k.f3 = (float)(0.5 * b0pt * invP64 * invP64 * invP64);
         k.a0 = (float)(1.0 + ref.G * ref.gamma0);
+        // a0 (P - 1) - da: the energy deviation's first-order terms of the bend's
+        // Omega_y, which cancel to O(Pt) for G gamma >> 1, combined in FP64
+        const double a0d = 1.0 + ref.G * ref.gamma0;
+        const double c1 = a0d * (P2m1 / (P + 1.0)) - ref.G * ref.gamma0 * ref.beta0 * Pt;
+        k.c1 = (float)c1;
+        k.aP = ff_make((1.0 + ref.G * gamma) * invP64);
+        k.a0P = ff_make(a0d * invP64);
+        k.c1P = ff_make(c1 * invP64);
+        k.invP2 = ff_make(1.0 / P2);
+        k.Ptf = ff_make(Pt);
+        k.b0ptf = ff_make(b0pt);
     }
     v = sxy[i];
     double sx = v.x, sy = v.y, sz = szp[i];
@@ -377,12 +458,11 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
             }
             const int N = el.n_slices;
             const float ds = el.ds;
-            float ox, oy, os;
+            float ox, os;
             if (type == ST_SBEND) {
                 const float h = el.h, eta = el.eta;
                 const float py = z.Py.hi;
                 const float Pa2 = k.P2 - py * py;
-                const float iPa2 = 1.0f / Pa2;
                 float px = z.Px.hi;
                 float ps2 = Pa2 - px * px;
                 float ips = rsqrtf(ps2);
@@ -397,59 +477,86 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 const FF cbmieh{el.cbmieh_ff.x, el.cbmieh_ff.y};
                 const FF etahff{el.etah_ff.x, el.etah_ff.y};
                 const FF omeff{el.ome_ff.x, el.ome_ff.y};
-                const float dT0 = -el.ieta * k.Pt * ds + el.dT_eta;
+                // T increment of the bend without the path term: (1 - 1/eta) ds/beta0 - Pt ds/eta
+                const FF dT0 = ff_add(FF{el.dTeta_ff.x, el.dTeta_ff.y}, ff_neg(ff_mul(k.Ptf, ietads)));
+                const FF cbm1ff{el.cbm1_ff.x, el.cbm1_ff.y};
+                // 1/P_a^2 = (1/P^2) / (1 - Py^2/P^2), compensated (the correction is tiny)
+                const float epy = py * py * k.invPf * k.invPf;
+                const FF iPa2ff = ff_add_f(k.invP2, k.invP2.hi * epy * (1.0f + epy));
                 // deviation of Omega (Eq. (6b)) from the on-axis reference:
-                //   dOy = eta h [a0 (Ps - 1 - hX) - (1 + hX) (a - a0)] / Ps + (1 + hX) cu Py / Ps
+                //   dOy = eta h N / Ps + (1 + hX) cu Py / Ps,
+                //     N = a0 (Ps - 1 - hX) - (1 + hX) (a - a0) = c1 + a0 (Ps - P) - hX (a0 + da),
+                //     c1 = a0 (P - 1) - da (per particle, FP64: its two terms cancel to O(Pt));
+                //   its first-order part eta h c1 / P - (eta h^2 a0 / P) X compensated, the rest
+                //   eta h [(a0 (Ps - P) - hX da) / P + N (1/Ps - 1/P)] + (1 + hX) cu Py / Ps in FP32;
                 //   dOx = (1 + hX) cu Px / Ps,  dOs = (1 + hX) cu
-                auto dev_omega = [&](float X, float Pxv, float Psv, float PsM1v, float ipsv, float& dx, float& dy,
-                                     float& dz) {
-                    const float hX = h * X;
+                const FF B0 = ff_mul(etahff, k.c1P);
+                const FF B1 = ff_mul(FF{el.eh2_ff.x, el.eh2_ff.y}, k.a0P);
+                const float apda = k.a0 + k.da;
+                auto dev_omega = [&](const FF& Xf, float Pxv, float Psv, float ipsv, float& dx, FF& dy, float& dz) {
+                    const float hX = h * Xf.hi;
                     const float g = (1.0f + hX) * ipsv;
-                    dy = etah * (k.a0 * (PsM1v - hX) * ipsv - g * k.da) + g * cu * py;
+                    const float dPsP = -(Pxv * Pxv + py * py) / (Psv + k.P);   // Ps - P
+                    const float dd = -dPsP * k.invPf * ipsv;                  // 1/Ps - 1/P
+                    const float Nf = k.c1 + k.a0 * dPsP - hX * apda;
+                    const float rest = etah * ((k.a0 * dPsP - hX * k.da) * k.invPf + Nf * dd) + g * cu * py;
+                    dy = ff_addn(ff_add(B0, ff_neg(ff_mul(B1, Xf))), rest);
                     dx = g * cu * Pxv;
                     dz = g * cu * Psv;
                 };
-                dev_omega(z.X.hi, px, Ps, PsM1.hi, ips, ox, oy, os);
+                FF oyf;
+                dev_omega(z.X, px, Ps, ips, ox, oyf, os);
                 const float2* rh = rho + el.rho_off;
-                lv.add_bend(0, N, el, 1.0f, 0.0f, ox, oy, os);
+                lv.add_bend(0, N, el, 1.0f, 0.0f, ox, oyf, os);
                 for (int s = 1; s <= N; ++s) {
                     // exact bend over ds, Eq. (10): (Px, A = Ps - eta(1+hX)) rotates by h ds;
                     // dX = (dPs - dA)/(eta h) with dA = A (cos - 1) - Px sin
                     // A = (Ps - 1) + (1 - eta) - eta h X, compensated (first order in the
                     // momentum deviation and in X)
                     const FF Aff = ff_add(ff_add(PsM1, omeff), ff_neg(ff_mul(etahff, z.X)));
-                    const float A = Aff.hi;
-                    const FF dPxff = ff_add_f(ff_mul(Aff, sbff), px * el.cbm1);
+                    const FF dPxff = ff_add(ff_mul(Aff, sbff), ff_mul(z.Px, cbm1ff));
+                    // dPx / (eta h) = A sin(h ds)/(eta h) + Px (cos(h ds) - 1)/(eta h)
+                    const FF dPxieh = ff_add(ff_mul(Aff, sbieh), ff_mul(z.Px, cbmieh));
                     const float dPx = dPxff.hi;
                     const float pxf = px + dPx;
                     const float ps2f = Pa2 - pxf * pxf;
                     const float ipsf = rsqrtf(ps2f);
                     const float Psf = ps2f * ipsf;
-                    const float dPs = -dPx * (px + pxf) / (Ps + Psf);
-                    const float sd = (px * dPs - dPx * Ps) * iPa2;   // sin(psi_i - psi_f)
-                    float dpsi;
+                    const FF PsfM1 = ff_add_f(k.PM1, -(pxf * pxf + py * py) / (Psf + k.P));
+                    // The second-order terms below carry the factor 1/(eta h) (hundreds of
+                    // metres in a large ring), so they are compensated as well.
+                    // Q = (Ps_f - Ps)/(eta h) = -dPx/(eta h) (Px + Px_f) / (Ps + Ps_f), with
+                    // 1/(Ps + Ps_f) = (1/2) / (1 + u/2), u = (Ps - 1) + (Ps_f - 1)
+                    const float hu = 0.5f * (PsM1.hi + PsfM1.hi);
+                    const FF invden = ff_add_f(FF{0.5f, 0.0f}, -0.5f * hu * fmaf(hu, hu - 1.0f, 1.0f));
+                    const FF pxsum = ff_add(ff_scale2(z.Px, 2.0f), dPxff);
+                    const FF Q = ff_neg(ff_mul(ff_mul(dPxieh, pxsum), invden));
+                    // sin(psi_i - psi_f)/(eta h) = (Px Q - dPx/(eta h) Ps) / P_a^2
+                    const FF Psff = ff_add_f(PsM1, 1.0f);
+                    const FF sdieh = ff_mul(ff_add_f(ff_neg(ff_mul(dPxieh, Psff)), px * Q.hi), iPa2ff);
+                    const float sd = sdieh.hi * etah;
+                    FF dpsieh;   // (psi_i - psi_f)/(eta h)
                     if (fabsf(sd) < 1e-2f) {
                         const float x2 = sd * sd;
-                        dpsi = sd * fmaf(x2, fmaf(x2, 3.0f / 40.0f, 1.0f / 6.0f), 1.0f);
+                        dpsieh = ff_add_f(sdieh, sdieh.hi * x2 * fmaf(x2, 3.0f / 40.0f, 1.0f / 6.0f));
                     } else {
-                        dpsi = asinf(sd);
+                        dpsieh = FF{asinf(sd) / etah, 0.0f};
                     }
                     // dX = (dPs - dA)/(eta h), dA = A (cos - 1) - Px sin
-                    const FF dX = ff_add_f(ff_add(ff_mul(z.Px, sbieh), ff_neg(ff_mul(Aff, cbmieh))), dPs * el.ieh);
-                    const FF dY = ff_add_f(ff_mul(z.Py, ietads), el.ieh * py * dpsi);
+                    const FF dX = ff_add(ff_add(ff_mul(z.Px, sbieh), ff_neg(ff_mul(Aff, cbmieh))), Q);
+                    const FF dY = ff_mul(z.Py, ff_add(ietads, dpsieh));
                     z.X = ff_add(z.X, dX);
                     z.Px = ff_add(z.Px, dPxff);
                     z.Y = ff_add(z.Y, dY);
-                    z.T = ff_add_f(z.T, dT0 - el.ieh * k.b0pt * dpsi);
-                    (void)A;
+                    z.T = ff_add(z.T, ff_add(dT0, ff_neg(ff_mul(k.b0ptf, dpsieh))));
                     px = z.Px.hi;
                     ps2 = Pa2 - px * px;
                     ips = rsqrtf(ps2);
                     Ps = ps2 * ips;
                     PsM1 = ff_add_f(k.PM1, -(px * px + py * py) / (Ps + k.P));
-                    dev_omega(z.X.hi, px, Ps, PsM1.hi, ips, ox, oy, os);
+                    dev_omega(z.X, px, Ps, ips, ox, oyf, os);
                     const float2 r = rh[s];
-                    lv.add_bend(s, N, el, r.x, r.y, ox, oy, os);
+                    lv.add_bend(s, N, el, r.x, r.y, ox, oyf, os);
                 }
             } else if (type == ST_MULT) {
                 const float k1 = el.k1, k2 = el.k2;
@@ -459,13 +566,13 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 const FF k2ds{el.k2ds_ff.x, el.k2ds_ff.y};
                 FF ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                 float ips = ips_ff.hi, Ps = (k.P2 - pp) * ips;
+                const FF Aw = ff_mul(k.aP, k1ds);   // (a/P) k1 ds
                 {
-                    const float X = z.X.hi, Y = z.Y.hi;
-                    const float bx = k1 * Y + k2 * X * Y;
-                    const float by = k1 * X + 0.5f * k2 * (X * X - Y * Y);
-                    omega_straight(k, z.Px.hi, z.Py.hi, bx, by, ips, Ps, ox, oy, os);
+                    FF bx, by;
+                    float bz;
+                    straight_edge(k, z, k1, k2, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
+                    lv.add_straight(0, bx, by, bz);
                 }
-                lv.add_straight(0, N, ds, ox, oy, os);
                 for (int s = 1; s <= N; ++s) {
                     drift_inc(z, k, half, ips_ff, d);
                     {
@@ -481,11 +588,13 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     ips = ips_ff.hi;
                     Ps = (k.P2 - pp) * ips;
                     drift_inc(z, k, half, ips_ff, d);
-                    const float X = z.X.hi, Y = z.Y.hi;
-                    const float bx = k1 * Y + k2 * X * Y;
-                    const float by = k1 * X + 0.5f * k2 * (X * X - Y * Y);
-                    omega_straight(k, z.Px.hi, z.Py.hi, bx, by, ips, Ps, ox, oy, os);
-                    lv.add_straight(s, N, ds, ox, oy, os);
+                    FF bx, by;
+                    float bz;
+                    if (s == N)
+                        straight_edge(k, z, k1, k2, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
+                    else
+                        straight_edge(k, z, k1, k2, Aw, ds, d, ips, Ps, bx, by, bz);
+                    lv.add_straight(s, bx, by, bz);
                 }
             } else {   // ST_QUAD_MK
                 const float k1 = el.k1, absk = el.k2;
@@ -495,9 +604,16 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                                  0.5 * ((double)el.ds_ff.x + (double)el.ds_ff.y), absk, half);
                 FF ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                 float ips = ips_ff.hi, Ps = (k.P2 - pp) * ips;
-                omega_straight(k, z.Px.hi, z.Py.hi, k1 * z.Y.hi, k1 * z.X.hi, ips, Ps, ox, oy, os);
-                lv.add_straight(0, N, ds, ox, oy, os);
                 const FF dsff{el.ds_ff.x, el.ds_ff.y};
+                // (a/P) k1 ds, compensated: the first-order rotation per unit Y (x) and X (y)
+                const FF Aw = ff_mul_f(ff_mul(ff_mul(k.aP, FF{el.k1ds_ff.x, el.k1ds_ff.y}), dsff),
+                                       k1 >= 0.0f ? 1.0f : -1.0f);
+                {
+                    FF bx, by;
+                    float bz;
+                    straight_edge(k, z, k1, 0.0f, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
+                    lv.add_straight(0, bx, by, bz);
+                }
                 for (int s = 1; s <= N; ++s) {
                     quad_linear_inc(z, k, mq, k1);
                     inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
@@ -510,18 +626,23 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                     ips = ips_ff.hi;
                     Ps = (k.P2 - pp) * ips;
-                    omega_straight(k, z.Px.hi, z.Py.hi, k1 * z.Y.hi, k1 * z.X.hi, ips, Ps, ox, oy, os);
-                    lv.add_straight(s, N, ds, ox, oy, os);
+                    FF bx, by;
+                    float bz;
+                    if (s == N)
+                        straight_edge(k, z, k1, 0.0f, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
+                    else
+                        straight_edge(k, z, k1, 0.0f, Aw, ds, d, ips, Ps, bx, by, bz);
+                    lv.add_straight(s, bx, by, bz);
                 }
             }
-            const NQ dq = lv.romberg();
-            if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi + dq.w + dq.x + dq.y + dq.z)) {
+            const CNQ dq = lv.romberg();
+            if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi + dq.w + dq.x.hi + dq.y.hi + dq.z.hi)) {
                 z = z0;
                 is_lost = true;
                 break;
             }
             // element rotation R_L (1 + D) into the compensated turn quaternion
-            fq_premul_nq(qt, dq);
+            fq_premul_cnq(qt, dq);
             if (type == ST_SBEND) fq_premul_ref(qt, el.rq);
         }
         // FP64 once per turn: compose, renormalise, rotate the spin (a particle lost

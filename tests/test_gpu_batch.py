@@ -12,6 +12,12 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-11
+# The mixed integrator is one non-inlined function shared by the batched and
+# single-job kernels, so both give the same results; the mixed results are
+# also checked against the FP64 tracker within the mixed tracker's accuracy on
+# these few-cell rings at G gamma up to 487 (~1e-8 after a few turns).
+TOL_MIXED = 1e-11
+MIXED_VS_FP64 = 1e-7
 
 
 def small_jobs(n_jobs=6, seed=5):
@@ -41,7 +47,12 @@ def test_batch_equals_single_job_tracking(precision, use_graph):
         zb, Sb, lb = b.download(k)
         zs, Ss, ls = st.track(j["ring"], *inputs[k], 3, 2, precision=precision)
         assert np.array_equal(lb, ls)
-        assert np.abs(zb - zs).max() < TOL and np.abs(Sb - Ss).max() < TOL, (k, precision)
+        tol = TOL if precision == "fp64" else TOL_MIXED
+        assert np.abs(zb - zs).max() < tol and np.abs(Sb - Ss).max() < tol, (k, precision)
+        if precision == "mixed":
+            zf, Sf, lf = st.track(j["ring"], *inputs[k], 3, 2, precision="fp64")
+            assert np.array_equal(lb, lf)
+            assert np.abs(Sb - Sf).max() < MIXED_VS_FP64 and np.abs(zb[:4] - zf[:4]).max() < MIXED_VS_FP64
     b.close()
 
 
