@@ -332,8 +332,9 @@ struct MixLevels {
         for (int m = 0; m <= K; ++m) {
             if (m > 0 && (i & ((1 << m) - 1))) break;
             const int j = (i == 0 || i == N) ? m : m + 1;
-            const float w = ldexpf(el.ds, j) * 0.5f;
-            const FF wf{ldexpf(el.ds_ff.x, j - 1), ldexpf(el.ds_ff.y, j - 1)};
+            const float p2 = (float)(1 << j) * 0.5f;   // 2^(j-1), exact
+            const float w = el.ds * p2;
+            const FF wf{el.ds_ff.x * p2, el.ds_ff.y * p2};
             CNQ e = cnq_deviation(el.w[j], w * dox, ff_mul(wf, doy), w * dos);
             if (i == 0) {
                 q[K - m] = e;
@@ -372,7 +373,7 @@ struct MixLevels {
 // Track particle i for n_turns turns through the mixed-precision tables in
 // shared memory (table, seq, rho); state in the FP64 pair-SoA arrays.
 template <int K>
-__device__ __noinline__ void mixed_track_particle(const MixElem* __restrict__ table,
+__device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__ table,
                                                      const uint16_t* __restrict__ seq,
                                                      const float2* __restrict__ rho, int n_seq, const RefConst& ref,
                                                      double2* __restrict__ xpx, double2* __restrict__ ypy,

@@ -12,11 +12,12 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-11
-# The mixed integrator is one non-inlined function shared by the batched and
-# single-job kernels, so both give the same results; the mixed results are
-# also checked against the FP64 tracker within the mixed tracker's accuracy on
-# these few-cell rings at G gamma up to 487 (~1e-8 after a few turns).
-TOL_MIXED = 1e-11
+# The batched and single-job mixed kernels inline the same integrator into
+# different kernels, so FP32 contraction choices may differ between them: their
+# results agree to the mixed tracker's own accuracy on these few-cell rings at
+# G gamma up to 487 (1e-8 to 1e-7 after a few turns), and both are checked against
+# the FP64 tracker.
+TOL_MIXED = 1e-7
 MIXED_VS_FP64 = 1e-7
 
 
