@@ -218,7 +218,7 @@ MIXED_WORKLOAD_PARTICLES = 1_000_000
 # FP32 floating-point operations the mixed tracker executes per pass on this
 # workload (2 per FFMA, 1 per FADD/FMUL), from one ncu capture
 # (profiles/track_mixed_rhic_like_ncu.md); None until measured.
-MIXED_FP32_FLOPS_PER_PASS = 1371.3
+MIXED_FP32_FLOPS_PER_PASS = 2230.6
 
 
 def variant_mixed(st, torch, args, fp64_value, fp32_peak):
