@@ -122,10 +122,11 @@ int st_particles_upload(st_ctx* ctx, const double* z_soa, const double* spin_soa
  * ST_ECUDA on a launch failure. */
 int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order);
 
-/* Track the orbits only (FP64 maps of st_track without the spin step; spins
- * are left untouched) for n_turns >= 0 turns.  Used by the learned spin map,
- * which supplies the spin rotation per turn.  Asynchronous.  Errors as
- * st_track. */
+/* Track the orbits only (the maps of st_track without the spin step; spins
+ * are left untouched) for n_turns >= 0 turns: FP64 for an ST_FP64 context,
+ * the mixed tracker's compensated FP32 arithmetic for an ST_MIXED context.
+ * Used by the learned spin map, which supplies the spin rotation per turn.
+ * Asynchronous.  Errors as st_track. */
 int st_track_orbit(st_ctx* ctx, int32_t n_turns);
 
 /* Track one turn (as st_track with n_turns = 1) and write every particle's
@@ -305,9 +306,10 @@ int st_mlp_adam_step(st_mlp* mlp, float lr, float beta1, float beta2, float eps)
 /* Stroboscopic spin tracking with the learned map: per turn, the network
  * gives each particle's one-turn rotation from its FP64 orbit at s = 0 (head
  * in FP64), the spin is rotated by it (FP64), and the orbit is tracked
- * exactly for one turn (st_track_orbit).  spin_sum (device double [3][n], may
- * be NULL) accumulates S after every turn.  Needs an FP64 context with
- * n <= max_batch.  Asynchronous on the context stream. */
+ * for one turn (st_track_orbit: FP64 or, for an ST_MIXED context, the mixed
+ * tracker's compensated orbit).  spin_sum (device double [3][n], may be NULL)
+ * accumulates S after every turn.  Needs n <= max_batch.  Asynchronous on the
+ * context stream. */
 int st_track_surrogate(st_ctx* ctx, st_mlp* mlp, int32_t n_turns, double* spin_sum);
 
 /* Message describing the last error on the calling thread ("" if none). */

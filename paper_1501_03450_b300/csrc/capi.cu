@@ -378,7 +378,7 @@ int st_track_orbit(st_ctx* ctx, int32_t n_turns) {
         return ST_EINVAL;
     }
     if (n_turns == 0) return ST_OK;
-    return launch_track_orbit(ctx, n_turns);
+    return ctx->precision == ST_MIXED ? launch_track_mixed_orbit(ctx, n_turns) : launch_track_orbit(ctx, n_turns);
 }
 
 int st_track_one_turn_map(st_ctx* ctx, int32_t spin_order, const double* q_ref, double* q_out) {

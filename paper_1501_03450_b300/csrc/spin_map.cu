@@ -1003,8 +1003,8 @@ int st_track_surrogate(st_ctx* ctx, st_mlp* n, int32_t n_turns, double* spin_sum
         set_error("st_track_surrogate: no particles uploaded");
         return ST_ESTATE;
     }
-    if (n_turns < 0 || ctx->n > n->max_batch || ctx->precision != ST_FP64) {
-        set_error("st_track_surrogate: need n_turns >= 0, n_particles <= the network's max_batch, FP64 context");
+    if (n_turns < 0 || ctx->n > n->max_batch) {
+        set_error("st_track_surrogate: need n_turns >= 0 and n_particles <= the network's max_batch");
         return ST_EINVAL;
     }
     const int B = (int)ctx->n;
@@ -1027,7 +1027,7 @@ int st_track_surrogate(st_ctx* ctx, st_mlp* n, int32_t n_turns, double* spin_sum
             rc = cuda_fail(e, "st_track_surrogate: spin step");
             break;
         }
-        rc = launch_track_orbit(ctx, 1);
+        rc = ctx->precision == ST_MIXED ? launch_track_mixed_orbit(ctx, 1) : launch_track_orbit(ctx, 1);
     }
     n->stream = keep;
     return rc;

@@ -372,7 +372,7 @@ struct MixLevels {
 
 // Track particle i for n_turns turns through the mixed-precision tables in
 // shared memory (table, seq, rho); state in the FP64 pair-SoA arrays.
-template <int K>
+template <int K, bool SPIN = true>
 __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__ table,
                                                      const uint16_t* __restrict__ seq,
                                                      const float2* __restrict__ rho, int n_seq, const RefConst& ref,
@@ -442,7 +442,7 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
             const MixElem& el = table[seq[e]];
             const int type = el.type;
             if (type == ST_SNAKE) {
-                fq_premul_ref(qt, el.rq);
+                if constexpr (SPIN) fq_premul_ref(qt, el.rq);
                 continue;
             }
             const MState z0 = z;
@@ -506,9 +506,11 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     dz = g * cu * Psv;
                 };
                 FF oyf;
-                dev_omega(z.X, px, Ps, ips, ox, oyf, os);
                 const float2* rh = rho + el.rho_off;
-                lv.add_bend(0, N, el, 1.0f, 0.0f, ox, oyf, os);
+                if constexpr (SPIN) {
+                    dev_omega(z.X, px, Ps, ips, ox, oyf, os);
+                    lv.add_bend(0, N, el, 1.0f, 0.0f, ox, oyf, os);
+                }
                 for (int s = 1; s <= N; ++s) {
                     // exact bend over ds, Eq. (10): (Px, A = Ps - eta(1+hX)) rotates by h ds;
                     // dX = (dPs - dA)/(eta h) with dA = A (cos - 1) - Px sin
@@ -555,9 +557,11 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     ips = rsqrtf(ps2);
                     Ps = ps2 * ips;
                     PsM1 = ff_add_f(k.PM1, -(px * px + py * py) / (Ps + k.P));
-                    dev_omega(z.X, px, Ps, ips, ox, oyf, os);
-                    const float2 r = rh[s];
-                    lv.add_bend(s, N, el, r.x, r.y, ox, oyf, os);
+                    if constexpr (SPIN) {
+                        dev_omega(z.X, px, Ps, ips, ox, oyf, os);
+                        const float2 r = rh[s];
+                        lv.add_bend(s, N, el, r.x, r.y, ox, oyf, os);
+                    }
                 }
             } else if (type == ST_MULT) {
                 const float k1 = el.k1, k2 = el.k2;
@@ -568,7 +572,7 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 FF ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                 float ips = ips_ff.hi, Ps = (k.P2 - pp) * ips;
                 const FF Aw = ff_mul(k.aP, k1ds);   // (a/P) k1 ds
-                {
+                if constexpr (SPIN) {
                     FF bx, by;
                     float bz;
                     straight_edge(k, z, k1, k2, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
@@ -589,13 +593,15 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     ips = ips_ff.hi;
                     Ps = (k.P2 - pp) * ips;
                     drift_inc(z, k, half, ips_ff, d);
-                    FF bx, by;
-                    float bz;
-                    if (s == N)
-                        straight_edge(k, z, k1, k2, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
-                    else
-                        straight_edge(k, z, k1, k2, Aw, ds, d, ips, Ps, bx, by, bz);
-                    lv.add_straight(s, bx, by, bz);
+                    if constexpr (SPIN) {
+                        FF bx, by;
+                        float bz;
+                        if (s == N)
+                            straight_edge(k, z, k1, k2, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
+                        else
+                            straight_edge(k, z, k1, k2, Aw, ds, d, ips, Ps, bx, by, bz);
+                        lv.add_straight(s, bx, by, bz);
+                    }
                 }
             } else {   // ST_QUAD_MK
                 const float k1 = el.k1, absk = el.k2;
@@ -609,7 +615,7 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 // (a/P) k1 ds, compensated: the first-order rotation per unit Y (x) and X (y)
                 const FF Aw = ff_mul_f(ff_mul(ff_mul(k.aP, FF{el.k1ds_ff.x, el.k1ds_ff.y}), dsff),
                                        k1 >= 0.0f ? 1.0f : -1.0f);
-                {
+                if constexpr (SPIN) {
                     FF bx, by;
                     float bz;
                     straight_edge(k, z, k1, 0.0f, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
@@ -627,30 +633,42 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                     ips = ips_ff.hi;
                     Ps = (k.P2 - pp) * ips;
-                    FF bx, by;
-                    float bz;
-                    if (s == N)
-                        straight_edge(k, z, k1, 0.0f, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
-                    else
-                        straight_edge(k, z, k1, 0.0f, Aw, ds, d, ips, Ps, bx, by, bz);
-                    lv.add_straight(s, bx, by, bz);
+                    if constexpr (SPIN) {
+                        FF bx, by;
+                        float bz;
+                        if (s == N)
+                            straight_edge(k, z, k1, 0.0f, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
+                        else
+                            straight_edge(k, z, k1, 0.0f, Aw, ds, d, ips, Ps, bx, by, bz);
+                        lv.add_straight(s, bx, by, bz);
+                    }
                 }
             }
-            const CNQ dq = lv.romberg();
-            if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi + dq.w + dq.x.hi + dq.y.hi + dq.z.hi)) {
-                z = z0;
-                is_lost = true;
-                break;
+            if constexpr (SPIN) {
+                const CNQ dq = lv.romberg();
+                if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi + dq.w + dq.x.hi + dq.y.hi + dq.z.hi)) {
+                    z = z0;
+                    is_lost = true;
+                    break;
+                }
+                // element rotation R_L (1 + D) into the compensated turn quaternion
+                fq_premul_cnq(qt, dq);
+                if (type == ST_SBEND) fq_premul_ref(qt, el.rq);
+            } else {
+                if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi)) {
+                    z = z0;
+                    is_lost = true;
+                    break;
+                }
             }
-            // element rotation R_L (1 + D) into the compensated turn quaternion
-            fq_premul_cnq(qt, dq);
-            if (type == ST_SBEND) fq_premul_ref(qt, el.rq);
         }
         // FP64 once per turn: compose, renormalise, rotate the spin (a particle lost
         // inside the turn gets the rotation up to the element where it was lost)
-        Quat q64{ff_to_double(qt.w), ff_to_double(qt.x), ff_to_double(qt.y), ff_to_double(qt.z)};
-        q64 = qnormalize(q64);
-        rotate_vec(q64, sx, sy, sz);
+        if constexpr (SPIN) {
+            Quat q64{ff_to_double(qt.w), ff_to_double(qt.x), ff_to_double(qt.y), ff_to_double(qt.z)};
+            q64 = qnormalize(q64);
+            rotate_vec(q64, sx, sy, sz);
+        }
     }
     xpx[i] = make_double2(ff_to_double(z.X), ff_to_double(z.Px));
     ypy[i] = make_double2(ff_to_double(z.Y), ff_to_double(z.Py));

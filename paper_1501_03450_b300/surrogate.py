@@ -314,10 +314,12 @@ class SpinMapSurrogate:
         return tot / n
 
     # ------------------------------------------------------------------- use
-    def track(self, z: np.ndarray, S: np.ndarray, n_turns: int, average: bool = True, timed: bool = False):
+    def track(self, z: np.ndarray, S: np.ndarray, n_turns: int, average: bool = True, timed: bool = False,
+              orbit: str = "fp64"):
         """Stroboscopic tracking with the learned map: returns (z, S, lost,
-        <S> or None, ms)."""
-        return _run(self, z, S, n_turns, average, timed, surrogate=True)
+        <S> or None, ms).  orbit: "fp64" or "mixed" (the mixed tracker's
+        compensated orbit maps)."""
+        return _run(self, z, S, n_turns, average, timed, surrogate=True, orbit=orbit)
 
     def track_plain(self, z: np.ndarray, S: np.ndarray, n_turns: int, average: bool = True,
                     timed: bool = False):
@@ -329,11 +331,11 @@ class SpinMapSurrogate:
         self.lattice.close()
 
 
-def _run(sg: SpinMapSurrogate, z, S, n_turns, average, timed, surrogate):
+def _run(sg: SpinMapSurrogate, z, S, n_turns, average, timed, surrogate, orbit="fp64"):
     n = z.shape[1]
     if surrogate and n > sg.max_batch:
         raise ValueError("more particles than the network's max_batch")
-    tr = sg._tracker(n)
+    tr = Tracker(sg.lattice, n, orbit, sg.sp) if surrogate else sg._tracker(n)
     try:
         with torch.cuda.stream(sg.stream):
             ssum = torch.zeros((3, n), dtype=torch.float64, device="cuda") if average else None

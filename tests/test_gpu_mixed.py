@@ -105,3 +105,26 @@ def test_mixed_spin_error_1000_turns_within_1e_6(gg):
     mean, mx = spin_err(Sm, Sf)
     assert mean <= 1e-6, (mean, mx)
     assert np.abs(zm[:4] - zf[:4]).max() < 1e-6
+
+
+def test_mixed_orbit_only_tracks_the_mixed_orbit():
+    """st_track_orbit on a mixed context: the mixed tracker's compensated orbit
+    maps without the spin step (spins untouched), agreeing with the full mixed
+    tracker's orbit and with the FP64 orbit."""
+    ring = W.with_spin_order(W.rhic_like_ring(487.0, n_cells=20), 2)
+    z, S = W.gaussian_particles(700, 487.0, seed=41)
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, z.shape[1], "mixed")
+    tr.upload(z, S)
+    tr.track_orbit(10)
+    zo, So, lo = tr.download()
+    tr.close()
+    lat.close()
+    np.testing.assert_array_equal(So, S)
+    zm, _, lm = st.track(ring, z, S, 10, 2, precision="mixed")
+    zf, _, lf = st.track(ring, z, S, 10, 2, precision="fp64")
+    assert np.array_equal(lo, lm) and np.array_equal(lo, lf)
+    # the two kernels inline the same maps but may contract FP32 operations
+    # differently: agreement to the mixed orbit's own accuracy
+    assert np.abs(zo[:4] - zm[:4]).max() < 1e-9
+    assert np.abs(zo[:4] - zf[:4]).max() < 1e-9

@@ -51,3 +51,19 @@ def test_spin_error_within_1e_4_after_1000_turns_and_faster(spin_map):
     sg.mlp.set_params(p)
     dL = np.linalg.norm(Sl - Sp, axis=0)
     assert dS.mean() < 0.1 * dL.mean(), (dS.mean(), dL.mean())
+
+
+def test_surrogate_with_the_mixed_orbit(spin_map):
+    """The same map with the orbit tracked by the mixed tracker's compensated
+    orbit maps: within the same spin-error bound and faster still."""
+    w, sg = spin_map
+    gg = w["ring"]["Ggamma0"]
+    z, S = W.gaussian_particles(w["eval_particles"], gg, seed=w["seed"], cut=w["cut"])
+    T = w["eval_turns"]
+    zs, Ss, ls, avs, ms_s = sg.track(z, S, T, orbit="mixed")
+    zp, Sp, lp, avp, ms_p = sg.track_plain(z, S, T)
+    assert ls.sum() == 0
+    assert np.abs(zs[:4] - zp[:4]).max() < 1e-6
+    assert np.linalg.norm(Ss - Sp, axis=0).mean() <= 1e-4
+    assert np.linalg.norm(avs - avp, axis=0).mean() <= 1e-4
+    assert ms_s < 0.25 * ms_p, (ms_s, ms_p)
