@@ -86,13 +86,13 @@ static int get_tmap(CUtensorMap* out, const void* base, int rows, int cols, int 
     return make_tmap(out, base, rows, cols, box_rows);
 }
 
-template <int BN>
+template <int BN, int ST>
 static int launch_gemm_bn(const void* A, const void* B, int M, int N, int K, const GemmEpi& epi, int32_t* status,
                           cudaStream_t stream, int splits) {
-    using Cf = GemmCfg<BN>;
+    using Cf = GemmCfg<BN, ST>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              Cf::SMEM_BYTES);
         if (e != cudaSuccess) return cuda_fail(e, "gemm: cudaFuncSetAttribute");
         attr = true;
@@ -104,7 +104,7 @@ static int launch_gemm_bn(const void* A, const void* B, int M, int N, int K, con
     const int kblocks = K / 64;
     const int per = (kblocks + splits - 1) / splits;
     dim3 grid(M / 128, N / BN, (kblocks + per - 1) / per);
-    gemm_bf16_tn_kernel<BN><<<grid, 128, Cf::SMEM_BYTES, stream>>>(ta, tb, K, per, epi, status);
+    gemm_bf16_tn_kernel<BN, ST><<<grid, 128, Cf::SMEM_BYTES, stream>>>(ta, tb, K, per, epi, status);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ST_OK : cuda_fail(e, "gemm launch");
 }
@@ -121,11 +121,18 @@ int gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const GemmEp
         set_error("gemm: split-K needs the plain FP32 epilogue");
         return ST_EINVAL;
     }
-    if (N % 256 == 0) return launch_gemm_bn<256>(A, B, M, N, K, epi, status, stream, splits);
-    if (N % 128 == 0) return launch_gemm_bn<128>(A, B, M, N, K, epi, status, stream, splits);
-    if (N % 64 == 0) return launch_gemm_bn<64>(A, B, M, N, K, epi, status, stream, splits);
-    if (N % 32 == 0) return launch_gemm_bn<32>(A, B, M, N, K, epi, status, stream, splits);
-    return launch_gemm_bn<16>(A, B, M, N, K, epi, status, stream, splits);
+    // K blocks per CTA decide the pipeline depth; tiles of at most 128 columns
+    const int kb = K / 64, per = (kb + splits - 1) / splits;
+    if (per <= 4) {
+        if (N % 128 == 0) return launch_gemm_bn<128, 2>(A, B, M, N, K, epi, status, stream, splits);
+        if (N % 64 == 0) return launch_gemm_bn<64, 2>(A, B, M, N, K, epi, status, stream, splits);
+        if (N % 32 == 0) return launch_gemm_bn<32, 2>(A, B, M, N, K, epi, status, stream, splits);
+        return launch_gemm_bn<16, 2>(A, B, M, N, K, epi, status, stream, splits);
+    }
+    if (N % 128 == 0) return launch_gemm_bn<128, 4>(A, B, M, N, K, epi, status, stream, splits);
+    if (N % 64 == 0) return launch_gemm_bn<64, 4>(A, B, M, N, K, epi, status, stream, splits);
+    if (N % 32 == 0) return launch_gemm_bn<32, 4>(A, B, M, N, K, epi, status, stream, splits);
+    return launch_gemm_bn<16, 4>(A, B, M, N, K, epi, status, stream, splits);
 }
 
 __global__ void split_reduce_kernel(const float4* __restrict__ ws, int splits, int64_t stride4, int64_t count4,

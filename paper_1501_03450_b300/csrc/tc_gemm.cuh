@@ -5,7 +5,7 @@
 //
 // One CTA of 128 threads computes a 128 x BN tile:
 //   thread 0   : TMA producer -- 2D tensor-map loads of 64-wide K blocks of A
-//                and B into a 4-stage shared-memory ring, 128-byte swizzle
+//                and B into a 2- or 4-stage shared-memory ring, 128-byte swizzle
 //                (the canonical K-major SW128 layout the MMA reads directly);
 //   thread 32  : MMA issuer -- 4 x tcgen05.mma (K = 16 each) per K block,
 //                tcgen05.commit to the stage's "empty" barrier, and to the
@@ -156,9 +156,13 @@ __device__ __forceinline__ float dsilu_f(float z) {
     return s * (1.0f + z * (1.0f - s));
 }
 
-template <int BN>
+// BN: tile width along N; ST: shared-memory pipeline stages (2 for the short
+// K = 64..256 of the network's layers, so that up to 3 CTAs share an SM and
+// overlap one tile's epilogue with the next tile's loads and MMAs; 4 for the
+// long K ranges of the weight gradients).
+template <int BN, int ST>
 struct GemmCfg {
-    static constexpr int BM = 128, BK = 64, STAGES = 4;
+    static constexpr int BM = 128, BK = 64, STAGES = ST;
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -166,11 +170,11 @@ struct GemmCfg {
     static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN;        // power of two >= 32
 };
 
-template <int BN>
+template <int BN, int ST>
 __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB, int K,
                                                               int kb_per_split, GemmEpi epi, int32_t* status) {
-    using C = GemmCfg<BN>;
+    using C = GemmCfg<BN, ST>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t full_bar[C::STAGES], empty_bar[C::STAGES], done_bar;
