@@ -390,6 +390,7 @@ def main():
         return run_reference(args)
     import torch
     import paper_1501_03450_b300 as st
+    from paper_1501_03450_b300.replicas import aggregate_rate, max_over_ranks, rank_seed
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
@@ -402,7 +403,7 @@ def main():
     ring = w["ring"]
     n_el = len(ring["elements"])
     npart = args.particles or w["n_particles"]
-    z, S = W.gaussian_particles(npart, args.ggamma, seed=w["seed"] + rank)
+    z, S = W.gaussian_particles(npart, args.ggamma, seed=rank_seed(w["seed"], rank))
     K = args.spin_order
 
     stream = torch.cuda.Stream()
@@ -443,13 +444,9 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_sum = sum(step_ms) * 1e-3
-    if dist:
-        tt = torch.tensor([t_sum], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_sum = float(tt.item())
+    t_sum = max_over_ranks(sum(step_ms) * 1e-3, dist, "cuda")
     passes_per_rank = npart * n_el * args.steps
-    value = passes_per_rank * world / t_sum
+    value = aggregate_rate(passes_per_rank, world, t_sum)
 
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
@@ -467,12 +464,8 @@ def main():
             tr.track(1, K)
             st.st_spins_download(tr.handle, So.data_ptr(), zo.data_ptr(), lo.data_ptr(), 0)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": npart * n_el * e2e_steps * world / te, "unit": "passes/s",
+        te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": aggregate_rate(npart * n_el * e2e_steps, world, te), "unit": "passes/s",
                "h2d_bytes_per_step": 9 * 8 * npart, "d2h_bytes_per_step": 9 * 8 * npart + npart}
 
     if rank != 0:
