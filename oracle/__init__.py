@@ -33,7 +33,7 @@ _VARIANTS = {
     "c128": ("double complex", np.complex128),
 }
 
-TYPE_CODES = {"drift": 0, "mult": 1, "quad_mk": 2, "sbend": 3, "snake": 4}
+TYPE_CODES = {"drift": 0, "mult": 1, "quad_mk": 2, "sbend": 3, "snake": 4, "solenoid": 5}
 
 _lock = threading.Lock()
 _libs = {}
@@ -85,6 +85,9 @@ def _lib(variant: str = "f64"):
                                         ctypes.c_double, ctypes.c_double]
             lib.orc_subflow.restype = ctypes.c_int
             lib.orc_omega.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, vp]
+            lib.orc_solenoid_fringe.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                vp, vp]
+            lib.orc_solenoid_fringe.restype = ctypes.c_int
             lib.orc_omega.restype = ctypes.c_int
             lib.orc_check_lattice.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             lib.orc_check_lattice.restype = ctypes.c_int
@@ -144,7 +147,7 @@ def orbit_map(el, G, Ggamma0, z6, variant="f64"):
     return z6, rc
 
 
-SUBFLOWS = {"drift": 0, "kick": 1, "quad_linear": 2, "quad_nonlinear": 3, "sbend": 4}
+SUBFLOWS = {"drift": 0, "kick": 1, "quad_linear": 2, "quad_nonlinear": 3, "sbend": 4, "solenoid": 5}
 
 
 def subflow(which, G, Ggamma0, z6, s, k1=0.0, k2=0.0, h=0.0, eta=1.0, variant="f64"):
@@ -159,6 +162,15 @@ def omega(el, G, Ggamma0, z6, variant="f64"):
     z6 = np.ascontiguousarray(np.array(z6, dtype=dt).reshape(6))
     out = np.zeros(3, dtype=dt)
     rc = _lib(variant).orc_omega(elements_array([el]), G, Ggamma0, _ptr(z6), _ptr(out))
+    return out, rc
+
+
+def solenoid_fringe(ks, sign, G, Ggamma0, z6, variant="f64"):
+    """Rotation vector of a thin-pancake solenoid fringe (Eq. (solFringe))."""
+    dt = _VARIANTS[variant][1]
+    z6 = np.ascontiguousarray(np.array(z6, dtype=dt).reshape(6))
+    out = np.zeros(3, dtype=dt)
+    rc = _lib(variant).orc_solenoid_fringe(float(ks), int(sign), G, Ggamma0, _ptr(z6), _ptr(out))
     return out, rc
 
 

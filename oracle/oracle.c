@@ -16,6 +16,10 @@
  *   Sec. 3.1  exact sector-bend map, Eqs. (7)-(10)       ("bend-kick")
  *   Sec. 3.3  quadrupole matrix-kick split, Eqs. (21)-(27)
  *   Sec. 3.4  multipole drift-kick split, Eqs. (28)-(29)
+ *   Sec. 3.7  solenoid: exact body map Eq. (solenoid) of the Hamiltonian
+ *             Eq. (Hsolenoid) with the vector potential Eq. (Asol); the
+ *             unit velocity from the kinetic momentum, Eq. (mgVSol)
+ *   Sec. 4.4  thin-pancake solenoid fringe spin kicks, Eq. (solFringe)
  *   Sec. 4.1  piece-wise constant spin rotations composed as quaternions,
  *             later slices on the left, Eq. (37)
  *   Sec. 4.3  trapezoid-weighted edge rotations, sub-sampled levels Q(h/2^k),
@@ -61,7 +65,7 @@ typedef ORACLE_REAL real;
 #define RE(x) ((double)creal(x))
 
 /* Element kinds (own numbering; the CUDA library has its own). */
-enum { ORC_DRIFT = 0, ORC_MULT = 1, ORC_QUAD_MK = 2, ORC_SBEND = 3, ORC_SNAKE = 4 };
+enum { ORC_DRIFT = 0, ORC_MULT = 1, ORC_QUAD_MK = 2, ORC_SBEND = 3, ORC_SNAKE = 4, ORC_SOLENOID = 5 };
 
 typedef struct {
     int32_t type;
@@ -222,6 +226,42 @@ static int quad_nonlinear(const orc_ref* r, orc_orbit* z, double s) {
     return 0;
 }
 
+/* Solenoid body, Sec. 3.7.  The element's k1 holds the normalised body field
+ * b0/(B rho) (MAD's ks); eta = b0/(2 B rho) and the scaled vector potential
+ * (e/p0)(A_x, A_y) = eta (-Y, X) (Eq. (Asol)), so the kinetic momenta are
+ * px = Px + eta Y, py = Py - eta X and Ps = sqrt(P^2 - px^2 - py^2) is
+ * conserved.  Over a length s the transverse variables go through the
+ * commuting matrices R1(kappa s) R2(kappa s) of Eq. (solenoid) with
+ * kappa = eta / Ps, and T shifts by Eq. (solT).  R1's entry sin(kappa s)/eta
+ * is written (s/Ps) sinc(kappa s), which stays finite as eta -> 0. */
+static void solenoid_kinetic(real eta, const orc_orbit* z, real* px, real* py) {
+    *px = z->Px + eta * z->Y;
+    *py = z->Py - eta * z->X;
+}
+
+static int solenoid_map(const orc_ref* r, orc_orbit* z, double ks, double s) {
+    real eta = 0.5 * ks;
+    real px, py;
+    solenoid_kinetic(eta, z, &px, &py);
+    real ps2 = momentum_sq(r, z->Pt) - px * px - py * py;
+    if (!(RE(ps2) > 0.0)) return 1;
+    real Ps = sqrt(ps2);
+    real ks_ = (eta / Ps) * s;                    /* kappa s */
+    real c = cos(ks_), sn = sin(ks_);
+    real a12 = (s / Ps) * sinc_(ks_);             /* sin(kappa s)/eta */
+    real a21 = -eta * sn;                         /* -eta sin(kappa s) */
+    /* R1: each plane (U, Pu) -> (c U + a12 Pu, a21 U + c Pu) */
+    real X1 = c * z->X + a12 * z->Px, Px1 = a21 * z->X + c * z->Px;
+    real Y1 = c * z->Y + a12 * z->Py, Py1 = a21 * z->Y + c * z->Py;
+    /* R2: rotation of the transverse plane, (X, Y) -> (c X + sn Y, -sn X + c Y), same for (Px, Py) */
+    z->X = c * X1 + sn * Y1;
+    z->Y = -sn * X1 + c * Y1;
+    z->Px = c * Px1 + sn * Py1;
+    z->Py = -sn * Px1 + c * Py1;
+    z->T = z->T - (1.0 / r->beta0 + z->Pt) * s / Ps + s / r->beta0;   /* Eq. (solT) */
+    return 0;
+}
+
 /* One integration slice of length ds of a spin-carrying element. */
 static int slice_map(const orc_ref* r, const orc_element* e, orc_orbit* z, double ds) {
     switch (e->type) {
@@ -236,6 +276,8 @@ static int slice_map(const orc_ref* r, const orc_element* e, orc_orbit* z, doubl
         return 0;
     case ORC_SBEND:   /* exact bend, Eq. (10) */
         return sbend_map(r, z, e->angle / e->L, e->eta, ds);
+    case ORC_SOLENOID: /* exact body map, Eq. (solenoid) */
+        return solenoid_map(r, z, e->k1, ds);
     default:
         return 1;
     }
@@ -258,13 +300,24 @@ static int omega(const orc_ref* r, const orc_element* e, const orc_orbit* z, rea
     real gamma = r->gamma0 * (1.0 + r->beta0 * z->Pt);
     real b[3] = {0.0, 0.0, 0.0};
     double h = 0.0;
+    real u[3] = {z->Px / P, z->Py / P, Ps / P};
     if (e->type == ORC_SBEND) {
         h = e->angle / e->L;
         b[1] = e->eta * h;             /* b1/(B rho) = eta h, Eq. (9) */
+    } else if (e->type == ORC_SOLENOID) {
+        /* body field along s; u from the kinetic momentum, Eq. (mgVSol) */
+        real px, py;
+        solenoid_kinetic(0.5 * e->k1, z, &px, &py);
+        ps2 = P2 - px * px - py * py;
+        if (!(RE(ps2) > 0.0)) return 1;
+        Ps = sqrt(ps2);
+        b[2] = e->k1;
+        u[0] = px / P;
+        u[1] = py / P;
+        u[2] = Ps / P;
     } else {
         mult_field(e->k1, e->k2, z->X, z->Y, &b[0], &b[1]);
     }
-    real u[3] = {z->Px / P, z->Py / P, Ps / P};
     real ub = u[0] * b[0] + u[1] * b[1] + u[2] * b[2];
     real pre = -(1.0 + h * z->X) / Ps;
     for (int i = 0; i < 3; ++i)
@@ -348,6 +401,37 @@ static void romberg_element_rotation(const real (*Om)[3], int N, double ds, int 
     for (int c = 0; c < 4; ++c) Q[c] = Tab[K][K][c] / n;
 }
 
+/* Net spin rotation vector of a thin-pancake solenoid fringe, Eq. (solFringe):
+ *   w = sign (b0/2)/(B rho Ps') [ (1 + G gamma)(X, Y, 0)
+ *                                 - G (gamma - 1)(X Px + Y Py)/P^2 m gamma V' ],
+ * sign +1 at the entrance, -1 at the exit, with the kinetic momentum
+ * m gamma V' and Ps' evaluated with half the vector potential (the middle of
+ * the fringe). */
+static int solenoid_fringe(const orc_ref* r, double ks, int sign, const orc_orbit* z, real w[3]) {
+    real P2 = momentum_sq(r, z->Pt);
+    real px, py;
+    solenoid_kinetic(0.25 * ks, z, &px, &py);
+    real ps2 = P2 - px * px - py * py;
+    if (!(RE(ps2) > 0.0)) return 1;
+    real Ps = sqrt(ps2);
+    real gamma = r->gamma0 * (1.0 + r->beta0 * z->Pt);
+    real pre = sign * 0.5 * ks / Ps;
+    real xp = (z->X * z->Px + z->Y * z->Py) / P2;
+    real a = 1.0 + r->G * gamma, cg = r->G * (gamma - 1.0);
+    w[0] = pre * (a * z->X - cg * xp * px);
+    w[1] = pre * (a * z->Y - cg * xp * py);
+    w[2] = pre * (-cg * xp * Ps);
+    return 0;
+}
+
+static int fringe_rotate(const orc_ref* r, double ks, int sign, const orc_orbit* z, real S[3]) {
+    real w[3], q[4];
+    if (solenoid_fringe(r, ks, sign, z, w)) return 1;
+    quat_from_rotation_vector(w, q);
+    rotate_spin(q, S);
+    return 0;
+}
+
 /* Track one particle through one element; the spin S is rotated by the
  * element's net rotation.  Returns 0, or 1 if the particle is lost. */
 static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, real S[3],
@@ -364,6 +448,8 @@ static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, r
     }
     int N = e->n_slices;
     double ds = e->L / N;
+    /* solenoid: entrance fringe kick (orbit unchanged across the fringe) */
+    if (e->type == ORC_SOLENOID && fringe_rotate(r, e->k1, +1, z, S)) return 1;
     real (*Om)[3] = malloc(sizeof(real[3]) * (size_t)(N + 1));
     if (!Om) return 2;
     int lost = omega(r, e, z, Om[0]);
@@ -376,6 +462,8 @@ static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, r
         romberg_element_rotation((const real(*)[3])Om, N, ds, K, Q, levels_out);
         rotate_spin(Q, S);
         if (Q_out) memcpy(Q_out, Q, sizeof(Q));
+        /* solenoid: exit fringe kick */
+        if (e->type == ORC_SOLENOID) lost = fringe_rotate(r, e->k1, -1, z, S);
     }
     free(Om);
     return lost;
@@ -393,8 +481,8 @@ int orc_check_lattice(const orc_element* els, int n_el, int K) {
     if (K < 0 || K > ORC_MAX_ORDER) return -1;
     for (int i = 0; i < n_el; ++i) {
         const orc_element* e = &els[i];
-        if (e->type < 0 || e->type > ORC_SNAKE) return -1;
-        if (e->type == ORC_MULT || e->type == ORC_QUAD_MK || e->type == ORC_SBEND) {
+        if (e->type < 0 || e->type > ORC_SOLENOID) return -1;
+        if (e->type == ORC_MULT || e->type == ORC_QUAD_MK || e->type == ORC_SBEND || e->type == ORC_SOLENOID) {
             if (e->n_slices < 1 || (e->n_slices % (1 << K)) != 0) return -1;
             if (e->L == 0.0) return -1;
         }
@@ -473,7 +561,8 @@ int orc_orbit_map(const orc_element* e, double G, double Ggamma0, real* z6) {
 
 /* Individual sub-flows, for the tests that pin them one by one:
  * which = 0 drift, 1 multipole kick, 2 quadrupole linear flow H_qL,
- *         3 quadrupole nonlinear flow H_qNL, 4 sector bend. */
+ *         3 quadrupole nonlinear flow H_qNL, 4 sector bend, 5 solenoid body
+ *         (k1 = b0/(B rho)). */
 int orc_subflow(int which, double G, double Ggamma0, real* z6, double s, double k1, double k2,
                 double h, double eta) {
     orc_ref r = make_ref(G, Ggamma0);
@@ -485,6 +574,7 @@ int orc_subflow(int which, double G, double Ggamma0, real* z6, double s, double 
     case 2: quad_linear(&r, &o, k1, s); break;
     case 3: rc = quad_nonlinear(&r, &o, s); break;
     case 4: rc = sbend_map(&r, &o, h, eta, s); break;
+    case 5: rc = solenoid_map(&r, &o, k1, s); break;
     default: return -1;
     }
     z6[0] = o.X; z6[1] = o.Px; z6[2] = o.Y; z6[3] = o.Py; z6[4] = o.T; z6[5] = o.Pt;
@@ -496,4 +586,11 @@ int orc_omega(const orc_element* e, double G, double Ggamma0, const real* z6, re
     orc_ref r = make_ref(G, Ggamma0);
     orc_orbit o = {z6[0], z6[1], z6[2], z6[3], z6[4], z6[5]};
     return omega(&r, e, &o, out3);
+}
+
+/* Rotation vector of a solenoid fringe (sign +1 entrance, -1 exit) at z6. */
+int orc_solenoid_fringe(double ks, int sign, double G, double Ggamma0, const real* z6, real* out3) {
+    orc_ref r = make_ref(G, Ggamma0);
+    orc_orbit o = {z6[0], z6[1], z6[2], z6[3], z6[4], z6[5]};
+    return solenoid_fringe(&r, ks, sign, &o, out3);
 }

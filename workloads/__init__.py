@@ -21,6 +21,7 @@ b/(B rho), Sec. 2.1 and Sec. 3):
     eta        field ratio eta = b1/(h B rho), Eq. (9)
     snake_phi  snake axis angle from the longitudinal axis, in the x-s plane
     snake_mu   snake rotation angle
+    (solenoid: "solenoid" with k1 = b0/(B rho), MAD's ks, Sec. 3.7)
 
 The ring description dict: {"G", "Ggamma0", "elements": [...], "name"}.
 
@@ -39,8 +40,8 @@ import numpy as np
 
 G_PROTON = 1.7928
 
-ELEMENT_TYPES = ("drift", "mult", "quad_mk", "sbend", "snake")
-SPIN_TYPES = ("mult", "quad_mk", "sbend")
+ELEMENT_TYPES = ("drift", "mult", "quad_mk", "sbend", "snake", "solenoid")
+SPIN_TYPES = ("mult", "quad_mk", "sbend", "solenoid")
 
 
 def element(type: str, L: float = 0.0, n_slices: int = 1, k1: float = 0.0,
