@@ -55,6 +55,13 @@ extern "C" {
                            (Eq. (9)), exact map Eq. (10) per slice                       */
 #define ST_SNAKE    4   /* thin, orbit-transparent spin rotation by snake_mu about the
                            horizontal axis (sin snake_phi, 0, cos snake_phi)            */
+#define ST_SOLENOID 5   /* solenoid of body field k1 = b0/(B rho) (MAD ks), Sec. 3.7:
+                           exact body map (Eq. (solenoid)) in n_slices slices, the
+                           velocity taken along the kinetic momentum (Eq. (mgVSol)),
+                           and thin-pancake fringes at both ends with the spin kicks of
+                           Eq. (solFringe) (orbit unchanged across a fringe).  FP64
+                           only: a mixed-precision context or batch over a lattice
+                           with solenoids is rejected (ST_EINVAL).                     */
 
 /* ---- precision of a tracking context ---------------------------------- */
 #define ST_FP64   0   /* all arithmetic in IEEE double                                 */

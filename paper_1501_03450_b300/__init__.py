@@ -20,10 +20,11 @@ from . import _build
 LIB_PATH = _build.LIB
 
 ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ESTATE = 0, -1, -2, -3, -4, -5
-ST_DRIFT, ST_MULT, ST_QUAD_MK, ST_SBEND, ST_SNAKE = 0, 1, 2, 3, 4
+ST_DRIFT, ST_MULT, ST_QUAD_MK, ST_SBEND, ST_SNAKE, ST_SOLENOID = 0, 1, 2, 3, 4, 5
 ST_FP64, ST_MIXED = 0, 1
 
-TYPE_CODES = {"drift": ST_DRIFT, "mult": ST_MULT, "quad_mk": ST_QUAD_MK, "sbend": ST_SBEND, "snake": ST_SNAKE}
+TYPE_CODES = {"drift": ST_DRIFT, "mult": ST_MULT, "quad_mk": ST_QUAD_MK, "sbend": ST_SBEND, "snake": ST_SNAKE,
+              "solenoid": ST_SOLENOID}
 PRECISIONS = {"fp64": ST_FP64, "mixed": ST_MIXED}
 
 

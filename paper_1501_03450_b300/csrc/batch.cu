@@ -310,6 +310,12 @@ int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particle
         set_error("st_batch_create: precision must be ST_FP64 or ST_MIXED");
         return ST_EINVAL;
     }
+    if (precision == ST_MIXED)
+        for (int j = 0; j < n_jobs; ++j)
+            if (lattices[j] && lattices[j]->impl.has_solenoid) {
+                set_error("st_batch_create: solenoids are tracked by the FP64 tracker only");
+                return ST_EINVAL;
+            }
     st_batch* b = new (std::nothrow) st_batch();
     if (!b) {
         set_error("st_batch_create: host allocation failed");

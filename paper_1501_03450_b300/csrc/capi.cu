@@ -26,7 +26,7 @@ int cuda_fail(cudaError_t e, const char* what) {
     return ST_ECUDA;
 }
 
-bool is_spin_type(int t) { return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND; }
+bool is_spin_type(int t) { return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND || t == ST_SOLENOID; }
 
 // Precompute the per-element constants the kernels use (all in FP64).
 DevElem pack_element(const st_element& e) {
@@ -59,6 +59,12 @@ DevElem pack_element(const st_element& e) {
         d.a[5] = 1.0 / e.eta;
         break;
     }
+    case ST_SOLENOID:
+        d.ds = e.L / e.n_slices;
+        d.a[0] = e.k1;           // b0/(B rho)
+        d.a[1] = 0.5 * e.k1;     // eta of Eq. (solenoid)
+        d.a[2] = 0.25 * e.k1;    // half of eta: the vector potential in the middle of a fringe
+        break;
     case ST_SNAKE: {
         double c = std::cos(0.5 * e.snake_mu), s = std::sin(0.5 * e.snake_mu);
         d.a[0] = c;
@@ -98,7 +104,7 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
     }
     for (int i = 0; i < n; ++i) {
         const st_element& e = elems[i];
-        if (e.type < ST_DRIFT || e.type > ST_SNAKE) {
+        if (e.type < ST_DRIFT || e.type > ST_SOLENOID) {
             set_error("element %d: unknown type %d", i, e.type);
             return ST_EINVAL;
         }
@@ -141,6 +147,7 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
             uniq.push_back(d);
         }
         seq[i] = (uint16_t)idx;
+        if (d.type == ST_SOLENOID) L.has_solenoid = true;
         if (is_spin_type(d.type)) {
             max_slices = std::max(max_slices, d.n_slices);
             int p = 0;
@@ -236,6 +243,10 @@ int st_ctx_create(const st_lattice* lat, int64_t n_particles, int32_t precision,
     }
     if (n_particles > (int64_t)1 << 31) {
         set_error("st_ctx_create: at most 2^31 particles");
+        return ST_EINVAL;
+    }
+    if (precision == ST_MIXED && lat->impl.has_solenoid) {
+        set_error("st_ctx_create: solenoids are tracked by the FP64 tracker only");
         return ST_EINVAL;
     }
     st_ctx* c = new (std::nothrow) st_ctx();

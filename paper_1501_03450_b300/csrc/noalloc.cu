@@ -78,7 +78,7 @@ extern "C" int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, c
     int n_unique = 0;
     for (int i = 0; i < n_elems; ++i) {
         const st_element& e = elems[i];
-        if (e.type < ST_DRIFT || e.type > ST_SNAKE ||
+        if (e.type < ST_DRIFT || e.type > ST_SOLENOID ||
             (is_spin_type(e.type) && (!(e.L > 0.0) || e.n_slices < 1 || e.n_slices > 4096 ||
                                       e.n_slices % (1 << spin_order) != 0)) ||
             (e.type == ST_DRIFT && !(e.L >= 0.0)) || (e.type == ST_SBEND && (e.angle == 0.0 || e.eta == 0.0))) {

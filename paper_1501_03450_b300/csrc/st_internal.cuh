@@ -102,6 +102,7 @@ struct LatticeImpl {
     int32_t n_unique;
     int32_t max_slices;
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
+    bool has_solenoid = false;     // solenoids: FP64 tracker only
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]
     void* d_blob = nullptr;
     size_t blob_bytes = 0;

@@ -168,6 +168,23 @@ struct LevelProducts {
 // Track particle i for n_turns turns through the lattice in shared memory
 // (table, seq); state in the pair-SoA arrays; qcache is the block's
 // [QC_N][blockDim] shared-memory cache of matrix-kick coefficients.
+// Spin rotation of a thin-pancake solenoid fringe, Eq. (solFringe):
+//   w = sign (ks/2)/Ps' [ (1 + G gamma)(X, Y, 0) - G (gamma - 1)(X Px + Y Py)/P^2 (px', py', Ps') ]
+// with the kinetic momentum (px', py', Ps') taken with half the vector
+// potential (etaf = ks/4); sign +1 at the entrance, -1 at the exit.  Returns
+// false if Ps'^2 <= 0.
+__device__ __forceinline__ bool solenoid_fringe_quat(const PConst& pc, const Particle& p, double ks, double etaf,
+                                                     double sign, Quat& q) {
+    const double px = p.Px + etaf * p.Y, py = p.Py - etaf * p.X;
+    const double ps2 = pc.P2 - px * px - py * py;
+    if (!(ps2 > 0.0)) return false;
+    const double iPs = rsqrt(ps2);
+    const double pre = sign * 0.5 * ks * iPs;
+    const double xp = (p.X * p.Px + p.Y * p.Py) * pc.invP2 * pc.c;
+    q = quat_from_rotvec(pre * (pc.a * p.X - xp * px), pre * (pc.a * p.Y - xp * py), -pre * xp * ps2 * iPs);
+    return true;
+}
+
 // Optional per-turn outputs: each particle's composed one-turn quaternion of
 // the last tracked turn, sign-aligned with ref (q: [4][n] or nullptr), and a
 // running sum of the spin at the start of the lattice after every turn
@@ -243,7 +260,50 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
             const int N = el.n_slices;
             const double ds = el.ds;
             double ox, oy, os;
-            if (type == ST_SBEND) {
+            Quat q_in{1.0, 0.0, 0.0, 0.0};   // solenoid entrance fringe
+            if (type == ST_SOLENOID) {
+                // Sec. 3.7: exact body map of Eq. (solenoid); Ps of the kinetic
+                // momentum (Px + eta Y, Py - eta X) is conserved in the body
+                const double ks = el.a[0], eta = el.a[1];
+                double kx = p.Px + eta * p.Y, ky = p.Py - eta * p.X;
+                const double ps2 = pc.P2 - kx * kx - ky * ky;
+                if (!(ps2 > 0.0)) {
+                    is_lost = true;
+                    break;
+                }
+                const double iPs = rsqrt(ps2), Ps = ps2 * iPs;
+                const double f = pc.c * ks * pc.invP2;   // G (gamma - 1) ks / P^2
+                if constexpr (SPIN) {
+                    if (!solenoid_fringe_quat(pc, p, el.a[0], el.a[2], 1.0, q_in)) {
+                        is_lost = true;
+                        break;
+                    }
+                    // Omega (Eq. (6b)) with the velocity along the kinetic momentum
+                    lv.add_edge(0, N, ds, f * kx, f * ky, f * Ps - pc.a * ks * iPs);
+                }
+                const double kds = eta * iPs * ds;
+                double sn, cs;
+                sincos(kds, &sn, &cs);
+                // sin(kappa ds)/eta = (ds/Ps) sinc(kappa ds)
+                const double a12 = fabs(kds) > 1e-4 ? sn / eta
+                                                    : ds * iPs * (1.0 - kds * kds * (1.0 / 6.0 - kds * kds / 120.0));
+                const double a21 = -eta * sn;
+                const double dT = ds * (ref.inv_beta0 - pc.b0pt * iPs);
+                for (int s = 1; s <= N; ++s) {
+                    const double X1 = cs * p.X + a12 * p.Px, Px1 = a21 * p.X + cs * p.Px;
+                    const double Y1 = cs * p.Y + a12 * p.Py, Py1 = a21 * p.Y + cs * p.Py;
+                    p.X = cs * X1 + sn * Y1;
+                    p.Y = cs * Y1 - sn * X1;
+                    p.Px = cs * Px1 + sn * Py1;
+                    p.Py = cs * Py1 - sn * Px1;
+                    p.T += dT;
+                    if constexpr (SPIN) {
+                        kx = p.Px + eta * p.Y;
+                        ky = p.Py - eta * p.X;
+                        lv.add_edge(s, N, ds, f * kx, f * ky, f * Ps - pc.a * ks * iPs);
+                    }
+                }
+            } else if (type == ST_SBEND) {
                 const double h = el.a[0], eta = el.a[1], cb = el.a[2], sb = el.a[3], ieh = el.a[4],
                              ieta = el.a[5];
                 const double Pa2 = pc.P2 - p.Py * p.Py;
@@ -359,7 +419,20 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 is_lost = true;
                 break;
             }
-            if constexpr (SPIN) qt = qmul(qe, qt);
+            if constexpr (SPIN) {
+                if (type == ST_SOLENOID) {
+                    // entrance fringe, body, exit fringe (later rotations on the left)
+                    Quat q_out;
+                    if (!solenoid_fringe_quat(pc, p, el.a[0], el.a[2], -1.0, q_out)) {
+                        p = p0;
+                        is_lost = true;
+                        break;
+                    }
+                    qt = qmul(q_out, qmul(qe, qmul(q_in, qt)));
+                } else {
+                    qt = qmul(qe, qt);
+                }
+            }
         }
         if constexpr (SPIN) {
             qt = qnormalize(qt);

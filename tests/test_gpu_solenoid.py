@@ -1,0 +1,150 @@
+"""GPU parity of the solenoid (Sec. 3.7 body map, Sec. 4.4 fringe spin kicks):
+the CUDA FP64 tracker through the C ABI against the CPU oracle on the same
+seeded inputs, every coordinate and spin component at 1e-11, for a single
+solenoid at two energies and field strengths and every Romberg order, a ring
+with solenoids, lost particles, the zero-field limit, the batched entry point,
+and the rejection of the mixed-precision tracker (FP64 only)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1501_03450_b300 as st
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+M_P = 0.93827208816
+C_LIGHT = 0.299792458
+
+
+def ks_for(field_T, Ggamma0):
+    """b0/(B rho) for a field in tesla and a proton of G gamma0."""
+    gamma = Ggamma0 / W.G_PROTON
+    p = M_P * math.sqrt(gamma * gamma - 1.0)
+    return field_T / (p / C_LIGHT)
+
+
+# (G gamma0, field): 200 GeV/c with a 1.3 T detector-like solenoid; 1.2 GeV
+# kinetic energy (G gamma0 = G (1 + 1.2/m_p)) with 2 T
+CASES = [(W.G_PROTON * math.hypot(200.0 / M_P, 1.0), 1.3), (W.G_PROTON * (1.0 + 1.2 / M_P), 2.0)]
+
+
+def compare(ring, z, S, turns, K, tol=TOL):
+    zg, Sg, lg = st.track(ring, z, S, turns, K)
+    zo, So, lo = oracle.track(ring, z, S, turns, K)
+    assert np.array_equal(lg, lo)
+    dz = np.abs(zg - zo).max(axis=1)
+    ds = np.abs(Sg - So).max()
+    assert dz.max() < tol and ds < tol, (dz, ds)
+    return zg, Sg, lg
+
+
+@pytest.mark.parametrize("gg,field", CASES)
+@pytest.mark.parametrize("K", [0, 1, 2, 3])
+def test_single_solenoid_every_order(gg, field, K):
+    el = W.element("solenoid", L=2.1, n_slices=16, k1=ks_for(field, gg))
+    ring = W.single_element_ring(el, gg)
+    z, S = W.gaussian_particles(257, gg, seed=40 + K,
+                                sigmas=dict(x=2e-3, px=2e-4, y=2e-3, py=2e-4))
+    zg, Sg, lg = compare(ring, z, S, 20, K)
+    assert lg.sum() == 0
+    # the solenoid couples the planes: the vertical spin components moved
+    assert np.abs(Sg - S).max() > 1e-6
+
+
+def test_ring_with_solenoids_100_turns():
+    ring = W.with_spin_order(W.solenoid_ring(45.5, ks=0.05), 2)
+    z, S = W.gaussian_particles(500, 45.5, seed=91)
+    compare(ring, z, S, 100, 2)
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_ring_with_strong_solenoids_high_energy(K):
+    """G gamma0 = 487 with ks = 0.2/m: orbit rounding, amplified by G gamma in
+    the spin, brings two FP64 trackers 1e-11 apart after about 10 turns (the
+    FP64 oracle itself is that far from its extended-precision build), so
+    parity is taken after 4 turns, and after 10 turns the CUDA result must be
+    as close to the extended-precision oracle as the FP64 oracle is."""
+    ring = W.with_spin_order(W.solenoid_ring(487.0, ks=0.2), K)
+    z, S = W.gaussian_particles(129, 487.0, seed=7)
+    compare(ring, z, S, 4, K)
+    zg, Sg, lg = st.track(ring, z, S, 10, K)
+    zo, So, lo = oracle.track(ring, z, S, 10, K)
+    zx, Sx, lx = oracle.track(ring, z, S, 10, K, variant="f80")
+    zx, Sx = zx.astype(np.float64), Sx.astype(np.float64)
+    assert np.array_equal(lg, lx) and np.array_equal(lo, lx)
+    err_o = np.abs(So - Sx).max()
+    assert np.abs(Sg - Sx).max() < 2.0 * err_o + 1e-13
+    assert np.abs(zg - zx).max() < 2.0 * np.abs(zo - zx).max() + 1e-14
+
+
+def test_zero_field_solenoid_is_a_drift():
+    gg = 45.5
+    ring_s = W.with_spin_order(W.solenoid_ring(gg, ks=0.0), 2)
+    ring_d = W.with_spin_order(W.toy_ring(gg), 2)
+    z, S = W.gaussian_particles(100, gg, seed=2)
+    zs, Ss, ls = st.track(ring_s, z, S, 5, 2)
+    zd, Sd, ld = st.track(ring_d, z, S, 5, 2)
+    assert np.array_equal(ls, ld)
+    assert np.abs(zs - zd).max() < 1e-13 and np.abs(Ss - Sd).max() < 1e-13
+
+
+def test_lost_in_solenoid_keeps_entrance_state():
+    gg = 45.5
+    ring = W.with_spin_order(W.solenoid_ring(gg, ks=0.05), 2)
+    # put a solenoid first, so that it is where the particles are lost
+    ring["elements"] = ring["elements"][1:] + ring["elements"][:1]
+    z, S = W.gaussian_particles(40, gg, seed=4)
+    z[1, 3] = 1.2        # transverse kinetic momentum above P at the solenoid entrance
+    z[3, 30] = -1.1
+    zg, Sg, lg = compare(ring, z, S, 3, 2)
+    assert lg[3] == 1 and lg[30] == 1 and lg.sum() == 2
+    assert np.array_equal(zg[:, 3], z[:, 3]) and np.array_equal(Sg[:, 30], S[:, 30])
+
+
+def test_batched_jobs_with_solenoids_equal_single_job():
+    rings = [W.with_spin_order(W.solenoid_ring(gg, ks=ks), 2) for gg, ks in ((45.5, 0.05), (120.0, -0.1))]
+    rings.append(W.with_spin_order(W.toy_ring(45.5), 2))
+    ns = [300, 77, 150]
+    b = st.Batch(rings, ns, "fp64")
+    inputs = []
+    for k, (ring, n) in enumerate(zip(rings, ns)):
+        z, S = W.gaussian_particles(n, ring["Ggamma0"], seed=60 + k)
+        b.upload(k, z, S)
+        inputs.append((z, S))
+    b.track(4, 2)
+    for k, (ring, (z, S)) in enumerate(zip(rings, inputs)):
+        zb, Sb, lb = b.download(k)
+        zo, So, lo = oracle.track(ring, z, S, 4, 2)
+        assert np.array_equal(lb, lo)
+        assert np.abs(zb - zo).max() < TOL and np.abs(Sb - So).max() < TOL
+    b.close()
+
+
+def test_mixed_precision_rejects_solenoids():
+    ring = W.with_spin_order(W.solenoid_ring(45.5), 2)
+    lat = st.Lattice(ring)
+    with pytest.raises(st.SpinTrackError):
+        st.Tracker(lat, 64, precision="mixed")
+    with pytest.raises(st.SpinTrackError):
+        st.Batch([ring], [64], "mixed")
+    # the FP64 tracker accepts the same lattice
+    t = st.Tracker(lat, 64)
+    t.close()
+    lat.close()
+
+
+def test_orbit_only_tracking_through_solenoids():
+    ring = W.with_spin_order(W.solenoid_ring(45.5, ks=0.05), 2)
+    z, S = W.gaussian_particles(200, 45.5, seed=13)
+    zg, _, lg = st.track(ring, z, S, 20, 2)
+    t = st.Tracker(st.Lattice(ring), 200)
+    t.upload(z, S)
+    t.track_orbit(20)
+    zo, _, lo = t.download()
+    t.close()
+    assert np.array_equal(lg, lo)
+    assert np.abs(zg - zo).max() < 1e-12

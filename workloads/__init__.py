@@ -106,6 +106,22 @@ def toy_ring(Ggamma0: float = 45.5, n_cells: int = 8, k1: float = 0.05,
     return dict(name="toy_proton_ring", G=G_PROTON, Ggamma0=float(Ggamma0), elements=els)
 
 
+def solenoid_ring(Ggamma0: float = 45.5, ks: float = 0.05, n_cells: int = 8,
+                  sol_slices: int = 8) -> Dict:
+    """The toy ring of toy_ring() with the first 2 m drift of cells 0 and
+    n_cells/2 replaced by 2 m solenoids of strength ks = b0/(B rho) [1/m]
+    (opposite signs, so that the transverse coupling of the two partly
+    cancels, as for a detector solenoid and its compensator)."""
+    ring = toy_ring(Ggamma0, n_cells=n_cells)
+    els = ring["elements"]
+    for c, sign in ((0, +1.0), (n_cells // 2, -1.0)):
+        i = 8 * c + 1
+        assert els[i]["type"] == "drift" and els[i]["L"] == 2.0
+        els[i] = element("solenoid", L=2.0, n_slices=sol_slices, k1=sign * ks, name=f"SOL{c}")
+    ring["name"] = "toy_ring_solenoids"
+    return ring
+
+
 def rhic_like_ring(Ggamma0: float = 45.5, n_cells: int = 108, k1: float = 0.03,
                    k2: float = 0.5, base_slices: int = 4, sext_slices: int = 2,
                    snakes: bool = True, quad_type: str = "quad_mk") -> Dict:
