@@ -148,3 +148,33 @@ def test_orbit_only_tracking_through_solenoids():
     t.close()
     assert np.array_equal(lg, lo)
     assert np.abs(zg - zo).max() < 1e-12
+
+
+def test_paper_solenoid_study_error_ranges_on_the_gpu():
+    """Sec. 5.2.1, low-energy solenoid (1.2 GeV kinetic, 1.3 T, 2.1 m) through
+    the CUDA tracker: over a 21 x 21 grid of (Px, Py) the spin error ranges of
+    8 slices without Romberg, 4 slices with two Romberg iterations and 8
+    slices with three do not overlap; the reference is the extended-precision
+    oracle with 128 slices and three iterations."""
+    p = math.sqrt(1.2 ** 2 + 2 * 1.2 * M_P)
+    gg = W.G_PROTON * math.sqrt(p * p + M_P * M_P) / M_P
+    ks = 1.3 / (p / C_LIGHT)
+    g = np.linspace(-3e-3, 3e-3, 21)
+    PX, PY = np.meshgrid(g, g)
+    n = PX.size
+    z = np.zeros((6, n))
+    z[0], z[2], z[1], z[3] = 1e-3, -1e-3, PX.ravel(), PY.ravel()
+    S = np.tile(np.array([[0.0], [1.0], [0.0]]), (1, n))
+
+    def ring(N):
+        return W.single_element_ring(W.element("solenoid", L=2.1, n_slices=N, k1=ks), gg)
+
+    _, ref, lo = oracle.track(ring(128), z, S, 1, 3, variant="f80")
+    ref = ref.astype(np.float64)
+    err = {}
+    for N, K in ((8, 0), (4, 2), (8, 3)):
+        _, Sg, lg = st.track(ring(N), z, S, 1, K)
+        assert not lg.any()
+        err[(N, K)] = np.linalg.norm(Sg - ref, axis=0)
+    assert err[(4, 2)].max() < err[(8, 0)].min()
+    assert err[(8, 3)].max() < err[(4, 2)].min()

@@ -218,6 +218,41 @@ def test_convergence_of_the_paper_single_element_study():
     assert e42 < 1e-2 * e[8] and e83 < 1e-2 * e42
 
 
+def _low_energy_grid():
+    """1.2 GeV kinetic-energy protons through the 1.3 T, 2.1 m solenoid of
+    Sec. 5.2.1 on a 21 x 21 grid of (Px, Py) in +-3e-3, X = 1 mm, Y = -1 mm,
+    spins vertical."""
+    p = math.sqrt(1.2 ** 2 + 2 * 1.2 * M_P)
+    g = np.linspace(-3e-3, 3e-3, 21)
+    PX, PY = np.meshgrid(g, g)
+    n = PX.size
+    z = np.zeros((6, n))
+    z[0], z[2], z[1], z[3] = 1e-3, -1e-3, PX.ravel(), PY.ravel()
+    S = np.tile(np.array([[0.0], [1.0], [0.0]]), (1, n))
+    return ggamma_of_momentum(p), ks_of(1.3, p), z, S
+
+
+def test_error_ranges_of_the_paper_solenoid_study_do_not_overlap():
+    """Sec. 5.2.1, low-energy solenoid: over the (Px, Py) plane, the spin
+    error ranges of 8 slices without Romberg, 4 slices with two Romberg
+    iterations and 8 slices with three do not overlap, each lying below the
+    previous one; the stand-in for exact tracking is 128 slices with three
+    Romberg iterations (the extended-precision build, so that the finest
+    range is not rounding noise)."""
+    gg, ks, z, S = _low_energy_grid()
+
+    def run(N, K):
+        ring = W.single_element_ring(W.element("solenoid", L=2.1, n_slices=N, k1=ks), gg)
+        _, So, lost = oracle.track(ring, z, S, 1, K, variant="f80")
+        assert not lost.any()
+        return So.astype(np.float64)
+
+    ref = run(128, 3)
+    err = {nk: np.linalg.norm(run(*nk) - ref, axis=0) for nk in ((8, 0), (4, 2), (8, 3))}
+    assert err[(4, 2)].max() < err[(8, 0)].min()
+    assert err[(8, 3)].max() < err[(4, 2)].min()
+
+
 @pytest.mark.parametrize("gg,ks", [(2.5, 1.3), (45.5, 0.08)])
 def test_body_spin_matches_thomas_bmt_ode(gg, ks):
     """The whole element against Thomas-BMT integrated through the body (velocity
