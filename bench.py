@@ -46,8 +46,8 @@ L2_BYTES = 126 * 1024 * 1024
 FP64_FLOPS_PER_PASS = 501.5
 # DRAM bytes (read + write) per particle per launch of the FP64 tracker, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the same capture (2e4
-# particles: 1.618 MB + 0 B), scaled linearly with the particle count.
-FP64_DRAM_BYTES_PER_PARTICLE = 80.9
+# particles: 1.585 MB + 0 B), scaled linearly with the particle count.
+FP64_DRAM_BYTES_PER_PARTICLE = 79.2
 
 
 def parse_args():

@@ -43,7 +43,8 @@ class OrcElement(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int32), ("n_slices", ctypes.c_int32),
                 ("L", ctypes.c_double), ("k1", ctypes.c_double), ("k2", ctypes.c_double),
                 ("angle", ctypes.c_double), ("eta", ctypes.c_double),
-                ("snake_phi", ctypes.c_double), ("snake_mu", ctypes.c_double)]
+                ("snake_phi", ctypes.c_double), ("snake_mu", ctypes.c_double),
+                ("fringe", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def _lib_path(variant: str) -> str:
@@ -88,6 +89,8 @@ def _lib(variant: str = "f64"):
             lib.orc_solenoid_fringe.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                 vp, vp]
             lib.orc_solenoid_fringe.restype = ctypes.c_int
+            lib.orc_element_fringe.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp]
+            lib.orc_element_fringe.restype = ctypes.c_int
             lib.orc_omega.restype = ctypes.c_int
             lib.orc_check_lattice.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             lib.orc_check_lattice.restype = ctypes.c_int
@@ -101,7 +104,7 @@ def elements_array(elements):
     arr = (OrcElement * max(1, len(elements)))()
     for i, e in enumerate(elements):
         arr[i] = OrcElement(TYPE_CODES[e["type"]], int(e["n_slices"]), e["L"], e["k1"], e["k2"],
-                            e["angle"], e["eta"], e["snake_phi"], e["snake_mu"])
+                            e["angle"], e["eta"], e["snake_phi"], e["snake_mu"], int(e.get("fringe", 0)), 0)
     return arr
 
 
@@ -171,6 +174,17 @@ def solenoid_fringe(ks, sign, G, Ggamma0, z6, variant="f64"):
     z6 = np.ascontiguousarray(np.array(z6, dtype=dt).reshape(6))
     out = np.zeros(3, dtype=dt)
     rc = _lib(variant).orc_solenoid_fringe(float(ks), int(sign), G, Ggamma0, _ptr(z6), _ptr(out))
+    return out, rc
+
+
+def element_fringe(el, sign, G, Ggamma0, z6, variant="f64"):
+    """Rotation vector of element el's thin fringe spin kick at its entrance
+    (sign +1) or exit (-1): Eq. (skfringe) for dipoles and multipoles,
+    Eq. (solFringe) for solenoids.  Returns (w[3], rc)."""
+    dt = _VARIANTS[variant][1]
+    z6 = np.ascontiguousarray(np.array(z6, dtype=dt).reshape(6))
+    out = np.zeros(3, dtype=dt)
+    rc = _lib(variant).orc_element_fringe(elements_array([el]), int(sign), G, Ggamma0, _ptr(z6), _ptr(out))
     return out, rc
 
 

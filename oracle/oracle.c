@@ -20,6 +20,8 @@
  *             Eq. (Hsolenoid) with the vector potential Eq. (Asol); the
  *             unit velocity from the kinetic momentum, Eq. (mgVSol)
  *   Sec. 4.4  thin-pancake solenoid fringe spin kicks, Eq. (solFringe)
+ *   Sec. 4.5  thin-fringe spin kicks of dipole and multipole fringes,
+ *             Eq. (skfringe), on elements whose fringe flag is set
  *   Sec. 4.1  piece-wise constant spin rotations composed as quaternions,
  *             later slices on the left, Eq. (37)
  *   Sec. 4.3  trapezoid-weighted edge rotations, sub-sampled levels Q(h/2^k),
@@ -71,6 +73,8 @@ typedef struct {
     int32_t type;
     int32_t n_slices;
     double L, k1, k2, angle, eta, snake_phi, snake_mu;
+    int32_t fringe;      /* 1: thin fringe spin kicks at both ends (mult, quad_mk, sbend) */
+    int32_t reserved;
 } orc_element;
 
 typedef struct {
@@ -432,6 +436,57 @@ static int fringe_rotate(const orc_ref* r, double ks, int sign, const orc_orbit*
     return 0;
 }
 
+/* Normal 2m-pole content of an element as (m, b_m/(B rho)) pairs, in the
+ * normalisation of Eq. (Amult): a sector bend is a dipole with
+ * b_1/(B rho) = eta h (Eq. (9)); a quadrupole has b_2/(B rho) = k1; the
+ * sextupole part of a multipole has b_3/(B rho) = k2/2 (MAD's k2 = B''/(B rho)).
+ * Returns the number of pairs. */
+static int normal_multipoles(const orc_element* e, int m[2], double bm[2]) {
+    switch (e->type) {
+    case ORC_SBEND: m[0] = 1; bm[0] = e->eta * e->angle / e->L; return 1;
+    case ORC_QUAD_MK: m[0] = 2; bm[0] = e->k1; return 1;
+    case ORC_MULT: m[0] = 2; bm[0] = e->k1; m[1] = 3; bm[1] = 0.5 * e->k2; return 2;
+    default: return 0;
+    }
+}
+
+/* Spin kick of a thin dipole or multipole fringe, Eq. (skfringe), to lowest
+ * order in the dynamical variables: a rotation about the longitudinal axis by
+ *   omega_s = -sign (1 + G) sum_m (b_m/(B rho)) r^m sin(m phi) / m,
+ * with r^m sin(m phi) = Im (X + iY)^m; sign +1 at the entrance, -1 at the
+ * exit.  The orbit is unchanged. */
+static void multipole_fringe(const orc_ref* r, const orc_element* e, int sign, const orc_orbit* z, real w[3]) {
+    int m[2];
+    double bm[2];
+    int n = normal_multipoles(e, m, bm);
+    real sum = 0.0;
+    for (int j = 0; j < n; ++j) {
+        real re = 1.0, im = 0.0;                 /* (X + iY)^k by repeated multiplication */
+        for (int k = 0; k < m[j]; ++k) {
+            real re2 = re * z->X - im * z->Y;
+            im = re * z->Y + im * z->X;
+            re = re2;
+        }
+        sum += bm[j] * im / m[j];
+    }
+    w[0] = 0.0;
+    w[1] = 0.0;
+    w[2] = -sign * (1.0 + r->G) * sum;
+}
+
+/* Fringe spin kick of element e at its entrance (sign +1) or exit (-1):
+ * solenoids always (thin-pancake model, Sec. 4.4), dipoles and multipoles
+ * when the element's fringe flag is set (Sec. 4.5).  Returns 1 if lost. */
+static int element_fringe(const orc_ref* r, const orc_element* e, int sign, const orc_orbit* z, real S[3]) {
+    if (e->type == ORC_SOLENOID) return fringe_rotate(r, e->k1, sign, z, S);
+    if (!e->fringe) return 0;
+    real w[3], q[4];
+    multipole_fringe(r, e, sign, z, w);
+    quat_from_rotation_vector(w, q);
+    rotate_spin(q, S);
+    return 0;
+}
+
 /* Track one particle through one element; the spin S is rotated by the
  * element's net rotation.  Returns 0, or 1 if the particle is lost. */
 static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, real S[3],
@@ -448,8 +503,8 @@ static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, r
     }
     int N = e->n_slices;
     double ds = e->L / N;
-    /* solenoid: entrance fringe kick (orbit unchanged across the fringe) */
-    if (e->type == ORC_SOLENOID && fringe_rotate(r, e->k1, +1, z, S)) return 1;
+    /* entrance fringe kick (orbit unchanged across the fringe) */
+    if (element_fringe(r, e, +1, z, S)) return 1;
     real (*Om)[3] = malloc(sizeof(real[3]) * (size_t)(N + 1));
     if (!Om) return 2;
     int lost = omega(r, e, z, Om[0]);
@@ -462,8 +517,8 @@ static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, r
         romberg_element_rotation((const real(*)[3])Om, N, ds, K, Q, levels_out);
         rotate_spin(Q, S);
         if (Q_out) memcpy(Q_out, Q, sizeof(Q));
-        /* solenoid: exit fringe kick */
-        if (e->type == ORC_SOLENOID) lost = fringe_rotate(r, e->k1, -1, z, S);
+        /* exit fringe kick */
+        lost = element_fringe(r, e, -1, z, S);
     }
     free(Om);
     return lost;
@@ -487,6 +542,8 @@ int orc_check_lattice(const orc_element* els, int n_el, int K) {
             if (e->L == 0.0) return -1;
         }
         if (e->type == ORC_SBEND && (e->angle == 0.0 || e->eta == 0.0)) return -1;
+        if (e->fringe != 0 && e->fringe != 1) return -1;
+        if (e->fringe && (e->type == ORC_DRIFT || e->type == ORC_SNAKE)) return -1;
     }
     return 0;
 }
@@ -593,4 +650,16 @@ int orc_solenoid_fringe(double ks, int sign, double G, double Ggamma0, const rea
     orc_ref r = make_ref(G, Ggamma0);
     orc_orbit o = {z6[0], z6[1], z6[2], z6[3], z6[4], z6[5]};
     return solenoid_fringe(&r, ks, sign, &o, out3);
+}
+
+/* Rotation vector of the thin fringe spin kick of element e (sign +1
+ * entrance, -1 exit) at z6: Eq. (skfringe) for dipoles and multipoles whatever
+ * their fringe flag, Eq. (solFringe) for solenoids.  Returns 0, 1 (lost), -1. */
+int orc_element_fringe(const orc_element* e, int sign, double G, double Ggamma0, const real* z6, real* out3) {
+    orc_ref r = make_ref(G, Ggamma0);
+    orc_orbit o = {z6[0], z6[1], z6[2], z6[3], z6[4], z6[5]};
+    if (e->type == ORC_SOLENOID) return solenoid_fringe(&r, e->k1, sign, &o, out3);
+    if (e->type != ORC_MULT && e->type != ORC_QUAD_MK && e->type != ORC_SBEND) return -1;
+    multipole_fringe(&r, e, sign, &o, out3);
+    return 0;
 }

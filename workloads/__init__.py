@@ -21,7 +21,10 @@ b/(B rho), Sec. 2.1 and Sec. 3):
     eta        field ratio eta = b1/(h B rho), Eq. (9)
     snake_phi  snake axis angle from the longitudinal axis, in the x-s plane
     snake_mu   snake rotation angle
-    (solenoid: "solenoid" with k1 = b0/(B rho), MAD's ks, Sec. 3.7)
+    fringe     1: thin fringe spin kicks at both ends of a mult, quad_mk or
+               sbend (Sec. 4.5, Eq. (skfringe)); 0: hard edges without kicks
+    (solenoid: "solenoid" with k1 = b0/(B rho), MAD's ks, Sec. 3.7; its
+    thin-pancake fringe kicks, Sec. 4.4, are always part of the element)
 
 The ring description dict: {"G", "Ggamma0", "elements": [...], "name"}.
 
@@ -46,13 +49,14 @@ SPIN_TYPES = ("mult", "quad_mk", "sbend", "solenoid")
 
 def element(type: str, L: float = 0.0, n_slices: int = 1, k1: float = 0.0,
             k2: float = 0.0, angle: float = 0.0, eta: float = 1.0,
-            snake_phi: float = 0.0, snake_mu: float = 0.0, name: str = "") -> Dict:
+            snake_phi: float = 0.0, snake_mu: float = 0.0, name: str = "",
+            fringe: int = 0) -> Dict:
     if type not in ELEMENT_TYPES:
         raise ValueError(f"unknown element type {type!r}")
     return dict(type=type, L=float(L), n_slices=int(n_slices), k1=float(k1),
                 k2=float(k2), angle=float(angle), eta=float(eta),
                 snake_phi=float(snake_phi), snake_mu=float(snake_mu),
-                name=name or type)
+                name=name or type, fringe=int(fringe))
 
 
 def slices_for_order(base: int, spin_order: int) -> int:
