@@ -85,6 +85,14 @@ typedef struct {
     double eta;
     double snake_phi;
     double snake_mu;
+    int32_t fringe;    /* 1: thin fringe spin kicks at both ends of an ST_MULT, ST_QUAD_MK
+                        * or ST_SBEND (Sec. 4.5, Eq. (skfringe)): a rotation about the
+                        * longitudinal axis by -(+-)(1 + G) sum_m (b_m/(B rho)) Im (X + iY)^m / m,
+                        * + at the entrance, - at the exit, with b_1/(B rho) = eta h,
+                        * b_2/(B rho) = k1, b_3/(B rho) = k2/2; orbit unchanged.  0: none.
+                        * Solenoids always carry their Sec. 4.4 fringe kicks; drifts and
+                        * snakes must have 0 (ST_EINVAL otherwise).  FP64 contexts only. */
+    int32_t reserved;  /* ignored; set to 0 */
 } st_element;
 
 /* Reference particle: anomaly G and naive spin tune G*gamma0 of the scale

@@ -312,8 +312,8 @@ int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particle
     }
     if (precision == ST_MIXED)
         for (int j = 0; j < n_jobs; ++j)
-            if (lattices[j] && lattices[j]->impl.has_solenoid) {
-                set_error("st_batch_create: solenoids are tracked by the FP64 tracker only");
+            if (lattices[j] && lattices[j]->impl.fp64_only) {
+                set_error("st_batch_create: solenoids and fringe spin kicks are tracked by the FP64 tracker only");
                 return ST_EINVAL;
             }
     st_batch* b = new (std::nothrow) st_batch();

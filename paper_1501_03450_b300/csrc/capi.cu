@@ -33,7 +33,8 @@ DevElem pack_element(const st_element& e) {
     DevElem d;
     memset(&d, 0, sizeof(d));
     d.type = e.type;
-    d.n_slices = is_spin_type(e.type) ? e.n_slices : 1;
+    d.n_slices = (int16_t)(is_spin_type(e.type) ? e.n_slices : 1);
+    d.flags = (e.fringe && e.type != ST_SOLENOID) ? ST_ELEM_FRINGE : 0;
     switch (e.type) {
     case ST_DRIFT:
         d.ds = e.L;
@@ -112,6 +113,14 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
             set_error("element %d: spin-carrying element needs L > 0 and 1 <= n_slices <= 4096", i);
             return ST_EINVAL;
         }
+        if (e.fringe != 0 && e.fringe != 1) {
+            set_error("element %d: fringe must be 0 or 1", i);
+            return ST_EINVAL;
+        }
+        if (e.fringe && (e.type == ST_DRIFT || e.type == ST_SNAKE)) {
+            set_error("element %d: fringe kicks need a multipole, quadrupole, bend or solenoid", i);
+            return ST_EINVAL;
+        }
         if (e.type == ST_DRIFT && !(e.L >= 0.0)) {
             set_error("element %d: drift needs L >= 0", i);
             return ST_EINVAL;
@@ -147,9 +156,9 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
             uniq.push_back(d);
         }
         seq[i] = (uint16_t)idx;
-        if (d.type == ST_SOLENOID) L.has_solenoid = true;
+        if (d.type == ST_SOLENOID || d.flags) L.fp64_only = true;
         if (is_spin_type(d.type)) {
-            max_slices = std::max(max_slices, d.n_slices);
+            max_slices = std::max(max_slices, (int)d.n_slices);
             int p = 0;
             while (((d.n_slices >> p) & 1) == 0 && p < 30) ++p;
             min_pow2 = std::min(min_pow2, p);
@@ -245,8 +254,8 @@ int st_ctx_create(const st_lattice* lat, int64_t n_particles, int32_t precision,
         set_error("st_ctx_create: at most 2^31 particles");
         return ST_EINVAL;
     }
-    if (precision == ST_MIXED && lat->impl.has_solenoid) {
-        set_error("st_ctx_create: solenoids are tracked by the FP64 tracker only");
+    if (precision == ST_MIXED && lat->impl.fp64_only) {
+        set_error("st_ctx_create: solenoids and fringe spin kicks are tracked by the FP64 tracker only");
         return ST_EINVAL;
     }
     st_ctx* c = new (std::nothrow) st_ctx();

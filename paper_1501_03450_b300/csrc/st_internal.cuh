@@ -15,10 +15,12 @@ namespace st {
 // copy).  Per-type constants are precomputed on the host in FP64.
 struct __align__(16) DevElem {
     int32_t type;
-    int32_t n_slices;
+    int16_t n_slices;
+    int16_t flags;  // ST_ELEM_FRINGE: thin fringe spin kicks at both ends (mult, quad, sbend)
     double ds;      // slice length (drift: full length)
     double a[6];    // type-specific constants, see pack_element()
 };
+enum { ST_ELEM_FRINGE = 1 };
 static_assert(sizeof(DevElem) == 64, "DevElem must be 64 bytes");
 
 // a[] layout per type
@@ -102,7 +104,7 @@ struct LatticeImpl {
     int32_t n_unique;
     int32_t max_slices;
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
-    bool has_solenoid = false;     // solenoids: FP64 tracker only
+    bool fp64_only = false;        // solenoids or fringe spin kicks: FP64 tracker only
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]
     void* d_blob = nullptr;
     size_t blob_bytes = 0;

@@ -185,6 +185,22 @@ __device__ __forceinline__ bool solenoid_fringe_quat(const PConst& pc, const Par
     return true;
 }
 
+// Spin rotation of a thin dipole or multipole fringe, Eq. (skfringe): about
+// the longitudinal axis by -sign (1 + G) sum_m (b_m/(B rho)) Im (X + iY)^m / m
+// with b_1 = eta h (sector bend), b_2 = k1, b_3 = k2/2 (multipole); sign +1 at
+// the entrance, -1 at the exit.
+__device__ __forceinline__ Quat multipole_fringe_quat(const DevElem& el, int type, double onepG, const Particle& p,
+                                                      double sign) {
+    double sum;
+    if (type == ST_SBEND) {
+        sum = el.a[0] * el.a[1] * p.Y;                                       // eta h Im(w)
+    } else {
+        sum = el.a[0] * p.X * p.Y;                                           // k1 Im(w^2)/2
+        if (type == ST_MULT) sum += 0.5 * el.a[1] * p.Y * (p.X * p.X - p.Y * p.Y * (1.0 / 3.0));   // k2/2 Im(w^3)/3
+    }
+    return quat_from_rotvec(0.0, 0.0, -sign * onepG * sum);
+}
+
 // Optional per-turn outputs: each particle's composed one-turn quaternion of
 // the last tracked turn, sign-aligned with ref (q: [4][n] or nullptr), and a
 // running sum of the spin at the start of the lattice after every turn
@@ -260,7 +276,11 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
             const int N = el.n_slices;
             const double ds = el.ds;
             double ox, oy, os;
-            Quat q_in{1.0, 0.0, 0.0, 0.0};   // solenoid entrance fringe
+            Quat q_in{1.0, 0.0, 0.0, 0.0};   // entrance fringe kick
+            const bool fringe = el.flags & ST_ELEM_FRINGE;
+            if constexpr (SPIN) {
+                if (fringe) q_in = multipole_fringe_quat(el, type, 1.0 + ref.G, p, 1.0);
+            }
             if (type == ST_SOLENOID) {
                 // Sec. 3.7: exact body map of Eq. (solenoid); Ps of the kinetic
                 // momentum (Px + eta Y, Py - eta X) is conserved in the body
@@ -428,6 +448,9 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                         is_lost = true;
                         break;
                     }
+                    qt = qmul(q_out, qmul(qe, qmul(q_in, qt)));
+                } else if (fringe) {
+                    const Quat q_out = multipole_fringe_quat(el, type, 1.0 + ref.G, p, -1.0);
                     qt = qmul(q_out, qmul(qe, qmul(q_in, qt)));
                 } else {
                     qt = qmul(qe, qt);

@@ -79,6 +79,16 @@ def with_spin_order(ring: Dict, spin_order: int) -> Dict:
     return out
 
 
+def with_fringes(ring: Dict, on: int = 1) -> Dict:
+    """Copy of `ring` with the thin fringe spin kicks of Sec. 4.5 switched on
+    (or off) at both ends of every multipole, quadrupole and sector bend."""
+    out = dict(ring)
+    out["elements"] = [dict(e, fringe=int(on)) if e["type"] in ("mult", "quad_mk", "sbend") else dict(e)
+                       for e in ring["elements"]]
+    out["name"] = ring["name"] + ("_fringes" if on else "")
+    return out
+
+
 def reference(Ggamma0: float, G: float = G_PROTON):
     """(gamma0, beta0) of the scale momentum for a given naive spin tune."""
     gamma0 = Ggamma0 / G
