@@ -44,7 +44,7 @@ class OrcElement(ctypes.Structure):
                 ("L", ctypes.c_double), ("k1", ctypes.c_double), ("k2", ctypes.c_double),
                 ("angle", ctypes.c_double), ("eta", ctypes.c_double),
                 ("snake_phi", ctypes.c_double), ("snake_mu", ctypes.c_double),
-                ("fringe", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("fringe", ctypes.c_int32), ("split_order", ctypes.c_int32)]
 
 
 def _lib_path(variant: str) -> str:
@@ -104,7 +104,7 @@ def elements_array(elements):
     arr = (OrcElement * max(1, len(elements)))()
     for i, e in enumerate(elements):
         arr[i] = OrcElement(TYPE_CODES[e["type"]], int(e["n_slices"]), e["L"], e["k1"], e["k2"],
-                            e["angle"], e["eta"], e["snake_phi"], e["snake_mu"], int(e.get("fringe", 0)), 0)
+                            e["angle"], e["eta"], e["snake_phi"], e["snake_mu"], int(e.get("fringe", 0)), int(e.get("split_order", 2)))
     return arr
 
 

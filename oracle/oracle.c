@@ -16,6 +16,9 @@
  *   Sec. 3.1  exact sector-bend map, Eqs. (7)-(10)       ("bend-kick")
  *   Sec. 3.3  quadrupole matrix-kick split, Eqs. (21)-(27)
  *   Sec. 3.4  multipole drift-kick split, Eqs. (28)-(29)
+ *   Sec. 3.3  (closing remark) higher-order versions of the symmetric split of
+ *             Eq. (27): Yoshida's fourth-order composition of the
+ *             second-order slice map, on elements with split_order 4
  *   Sec. 3.7  solenoid: exact body map Eq. (solenoid) of the Hamiltonian
  *             Eq. (Hsolenoid) with the vector potential Eq. (Asol); the
  *             unit velocity from the kinetic momentum, Eq. (mgVSol)
@@ -74,7 +77,7 @@ typedef struct {
     int32_t n_slices;
     double L, k1, k2, angle, eta, snake_phi, snake_mu;
     int32_t fringe;      /* 1: thin fringe spin kicks at both ends (mult, quad_mk, sbend) */
-    int32_t reserved;
+    int32_t split_order; /* mult, quad_mk: 0 or 2 = Eq. (27), 4 = Yoshida's fourth order */
 } orc_element;
 
 typedef struct {
@@ -267,7 +270,7 @@ static int solenoid_map(const orc_ref* r, orc_orbit* z, double ks, double s) {
 }
 
 /* One integration slice of length ds of a spin-carrying element. */
-static int slice_map(const orc_ref* r, const orc_element* e, orc_orbit* z, double ds) {
+static int slice_map2(const orc_ref* r, const orc_element* e, orc_orbit* z, double ds) {
     switch (e->type) {
     case ORC_MULT:   /* drift-kick-drift, Sec. 3.4 with the symmetric form of Eq. (27) */
         if (drift(r, z, 0.5 * ds)) return 1;
@@ -285,6 +288,20 @@ static int slice_map(const orc_ref* r, const orc_element* e, orc_orbit* z, doubl
     default:
         return 1;
     }
+}
+
+/* One slice of an element.  With split_order 4 the symmetric second-order
+ * slice map S2 of Eq. (27) is composed as Yoshida's fourth-order product
+ * S2(x1 ds) S2(x0 ds) S2(x1 ds), with x1 = 1/(2 - 2^(1/3)) and
+ * x0 = 1 - 2 x1, the weights that cancel the third-order error term
+ * (2 x1^3 + x0^3 = 0) of a symmetric method (Yoshida 1990). */
+static int slice_map(const orc_ref* r, const orc_element* e, orc_orbit* z, double ds) {
+    if (e->split_order != 4) return slice_map2(r, e, z, ds);
+    double x1 = 1.0 / (2.0 - cbrt(2.0));
+    double x0 = 1.0 - 2.0 * x1;
+    if (slice_map2(r, e, z, x1 * ds)) return 1;
+    if (slice_map2(r, e, z, x0 * ds)) return 1;
+    return slice_map2(r, e, z, x1 * ds);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -544,6 +561,8 @@ int orc_check_lattice(const orc_element* els, int n_el, int K) {
         if (e->type == ORC_SBEND && (e->angle == 0.0 || e->eta == 0.0)) return -1;
         if (e->fringe != 0 && e->fringe != 1) return -1;
         if (e->fringe && (e->type == ORC_DRIFT || e->type == ORC_SNAKE)) return -1;
+        if (e->split_order != 0 && e->split_order != 2 && e->split_order != 4) return -1;
+        if (e->split_order == 4 && e->type != ORC_MULT && e->type != ORC_QUAD_MK) return -1;
     }
     return 0;
 }

@@ -23,6 +23,8 @@ b/(B rho), Sec. 2.1 and Sec. 3):
     snake_mu   snake rotation angle
     fringe     1: thin fringe spin kicks at both ends of a mult, quad_mk or
                sbend (Sec. 4.5, Eq. (skfringe)); 0: hard edges without kicks
+    split_order  orbit slice map of a mult or quad_mk: 2 = the symmetric split
+               of Eq. (27), 4 = its fourth-order Yoshida composition (Sec. 3.3)
     (solenoid: "solenoid" with k1 = b0/(B rho), MAD's ks, Sec. 3.7; its
     thin-pancake fringe kicks, Sec. 4.4, are always part of the element)
 
@@ -50,13 +52,13 @@ SPIN_TYPES = ("mult", "quad_mk", "sbend", "solenoid")
 def element(type: str, L: float = 0.0, n_slices: int = 1, k1: float = 0.0,
             k2: float = 0.0, angle: float = 0.0, eta: float = 1.0,
             snake_phi: float = 0.0, snake_mu: float = 0.0, name: str = "",
-            fringe: int = 0) -> Dict:
+            fringe: int = 0, split_order: int = 2) -> Dict:
     if type not in ELEMENT_TYPES:
         raise ValueError(f"unknown element type {type!r}")
     return dict(type=type, L=float(L), n_slices=int(n_slices), k1=float(k1),
                 k2=float(k2), angle=float(angle), eta=float(eta),
                 snake_phi=float(snake_phi), snake_mu=float(snake_mu),
-                name=name or type, fringe=int(fringe))
+                name=name or type, fringe=int(fringe), split_order=int(split_order))
 
 
 def slices_for_order(base: int, spin_order: int) -> int:
