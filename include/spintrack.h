@@ -91,8 +91,15 @@ typedef struct {
                         * + at the entrance, - at the exit, with b_1/(B rho) = eta h,
                         * b_2/(B rho) = k1, b_3/(B rho) = k2/2; orbit unchanged.  0: none.
                         * Solenoids always carry their Sec. 4.4 fringe kicks; drifts and
-                        * snakes must have 0 (ST_EINVAL otherwise).  FP64 contexts only. */
-    int32_t reserved;  /* ignored; set to 0 */
+                        * snakes must have 0 (ST_EINVAL otherwise).  FP64 contexts only
+                        * when 1. */
+    int32_t split_order; /* orbit slice map of an ST_MULT or ST_QUAD_MK: 0 or 2 = the
+                          * symmetric second-order split of Eq. (27) (drift-kick-drift,
+                          * matrix-kick); 4 = Yoshida's fourth-order composition
+                          * S2(x1 ds) S2(x0 ds) S2(x1 ds), x1 = 1/(2 - 2^(1/3)),
+                          * x0 = 1 - 2 x1 (Sec. 3.3's higher-order versions).  Spin is
+                          * still sampled at the slice edges.  Other types: 0 or 2
+                          * (ST_EINVAL otherwise).  FP64 contexts only when 4. */
 } st_element;
 
 /* Reference particle: anomaly G and naive spin tune G*gamma0 of the scale

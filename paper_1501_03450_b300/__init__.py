@@ -32,7 +32,7 @@ class StElement(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int32), ("n_slices", ctypes.c_int32), ("L", ctypes.c_double),
                 ("k1", ctypes.c_double), ("k2", ctypes.c_double), ("angle", ctypes.c_double),
                 ("eta", ctypes.c_double), ("snake_phi", ctypes.c_double), ("snake_mu", ctypes.c_double),
-                ("fringe", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("fringe", ctypes.c_int32), ("split_order", ctypes.c_int32)]
 
 
 class StReference(ctypes.Structure):
@@ -129,7 +129,8 @@ def elements_array(elements: List[Dict]):
     arr = (StElement * len(elements))()
     for i, e in enumerate(elements):
         arr[i] = StElement(TYPE_CODES[e["type"]], int(e["n_slices"]), e["L"], e["k1"], e["k2"], e["angle"],
-                           e["eta"], e["snake_phi"], e["snake_mu"], int(e.get("fringe", 0)), 0)
+                           e["eta"], e["snake_phi"], e["snake_mu"], int(e.get("fringe", 0)),
+                           int(e.get("split_order", 2)))
     return arr
 
 

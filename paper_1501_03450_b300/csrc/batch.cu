@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128, MINB) track_batch_fp64_kernel(const JobDe
                                                                       int32_t* status) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
-    __shared__ double qcache[QC_N * 128];
+    __shared__ double qcache[(2 * QC_N + 2) * 128];
     batch_loop(jobs, items, n_items, queue, status, smem, &bar, [&](const JobDesc& J, int64_t i) {
         fp64_track_particle<K>((const DevElem*)smem, (const uint16_t*)(smem + J.seq_offset), J.n_seq, J.ref, J.xpx,
                                J.ypy, J.tpt, J.sxy, J.sz, J.lost, i, n_turns, qcache);

@@ -35,6 +35,7 @@ DevElem pack_element(const st_element& e) {
     d.type = e.type;
     d.n_slices = (int16_t)(is_spin_type(e.type) ? e.n_slices : 1);
     d.flags = (e.fringe && e.type != ST_SOLENOID) ? ST_ELEM_FRINGE : 0;
+    if (e.split_order == 4 && (e.type == ST_MULT || e.type == ST_QUAD_MK)) d.flags |= ST_ELEM_ORDER4;
     switch (e.type) {
     case ST_DRIFT:
         d.ds = e.L;
@@ -49,6 +50,19 @@ DevElem pack_element(const st_element& e) {
         d.a[0] = e.k1;
         d.a[1] = std::fabs(e.k1);
         break;
+    default:
+        break;
+    }
+    if (d.flags & ST_ELEM_ORDER4) {
+        // Yoshida (1990): S2(x1 ds) S2(x0 ds) S2(x1 ds) is fourth order for a
+        // symmetric second-order S2 when 2 x1 + x0 = 1 and 2 x1^3 + x0^3 = 0
+        const double x1 = 1.0 / (2.0 - std::cbrt(2.0)), x0 = 1.0 - 2.0 * x1;
+        d.a[2] = 0.5 * x1 * d.ds;
+        d.a[3] = 0.5 * (x1 + x0) * d.ds;
+        d.a[4] = x1 * d.ds;
+        d.a[5] = x0 * d.ds;
+    }
+    switch (e.type) {
     case ST_SBEND: {
         d.ds = e.L / e.n_slices;
         double h = e.angle / e.L;
@@ -119,6 +133,11 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
         }
         if (e.fringe && (e.type == ST_DRIFT || e.type == ST_SNAKE)) {
             set_error("element %d: fringe kicks need a multipole, quadrupole, bend or solenoid", i);
+            return ST_EINVAL;
+        }
+        if ((e.split_order != 0 && e.split_order != 2 && e.split_order != 4) ||
+            (e.split_order == 4 && e.type != ST_MULT && e.type != ST_QUAD_MK)) {
+            set_error("element %d: split_order must be 0 or 2, or 4 for a multipole or matrix-kick quadrupole", i);
             return ST_EINVAL;
         }
         if (e.type == ST_DRIFT && !(e.L >= 0.0)) {

@@ -82,7 +82,9 @@ extern "C" int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, c
             (is_spin_type(e.type) && (!(e.L > 0.0) || e.n_slices < 1 || e.n_slices > 4096 ||
                                       e.n_slices % (1 << spin_order) != 0)) ||
             (e.type == ST_DRIFT && !(e.L >= 0.0)) || (e.type == ST_SBEND && (e.angle == 0.0 || e.eta == 0.0)) ||
-            (e.fringe != 0 && e.fringe != 1) || (e.fringe && (e.type == ST_DRIFT || e.type == ST_SNAKE))) {
+            (e.fringe != 0 && e.fringe != 1) || (e.fringe && (e.type == ST_DRIFT || e.type == ST_SNAKE)) ||
+            (e.split_order != 0 && e.split_order != 2 && e.split_order != 4) ||
+            (e.split_order == 4 && e.type != ST_MULT && e.type != ST_QUAD_MK)) {
             set_error("st_track_fp64_noalloc: element %d invalid (type, length, slices, bend parameters or fringe)", i);
             return ST_EINVAL;
         }

@@ -16,17 +16,20 @@ namespace st {
 struct __align__(16) DevElem {
     int32_t type;
     int16_t n_slices;
-    int16_t flags;  // ST_ELEM_FRINGE: thin fringe spin kicks at both ends (mult, quad, sbend)
+    int16_t flags;  // ST_ELEM_FRINGE: thin fringe spin kicks at both ends (mult, quad, sbend);
+                    // ST_ELEM_ORDER4: fourth-order slice map (mult, quad; a[2..5] its sub-steps)
     double ds;      // slice length (drift: full length)
     double a[6];    // type-specific constants, see pack_element()
 };
-enum { ST_ELEM_FRINGE = 1 };
+enum { ST_ELEM_FRINGE = 1, ST_ELEM_ORDER4 = 2 };
 static_assert(sizeof(DevElem) == 64, "DevElem must be 64 bytes");
 
 // a[] layout per type
 //   ST_DRIFT   : (unused)
 //   ST_MULT    : a0 = k1, a1 = k2
 //   ST_QUAD_MK : a0 = k1, a1 = |k1|
+//   (both, fourth-order map: a2 = x1 ds/2, a3 = (x1 + x0) ds/2, a4 = x1 ds,
+//    a5 = x0 ds with Yoshida's x1 = 1/(2 - 2^(1/3)), x0 = 1 - 2 x1)
 //   ST_SBEND   : a0 = h, a1 = eta, a2 = cos(h ds), a3 = sin(h ds),
 //                a4 = 1/(eta h), a5 = 1/eta
 //   ST_SNAKE   : a0..a3 = unit quaternion (scalar first)

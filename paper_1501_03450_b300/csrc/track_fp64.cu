@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(128, 3) track_fp64_kernel(const void* __restri
                                                          TurnOut tq) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
-    __shared__ double qcache[QC_N * 128];
+    __shared__ double qcache[(2 * QC_N + 2) * 128];
     if (!stage_to_smem(smem, blob, blob_bytes, &bar, status)) return;
     const DevElem* table = (const DevElem*)smem;
     const uint16_t* seq = (const uint16_t*)(smem + seq_offset);

@@ -39,14 +39,17 @@ struct QuadCache {
     double* col;      // &smem[0][threadIdx.x]
     int stride;       // blockDim.x
     __device__ __forceinline__ double get(int f) const { return col[f * stride]; }
+    // re-read on every use (not hoisted into registers across a loop)
+    __device__ __forceinline__ double getv(int f) const { return *(const volatile double*)&col[f * stride]; }
     __device__ __forceinline__ void set(int f, double v) { col[f * stride] = v; }
 };
 enum { QC_C1, QC_S1, QC_AL1, QC_BE1, QC_GA1, QC_C2, QC_S2, QC_AL2, QC_BE2, QC_GA2, QC_N };
 
-__device__ __forceinline__ void quad_coeffs(QuadCache& qc, const PConst& pc, double absk1, double s) {
-    qc.key_k = absk1;
-    qc.key_s = s;
-    double w = sqrt(absk1 * pc.invP);
+// Fill one coefficient set (column col, row stride) for (|k1|, s).  Called
+// only when the key changes, so it is kept out of line: its transcendental
+// functions then add no register pressure to the tracking loop.
+static __device__ __noinline__ void quad_coeffs_fill(double* col, int stride, double invP, double absk1, double s) {
+    double w = sqrt(absk1 * invP);
     double ws = w * s;
     double C1, S1, C2, S2;
     if (w > 0.0) {
@@ -65,29 +68,42 @@ __device__ __forceinline__ void quad_coeffs(QuadCache& qc, const PConst& pc, dou
         S1 = S2 = s;
     }
     // integrals over the half slice used by the T update: (s + C S)/2, S^2, (s - C S)/2
-    qc.set(QC_C1, C1);
-    qc.set(QC_S1, S1);
-    qc.set(QC_AL1, 0.5 * (s + C1 * S1));
-    qc.set(QC_BE1, S1 * S1);
-    qc.set(QC_GA1, 0.5 * (s - C1 * S1));
-    qc.set(QC_C2, C2);
-    qc.set(QC_S2, S2);
-    qc.set(QC_AL2, 0.5 * (s + C2 * S2));
-    qc.set(QC_BE2, S2 * S2);
-    qc.set(QC_GA2, 0.5 * (s - C2 * S2));
+    col[QC_C1 * stride] = C1;
+    col[QC_S1 * stride] = S1;
+    col[QC_AL1 * stride] = 0.5 * (s + C1 * S1);
+    col[QC_BE1 * stride] = S1 * S1;
+    col[QC_GA1 * stride] = 0.5 * (s - C1 * S1);
+    col[QC_C2 * stride] = C2;
+    col[QC_S2 * stride] = S2;
+    col[QC_AL2 * stride] = 0.5 * (s + C2 * S2);
+    col[QC_BE2 * stride] = S2 * S2;
+    col[QC_GA2 * stride] = 0.5 * (s - C2 * S2);
+}
+
+__device__ __forceinline__ void quad_coeffs(QuadCache& qc, const PConst& pc, double absk1, double s) {
+    qc.key_k = absk1;
+    qc.key_s = s;
+    quad_coeffs_fill(qc.col, qc.stride, pc.invP, absk1, s);
 }
 
 // Linear quadrupole flow H_qL over s (Eq. (24)); per plane with focusing
 // constant K_u = +-k1/P: u' = u C + (pu/P) S, pu' = pu C - P K_u u S, and
 // T' = T - (1/beta0 + Pt)/(2 P^3) * sum_u [pu^2 (s + C S)/2 - P K_u u pu S^2
 //                                          + P^2 K_u u^2 (s - C S)/2].
+template <bool REREAD>
+__device__ __forceinline__ double qcget(const QuadCache& qc, int f) {
+    if constexpr (REREAD) return qc.getv(f);
+    return qc.get(f);
+}
+
+template <bool REREAD = false>
 __device__ __forceinline__ void quad_linear(Particle& p, const PConst& pc, const QuadCache& qc, double k1) {
     const bool foc = k1 >= 0.0;
     const int ox_ = foc ? 0 : 5, oy_ = foc ? 5 : 0;   // field offsets of the x and y planes
-    const double Cx = qc.get(QC_C1 + ox_), Sx = qc.get(QC_S1 + ox_);
-    const double Cy = qc.get(QC_C1 + oy_), Sy = qc.get(QC_S1 + oy_);
-    const double alx = qc.get(QC_AL1 + ox_), bex = qc.get(QC_BE1 + ox_), gax = qc.get(QC_GA1 + ox_);
-    const double aly = qc.get(QC_AL1 + oy_), bey = qc.get(QC_BE1 + oy_), gay = qc.get(QC_GA1 + oy_);
+    const double Cx = qcget<REREAD>(qc, QC_C1 + ox_), Sx = qcget<REREAD>(qc, QC_S1 + ox_);
+    const double Cy = qcget<REREAD>(qc, QC_C1 + oy_), Sy = qcget<REREAD>(qc, QC_S1 + oy_);
+    const double alx = qcget<REREAD>(qc, QC_AL1 + ox_), bex = qcget<REREAD>(qc, QC_BE1 + ox_), gax = qcget<REREAD>(qc, QC_GA1 + ox_);
+    const double aly = qcget<REREAD>(qc, QC_AL1 + oy_), bey = qcget<REREAD>(qc, QC_BE1 + oy_), gay = qcget<REREAD>(qc, QC_GA1 + oy_);
     double X = p.X, Px = p.Px, Y = p.Y, Py = p.Py;
     double Pk = pc.P * k1;   // P^2 K_x = P k1
     double tsum = Px * Px * alx - k1 * X * Px * bex + Pk * X * X * gax
@@ -108,6 +124,31 @@ __device__ __forceinline__ double inv_sqrt_diff(double a2, double ia, double ia2
     const double e = p2 * ia2;
     if (e < 1e-6) return ia * fma(e, fma(e, 0.375, 0.5), 1.0);
     return rsqrt(a2 - p2);
+}
+
+// Nonlinear remainder H_qNL of the quadrupole over s, Eq. (25).
+__device__ __forceinline__ void quad_nonlinear(Particle& p, const PConst& pc, const RefConst& ref, double s) {
+    const double pp = p.Px * p.Px + p.Py * p.Py;
+    const double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+    const double d = ips - pc.invP;
+    p.X += s * p.Px * d;
+    p.Y += s * p.Py * d;
+    p.T += -s * pc.b0pt * (ips - pc.invP * pp * 0.5 * pc.invP2) + s * ref.inv_beta0;
+}
+
+// Exact drift over s (Eq. (29b)) given ips = 1/Ps of the current momentum.
+__device__ __forceinline__ void dkd_drift(Particle& p, const PConst& pc, const RefConst& ref, double ips, double s) {
+    p.X += s * p.Px * ips;
+    p.Y += s * p.Py * ips;
+    p.T += s * (ref.inv_beta0 - pc.b0pt * ips);
+}
+
+// Multipole kick over s (Eq. (28)): quadrupole k1 and sextupole k2 (MAD).
+__device__ __forceinline__ void mult_kick(Particle& p, double k1, double k2, double s) {
+    const double by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
+    const double bx = k1 * p.Y + k2 * p.X * p.Y;
+    p.Px -= s * by;
+    p.Py += s * bx;
 }
 
 // Precession vector Omega (Eq. (6b)) for a transverse field b = (bx, by, 0),
@@ -246,6 +287,9 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
     qc.key_s = 0.0;
     qc.col = &qcache[threadIdx.x];
     qc.stride = blockDim.x;
+    // second coefficient set (the inner linear sub-step of fourth-order maps)
+    // in rows QC_N..2 QC_N-1, its key in rows 2 QC_N, 2 QC_N+1
+    qc.col[(2 * QC_N) * qc.stride] = -1.0;
     LevelProducts<K> lv;
     bool is_lost = false;
 
@@ -381,7 +425,24 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
                     lv.add_edge(0, N, ds, ox, oy, os);
                 }
+                const bool o4 = el.flags & ST_ELEM_ORDER4;
                 for (int s = 1; s <= N; ++s) {
+                    if (o4) {
+                        // Yoshida's fourth-order product of three DKD maps, the
+                        // adjacent half drifts merged: D K D' K0 D' K D
+                        dkd_drift(p, pc, ref, ips, el.a[2]);
+                        mult_kick(p, k1, k2, el.a[4]);
+                        ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Px * p.Px + p.Py * p.Py);
+                        dkd_drift(p, pc, ref, ips, el.a[3]);
+                        mult_kick(p, k1, k2, el.a[5]);
+                        ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Px * p.Px + p.Py * p.Py);
+                        dkd_drift(p, pc, ref, ips, el.a[3]);
+                        mult_kick(p, k1, k2, el.a[4]);
+                        pp = p.Px * p.Px + p.Py * p.Py;
+                        ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                        Ps = (pc.P2 - pp) * ips;
+                        dkd_drift(p, pc, ref, ips, el.a[2]);
+                    } else {
                     p.X += half * p.Px * ips;
                     p.Y += half * p.Py * ips;
                     p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
@@ -395,6 +456,7 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     p.X += half * p.Px * ips;
                     p.Y += half * p.Py * ips;
                     p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
+                    }
                     bx = k1 * p.Y + k2 * p.X * p.Y;
                     by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
                     if constexpr (SPIN) {
@@ -404,8 +466,17 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 }
             } else {   // ST_QUAD_MK
                 const double k1 = el.a[0], absk = el.a[1];
-                const double half = 0.5 * ds;
+                const bool o4 = el.flags & ST_ELEM_ORDER4;
+                const double half = o4 ? el.a[2] : 0.5 * ds;   // outer linear sub-step
                 if (qc.key_k != absk || qc.key_s != half) quad_coeffs(qc, pc, absk, half);
+                if (o4) {
+                    double* key2 = qc.col + (2 * QC_N) * qc.stride;
+                    if (key2[0] != absk || key2[qc.stride] != el.a[3]) {
+                        quad_coeffs_fill(qc.col + QC_N * qc.stride, qc.stride, pc.invP, absk, el.a[3]);
+                        key2[0] = absk;
+                        key2[qc.stride] = el.a[3];
+                    }
+                }
                 double pp = p.Px * p.Px + p.Py * p.Py;
                 double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
                 double Ps = (pc.P2 - pp) * ips;
@@ -415,13 +486,18 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 }
                 for (int s = 1; s <= N; ++s) {
                     quad_linear(p, pc, qc, k1);
-                    // nonlinear remainder H_qNL over ds, Eq. (25)
-                    pp = p.Px * p.Px + p.Py * p.Py;
-                    ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
-                    double d = ips - pc.invP;
-                    p.X += ds * p.Px * d;
-                    p.Y += ds * p.Py * d;
-                    p.T += -ds * pc.b0pt * (ips - pc.invP * pp * 0.5 * pc.invP2) + ds * ref.inv_beta0;
+                    if (o4) {
+                        // Yoshida's fourth-order product of three MK maps, the
+                        // adjacent linear half steps merged: L N L' N0 L' N L
+                        const QuadCache qc2{0.0, 0.0, qc.col + QC_N * qc.stride, qc.stride};
+                        quad_nonlinear(p, pc, ref, el.a[4]);
+                        quad_linear<true>(p, pc, qc2, k1);
+                        quad_nonlinear(p, pc, ref, el.a[5]);
+                        quad_linear<true>(p, pc, qc2, k1);
+                        quad_nonlinear(p, pc, ref, el.a[4]);
+                    } else {
+                        quad_nonlinear(p, pc, ref, ds);   // H_qNL over ds, Eq. (25)
+                    }
                     quad_linear(p, pc, qc, k1);
                     pp = p.Px * p.Px + p.Py * p.Py;
                     ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);

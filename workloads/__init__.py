@@ -91,6 +91,16 @@ def with_fringes(ring: Dict, on: int = 1) -> Dict:
     return out
 
 
+def with_split_order(ring: Dict, order: int) -> Dict:
+    """Copy of `ring` whose multipoles and matrix-kick quadrupoles use the
+    second-order (2) or fourth-order (4) slice map (Sec. 3.3)."""
+    out = dict(ring)
+    out["elements"] = [dict(e, split_order=int(order)) if e["type"] in ("mult", "quad_mk") else dict(e)
+                       for e in ring["elements"]]
+    out["name"] = ring["name"] + (f"_split{order}" if order != 2 else "")
+    return out
+
+
 def reference(Ggamma0: float, G: float = G_PROTON):
     """(gamma0, beta0) of the scale momentum for a given naive spin tune."""
     gamma0 = Ggamma0 / G
