@@ -176,6 +176,7 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
         }
         seq[i] = (uint16_t)idx;
         if (d.type == ST_SOLENOID || d.flags) L.fp64_only = true;
+        if (d.flags & ST_ELEM_ORDER4) L.has_order4 = true;
         if (is_spin_type(d.type)) {
             max_slices = std::max(max_slices, (int)d.n_slices);
             int p = 0;

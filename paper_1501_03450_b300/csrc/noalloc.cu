@@ -140,6 +140,8 @@ extern "C" int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, c
         L.blob_bytes = table_bytes + seq_bytes;
         L.table_bytes = table_bytes;
         L.seq_offset = table_bytes;
+        for (int u = 0; u < n_unique; ++u)
+            if (table[u].flags & ST_ELEM_ORDER4) L.has_order4 = true;
         st_ctx ctx;
         ctx.lat = &lat;
         ctx.n = n_particles;

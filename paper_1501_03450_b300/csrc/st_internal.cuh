@@ -107,7 +107,8 @@ struct LatticeImpl {
     int32_t n_unique;
     int32_t max_slices;
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
-    bool fp64_only = false;        // solenoids or fringe spin kicks: FP64 tracker only
+    bool fp64_only = false;        // solenoids, fringe spin kicks or fourth-order maps: FP64 only
+    bool has_order4 = false;       // some element uses the fourth-order slice map
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]
     void* d_blob = nullptr;
     size_t blob_bytes = 0;

@@ -7,7 +7,7 @@
 
 namespace st {
 
-template <int K, bool SPIN = true>
+template <int K, bool SPIN = true, bool ORDER4 = false>
 __global__ void __launch_bounds__(128, 3) track_fp64_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
                                                          uint32_t seq_offset, int n_seq, RefConst ref,
                                                          double2* __restrict__ xpx, double2* __restrict__ ypy,
@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(128, 3) track_fp64_kernel(const void* __restri
     const int64_t i = wi * 32 + lane;
     if (i >= n || lost[i]) continue;
 
-    fp64_track_particle<K, SPIN>(table, seq, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns, qcache, tq);
+    fp64_track_particle<K, SPIN, ORDER4>(table, seq, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns, qcache,
+                                         tq);
     }  // particle loop
 }
 
@@ -83,14 +84,14 @@ int launch_unpack(st_ctx* ctx, double* z, double* s) {
     return e == cudaSuccess ? ST_OK : cuda_fail(e, "unpack kernel launch");
 }
 
-template <int K, bool SPIN = true>
-static int launch_k(st_ctx* ctx, int n_turns, const TurnOut& tq) {
+template <int K, bool SPIN, bool ORDER4>
+static int launch_k_(st_ctx* ctx, int n_turns, const TurnOut& tq) {
     const LatticeImpl& L = ctx->lat->impl;
     const int threads = ctx->block_threads;
     const size_t smem = L.blob_bytes;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(track_fp64_kernel<K, SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(track_fp64_kernel<K, SPIN, ORDER4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fp64 tracker)");
         attr_set = true;
@@ -99,7 +100,7 @@ static int launch_k(st_ctx* ctx, int n_turns, const TurnOut& tq) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_fp64_kernel<K, SPIN>, threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_fp64_kernel<K, SPIN, ORDER4>, threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "fp64 tracker occupancy query");
     if (per_sm < 1) {
         set_error("fp64 tracker: block of %d threads with %zu B shared memory does not fit on an SM", threads,
@@ -113,13 +114,20 @@ static int launch_k(st_ctx* ctx, int n_turns, const TurnOut& tq) {
     const int tpl = ctx->turns_per_launch;
     for (int t = 0; t < n_turns; t += tpl) {
         int nt = n_turns - t < tpl ? n_turns - t : tpl;
-        track_fp64_kernel<K, SPIN><<<(unsigned)grid, threads, smem, ctx->stream>>>(
+        track_fp64_kernel<K, SPIN, ORDER4><<<(unsigned)grid, threads, smem, ctx->stream>>>(
             L.d_blob, (uint32_t)L.blob_bytes, (uint32_t)L.seq_offset, L.n_elements, L.ref, ctx->xpx, ctx->ypy,
             ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status, tq);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "fp64 tracker launch");
     }
     return ST_OK;
+}
+
+// The fourth-order instantiation only for lattices with fourth-order elements.
+template <int K, bool SPIN = true>
+static int launch_k(st_ctx* ctx, int n_turns, const TurnOut& tq) {
+    return ctx->lat->impl.has_order4 ? launch_k_<K, SPIN, true>(ctx, n_turns, tq)
+                                     : launch_k_<K, SPIN, false>(ctx, n_turns, tq);
 }
 
 // Orbit only (spins untouched): the orbit maps of the FP64 tracker without the

@@ -253,7 +253,10 @@ struct TurnOut {
     double ref[4];
 };
 
-template <int K, bool SPIN = true>
+// ORDER4: compile the fourth-order slice maps in (a separate instantiation,
+// chosen only for lattices that use them, so that the second-order loop keeps
+// its register budget).
+template <int K, bool SPIN = true, bool ORDER4 = false>
 __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ table, const uint16_t* __restrict__ seq,
                                                     int n_seq, const RefConst& ref, double2* __restrict__ xpx,
                                                     double2* __restrict__ ypy, double2* __restrict__ tpt,
@@ -413,7 +416,7 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                         lv.add_edge(s, N, ds, ox, oy, os);
                     }
                 }
-            } else if (type == ST_MULT) {
+            } else if (type == ST_MULT && !(el.flags & ST_ELEM_ORDER4)) {
                 const double k1 = el.a[0], k2 = el.a[1];
                 const double half = 0.5 * ds;
                 double pp = p.Px * p.Px + p.Py * p.Py;
@@ -425,24 +428,7 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
                     lv.add_edge(0, N, ds, ox, oy, os);
                 }
-                const bool o4 = el.flags & ST_ELEM_ORDER4;
                 for (int s = 1; s <= N; ++s) {
-                    if (o4) {
-                        // Yoshida's fourth-order product of three DKD maps, the
-                        // adjacent half drifts merged: D K D' K0 D' K D
-                        dkd_drift(p, pc, ref, ips, el.a[2]);
-                        mult_kick(p, k1, k2, el.a[4]);
-                        ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Px * p.Px + p.Py * p.Py);
-                        dkd_drift(p, pc, ref, ips, el.a[3]);
-                        mult_kick(p, k1, k2, el.a[5]);
-                        ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Px * p.Px + p.Py * p.Py);
-                        dkd_drift(p, pc, ref, ips, el.a[3]);
-                        mult_kick(p, k1, k2, el.a[4]);
-                        pp = p.Px * p.Px + p.Py * p.Py;
-                        ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
-                        Ps = (pc.P2 - pp) * ips;
-                        dkd_drift(p, pc, ref, ips, el.a[2]);
-                    } else {
                     p.X += half * p.Px * ips;
                     p.Y += half * p.Py * ips;
                     p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
@@ -456,7 +442,6 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     p.X += half * p.Px * ips;
                     p.Y += half * p.Py * ips;
                     p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
-                    }
                     bx = k1 * p.Y + k2 * p.X * p.Y;
                     by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
                     if constexpr (SPIN) {
@@ -464,12 +449,40 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                         lv.add_edge(s, N, ds, ox, oy, os);
                     }
                 }
-            } else {   // ST_QUAD_MK
+            } else if (type == ST_QUAD_MK && !(el.flags & ST_ELEM_ORDER4)) {
                 const double k1 = el.a[0], absk = el.a[1];
-                const bool o4 = el.flags & ST_ELEM_ORDER4;
-                const double half = o4 ? el.a[2] : 0.5 * ds;   // outer linear sub-step
+                const double half = 0.5 * ds;
                 if (qc.key_k != absk || qc.key_s != half) quad_coeffs(qc, pc, absk, half);
-                if (o4) {
+                double pp = p.Px * p.Px + p.Py * p.Py;
+                double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                double Ps = (pc.P2 - pp) * ips;
+                if constexpr (SPIN) {
+                    precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
+                    lv.add_edge(0, N, ds, ox, oy, os);
+                }
+                for (int s = 1; s <= N; ++s) {
+                    quad_linear(p, pc, qc, k1);
+                    quad_nonlinear(p, pc, ref, ds);   // H_qNL over ds, Eq. (25)
+                    quad_linear(p, pc, qc, k1);
+                    pp = p.Px * p.Px + p.Py * p.Py;
+                    ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                    Ps = (pc.P2 - pp) * ips;
+                    if constexpr (SPIN) {
+                        precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
+                        lv.add_edge(s, N, ds, ox, oy, os);
+                    }
+                }
+            } else if constexpr (ORDER4) {
+                // fourth-order multipole (DKD) or matrix-kick quadrupole:
+                // Yoshida's product S2(x1 ds) S2(x0 ds) S2(x1 ds) of the
+                // symmetric maps with adjacent half steps merged,
+                // D K D' K0 D' K D or L N L' N0 L' N L; the spin is sampled at
+                // the slice edges as for the second-order maps
+                const bool is_quad = type == ST_QUAD_MK;
+                const double k1 = el.a[0], k2 = is_quad ? 0.0 : el.a[1];
+                if (is_quad) {
+                    const double absk = el.a[1];
+                    if (qc.key_k != absk || qc.key_s != el.a[2]) quad_coeffs(qc, pc, absk, el.a[2]);
                     double* key2 = qc.col + (2 * QC_N) * qc.stride;
                     if (key2[0] != absk || key2[qc.stride] != el.a[3]) {
                         quad_coeffs_fill(qc.col + QC_N * qc.stride, qc.stride, pc.invP, absk, el.a[3]);
@@ -481,29 +494,38 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
                 double Ps = (pc.P2 - pp) * ips;
                 if constexpr (SPIN) {
-                    precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
+                    precession(p, pc, k1 * p.Y + k2 * p.X * p.Y, k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y), 0.0,
+                               ips, Ps, ox, oy, os);
                     lv.add_edge(0, N, ds, ox, oy, os);
                 }
                 for (int s = 1; s <= N; ++s) {
-                    quad_linear(p, pc, qc, k1);
-                    if (o4) {
-                        // Yoshida's fourth-order product of three MK maps, the
-                        // adjacent linear half steps merged: L N L' N0 L' N L
+                    if (is_quad) {
                         const QuadCache qc2{0.0, 0.0, qc.col + QC_N * qc.stride, qc.stride};
+                        quad_linear<true>(p, pc, qc, k1);
                         quad_nonlinear(p, pc, ref, el.a[4]);
                         quad_linear<true>(p, pc, qc2, k1);
                         quad_nonlinear(p, pc, ref, el.a[5]);
                         quad_linear<true>(p, pc, qc2, k1);
                         quad_nonlinear(p, pc, ref, el.a[4]);
+                        quad_linear<true>(p, pc, qc, k1);
                     } else {
-                        quad_nonlinear(p, pc, ref, ds);   // H_qNL over ds, Eq. (25)
+                        dkd_drift(p, pc, ref, ips, el.a[2]);
+                        mult_kick(p, k1, k2, el.a[4]);
+                        ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Px * p.Px + p.Py * p.Py);
+                        dkd_drift(p, pc, ref, ips, el.a[3]);
+                        mult_kick(p, k1, k2, el.a[5]);
+                        ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Px * p.Px + p.Py * p.Py);
+                        dkd_drift(p, pc, ref, ips, el.a[3]);
+                        mult_kick(p, k1, k2, el.a[4]);
+                        ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, p.Px * p.Px + p.Py * p.Py);
+                        dkd_drift(p, pc, ref, ips, el.a[2]);
                     }
-                    quad_linear(p, pc, qc, k1);
                     pp = p.Px * p.Px + p.Py * p.Py;
                     ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
                     Ps = (pc.P2 - pp) * ips;
                     if constexpr (SPIN) {
-                        precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
+                        precession(p, pc, k1 * p.Y + k2 * p.X * p.Y, k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y),
+                                   0.0, ips, Ps, ox, oy, os);
                         lv.add_edge(s, N, ds, ox, oy, os);
                     }
                 }
