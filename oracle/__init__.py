@@ -33,7 +33,7 @@ _VARIANTS = {
     "c128": ("double complex", np.complex128),
 }
 
-TYPE_CODES = {"drift": 0, "mult": 1, "quad_mk": 2, "sbend": 3, "snake": 4, "solenoid": 5}
+TYPE_CODES = {"drift": 0, "mult": 1, "quad_mk": 2, "sbend": 3, "snake": 4, "solenoid": 5, "rbend": 6}
 
 _lock = threading.Lock()
 _libs = {}
@@ -44,7 +44,7 @@ class OrcElement(ctypes.Structure):
                 ("L", ctypes.c_double), ("k1", ctypes.c_double), ("k2", ctypes.c_double),
                 ("angle", ctypes.c_double), ("eta", ctypes.c_double),
                 ("snake_phi", ctypes.c_double), ("snake_mu", ctypes.c_double),
-                ("fringe", ctypes.c_int32), ("split_order", ctypes.c_int32)]
+                ("fringe", ctypes.c_int32), ("split_order", ctypes.c_int32), ("e1", ctypes.c_double)]
 
 
 def _lib_path(variant: str) -> str:
@@ -104,7 +104,8 @@ def elements_array(elements):
     arr = (OrcElement * max(1, len(elements)))()
     for i, e in enumerate(elements):
         arr[i] = OrcElement(TYPE_CODES[e["type"]], int(e["n_slices"]), e["L"], e["k1"], e["k2"],
-                            e["angle"], e["eta"], e["snake_phi"], e["snake_mu"], int(e.get("fringe", 0)), int(e.get("split_order", 2)))
+                            e["angle"], e["eta"], e["snake_phi"], e["snake_mu"], int(e.get("fringe", 0)), int(e.get("split_order", 2)),
+                            float(e.get("e1", 0.0)))
     return arr
 
 
@@ -150,7 +151,8 @@ def orbit_map(el, G, Ggamma0, z6, variant="f64"):
     return z6, rc
 
 
-SUBFLOWS = {"drift": 0, "kick": 1, "quad_linear": 2, "quad_nonlinear": 3, "sbend": 4, "solenoid": 5}
+SUBFLOWS = {"drift": 0, "kick": 1, "quad_linear": 2, "quad_nonlinear": 3, "sbend": 4, "solenoid": 5,
+            "rbend_body": 6, "rbend_rotation": 7, "rbend_fringe": 8}
 
 
 def subflow(which, G, Ggamma0, z6, s, k1=0.0, k2=0.0, h=0.0, eta=1.0, variant="f64"):

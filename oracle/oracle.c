@@ -19,6 +19,11 @@
  *   Sec. 3.3  (closing remark) higher-order versions of the symmetric split of
  *             Eq. (27): Yoshida's fourth-order composition of the
  *             second-order slice map, on elements with split_order 4
+ *   Sec. 3.2  rectangular bend: dynamic rotations into and out of the
+ *             magnet's Cartesian frame, Eqs. (Hprot), (prot); thin-fringe
+ *             orbit map, Eq. (dipolefringe); exact body map, Eqs. (rhob),
+ *             (rbend); offsets, Eqs. (Xoffset), (Toffset); fringe spin kick
+ *             of a rectangular bend, Eq. (skfringeRB)
  *   Sec. 3.7  solenoid: exact body map Eq. (solenoid) of the Hamiltonian
  *             Eq. (Hsolenoid) with the vector potential Eq. (Asol); the
  *             unit velocity from the kinetic momentum, Eq. (mgVSol)
@@ -70,7 +75,7 @@ typedef ORACLE_REAL real;
 #define RE(x) ((double)creal(x))
 
 /* Element kinds (own numbering; the CUDA library has its own). */
-enum { ORC_DRIFT = 0, ORC_MULT = 1, ORC_QUAD_MK = 2, ORC_SBEND = 3, ORC_SNAKE = 4, ORC_SOLENOID = 5 };
+enum { ORC_DRIFT = 0, ORC_MULT = 1, ORC_QUAD_MK = 2, ORC_SBEND = 3, ORC_SNAKE = 4, ORC_SOLENOID = 5, ORC_RBEND = 6 };
 
 typedef struct {
     int32_t type;
@@ -78,6 +83,8 @@ typedef struct {
     double L, k1, k2, angle, eta, snake_phi, snake_mu;
     int32_t fringe;      /* 1: thin fringe spin kicks at both ends (mult, quad_mk, sbend) */
     int32_t split_order; /* mult, quad_mk: 0 or 2 = Eq. (27), 4 = Yoshida's fourth order */
+    double e1;           /* rbend: the beam meets the entrance face at phi_entr = angle/2 + e1
+                          * and the exit face at phi_exit = -angle/2 + e1 */
 } orc_element;
 
 typedef struct {
@@ -270,6 +277,84 @@ static int solenoid_map(const orc_ref* r, orc_orbit* z, double ks, double s) {
 }
 
 /* One integration slice of length ds of a spin-carrying element. */
+/* Rectangular bend, Sec. 3.2.  The magnet's Cartesian frame has both faces
+ * normal to its axis; the beam meets the entrance face at phi_entr and the
+ * exit face at phi_exit (total bend phi_entr - phi_exit = angle).  The design
+ * field makes the reference particle enter with Px = sin(phi_entr) and leave
+ * with Px = sin(phi_exit) after the magnet length L, so that
+ * b1/(B rho) = 1/rho_b = eta (sin phi_entr - sin phi_exit) / L (Eq. (rhob)). */
+static void rbend_geometry(const orc_element* e, double* phi_in, double* phi_out, double* b) {
+    *phi_in = 0.5 * e->angle + e->e1;
+    *phi_out = -0.5 * e->angle + e->e1;
+    *b = e->eta * (sin(*phi_in) - sin(*phi_out)) / e->L;
+}
+
+/* Body of the rectangular bend over a length s, Eq. (rbend): Px falls
+ * linearly, X follows from the longitudinal momentum, Y and T from the change
+ * of the angle asin(Px/P_alpha).  T is the printed form (the reference
+ * particle's time across the magnet, -L_arc/beta0, is removed by Eq. (Toffset)
+ * at the end of the element). */
+static int rbend_body(const orc_ref* r, orc_orbit* z, double b, double s) {
+    real Pa2 = momentum_sq(r, z->Pt) - z->Py * z->Py;
+    real Pxf = z->Px - s * b;
+    real qi = Pa2 - z->Px * z->Px, qf = Pa2 - Pxf * Pxf;
+    if (!(RE(qi) > 0.0) || !(RE(qf) > 0.0)) return 1;
+    real Pa = sqrt(Pa2);
+    real dpsi = asin(z->Px / Pa) - asin(Pxf / Pa);
+    z->X += (sqrt(qf) - sqrt(qi)) / b;
+    z->Y += z->Py * dpsi / b;
+    z->T -= (1.0 / r->beta0 + z->Pt) * dpsi / b;
+    z->Px = Pxf;
+    return 0;
+}
+
+/* Dynamic rotation by phi: the flow of H_prot = -X Ps (Eq. (Hprot)) with phi
+ * as the independent variable, Eq. (prot).  The arrival-time update takes the
+ * sign of Hamilton's equation dT/dphi = dH/dPt = -X (1/beta0 + Pt)/Ps (the
+ * same sign as the drift towards the rotated face implied by the Y update);
+ * the printed Eq. (prot) shows the opposite sign for T. */
+static int rbend_rotation(const orc_ref* r, orc_orbit* z, double phi) {
+    real ps2 = momentum_sq(r, z->Pt) - z->Px * z->Px - z->Py * z->Py;
+    if (!(RE(ps2) > 0.0)) return 1;
+    real Ps = sqrt(ps2);
+    real t = tan(phi);
+    real den = 1.0 - z->Px / Ps * t;
+    if (!(RE(den) > 0.0)) return 1;
+    real d = z->X * t / den;              /* longitudinal distance to the rotated face */
+    real Px = z->Px * cos(phi) + Ps * sin(phi);
+    z->Y += z->Py / Ps * d;
+    z->T -= (1.0 / r->beta0 + z->Pt) / Ps * d;
+    z->X = z->X / (cos(phi) * den);
+    z->Px = Px;
+    return 0;
+}
+
+/* Thin dipole fringe of the rectangular bend without a finite-gap correction,
+ * Eq. (dipolefringe), sign +1 at the entrance and -1 at the exit; bs =
+ * b1/(B rho); x' = Px/Ps, y' = Py/Ps and Ps from the incoming momenta.  The
+ * map is the canonical transformation generated by
+ *   Phi = -(sign bs / 2) x'/(1 + y'^2) Y_f^2
+ * (new coordinates, old momenta): X, Py and T follow Eq. (dipolefringe) as
+ * printed; Y_f solves Y_i = Y_f + (sign bs / 2) x'y'/(Ps (1 + y'^2)) Y_f^2,
+ * i.e. the printed root with the factor 1/Ps inside the square root, which
+ * the printed equation omits (without it the map is not symplectic). */
+static int rbend_fringe_orbit(const orc_ref* r, orc_orbit* z, double bs, int sign) {
+    real ps2 = momentum_sq(r, z->Pt) - z->Px * z->Px - z->Py * z->Py;
+    if (!(RE(ps2) > 0.0)) return 1;
+    real Ps = sqrt(ps2);
+    real xp = z->Px / Ps, yp = z->Py / Ps;
+    real g = 1.0 + yp * yp;
+    real sb = sign * bs;
+    real arg = 1.0 + sb * (xp * yp / (g * Ps)) * 2.0 * z->Y;
+    if (!(RE(arg) > 0.0)) return 1;
+    real Yf = 2.0 * z->Y / (1.0 + sqrt(arg));
+    z->X += sb / (2.0 * Ps) * ((1.0 + xp * xp) / g - 2.0 * (xp * yp) * (xp * yp) / (g * g)) * Yf * Yf;
+    z->Py -= sb * xp / g * Yf;
+    z->T -= sb * (1.0 / r->beta0 + z->Pt) * xp / (2.0 * ps2) * (1.0 - yp * yp) / (g * g) * Yf * Yf;
+    z->Y = Yf;
+    return 0;
+}
+
 static int slice_map2(const orc_ref* r, const orc_element* e, orc_orbit* z, double ds) {
     switch (e->type) {
     case ORC_MULT:   /* drift-kick-drift, Sec. 3.4 with the symmetric form of Eq. (27) */
@@ -285,6 +370,11 @@ static int slice_map2(const orc_ref* r, const orc_element* e, orc_orbit* z, doub
         return sbend_map(r, z, e->angle / e->L, e->eta, ds);
     case ORC_SOLENOID: /* exact body map, Eq. (solenoid) */
         return solenoid_map(r, z, e->k1, ds);
+    case ORC_RBEND: { /* exact body map in the magnet's Cartesian frame, Eq. (rbend) */
+        double pi_, po_, b;
+        rbend_geometry(e, &pi_, &po_, &b);
+        return rbend_body(r, z, b, ds);
+    }
     default:
         return 1;
     }
@@ -325,6 +415,10 @@ static int omega(const orc_ref* r, const orc_element* e, const orc_orbit* z, rea
     if (e->type == ORC_SBEND) {
         h = e->angle / e->L;
         b[1] = e->eta * h;             /* b1/(B rho) = eta h, Eq. (9) */
+    } else if (e->type == ORC_RBEND) {
+        double pi_, po_, bs;           /* uniform vertical field, straight frame (h = 0) */
+        rbend_geometry(e, &pi_, &po_, &bs);
+        b[1] = bs;
     } else if (e->type == ORC_SOLENOID) {
         /* body field along s; u from the kinetic momentum, Eq. (mgVSol) */
         real px, py;
@@ -504,12 +598,90 @@ static int element_fringe(const orc_ref* r, const orc_element* e, int sign, cons
     return 0;
 }
 
+/* Spin kick of a rectangular-bend fringe, Eq. (skfringeRB), sign +1 at the
+ * entrance and -1 at the exit, in the magnet's Cartesian frame: the dipole
+ * kick of Eq. (skfringe) (m = 1) plus the part of the longitudinal fringe
+ * field transverse to a velocity inclined by Px,
+ *   w = (+-b1/(B rho)) [ G (gamma - 1) Px Y x^ - (1 + G) Y z^ ].
+ * The factor Y of the second term is the fringe's integrated longitudinal
+ * field per unit b1/(B rho); the printed equation shows Px alone, which is not
+ * an angle. */
+static void rbend_fringe_spin(const orc_ref* r, double bs, int sign, const orc_orbit* z, real w[3]) {
+    real gamma = r->gamma0 * (1.0 + r->beta0 * z->Pt);
+    real sb = sign * bs;
+    w[0] = sb * r->G * (gamma - 1.0) * z->Px * z->Y;
+    w[1] = 0.0;
+    w[2] = -sb * (1.0 + r->G) * z->Y;
+}
+
+static void rotate_about_y(double phi, real S[3]) {
+    real w[3] = {0.0, phi, 0.0}, q[4];
+    quat_from_rotation_vector(w, q);
+    rotate_spin(q, S);
+}
+
+/* Rectangular bend through its entrance rotation (orbit, Eq. (prot), and the
+ * spin components, rotated about y by the same angle), entrance fringe (spin
+ * kick if the fringe flag is set, Eq. (skfringeRB); orbit, Eq. (dipolefringe)),
+ * the body in n_slices slices with the spin integrated as for every element
+ * (Omega of Eq. (6b) with the uniform field and h = 0), exit fringe, the
+ * horizontal offset of Eq. (Xoffset) in the magnet frame, the exit rotation by
+ * -phi_exit, and the reference time of Eq. (Toffset). */
+static int track_rbend(const orc_ref* r, const orc_element* e, orc_orbit* z, real S[3], int K,
+                       real* levels_out, real* Q_out) {
+    double phi_in, phi_out, b;
+    rbend_geometry(e, &phi_in, &phi_out, &b);
+    double sd = sin(phi_in) - sin(phi_out);
+    double x_offset = -e->L * (cos(phi_in) - cos(phi_out)) / sd;
+    double t_offset = -e->L / r->beta0 * (phi_in - phi_out) / sd;
+    if (rbend_rotation(r, z, phi_in)) return 1;
+    rotate_about_y(phi_in, S);
+    if (e->fringe) {
+        real w[3], q[4];
+        rbend_fringe_spin(r, b, +1, z, w);
+        quat_from_rotation_vector(w, q);
+        rotate_spin(q, S);
+    }
+    if (rbend_fringe_orbit(r, z, b, +1)) return 1;
+    int N = e->n_slices;
+    double ds = e->L / N;
+    real (*Om)[3] = malloc(sizeof(real[3]) * (size_t)(N + 1));
+    if (!Om) return 2;
+    int lost = omega(r, e, z, Om[0]);
+    for (int i = 1; i <= N && !lost; ++i) {
+        lost = rbend_body(r, z, b, ds);
+        if (!lost) lost = omega(r, e, z, Om[i]);
+    }
+    if (!lost) {
+        real Q[4];
+        romberg_element_rotation((const real(*)[3])Om, N, ds, K, Q, levels_out);
+        rotate_spin(Q, S);
+        if (Q_out) memcpy(Q_out, Q, sizeof(Q));
+    }
+    free(Om);
+    if (lost) return 1;
+    if (e->fringe) {
+        real w[3], q[4];
+        rbend_fringe_spin(r, b, -1, z, w);
+        quat_from_rotation_vector(w, q);
+        rotate_spin(q, S);
+    }
+    if (rbend_fringe_orbit(r, z, b, -1)) return 1;
+    z->X -= x_offset;
+    if (rbend_rotation(r, z, -phi_out)) return 1;
+    rotate_about_y(-phi_out, S);
+    z->T -= t_offset;
+    return 0;
+}
+
 /* Track one particle through one element; the spin S is rotated by the
  * element's net rotation.  Returns 0, or 1 if the particle is lost. */
 static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, real S[3],
                          int K, real* levels_out, real* Q_out) {
     if (e->type == ORC_DRIFT)
         return drift(r, z, e->L);
+    if (e->type == ORC_RBEND)
+        return track_rbend(r, e, z, S, K, levels_out, Q_out);
     if (e->type == ORC_SNAKE) {
         /* orbit-transparent rotation by snake_mu about (sin phi, 0, cos phi) */
         real Q[4] = {cos(0.5 * e->snake_mu), sin(0.5 * e->snake_mu) * sin(e->snake_phi), 0.0,
@@ -553,12 +725,16 @@ int orc_check_lattice(const orc_element* els, int n_el, int K) {
     if (K < 0 || K > ORC_MAX_ORDER) return -1;
     for (int i = 0; i < n_el; ++i) {
         const orc_element* e = &els[i];
-        if (e->type < 0 || e->type > ORC_SOLENOID) return -1;
-        if (e->type == ORC_MULT || e->type == ORC_QUAD_MK || e->type == ORC_SBEND || e->type == ORC_SOLENOID) {
+        if (e->type < 0 || e->type > ORC_RBEND) return -1;
+        if (e->type == ORC_MULT || e->type == ORC_QUAD_MK || e->type == ORC_SBEND || e->type == ORC_SOLENOID ||
+            e->type == ORC_RBEND) {
             if (e->n_slices < 1 || (e->n_slices % (1 << K)) != 0) return -1;
             if (e->L == 0.0) return -1;
         }
         if (e->type == ORC_SBEND && (e->angle == 0.0 || e->eta == 0.0)) return -1;
+        if (e->type == ORC_RBEND && (e->angle == 0.0 || e->eta == 0.0 || !(e->L > 0.0) ||
+                                     fabs(0.5 * e->angle + e->e1) >= 1.5 || fabs(-0.5 * e->angle + e->e1) >= 1.5))
+            return -1;
         if (e->fringe != 0 && e->fringe != 1) return -1;
         if (e->fringe && (e->type == ORC_DRIFT || e->type == ORC_SNAKE)) return -1;
         if (e->split_order != 0 && e->split_order != 2 && e->split_order != 4) return -1;
@@ -626,6 +802,10 @@ int orc_orbit_map(const orc_element* e, double G, double Ggamma0, real* z6) {
         rc = drift(&r, &o, e->L);
     } else if (e->type == ORC_SNAKE) {
         rc = 0;
+    } else if (e->type == ORC_RBEND) {   /* the whole element: rotations, fringes, body, offsets */
+        if (e->n_slices < 1) return -1;
+        real S[3] = {0.0, 0.0, 1.0};
+        rc = track_rbend(&r, e, &o, S, 0, NULL, NULL);
     } else {
         if (e->n_slices < 1) return -1;
         double ds = e->L / e->n_slices;
@@ -638,7 +818,9 @@ int orc_orbit_map(const orc_element* e, double G, double Ggamma0, real* z6) {
 /* Individual sub-flows, for the tests that pin them one by one:
  * which = 0 drift, 1 multipole kick, 2 quadrupole linear flow H_qL,
  *         3 quadrupole nonlinear flow H_qNL, 4 sector bend, 5 solenoid body
- *         (k1 = b0/(B rho)). */
+ *         (k1 = b0/(B rho)), 6 rectangular-bend body (k1 = b1/(B rho)),
+ *         7 dynamic rotation by the angle s, 8 rectangular-bend fringe orbit map
+ *         (k1 = b1/(B rho), sign of k2 = entrance/exit). */
 int orc_subflow(int which, double G, double Ggamma0, real* z6, double s, double k1, double k2,
                 double h, double eta) {
     orc_ref r = make_ref(G, Ggamma0);
@@ -651,6 +833,9 @@ int orc_subflow(int which, double G, double Ggamma0, real* z6, double s, double 
     case 3: rc = quad_nonlinear(&r, &o, s); break;
     case 4: rc = sbend_map(&r, &o, h, eta, s); break;
     case 5: rc = solenoid_map(&r, &o, k1, s); break;
+    case 6: rc = rbend_body(&r, &o, k1, s); break;                 /* k1 = b1/(B rho) */
+    case 7: rc = rbend_rotation(&r, &o, s); break;                 /* s = phi */
+    case 8: rc = rbend_fringe_orbit(&r, &o, k1, k2 > 0.0 ? 1 : -1); break;   /* k1 = b1/(B rho), k2 = sign */
     default: return -1;
     }
     z6[0] = o.X; z6[1] = o.Px; z6[2] = o.Y; z6[3] = o.Py; z6[4] = o.T; z6[5] = o.Pt;
@@ -678,6 +863,12 @@ int orc_element_fringe(const orc_element* e, int sign, double G, double Ggamma0,
     orc_ref r = make_ref(G, Ggamma0);
     orc_orbit o = {z6[0], z6[1], z6[2], z6[3], z6[4], z6[5]};
     if (e->type == ORC_SOLENOID) return solenoid_fringe(&r, e->k1, sign, &o, out3);
+    if (e->type == ORC_RBEND) {   /* in the magnet's Cartesian frame */
+        double pi_, po_, b;
+        rbend_geometry(e, &pi_, &po_, &b);
+        rbend_fringe_spin(&r, b, sign, &o, out3);
+        return 0;
+    }
     if (e->type != ORC_MULT && e->type != ORC_QUAD_MK && e->type != ORC_SBEND) return -1;
     multipole_fringe(&r, e, sign, &o, out3);
     return 0;

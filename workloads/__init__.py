@@ -25,6 +25,11 @@ b/(B rho), Sec. 2.1 and Sec. 3):
                sbend (Sec. 4.5, Eq. (skfringe)); 0: hard edges without kicks
     split_order  orbit slice map of a mult or quad_mk: 2 = the symmetric split
                of Eq. (27), 4 = its fourth-order Yoshida composition (Sec. 3.3)
+    e1         rbend: the beam meets the entrance face at angle/2 + e1 and the
+               exit face at -angle/2 + e1 (0: symmetric rectangular bend)
+    (rbend: "rbend", Sec. 3.2: L is the magnet length along its Cartesian
+    axis, angle the total bend, eta the field factor; its thin-fringe orbit
+    map is always applied, its Eq. (skfringeRB) spin kicks when fringe = 1)
     (solenoid: "solenoid" with k1 = b0/(B rho), MAD's ks, Sec. 3.7; its
     thin-pancake fringe kicks, Sec. 4.4, are always part of the element)
 
@@ -45,20 +50,20 @@ import numpy as np
 
 G_PROTON = 1.7928
 
-ELEMENT_TYPES = ("drift", "mult", "quad_mk", "sbend", "snake", "solenoid")
-SPIN_TYPES = ("mult", "quad_mk", "sbend", "solenoid")
+ELEMENT_TYPES = ("drift", "mult", "quad_mk", "sbend", "snake", "solenoid", "rbend")
+SPIN_TYPES = ("mult", "quad_mk", "sbend", "solenoid", "rbend")
 
 
 def element(type: str, L: float = 0.0, n_slices: int = 1, k1: float = 0.0,
             k2: float = 0.0, angle: float = 0.0, eta: float = 1.0,
             snake_phi: float = 0.0, snake_mu: float = 0.0, name: str = "",
-            fringe: int = 0, split_order: int = 2) -> Dict:
+            fringe: int = 0, split_order: int = 2, e1: float = 0.0) -> Dict:
     if type not in ELEMENT_TYPES:
         raise ValueError(f"unknown element type {type!r}")
     return dict(type=type, L=float(L), n_slices=int(n_slices), k1=float(k1),
                 k2=float(k2), angle=float(angle), eta=float(eta),
                 snake_phi=float(snake_phi), snake_mu=float(snake_mu),
-                name=name or type, fringe=int(fringe), split_order=int(split_order))
+                name=name or type, fringe=int(fringe), split_order=int(split_order), e1=float(e1))
 
 
 def slices_for_order(base: int, spin_order: int) -> int:
