@@ -63,6 +63,17 @@ extern "C" {
                            only: a mixed-precision context or batch over a lattice
                            with solenoids is rejected (ST_EINVAL).                     */
 
+#define ST_RBEND    6   /* rectangular bend, Sec. 3.2: L = magnet length along its
+                           Cartesian axis, angle = total bend, eta = field factor, e1 =
+                           face asymmetry (the beam meets the entrance face at
+                           angle/2 + e1 and the exit face at -angle/2 + e1).  Dynamic
+                           rotations into and out of the magnet frame (Eq. (prot); the
+                           spin components turn with the frame), thin-fringe orbit maps
+                           (Eq. (dipolefringe), symplectic form) at both faces, the
+                           exact body map (Eq. (rbend)) in n_slices slices, the offsets
+                           of Eqs. (Xoffset), (Toffset); fringe = 1 adds the spin kicks
+                           of Eq. (skfringeRB).  FP64 only.                           */
+
 /* ---- precision of a tracking context ---------------------------------- */
 #define ST_FP64   0   /* all arithmetic in IEEE double                                 */
 #define ST_MIXED  1   /* FP32 slice arithmetic with compensated coordinates, FP64
@@ -74,7 +85,8 @@ typedef struct st_ctx st_ctx;           /* opaque; particle state on the device 
 /* One beamline element.  Units: metres, radians; k1 = b2/(B rho) [m^-2],
  * k2 = B''/(B rho) [m^-3] (MAD convention).  n_slices is the number of
  * integration slices of a spin-carrying element (ST_MULT, ST_QUAD_MK,
- * ST_SBEND) and must be a multiple of 2^spin_order at st_track time. */
+ * ST_SBEND, ST_SOLENOID, ST_RBEND) and must be a multiple of 2^spin_order at
+ * st_track time. */
 typedef struct {
     int32_t type;
     int32_t n_slices;
@@ -86,7 +98,8 @@ typedef struct {
     double snake_phi;
     double snake_mu;
     int32_t fringe;    /* 1: thin fringe spin kicks at both ends of an ST_MULT, ST_QUAD_MK
-                        * or ST_SBEND (Sec. 4.5, Eq. (skfringe)): a rotation about the
+                        * or ST_SBEND (Sec. 4.5, Eq. (skfringe)), or of an ST_RBEND
+                        * (Eq. (skfringeRB), see ST_RBEND); for the others: a rotation about the
                         * longitudinal axis by -(+-)(1 + G) sum_m (b_m/(B rho)) Im (X + iY)^m / m,
                         * + at the entrance, - at the exit, with b_1/(B rho) = eta h,
                         * b_2/(B rho) = k1, b_3/(B rho) = k2/2; orbit unchanged.  0: none.
@@ -100,6 +113,7 @@ typedef struct {
                           * x0 = 1 - 2 x1 (Sec. 3.3's higher-order versions).  Spin is
                           * still sampled at the slice edges.  Other types: 0 or 2
                           * (ST_EINVAL otherwise).  FP64 contexts only when 4. */
+    double e1;           /* ST_RBEND only: face asymmetry (see ST_RBEND); ignored otherwise */
 } st_element;
 
 /* Reference particle: anomaly G and naive spin tune G*gamma0 of the scale

@@ -20,11 +20,11 @@ from . import _build
 LIB_PATH = _build.LIB
 
 ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ESTATE = 0, -1, -2, -3, -4, -5
-ST_DRIFT, ST_MULT, ST_QUAD_MK, ST_SBEND, ST_SNAKE, ST_SOLENOID = 0, 1, 2, 3, 4, 5
+ST_DRIFT, ST_MULT, ST_QUAD_MK, ST_SBEND, ST_SNAKE, ST_SOLENOID, ST_RBEND = 0, 1, 2, 3, 4, 5, 6
 ST_FP64, ST_MIXED = 0, 1
 
 TYPE_CODES = {"drift": ST_DRIFT, "mult": ST_MULT, "quad_mk": ST_QUAD_MK, "sbend": ST_SBEND, "snake": ST_SNAKE,
-              "solenoid": ST_SOLENOID}
+              "solenoid": ST_SOLENOID, "rbend": ST_RBEND}
 PRECISIONS = {"fp64": ST_FP64, "mixed": ST_MIXED}
 
 
@@ -32,7 +32,7 @@ class StElement(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int32), ("n_slices", ctypes.c_int32), ("L", ctypes.c_double),
                 ("k1", ctypes.c_double), ("k2", ctypes.c_double), ("angle", ctypes.c_double),
                 ("eta", ctypes.c_double), ("snake_phi", ctypes.c_double), ("snake_mu", ctypes.c_double),
-                ("fringe", ctypes.c_int32), ("split_order", ctypes.c_int32)]
+                ("fringe", ctypes.c_int32), ("split_order", ctypes.c_int32), ("e1", ctypes.c_double)]
 
 
 class StReference(ctypes.Structure):
@@ -130,7 +130,7 @@ def elements_array(elements: List[Dict]):
     for i, e in enumerate(elements):
         arr[i] = StElement(TYPE_CODES[e["type"]], int(e["n_slices"]), e["L"], e["k1"], e["k2"], e["angle"],
                            e["eta"], e["snake_phi"], e["snake_mu"], int(e.get("fringe", 0)),
-                           int(e.get("split_order", 2)))
+                           int(e.get("split_order", 2)), float(e.get("e1", 0.0)))
     return arr
 
 

@@ -82,8 +82,8 @@ __device__ __forceinline__ void batch_loop(const JobDesc* __restrict__ jobs, con
     }
 }
 
-template <int K, int MINB, bool ORDER4>
-__global__ void __launch_bounds__(128, MINB) track_batch_fp64_kernel(const JobDesc* __restrict__ jobs,
+template <int K, int MINB, bool EXT>
+__global__ void __launch_bounds__(128, EXT ? (MINB > 2 ? MINB - 1 : MINB) : MINB) track_batch_fp64_kernel(const JobDesc* __restrict__ jobs,
                                                                       const WorkItem* __restrict__ items,
                                                                       int n_items, int32_t* queue, int n_turns,
                                                                       int32_t* status) {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(128, MINB) track_batch_fp64_kernel(const JobDe
     __shared__ uint64_t bar;
     __shared__ double qcache[(2 * QC_N + 2) * 128];
     batch_loop(jobs, items, n_items, queue, status, smem, &bar, [&](const JobDesc& J, int64_t i) {
-        fp64_track_particle<K, true, ORDER4>((const DevElem*)smem, (const uint16_t*)(smem + J.seq_offset), J.n_seq, J.ref, J.xpx,
+        fp64_track_particle<K, true, EXT>((const DevElem*)smem, (const uint16_t*)(smem + J.seq_offset), J.n_seq, J.ref, J.xpx,
                                J.ypy, J.tpt, J.sxy, J.sz, J.lost, i, n_turns, qcache);
     });
 }
@@ -113,12 +113,12 @@ __global__ void __launch_bounds__(128, MINB) track_batch_mixed_kernel(const JobD
 typedef void (*BatchKernel)(const JobDesc*, const WorkItem*, int, int32_t*, int, int32_t*);
 
 // variant 0 / 1 = larger / smaller register budget (fewer / more resident blocks)
-// order4: the FP64 instantiation with the fourth-order slice maps compiled in
-static BatchKernel batch_kernel(int precision, int K, int variant, bool order4) {
+// ext: the FP64 instantiation with the extended element set compiled in
+static BatchKernel batch_kernel(int precision, int K, int variant, bool ext) {
 #define ST_SEL(KK)                                                                                            \
     case KK:                                                                                                  \
         if (precision == ST_FP64) {                                                                           \
-            if (order4)                                                                                       \
+            if (ext)                                                                                       \
                 return variant ? track_batch_fp64_kernel<KK, 3, true> : track_batch_fp64_kernel<KK, 2, true>; \
             return variant ? track_batch_fp64_kernel<KK, 3, false> : track_batch_fp64_kernel<KK, 2, false>;   \
         }                                                                                                     \
@@ -143,7 +143,7 @@ struct st_batch {
     int32_t precision = ST_FP64;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    bool has_order4 = false;   // some job's lattice uses fourth-order slice maps
+    bool has_ext = false;   // some job's lattice uses fourth-order maps or rectangular bends
     std::vector<const st_lattice*> lats;
     std::vector<int64_t> n, offset;
     std::vector<double> cost_per_particle;
@@ -262,7 +262,7 @@ static int build_jobs(st_batch* b) {
 
 // Kernel and grid for the current launch shape (no stream work; safe before a capture).
 static int prepare_launch(st_batch* b, int K, BatchKernel* kern_out, int* grid_out) {
-    BatchKernel kern = batch_kernel(b->precision, K, b->variant, b->has_order4);
+    BatchKernel kern = batch_kernel(b->precision, K, b->variant, b->has_ext);
     cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "batch: cudaFuncSetAttribute");
     int dev = 0, sms = 0, per_sm = 0;
@@ -337,7 +337,7 @@ int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particle
             return ST_EINVAL;
         }
         b->lats.push_back(lattices[j]);
-        if (lattices[j]->impl.has_order4) b->has_order4 = true;
+        if (lattices[j]->impl.has_ext) b->has_ext = true;
         b->n.push_back(n_particles[j]);
         b->offset.push_back(total);
         total += n_particles[j];

@@ -26,7 +26,9 @@ int cuda_fail(cudaError_t e, const char* what) {
     return ST_ECUDA;
 }
 
-bool is_spin_type(int t) { return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND || t == ST_SOLENOID; }
+bool is_spin_type(int t) {
+    return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND || t == ST_SOLENOID || t == ST_RBEND;
+}
 
 // Precompute the per-element constants the kernels use (all in FP64).
 DevElem pack_element(const st_element& e) {
@@ -74,6 +76,21 @@ DevElem pack_element(const st_element& e) {
         d.a[5] = 1.0 / e.eta;
         break;
     }
+    case ST_RBEND: {
+        // Sec. 3.2: faces met at phi_in and phi_out, design field from
+        // Px = sin(phi_in) -> sin(phi_out) over L (Eq. (rhob)), offsets of
+        // Eqs. (Xoffset), (Toffset) (the latter as the arc length; the
+        // kernel divides by beta0)
+        d.ds = e.L / e.n_slices;
+        const double phi_in = 0.5 * e.angle + e.e1, phi_out = -0.5 * e.angle + e.e1;
+        const double sd = std::sin(phi_in) - std::sin(phi_out);
+        d.a[0] = e.eta * sd / e.L;
+        d.a[1] = phi_in;
+        d.a[2] = -phi_out;
+        d.a[3] = -e.L * (std::cos(phi_in) - std::cos(phi_out)) / sd;
+        d.a[4] = e.L * (phi_in - phi_out) / sd;
+        break;
+    }
     case ST_SOLENOID:
         d.ds = e.L / e.n_slices;
         d.a[0] = e.k1;           // b0/(B rho)
@@ -119,7 +136,7 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
     }
     for (int i = 0; i < n; ++i) {
         const st_element& e = elems[i];
-        if (e.type < ST_DRIFT || e.type > ST_SOLENOID) {
+        if (e.type < ST_DRIFT || e.type > ST_RBEND) {
             set_error("element %d: unknown type %d", i, e.type);
             return ST_EINVAL;
         }
@@ -142,6 +159,12 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
         }
         if (e.type == ST_DRIFT && !(e.L >= 0.0)) {
             set_error("element %d: drift needs L >= 0", i);
+            return ST_EINVAL;
+        }
+        if (e.type == ST_RBEND &&
+            (e.angle == 0.0 || e.eta == 0.0 || !std::isfinite(e.e1) || !(std::fabs(0.5 * e.angle + e.e1) < 1.5) ||
+             !(std::fabs(-0.5 * e.angle + e.e1) < 1.5))) {
+            set_error("element %d: rectangular bend needs angle != 0, eta != 0 and face angles below 1.5 rad", i);
             return ST_EINVAL;
         }
         if (e.type == ST_SBEND && (e.angle == 0.0 || e.eta == 0.0 || !std::isfinite(e.angle / e.L))) {
@@ -176,7 +199,8 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
         }
         seq[i] = (uint16_t)idx;
         if (d.type == ST_SOLENOID || d.flags) L.fp64_only = true;
-        if (d.flags & ST_ELEM_ORDER4) L.has_order4 = true;
+        if ((d.flags & ST_ELEM_ORDER4) || d.type == ST_RBEND) L.has_ext = true;
+        if (d.type == ST_RBEND) L.fp64_only = true;
         if (is_spin_type(d.type)) {
             max_slices = std::max(max_slices, (int)d.n_slices);
             int p = 0;

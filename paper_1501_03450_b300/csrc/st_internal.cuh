@@ -33,6 +33,8 @@ static_assert(sizeof(DevElem) == 64, "DevElem must be 64 bytes");
 //   ST_SBEND   : a0 = h, a1 = eta, a2 = cos(h ds), a3 = sin(h ds),
 //                a4 = 1/(eta h), a5 = 1/eta
 //   ST_SNAKE   : a0..a3 = unit quaternion (scalar first)
+//   ST_RBEND   : a0 = b1/(B rho), a1 = phi_entr, a2 = -phi_exit, a3 = X offset,
+//                a4 = arc length of the reference orbit
 
 // Reference-particle constants passed by value to the kernels.
 struct RefConst {
@@ -108,7 +110,7 @@ struct LatticeImpl {
     int32_t max_slices;
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
     bool fp64_only = false;        // solenoids, fringe spin kicks or fourth-order maps: FP64 only
-    bool has_order4 = false;       // some element uses the fourth-order slice map
+    bool has_ext = false;          // fourth-order slice maps or rectangular bends present
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]
     void* d_blob = nullptr;
     size_t blob_bytes = 0;

@@ -7,8 +7,10 @@
 
 namespace st {
 
-template <int K, bool SPIN = true, bool ORDER4 = false>
-__global__ void __launch_bounds__(128, 3) track_fp64_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
+// The extended instantiation runs 2 blocks of 128 per SM (up to 255 registers,
+// no spills); the FP64 pipe is already saturated from 4 resident warps per SM.
+template <int K, bool SPIN = true, bool EXT = false>
+__global__ void __launch_bounds__(128, EXT ? 2 : 3) track_fp64_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
                                                          uint32_t seq_offset, int n_seq, RefConst ref,
                                                          double2* __restrict__ xpx, double2* __restrict__ ypy,
                                                          double2* __restrict__ tpt, double2* __restrict__ sxy,
@@ -34,7 +36,7 @@ __global__ void __launch_bounds__(128, 3) track_fp64_kernel(const void* __restri
     const int64_t i = wi * 32 + lane;
     if (i >= n || lost[i]) continue;
 
-    fp64_track_particle<K, SPIN, ORDER4>(table, seq, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns, qcache,
+    fp64_track_particle<K, SPIN, EXT>(table, seq, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns, qcache,
                                          tq);
     }  // particle loop
 }
@@ -84,14 +86,14 @@ int launch_unpack(st_ctx* ctx, double* z, double* s) {
     return e == cudaSuccess ? ST_OK : cuda_fail(e, "unpack kernel launch");
 }
 
-template <int K, bool SPIN, bool ORDER4>
+template <int K, bool SPIN, bool EXT>
 static int launch_k_(st_ctx* ctx, int n_turns, const TurnOut& tq) {
     const LatticeImpl& L = ctx->lat->impl;
     const int threads = ctx->block_threads;
     const size_t smem = L.blob_bytes;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(track_fp64_kernel<K, SPIN, ORDER4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(track_fp64_kernel<K, SPIN, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fp64 tracker)");
         attr_set = true;
@@ -100,7 +102,7 @@ static int launch_k_(st_ctx* ctx, int n_turns, const TurnOut& tq) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_fp64_kernel<K, SPIN, ORDER4>, threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_fp64_kernel<K, SPIN, EXT>, threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "fp64 tracker occupancy query");
     if (per_sm < 1) {
         set_error("fp64 tracker: block of %d threads with %zu B shared memory does not fit on an SM", threads,
@@ -114,7 +116,7 @@ static int launch_k_(st_ctx* ctx, int n_turns, const TurnOut& tq) {
     const int tpl = ctx->turns_per_launch;
     for (int t = 0; t < n_turns; t += tpl) {
         int nt = n_turns - t < tpl ? n_turns - t : tpl;
-        track_fp64_kernel<K, SPIN, ORDER4><<<(unsigned)grid, threads, smem, ctx->stream>>>(
+        track_fp64_kernel<K, SPIN, EXT><<<(unsigned)grid, threads, smem, ctx->stream>>>(
             L.d_blob, (uint32_t)L.blob_bytes, (uint32_t)L.seq_offset, L.n_elements, L.ref, ctx->xpx, ctx->ypy,
             ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status, tq);
         e = cudaGetLastError();
@@ -126,7 +128,7 @@ static int launch_k_(st_ctx* ctx, int n_turns, const TurnOut& tq) {
 // The fourth-order instantiation only for lattices with fourth-order elements.
 template <int K, bool SPIN = true>
 static int launch_k(st_ctx* ctx, int n_turns, const TurnOut& tq) {
-    return ctx->lat->impl.has_order4 ? launch_k_<K, SPIN, true>(ctx, n_turns, tq)
+    return ctx->lat->impl.has_ext ? launch_k_<K, SPIN, true>(ctx, n_turns, tq)
                                      : launch_k_<K, SPIN, false>(ctx, n_turns, tq);
 }
 

@@ -151,6 +151,77 @@ __device__ __forceinline__ void mult_kick(Particle& p, double k1, double k2, dou
     p.Py += s * bx;
 }
 
+// ---- rectangular bend (Sec. 3.2), in the magnet's Cartesian frame ----------
+// Each returns false if the particle is lost (no real longitudinal momentum,
+// or a trajectory parallel to the rotated face).
+
+// Dynamic rotation by phi: the flow of H_prot = -X Ps (Eqs. (Hprot), (prot));
+// T from Hamilton's equation dT/dphi = -X (1/beta0 + Pt)/Ps.
+__device__ __forceinline__ bool rbend_rotation(Particle& p, const PConst& pc, double phi) {
+    const double ps2 = pc.P2 - p.Px * p.Px - p.Py * p.Py;
+    if (!(ps2 > 0.0)) return false;
+    const double iPs = rsqrt(ps2), Ps = ps2 * iPs;
+    double sn, cs;
+    sincos(phi, &sn, &cs);
+    const double t = sn / cs;
+    const double den = 1.0 - p.Px * iPs * t;
+    if (!(den > 0.0)) return false;
+    const double d = p.X * t / den;           // longitudinal distance to the rotated face
+    p.Y += p.Py * iPs * d;
+    p.T -= pc.b0pt * iPs * d;
+    p.X = p.X / (cs * den);
+    p.Px = p.Px * cs + Ps * sn;
+    return true;
+}
+
+// Thin fringe orbit map, Eq. (dipolefringe), as the canonical transformation
+// generated by -(sb/2) x'/(1 + y'^2) Y_f^2 (sb = +-b1/(B rho); x', y', Ps of
+// the incoming momenta): Y_f solves Y = Y_f + (sb/2) x'y'/(Ps (1 + y'^2)) Y_f^2.
+__device__ __forceinline__ bool rbend_fringe_orbit(Particle& p, const PConst& pc, double sb) {
+    const double ps2 = pc.P2 - p.Px * p.Px - p.Py * p.Py;
+    if (!(ps2 > 0.0)) return false;
+    const double iPs = rsqrt(ps2);
+    const double xp = p.Px * iPs, yp = p.Py * iPs;
+    const double ig = 1.0 / (1.0 + yp * yp);
+    const double arg = 1.0 + 2.0 * sb * xp * yp * ig * iPs * p.Y;
+    if (!(arg > 0.0)) return false;
+    const double Yf = 2.0 * p.Y / (1.0 + sqrt(arg));
+    const double Yf2 = Yf * Yf;
+    p.X += 0.5 * sb * iPs * ((1.0 + xp * xp) * ig - 2.0 * (xp * yp) * (xp * yp) * ig * ig) * Yf2;
+    p.Py -= sb * xp * ig * Yf;
+    p.T -= 0.5 * sb * pc.b0pt * xp * iPs * iPs * (1.0 - yp * yp) * ig * ig * Yf2;
+    p.Y = Yf;
+    return true;
+}
+
+// Body over s in the uniform field b (Eq. (rbend)); X written without the
+// cancelling difference of square roots.
+__device__ __forceinline__ bool rbend_body(Particle& p, const PConst& pc, double b, double s) {
+    const double Pa2 = pc.P2 - p.Py * p.Py;
+    const double Pxf = p.Px - s * b;
+    const double qi = Pa2 - p.Px * p.Px, qf = Pa2 - Pxf * Pxf;
+    if (!(qi > 0.0) || !(qf > 0.0)) return false;
+    const double iPa = rsqrt(Pa2);
+    const double dpsi = asin(p.Px * iPa) - asin(Pxf * iPa);
+    p.X += s * (p.Px + Pxf) / (sqrt(qf) + sqrt(qi));
+    p.Y += p.Py * dpsi / b;
+    p.T -= pc.b0pt * dpsi / b;
+    p.Px = Pxf;
+    return true;
+}
+
+// Spin kick of a rectangular-bend fringe, Eq. (skfringeRB) with its factor Y:
+// w = sb [G (gamma - 1) Px Y x^ - (1 + G) Y s^].
+__device__ __forceinline__ Quat rbend_fringe_quat(const PConst& pc, double onepG, const Particle& p, double sb) {
+    return quat_from_rotvec(sb * pc.c * p.Px * p.Y, 0.0, -sb * onepG * p.Y);
+}
+
+__device__ __forceinline__ Quat quat_about_y(double phi) {
+    double sn, cs;
+    sincos(0.5 * phi, &sn, &cs);
+    return Quat{cs, 0.0, sn, 0.0};
+}
+
 // Precession vector Omega (Eq. (6b)) for a transverse field b = (bx, by, 0),
 // frame curvature h; ips = 1/Ps, Ps = longitudinal momentum.
 __device__ __forceinline__ void precession(const Particle& p, const PConst& pc, double bx, double by, double h,
@@ -253,10 +324,10 @@ struct TurnOut {
     double ref[4];
 };
 
-// ORDER4: compile the fourth-order slice maps in (a separate instantiation,
-// chosen only for lattices that use them, so that the second-order loop keeps
-// its register budget).
-template <int K, bool SPIN = true, bool ORDER4 = false>
+// EXT: compile the extended element set in (fourth-order slice maps and
+// rectangular bends; a separate instantiation, chosen only for lattices that
+// use them, so that the common tracking loop keeps its register budget).
+template <int K, bool SPIN = true, bool EXT = false>
 __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ table, const uint16_t* __restrict__ seq,
                                                     int n_seq, const RefConst& ref, double2* __restrict__ xpx,
                                                     double2* __restrict__ ypy, double2* __restrict__ tpt,
@@ -323,8 +394,9 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
             const int N = el.n_slices;
             const double ds = el.ds;
             double ox, oy, os;
-            Quat q_in{1.0, 0.0, 0.0, 0.0};   // entrance fringe kick
-            const bool fringe = el.flags & ST_ELEM_FRINGE;
+            Quat q_in{1.0, 0.0, 0.0, 0.0};   // entrance fringe kick (rbend: with the entrance rotation)
+            Quat q_x{1.0, 0.0, 0.0, 0.0};    // rbend: exit fringe kick and rotation
+            const bool fringe = (el.flags & ST_ELEM_FRINGE) && type != ST_RBEND;
             if constexpr (SPIN) {
                 if (fringe) q_in = multipole_fringe_quat(el, type, 1.0 + ref.G, p, 1.0);
             }
@@ -472,7 +544,48 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                         lv.add_edge(s, N, ds, ox, oy, os);
                     }
                 }
-            } else if constexpr (ORDER4) {
+            } else if constexpr (EXT) {
+              if (type == ST_RBEND) {
+                // Sec. 3.2: entrance rotation into the magnet's Cartesian frame
+                // (the spin components turn with the frame), entrance fringe,
+                // body, exit fringe, offset of Eq. (Xoffset), exit rotation,
+                // time of Eq. (Toffset); a loss anywhere poisons X, so that the
+                // check after the Romberg step restores the entrance state
+                const double b = el.a[0];
+                bool ok = rbend_rotation(p, pc, el.a[1]);
+                if constexpr (SPIN) {
+                    q_in = quat_about_y(el.a[1]);
+                    if (el.flags & ST_ELEM_FRINGE) q_in = qmul(rbend_fringe_quat(pc, 1.0 + ref.G, p, b), q_in);
+                }
+                ok = ok && rbend_fringe_orbit(p, pc, b);
+                double pp = p.Px * p.Px + p.Py * p.Py;
+                double ips = rsqrt(pc.P2 - pp);
+                double Ps = (pc.P2 - pp) * ips;
+                if constexpr (SPIN) {
+                    precession(p, pc, 0.0, b, 0.0, ips, Ps, ox, oy, os);
+                    lv.add_edge(0, N, ds, ox, oy, os);
+                }
+                for (int s = 1; s <= N; ++s) {
+                    ok = ok && rbend_body(p, pc, b, ds);
+                    pp = p.Px * p.Px + p.Py * p.Py;
+                    ips = rsqrt(pc.P2 - pp);
+                    Ps = (pc.P2 - pp) * ips;
+                    if constexpr (SPIN) {
+                        precession(p, pc, 0.0, b, 0.0, ips, Ps, ox, oy, os);
+                        lv.add_edge(s, N, ds, ox, oy, os);
+                    }
+                }
+                if constexpr (SPIN) {
+                    q_x = (el.flags & ST_ELEM_FRINGE) ? rbend_fringe_quat(pc, 1.0 + ref.G, p, -b)
+                                                      : Quat{1.0, 0.0, 0.0, 0.0};
+                }
+                ok = ok && rbend_fringe_orbit(p, pc, -b);
+                p.X -= el.a[3];
+                ok = ok && rbend_rotation(p, pc, el.a[2]);
+                if constexpr (SPIN) q_x = qmul(quat_about_y(el.a[2]), q_x);
+                p.T += el.a[4] * ref.inv_beta0;
+                if (!ok) p.X = __longlong_as_double(0x7ff8000000000000LL);   // quiet NaN
+              } else {
                 // fourth-order multipole (DKD) or matrix-kick quadrupole:
                 // Yoshida's product S2(x1 ds) S2(x0 ds) S2(x1 ds) of the
                 // symmetric maps with adjacent half steps merged,
@@ -529,6 +642,7 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                         lv.add_edge(s, N, ds, ox, oy, os);
                     }
                 }
+              }
             }
             Quat qe{1.0, 0.0, 0.0, 0.0};
             if constexpr (SPIN) qe = lv.romberg();
@@ -551,7 +665,12 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     const Quat q_out = multipole_fringe_quat(el, type, 1.0 + ref.G, p, -1.0);
                     qt = qmul(q_out, qmul(qe, qmul(q_in, qt)));
                 } else {
-                    qt = qmul(qe, qt);
+                    if constexpr (EXT) {
+                        if (type == ST_RBEND) qt = qmul(q_x, qmul(qe, qmul(q_in, qt)));
+                        else qt = qmul(qe, qt);
+                    } else {
+                        qt = qmul(qe, qt);
+                    }
                 }
             }
         }

@@ -153,6 +153,25 @@ def solenoid_ring(Ggamma0: float = 45.5, ks: float = 0.05, n_cells: int = 8,
     return ring
 
 
+def rbend_ring(Ggamma0: float = 45.5, n_cells: int = 8, e1: float = 0.0, fringe: int = 0,
+               bend_slices: int = 4) -> Dict:
+    """The toy ring of toy_ring() with every 3 m sector bend replaced by a
+    rectangular bend of the same angle and the same reference arc (magnet
+    length = chord 2 rho sin(angle/2), rho = 3 m / angle), Sec. 3.2."""
+    ring = toy_ring(Ggamma0, n_cells=n_cells)
+    els = []
+    for e in ring["elements"]:
+        if e["type"] == "sbend":
+            ang = e["angle"]
+            rho = e["L"] / ang
+            e = element("rbend", L=2.0 * rho * math.sin(0.5 * ang), n_slices=bend_slices, angle=ang, e1=e1,
+                        fringe=fringe, name=e["name"].replace("B", "RB"))
+        els.append(e)
+    ring["elements"] = els
+    ring["name"] = "toy_ring_rbends"
+    return ring
+
+
 def rhic_like_ring(Ggamma0: float = 45.5, n_cells: int = 108, k1: float = 0.03,
                    k2: float = 0.5, base_slices: int = 4, sext_slices: int = 2,
                    snakes: bool = True, quad_type: str = "quad_mk") -> Dict:
