@@ -39,15 +39,27 @@ import workloads as W  # noqa: E402
 WORKLOAD = "rhic_like_1e5"
 L2_BYTES = 126 * 1024 * 1024
 
+# Algorithmic work per particle-element pass of this workload at Romberg order
+# 2: the floating-point additions, multiplications and divisions the method
+# performs on particle data as the oracle states it, tallied by the oracle's
+# operation-counting build (oracle.op_counts on 8 particles x 1 turn; the counts
+# do not depend on the particle), special functions listed apart and not
+# charged.  tests/test_oracle_opcount.py recomputes these numbers.
+ALGO_FLOPS_PER_PASS = {2: 671.4716}
+ALGO_SPECIAL_PER_PASS = {2: {"sqrt": 20.4016, "sin_cos": 19.4029, "asin": 2.2827, "sinh_cosh": 7.9894}}
+ALGO_FLOPS_PER_TYPE = {2: {"snake": 56.0, "quad_mk": 1645.0, "mult": 1053.0, "drift": 20.0, "sbend": 974.0}}
 # FP64 floating-point operations the FP64 tracker executes per particle-element
-# pass on this workload (2 per DFMA, 1 per DADD/DMUL), from the thread-level
-# instruction counters of one ncu capture (profiles/track_fp64_rhic_like_ncu.md).
-# None until measured for the current kernel.
+# pass on this workload (2 per DFMA, 1 per DADD/DMUL), and FP64-pipe
+# instructions per pass, from the thread-level instruction counters of one ncu
+# capture (profiles/track_fp64_rhic_like_ncu.md).  None until measured for the
+# current kernel.
 FP64_FLOPS_PER_PASS = 501.5
+FP64_PIPE_INSTR_PER_PASS = 341.8
+FP64_PIPE_LANES_PER_SM_CLOCK = 2
 # DRAM bytes (read + write) per particle per launch of the FP64 tracker, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the same capture (2e4
-# particles: 1.585 MB + 0 B), scaled linearly with the particle count.
-FP64_DRAM_BYTES_PER_PARTICLE = 79.2
+# particles: 1.593 MB + 0 B), scaled linearly with the particle count.
+FP64_DRAM_BYTES_PER_PARTICLE = 79.6
 
 
 def parse_args():
@@ -248,13 +260,18 @@ def variant_mixed(st, torch, args, fp64_value, fp32_peak):
     value = n * n_el * steps / t
     tr.close()
     lat.close()
-    achieved = MIXED_FP32_FLOPS_PER_PASS * n * n_el / (t / steps) / 1e12 if MIXED_FP32_FLOPS_PER_PASS else None
+    algo = ALGO_FLOPS_PER_PASS.get(args.spin_order)
+    achieved = algo * n * n_el / (t / steps) / 1e12 if algo else None
+    ex = MIXED_FP32_FLOPS_PER_PASS * n * n_el / (t / steps) / 1e12 if MIXED_FP32_FLOPS_PER_PASS else None
     out = {"metric": "particle-element passes/s", "value": value, "unit": "passes/s",
            "speedup_vs_fp64": value / fp64_value, "dtype": "f32 (compensated) + f64 per turn",
            "config": {"workload": f"108-cell RHIC-like ring, {n} Gaussian protons, Ggamma={args.ggamma}, "
                       f"Romberg order {args.spin_order}, 1 turn per step", "steps": steps},
            "roofline": {"bound": "alu", "pipe": "fp32", "achieved": achieved, "peak": fp32_peak / 1e12,
-                        "unit": "TFLOP/s", "frac": achieved / (fp32_peak / 1e12) if achieved else None},
+                        "unit": "TFLOP/s", "frac": achieved / (fp32_peak / 1e12) if achieved else None,
+                        "algorithmic_flops_per_pass": algo,
+                        "executed": {"fp32_flops_per_pass": MIXED_FP32_FLOPS_PER_PASS, "tflops": ex,
+                                     "frac_of_peak": ex / (fp32_peak / 1e12) if ex else None}},
            "error_vs_fp64": {}}
     # accuracy: 1024-particle subset, mixed vs the FP64 tracker (pinned to the oracle)
     for gg in sorted({args.ggamma, 45.5, 487.0}):
@@ -382,6 +399,47 @@ def variant_surrogate(st, torch, args, fp64_value, throughput_turns=30):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def element_type_breakdown(st, torch, ring, npart, seed, K, ggamma, min_elements=200):
+    """Pass rate of the FP64 tracker per element type: for each type in the
+    ring, a ring made of that type's elements only (in ring order, repeated
+    to at least min_elements) is tracked for one turn on the same ensemble
+    size; its share of the full ring's time is count / rate normalised."""
+    z, S = W.gaussian_particles(npart, ggamma, seed=seed)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    out = {}
+    for t in dict.fromkeys(e["type"] for e in ring["elements"]):
+        els = [e for e in ring["elements"] if e["type"] == t]
+        reps = -(-min_elements // len(els))
+        sub = dict(ring, elements=els * reps, name=f"{t}_only")
+        lat = st.Lattice(sub)
+        tr = st.Tracker(lat, npart, "fp64", stream=stream.cuda_stream)
+        tr.set_launch(block_threads=128, turns_per_launch=1)
+        tr.upload(z, S)
+        tr.track(1, K)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+        with torch.cuda.stream(stream):
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                tr.track(1, K)
+                b.record(stream)
+        torch.cuda.synchronize()
+        t_s = sum(a.elapsed_time(b) for a, b in ev) * 1e-3 / len(ev)
+        tr.close()
+        lat.close()
+        rate = npart * len(sub["elements"]) / t_s
+        algo = ALGO_FLOPS_PER_TYPE.get(K, {}).get(t)
+        out[t] = {"passes_per_s": rate, "count_in_ring": len(els), "slices": sorted({e["n_slices"] for e in els}),
+                  "algorithmic_flops_per_pass": algo, "algorithmic_tflops": algo * rate / 1e12 if algo else None}
+    total = sum(v["count_in_ring"] / v["passes_per_s"] for v in out.values())
+    for v in out.values():
+        v["time_share"] = v["count_in_ring"] / v["passes_per_s"] / total
+    return {"workload": f"one element type per ring, {npart} particles, order {K}, 1 turn",
+            "types": out, "predicted_ring_passes_per_s": len(ring["elements"]) / total}
+
+
 def main():
     args = parse_args()
     if args.profile_train:
@@ -476,15 +534,33 @@ def main():
     # ---- roofline of the tracking kernel ---------------------------------
     peak = fp64_peak if args.precision == "fp64" else fp32_peak
     avg_launch_s = t_sum / (args.steps * launches_per_step)
-    if args.precision == "fp64" and FP64_FLOPS_PER_PASS:
-        achieved = FP64_FLOPS_PER_PASS * npart * n_el / avg_launch_s / 1e12
-    else:
-        achieved = None
+    passes_per_launch = npart * n_el
+    algo = ALGO_FLOPS_PER_PASS.get(K)
+    achieved = algo * passes_per_launch / avg_launch_s / 1e12 if algo else None
+    executed = None
+    if args.precision == "fp64" and K == 2 and FP64_FLOPS_PER_PASS:
+        ex_tflops = FP64_FLOPS_PER_PASS * passes_per_launch / avg_launch_s / 1e12
+        issue = FP64_PIPE_INSTR_PER_PASS * passes_per_launch / avg_launch_s
+        sm_hz = (clocks.get("sm_mhz") or 2032.0) * 1e6
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        executed = {"fp64_flops_per_pass": FP64_FLOPS_PER_PASS, "tflops": ex_tflops,
+                    "frac_of_peak": ex_tflops / (peak / 1e12),
+                    "fp64_pipe_instr_per_pass": FP64_PIPE_INSTR_PER_PASS,
+                    "pipe_issue_frac": issue / (FP64_PIPE_LANES_PER_SM_CLOCK * n_sm * sm_hz)}
     roofline = {"bound": "alu", "pipe": "fp64" if args.precision == "fp64" else "fp32",
                 "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": (achieved / (peak / 1e12)) if achieved else None,
                 "traffic": FP64_DRAM_BYTES_PER_PARTICLE * npart if args.precision == "fp64" else None,
-                "peak_source": "measured by st_measure_peaks (independent FMA chains) at run time"}
+                "peak_source": "measured by st_measure_peaks (independent FMA chains) at run time",
+                "algorithmic_flops_per_pass": algo,
+                "algorithmic_basis": "additions, multiplications and divisions on particle data counted by the "
+                                     "oracle's operation-counting build for this ring and order; special functions "
+                                     "per pass not charged: " + json.dumps(ALGO_SPECIAL_PER_PASS.get(K)),
+                "executed": executed}
+
+    breakdown = None
+    if not args.no_variants and world == 1 and args.precision == "fp64":
+        breakdown = element_type_breakdown(st, torch, ring, npart, w["seed"], K, args.ggamma)
 
     variants = None
     if not args.no_variants and world == 1:
@@ -512,6 +588,7 @@ def main():
         "gpu_launches": args.steps * launches_per_step,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "per_element_type": breakdown,
         "variants": variants,
         "clocks": clocks,
         "wall_s_timed": wall,

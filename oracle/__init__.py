@@ -12,6 +12,10 @@ header for the section/equation map).  The same source is compiled three ways:
                              oracle's own rounding noise
     c128  double complex  -- complex-step derivatives (exact Jacobians)
 
+`opcount.cpp` compiles the same source once more with a scalar that tallies
+every floating-point operation on particle data (the method's algorithmic
+work per pass, used for the roofline's numerator).
+
 `mlp.py` holds the FP64 NumPy reference of the learned one-turn spin map.
 """
 from __future__ import annotations
@@ -47,6 +51,10 @@ class OrcElement(ctypes.Structure):
                 ("fringe", ctypes.c_int32), ("split_order", ctypes.c_int32), ("e1", ctypes.c_double)]
 
 
+_OPC_LIB = os.path.join(_BUILD, "liboracle_opcount.so")
+OP_NAMES = ("add", "mul", "div", "sqrt", "sincos", "tan", "asin", "sinh_cosh")
+
+
 def _lib_path(variant: str) -> str:
     return os.path.join(_BUILD, f"liboracle_{variant}.so")
 
@@ -61,6 +69,13 @@ def build(force: bool = False) -> None:
             continue
         cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                "-fPIC", "-shared", f"-DORACLE_REAL={ctype}", _SRC, "-o", out + ".tmp", "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(out + ".tmp", out)
+    out = _OPC_LIB
+    cpp = os.path.join(_HERE, "opcount.cpp")
+    if force or not os.path.exists(out) or os.path.getmtime(out) < max(os.path.getmtime(_SRC), os.path.getmtime(cpp)):
+        cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-I", _HERE, cpp, "-o", out + ".tmp", "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(out + ".tmp", out)
 
@@ -188,6 +203,36 @@ def element_fringe(el, sign, G, Ggamma0, z6, variant="f64"):
     out = np.zeros(3, dtype=dt)
     rc = _lib(variant).orc_element_fringe(elements_array([el]), int(sign), G, Ggamma0, _ptr(z6), _ptr(out))
     return out, rc
+
+
+_opc = None
+
+
+def op_counts(ring, z, S, n_turns, spin_order):
+    """Track (single thread) with the operation-counting build and return
+    (counts, z, S, lost): counts maps OP_NAMES to the number of operations on
+    particle data (additions include subtractions; sincos counts each sin and
+    each cos)."""
+    global _opc
+    with _lock:
+        if _opc is None:
+            build()
+            lib = ctypes.CDLL(_OPC_LIB)
+            vp = ctypes.c_void_p
+            lib.opc_track.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_long,
+                                      vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+            lib.opc_track.restype = ctypes.c_int
+            _opc = lib
+    z = np.ascontiguousarray(np.array(z, dtype=np.float64))
+    S = np.ascontiguousarray(np.array(S, dtype=np.float64))
+    n = z.shape[1]
+    lost = np.zeros(n, np.uint8)
+    out = np.zeros(len(OP_NAMES), np.uint64)
+    rc = _opc.opc_track(elements_array(ring["elements"]), len(ring["elements"]), ring["G"], ring["Ggamma0"], n,
+                        _ptr(z), _ptr(S), _ptr(lost), int(n_turns), int(spin_order), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle: invalid lattice for this spin order")
+    return {k: int(v) for k, v in zip(OP_NAMES, out)}, z, S, lost
 
 
 def check_lattice(ring, spin_order) -> bool:

@@ -57,8 +57,10 @@
  * step derivatives for exact Jacobians in the symplecticity tests).
  * <tgmath.h> makes sqrt/sin/... dispatch on the argument type.
  */
+#ifndef ORACLE_OPCOUNT
 #include <tgmath.h>
 #include <complex.h>
+#endif
 #include <stdint.h>
 #include <string.h>
 #include <stdlib.h>
@@ -645,7 +647,7 @@ static int track_rbend(const orc_ref* r, const orc_element* e, orc_orbit* z, rea
     if (rbend_fringe_orbit(r, z, b, +1)) return 1;
     int N = e->n_slices;
     double ds = e->L / N;
-    real (*Om)[3] = malloc(sizeof(real[3]) * (size_t)(N + 1));
+    real (*Om)[3] = (real (*)[3])malloc(sizeof(real[3]) * (size_t)(N + 1));
     if (!Om) return 2;
     int lost = omega(r, e, z, Om[0]);
     for (int i = 1; i <= N && !lost; ++i) {
@@ -694,7 +696,7 @@ static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, r
     double ds = e->L / N;
     /* entrance fringe kick (orbit unchanged across the fringe) */
     if (element_fringe(r, e, +1, z, S)) return 1;
-    real (*Om)[3] = malloc(sizeof(real[3]) * (size_t)(N + 1));
+    real (*Om)[3] = (real (*)[3])malloc(sizeof(real[3]) * (size_t)(N + 1));
     if (!Om) return 2;
     int lost = omega(r, e, z, Om[0]);
     for (int i = 1; i <= N && !lost; ++i) {
