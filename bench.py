@@ -39,14 +39,16 @@ import workloads as W  # noqa: E402
 WORKLOAD = "rhic_like_1e5"
 L2_BYTES = 126 * 1024 * 1024
 
-# Algorithmic work per particle-element pass of this workload at Romberg order
-# 2: the floating-point additions, multiplications and divisions the method
+# Algorithmic work per particle-element pass of this workload (both G gamma0;
+# slices max(4, 2^K) at Romberg order K): the floating-point additions, multiplications and divisions the method
 # performs on particle data as the oracle states it, tallied by the oracle's
 # operation-counting build (oracle.op_counts on 8 particles x 1 turn; the counts
 # do not depend on the particle), special functions listed apart and not
 # charged.  tests/test_oracle_opcount.py recomputes these numbers.
-ALGO_FLOPS_PER_PASS = {2: 671.4716}
-ALGO_SPECIAL_PER_PASS = {2: {"sqrt": 20.4016, "sin_cos": 19.4029, "asin": 2.2827, "sinh_cosh": 7.9894}}
+ALGO_FLOPS_PER_PASS = {2: 671.4716, 3: 1239.8626, 4: 2338.9802}
+ALGO_SPECIAL_PER_PASS = {2: {"sqrt": 20.4016, "sin_cos": 19.4029, "asin": 2.2827, "sinh_cosh": 7.9894},
+                         3: {"sqrt": 38.0925, "sin_cos": 37.6645, "asin": 4.5654, "sinh_cosh": 15.9789},
+                         4: {"sqrt": 72.9036, "sin_cos": 73.0462, "asin": 9.1308, "sinh_cosh": 31.9577}}
 ALGO_FLOPS_PER_TYPE = {2: {"snake": 56.0, "quad_mk": 1645.0, "mult": 1053.0, "drift": 20.0, "sbend": 974.0}}
 # FP64 floating-point operations the FP64 tracker executes per particle-element
 # pass on this workload (2 per DFMA, 1 per DADD/DMUL), and FP64-pipe
@@ -168,11 +170,12 @@ class ClockSampler:
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_rate(ring, z, S, spin_order, seconds_target=10.0):
-    """Time the FP64 oracle on a bounded sample of the workload; returns
-    (passes/s, sample description, threads)."""
+def oracle_rate(ring, z, S, spin_order, seconds_target=10.0, threads=None):
+    """Time the FP64 oracle on a bounded sample of the workload on `threads`
+    host threads (all cores by default); returns (passes/s, sample
+    description, threads, particles)."""
     import oracle
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     n_el = len(ring["elements"])
     probe_n = min(z.shape[1], 4 * threads)
     t0 = time.perf_counter()
@@ -399,6 +402,43 @@ def variant_surrogate(st, torch, args, fp64_value, throughput_turns=30):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def variant_fp64_configs(st, torch, npart, fp64_peak, seed):
+    """FP64 pass rate on the RHIC-like ring at G gamma0 = 45.5 and 487 and
+    Romberg orders 2, 3, 4 (slices max(4, 2^K)), one turn per launch, with the
+    algorithmic roofline fraction of each."""
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    out = {}
+    for gg in (45.5, 487.0):
+        z, S = W.gaussian_particles(npart, gg, seed=seed)
+        for K in (2, 3, 4):
+            ring = W.workload(WORKLOAD, spin_order=K, Ggamma0=gg)["ring"]
+            n_el = len(ring["elements"])
+            lat = st.Lattice(ring)
+            tr = st.Tracker(lat, npart, "fp64", stream=stream.cuda_stream)
+            tr.set_launch(block_threads=128, turns_per_launch=1)
+            tr.upload(z, S)
+            tr.track(1, K)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+            with torch.cuda.stream(stream):
+                for a, b in ev:
+                    flush.zero_()
+                    a.record(stream)
+                    tr.track(1, K)
+                    b.record(stream)
+            torch.cuda.synchronize()
+            t_s = sum(a.elapsed_time(b) for a, b in ev) * 1e-3 / len(ev)
+            tr.close()
+            lat.close()
+            rate = npart * n_el / t_s
+            algo = ALGO_FLOPS_PER_PASS.get(K)
+            out[f"Ggamma={gg},K={K}"] = {"passes_per_s": rate, "ms_per_turn": 1e3 * t_s,
+                                         "algorithmic_flops_per_pass": algo,
+                                         "roofline_frac": algo * rate / fp64_peak if algo else None}
+    return {"workload": f"108-cell RHIC-like ring, {npart} particles, 1 turn per launch", "configs": out}
+
+
 def element_type_breakdown(st, torch, ring, npart, seed, K, ggamma, min_elements=200):
     """Pass rate of the FP64 tracker per element type: for each type in the
     ring, a ring made of that type's elements only (in ring order, repeated
@@ -564,14 +604,17 @@ def main():
 
     variants = None
     if not args.no_variants and world == 1:
-        variants = {"mixed": variant_mixed(st, torch, args, value, fp32_peak),
+        variants = {"fp64_configs": variant_fp64_configs(st, torch, npart, fp64_peak, w["seed"]),
+                    "mixed": variant_mixed(st, torch, args, value, fp32_peak),
                     "batched": variant_batched(st, torch, args),
                     "surrogate": variant_surrogate(st, torch, args, value)}
 
     cpu = None
     if not args.no_cpu_baseline:
         rate, sample, threads, _ = oracle_rate(ring, z, S, K)
-        cpu = {"value": rate, "unit": "passes/s", "cores": threads, "kind": "oracle", "sample": sample}
+        rate1, sample1, _, _ = oracle_rate(ring, z, S, K, seconds_target=3.0, threads=1)
+        cpu = {"value": rate, "unit": "passes/s", "cores": threads, "kind": "oracle", "sample": sample,
+               "value_1_core": rate1, "sample_1_core": sample1}
 
     out = {
         "metric": "particle-element passes/s", "value": value, "unit": "passes/s", "n_gpus": world,

@@ -61,6 +61,10 @@ def test_bench_algorithmic_figures_are_current():
     sp = b.ALGO_SPECIAL_PER_PASS[2]
     assert abs(c["sqrt"] / passes - sp["sqrt"]) < 1e-3 and abs(c["sincos"] / passes - sp["sin_cos"]) < 1e-3
     assert abs(c["asin"] / passes - sp["asin"]) < 1e-3 and abs(c["sinh_cosh"] / passes - sp["sinh_cosh"]) < 1e-3
+    for K in (3, 4):
+        rk = W.workload("rhic_like_1e5", spin_order=K)["ring"]
+        ck, _, _, _ = oracle.op_counts(rk, z, S, 1, K)
+        assert abs((ck["add"] + ck["mul"] + ck["div"]) / (8 * len(rk["elements"])) - b.ALGO_FLOPS_PER_PASS[K]) < 1e-3
     for t, v in b.ALGO_FLOPS_PER_TYPE[2].items():
         els = [e for e in ring["elements"] if e["type"] == t]
         ct, _, _, _ = oracle.op_counts(dict(ring, elements=els), z, S, 1, 2)
