@@ -507,11 +507,10 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 };
                 FF oyf;
                 const float2* rh = rho + el.rho_off;
-                if constexpr (SPIN) {
-                    dev_omega(z.X, px, Ps, ips, ox, oyf, os);
-                    lv.add_bend(0, N, el, 1.0f, 0.0f, ox, oyf, os);
-                }
-                for (int s = 1; s <= N; ++s) {
+                // one loop over the slice edges (edge 0: no orbit step), so that the
+                // spin edge code exists once
+                for (int s = 0; s <= N; ++s) {
+                  if (s > 0) {
                     // exact bend over ds, Eq. (10): (Px, A = Ps - eta(1+hX)) rotates by h ds;
                     // dX = (dPs - dA)/(eta h) with dA = A (cos - 1) - Px sin
                     // A = (Ps - 1) + (1 - eta) - eta h X, compensated (first order in the
@@ -557,89 +556,71 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     ips = rsqrtf(ps2);
                     Ps = ps2 * ips;
                     PsM1 = ff_add_f(k.PM1, -(px * px + py * py) / (Ps + k.P));
+                  }
                     if constexpr (SPIN) {
                         dev_omega(z.X, px, Ps, ips, ox, oyf, os);
                         const float2 r = rh[s];
                         lv.add_bend(s, N, el, r.x, r.y, ox, oyf, os);
                     }
                 }
-            } else if (type == ST_MULT) {
-                const float k1 = el.k1, k2 = el.k2;
+            } else {   // ST_MULT (drift-kick-drift) or ST_QUAD_MK (matrix-kick)
+                // one loop over the slice edges for both straight element kinds (edge
+                // 0: no orbit step), so that the spin edge code exists once
+                const bool is_mult = type == ST_MULT;
+                const float k1 = el.k1;
+                const float k2 = is_mult ? el.k2 : 0.0f;   // quadrupoles keep |k1| in el.k2
+                const FF dsff{el.ds_ff.x, el.ds_ff.y};
                 const FF half{0.5f * el.ds_ff.x, 0.5f * el.ds_ff.y};
-                const FF k1ds{el.k1ds_ff.x, el.k1ds_ff.y};
+                const FF k1ds{el.k1ds_ff.x, el.k1ds_ff.y};   // quadrupoles: |k1|
                 const FF k2h{el.k2h_ff.x, el.k2h_ff.y};
                 const FF k2ds{el.k2ds_ff.x, el.k2ds_ff.y};
+                FF Aw;   // (a/P) k1 ds, compensated: the first-order rotation per unit Y (x) and X (y)
+                if (is_mult) {
+                    Aw = ff_mul(k.aP, k1ds);
+                } else {
+                    const float absk = el.k2, hs = 0.5f * ds;
+                    if (mq.key_k != absk || mq.key_s != hs)
+                        mquad_coeffs(mq, invP64, (double)el.k1ds_ff.x + (double)el.k1ds_ff.y,
+                                     0.5 * ((double)el.ds_ff.x + (double)el.ds_ff.y), absk, hs);
+                    Aw = ff_mul_f(ff_mul(ff_mul(k.aP, k1ds), dsff), k1 >= 0.0f ? 1.0f : -1.0f);
+                }
                 FF ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                 float ips = ips_ff.hi, Ps = (k.P2 - pp) * ips;
-                const FF Aw = ff_mul(k.aP, k1ds);   // (a/P) k1 ds
-                if constexpr (SPIN) {
-                    FF bx, by;
-                    float bz;
-                    straight_edge(k, z, k1, k2, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
-                    lv.add_straight(0, bx, by, bz);
-                }
-                for (int s = 1; s <= N; ++s) {
-                    drift_inc(z, k, half, ips_ff, d);
-                    {
-                        // kick of H_m over ds, compensated (the sextupole kick is first order
-                        // in the betatron offset around a dispersive orbit)
-                        const FF x2my2 = ff_add(ff_mul(z.X, z.X), ff_neg(ff_mul(z.Y, z.Y)));
-                        const FF kx = ff_add(ff_mul(z.X, k1ds), ff_mul(x2my2, k2h));
-                        const FF ky = ff_add(ff_mul(z.Y, k1ds), ff_mul(ff_mul(z.X, z.Y), k2ds));
-                        z.Px = ff_add(z.Px, ff_neg(kx));
-                        z.Py = ff_add(z.Py, ky);
+                for (int s = 0; s <= N; ++s) {
+                    if (s > 0) {
+                        if (is_mult) {
+                            drift_inc(z, k, half, ips_ff, d);
+                            // kick of H_m over ds, compensated (the sextupole kick is first
+                            // order in the betatron offset around a dispersive orbit)
+                            const FF x2my2 = ff_add(ff_mul(z.X, z.X), ff_neg(ff_mul(z.Y, z.Y)));
+                            const FF kx = ff_add(ff_mul(z.X, k1ds), ff_mul(x2my2, k2h));
+                            const FF ky = ff_add(ff_mul(z.Y, k1ds), ff_mul(ff_mul(z.X, z.Y), k2ds));
+                            z.Px = ff_add(z.Px, ff_neg(kx));
+                            z.Py = ff_add(z.Py, ky);
+                            ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
+                            ips = ips_ff.hi;
+                            Ps = (k.P2 - pp) * ips;
+                            drift_inc(z, k, half, ips_ff, d);
+                        } else {
+                            quad_linear_inc(z, k, mq, k1);
+                            inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
+                            // H_qNL over ds, Eq. (25), in increment form:
+                            // dX = ds Px (1/Ps - 1/P); dT = ds [tau - (1/beta0+Pt)(d - p^2/(2P^3))]
+                            z.X = ff_add_f(z.X, ds * z.Px.hi * d);
+                            z.Y = ff_add_f(z.Y, ds * z.Py.hi * d);
+                            z.T = ff_add(z.T, ff_mul(dsff, ff_add_f(k.tau, -k.b0pt * (d - 0.5f * pp * k.invPf * k.invPf * k.invPf))));
+                            quad_linear_inc(z, k, mq, k1);
+                            ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
+                            ips = ips_ff.hi;
+                            Ps = (k.P2 - pp) * ips;
+                        }
                     }
-                    ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-                    ips = ips_ff.hi;
-                    Ps = (k.P2 - pp) * ips;
-                    drift_inc(z, k, half, ips_ff, d);
                     if constexpr (SPIN) {
+                        const bool end = s == 0 || s == N;   // trapezoid end weights
                         FF bx, by;
                         float bz;
-                        if (s == N)
-                            straight_edge(k, z, k1, k2, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
-                        else
-                            straight_edge(k, z, k1, k2, Aw, ds, d, ips, Ps, bx, by, bz);
-                        lv.add_straight(s, bx, by, bz);
-                    }
-                }
-            } else {   // ST_QUAD_MK
-                const float k1 = el.k1, absk = el.k2;
-                const float half = 0.5f * ds;
-                if (mq.key_k != absk || mq.key_s != half)
-                    mquad_coeffs(mq, invP64, (double)el.k1ds_ff.x + (double)el.k1ds_ff.y,
-                                 0.5 * ((double)el.ds_ff.x + (double)el.ds_ff.y), absk, half);
-                FF ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-                float ips = ips_ff.hi, Ps = (k.P2 - pp) * ips;
-                const FF dsff{el.ds_ff.x, el.ds_ff.y};
-                // (a/P) k1 ds, compensated: the first-order rotation per unit Y (x) and X (y)
-                const FF Aw = ff_mul_f(ff_mul(ff_mul(k.aP, FF{el.k1ds_ff.x, el.k1ds_ff.y}), dsff),
-                                       k1 >= 0.0f ? 1.0f : -1.0f);
-                if constexpr (SPIN) {
-                    FF bx, by;
-                    float bz;
-                    straight_edge(k, z, k1, 0.0f, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
-                    lv.add_straight(0, bx, by, bz);
-                }
-                for (int s = 1; s <= N; ++s) {
-                    quad_linear_inc(z, k, mq, k1);
-                    inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-                    // H_qNL over ds, Eq. (25), in increment form:
-                    // dX = ds Px (1/Ps - 1/P); dT = ds [tau - (1/beta0+Pt)(d - p^2/(2P^3))]
-                    z.X = ff_add_f(z.X, ds * z.Px.hi * d);
-                    z.Y = ff_add_f(z.Y, ds * z.Py.hi * d);
-                    z.T = ff_add(z.T, ff_mul(dsff, ff_add_f(k.tau, -k.b0pt * (d - 0.5f * pp * k.invPf * k.invPf * k.invPf))));
-                    quad_linear_inc(z, k, mq, k1);
-                    ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-                    ips = ips_ff.hi;
-                    Ps = (k.P2 - pp) * ips;
-                    if constexpr (SPIN) {
-                        FF bx, by;
-                        float bz;
-                        if (s == N)
-                            straight_edge(k, z, k1, 0.0f, ff_scale2(Aw, 0.5f), 0.5f * ds, d, ips, Ps, bx, by, bz);
-                        else
-                            straight_edge(k, z, k1, 0.0f, Aw, ds, d, ips, Ps, bx, by, bz);
+                        straight_edge(k, z, k1, k2, end ? ff_scale2(Aw, 0.5f) : Aw, end ? 0.5f * ds : ds, d, ips, Ps,
+                                      bx, by, bz);
                         lv.add_straight(s, bx, by, bz);
                     }
                 }
