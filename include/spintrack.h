@@ -182,6 +182,16 @@ int st_track_one_turn_map(st_ctx* ctx, int32_t spin_order, const double* q_ref, 
  * Asynchronous. */
 int st_track_average(st_ctx* ctx, int32_t n_turns, int32_t spin_order, double* spin_sum);
 
+/* Restore lost flags ([n] bytes, nonzero = lost; host or device memory as
+ * st_particles_upload) after st_particles_upload, which clears them.  With
+ * st_spins_download this checkpoints and resumes a run: the state between
+ * launches is the FP64 orbit, the spins and the lost flags, so tracking
+ * n1 turns, downloading, uploading into a new context and tracking n2 more
+ * gives bit for bit the result of n1 + n2 turns in one context (FP64; the
+ * mixed tracker too when the checkpoint falls on a launch boundary).
+ * Errors: ST_EINVAL (NULL), ST_ESTATE (no particles uploaded), ST_ECUDA. */
+int st_lost_upload(st_ctx* ctx, const uint8_t* lost, int32_t src_is_device);
+
 /* Copy the tracked state out: spin_soa [3][n] (required), z_soa [6][n] and
  * lost [n] (each may be NULL), to host (dst_is_device = 0) or device memory.
  * Synchronises the context stream.  Returns ST_ETIMEOUT if a kernel reported
@@ -238,6 +248,15 @@ int st_batch_autotune(st_batch* batch, int32_t spin_order, int32_t trial_turns, 
  * timed by CUDA events (about 0.2 s).  These are the denominators of the
  * trackers' arithmetic roofline.  Errors: ST_EINVAL (NULL), ST_ECUDA. */
 int st_measure_peaks(double* fp64_flops, double* fp32_flops);
+
+/* Failure-path self-test of the device-side bounded waits: one block waits,
+ * with the library's bounded mbarrier wait, on a barrier that nothing ever
+ * completes (no copy is issued, so nothing is left in flight).  The wait
+ * gives up after limit_s seconds (1e-4 .. 2) and the call returns
+ * ST_ETIMEOUT with the measured wait in *elapsed_s; the context stays usable.
+ * Returns ST_OK only if the wait did not give up (which would be a bug).
+ * Errors: ST_EINVAL, ST_ECUDA. */
+int st_selftest_bounded_wait(double limit_s, double* elapsed_s);
 
 /* Allocation-free FP64 tracking.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory (code running

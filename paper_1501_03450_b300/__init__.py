@@ -54,6 +54,8 @@ SIGNATURES = {
     "st_ctx_create": ([_VP, ctypes.c_int64, ctypes.c_int32, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "st_ctx_destroy": ([_VP], ctypes.c_int),
     "st_particles_upload": ([_VP, _VP, _VP, ctypes.c_int32], ctypes.c_int),
+    "st_lost_upload": ([_VP, _VP, ctypes.c_int32], ctypes.c_int),
+    "st_selftest_bounded_wait": ([ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "st_track": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "st_spins_download": ([_VP, _VP, _VP, _VP, ctypes.c_int32], ctypes.c_int),
     "st_track_orbit": ([_VP, ctypes.c_int32], ctypes.c_int),
@@ -161,6 +163,17 @@ def st_ctx_destroy(ctx: int) -> None:
 
 def st_particles_upload(ctx: int, z_ptr: int, s_ptr: int, src_is_device: int) -> None:
     _check(load().st_particles_upload(ctx, z_ptr, s_ptr, int(src_is_device)))
+
+
+def st_lost_upload(ctx: int, lost_ptr: int, src_is_device: int) -> None:
+    _check(load().st_lost_upload(ctx, lost_ptr, src_is_device))
+
+
+def st_selftest_bounded_wait(limit_s: float):
+    """Run the bounded-wait self-test; returns (rc, elapsed seconds)."""
+    el = ctypes.c_double(0.0)
+    rc = load().st_selftest_bounded_wait(float(limit_s), ctypes.byref(el))
+    return rc, el.value
 
 
 def st_track(ctx: int, n_turns: int, spin_order: int) -> None:
@@ -476,6 +489,13 @@ class Tracker:
         lost = np.empty(self.n, np.uint8)
         st_spins_download(self.handle, S.ctypes.data, z.ctypes.data, lost.ctypes.data, 0)
         return z, S, lost
+
+    def upload_lost(self, lost: np.ndarray):
+        """Restore lost flags after upload() (which clears them): with
+        download() this checkpoints and resumes a run bit for bit."""
+        lost = np.ascontiguousarray(lost, dtype=np.uint8)
+        assert lost.shape == (self.n,)
+        st_lost_upload(self.handle, lost.ctypes.data, 0)
 
     def download_device(self, s_ptr: int, z_ptr: Optional[int] = None, lost_ptr: Optional[int] = None):
         st_spins_download(self.handle, s_ptr, z_ptr, lost_ptr, 1)

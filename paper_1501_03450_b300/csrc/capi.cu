@@ -405,6 +405,23 @@ int st_particles_upload(st_ctx* ctx, const double* z_soa, const double* spin_soa
     return ST_OK;
 }
 
+int st_lost_upload(st_ctx* ctx, const uint8_t* lost, int32_t src_is_device) {
+    if (!ctx || !lost) {
+        set_error("st_lost_upload: null pointer");
+        return ST_EINVAL;
+    }
+    if (!ctx->uploaded) {
+        set_error("st_lost_upload: upload the particles first");
+        return ST_ESTATE;
+    }
+    const size_t n = (size_t)ctx->n;
+    cudaError_t e = cudaMemcpyAsync(ctx->lost, lost, n, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess && !src_is_device) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "st_lost_upload");
+    return ST_OK;
+}
+
 int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order) {
     if (!ctx) {
         set_error("st_track: null context");

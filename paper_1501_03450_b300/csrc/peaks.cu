@@ -2,6 +2,7 @@
 // rates of the current device, measured with independent FMA chains and CUDA
 // events.  The tracker's roofline denominators come from here.
 #include "st_internal.cuh"
+#include "device_common.cuh"
 
 namespace st {
 
@@ -69,5 +70,56 @@ extern "C" int st_measure_peaks(double* fp64_flops, double* fp32_flops) {
     if (rc) return rc;
     *fp64_flops = 2.0 * r64;
     *fp32_flops = 2.0 * r32;
+    return ST_OK;
+}
+
+// ---- bounded-wait self-test ------------------------------------------------
+namespace st {
+
+// One block: thread 0 initialises an mbarrier that expects one arrival which
+// nothing ever makes (no copy is issued), every thread then runs the
+// library's bounded wait on it; the wait gives up after limit_ns, and thread
+// 0 records the outcome and the elapsed time.
+__global__ void bounded_wait_selftest_kernel(uint64_t limit_ns, int32_t* status, unsigned long long* elapsed_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const uint64_t t0 = global_timer_ns();
+    const bool ok = mbar_wait_bounded(&bar, limit_ns);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *status = ok ? STATUS_OK : STATUS_TMA_TIMEOUT;
+        *elapsed_ns = global_timer_ns() - t0;
+    }
+}
+
+}  // namespace st
+
+extern "C" int st_selftest_bounded_wait(double limit_s, double* elapsed_s) {
+    if (!elapsed_s || !(limit_s >= 1e-4) || !(limit_s <= 2.0)) {
+        st::set_error("st_selftest_bounded_wait: need elapsed_s and 1e-4 <= limit_s <= 2");
+        return ST_EINVAL;
+    }
+    void* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 16);
+    if (e != cudaSuccess) return st::cuda_fail(e, "st_selftest_bounded_wait: allocation");
+    int32_t* d_status = (int32_t*)buf;
+    unsigned long long* d_elapsed = (unsigned long long*)((char*)buf + 8);
+    st::bounded_wait_selftest_kernel<<<1, 32>>>((uint64_t)(limit_s * 1e9), d_status, d_elapsed);
+    e = cudaGetLastError();
+    int32_t h_status = -1;
+    unsigned long long h_elapsed = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h_status, d_status, sizeof(h_status), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&h_elapsed, d_elapsed, sizeof(h_elapsed), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return st::cuda_fail(e, "st_selftest_bounded_wait");
+    *elapsed_s = (double)h_elapsed * 1e-9;
+    if (h_status != st::STATUS_OK) {
+        st::set_error("st_selftest_bounded_wait: the wait gave up after %.3g s (status %d)", *elapsed_s, h_status);
+        return ST_ETIMEOUT;
+    }
     return ST_OK;
 }

@@ -73,6 +73,40 @@ def slices_for_order(base: int, spin_order: int) -> int:
     return max(m, ((base + m - 1) // m) * m)
 
 
+RING_FORMAT = "spintrack-ring-1"
+_ELEMENT_KEYS = ("type", "L", "n_slices", "k1", "k2", "angle", "eta", "snake_phi", "snake_mu", "name", "fringe",
+                 "split_order", "e1")
+
+
+def save_ring(ring: Dict, path: str) -> None:
+    """Write a ring as JSON: {"format", "name", "G", "Ggamma0", "elements": [...]}
+    with every element field written out (the lattice description file)."""
+    import json
+    out = {"format": RING_FORMAT, "name": ring.get("name", ""), "G": float(ring["G"]),
+           "Ggamma0": float(ring["Ggamma0"]),
+           "elements": [{k: element(**{kk: e[kk] for kk in _ELEMENT_KEYS if kk in e})[k] for k in _ELEMENT_KEYS}
+                        for e in ring["elements"]]}
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+
+
+def load_ring(path: str) -> Dict:
+    """Read a ring written by save_ring (or by hand).  Unknown element types or
+    fields raise ValueError; omitted fields take element()'s defaults."""
+    import json
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("format") != RING_FORMAT:
+        raise ValueError(f"{path}: not a {RING_FORMAT} file")
+    els = []
+    for i, e in enumerate(d["elements"]):
+        extra = set(e) - set(_ELEMENT_KEYS)
+        if extra:
+            raise ValueError(f"{path}: element {i}: unknown fields {sorted(extra)}")
+        els.append(element(**e))
+    return dict(name=d.get("name", ""), G=float(d["G"]), Ggamma0=float(d["Ggamma0"]), elements=els)
+
+
 def with_spin_order(ring: Dict, spin_order: int) -> Dict:
     """Copy of `ring` whose spin-carrying elements have slice counts valid for
     Romberg order `spin_order`."""
