@@ -192,16 +192,32 @@ __device__ __forceinline__ void half_angle_series(double u, double& c, double& f
     HalfAngleHorner<DEG - 1>::step(u, c, f);
 }
 
+// High words of the series thresholds 4e-6, 4e-4 and 0.04: for a non-negative
+// double the high 32 bits, read as a signed integer, order it like its value,
+// so the thresholds are tested on the integer pipe (the FP64 pipe is the
+// tracker's bottleneck).  Each comparison is conservative by < 1e-6 relative.
+constexpr int HIWORD_4EM6 = 0x3ed0c6f7;
+constexpr int HIWORD_4EM4 = 0x3f3a36e2;
+constexpr int HIWORD_0P04 = 0x3fa47ae1;
+
 // Unit quaternion of the rotation by |w| about w^ without library calls:
 // q = (cos(t/2), sin(t/2)/t * w) with t^2 = w.w, both even functions of t
-// evaluated as truncated Taylor series in u = t^2 (degree 5 for u <= 0.04,
-// degree 11 for u <= 4; truncation below 1e-20 relative).  Larger angles are
-// halved until u <= 4 and the quaternion squared back.
+// evaluated as truncated Taylor series in u = t^2: degree 2 for u < 4e-6,
+// 3 for u < 4e-4, 5 for u < 0.04, 11 for u <= 4 (truncation below 3e-21
+// relative in every range).  Larger angles are halved until u <= 4 and the
+// quaternion squared back.  The degree is the largest one any active lane of
+// the warp needs, so that the branch stays uniform (a lane never gets less
+// than its own u requires).
 __device__ __forceinline__ Quat quat_from_rotvec(double wx, double wy, double wz) {
     double u = wx * wx + wy * wy + wz * wz;
     double c, f;
-    if (u <= 0.04) {
-        half_angle_series<5>(u, c, f);
+    const int hu = __double2hiint(u);   // NaN orders above every threshold
+    int need = hu < HIWORD_4EM6 ? 2 : hu < HIWORD_4EM4 ? 3 : hu < HIWORD_0P04 ? 5 : 11;
+    need = __reduce_max_sync(__activemask(), need);
+    if (need <= 5) {
+        if (need == 2) half_angle_series<2>(u, c, f);
+        else if (need == 3) half_angle_series<3>(u, c, f);
+        else half_angle_series<5>(u, c, f);
         return Quat{c, f * wx, f * wy, f * wz};
     }
     int m = 0;

@@ -122,7 +122,8 @@ __device__ __forceinline__ void quad_linear(Particle& p, const PConst& pc, const
 // library reciprocal square root.
 __device__ __forceinline__ double inv_sqrt_diff(double a2, double ia, double ia2, double p2) {
     const double e = p2 * ia2;
-    if (e < 1e-6) return ia * fma(e, fma(e, 0.375, 0.5), 1.0);
+    // e >= 0: test e < 1e-6 (high word 0x3eb0c6f7) on the integer pipe
+    if (__double2hiint(e) < 0x3eb0c6f7) return ia * fma(e, fma(e, 0.375, 0.5), 1.0);
     return rsqrt(a2 - p2);
 }
 
