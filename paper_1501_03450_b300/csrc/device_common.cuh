@@ -128,14 +128,11 @@ __device__ __forceinline__ Quat qmul(const Quat& a, const Quat& b) {
     return o;
 }
 
+// Square of a unit quaternion: (w^2 - |v|^2, 2 w v) with w^2 - |v|^2 = 2 w^2 - 1
+// for |q| = 1 (one fused operation instead of four products).
 __device__ __forceinline__ Quat qsquare(const Quat& a) {
-    Quat o;
-    double w2 = a.w + a.w;
-    o.w = a.w * a.w - a.x * a.x - a.y * a.y - a.z * a.z;
-    o.x = w2 * a.x;
-    o.y = w2 * a.y;
-    o.z = w2 * a.z;
-    return o;
+    const double w2 = a.w + a.w;
+    return Quat{fma(w2, a.w, -1.0), w2 * a.x, w2 * a.y, w2 * a.z};
 }
 
 __device__ __forceinline__ Quat qnormalize(const Quat& a) {

@@ -127,6 +127,18 @@ __device__ __forceinline__ double inv_sqrt_diff(double a2, double ia, double ia2
     return rsqrt(a2 - p2);
 }
 
+// Exponent field of a double's high word (0x7ff00000 for infinities and NaNs):
+// finiteness tests on the integer pipe instead of FP64 sums and compares.
+__device__ __forceinline__ int exp_bits(double x) { return __double2hiint(x) & 0x7ff00000; }
+__device__ __forceinline__ bool all_finite(double a, double b, double c) {
+    return max(max(exp_bits(a), exp_bits(b)), exp_bits(c)) != 0x7ff00000;
+}
+__device__ __forceinline__ bool all_finite(const Particle& p, double w, double x, double y, double z) {
+    const int m = max(max(max(exp_bits(p.X), exp_bits(p.Px)), max(exp_bits(p.Y), exp_bits(p.Py))),
+                      max(max(exp_bits(p.T), exp_bits(w)), max(max(exp_bits(x), exp_bits(y)), exp_bits(z))));
+    return m != 0x7ff00000;
+}
+
 // Nonlinear remainder H_qNL of the quadrupole over s, Eq. (25).
 __device__ __forceinline__ void quad_nonlinear(Particle& p, const PConst& pc, const RefConst& ref, double s) {
     const double pp = p.Px * p.Px + p.Py * p.Py;
@@ -260,18 +272,20 @@ struct LevelProducts {
             q[K - m] = qmul(e, q[K - m]);
         }
     }
-    // Romberg table, Eq. (39b), in place (column j -> j+1), then normalise
+    // Romberg table, Eq. (39b), in place (column j -> j+1), then normalise.
+    // Every entry of column j+1 carries the same divisor 4^(j+1) - 1, so the
+    // divisions are left out: they scale the final entry by a constant that
+    // the normalisation removes.
     __device__ __forceinline__ Quat romberg() {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const double f = (double)(1 << (2 * (j + 1)));
-            const double inv = 1.0 / (f - 1.0);
 #pragma unroll
             for (int k = K; k >= j + 1; --k) {
-                q[k].w = (f * q[k].w - q[k - 1].w) * inv;
-                q[k].x = (f * q[k].x - q[k - 1].x) * inv;
-                q[k].y = (f * q[k].y - q[k - 1].y) * inv;
-                q[k].z = (f * q[k].z - q[k - 1].z) * inv;
+                q[k].w = fma(f, q[k].w, -q[k - 1].w);
+                q[k].x = fma(f, q[k].x, -q[k - 1].x);
+                q[k].y = fma(f, q[k].y, -q[k - 1].y);
+                q[k].z = fma(f, q[k].z, -q[k - 1].z);
             }
         }
         return qnormalize(q[K]);
@@ -384,7 +398,7 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 p.X += L * p.Px * ips;
                 p.Y += L * p.Py * ips;
                 p.T += L * (ref.inv_beta0 - pc.b0pt * ips);
-                if (!isfinite(p.X + p.Y + p.T)) {
+                if (!all_finite(p.X, p.Y, p.T)) {
                     p = p0;
                     is_lost = true;
                     break;
@@ -475,7 +489,7 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     // sin(psi_i - psi_f) = (Px_i Ps_f - Px_f Ps_i) / P_a^2
                     const double sd = (Pxi * Ps - Pxf * Psi) * iPa2;
                     double dpsi;
-                    if (fabs(sd) < 1e-2) {
+                    if ((__double2hiint(sd) & 0x7fffffff) < 0x3f847ae1) {   // |sd| < 1e-2, integer test
                         const double x2 = sd * sd;   // Taylor series of asin, truncation < 1e-21 relative
                         dpsi = sd * fma(x2, fma(x2, fma(x2, fma(x2, 35.0 / 1152.0, 5.0 / 112.0), 3.0 / 40.0),
                                                 1.0 / 6.0), 1.0);
@@ -647,7 +661,7 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
             }
             Quat qe{1.0, 0.0, 0.0, 0.0};
             if constexpr (SPIN) qe = lv.romberg();
-            if (!isfinite(p.X + p.Px + p.Y + p.Py + p.T + qe.w + qe.x + qe.y + qe.z)) {
+            if (!all_finite(p, qe.w, qe.x, qe.y, qe.z)) {
                 p = p0;
                 is_lost = true;
                 break;
