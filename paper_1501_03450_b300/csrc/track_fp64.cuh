@@ -27,6 +27,7 @@ struct Particle {
 
 struct PConst {
     double Pt, P2, P, invP, invP2, b0pt, a, c;   // b0pt = 1/beta0 + Pt, a = 1 + G gamma, c = G (gamma - 1)
+    double cP2;                                   // c / P^2
 };
 
 // Cached matrix-kick coefficients of the linear quadrupole flow over a half
@@ -247,6 +248,19 @@ __device__ __forceinline__ void precession(const Particle& p, const PConst& pc, 
     os = -pre * cu * Ps;
 }
 
+// Omega (Eq. (6b)) times the trapezoid weight w of the edge, for a transverse
+// field b = (bx, by, 0) and frame curvature h (hw = h w): the weight is taken
+// into the common prefactor, G (gamma - 1)(u.b)/P into c/P^2.
+__device__ __forceinline__ void precession_w(const Particle& p, const PConst& pc, double bx, double by, double h,
+                                             double hw, double ips, double Ps, double w, double& ox, double& oy,
+                                             double& os) {
+    const double cu = (p.Px * bx + p.Py * by) * pc.cP2;   // G (gamma-1) (u.b) / P
+    const double pre = -fma(h, p.X, 1.0) * ips * w;
+    ox = pre * (pc.a * bx - cu * p.Px);
+    oy = fma(pre, pc.a * by - cu * p.Py, hw);
+    os = -pre * cu * Ps;
+}
+
 template <int K>
 struct LevelProducts {
     Quat q[K + 1];
@@ -254,7 +268,11 @@ struct LevelProducts {
     // level that samples this edge (the entrance edge starts every level)
     __device__ __forceinline__ void add_edge(int i, int N, double ds, double ox, double oy, double os) {
         double w = (i == 0 || i == N) ? 0.5 * ds : ds;
-        Quat e = quat_from_rotvec(w * ox, w * oy, w * os);
+        add_edge_w(i, w * ox, w * oy, w * os);
+    }
+    // the same with the rotation vector already weighted
+    __device__ __forceinline__ void add_edge_w(int i, double wx, double wy, double wz) {
+        Quat e = quat_from_rotvec(wx, wy, wz);
         if (i == 0) {
             q[K] = e;
 #pragma unroll
@@ -368,6 +386,7 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
     const double gamma = ref.gamma0 * (1.0 + ref.beta0 * pc.Pt);
     pc.a = 1.0 + ref.G * gamma;
     pc.c = ref.G * (gamma - 1.0);
+    pc.cP2 = pc.c * pc.invP2;
     v = sxy[i];
     double sx = v.x, sy = v.y, sz = szp[i];
 
@@ -468,8 +487,8 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 double Ps = ps2 * ips;
                 const double by = eta * h;
                 if constexpr (SPIN) {
-                    precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
-                    lv.add_edge(0, N, ds, ox, oy, os);
+                    precession_w(p, pc, 0.0, by, h, 0.5 * h * ds, ips, Ps, 0.5 * ds, ox, oy, os);
+                    lv.add_edge_w(0, ox, oy, os);
                 }
                 const double dY = ieta * p.Py * ds;
                 const double dT = -ieta * pc.Pt * ds + (1.0 - ieta) * ds * ref.inv_beta0;
@@ -499,8 +518,9 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     p.Y += dY + ieh * p.Py * dpsi;
                     p.T += dT - ieh * pc.b0pt * dpsi;
                     if constexpr (SPIN) {
-                        precession(p, pc, 0.0, by, h, ips, Ps, ox, oy, os);
-                        lv.add_edge(s, N, ds, ox, oy, os);
+                        const double w = s == N ? 0.5 * ds : ds;
+                        precession_w(p, pc, 0.0, by, h, h * w, ips, Ps, w, ox, oy, os);
+                        lv.add_edge_w(s, ox, oy, os);
                     }
                 }
             } else if (type == ST_MULT && !(el.flags & ST_ELEM_ORDER4)) {
@@ -512,8 +532,8 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 double bx = k1 * p.Y + k2 * p.X * p.Y;
                 double by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
                 if constexpr (SPIN) {
-                    precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
-                    lv.add_edge(0, N, ds, ox, oy, os);
+                    precession_w(p, pc, bx, by, 0.0, 0.0, ips, Ps, 0.5 * ds, ox, oy, os);
+                    lv.add_edge_w(0, ox, oy, os);
                 }
                 for (int s = 1; s <= N; ++s) {
                     p.X += half * p.Px * ips;
@@ -532,8 +552,8 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     bx = k1 * p.Y + k2 * p.X * p.Y;
                     by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
                     if constexpr (SPIN) {
-                        precession(p, pc, bx, by, 0.0, ips, Ps, ox, oy, os);
-                        lv.add_edge(s, N, ds, ox, oy, os);
+                        precession_w(p, pc, bx, by, 0.0, 0.0, ips, Ps, s == N ? 0.5 * ds : ds, ox, oy, os);
+                        lv.add_edge_w(s, ox, oy, os);
                     }
                 }
             } else if (type == ST_QUAD_MK && !(el.flags & ST_ELEM_ORDER4)) {
@@ -544,8 +564,8 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
                 double Ps = (pc.P2 - pp) * ips;
                 if constexpr (SPIN) {
-                    precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
-                    lv.add_edge(0, N, ds, ox, oy, os);
+                    precession_w(p, pc, k1 * p.Y, k1 * p.X, 0.0, 0.0, ips, Ps, 0.5 * ds, ox, oy, os);
+                    lv.add_edge_w(0, ox, oy, os);
                 }
                 for (int s = 1; s <= N; ++s) {
                     quad_linear(p, pc, qc, k1);
@@ -555,8 +575,9 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
                     Ps = (pc.P2 - pp) * ips;
                     if constexpr (SPIN) {
-                        precession(p, pc, k1 * p.Y, k1 * p.X, 0.0, ips, Ps, ox, oy, os);
-                        lv.add_edge(s, N, ds, ox, oy, os);
+                        precession_w(p, pc, k1 * p.Y, k1 * p.X, 0.0, 0.0, ips, Ps, s == N ? 0.5 * ds : ds, ox, oy,
+                                     os);
+                        lv.add_edge_w(s, ox, oy, os);
                     }
                 }
             } else if constexpr (EXT) {
