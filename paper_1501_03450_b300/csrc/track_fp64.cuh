@@ -33,7 +33,7 @@ struct PConst {
 // Cached matrix-kick coefficients of the linear quadrupole flow over a half
 // slice for one (|k1|, s): trig plane (C1, S1, al1, be1, ga1) and hyperbolic
 // plane (C2, ...).  They depend only on the particle's P, so they are kept per
-// thread in shared memory (column threadIdx.x of a [10][blockDim] array) and
+// thread in shared memory (column threadIdx.x of a [QC_N][blockDim] array) and
 // recomputed only when the (|k1|, s) key changes.
 struct QuadCache {
     double key_k, key_s;
@@ -44,12 +44,18 @@ struct QuadCache {
     __device__ __forceinline__ double getv(int f) const { return *(const volatile double*)&col[f * stride]; }
     __device__ __forceinline__ void set(int f, double v) { col[f * stride] = v; }
 };
-enum { QC_C1, QC_S1, QC_AL1, QC_BE1, QC_GA1, QC_C2, QC_S2, QC_AL2, QC_BE2, QC_GA2, QC_N };
+// Per plane kind (1: trigonometric, the focusing plane; 2: hyperbolic) over a
+// half slice s, for this particle's P: C = cos/cosh(w s), SP = S/P (S =
+// sin/sinh(w s)/w), KS = -/+ |k1| S (the Px update of that plane), and the T
+// integrals of the linear flow, (s + C S)/2 (AL), -/+ |k1| S^2 (BE) and
+// +/- P |k1| (s - C S)/2 (GA), multiplied by (1/beta0 + Pt)/(2 P^3).
+enum { QC_C1, QC_SP1, QC_KS1, QC_AL1, QC_BE1, QC_GA1, QC_C2, QC_SP2, QC_KS2, QC_AL2, QC_BE2, QC_GA2, QC_N };
 
 // Fill one coefficient set (column col, row stride) for (|k1|, s).  Called
 // only when the key changes, so it is kept out of line: its transcendental
 // functions then add no register pressure to the tracking loop.
-static __device__ __noinline__ void quad_coeffs_fill(double* col, int stride, double invP, double absk1, double s) {
+static __device__ __noinline__ void quad_coeffs_fill(double* col, int stride, double invP, double P, double fT,
+                                                     double absk1, double s) {
     double w = sqrt(absk1 * invP);
     double ws = w * s;
     double C1, S1, C2, S2;
@@ -68,53 +74,58 @@ static __device__ __noinline__ void quad_coeffs_fill(double* col, int stride, do
         C1 = C2 = 1.0;
         S1 = S2 = s;
     }
-    // integrals over the half slice used by the T update: (s + C S)/2, S^2, (s - C S)/2
     col[QC_C1 * stride] = C1;
-    col[QC_S1 * stride] = S1;
-    col[QC_AL1 * stride] = 0.5 * (s + C1 * S1);
-    col[QC_BE1 * stride] = S1 * S1;
-    col[QC_GA1 * stride] = 0.5 * (s - C1 * S1);
+    col[QC_SP1 * stride] = S1 * invP;
+    col[QC_KS1 * stride] = -absk1 * S1;
+    col[QC_AL1 * stride] = fT * 0.5 * (s + C1 * S1);
+    col[QC_BE1 * stride] = -fT * absk1 * S1 * S1;
+    col[QC_GA1 * stride] = fT * P * absk1 * 0.5 * (s - C1 * S1);
     col[QC_C2 * stride] = C2;
-    col[QC_S2 * stride] = S2;
-    col[QC_AL2 * stride] = 0.5 * (s + C2 * S2);
-    col[QC_BE2 * stride] = S2 * S2;
-    col[QC_GA2 * stride] = 0.5 * (s - C2 * S2);
+    col[QC_SP2 * stride] = S2 * invP;
+    col[QC_KS2 * stride] = absk1 * S2;
+    col[QC_AL2 * stride] = fT * 0.5 * (s + C2 * S2);
+    col[QC_BE2 * stride] = fT * absk1 * S2 * S2;
+    col[QC_GA2 * stride] = -fT * P * absk1 * 0.5 * (s - C2 * S2);
 }
 
 __device__ __forceinline__ void quad_coeffs(QuadCache& qc, const PConst& pc, double absk1, double s) {
     qc.key_k = absk1;
     qc.key_s = s;
-    quad_coeffs_fill(qc.col, qc.stride, pc.invP, absk1, s);
+    quad_coeffs_fill(qc.col, qc.stride, pc.invP, pc.P, 0.5 * pc.b0pt * pc.invP * pc.invP2, absk1, s);
 }
 
-// Linear quadrupole flow H_qL over s (Eq. (24)); per plane with focusing
-// constant K_u = +-k1/P: u' = u C + (pu/P) S, pu' = pu C - P K_u u S, and
-// T' = T - (1/beta0 + Pt)/(2 P^3) * sum_u [pu^2 (s + C S)/2 - P K_u u pu S^2
-//                                          + P^2 K_u u^2 (s - C S)/2].
 template <bool REREAD>
 __device__ __forceinline__ double qcget(const QuadCache& qc, int f) {
     if constexpr (REREAD) return qc.getv(f);
     return qc.get(f);
 }
 
+// Linear quadrupole flow H_qL over a half slice (Eq. (24)): per plane with
+// focusing constant K_u = +-k1/P,
+//   u' = u C + (pu/P) S,  pu' = pu C - P K_u u S,
+//   T' = T - (1/beta0 + Pt)/(2 P^3) [pu^2 (s + C S)/2 - P K_u u pu S^2 + P^2 K_u u^2 (s - C S)/2];
+// the x plane is the trigonometric one for k1 >= 0, the hyperbolic one for
+// k1 < 0, and the y plane the other (the signs sit in the cached coefficients).
 template <bool REREAD = false>
 __device__ __forceinline__ void quad_linear(Particle& p, const PConst& pc, const QuadCache& qc, double k1) {
     const bool foc = k1 >= 0.0;
-    const int ox_ = foc ? 0 : 5, oy_ = foc ? 5 : 0;   // field offsets of the x and y planes
-    const double Cx = qcget<REREAD>(qc, QC_C1 + ox_), Sx = qcget<REREAD>(qc, QC_S1 + ox_);
-    const double Cy = qcget<REREAD>(qc, QC_C1 + oy_), Sy = qcget<REREAD>(qc, QC_S1 + oy_);
-    const double alx = qcget<REREAD>(qc, QC_AL1 + ox_), bex = qcget<REREAD>(qc, QC_BE1 + ox_), gax = qcget<REREAD>(qc, QC_GA1 + ox_);
-    const double aly = qcget<REREAD>(qc, QC_AL1 + oy_), bey = qcget<REREAD>(qc, QC_BE1 + oy_), gay = qcget<REREAD>(qc, QC_GA1 + oy_);
-    double X = p.X, Px = p.Px, Y = p.Y, Py = p.Py;
-    double Pk = pc.P * k1;   // P^2 K_x = P k1
-    double tsum = Px * Px * alx - k1 * X * Px * bex + Pk * X * X * gax
-                + Py * Py * aly + k1 * Y * Py * bey - Pk * Y * Y * gay;
-    double f = 0.5 * pc.b0pt * pc.invP * pc.invP * pc.invP;
-    p.T -= f * tsum;
-    p.X = X * Cx + Px * pc.invP * Sx;
-    p.Px = Px * Cx - k1 * X * Sx;
-    p.Y = Y * Cy + Py * pc.invP * Sy;
-    p.Py = Py * Cy + k1 * Y * Sy;
+    const int ox_ = foc ? 0 : 6, oy_ = foc ? 6 : 0;   // coefficient offsets of the x and y planes
+    const double Cx = qcget<REREAD>(qc, QC_C1 + ox_), SPx = qcget<REREAD>(qc, QC_SP1 + ox_),
+                 KSx = qcget<REREAD>(qc, QC_KS1 + ox_);
+    const double Cy = qcget<REREAD>(qc, QC_C1 + oy_), SPy = qcget<REREAD>(qc, QC_SP1 + oy_),
+                 KSy = qcget<REREAD>(qc, QC_KS1 + oy_);
+    const double alx = qcget<REREAD>(qc, QC_AL1 + ox_), bex = qcget<REREAD>(qc, QC_BE1 + ox_),
+                 gax = qcget<REREAD>(qc, QC_GA1 + ox_);
+    const double aly = qcget<REREAD>(qc, QC_AL1 + oy_), bey = qcget<REREAD>(qc, QC_BE1 + oy_),
+                 gay = qcget<REREAD>(qc, QC_GA1 + oy_);
+    const double X = p.X, Px = p.Px, Y = p.Y, Py = p.Py;
+    const double tx = fma(X * gax, X, Px * fma(Px, alx, X * bex));
+    const double ty = fma(Y * gay, Y, Py * fma(Py, aly, Y * bey));
+    p.T -= tx + ty;
+    p.X = fma(Px, SPx, X * Cx);
+    p.Px = fma(X, KSx, Px * Cx);
+    p.Y = fma(Py, SPy, Y * Cy);
+    p.Py = fma(Y, KSy, Py * Cy);
 }
 
 // 1/sqrt(a2 - p2) given ia = 1/sqrt(a2), ia2 = 1/a2 and p2 >= 0.  Near the
@@ -634,7 +645,8 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     if (qc.key_k != absk || qc.key_s != el.a[2]) quad_coeffs(qc, pc, absk, el.a[2]);
                     double* key2 = qc.col + (2 * QC_N) * qc.stride;
                     if (key2[0] != absk || key2[qc.stride] != el.a[3]) {
-                        quad_coeffs_fill(qc.col + QC_N * qc.stride, qc.stride, pc.invP, absk, el.a[3]);
+                        quad_coeffs_fill(qc.col + QC_N * qc.stride, qc.stride, pc.invP, pc.P, 0.5 * pc.b0pt * pc.invP * pc.invP2,
+                                         absk, el.a[3]);
                         key2[0] = absk;
                         key2[qc.stride] = el.a[3];
                     }
