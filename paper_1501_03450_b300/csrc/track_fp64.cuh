@@ -272,6 +272,13 @@ __device__ __forceinline__ void precession_w(const Particle& p, const PConst& pc
     os = -pre * cu * Ps;
 }
 
+// prod_{j=1..K} (4^j - 1), the divisor of the bottom-right Romberg entry
+__host__ __device__ constexpr double romberg_divisor(int K) {
+    double d = 1.0;
+    for (int j = 1; j <= K; ++j) d *= (double)((1 << (2 * j)) - 1);
+    return d;
+}
+
 template <int K>
 struct LevelProducts {
     Quat q[K + 1];
@@ -301,10 +308,12 @@ struct LevelProducts {
             q[K - m] = qmul(e, q[K - m]);
         }
     }
-    // Romberg table, Eq. (39b), in place (column j -> j+1), then normalise.
-    // Every entry of column j+1 carries the same divisor 4^(j+1) - 1, so the
-    // divisions are left out: they scale the final entry by a constant that
-    // the normalisation removes.
+    // Romberg table, Eq. (39b), in place (column j -> j+1).  Every entry of
+    // column j+1 carries the same divisor 4^(j+1) - 1, so the divisions are
+    // applied once, to the final entry, as the exact product of the divisors.
+    // The entry is not normalised here: scalar factors commute through the
+    // composition, so normalising the turn quaternion once per turn gives the
+    // same rotation as normalising every element (Sec. 4.3).
     __device__ __forceinline__ Quat romberg() {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
@@ -317,7 +326,8 @@ struct LevelProducts {
                 q[k].z = fma(f, q[k].z, -q[k - 1].z);
             }
         }
-        return qnormalize(q[K]);
+        constexpr double inv = 1.0 / romberg_divisor(K);
+        return Quat{q[K].w * inv, q[K].x * inv, q[K].y * inv, q[K].z * inv};
     }
 };
 
@@ -503,17 +513,19 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 }
                 const double dY = ieta * p.Py * ds;
                 const double dT = -ieta * pc.Pt * ds + (1.0 - ieta) * ds * ref.inv_beta0;
+                double PsE = Ps - eta;
                 for (int s = 1; s <= N; ++s) {
                     // exact sector-bend map over ds, Eq. (10): (Px, A = Ps - eta(1+hX))
                     // rotates by h ds; X follows from Ps - A = eta (1 + hX)
                     const double Pxi = p.Px, Psi = Ps;
-                    double A = Ps - eta * (1.0 + h * p.X);
+                    double A = fma(-by, p.X, PsE);   // by = eta h
                     double Pxf = Pxi * cb + A * sb;
                     double Af = A * cb - Pxi * sb;
                     ps2 = Pa2 - Pxf * Pxf;
                     ips = inv_sqrt_diff(Pa2, iPa, iPa2, Pxf * Pxf);
                     Ps = ps2 * ips;
-                    p.X = (Ps - Af - eta) * ieh;
+                    PsE = Ps - eta;
+                    p.X = (PsE - Af) * ieh;
                     p.Px = Pxf;
                     // asin(Px_i/P_a) - asin(Px_f/P_a) = asin(sin of the difference),
                     // sin(psi_i - psi_f) = (Px_i Ps_f - Px_f Ps_i) / P_a^2
@@ -547,9 +559,10 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     lv.add_edge_w(0, ox, oy, os);
                 }
                 for (int s = 1; s <= N; ++s) {
-                    p.X += half * p.Px * ips;
-                    p.Y += half * p.Py * ips;
-                    p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
+                    double hips = half * ips;
+                    p.X = fma(p.Px, hips, p.X);
+                    p.Y = fma(p.Py, hips, p.Y);
+                    p.T = fma(half, fma(-pc.b0pt, ips, ref.inv_beta0), p.T);
                     by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
                     bx = k1 * p.Y + k2 * p.X * p.Y;
                     p.Px -= ds * by;
@@ -557,9 +570,10 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                     pp = p.Px * p.Px + p.Py * p.Py;
                     ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
                     Ps = (pc.P2 - pp) * ips;
-                    p.X += half * p.Px * ips;
-                    p.Y += half * p.Py * ips;
-                    p.T += half * (ref.inv_beta0 - pc.b0pt * ips);
+                    hips = half * ips;
+                    p.X = fma(p.Px, hips, p.X);
+                    p.Y = fma(p.Py, hips, p.Y);
+                    p.T = fma(half, fma(-pc.b0pt, ips, ref.inv_beta0), p.T);
                     bx = k1 * p.Y + k2 * p.X * p.Y;
                     by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
                     if constexpr (SPIN) {
