@@ -28,6 +28,7 @@ struct Particle {
 struct PConst {
     double Pt, P2, P, invP, invP2, b0pt, a, c;   // b0pt = 1/beta0 + Pt, a = 1 + G gamma, c = G (gamma - 1)
     double cP2;                                   // c / P^2
+    double hP3;                                   // 1 / (2 P^3)
 };
 
 // Cached matrix-kick coefficients of the linear quadrupole flow over a half
@@ -155,10 +156,11 @@ __device__ __forceinline__ bool all_finite(const Particle& p, double w, double x
 __device__ __forceinline__ void quad_nonlinear(Particle& p, const PConst& pc, const RefConst& ref, double s) {
     const double pp = p.Px * p.Px + p.Py * p.Py;
     const double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
-    const double d = ips - pc.invP;
-    p.X += s * p.Px * d;
-    p.Y += s * p.Py * d;
-    p.T += -s * pc.b0pt * (ips - pc.invP * pp * 0.5 * pc.invP2) + s * ref.inv_beta0;
+    const double sd = s * (ips - pc.invP);
+    p.X = fma(p.Px, sd, p.X);
+    p.Y = fma(p.Py, sd, p.Y);
+    // T += s [1/beta0 - (1/beta0 + Pt)(1/Ps - p^2/(2 P^3))]
+    p.T = fma(s, fma(-pc.b0pt, fma(-pc.hP3, pp, ips), ref.inv_beta0), p.T);
 }
 
 // Exact drift over s (Eq. (29b)) given ips = 1/Ps of the current momentum.
@@ -408,6 +410,7 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
     pc.a = 1.0 + ref.G * gamma;
     pc.c = ref.G * (gamma - 1.0);
     pc.cP2 = pc.c * pc.invP2;
+    pc.hP3 = 0.5 * pc.invP * pc.invP2;
     v = sxy[i];
     double sx = v.x, sy = v.y, sz = szp[i];
 
