@@ -122,7 +122,7 @@ static BatchKernel batch_kernel(int precision, int K, int variant, bool ext) {
                 return variant ? track_batch_fp64_kernel<KK, 3, true> : track_batch_fp64_kernel<KK, 2, true>; \
             return variant ? track_batch_fp64_kernel<KK, 3, false> : track_batch_fp64_kernel<KK, 2, false>;   \
         }                                                                                                     \
-        return variant ? track_batch_mixed_kernel<KK, 4> : track_batch_mixed_kernel<KK, 3>;
+        return variant ? track_batch_mixed_kernel<KK, 3> : track_batch_mixed_kernel<KK, 2>;
     switch (K) {
         ST_SEL(0)
         ST_SEL(1)
