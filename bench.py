@@ -60,8 +60,8 @@ FP64_PIPE_INSTR_PER_PASS = 278.4
 FP64_PIPE_LANES_PER_SM_CLOCK = 2
 # DRAM bytes (read + write) per particle per launch of the FP64 tracker, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the same capture (2e4
-# particles: 1.586 MB + 0 B), scaled linearly with the particle count.
-FP64_DRAM_BYTES_PER_PARTICLE = 79.3
+# particles: 1.590 MB + 0 B), scaled linearly with the particle count.
+FP64_DRAM_BYTES_PER_PARTICLE = 79.5
 
 
 def parse_args():
@@ -233,7 +233,7 @@ MIXED_WORKLOAD_PARTICLES = 1_000_000
 # FP32 floating-point operations the mixed tracker executes per pass on this
 # workload (2 per FFMA, 1 per FADD/FMUL), from one ncu capture
 # (profiles/track_mixed_rhic_like_ncu.md); None until measured.
-MIXED_FP32_FLOPS_PER_PASS = 2254.1
+MIXED_FP32_FLOPS_PER_PASS = 2251.3
 
 
 def variant_mixed(st, torch, args, fp64_value, fp32_peak):
