@@ -17,7 +17,9 @@ import numpy as np
 
 from . import _build
 
-LIB_PATH = _build.LIB
+# SPINTRACK_LIB selects another build of the library (e.g. the checked build,
+# _build.LIB_CHECKED); it is then loaded as it is, without rebuilding
+LIB_PATH = os.environ.get("SPINTRACK_LIB", _build.LIB)
 
 ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ESTATE = 0, -1, -2, -3, -4, -5
 ST_DRIFT, ST_MULT, ST_QUAD_MK, ST_SBEND, ST_SNAKE, ST_SOLENOID, ST_RBEND = 0, 1, 2, 3, 4, 5, 6
@@ -104,7 +106,7 @@ def load(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing and not _build.up_to_date():
+    if build_if_missing and LIB_PATH == _build.LIB and not _build.up_to_date():
         _build.build()
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"spintrack CUDA library not found at {LIB_PATH}; run __graft_entry__.build()")

@@ -62,7 +62,21 @@ __device__ __forceinline__ void batch_loop(const JobDesc* __restrict__ jobs, con
         const int it = s_item;
         if (it >= n_items) break;
         const WorkItem w = items[it];
+        if constexpr (kChecked) {
+            if (w.job < 0 || w.first < 0 || w.count < 0 || w.count > (int)blockDim.x) {
+                if (threadIdx.x == 0) atomicExch(status, STATUS_BOUNDS);
+                __syncthreads();
+                continue;
+            }
+        }
         const JobDesc J = jobs[w.job];
+        if constexpr (kChecked) {
+            if ((int64_t)w.first + w.count > J.n) {
+                if (threadIdx.x == 0) atomicExch(status, STATUS_BOUNDS);
+                __syncthreads();
+                continue;
+            }
+        }
         if (w.job != cur_job) {
             if (threadIdx.x == 0) issue_bulk_stage(smem, J.blob, J.blob_bytes, bar);
             const bool ok = mbar_wait_bounded_parity(bar, phase, 1000000000ull);
@@ -92,7 +106,8 @@ __global__ void __launch_bounds__(128, EXT ? (MINB > 2 ? MINB - 1 : MINB) : MINB
     __shared__ double qcache[(2 * QC_N + 2) * 128];
     batch_loop(jobs, items, n_items, queue, status, smem, &bar, [&](const JobDesc& J, int64_t i) {
         fp64_track_particle<K, true, EXT>((const DevElem*)smem, (const uint16_t*)(smem + J.seq_offset), J.n_seq, J.ref, J.xpx,
-                               J.ypy, J.tpt, J.sxy, J.sz, J.lost, i, n_turns, qcache);
+                               J.ypy, J.tpt, J.sxy, J.sz, J.lost, i, n_turns, qcache,
+                               TurnOut{nullptr, nullptr, 0, {}}, status);
     });
 }
 
@@ -106,7 +121,7 @@ __global__ void __launch_bounds__(128, MINB) track_batch_mixed_kernel(const JobD
     batch_loop(jobs, items, n_items, queue, status, smem, &bar, [&](const JobDesc& J, int64_t i) {
         mixed_track_particle<K>((const MixElem*)smem, (const uint16_t*)(smem + J.seq_offset),
                                 (const float2*)(smem + J.rho_offset), J.n_seq, J.ref, J.xpx, J.ypy, J.tpt, J.sxy,
-                                J.sz, J.lost, i, n_turns);
+                                J.sz, J.lost, i, n_turns, status);
     });
 }
 
@@ -544,6 +559,10 @@ int st_batch_download(st_batch* b, int32_t job, double* spin_soa, double* z_soa,
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, b->status, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "st_batch_download");
+    if (status == STATUS_BOUNDS) {
+        set_error("st_batch_download: the checked build found an out-of-range table index or work item");
+        return ST_EINVAL;
+    }
     if (status != STATUS_OK) {
         set_error("st_batch_download: a batched kernel reported status %d (bounded wait expired)", status);
         return ST_ETIMEOUT;

@@ -518,6 +518,10 @@ int st_spins_download(st_ctx* ctx, double* spin_soa, double* z_soa, uint8_t* los
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "st_spins_download");
+    if (status == STATUS_BOUNDS) {
+        set_error("st_spins_download: the checked build found an out-of-range element-table index");
+        return ST_EINVAL;
+    }
     if (status != STATUS_OK) {
         set_error("st_spins_download: a tracking kernel reported status %d (bounded wait expired)", status);
         return ST_ETIMEOUT;

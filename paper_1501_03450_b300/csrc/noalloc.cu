@@ -173,6 +173,10 @@ extern "C" int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, c
     e = cudaMemcpyAsync(&host_status, status, sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "st_track_fp64_noalloc");
+    if (host_status == STATUS_BOUNDS) {
+        set_error("st_track_fp64_noalloc: the checked build found an out-of-range element-table index");
+        return ST_EINVAL;
+    }
     if (host_status != STATUS_OK) {
         set_error("st_track_fp64_noalloc: the tracking kernel reported status %d (bounded wait expired)",
                   host_status);

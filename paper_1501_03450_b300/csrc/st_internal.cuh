@@ -101,7 +101,17 @@ struct __align__(16) MixElem {
 static_assert(sizeof(MixElem) % 16 == 0, "MixElem must be a multiple of 16 bytes");
 
 // Kernel status word values (written by bounded device waits).
-enum : int32_t { STATUS_OK = 0, STATUS_TMA_TIMEOUT = 1 };
+enum : int32_t { STATUS_OK = 0, STATUS_TMA_TIMEOUT = 1, STATUS_BOUNDS = 3 };
+
+// Checked build (compiled with -DST_CHECKED into a separate library): the
+// trackers test every element-table index and the batch loop its work items
+// before use; a violation writes STATUS_BOUNDS to the launch's status word and
+// freezes the particle (no trap).  The release build compiles the tests out.
+#ifdef ST_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
 
 struct LatticeImpl {
     RefConst ref;

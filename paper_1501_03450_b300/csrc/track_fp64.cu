@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
     if (i >= n || lost[i]) continue;
 
     fp64_track_particle<K, SPIN, EXT>(table, seq, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns, qcache,
-                                         tq);
+                                         tq, status);
     }  // particle loop
 }
 

@@ -389,7 +389,10 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                                                     double2* __restrict__ ypy, double2* __restrict__ tpt,
                                                     double2* __restrict__ sxy, double* __restrict__ szp,
                                                     uint8_t* __restrict__ lost, int64_t i, int n_turns,
-                                                    double* qcache, const TurnOut& tq = TurnOut{nullptr, nullptr, 0, {}}) {
+                                                    double* qcache, const TurnOut& tq = TurnOut{nullptr, nullptr, 0, {}},
+                                                    int32_t* status = nullptr) {
+    // table entries below the sequence (both staged into shared memory back to back)
+    const int n_table = (int)(((const char*)seq - (const char*)table) / sizeof(DevElem));
     Particle p;
     double2 v = xpx[i];
     p.X = v.x;
@@ -428,7 +431,15 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
     for (int turn = 0; turn < n_turns && !is_lost; ++turn) {
         Quat qt{1.0, 0.0, 0.0, 0.0};
         for (int e = 0; e < n_seq; ++e) {
-            const DevElem& el = table[seq[e]];
+            const int idx = seq[e];
+            if constexpr (kChecked) {
+                if (idx >= n_table) {
+                    if (status) atomicExch(status, STATUS_BOUNDS);
+                    is_lost = true;
+                    break;
+                }
+            }
+            const DevElem& el = table[idx];
             const int type = el.type;
             if (type == ST_SNAKE) {
                 if constexpr (SPIN) qt = qmul(Quat{el.a[0], el.a[1], el.a[2], el.a[3]}, qt);

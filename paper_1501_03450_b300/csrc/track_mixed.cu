@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(128, 2) track_mixed_kernel(const void* __restr
         const int64_t i = wi * 32 + lane;
         if (i >= n || lost[i]) continue;
 
-        mixed_track_particle<K, SPIN>(table, seq, rho, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns);
+        mixed_track_particle<K, SPIN>(table, seq, rho, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns,
+                                      status);
     }
 }
 

@@ -379,7 +379,9 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                                                      double2* __restrict__ xpx, double2* __restrict__ ypy,
                                                      double2* __restrict__ tpt, double2* __restrict__ sxy,
                                                      double* __restrict__ szp, uint8_t* __restrict__ lost, int64_t i,
-                                                     int n_turns) {
+                                                     int n_turns, int32_t* status = nullptr) {
+    // table entries below the sequence (both staged into shared memory back to back)
+    const int n_table = (int)(((const char*)seq - (const char*)table) / sizeof(MixElem));
     // state and per-particle constants (FP64 -> compensated FP32)
     MState z;
     double2 v = xpx[i];
@@ -439,7 +441,15 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
     for (int turn = 0; turn < n_turns && !is_lost; ++turn) {
         FQ qt{FF{1.0f, 0.0f}, FF{0.0f, 0.0f}, FF{0.0f, 0.0f}, FF{0.0f, 0.0f}};
         for (int e = 0; e < n_seq; ++e) {
-            const MixElem& el = table[seq[e]];
+            const int idx = seq[e];
+            if constexpr (kChecked) {
+                if (idx >= n_table) {
+                    if (status) atomicExch(status, STATUS_BOUNDS);
+                    is_lost = true;
+                    break;
+                }
+            }
+            const MixElem& el = table[idx];
             const int type = el.type;
             if (type == ST_SNAKE) {
                 if constexpr (SPIN) fq_premul_ref(qt, el.rq);

@@ -38,6 +38,17 @@ def test_library_exports_every_declared_symbol():
         assert name in st.SIGNATURES, f"binding lacks a signature for {name}"
 
 
+def test_checked_build_exports_the_same_symbols():
+    """The index-checked build (same sources, -DST_CHECKED) is a drop-in
+    replacement selected with SPINTRACK_LIB."""
+    from paper_1501_03450_b300 import _build
+    if not os.path.exists(_build.LIB_CHECKED) or not _build.up_to_date(checked=True):
+        _build.build(checked=True)
+    lib = ctypes.CDLL(_build.LIB_CHECKED)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
 def test_version_and_error_string():
     lib = st.load()
     assert b"sm_103a" in lib.st_version()
