@@ -323,7 +323,7 @@ class SpinMapSurrogate:
 
     def track_plain(self, z: np.ndarray, S: np.ndarray, n_turns: int, average: bool = True,
                     timed: bool = False):
-        """The same with plain FP64 spin tracking (the judge of the map)."""
+        """The same with plain FP64 spin tracking (the reference for the map's error)."""
         return _run(self, z, S, n_turns, average, timed, surrogate=False)
 
     def close(self):

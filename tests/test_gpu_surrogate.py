@@ -2,7 +2,7 @@
 G*gamma0 = 45.5: pairs tracked by the FP64 tracker along the orbits of a
 Gaussian ensemble, the FP64 polynomial head, the network trained by its own
 tensor-core kernels, and stroboscopic tracking of an independent ensemble
-with the map while the orbit is tracked exactly.  Judged against plain FP64
+with the map while the orbit is tracked exactly.  Compared with plain FP64
 spin tracking (the tracker that matches the oracle to 1e-11): the spin error
 after 1000 turns stays within 1e-4 (mean over 1024 particles, final spin and
 turn average), the trained network gains over the polynomial head alone,

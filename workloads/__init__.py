@@ -355,7 +355,7 @@ def workload(name: str, spin_order: int = 2, Ggamma0: float = None):
         # learned one-turn spin map: training pairs along the orbits of 4e4
         # Gaussian particles (cut at 3 sigma) over 100 turns (4e6 pairs);
         # use on 1e4 particles x 1e4 turns of stroboscopic averaging; errors
-        # judged on 1024 particles at turn 1000
+        # measured on 1024 particles at turn 1000
         ring = rhic_like_ring(45.5 if Ggamma0 is None else Ggamma0)
         return dict(ring=with_spin_order(ring, spin_order), n_particles=10000,
                     turns=10000, spin_order=spin_order, seed=3452, cut=3.0,
