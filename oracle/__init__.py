@@ -37,7 +37,13 @@ _VARIANTS = {
     "c128": ("double complex", np.complex128),
 }
 
-TYPE_CODES = {"drift": 0, "mult": 1, "quad_mk": 2, "sbend": 3, "snake": 4, "solenoid": 5, "rbend": 6}
+TYPE_CODES = {"drift": 0, "mult": 1, "quad_mk": 2, "sbend": 3, "snake": 4, "solenoid": 5, "rbend": 6,
+              "teapot": 7}
+
+# spin_order values of the midpoint (piece-wise constant) schemes; 0..6 are
+# Romberg orders over slice-edge samples
+MID_HALF = -1   # each slice as two half-slices, the spin rotation between them
+MID_KICK = -2   # second-order drift-kick / matrix-kick slices: between the halves of the central kick
 
 _lock = threading.Lock()
 _libs = {}
@@ -130,7 +136,8 @@ def _ptr(a: np.ndarray):
 
 def track(ring, z, S, n_turns, spin_order, lost=None, variant="f64", n_threads=0):
     """Track particles (z [6,n], S [3,n]) through `ring` for n_turns turns with
-    Romberg order spin_order.  Returns new arrays (z, S, lost)."""
+    Romberg order spin_order (or one of the midpoint schemes MID_HALF,
+    MID_KICK).  Returns new arrays (z, S, lost)."""
     dt = _VARIANTS[variant][1]
     z = np.ascontiguousarray(np.array(z, dtype=dt))
     S = np.ascontiguousarray(np.array(S, dtype=dt))
@@ -150,7 +157,7 @@ def element_detail(el, G, Ggamma0, z6, S3, spin_order, variant="f64"):
     dt = _VARIANTS[variant][1]
     z6 = np.ascontiguousarray(np.array(z6, dtype=dt).reshape(6))
     S3 = np.ascontiguousarray(np.array(S3, dtype=dt).reshape(3))
-    levels = np.zeros((spin_order + 1, 4), dtype=dt)
+    levels = np.zeros((max(spin_order, 0) + 1, 4), dtype=dt)
     Q = np.zeros(4, dtype=dt)
     rc = _lib(variant).orc_element_detail(elements_array([el]), G, Ggamma0, _ptr(z6), _ptr(S3),
                                           int(spin_order), _ptr(levels), _ptr(Q))
@@ -167,7 +174,7 @@ def orbit_map(el, G, Ggamma0, z6, variant="f64"):
 
 
 SUBFLOWS = {"drift": 0, "kick": 1, "quad_linear": 2, "quad_nonlinear": 3, "sbend": 4, "solenoid": 5,
-            "rbend_body": 6, "rbend_rotation": 7, "rbend_fringe": 8}
+            "rbend_body": 6, "rbend_rotation": 7, "rbend_fringe": 8, "curved_drift": 9, "teapot_kick": 10}
 
 
 def subflow(which, G, Ggamma0, z6, s, k1=0.0, k2=0.0, h=0.0, eta=1.0, variant="f64"):

@@ -24,6 +24,8 @@
  *             orbit map, Eq. (dipolefringe); exact body map, Eqs. (rhob),
  *             (rbend); offsets, Eqs. (Xoffset), (Toffset); fringe spin kick
  *             of a rectangular bend, Eq. (skfringeRB)
+ *   Sec. 3.6  TEAPOT split of a sector bend, Eqs. (DKsplit), (teapotD): curved
+ *             drift and the kick of the bend's uniform field (Eq. (sbendA))
  *   Sec. 3.7  solenoid: exact body map Eq. (solenoid) of the Hamiltonian
  *             Eq. (Hsolenoid) with the vector potential Eq. (Asol); the
  *             unit velocity from the kinetic momentum, Eq. (mgVSol)
@@ -32,6 +34,9 @@
  *             Eq. (skfringe), on elements whose fringe flag is set
  *   Sec. 4.1  piece-wise constant spin rotations composed as quaternions,
  *             later slices on the left, Eq. (37)
+ *             or, for the midpoint schemes, with Omega at the middle of each
+ *             slice (each slice as two half-slices, or its central kick split;
+ *             Sec. 5.3, Fig. oneTurnSpinErrs)
  *   Sec. 4.3  trapezoid-weighted edge rotations, sub-sampled levels Q(h/2^k),
  *             Romberg table and normalisation per element, Eqs. (38)-(39)
  *   Sec. 5    thin Siberian snakes (orbit-transparent spin rotators)
@@ -77,14 +82,26 @@ typedef ORACLE_REAL real;
 #define RE(x) ((double)creal(x))
 
 /* Element kinds (own numbering; the CUDA library has its own). */
-enum { ORC_DRIFT = 0, ORC_MULT = 1, ORC_QUAD_MK = 2, ORC_SBEND = 3, ORC_SNAKE = 4, ORC_SOLENOID = 5, ORC_RBEND = 6 };
+enum { ORC_DRIFT = 0, ORC_MULT = 1, ORC_QUAD_MK = 2, ORC_SBEND = 3, ORC_SNAKE = 4, ORC_SOLENOID = 5, ORC_RBEND = 6,
+       ORC_TEAPOT = 7 };
+
+/* Spin integration schemes other than the Romberg orders K >= 0 (Sec. 4.1,
+ * Eq. (37) with Omega taken at the middle of each slice):
+ *   ORC_MID_HALF  each slice is traversed as two half-slices of its own map,
+ *                 the spin rotation by ds Omega between them ("half-DKD,
+ *                 spin rotation, half-DKD");
+ *   ORC_MID_KICK  the slices of the second-order drift-kick and matrix-kick
+ *                 splits keep their map and rotate the spin between the two
+ *                 halves of the central kick ("half-drift, half-kick, spin
+ *                 rotation, half-kick, half-drift"); exact maps as ORC_MID_HALF. */
+enum { ORC_MID_HALF = -1, ORC_MID_KICK = -2 };
 
 typedef struct {
     int32_t type;
     int32_t n_slices;
     double L, k1, k2, angle, eta, snake_phi, snake_mu;
     int32_t fringe;      /* 1: thin fringe spin kicks at both ends (mult, quad_mk, sbend) */
-    int32_t split_order; /* mult, quad_mk: 0 or 2 = Eq. (27), 4 = Yoshida's fourth order */
+    int32_t split_order; /* mult, quad_mk, teapot: 0 or 2 = Eq. (27), 4 = Yoshida's fourth order */
     double e1;           /* rbend: the beam meets the entrance face at phi_entr = angle/2 + e1
                           * and the exit face at phi_exit = -angle/2 + e1 */
 } orc_element;
@@ -173,6 +190,36 @@ static int sbend_map(const orc_ref* r, orc_orbit* z, double h, double eta, doubl
     z->X = Xf;
     z->Px = Pxf;
     return 0;
+}
+
+/* TEAPOT split of a sector bend, Sec. 3.6, Eq. (DKsplit): H_T = H_D + H_K.
+ * Drift part: the flow of H_D = -(1 + hX) Ps + Pt/beta0 over s, Eq. (teapotD)
+ * (a straight line seen from the frame that turns by h s about the centre of
+ * curvature).  The arrival time also carries the reference term s/beta0 of
+ * the Pt/beta0 part of Eq. (generalH), which the printed Eq. (teapotD) leaves
+ * out. */
+static int curved_drift(const orc_ref* r, orc_orbit* z, double h, double s) {
+    real ps2 = momentum_sq(r, z->Pt) - z->Px * z->Px - z->Py * z->Py;
+    if (!(RE(ps2) > 0.0)) return 1;
+    real Ps = sqrt(ps2);
+    double phi = h * s;
+    double t = tan(phi), c = cos(phi), sn = sin(phi);
+    real den = 1.0 - (z->Px / Ps) * t;
+    if (!(RE(den) > 0.0)) return 1;
+    real R = 1.0 / h + z->X;
+    real d = R * t / den;                    /* (1/h + X^i) tan(hs) / (1 - (Px^i/Ps^i) tan(hs)) */
+    z->X = R / (c * den) - 1.0 / h;          /* Eq. (teapotD), X */
+    z->Y = z->Y + (z->Py / Ps) * d;          /* Y */
+    z->T = z->T - ((1.0 / r->beta0 + z->Pt) / Ps) * d + s / r->beta0;   /* T, with s/beta0 */
+    z->Px = z->Px * c + Ps * sn;             /* Px */
+    return 0;
+}
+
+/* Kick part: the flow of H_K = -(q/p0)(1 + hX) A_s over s for the sector
+ * bend's uniform field, whose vector-potential term is (eta/2)(1 + hX)^2
+ * (Eq. (sbendA) with eta of Eq. (9)): dPx/ds = -eta h (1 + hX). */
+static void teapot_kick(orc_orbit* z, double h, double eta, double s) {
+    z->Px -= s * eta * h * (1.0 + h * z->X);
 }
 
 static real sinc_(real x) { return (RE(x) == 0.0 && cimag(x) == 0.0) ? (real)1.0 : sin(x) / x; }
@@ -370,6 +417,10 @@ static int slice_map2(const orc_ref* r, const orc_element* e, orc_orbit* z, doub
         return 0;
     case ORC_SBEND:   /* exact bend, Eq. (10) */
         return sbend_map(r, z, e->angle / e->L, e->eta, ds);
+    case ORC_TEAPOT:  /* curved drift - kick - curved drift, Sec. 3.6 in the symmetric form of Eq. (27) */
+        if (curved_drift(r, z, e->angle / e->L, 0.5 * ds)) return 1;
+        teapot_kick(z, e->angle / e->L, e->eta, ds);
+        return curved_drift(r, z, e->angle / e->L, 0.5 * ds);
     case ORC_SOLENOID: /* exact body map, Eq. (solenoid) */
         return solenoid_map(r, z, e->k1, ds);
     case ORC_RBEND: { /* exact body map in the magnet's Cartesian frame, Eq. (rbend) */
@@ -414,7 +465,7 @@ static int omega(const orc_ref* r, const orc_element* e, const orc_orbit* z, rea
     real b[3] = {0.0, 0.0, 0.0};
     double h = 0.0;
     real u[3] = {z->Px / P, z->Py / P, Ps / P};
-    if (e->type == ORC_SBEND) {
+    if (e->type == ORC_SBEND || e->type == ORC_TEAPOT) {
         h = e->angle / e->L;
         b[1] = e->eta * h;             /* b1/(B rho) = eta h, Eq. (9) */
     } else if (e->type == ORC_RBEND) {
@@ -518,6 +569,71 @@ static void romberg_element_rotation(const real (*Om)[3], int N, double ds, int 
     for (int c = 0; c < 4; ++c) Q[c] = Tab[K][K][c] / n;
 }
 
+/* Half of one slice of length ds for the midpoint schemes: part 0 takes the
+ * state from the slice entrance to its middle, part 1 from the middle to the
+ * exit.  ORC_MID_KICK splits the central kick of the second-order drift-kick
+ * (Sec. 3.4, 3.6) and matrix-kick (Eq. (27)) slices in two (the kicks of a
+ * slice commute, so the orbit map is that of the slice); every other map, and
+ * every map under ORC_MID_HALF, is run over half the slice. */
+static int slice_half(const orc_ref* r, const orc_element* e, orc_orbit* z, double ds, int scheme, int part) {
+    if (scheme == ORC_MID_KICK && e->split_order != 4) {
+        double hd = 0.5 * ds;
+        switch (e->type) {
+        case ORC_MULT:
+            if (part == 0) {
+                if (drift(r, z, hd)) return 1;
+                mult_kick(z, e->k1, e->k2, hd);
+                return 0;
+            }
+            mult_kick(z, e->k1, e->k2, hd);
+            return drift(r, z, hd);
+        case ORC_TEAPOT: {
+            double h = e->angle / e->L;
+            if (part == 0) {
+                if (curved_drift(r, z, h, hd)) return 1;
+                teapot_kick(z, h, e->eta, hd);
+                return 0;
+            }
+            teapot_kick(z, h, e->eta, hd);
+            return curved_drift(r, z, h, hd);
+        }
+        case ORC_QUAD_MK:
+            if (part == 0) {
+                quad_linear(r, z, e->k1, hd);
+                return quad_nonlinear(r, z, hd);
+            }
+            if (quad_nonlinear(r, z, hd)) return 1;
+            quad_linear(r, z, e->k1, hd);
+            return 0;
+        default:
+            break;
+        }
+    }
+    return slice_map(r, e, z, 0.5 * ds);
+}
+
+/* Piece-wise constant spin integration with Omega at the middle of each slice
+ * (Sec. 4.1, Eq. (37)): the rotation of slice i is R(ds Omega(s_i + ds/2)),
+ * later slices on the left.  The orbit is advanced through the N slices on
+ * the way.  The product is normalised once (it differs from a unit
+ * quaternion by rounding only).  Returns 1 if the particle is lost. */
+static int midpoint_rotation(const orc_ref* r, const orc_element* e, orc_orbit* z, int N, double ds,
+                             int scheme, real Q[4]) {
+    Q[0] = 1.0; Q[1] = Q[2] = Q[3] = 0.0;
+    for (int i = 0; i < N; ++i) {
+        if (slice_half(r, e, z, ds, scheme, 0)) return 1;
+        real Om[3], q[4];
+        if (omega(r, e, z, Om)) return 1;
+        real w[3] = {ds * Om[0], ds * Om[1], ds * Om[2]};
+        quat_from_rotation_vector(w, q);
+        qmul(q, Q, Q);
+        if (slice_half(r, e, z, ds, scheme, 1)) return 1;
+    }
+    real n = sqrt(Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3]);
+    for (int c = 0; c < 4; ++c) Q[c] = Q[c] / n;
+    return 0;
+}
+
 /* Net spin rotation vector of a thin-pancake solenoid fringe, Eq. (solFringe):
  *   w = sign (b0/2)/(B rho Ps') [ (1 + G gamma)(X, Y, 0)
  *                                 - G (gamma - 1)(X Px + Y Py)/P^2 m gamma V' ],
@@ -556,7 +672,8 @@ static int fringe_rotate(const orc_ref* r, double ks, int sign, const orc_orbit*
  * Returns the number of pairs. */
 static int normal_multipoles(const orc_element* e, int m[2], double bm[2]) {
     switch (e->type) {
-    case ORC_SBEND: m[0] = 1; bm[0] = e->eta * e->angle / e->L; return 1;
+    case ORC_SBEND:
+    case ORC_TEAPOT: m[0] = 1; bm[0] = e->eta * e->angle / e->L; return 1;
     case ORC_QUAD_MK: m[0] = 2; bm[0] = e->k1; return 1;
     case ORC_MULT: m[0] = 2; bm[0] = e->k1; m[1] = 3; bm[1] = 0.5 * e->k2; return 2;
     default: return 0;
@@ -647,21 +764,28 @@ static int track_rbend(const orc_ref* r, const orc_element* e, orc_orbit* z, rea
     if (rbend_fringe_orbit(r, z, b, +1)) return 1;
     int N = e->n_slices;
     double ds = e->L / N;
-    real (*Om)[3] = (real (*)[3])malloc(sizeof(real[3]) * (size_t)(N + 1));
-    if (!Om) return 2;
-    int lost = omega(r, e, z, Om[0]);
-    for (int i = 1; i <= N && !lost; ++i) {
-        lost = rbend_body(r, z, b, ds);
-        if (!lost) lost = omega(r, e, z, Om[i]);
-    }
-    if (!lost) {
+    if (K < 0) {
         real Q[4];
-        romberg_element_rotation((const real(*)[3])Om, N, ds, K, Q, levels_out);
+        if (midpoint_rotation(r, e, z, N, ds, K, Q)) return 1;
         rotate_spin(Q, S);
         if (Q_out) memcpy(Q_out, Q, sizeof(Q));
+    } else {
+        real (*Om)[3] = (real (*)[3])malloc(sizeof(real[3]) * (size_t)(N + 1));
+        if (!Om) return 2;
+        int lost = omega(r, e, z, Om[0]);
+        for (int i = 1; i <= N && !lost; ++i) {
+            lost = rbend_body(r, z, b, ds);
+            if (!lost) lost = omega(r, e, z, Om[i]);
+        }
+        if (!lost) {
+            real Q[4];
+            romberg_element_rotation((const real(*)[3])Om, N, ds, K, Q, levels_out);
+            rotate_spin(Q, S);
+            if (Q_out) memcpy(Q_out, Q, sizeof(Q));
+        }
+        free(Om);
+        if (lost) return 1;
     }
-    free(Om);
-    if (lost) return 1;
     if (e->fringe) {
         real w[3], q[4];
         rbend_fringe_spin(r, b, -1, z, w);
@@ -696,6 +820,13 @@ static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, r
     double ds = e->L / N;
     /* entrance fringe kick (orbit unchanged across the fringe) */
     if (element_fringe(r, e, +1, z, S)) return 1;
+    if (K < 0) {
+        real Q[4];
+        if (midpoint_rotation(r, e, z, N, ds, K, Q)) return 1;
+        rotate_spin(Q, S);
+        if (Q_out) memcpy(Q_out, Q, sizeof(Q));
+        return element_fringe(r, e, -1, z, S);
+    }
     real (*Om)[3] = (real (*)[3])malloc(sizeof(real[3]) * (size_t)(N + 1));
     if (!Om) return 2;
     int lost = omega(r, e, z, Om[0]);
@@ -722,25 +853,30 @@ static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, r
 int orc_real_size(void) { return (int)sizeof(real); }
 
 /* Validate a lattice as the tracker reads it: Romberg order k needs every
- * spin-carrying element's slice count divisible by 2^k. */
+ * spin-carrying element's slice count divisible by 2^k; the midpoint schemes
+ * (K = ORC_MID_HALF, ORC_MID_KICK) take any slice count but not the
+ * fourth-order slice maps. */
 int orc_check_lattice(const orc_element* els, int n_el, int K) {
-    if (K < 0 || K > ORC_MAX_ORDER) return -1;
+    if (K < ORC_MID_KICK || K > ORC_MAX_ORDER) return -1;
+    int div = K > 0 ? 1 << K : 1;
     for (int i = 0; i < n_el; ++i) {
         const orc_element* e = &els[i];
-        if (e->type < 0 || e->type > ORC_RBEND) return -1;
+        if (e->type < 0 || e->type > ORC_TEAPOT) return -1;
         if (e->type == ORC_MULT || e->type == ORC_QUAD_MK || e->type == ORC_SBEND || e->type == ORC_SOLENOID ||
-            e->type == ORC_RBEND) {
-            if (e->n_slices < 1 || (e->n_slices % (1 << K)) != 0) return -1;
+            e->type == ORC_RBEND || e->type == ORC_TEAPOT) {
+            if (e->n_slices < 1 || (e->n_slices % div) != 0) return -1;
             if (e->L == 0.0) return -1;
         }
         if (e->type == ORC_SBEND && (e->angle == 0.0 || e->eta == 0.0)) return -1;
+        if (e->type == ORC_TEAPOT && (e->angle == 0.0 || !(fabs(e->angle / e->n_slices) < 1.0))) return -1;
+        if (K < 0 && e->split_order == 4) return -1;
         if (e->type == ORC_RBEND && (e->angle == 0.0 || e->eta == 0.0 || !(e->L > 0.0) ||
                                      fabs(0.5 * e->angle + e->e1) >= 1.5 || fabs(-0.5 * e->angle + e->e1) >= 1.5))
             return -1;
         if (e->fringe != 0 && e->fringe != 1) return -1;
         if (e->fringe && (e->type == ORC_DRIFT || e->type == ORC_SNAKE)) return -1;
         if (e->split_order != 0 && e->split_order != 2 && e->split_order != 4) return -1;
-        if (e->split_order == 4 && e->type != ORC_MULT && e->type != ORC_QUAD_MK) return -1;
+        if (e->split_order == 4 && e->type != ORC_MULT && e->type != ORC_QUAD_MK && e->type != ORC_TEAPOT) return -1;
     }
     return 0;
 }
@@ -822,7 +958,8 @@ int orc_orbit_map(const orc_element* e, double G, double Ggamma0, real* z6) {
  *         3 quadrupole nonlinear flow H_qNL, 4 sector bend, 5 solenoid body
  *         (k1 = b0/(B rho)), 6 rectangular-bend body (k1 = b1/(B rho)),
  *         7 dynamic rotation by the angle s, 8 rectangular-bend fringe orbit map
- *         (k1 = b1/(B rho), sign of k2 = entrance/exit). */
+ *         (k1 = b1/(B rho), sign of k2 = entrance/exit), 9 TEAPOT curved drift,
+ *         10 TEAPOT kick of a sector bend (h, eta). */
 int orc_subflow(int which, double G, double Ggamma0, real* z6, double s, double k1, double k2,
                 double h, double eta) {
     orc_ref r = make_ref(G, Ggamma0);
@@ -838,6 +975,8 @@ int orc_subflow(int which, double G, double Ggamma0, real* z6, double s, double 
     case 6: rc = rbend_body(&r, &o, k1, s); break;                 /* k1 = b1/(B rho) */
     case 7: rc = rbend_rotation(&r, &o, s); break;                 /* s = phi */
     case 8: rc = rbend_fringe_orbit(&r, &o, k1, k2 > 0.0 ? 1 : -1); break;   /* k1 = b1/(B rho), k2 = sign */
+    case 9: rc = curved_drift(&r, &o, h, s); break;                /* TEAPOT drift, curvature h */
+    case 10: teapot_kick(&o, h, eta, s); break;                    /* TEAPOT kick, curvature h, eta */
     default: return -1;
     }
     z6[0] = o.X; z6[1] = o.Px; z6[2] = o.Y; z6[3] = o.Py; z6[4] = o.T; z6[5] = o.Pt;
@@ -871,7 +1010,7 @@ int orc_element_fringe(const orc_element* e, int sign, double G, double Ggamma0,
         rbend_fringe_spin(&r, b, sign, &o, out3);
         return 0;
     }
-    if (e->type != ORC_MULT && e->type != ORC_QUAD_MK && e->type != ORC_SBEND) return -1;
+    if (e->type != ORC_MULT && e->type != ORC_QUAD_MK && e->type != ORC_SBEND && e->type != ORC_TEAPOT) return -1;
     multipole_fringe(&r, e, sign, &o, out3);
     return 0;
 }

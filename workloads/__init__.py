@@ -13,6 +13,8 @@ b/(B rho), Sec. 2.1 and Sec. 3):
                | "quad_mk" (matrix-kick quadrupole, Sec. 3.3)
                | "sbend" (exact bend-kick sector bend, Sec. 3.1)
                | "snake" (thin spin rotator, Sec. 5)
+               | "teapot" (sector bend integrated by the TEAPOT drift-kick
+                 split, Sec. 3.6: curved drift, kick, curved drift)
     L          length
     n_slices   number of integration slices (spin-carrying elements)
     k1         quadrupole gradient b2/(B rho)            [m^-2]
@@ -21,9 +23,10 @@ b/(B rho), Sec. 2.1 and Sec. 3):
     eta        field ratio eta = b1/(h B rho), Eq. (9)
     snake_phi  snake axis angle from the longitudinal axis, in the x-s plane
     snake_mu   snake rotation angle
-    fringe     1: thin fringe spin kicks at both ends of a mult, quad_mk or
-               sbend (Sec. 4.5, Eq. (skfringe)); 0: hard edges without kicks
-    split_order  orbit slice map of a mult or quad_mk: 2 = the symmetric split
+    fringe     1: thin fringe spin kicks at both ends of a mult, quad_mk,
+               sbend or teapot (Sec. 4.5, Eq. (skfringe)); 0: hard edges
+               without kicks
+    split_order  orbit slice map of a mult, quad_mk or teapot: 2 = the symmetric split
                of Eq. (27), 4 = its fourth-order Yoshida composition (Sec. 3.3)
     e1         rbend: the beam meets the entrance face at angle/2 + e1 and the
                exit face at -angle/2 + e1 (0: symmetric rectangular bend)
@@ -50,8 +53,8 @@ import numpy as np
 
 G_PROTON = 1.7928
 
-ELEMENT_TYPES = ("drift", "mult", "quad_mk", "sbend", "snake", "solenoid", "rbend")
-SPIN_TYPES = ("mult", "quad_mk", "sbend", "solenoid", "rbend")
+ELEMENT_TYPES = ("drift", "mult", "quad_mk", "sbend", "snake", "solenoid", "rbend", "teapot")
+SPIN_TYPES = ("mult", "quad_mk", "sbend", "solenoid", "rbend", "teapot")
 
 
 def element(type: str, L: float = 0.0, n_slices: int = 1, k1: float = 0.0,
@@ -124,7 +127,7 @@ def with_fringes(ring: Dict, on: int = 1) -> Dict:
     """Copy of `ring` with the thin fringe spin kicks of Sec. 4.5 switched on
     (or off) at both ends of every multipole, quadrupole and sector bend."""
     out = dict(ring)
-    out["elements"] = [dict(e, fringe=int(on)) if e["type"] in ("mult", "quad_mk", "sbend") else dict(e)
+    out["elements"] = [dict(e, fringe=int(on)) if e["type"] in ("mult", "quad_mk", "sbend", "teapot") else dict(e)
                        for e in ring["elements"]]
     out["name"] = ring["name"] + ("_fringes" if on else "")
     return out
@@ -137,6 +140,27 @@ def with_split_order(ring: Dict, order: int) -> Dict:
     out["elements"] = [dict(e, split_order=int(order)) if e["type"] in ("mult", "quad_mk") else dict(e)
                        for e in ring["elements"]]
     out["name"] = ring["name"] + (f"_split{order}" if order != 2 else "")
+    return out
+
+
+def drift_kick_ring(ring: Dict) -> Dict:
+    """Copy of `ring` integrated by drift-kick splits only (the integrators the
+    paper compares against, Sec. 3.4, 3.6, 5.3): matrix-kick quadrupoles
+    become drift-kick-drift multipoles of the same gradient and exact sector
+    bends become TEAPOT bends of the same angle and field."""
+    conv = {"quad_mk": "mult", "sbend": "teapot"}
+    out = dict(ring)
+    out["elements"] = [dict(e, type=conv.get(e["type"], e["type"])) for e in ring["elements"]]
+    out["name"] = ring["name"] + "_drift_kick"
+    return out
+
+
+def with_slices(ring: Dict, n_slices: int) -> Dict:
+    """Copy of `ring` with every spin-carrying element cut into n_slices
+    slices (the paper's n_b)."""
+    out = dict(ring)
+    out["elements"] = [dict(e, n_slices=int(n_slices)) if e["type"] in SPIN_TYPES else dict(e)
+                       for e in ring["elements"]]
     return out
 
 
