@@ -439,6 +439,65 @@ def variant_fp64_configs(st, torch, npart, fp64_peak, seed):
     return {"workload": f"108-cell RHIC-like ring, {npart} particles, 1 turn per launch", "configs": out}
 
 
+def _time_turn(st, torch, ring, z, S, spin_order, flush, stream):
+    """Seconds per turn of the FP64 tracker (one turn per launch, L2 flushed,
+    mean of two launches after one warm-up)."""
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, z.shape[1], "fp64", stream=stream.cuda_stream)
+    tr.set_launch(block_threads=128, turns_per_launch=1)
+    tr.upload(z, S)
+    tr.track(1, spin_order)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            tr.track(1, spin_order)
+            b.record(stream)
+    torch.cuda.synchronize()
+    tr.close()
+    lat.close()
+    return sum(a.elapsed_time(b) for a, b in ev) * 1e-3 / len(ev)
+
+
+def variant_drift_kick(st, torch, npart, seed, ggamma=45.5, dS_particles=4096):
+    """The paper's comparison of integrators (Sec. 3.6, 5.3) on the RHIC-like
+    ring: FP64 pass rates of the drift-kick version (TEAPOT bends,
+    drift-kick-drift quadrupoles) with two Romberg iterations and with the
+    split-kick midpoint scheme, of the bend-kick / matrix-kick ring with the
+    half-slice midpoint scheme, and the one-turn mean spin error Delta S of
+    each midpoint scheme without Romberg steps against bend-kick /
+    matrix-kick tracking with 256 slices and three Romberg iterations (all
+    tracked here on the GPU)."""
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    base = W.workload(WORKLOAD, spin_order=2, Ggamma0=ggamma)["ring"]
+    dk = W.drift_kick_ring(base)
+    n_el = len(base["elements"])
+    z, S = W.gaussian_particles(npart, ggamma, seed=seed)
+    rates = {}
+    for name, ring, K in (("drift_kick_romberg2", dk, 2), ("drift_kick_mid_kick", dk, st.ST_SPIN_MID_KICK),
+                          ("bend_kick_mid_half", base, st.ST_SPIN_MID_HALF), ("bend_kick_romberg2", base, 2)):
+        rates[name] = npart * n_el / _time_turn(st, torch, ring, z, S, K, flush, stream)
+    zs, Ss = W.gaussian_particles(dS_particles, ggamma, seed=seed + 1)
+    _, Sref, _ = st.track(W.with_slices(base, 256), zs, Ss, 1, 3)
+    dS = {}
+    for nb in (4, 16, 64):
+        row = {}
+        for name, ring, K in (("drift_kick_mid_kick", dk, st.ST_SPIN_MID_KICK),
+                              ("drift_kick_mid_half", dk, st.ST_SPIN_MID_HALF),
+                              ("bend_kick_mid_half", base, st.ST_SPIN_MID_HALF)):
+            _, S1, _ = st.track(W.with_slices(ring, nb), zs, Ss, 1, K)
+            row[name] = float(np.linalg.norm(S1 - Sref, axis=0).mean())
+        row["drift_kick_over_bend_kick"] = row["drift_kick_mid_kick"] / row["bend_kick_mid_half"]
+        dS[f"n_b={nb}"] = row
+    return {"workload": f"108-cell RHIC-like ring at G gamma0 = {ggamma}, {npart} particles, 1 turn per launch",
+            "passes_per_s": rates, "one_turn_dS": dS,
+            "dS_sample": f"{dS_particles} particles, reference: bend-kick/matrix-kick, 256 slices, 3 Romberg "
+                         "iterations"}
+
+
 def element_type_breakdown(st, torch, ring, npart, seed, K, ggamma, min_elements=200):
     """Pass rate of the FP64 tracker per element type: for each type in the
     ring, a ring made of that type's elements only (in ring order, repeated
@@ -605,6 +664,7 @@ def main():
     variants = None
     if not args.no_variants and world == 1:
         variants = {"fp64_configs": variant_fp64_configs(st, torch, npart, fp64_peak, w["seed"]),
+                    "drift_kick": variant_drift_kick(st, torch, npart, w["seed"]),
                     "mixed": variant_mixed(st, torch, args, value, fp32_peak),
                     "batched": variant_batched(st, torch, args),
                     "surrogate": variant_surrogate(st, torch, args, value)}

@@ -14,7 +14,10 @@
  *     integrated per element by trapezoid-weighted edge rotations composed as
  *     unit quaternions, later slices on the left (Sec. 4.1, Eq. (37)), at the
  *     2^k sub-sampled step sizes of Eq. (38), extrapolated with the Romberg
- *     table of Eq. (39) and normalised per element (Sec. 4.3).
+ *     table of Eq. (39) and normalised per element (Sec. 4.3); or, for the
+ *     comparisons of Sec. 5.3, piece-wise constant rotations with the
+ *     precession vector at the middle of each slice (ST_SPIN_MID_HALF,
+ *     ST_SPIN_MID_KICK below).
  *
  * Conventions of this library (the paper leaves them open):
  *   - quaternions are Hamilton, scalar first; the spin is rotated actively;
@@ -74,6 +77,31 @@ extern "C" {
                            of Eqs. (Xoffset), (Toffset); fringe = 1 adds the spin kicks
                            of Eq. (skfringeRB).  FP64 only.                           */
 
+#define ST_TEAPOT   7   /* sector bend (h = angle/L, field ratio eta as ST_SBEND) integrated
+                           by the TEAPOT drift-kick split, Sec. 3.6, Eqs. (DKsplit),
+                           (teapotD): each slice is a curved drift of ds/2 (the flow of
+                           -(1 + hX) Ps + Pt/beta0, including the reference time s/beta0),
+                           the kick of the bend's uniform field over ds (dPx/ds =
+                           -eta h (1 + hX), Eq. (sbendA)) and another curved drift;
+                           split_order 4 composes it to fourth order.  eta = 0 is a
+                           field-free curved frame.  The paper's comparison integrator:
+                           less accurate than ST_SBEND at any slice count.  FP64 only. */
+
+/* ---- spin integration schemes (spin_order arguments) ------------------ */
+/* spin_order 0..4 is the number of Romberg iterations over slice-edge
+ * samples.  Two negative values select the piece-wise constant rotation
+ * R(ds Omega) per slice with Omega at the slice middle (Sec. 4.1, Eq. (37);
+ * Sec. 5.3, Fig. oneTurnSpinErrs), FP64 contexts only, any n_slices, no
+ * fourth-order slice maps (ST_EINVAL otherwise):                             */
+#define ST_SPIN_MID_HALF  -1   /* each slice traversed as two half-slices of its own
+                                  map, the rotation between them ("half-DKD, spin,
+                                  half-DKD")                                        */
+#define ST_SPIN_MID_KICK  -2   /* drift-kick (ST_MULT, ST_TEAPOT) and matrix-kick
+                                  (ST_QUAD_MK) slices keep their map and rotate the
+                                  spin between the two halves of the central kick
+                                  ("half-drift, half-kick, spin, half-kick,
+                                  half-drift"); exact maps as ST_SPIN_MID_HALF       */
+
 /* ---- precision of a tracking context ---------------------------------- */
 #define ST_FP64   0   /* all arithmetic in IEEE double                                 */
 #define ST_MIXED  1   /* FP32 slice arithmetic with compensated coordinates, FP64
@@ -85,8 +113,8 @@ typedef struct st_ctx st_ctx;           /* opaque; particle state on the device 
 /* One beamline element.  Units: metres, radians; k1 = b2/(B rho) [m^-2],
  * k2 = B''/(B rho) [m^-3] (MAD convention).  n_slices is the number of
  * integration slices of a spin-carrying element (ST_MULT, ST_QUAD_MK,
- * ST_SBEND, ST_SOLENOID, ST_RBEND) and must be a multiple of 2^spin_order at
- * st_track time. */
+ * ST_SBEND, ST_SOLENOID, ST_RBEND, ST_TEAPOT) and must be a multiple of
+ * 2^spin_order at st_track time (Romberg orders). */
 typedef struct {
     int32_t type;
     int32_t n_slices;
@@ -97,8 +125,8 @@ typedef struct {
     double eta;
     double snake_phi;
     double snake_mu;
-    int32_t fringe;    /* 1: thin fringe spin kicks at both ends of an ST_MULT, ST_QUAD_MK
-                        * or ST_SBEND (Sec. 4.5, Eq. (skfringe)), or of an ST_RBEND
+    int32_t fringe;    /* 1: thin fringe spin kicks at both ends of an ST_MULT, ST_QUAD_MK,
+                        * ST_SBEND or ST_TEAPOT (Sec. 4.5, Eq. (skfringe)), or of an ST_RBEND
                         * (Eq. (skfringeRB), see ST_RBEND); for the others: a rotation about the
                         * longitudinal axis by -(+-)(1 + G) sum_m (b_m/(B rho)) Im (X + iY)^m / m,
                         * + at the entrance, - at the exit, with b_1/(B rho) = eta h,
@@ -106,9 +134,9 @@ typedef struct {
                         * Solenoids always carry their Sec. 4.4 fringe kicks; drifts and
                         * snakes must have 0 (ST_EINVAL otherwise).  FP64 contexts only
                         * when 1. */
-    int32_t split_order; /* orbit slice map of an ST_MULT or ST_QUAD_MK: 0 or 2 = the
-                          * symmetric second-order split of Eq. (27) (drift-kick-drift,
-                          * matrix-kick); 4 = Yoshida's fourth-order composition
+    int32_t split_order; /* orbit slice map of an ST_MULT, ST_QUAD_MK or ST_TEAPOT: 0 or
+                          * 2 = the symmetric second-order split of Eq. (27) (drift-kick-
+                          * drift, matrix-kick, TEAPOT); 4 = Yoshida's fourth-order composition
                           * S2(x1 ds) S2(x0 ds) S2(x1 ds), x1 = 1/(2 - 2^(1/3)),
                           * x0 = 1 - 2 x1 (Sec. 3.3's higher-order versions).  Spin is
                           * still sampled at the slice edges.  Other types: 0 or 2
@@ -152,10 +180,12 @@ int st_particles_upload(st_ctx* ctx, const double* z_soa, const double* spin_soa
                         int32_t src_is_device);
 
 /* Track every particle for n_turns >= 0 turns with Romberg order spin_order
- * (0..4).  Asynchronous on the context stream.  Errors: ST_ESTATE before the
- * first upload, ST_EINVAL for n_turns < 0, spin_order outside 0..4 or a
- * spin-carrying element whose n_slices is not a multiple of 2^spin_order,
- * ST_ECUDA on a launch failure. */
+ * (0..4) or a midpoint scheme (ST_SPIN_MID_HALF, ST_SPIN_MID_KICK; FP64
+ * contexts).  Asynchronous on the context stream.  Errors: ST_ESTATE before
+ * the first upload, ST_EINVAL for n_turns < 0, spin_order outside -2..4, a
+ * spin-carrying element whose n_slices is not a multiple of 2^spin_order, a
+ * midpoint scheme on a mixed-precision context or with fourth-order slice
+ * maps, ST_ECUDA on a launch failure. */
 int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order);
 
 /* Track the orbits only (the maps of st_track without the spin step; spins

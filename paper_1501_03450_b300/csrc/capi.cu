@@ -27,7 +27,32 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 bool is_spin_type(int t) {
-    return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND || t == ST_SOLENOID || t == ST_RBEND;
+    return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND || t == ST_SOLENOID || t == ST_RBEND || t == ST_TEAPOT;
+}
+
+// Field checks of one element (every entry point that takes elements):
+// nullptr if valid, else what is wrong.
+const char* element_error(const st_element& e) {
+    if (e.type < ST_DRIFT || e.type > ST_TEAPOT) return "unknown type";
+    if (is_spin_type(e.type) && (!(e.L > 0.0) || e.n_slices < 1 || e.n_slices > 4096))
+        return "spin-carrying element needs L > 0 and 1 <= n_slices <= 4096";
+    if (e.fringe != 0 && e.fringe != 1) return "fringe must be 0 or 1";
+    if (e.fringe && (e.type == ST_DRIFT || e.type == ST_SNAKE))
+        return "fringe kicks need a multipole, quadrupole, bend or solenoid";
+    if ((e.split_order != 0 && e.split_order != 2 && e.split_order != 4) ||
+        (e.split_order == 4 && e.type != ST_MULT && e.type != ST_QUAD_MK && e.type != ST_TEAPOT))
+        return "split_order must be 0 or 2, or 4 for a multipole, matrix-kick quadrupole or TEAPOT bend";
+    if (e.type == ST_DRIFT && !(e.L >= 0.0)) return "drift needs L >= 0";
+    if (e.type == ST_RBEND &&
+        (e.angle == 0.0 || e.eta == 0.0 || !std::isfinite(e.e1) || !(std::fabs(0.5 * e.angle + e.e1) < 1.5) ||
+         !(std::fabs(-0.5 * e.angle + e.e1) < 1.5)))
+        return "rectangular bend needs angle != 0, eta != 0 and face angles below 1.5 rad";
+    if (e.type == ST_SBEND && (e.angle == 0.0 || e.eta == 0.0 || !std::isfinite(e.angle / e.L)))
+        return "sector bend needs angle != 0 and eta != 0";
+    if (e.type == ST_TEAPOT && (e.angle == 0.0 || !std::isfinite(e.eta) || !std::isfinite(e.angle / e.L) ||
+                                !(std::fabs(e.angle / e.n_slices) < 1.0)))
+        return "TEAPOT bend needs angle != 0 and less than 1 rad per slice";
+    return nullptr;
 }
 
 // Precompute the per-element constants the kernels use (all in FP64).
@@ -37,7 +62,8 @@ DevElem pack_element(const st_element& e) {
     d.type = e.type;
     d.n_slices = (int16_t)(is_spin_type(e.type) ? e.n_slices : 1);
     d.flags = (e.fringe && e.type != ST_SOLENOID) ? ST_ELEM_FRINGE : 0;
-    if (e.split_order == 4 && (e.type == ST_MULT || e.type == ST_QUAD_MK)) d.flags |= ST_ELEM_ORDER4;
+    if (e.split_order == 4 && (e.type == ST_MULT || e.type == ST_QUAD_MK || e.type == ST_TEAPOT))
+        d.flags |= ST_ELEM_ORDER4;
     switch (e.type) {
     case ST_DRIFT:
         d.ds = e.L;
@@ -51,6 +77,15 @@ DevElem pack_element(const st_element& e) {
         d.ds = e.L / e.n_slices;
         d.a[0] = e.k1;
         d.a[1] = std::fabs(e.k1);
+        break;
+    case ST_TEAPOT:
+        // curvature and field ratio; the second-order slice's curved drift
+        // and kick lengths in the places of the fourth-order sub-steps
+        d.ds = e.L / e.n_slices;
+        d.a[0] = e.angle / e.L;
+        d.a[1] = e.eta;
+        d.a[2] = 0.5 * d.ds;
+        d.a[4] = d.ds;
         break;
     default:
         break;
@@ -135,40 +170,8 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
         return ST_EINVAL;
     }
     for (int i = 0; i < n; ++i) {
-        const st_element& e = elems[i];
-        if (e.type < ST_DRIFT || e.type > ST_RBEND) {
-            set_error("element %d: unknown type %d", i, e.type);
-            return ST_EINVAL;
-        }
-        if (is_spin_type(e.type) && (!(e.L > 0.0) || e.n_slices < 1 || e.n_slices > 4096)) {
-            set_error("element %d: spin-carrying element needs L > 0 and 1 <= n_slices <= 4096", i);
-            return ST_EINVAL;
-        }
-        if (e.fringe != 0 && e.fringe != 1) {
-            set_error("element %d: fringe must be 0 or 1", i);
-            return ST_EINVAL;
-        }
-        if (e.fringe && (e.type == ST_DRIFT || e.type == ST_SNAKE)) {
-            set_error("element %d: fringe kicks need a multipole, quadrupole, bend or solenoid", i);
-            return ST_EINVAL;
-        }
-        if ((e.split_order != 0 && e.split_order != 2 && e.split_order != 4) ||
-            (e.split_order == 4 && e.type != ST_MULT && e.type != ST_QUAD_MK)) {
-            set_error("element %d: split_order must be 0 or 2, or 4 for a multipole or matrix-kick quadrupole", i);
-            return ST_EINVAL;
-        }
-        if (e.type == ST_DRIFT && !(e.L >= 0.0)) {
-            set_error("element %d: drift needs L >= 0", i);
-            return ST_EINVAL;
-        }
-        if (e.type == ST_RBEND &&
-            (e.angle == 0.0 || e.eta == 0.0 || !std::isfinite(e.e1) || !(std::fabs(0.5 * e.angle + e.e1) < 1.5) ||
-             !(std::fabs(-0.5 * e.angle + e.e1) < 1.5))) {
-            set_error("element %d: rectangular bend needs angle != 0, eta != 0 and face angles below 1.5 rad", i);
-            return ST_EINVAL;
-        }
-        if (e.type == ST_SBEND && (e.angle == 0.0 || e.eta == 0.0 || !std::isfinite(e.angle / e.L))) {
-            set_error("element %d: sector bend needs angle != 0 and eta != 0", i);
+        if (const char* why = element_error(elems[i])) {
+            set_error("element %d: %s", i, why);
             return ST_EINVAL;
         }
     }
@@ -199,8 +202,9 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
         }
         seq[i] = (uint16_t)idx;
         if (d.type == ST_SOLENOID || d.flags) L.fp64_only = true;
-        if ((d.flags & ST_ELEM_ORDER4) || d.type == ST_RBEND) L.has_ext = true;
-        if (d.type == ST_RBEND) L.fp64_only = true;
+        if ((d.flags & ST_ELEM_ORDER4) || d.type == ST_RBEND || d.type == ST_TEAPOT) L.has_ext = true;
+        if (d.type == ST_RBEND || d.type == ST_TEAPOT) L.fp64_only = true;
+        if (d.flags & ST_ELEM_ORDER4) L.has_order4 = true;
         if (is_spin_type(d.type)) {
             max_slices = std::max(max_slices, (int)d.n_slices);
             int p = 0;
@@ -422,6 +426,30 @@ int st_lost_upload(st_ctx* ctx, const uint8_t* lost, int32_t src_is_device) {
     return ST_OK;
 }
 
+// spin_order: a Romberg order 0..4 that every spin-carrying element's slice
+// count admits, or a midpoint scheme on an FP64 context without fourth-order
+// slice maps.
+static bool spin_scheme_ok(const st_ctx* ctx, int spin_order, const char* who) {
+    const LatticeImpl& L = ctx->lat->impl;
+    if (spin_order < ST_SPIN_MID_KICK || spin_order > 4) {
+        set_error("%s: spin_order must be a Romberg order 0..4 or a midpoint scheme (-1, -2)", who);
+        return false;
+    }
+    if (spin_order < 0) {
+        if (ctx->precision != ST_FP64 || L.has_order4) {
+            set_error("%s: the midpoint schemes need an FP64 context and second-order slice maps", who);
+            return false;
+        }
+        return true;
+    }
+    if (spin_order > L.min_spin_slices_pow2) {
+        set_error("%s: spin_order %d needs every spin-carrying element's n_slices divisible by %d", who,
+                  spin_order, 1 << spin_order);
+        return false;
+    }
+    return true;
+}
+
 int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order) {
     if (!ctx) {
         set_error("st_track: null context");
@@ -431,15 +459,11 @@ int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order) {
         set_error("st_track: no particles uploaded");
         return ST_ESTATE;
     }
-    if (n_turns < 0 || spin_order < 0 || spin_order > 4) {
-        set_error("st_track: need n_turns >= 0 and 0 <= spin_order <= 4");
+    if (n_turns < 0) {
+        set_error("st_track: need n_turns >= 0");
         return ST_EINVAL;
     }
-    if (spin_order > ctx->lat->impl.min_spin_slices_pow2) {
-        set_error("st_track: spin_order %d needs every spin-carrying element's n_slices divisible by %d",
-                  spin_order, 1 << spin_order);
-        return ST_EINVAL;
-    }
+    if (!spin_scheme_ok(ctx, spin_order, "st_track")) return ST_EINVAL;
     if (n_turns == 0) return ST_OK;
     if (ctx->precision == ST_FP64) return launch_track_fp64(ctx, n_turns, spin_order);
     return launch_track_mixed(ctx, n_turns, spin_order);
@@ -471,11 +495,11 @@ int st_track_one_turn_map(st_ctx* ctx, int32_t spin_order, const double* q_ref, 
         set_error("st_track_one_turn_map: no particles uploaded");
         return ST_ESTATE;
     }
-    if (ctx->precision != ST_FP64 || spin_order < 0 || spin_order > 4 ||
-        spin_order > ctx->lat->impl.min_spin_slices_pow2) {
-        set_error("st_track_one_turn_map: needs an FP64 context and a valid spin_order");
+    if (ctx->precision != ST_FP64) {
+        set_error("st_track_one_turn_map: needs an FP64 context");
         return ST_EINVAL;
     }
+    if (!spin_scheme_ok(ctx, spin_order, "st_track_one_turn_map")) return ST_EINVAL;
     return launch_track_turn_map(ctx, spin_order, q_out, q_ref);
 }
 
@@ -488,11 +512,11 @@ int st_track_average(st_ctx* ctx, int32_t n_turns, int32_t spin_order, double* s
         set_error("st_track_average: no particles uploaded");
         return ST_ESTATE;
     }
-    if (ctx->precision != ST_FP64 || n_turns < 0 || spin_order < 0 || spin_order > 4 ||
-        spin_order > ctx->lat->impl.min_spin_slices_pow2) {
-        set_error("st_track_average: needs an FP64 context, n_turns >= 0 and a valid spin_order");
+    if (ctx->precision != ST_FP64 || n_turns < 0) {
+        set_error("st_track_average: needs an FP64 context and n_turns >= 0");
         return ST_EINVAL;
     }
+    if (!spin_scheme_ok(ctx, spin_order, "st_track_average")) return ST_EINVAL;
     if (n_turns == 0) return ST_OK;
     return launch_track_average(ctx, n_turns, spin_order, spin_sum);
 }

@@ -78,16 +78,12 @@ extern "C" int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, c
     int n_unique = 0;
     for (int i = 0; i < n_elems; ++i) {
         const st_element& e = elems[i];
-        if (e.type < ST_DRIFT || e.type > ST_RBEND ||
-            (is_spin_type(e.type) && (!(e.L > 0.0) || e.n_slices < 1 || e.n_slices > 4096 ||
-                                      e.n_slices % (1 << spin_order) != 0)) ||
-            (e.type == ST_DRIFT && !(e.L >= 0.0)) || (e.type == ST_SBEND && (e.angle == 0.0 || e.eta == 0.0)) ||
-            (e.fringe != 0 && e.fringe != 1) || (e.fringe && (e.type == ST_DRIFT || e.type == ST_SNAKE)) ||
-            (e.split_order != 0 && e.split_order != 2 && e.split_order != 4) ||
-            (e.split_order == 4 && e.type != ST_MULT && e.type != ST_QUAD_MK) ||
-            (e.type == ST_RBEND && (e.angle == 0.0 || e.eta == 0.0 || !(std::fabs(0.5 * e.angle + e.e1) < 1.5) ||
-                                    !(std::fabs(-0.5 * e.angle + e.e1) < 1.5)))) {
-            set_error("st_track_fp64_noalloc: element %d invalid (type, length, slices, bend parameters or fringe)", i);
+        if (const char* why = element_error(e)) {
+            set_error("st_track_fp64_noalloc: element %d: %s", i, why);
+            return ST_EINVAL;
+        }
+        if (is_spin_type(e.type) && e.n_slices % (1 << spin_order) != 0) {
+            set_error("st_track_fp64_noalloc: element %d: n_slices not a multiple of 2^spin_order", i);
             return ST_EINVAL;
         }
         DevElem d = pack_element(e);
@@ -143,7 +139,8 @@ extern "C" int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, c
         L.table_bytes = table_bytes;
         L.seq_offset = table_bytes;
         for (int u = 0; u < n_unique; ++u)
-            if ((table[u].flags & ST_ELEM_ORDER4) || table[u].type == ST_RBEND) L.has_ext = true;
+            if ((table[u].flags & ST_ELEM_ORDER4) || table[u].type == ST_RBEND || table[u].type == ST_TEAPOT)
+                L.has_ext = true;
         st_ctx ctx;
         ctx.lat = &lat;
         ctx.n = n_particles;

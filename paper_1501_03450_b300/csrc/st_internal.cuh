@@ -16,8 +16,8 @@ namespace st {
 struct __align__(16) DevElem {
     int32_t type;
     int16_t n_slices;
-    int16_t flags;  // ST_ELEM_FRINGE: thin fringe spin kicks at both ends (mult, quad, sbend);
-                    // ST_ELEM_ORDER4: fourth-order slice map (mult, quad; a[2..5] its sub-steps)
+    int16_t flags;  // ST_ELEM_FRINGE: thin fringe spin kicks at both ends (mult, quad, sbend, teapot);
+                    // ST_ELEM_ORDER4: fourth-order slice map (mult, quad, teapot; a[2..5] its sub-steps)
     double ds;      // slice length (drift: full length)
     double a[6];    // type-specific constants, see pack_element()
 };
@@ -35,6 +35,8 @@ static_assert(sizeof(DevElem) == 64, "DevElem must be 64 bytes");
 //   ST_SNAKE   : a0..a3 = unit quaternion (scalar first)
 //   ST_RBEND   : a0 = b1/(B rho), a1 = phi_entr, a2 = -phi_exit, a3 = X offset,
 //                a4 = arc length of the reference orbit
+//   ST_TEAPOT  : a0 = h, a1 = eta; second-order slice: a2 = ds/2 (curved
+//                drifts), a4 = ds (kick); fourth-order: a2..a5 as ST_MULT's
 
 // Reference-particle constants passed by value to the kernels.
 struct RefConst {
@@ -120,7 +122,8 @@ struct LatticeImpl {
     int32_t max_slices;
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
     bool fp64_only = false;        // solenoids, fringe spin kicks or fourth-order maps: FP64 only
-    bool has_ext = false;          // fourth-order slice maps or rectangular bends present
+    bool has_ext = false;          // fourth-order slice maps, rectangular or TEAPOT bends present
+    bool has_order4 = false;       // fourth-order slice maps present
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]
     void* d_blob = nullptr;
     size_t blob_bytes = 0;
@@ -168,6 +171,7 @@ void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 bool is_spin_type(int t);
 DevElem pack_element(const st_element& e);
+const char* element_error(const st_element& e);
 
 // kernel launchers (track_fp64.cu, track_mixed.cu)
 int launch_track_fp64(st_ctx* ctx, int n_turns, int spin_order);

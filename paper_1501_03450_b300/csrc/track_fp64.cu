@@ -1,9 +1,11 @@
 // FP64 tracker kernel over one particle ensemble (persistent warp ranges,
 // equal FP64 work per SM), its launcher and the state pack/unpack kernels.
-// The per-particle integrator is fp64_track_particle in track_fp64.cuh.
+// The per-particle integrators are fp64_track_particle in track_fp64.cuh
+// (Romberg orders) and fp64_track_particle_mid in track_mid.cuh (midpoint
+// schemes).
 #include <cstdio>
 
-#include "track_fp64.cuh"
+#include "track_mid.cuh"
 
 namespace st {
 
@@ -38,8 +40,12 @@ __global__ void __launch_bounds__(128, 2) track_fp64_kernel(const void* __restri
     const int64_t i = wi * 32 + lane;
     if (i >= n || lost[i]) continue;
 
-    fp64_track_particle<K, SPIN, EXT>(table, seq, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns, qcache,
-                                         tq, status);
+    if constexpr (K < 0)   // midpoint schemes: K = ST_SPIN_MID_HALF or ST_SPIN_MID_KICK
+        fp64_track_particle_mid<K == ST_SPIN_MID_KICK>(table, seq, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i,
+                                                        n_turns, qcache, tq, status);
+    else
+        fp64_track_particle<K, SPIN, EXT>(table, seq, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns,
+                                          qcache, tq, status);
     }  // particle loop
 }
 
@@ -127,11 +133,15 @@ static int launch_k_(st_ctx* ctx, int n_turns, const TurnOut& tq) {
     return ST_OK;
 }
 
-// The fourth-order instantiation only for lattices with fourth-order elements.
+// The extended instantiation only for lattices with extended elements; the
+// midpoint schemes have one instantiation each, with every element type.
 template <int K, bool SPIN = true>
 static int launch_k(st_ctx* ctx, int n_turns, const TurnOut& tq) {
-    return ctx->lat->impl.has_ext ? launch_k_<K, SPIN, true>(ctx, n_turns, tq)
-                                     : launch_k_<K, SPIN, false>(ctx, n_turns, tq);
+    if constexpr (K < 0)
+        return launch_k_<K, true, true>(ctx, n_turns, tq);
+    else
+        return ctx->lat->impl.has_ext ? launch_k_<K, SPIN, true>(ctx, n_turns, tq)
+                                         : launch_k_<K, SPIN, false>(ctx, n_turns, tq);
 }
 
 // Orbit only (spins untouched): the orbit maps of the FP64 tracker without the
@@ -160,6 +170,8 @@ int launch_track_fp64(st_ctx* ctx, int n_turns, int spin_order, const TurnOut& o
         return ST_EINVAL;
     }
     switch (spin_order) {
+    case ST_SPIN_MID_HALF: return launch_k<ST_SPIN_MID_HALF>(ctx, n_turns, out);
+    case ST_SPIN_MID_KICK: return launch_k<ST_SPIN_MID_KICK>(ctx, n_turns, out);
     case 0: return launch_k<0>(ctx, n_turns, out);
     case 1: return launch_k<1>(ctx, n_turns, out);
     case 2: return launch_k<2>(ctx, n_turns, out);

@@ -237,6 +237,55 @@ __device__ __forceinline__ bool rbend_body(Particle& p, const PConst& pc, double
     return true;
 }
 
+// ---- TEAPOT sector bend (Sec. 3.6): curved drift and kick -------------------
+// Constants of a curved drift over len in a frame of curvature h (ih = 1/h):
+// c = cos(h len), sn = sin(h len), A1 = (1 - c)/h, A2 = sn/h, the first two
+// from the half angle so that A1 keeps its digits for small h len.
+struct CurvedDrift {
+    double c, sn, A1, A2, len;
+};
+__device__ __forceinline__ CurvedDrift curved_drift_consts(double h, double ih, double len) {
+    double s2, c2;
+    sincos(0.5 * h * len, &s2, &c2);
+    CurvedDrift d;
+    const double omc = 2.0 * s2 * s2;
+    d.c = 1.0 - omc;
+    d.sn = 2.0 * s2 * c2;
+    d.A1 = omc * ih;
+    d.A2 = d.sn * ih;
+    d.len = len;
+    return d;
+}
+
+// Flow of H_D = -(1 + hX) Ps + Pt/beta0 over len, Eq. (teapotD) with the
+// reference time len/beta0: with x' = Px/Ps and cden = cos - x' sin,
+//   X <- (X + (1 - cos)/h + x' sin/h) / cden   ((1/h + X) sec/(1 - x' tan) - 1/h)
+//   d  = (sin/h + X sin) / cden                ((1/h + X) tan/(1 - x' tan))
+//   Y += (Py/Ps) d,  T += len/beta0 - (1/beta0 + Pt) d/Ps,  Px <- Px cos + Ps sin,
+// written without the difference of 1/h-sized terms.  Returns false (state
+// unchanged) if Ps^2 <= 0 or the line does not meet the turned frame.
+__device__ __forceinline__ bool curved_drift(Particle& p, const PConst& pc, const RefConst& ref,
+                                             const CurvedDrift& d) {
+    const double ps2 = pc.P2 - p.Px * p.Px - p.Py * p.Py;
+    if (!(ps2 > 0.0)) return false;
+    const double iPs = rsqrt(ps2), Ps = ps2 * iPs;
+    const double xp = p.Px * iPs;
+    const double cden = fma(-xp, d.sn, d.c);
+    if (!(cden > 0.0)) return false;
+    const double icd = 1.0 / cden;
+    const double dist = fma(p.X, d.sn, d.A2) * icd;
+    p.X = (p.X + fma(xp, d.A2, d.A1)) * icd;
+    p.Y = fma(p.Py * iPs, dist, p.Y);
+    p.T += fma(-pc.b0pt * iPs, dist, d.len * ref.inv_beta0);
+    p.Px = fma(p.Px, d.c, Ps * d.sn);
+    return true;
+}
+
+// Kick of the bend's uniform field over len: dPx/ds = -eta h (1 + hX).
+__device__ __forceinline__ void teapot_kick(Particle& p, double h, double etah, double len) {
+    p.Px = fma(-len * etah, fma(h, p.X, 1.0), p.Px);
+}
+
 // Spin kick of a rectangular-bend fringe, Eq. (skfringeRB) with its factor Y:
 // w = sb [G (gamma - 1) Px Y x^ - (1 + G) Y s^].
 __device__ __forceinline__ Quat rbend_fringe_quat(const PConst& pc, double onepG, const Particle& p, double sb) {
@@ -355,12 +404,14 @@ __device__ __forceinline__ bool solenoid_fringe_quat(const PConst& pc, const Par
 
 // Spin rotation of a thin dipole or multipole fringe, Eq. (skfringe): about
 // the longitudinal axis by -sign (1 + G) sum_m (b_m/(B rho)) Im (X + iY)^m / m
-// with b_1 = eta h (sector bend), b_2 = k1, b_3 = k2/2 (multipole); sign +1 at
-// the entrance, -1 at the exit.
+// with b_1 = eta h (sector or TEAPOT bend: a0 = h, a1 = eta), b_2 = k1,
+// b_3 = k2/2 (multipole); sign +1 at the entrance, -1 at the exit.  Called
+// for ST_MULT, ST_QUAD_MK, ST_SBEND and ST_TEAPOT only, so the dipoles are the
+// types above ST_QUAD_MK.
 __device__ __forceinline__ Quat multipole_fringe_quat(const DevElem& el, int type, double onepG, const Particle& p,
                                                       double sign) {
     double sum;
-    if (type == ST_SBEND) {
+    if (type > ST_QUAD_MK) {
         sum = el.a[0] * el.a[1] * p.Y;                                       // eta h Im(w)
     } else {
         sum = el.a[0] * p.X * p.Y;                                           // k1 Im(w^2)/2
@@ -380,9 +431,10 @@ struct TurnOut {
     double ref[4];
 };
 
-// EXT: compile the extended element set in (fourth-order slice maps and
-// rectangular bends; a separate instantiation, chosen only for lattices that
-// use them, so that the common tracking loop keeps its register budget).
+// EXT: compile the extended element set in (fourth-order slice maps,
+// rectangular and TEAPOT bends; a separate instantiation, chosen only for
+// lattices that use them, so that the common tracking loop keeps its register
+// budget).
 template <int K, bool SPIN = true, bool EXT = false>
 __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ table, const uint16_t* __restrict__ seq,
                                                     int n_seq, const RefConst& ref, double2* __restrict__ xpx,
@@ -659,6 +711,42 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 ok = ok && rbend_rotation(p, pc, el.a[2]);
                 if constexpr (SPIN) q_x = qmul(quat_about_y(el.a[2]), q_x);
                 p.T += el.a[4] * ref.inv_beta0;
+                if (!ok) p.X = __longlong_as_double(0x7ff8000000000000LL);   // quiet NaN
+              } else if (type == ST_TEAPOT) {
+                // Sec. 3.6: curved drift, kick, curved drift per slice (or
+                // Yoshida's composition D K D' K0 D' K D of it); Omega at the
+                // slice edges as in the sector bend (field eta h, curvature h)
+                const double h = el.a[0], etah = el.a[1] * el.a[0], ih = 1.0 / h;
+                const bool o4 = el.flags & ST_ELEM_ORDER4;
+                const CurvedDrift da = curved_drift_consts(h, ih, el.a[2]);
+                CurvedDrift db = da;
+                if (o4) db = curved_drift_consts(h, ih, el.a[3]);
+                bool ok = true;
+                double pp = p.Px * p.Px + p.Py * p.Py;
+                double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                double Ps = (pc.P2 - pp) * ips;
+                if constexpr (SPIN) {
+                    precession(p, pc, 0.0, etah, h, ips, Ps, ox, oy, os);
+                    lv.add_edge(0, N, ds, ox, oy, os);
+                }
+                for (int s = 1; s <= N; ++s) {
+                    ok = curved_drift(p, pc, ref, da) && ok;
+                    teapot_kick(p, h, etah, el.a[4]);
+                    if (o4) {
+                        ok = curved_drift(p, pc, ref, db) && ok;
+                        teapot_kick(p, h, etah, el.a[5]);
+                        ok = curved_drift(p, pc, ref, db) && ok;
+                        teapot_kick(p, h, etah, el.a[4]);
+                    }
+                    ok = curved_drift(p, pc, ref, da) && ok;
+                    pp = p.Px * p.Px + p.Py * p.Py;
+                    ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                    Ps = (pc.P2 - pp) * ips;
+                    if constexpr (SPIN) {
+                        precession(p, pc, 0.0, etah, h, ips, Ps, ox, oy, os);
+                        lv.add_edge(s, N, ds, ox, oy, os);
+                    }
+                }
                 if (!ok) p.X = __longlong_as_double(0x7ff8000000000000LL);   // quiet NaN
               } else {
                 // fourth-order multipole (DKD) or matrix-kick quadrupole:

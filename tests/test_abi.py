@@ -87,3 +87,32 @@ def test_null_context_calls_are_rejected():
     assert lib.st_ctx_set_launch(None, 64, 1) == st.ST_EINVAL
     assert lib.st_ctx_destroy(None) == st.ST_OK
     assert lib.st_lattice_destroy(None) == st.ST_OK
+
+
+def header_constants():
+    txt = open(os.path.join(ROOT, "include", "spintrack.h")).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define\s+(ST_\w+)\s+(-?\d+)", txt, flags=re.M)}
+
+
+def test_binding_constants_match_the_header():
+    consts = header_constants()
+    for name, value in consts.items():
+        assert getattr(st, name) == value, name
+    assert st.TYPE_CODES["teapot"] == consts["ST_TEAPOT"]
+    assert (consts["ST_SPIN_MID_HALF"], consts["ST_SPIN_MID_KICK"]) == (-1, -2)
+
+
+def test_teapot_validation_happens_on_host():
+    """Invalid TEAPOT bends are rejected before any device call; the fourth-
+    order split is allowed for them (and still refused for an exact bend)."""
+    lib = st.load()
+    out = ctypes.c_void_p()
+    ref = st.StReference(1.7928, 45.5)
+    base = dict(type="teapot", L=3.0, n_slices=4, k1=0, k2=0, angle=0.1, eta=1, snake_phi=0, snake_mu=0)
+    for bad in (dict(angle=0.0), dict(angle=4.5), dict(L=0.0), dict(split_order=3), dict(fringe=2)):
+        arr = st.elements_array([dict(base, **bad)])
+        assert lib.st_lattice_create(arr, 1, ctypes.byref(ref), ctypes.byref(out)) == st.ST_EINVAL, bad
+    arr = st.elements_array([dict(base, type="sbend", split_order=4)])
+    assert lib.st_lattice_create(arr, 1, ctypes.byref(ref), ctypes.byref(out)) == st.ST_EINVAL
+    assert b"split_order" in lib.st_last_error()
+    assert out.value is None
