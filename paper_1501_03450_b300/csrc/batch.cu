@@ -17,7 +17,7 @@
 #include <cstring>
 #include <vector>
 
-#include "track_fp64.cuh"
+#include "track_mid.cuh"
 #include "track_mixed.cuh"
 
 namespace st {
@@ -105,9 +105,15 @@ __global__ void __launch_bounds__(128, EXT ? (MINB > 2 ? MINB - 1 : MINB) : MINB
     __shared__ uint64_t bar;
     __shared__ double qcache[(2 * QC_N + 2) * 128];
     batch_loop(jobs, items, n_items, queue, status, smem, &bar, [&](const JobDesc& J, int64_t i) {
-        fp64_track_particle<K, true, EXT>((const DevElem*)smem, (const uint16_t*)(smem + J.seq_offset), J.n_seq, J.ref, J.xpx,
-                               J.ypy, J.tpt, J.sxy, J.sz, J.lost, i, n_turns, qcache,
-                               TurnOut{nullptr, nullptr, 0, {}}, status);
+        if constexpr (K < 0)   // midpoint schemes
+            fp64_track_particle_mid<K == ST_SPIN_MID_KICK>((const DevElem*)smem,
+                                                            (const uint16_t*)(smem + J.seq_offset), J.n_seq, J.ref,
+                                                            J.xpx, J.ypy, J.tpt, J.sxy, J.sz, J.lost, i, n_turns,
+                                                            qcache, TurnOut{nullptr, nullptr, 0, {}}, status);
+        else
+            fp64_track_particle<K, true, EXT>((const DevElem*)smem, (const uint16_t*)(smem + J.seq_offset), J.n_seq,
+                                              J.ref, J.xpx, J.ypy, J.tpt, J.sxy, J.sz, J.lost, i, n_turns, qcache,
+                                              TurnOut{nullptr, nullptr, 0, {}}, status);
     });
 }
 
@@ -139,6 +145,14 @@ static BatchKernel batch_kernel(int precision, int K, int variant, bool ext) {
         }                                                                                                     \
         return variant ? track_batch_mixed_kernel<KK, 3> : track_batch_mixed_kernel<KK, 2>;
     switch (K) {
+    case ST_SPIN_MID_HALF:
+        if (precision != ST_FP64) return nullptr;
+        return variant ? track_batch_fp64_kernel<ST_SPIN_MID_HALF, 3, true>
+                       : track_batch_fp64_kernel<ST_SPIN_MID_HALF, 2, true>;
+    case ST_SPIN_MID_KICK:
+        if (precision != ST_FP64) return nullptr;
+        return variant ? track_batch_fp64_kernel<ST_SPIN_MID_KICK, 3, true>
+                       : track_batch_fp64_kernel<ST_SPIN_MID_KICK, 2, true>;
         ST_SEL(0)
         ST_SEL(1)
         ST_SEL(2)
@@ -488,9 +502,17 @@ int st_batch_track(st_batch* b, int32_t n_turns, int32_t spin_order) {
             set_error("st_batch_track: job %d has no particles uploaded", j);
             return ST_ESTATE;
         }
-    if (n_turns < 0 || spin_order < 0 || spin_order > 4) {
-        set_error("st_batch_track: need n_turns >= 0 and 0 <= spin_order <= 4");
+    if (n_turns < 0 || spin_order < ST_SPIN_MID_KICK || spin_order > 4) {
+        set_error("st_batch_track: need n_turns >= 0 and spin_order in -2..4");
         return ST_EINVAL;
+    }
+    if (spin_order < 0) {
+        bool order4 = false;
+        for (int j = 0; j < b->n_jobs; ++j) order4 = order4 || b->lats[j]->impl.has_order4;
+        if (b->precision != ST_FP64 || order4) {
+            set_error("st_batch_track: the midpoint schemes need an FP64 batch and second-order slice maps");
+            return ST_EINVAL;
+        }
     }
     for (int j = 0; j < b->n_jobs; ++j)
         if (spin_order > b->lats[j]->impl.min_spin_slices_pow2) {

@@ -3,13 +3,14 @@ schemes (Sec. 4.1 with Omega at the slice middle; Sec. 5.3): the CUDA FP64
 tracker through the C ABI against the CPU oracle on the same seeded inputs.
 
 Parity is every coordinate and spin component at 1e-11.  The one exception
-is a whole drift-kick ring tracked for many turns.  The oracle evaluates the
-curved drift in the printed form of Eq. (teapotD), which subtracts 1/h (about
-275 m here) at every step, so its own rounding noise against its
-extended-precision build reaches 1e-10 after 20 turns; the CUDA kernel
-evaluates the same map without that difference.  There parity is taken
-after 2 turns, and after 20 turns the CUDA result must be as close to the
-extended-precision oracle as the FP64 oracle is."""
+is a whole drift-kick ring.  The oracle evaluates the curved drift in the
+printed form of Eq. (teapotD), which subtracts 1/h (about 275 m here) at
+every step, so its own rounding noise against its extended-precision build
+is 2.5e-11 in the spin after 2 turns at G gamma0 = 487 and reaches 1e-10
+after 20 turns; the CUDA kernel evaluates the same map without that
+difference.  There parity is taken after 2 turns at G gamma0 = 45.5, and
+otherwise the CUDA result must be as close to the extended-precision oracle
+as the FP64 oracle is."""
 import math
 
 import numpy as np
@@ -69,7 +70,10 @@ def test_single_teapot_bend_every_order(kw, K):
 def test_drift_kick_ring(gg):
     ring = W.with_spin_order(W.drift_kick_ring(W.rhic_like_ring(gg)), 2)
     z, S = W.gaussian_particles(128, gg, seed=17)
-    compare(ring, z, S, 2, 2)
+    if gg < 100.0:
+        compare(ring, z, S, 2, 2)
+    else:
+        against_extended(ring, z, S, 2, 2)
     against_extended(ring, z, S, 20, 2)
 
 
@@ -138,9 +142,13 @@ def mid_rings():
 @pytest.mark.parametrize("name", list(mid_rings()))
 @pytest.mark.parametrize("K", MID)
 def test_midpoint_schemes_on_every_element_type(name, K):
+    """The RHIC-scale rings for a few turns only: their 1728 bend slices per
+    turn each round X to about an ulp of 1/(eta h) = 275 m in both trackers
+    (the sector bend's Eq. (10a); the curved drift of Eq. (teapotD) in the
+    oracle), 1e-11 after about 10 turns."""
     ring = mid_rings()[name]
     z, S = W.gaussian_particles(200, ring["Ggamma0"], seed=31)
-    turns = 2 if name == "rhic_like_drift_kick" else 10
+    turns = {"rhic_like": 3, "rhic_like_drift_kick": 2}.get(name, 10)
     compare(ring, z, S, turns, K)
 
 
@@ -241,3 +249,31 @@ def test_one_turn_errors_drift_kick_against_bend_kick_on_the_gpu():
         e_dk = np.linalg.norm(s_dk - Sref, axis=0).mean()
         e_bk = np.linalg.norm(s_bk - Sref, axis=0).mean()
         assert e_dk > 100.0 * e_bk, (nb, e_dk, e_bk)
+
+
+@pytest.mark.parametrize("K", MID)
+def test_batched_jobs_with_midpoint_schemes(K):
+    """Uneven jobs (drift-kick, bend-kick and solenoid rings) in one
+    persistent launch with a midpoint scheme, each job against the oracle."""
+    rings = [W.drift_kick_ring(W.toy_ring(45.5)), W.with_fringes(W.toy_ring(120.0)),
+             W.solenoid_ring(45.5, ks=0.05), W.with_slices(W.rbend_ring(45.5, fringe=1), 3)]
+    ns = [300, 77, 150, 33]
+    b = st.Batch(rings, ns, "fp64")
+    inputs = []
+    for k, (ring, n) in enumerate(zip(rings, ns)):
+        z, S = W.gaussian_particles(n, ring["Ggamma0"], seed=80 + k)
+        b.upload(k, z, S)
+        inputs.append((z, S))
+    b.track(4, K)
+    for k, (ring, (z, S)) in enumerate(zip(rings, inputs)):
+        zb, Sb, lb = b.download(k)
+        zo, So, lo = oracle.track(ring, z, S, 4, K)
+        assert np.array_equal(lb, lo)
+        assert np.abs(zb - zo).max() < TOL and np.abs(Sb - So).max() < TOL
+    b.close()
+    bm = st.Batch([W.toy_ring(45.5)], [64], "mixed")
+    z, S = W.gaussian_particles(64, 45.5, seed=1)
+    bm.upload(0, z, S)
+    with pytest.raises(st.SpinTrackError):
+        bm.track(1, K)
+    bm.close()
