@@ -34,6 +34,8 @@ ext = W.with_spin_order(ext, 2)
 ext["elements"] += [W.element("solenoid", L=2.0, n_slices=4, k1=0.05)]
 out["ext_z"], out["ext_S"], out["ext_l"] = st.track(ext, z, S, 5, 2)
 out["mix_z"], out["mix_S"], out["mix_l"] = st.track(toy, z, S, 20, 2, precision="mixed")
+dk = W.drift_kick_ring(W.with_fringes(W.toy_ring(45.5)))
+out["mid_z"], out["mid_S"], out["mid_l"] = st.track(dk, z, S, 5, st.ST_SPIN_MID_KICK)
 b = st.Batch([toy, W.with_spin_order(W.rhic_like_ring(300.0, n_cells=6), 2)], [300, 77], "mixed")
 b.upload(0, z, S)
 z2, S2 = W.gaussian_particles(77, 300.0, seed=6)
@@ -66,6 +68,10 @@ def test_checked_build_runs_clean_and_matches_the_oracle(tmp_path):
     zo, So, lo = oracle.track(ext, z, S, 5, 2)
     assert np.array_equal(d["ext_l"], lo)
     assert np.abs(d["ext_z"] - zo).max() < 1e-11 and np.abs(d["ext_S"] - So).max() < 1e-11
+    dk = W.drift_kick_ring(W.with_fringes(W.toy_ring(45.5)))
+    zo, So, lo = oracle.track(dk, z, S, 5, oracle.MID_KICK)
+    assert np.array_equal(d["mid_l"], lo)
+    assert np.abs(d["mid_z"] - zo).max() < 1e-11 and np.abs(d["mid_S"] - So).max() < 1e-11
     # mixed precision: its own accuracy against the FP64 oracle on this ring
     zo, So, lo = oracle.track(toy, z, S, 20, 2)
     assert np.array_equal(d["mix_l"], lo)

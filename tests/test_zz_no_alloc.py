@@ -62,3 +62,15 @@ def test_noalloc_rejects_oversized_lattice_and_bad_order():
     with pytest.raises(st.SpinTrackError) as e:
         st.st_track_fp64_noalloc(big, 1.7928, 45.5, state.data_ptr(), lost.data_ptr(), n, 1, 0)
     assert e.value.code == st.ST_EINVAL
+
+
+def test_noalloc_with_teapot_bends_matches_context_entry_point():
+    """A drift-kick lattice (TEAPOT bends, extended instantiation) through the
+    allocation-free entry point."""
+    torch = pytest.importorskip("torch")
+    ring = W.with_spin_order(W.drift_kick_ring(W.rhic_like_ring(45.5, n_cells=12)), 2)
+    z, S = W.gaussian_particles(500, 45.5, seed=103)
+    a = _run_noalloc(torch, ring, z, S, 5, 2)
+    b = st.track(ring, z, S, 5, 2)
+    assert np.array_equal(a[2], b[2])
+    assert np.abs(a[0] - b[0]).max() < TOL and np.abs(a[1] - b[1]).max() < TOL
