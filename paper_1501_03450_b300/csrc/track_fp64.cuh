@@ -431,6 +431,74 @@ struct TurnOut {
     double ref[4];
 };
 
+// Particle i's orbit, its per-particle constants (Eq. 2: P^2 = 1 + 2 Pt/beta0
+// + Pt^2; gamma = gamma0 (1 + beta0 Pt) for Eq. 6b) and its spin, from the
+// state pairs.
+__device__ __forceinline__ void load_particle(const RefConst& ref, const double2* __restrict__ xpx,
+                                              const double2* __restrict__ ypy, const double2* __restrict__ tpt,
+                                              const double2* __restrict__ sxy, const double* __restrict__ szp,
+                                              int64_t i, Particle& p, PConst& pc, double& sx, double& sy,
+                                              double& sz) {
+    double2 v = xpx[i];
+    p.X = v.x;
+    p.Px = v.y;
+    v = ypy[i];
+    p.Y = v.x;
+    p.Py = v.y;
+    v = tpt[i];
+    p.T = v.x;
+    pc.Pt = v.y;
+    pc.P2 = 1.0 + 2.0 * pc.Pt * ref.inv_beta0 + pc.Pt * pc.Pt;
+    pc.invP = rsqrt(pc.P2);
+    pc.P = pc.P2 * pc.invP;
+    pc.invP2 = pc.invP * pc.invP;
+    pc.b0pt = ref.inv_beta0 + pc.Pt;
+    const double gamma = ref.gamma0 * (1.0 + ref.beta0 * pc.Pt);
+    pc.a = 1.0 + ref.G * gamma;
+    pc.c = ref.G * (gamma - 1.0);
+    pc.cP2 = pc.c * pc.invP2;
+    pc.hP3 = 0.5 * pc.invP * pc.invP2;
+    v = sxy[i];
+    sx = v.x;
+    sy = v.y;
+    sz = szp[i];
+}
+
+// End of a turn: normalise the composed turn quaternion, rotate the spin by
+// it, and write the optional per-turn outputs.
+__device__ __forceinline__ void end_turn(Quat& qt, double& sx, double& sy, double& sz, const TurnOut& tq,
+                                         int64_t i) {
+    qt = qnormalize(qt);
+    rotate_vec(qt, sx, sy, sz);
+    if (tq.q) {
+        const double sgn =
+            (qt.w * tq.ref[0] + qt.x * tq.ref[1] + qt.y * tq.ref[2] + qt.z * tq.ref[3]) < 0.0 ? -1.0 : 1.0;
+        tq.q[i] = sgn * qt.w;
+        tq.q[tq.n + i] = sgn * qt.x;
+        tq.q[2 * tq.n + i] = sgn * qt.y;
+        tq.q[3 * tq.n + i] = sgn * qt.z;
+    }
+    if (tq.sum) {
+        tq.sum[i] += sx;
+        tq.sum[tq.n + i] += sy;
+        tq.sum[2 * tq.n + i] += sz;
+    }
+}
+
+// Write particle i's state back (Pt is a constant of the motion) and its
+// lost flag.
+__device__ __forceinline__ void store_particle(const Particle& p, double sx, double sy, double sz, bool is_lost,
+                                               double2* __restrict__ xpx, double2* __restrict__ ypy,
+                                               double2* __restrict__ tpt, double2* __restrict__ sxy,
+                                               double* __restrict__ szp, uint8_t* __restrict__ lost, int64_t i) {
+    xpx[i] = make_double2(p.X, p.Px);
+    ypy[i] = make_double2(p.Y, p.Py);
+    tpt[i].x = p.T;
+    sxy[i] = make_double2(sx, sy);
+    szp[i] = sz;
+    if (is_lost) lost[i] = 1;
+}
+
 // EXT: compile the extended element set in (fourth-order slice maps,
 // rectangular and TEAPOT bends; a separate instantiation, chosen only for
 // lattices that use them, so that the common tracking loop keeps its register
@@ -446,28 +514,9 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
     // table entries below the sequence (both staged into shared memory back to back)
     const int n_table = (int)(((const char*)seq - (const char*)table) / sizeof(DevElem));
     Particle p;
-    double2 v = xpx[i];
-    p.X = v.x;
-    p.Px = v.y;
-    v = ypy[i];
-    p.Y = v.x;
-    p.Py = v.y;
-    v = tpt[i];
-    p.T = v.x;
     PConst pc;
-    pc.Pt = v.y;
-    pc.P2 = 1.0 + 2.0 * pc.Pt * ref.inv_beta0 + pc.Pt * pc.Pt;
-    pc.invP = rsqrt(pc.P2);
-    pc.P = pc.P2 * pc.invP;
-    pc.invP2 = pc.invP * pc.invP;
-    pc.b0pt = ref.inv_beta0 + pc.Pt;
-    const double gamma = ref.gamma0 * (1.0 + ref.beta0 * pc.Pt);
-    pc.a = 1.0 + ref.G * gamma;
-    pc.c = ref.G * (gamma - 1.0);
-    pc.cP2 = pc.c * pc.invP2;
-    pc.hP3 = 0.5 * pc.invP * pc.invP2;
-    v = sxy[i];
-    double sx = v.x, sy = v.y, sz = szp[i];
+    double sx, sy, sz;
+    load_particle(ref, xpx, ypy, tpt, sxy, szp, i, p, pc, sx, sy, sz);
 
     QuadCache qc;
     qc.key_k = -1.0;
@@ -838,30 +887,9 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 }
             }
         }
-        if constexpr (SPIN) {
-            qt = qnormalize(qt);
-            rotate_vec(qt, sx, sy, sz);
-            if (tq.q) {
-                const double sgn =
-                    (qt.w * tq.ref[0] + qt.x * tq.ref[1] + qt.y * tq.ref[2] + qt.z * tq.ref[3]) < 0.0 ? -1.0 : 1.0;
-                tq.q[i] = sgn * qt.w;
-                tq.q[tq.n + i] = sgn * qt.x;
-                tq.q[2 * tq.n + i] = sgn * qt.y;
-                tq.q[3 * tq.n + i] = sgn * qt.z;
-            }
-            if (tq.sum) {
-                tq.sum[i] += sx;
-                tq.sum[tq.n + i] += sy;
-                tq.sum[2 * tq.n + i] += sz;
-            }
-        }
+        if constexpr (SPIN) end_turn(qt, sx, sy, sz, tq, i);
     }
-    xpx[i] = make_double2(p.X, p.Px);
-    ypy[i] = make_double2(p.Y, p.Py);
-    tpt[i].x = p.T;
-    sxy[i] = make_double2(sx, sy);
-    szp[i] = sz;
-    if (is_lost) lost[i] = 1;
+    store_particle(p, sx, sy, sz, is_lost, xpx, ypy, tpt, sxy, szp, lost, i);
 }
 
 }  // namespace st

@@ -79,28 +79,9 @@ __device__ __forceinline__ void fp64_track_particle_mid(const DevElem* __restric
                                                         double* qcache, const TurnOut& tq, int32_t* status) {
     const int n_table = (int)(((const char*)seq - (const char*)table) / sizeof(DevElem));
     Particle p;
-    double2 v = xpx[i];
-    p.X = v.x;
-    p.Px = v.y;
-    v = ypy[i];
-    p.Y = v.x;
-    p.Py = v.y;
-    v = tpt[i];
-    p.T = v.x;
     PConst pc;
-    pc.Pt = v.y;
-    pc.P2 = 1.0 + 2.0 * pc.Pt * ref.inv_beta0 + pc.Pt * pc.Pt;
-    pc.invP = rsqrt(pc.P2);
-    pc.P = pc.P2 * pc.invP;
-    pc.invP2 = pc.invP * pc.invP;
-    pc.b0pt = ref.inv_beta0 + pc.Pt;
-    const double gamma = ref.gamma0 * (1.0 + ref.beta0 * pc.Pt);
-    pc.a = 1.0 + ref.G * gamma;
-    pc.c = ref.G * (gamma - 1.0);
-    pc.cP2 = pc.c * pc.invP2;
-    pc.hP3 = 0.5 * pc.invP * pc.invP2;
-    v = sxy[i];
-    double sx = v.x, sy = v.y, sz = szp[i];
+    double sx, sy, sz;
+    load_particle(ref, xpx, ypy, tpt, sxy, szp, i, p, pc, sx, sy, sz);
     const double onepG = 1.0 + ref.G;
 
     QuadCache qc;
@@ -269,28 +250,9 @@ __device__ __forceinline__ void fp64_track_particle_mid(const DevElem* __restric
             }
             qt = qmul(q_out, qmul(qe, qmul(q_in, qt)));
         }
-        qt = qnormalize(qt);
-        rotate_vec(qt, sx, sy, sz);
-        if (tq.q) {
-            const double sgn =
-                (qt.w * tq.ref[0] + qt.x * tq.ref[1] + qt.y * tq.ref[2] + qt.z * tq.ref[3]) < 0.0 ? -1.0 : 1.0;
-            tq.q[i] = sgn * qt.w;
-            tq.q[tq.n + i] = sgn * qt.x;
-            tq.q[2 * tq.n + i] = sgn * qt.y;
-            tq.q[3 * tq.n + i] = sgn * qt.z;
-        }
-        if (tq.sum) {
-            tq.sum[i] += sx;
-            tq.sum[tq.n + i] += sy;
-            tq.sum[2 * tq.n + i] += sz;
-        }
+        end_turn(qt, sx, sy, sz, tq, i);
     }
-    xpx[i] = make_double2(p.X, p.Px);
-    ypy[i] = make_double2(p.Y, p.Py);
-    tpt[i].x = p.T;
-    sxy[i] = make_double2(sx, sy);
-    szp[i] = sz;
-    if (is_lost) lost[i] = 1;
+    store_particle(p, sx, sy, sz, is_lost, xpx, ypy, tpt, sxy, szp, lost, i);
 }
 
 }  // namespace st

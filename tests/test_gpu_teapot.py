@@ -277,3 +277,40 @@ def test_batched_jobs_with_midpoint_schemes(K):
     with pytest.raises(st.SpinTrackError):
         bm.track(1, K)
     bm.close()
+
+
+def test_spin_errors_over_turns_order_on_the_gpu():
+    """Sec. 5.3, Fig. spinErrVsTurns, through the CUDA tracker on the
+    RHIC-scale ring at G gamma0 = 45.5 with n_b = 4, against the oracle's
+    bend-kick / matrix-kick reference (128 slices, three Romberg
+    iterations) turn by turn: TEAPOT (split-kick placement) more than 100
+    times above bend-kick / matrix-kick with the trapezoid rule, which stays
+    at least 2 times above bend-kick / matrix-kick with two Romberg
+    iterations."""
+    gg = 45.5
+    base = W.rhic_like_ring(gg)
+    z, S = W.gaussian_particles(64, gg, seed=5)
+    runs = {"teapot": (W.with_slices(W.drift_kick_ring(base), 4), st.ST_SPIN_MID_KICK),
+            "bkmk_pwc": (W.with_slices(base, 4), 0),
+            "bkmk_romberg": (W.with_slices(base, 4), 2)}
+    trackers = {}
+    for k, (ring, K) in runs.items():
+        lat = st.Lattice(ring)
+        t = st.Tracker(lat, z.shape[1])
+        t.upload(z, S)
+        trackers[k] = (lat, t, K)
+    zr, Sr = z, S
+    ref_ring = W.with_slices(base, 128)
+    for turn in range(6):
+        zr, Sr, _ = oracle.track(ref_ring, zr, Sr, 1, 3)
+        errs = {}
+        for k, (lat, t, K) in trackers.items():
+            t.track(1, K)
+            _, Sk, lk = t.download()
+            assert not lk.any()
+            errs[k] = np.linalg.norm(Sk - Sr, axis=0).mean()
+        assert errs["teapot"] > 100 * errs["bkmk_pwc"], (turn, errs)
+        assert errs["bkmk_pwc"] > 2 * errs["bkmk_romberg"], (turn, errs)
+    for lat, t, _ in trackers.values():
+        t.close()
+        lat.close()
