@@ -50,6 +50,12 @@ ALGO_SPECIAL_PER_PASS = {2: {"sqrt": 20.4016, "sin_cos": 19.4029, "asin": 2.2827
                          3: {"sqrt": 38.0925, "sin_cos": 37.6645, "asin": 4.5654, "sinh_cosh": 15.9789},
                          4: {"sqrt": 72.9036, "sin_cos": 73.0462, "asin": 9.1308, "sinh_cosh": 31.9577}}
 ALGO_FLOPS_PER_TYPE = {2: {"snake": 56.0, "quad_mk": 1645.0, "mult": 1053.0, "drift": 20.0, "sbend": 974.0}}
+# The same count for the integrator comparison (Sec. 3.6, 5.3) on this ring:
+# its drift-kick version (TEAPOT bends, drift-kick-drift quadrupoles) with two
+# Romberg iterations and with the split-kick midpoint scheme, and the ring
+# itself with the half-slice midpoint scheme and with two Romberg iterations.
+ALGO_FLOPS_COMPARISON = {"drift_kick_romberg2": 601.8494, "drift_kick_mid_kick": 426.9379,
+                         "bend_kick_mid_half": 678.0343, "bend_kick_romberg2": 671.4716}
 # FP64 floating-point operations the FP64 tracker executes per particle-element
 # pass on this workload (2 per DFMA, 1 per DADD/DMUL), and FP64-pipe
 # instructions per pass, from the thread-level instruction counters of one ncu
@@ -461,7 +467,7 @@ def _time_turn(st, torch, ring, z, S, spin_order, flush, stream):
     return sum(a.elapsed_time(b) for a, b in ev) * 1e-3 / len(ev)
 
 
-def variant_drift_kick(st, torch, npart, seed, ggamma=45.5, dS_particles=4096):
+def variant_drift_kick(st, torch, npart, seed, fp64_peak, ggamma=45.5, dS_particles=4096):
     """The paper's comparison of integrators (Sec. 3.6, 5.3) on the RHIC-like
     ring: FP64 pass rates of the drift-kick version (TEAPOT bends,
     drift-kick-drift quadrupoles) with two Romberg iterations and with the
@@ -492,8 +498,10 @@ def variant_drift_kick(st, torch, npart, seed, ggamma=45.5, dS_particles=4096):
             row[name] = float(np.linalg.norm(S1 - Sref, axis=0).mean())
         row["drift_kick_over_bend_kick"] = row["drift_kick_mid_kick"] / row["bend_kick_mid_half"]
         dS[f"n_b={nb}"] = row
+    roof = {k: {"algorithmic_flops_per_pass": ALGO_FLOPS_COMPARISON[k],
+                "frac_of_fp64_peak": ALGO_FLOPS_COMPARISON[k] * v / fp64_peak} for k, v in rates.items()}
     return {"workload": f"108-cell RHIC-like ring at G gamma0 = {ggamma}, {npart} particles, 1 turn per launch",
-            "passes_per_s": rates, "one_turn_dS": dS,
+            "passes_per_s": rates, "roofline": roof, "one_turn_dS": dS,
             "dS_sample": f"{dS_particles} particles, reference: bend-kick/matrix-kick, 256 slices, 3 Romberg "
                          "iterations"}
 
@@ -664,7 +672,7 @@ def main():
     variants = None
     if not args.no_variants and world == 1:
         variants = {"fp64_configs": variant_fp64_configs(st, torch, npart, fp64_peak, w["seed"]),
-                    "drift_kick": variant_drift_kick(st, torch, npart, w["seed"]),
+                    "drift_kick": variant_drift_kick(st, torch, npart, w["seed"], fp64_peak),
                     "mixed": variant_mixed(st, torch, args, value, fp32_peak),
                     "batched": variant_batched(st, torch, args),
                     "surrogate": variant_surrogate(st, torch, args, value)}

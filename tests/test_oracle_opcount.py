@@ -69,3 +69,18 @@ def test_bench_algorithmic_figures_are_current():
         els = [e for e in ring["elements"] if e["type"] == t]
         ct, _, _, _ = oracle.op_counts(dict(ring, elements=els), z, S, 1, 2)
         assert (ct["add"] + ct["mul"] + ct["div"]) / (8 * len(els)) == v
+
+
+def test_bench_comparison_figures_are_current():
+    """Algorithmic work per pass of the integrator comparison (drift-kick ring
+    with Romberg and split-kick midpoint schemes; the ring with the
+    half-slice midpoint scheme and with Romberg)."""
+    b = _bench()
+    base = W.workload("rhic_like_1e5")["ring"]
+    dk = W.drift_kick_ring(base)
+    z, S = W.gaussian_particles(8, 45.5, seed=1)
+    for name, ring, K in (("drift_kick_romberg2", dk, 2), ("drift_kick_mid_kick", dk, oracle.MID_KICK),
+                          ("bend_kick_mid_half", base, oracle.MID_HALF), ("bend_kick_romberg2", base, 2)):
+        c, _, _, _ = oracle.op_counts(ring, z, S, 1, K)
+        per_pass = (c["add"] + c["mul"] + c["div"]) / (8 * len(ring["elements"]))
+        assert abs(per_pass - b.ALGO_FLOPS_COMPARISON[name]) < 1e-3, name
