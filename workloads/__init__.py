@@ -71,8 +71,9 @@ def element(type: str, L: float = 0.0, n_slices: int = 1, k1: float = 0.0,
 
 def slices_for_order(base: int, spin_order: int) -> int:
     """Smallest multiple of 2**spin_order that is >= base (Romberg needs the
-    slice count divisible by 2**k, Sec. 4.3)."""
-    m = 1 << spin_order
+    slice count divisible by 2**k, Sec. 4.3); any count >= 1 for the midpoint
+    schemes (negative spin_order)."""
+    m = 1 << max(spin_order, 0)
     return max(m, ((base + m - 1) // m) * m)
 
 
