@@ -305,7 +305,9 @@ int st_selftest_bounded_wait(double limit_s, double* elapsed_s);
  *          then Sz[n];  lost: device buffer of n flags (0 = tracked; set to 1
  *          when a particle is lost; particles flagged on entry are skipped).
  *   n_turns >= 0, spin_order 0..4 (every spin-carrying element's n_slices a
- *   multiple of 2^spin_order); cuda_stream may be NULL (legacy stream).
+ *   multiple of 2^spin_order) or a midpoint scheme (ST_SPIN_MID_HALF,
+ *   ST_SPIN_MID_KICK; no fourth-order slice maps); cuda_stream may be NULL
+ *   (legacy stream).
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call shares the scratch and rewrites it;

@@ -62,8 +62,8 @@ extern "C" int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, c
         set_error("st_track_fp64_noalloc: at most 2^31-1 particles and 16384 elements");
         return ST_EINVAL;
     }
-    if (n_turns < 0 || spin_order < 0 || spin_order > 4) {
-        set_error("st_track_fp64_noalloc: need n_turns >= 0 and 0 <= spin_order <= 4");
+    if (n_turns < 0 || spin_order < ST_SPIN_MID_KICK || spin_order > 4) {
+        set_error("st_track_fp64_noalloc: need n_turns >= 0 and spin_order in -2..4");
         return ST_EINVAL;
     }
     if (!(ref->G > 0.0) || !(ref->Ggamma0 > ref->G)) {
@@ -82,8 +82,12 @@ extern "C" int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, c
             set_error("st_track_fp64_noalloc: element %d: %s", i, why);
             return ST_EINVAL;
         }
-        if (is_spin_type(e.type) && e.n_slices % (1 << spin_order) != 0) {
+        if (is_spin_type(e.type) && spin_order > 0 && e.n_slices % (1 << spin_order) != 0) {
             set_error("st_track_fp64_noalloc: element %d: n_slices not a multiple of 2^spin_order", i);
+            return ST_EINVAL;
+        }
+        if (spin_order < 0 && e.split_order == 4) {
+            set_error("st_track_fp64_noalloc: element %d: the midpoint schemes need second-order slice maps", i);
             return ST_EINVAL;
         }
         DevElem d = pack_element(e);

@@ -74,3 +74,22 @@ def test_noalloc_with_teapot_bends_matches_context_entry_point():
     b = st.track(ring, z, S, 5, 2)
     assert np.array_equal(a[2], b[2])
     assert np.abs(a[0] - b[0]).max() < TOL and np.abs(a[1] - b[1]).max() < TOL
+
+
+def test_noalloc_midpoint_schemes_match_context_entry_point():
+    torch = pytest.importorskip("torch")
+    ring = W.with_slices(W.drift_kick_ring(W.toy_ring(45.5)), 3)
+    z, S = W.gaussian_particles(300, 45.5, seed=104)
+    for K in (st.ST_SPIN_MID_HALF, st.ST_SPIN_MID_KICK):
+        a = _run_noalloc(torch, ring, z, S, 4, K)
+        b = st.track(ring, z, S, 4, K)
+        assert np.array_equal(a[2], b[2])
+        assert np.abs(a[0] - b[0]).max() < TOL and np.abs(a[1] - b[1]).max() < TOL
+    n = 64
+    state = torch.zeros(9 * n, dtype=torch.float64, device="cuda")
+    lost = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    r4 = W.with_split_order(W.toy_ring(45.5), 4)
+    with pytest.raises(st.SpinTrackError) as e:
+        st.st_track_fp64_noalloc(r4["elements"], r4["G"], r4["Ggamma0"], state.data_ptr(), lost.data_ptr(), n, 1,
+                                 st.ST_SPIN_MID_KICK)
+    assert e.value.code == st.ST_EINVAL
