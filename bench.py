@@ -77,7 +77,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
-    ap.add_argument("--spin-order", type=int, default=2)
+    ap.add_argument("--spin-order", type=int, default=2,
+                    help="Romberg order 0..4, or -1 / -2 for the half-slice / split-kick midpoint schemes")
+    ap.add_argument("--ring", choices=["rhic_like", "drift_kick"], default="rhic_like",
+                    help="drift_kick: the same ring with TEAPOT bends and drift-kick-drift quadrupoles")
     ap.add_argument("--ggamma", type=float, default=45.5)
     ap.add_argument("--particles", type=int, default=None, help="override particles per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -564,12 +567,18 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    w = W.workload(WORKLOAD, spin_order=args.spin_order, Ggamma0=args.ggamma)
+    # the midpoint schemes run on the slicing of Romberg order 2 (4 slices per
+    # element), the ring of the integrator comparison
+    w = W.workload(WORKLOAD, spin_order=max(args.spin_order, 2) if args.spin_order < 0 else args.spin_order,
+                   Ggamma0=args.ggamma)
     ring = w["ring"]
+    if args.ring == "drift_kick":
+        ring = W.drift_kick_ring(ring)
     n_el = len(ring["elements"])
     npart = args.particles or w["n_particles"]
     z, S = W.gaussian_particles(npart, args.ggamma, seed=rank_seed(w["seed"], rank))
     K = args.spin_order
+    headline = args.ring == "rhic_like" and K >= 0
 
     stream = torch.cuda.Stream()
     lat = st.Lattice(ring)
@@ -642,10 +651,15 @@ def main():
     peak = fp64_peak if args.precision == "fp64" else fp32_peak
     avg_launch_s = t_sum / (args.steps * launches_per_step)
     passes_per_launch = npart * n_el
-    algo = ALGO_FLOPS_PER_PASS.get(K)
+    if headline:
+        algo = ALGO_FLOPS_PER_PASS.get(K)
+    else:
+        algo = {("drift_kick", 2): ALGO_FLOPS_COMPARISON["drift_kick_romberg2"],
+                ("drift_kick", -2): ALGO_FLOPS_COMPARISON["drift_kick_mid_kick"],
+                ("rhic_like", -1): ALGO_FLOPS_COMPARISON["bend_kick_mid_half"]}.get((args.ring, K))
     achieved = algo * passes_per_launch / avg_launch_s / 1e12 if algo else None
     executed = None
-    if args.precision == "fp64" and K == 2 and FP64_FLOPS_PER_PASS:
+    if args.precision == "fp64" and K == 2 and headline and FP64_FLOPS_PER_PASS:
         ex_tflops = FP64_FLOPS_PER_PASS * passes_per_launch / avg_launch_s / 1e12
         issue = FP64_PIPE_INSTR_PER_PASS * passes_per_launch / avg_launch_s
         sm_hz = (clocks.get("sm_mhz") or 2032.0) * 1e6
@@ -657,12 +671,13 @@ def main():
     roofline = {"bound": "alu", "pipe": "fp64" if args.precision == "fp64" else "fp32",
                 "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": (achieved / (peak / 1e12)) if achieved else None,
-                "traffic": FP64_DRAM_BYTES_PER_PARTICLE * npart if args.precision == "fp64" else None,
+                "traffic": FP64_DRAM_BYTES_PER_PARTICLE * npart if args.precision == "fp64" and headline else None,
                 "peak_source": "measured by st_measure_peaks (independent FMA chains) at run time",
                 "algorithmic_flops_per_pass": algo,
                 "algorithmic_basis": "additions, multiplications and divisions on particle data counted by the "
                                      "oracle's operation-counting build for this ring and order; special functions "
-                                     "per pass not charged: " + json.dumps(ALGO_SPECIAL_PER_PASS.get(K)),
+                                     "per pass not charged: " + json.dumps(ALGO_SPECIAL_PER_PASS.get(K) if headline
+                                                                           else None),
                 "executed": executed}
 
     breakdown = None
@@ -690,8 +705,13 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: 108-cell RHIC-like ring (1514 elements/turn), "
-                   f"{npart} Gaussian protons per GPU, Ggamma={args.ggamma}, Romberg order {K}, 1 turn per step",
+        "config": {"workload": f"{WORKLOAD}: 108-cell RHIC-like ring (1514 elements/turn)"
+                   + (", drift-kick version (TEAPOT bends, drift-kick-drift quadrupoles)" if args.ring == "drift_kick"
+                      else "")
+                   + f", {npart} Gaussian protons per GPU, Ggamma={args.ggamma}, "
+                   + (f"Romberg order {K}" if K >= 0 else ("half-slice" if K == -1 else "split-kick")
+                      + " midpoint spin scheme") + ", 1 turn per step",
+                   "ring": args.ring,
                    "particles_per_gpu": npart, "elements_per_turn": n_el, "precision": args.precision,
                    "spin_order": K, "turns_per_step": 1, "parallelism": f"replicas{world}",
                    "l2": "flushed between steps (2x L2 buffer written outside the timed events)"},
