@@ -38,7 +38,7 @@ _VARIANTS = {
 }
 
 TYPE_CODES = {"drift": 0, "mult": 1, "quad_mk": 2, "sbend": 3, "snake": 4, "solenoid": 5, "rbend": 6,
-              "teapot": 7}
+              "teapot": 7, "thin_mult": 8}
 
 # spin_order values of the midpoint (piece-wise constant) schemes; 0..6 are
 # Romberg orders over slice-edge samples

@@ -26,6 +26,8 @@
  *             of a rectangular bend, Eq. (skfringeRB)
  *   Sec. 3.6  TEAPOT split of a sector bend, Eqs. (DKsplit), (teapotD): curved
  *             drift and the kick of the bend's uniform field (Eq. (sbendA))
+ *   Sec. 3.5  thin lens: the multipole of Sec. 3.4 in the limit of zero length
+ *             at fixed integrated strengths, spin sampled like any element
  *   Sec. 3.7  solenoid: exact body map Eq. (solenoid) of the Hamiltonian
  *             Eq. (Hsolenoid) with the vector potential Eq. (Asol); the
  *             unit velocity from the kinetic momentum, Eq. (mgVSol)
@@ -83,7 +85,7 @@ typedef ORACLE_REAL real;
 
 /* Element kinds (own numbering; the CUDA library has its own). */
 enum { ORC_DRIFT = 0, ORC_MULT = 1, ORC_QUAD_MK = 2, ORC_SBEND = 3, ORC_SNAKE = 4, ORC_SOLENOID = 5, ORC_RBEND = 6,
-       ORC_TEAPOT = 7 };
+       ORC_TEAPOT = 7, ORC_THIN = 8 };
 
 /* Spin integration schemes other than the Romberg orders K >= 0 (Sec. 4.1,
  * Eq. (37) with Omega taken at the middle of each slice):
@@ -417,6 +419,10 @@ static int slice_map2(const orc_ref* r, const orc_element* e, orc_orbit* z, doub
         return 0;
     case ORC_SBEND:   /* exact bend, Eq. (10) */
         return sbend_map(r, z, e->angle / e->L, e->eta, ds);
+    case ORC_THIN:    /* Sec. 3.5: the drift-kick slice without its drifts; ds is the slice's share of the
+                         unit kick parameter and k1, k2 hold integrated strengths */
+        mult_kick(z, e->k1, e->k2, ds);
+        return 0;
     case ORC_TEAPOT:  /* curved drift - kick - curved drift, Sec. 3.6 in the symmetric form of Eq. (27) */
         if (curved_drift(r, z, e->angle / e->L, 0.5 * ds)) return 1;
         teapot_kick(z, e->angle / e->L, e->eta, ds);
@@ -817,7 +823,11 @@ static int track_element(const orc_ref* r, const orc_element* e, orc_orbit* z, r
         return 0;
     }
     int N = e->n_slices;
-    double ds = e->L / N;
+    /* a thin lens (Sec. 3.5) is the L -> 0 limit of the multipole at fixed
+     * integrated strengths: in terms of t = s/L in [0, 1] its slices are
+     * kicks of 1/N of the integrated field with no drift between them, and
+     * Omega (Eq. (6b)) per unit t is that of the integrated field */
+    double ds = e->type == ORC_THIN ? 1.0 / N : e->L / N;
     /* entrance fringe kick (orbit unchanged across the fringe) */
     if (element_fringe(r, e, +1, z, S)) return 1;
     if (K < 0) {
@@ -861,12 +871,13 @@ int orc_check_lattice(const orc_element* els, int n_el, int K) {
     int div = K > 0 ? 1 << K : 1;
     for (int i = 0; i < n_el; ++i) {
         const orc_element* e = &els[i];
-        if (e->type < 0 || e->type > ORC_TEAPOT) return -1;
+        if (e->type < 0 || e->type > ORC_THIN) return -1;
         if (e->type == ORC_MULT || e->type == ORC_QUAD_MK || e->type == ORC_SBEND || e->type == ORC_SOLENOID ||
-            e->type == ORC_RBEND || e->type == ORC_TEAPOT) {
+            e->type == ORC_RBEND || e->type == ORC_TEAPOT || e->type == ORC_THIN) {
             if (e->n_slices < 1 || (e->n_slices % div) != 0) return -1;
-            if (e->L == 0.0) return -1;
+            if ((e->L == 0.0) != (e->type == ORC_THIN)) return -1;
         }
+        if (e->type == ORC_THIN && (e->fringe || e->split_order == 4)) return -1;
         if (e->type == ORC_SBEND && (e->angle == 0.0 || e->eta == 0.0)) return -1;
         if (e->type == ORC_TEAPOT && (e->angle == 0.0 || !(fabs(e->angle / e->n_slices) < 1.0))) return -1;
         if (K < 0 && e->split_order == 4) return -1;
@@ -946,7 +957,7 @@ int orc_orbit_map(const orc_element* e, double G, double Ggamma0, real* z6) {
         rc = track_rbend(&r, e, &o, S, 0, NULL, NULL);
     } else {
         if (e->n_slices < 1) return -1;
-        double ds = e->L / e->n_slices;
+        double ds = e->type == ORC_THIN ? 1.0 / e->n_slices : e->L / e->n_slices;
         for (int i = 0; i < e->n_slices && !rc; ++i) rc = slice_map(&r, e, &o, ds);
     }
     z6[0] = o.X; z6[1] = o.Px; z6[2] = o.Y; z6[3] = o.Py; z6[4] = o.T; z6[5] = o.Pt;

@@ -15,6 +15,9 @@ b/(B rho), Sec. 2.1 and Sec. 3):
                | "snake" (thin spin rotator, Sec. 5)
                | "teapot" (sector bend integrated by the TEAPOT drift-kick
                  split, Sec. 3.6: curved drift, kick, curved drift)
+               | "thin_mult" (thin lens, Sec. 3.5: L = 0, k1 and k2 hold the
+                 integrated strengths k1 L [m^-1] and k2 L [m^-2]; n_slices
+                 samples the spin along the kick)
     L          length
     n_slices   number of integration slices (spin-carrying elements)
     k1         quadrupole gradient b2/(B rho)            [m^-2]
@@ -53,8 +56,8 @@ import numpy as np
 
 G_PROTON = 1.7928
 
-ELEMENT_TYPES = ("drift", "mult", "quad_mk", "sbend", "snake", "solenoid", "rbend", "teapot")
-SPIN_TYPES = ("mult", "quad_mk", "sbend", "solenoid", "rbend", "teapot")
+ELEMENT_TYPES = ("drift", "mult", "quad_mk", "sbend", "snake", "solenoid", "rbend", "teapot", "thin_mult")
+SPIN_TYPES = ("mult", "quad_mk", "sbend", "solenoid", "rbend", "teapot", "thin_mult")
 
 
 def element(type: str, L: float = 0.0, n_slices: int = 1, k1: float = 0.0,
@@ -153,6 +156,24 @@ def drift_kick_ring(ring: Dict) -> Dict:
     out = dict(ring)
     out["elements"] = [dict(e, type=conv.get(e["type"], e["type"])) for e in ring["elements"]]
     out["name"] = ring["name"] + "_drift_kick"
+    return out
+
+
+def with_thin_sextupoles(ring: Dict) -> Dict:
+    """Copy of `ring` whose thick sextupoles (mult elements without a
+    quadrupole part) are thin lenses of the same integrated strength
+    (Sec. 3.5) between two drifts of half their length."""
+    out = dict(ring)
+    els = []
+    for e in ring["elements"]:
+        if e["type"] == "mult" and e["k1"] == 0.0 and e["L"] > 0.0:
+            half = element("drift", L=0.5 * e["L"], name=e["name"] + "_d")
+            els += [half, element("thin_mult", n_slices=e["n_slices"], k2=e["k2"] * e["L"], name=e["name"]),
+                    dict(half)]
+        else:
+            els.append(dict(e))
+    out["elements"] = els
+    out["name"] = ring["name"] + "_thin_sext"
     return out
 
 
