@@ -87,6 +87,16 @@ extern "C" {
                            field-free curved frame.  The paper's comparison integrator:
                            less accurate than ST_SBEND at any slice count.  FP64 only. */
 
+#define ST_THIN_MULT 8  /* thin lens, Sec. 3.5: the ST_MULT multipole in the limit of zero
+                           length at fixed integrated strengths, k1 = integrated quadrupole
+                           strength k1 L [m^-1], k2 = integrated sextupole strength k2 L
+                           [m^-2], L = 0.  Orbit: the kick of the integrated field (positions,
+                           T and Pt unchanged).  Spin: sampled along the kick, n_slices
+                           partial kicks of 1/n_slices each with Omega (Eq. (6b)) of the
+                           integrated field at their edges, then the chosen spin scheme,
+                           as for any element.  No fringe kicks, second-order only; FP64
+                           only.                                                        */
+
 /* ---- spin integration schemes (spin_order arguments) ------------------ */
 /* spin_order 0..4 is the number of Romberg iterations over slice-edge
  * samples.  Two negative values select the piece-wise constant rotation
@@ -113,8 +123,8 @@ typedef struct st_ctx st_ctx;           /* opaque; particle state on the device 
 /* One beamline element.  Units: metres, radians; k1 = b2/(B rho) [m^-2],
  * k2 = B''/(B rho) [m^-3] (MAD convention).  n_slices is the number of
  * integration slices of a spin-carrying element (ST_MULT, ST_QUAD_MK,
- * ST_SBEND, ST_SOLENOID, ST_RBEND, ST_TEAPOT) and must be a multiple of
- * 2^spin_order at st_track time (Romberg orders). */
+ * ST_SBEND, ST_SOLENOID, ST_RBEND, ST_TEAPOT, ST_THIN_MULT) and must be a
+ * multiple of 2^spin_order at st_track time (Romberg orders). */
 typedef struct {
     int32_t type;
     int32_t n_slices;

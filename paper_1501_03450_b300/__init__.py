@@ -22,13 +22,13 @@ from . import _build
 LIB_PATH = os.environ.get("SPINTRACK_LIB", _build.LIB)
 
 ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ESTATE = 0, -1, -2, -3, -4, -5
-ST_DRIFT, ST_MULT, ST_QUAD_MK, ST_SBEND, ST_SNAKE, ST_SOLENOID, ST_RBEND, ST_TEAPOT = 0, 1, 2, 3, 4, 5, 6, 7
+ST_DRIFT, ST_MULT, ST_QUAD_MK, ST_SBEND, ST_SNAKE, ST_SOLENOID, ST_RBEND, ST_TEAPOT, ST_THIN_MULT = range(9)
 ST_FP64, ST_MIXED = 0, 1
 # spin_order values of the midpoint schemes (0..4 are Romberg orders)
 ST_SPIN_MID_HALF, ST_SPIN_MID_KICK = -1, -2
 
 TYPE_CODES = {"drift": ST_DRIFT, "mult": ST_MULT, "quad_mk": ST_QUAD_MK, "sbend": ST_SBEND, "snake": ST_SNAKE,
-              "solenoid": ST_SOLENOID, "rbend": ST_RBEND, "teapot": ST_TEAPOT}
+              "solenoid": ST_SOLENOID, "rbend": ST_RBEND, "teapot": ST_TEAPOT, "thin_mult": ST_THIN_MULT}
 PRECISIONS = {"fp64": ST_FP64, "mixed": ST_MIXED}
 
 

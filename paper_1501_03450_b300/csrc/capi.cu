@@ -27,15 +27,21 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 bool is_spin_type(int t) {
-    return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND || t == ST_SOLENOID || t == ST_RBEND || t == ST_TEAPOT;
+    return t == ST_MULT || t == ST_QUAD_MK || t == ST_SBEND || t == ST_SOLENOID || t == ST_RBEND || t == ST_TEAPOT ||
+           t == ST_THIN_MULT;
 }
 
 // Field checks of one element (every entry point that takes elements):
 // nullptr if valid, else what is wrong.
 const char* element_error(const st_element& e) {
-    if (e.type < ST_DRIFT || e.type > ST_TEAPOT) return "unknown type";
-    if (is_spin_type(e.type) && (!(e.L > 0.0) || e.n_slices < 1 || e.n_slices > 4096))
+    if (e.type < ST_DRIFT || e.type > ST_THIN_MULT) return "unknown type";
+    if (e.type == ST_THIN_MULT) {
+        if (e.L != 0.0 || e.n_slices < 1 || e.n_slices > 4096 || !std::isfinite(e.k1) || !std::isfinite(e.k2))
+            return "thin lens needs L = 0, finite integrated strengths and 1 <= n_slices <= 4096";
+        if (e.fringe || e.split_order == 4) return "thin lens has no fringe kicks and no fourth-order map";
+    } else if (is_spin_type(e.type) && (!(e.L > 0.0) || e.n_slices < 1 || e.n_slices > 4096)) {
         return "spin-carrying element needs L > 0 and 1 <= n_slices <= 4096";
+    }
     if (e.fringe != 0 && e.fringe != 1) return "fringe must be 0 or 1";
     if (e.fringe && (e.type == ST_DRIFT || e.type == ST_SNAKE))
         return "fringe kicks need a multipole, quadrupole, bend or solenoid";
@@ -77,6 +83,12 @@ DevElem pack_element(const st_element& e) {
         d.ds = e.L / e.n_slices;
         d.a[0] = e.k1;
         d.a[1] = std::fabs(e.k1);
+        break;
+    case ST_THIN_MULT:
+        // integrated strengths; the slice is 1/N of the unit kick parameter
+        d.ds = 1.0 / e.n_slices;
+        d.a[0] = e.k1;
+        d.a[1] = e.k2;
         break;
     case ST_TEAPOT:
         // curvature and field ratio; the second-order slice's curved drift
@@ -202,8 +214,9 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
         }
         seq[i] = (uint16_t)idx;
         if (d.type == ST_SOLENOID || d.flags) L.fp64_only = true;
-        if ((d.flags & ST_ELEM_ORDER4) || d.type == ST_RBEND || d.type == ST_TEAPOT) L.has_ext = true;
-        if (d.type == ST_RBEND || d.type == ST_TEAPOT) L.fp64_only = true;
+        if ((d.flags & ST_ELEM_ORDER4) || d.type == ST_RBEND || d.type == ST_TEAPOT || d.type == ST_THIN_MULT)
+            L.has_ext = true;
+        if (d.type == ST_RBEND || d.type == ST_TEAPOT || d.type == ST_THIN_MULT) L.fp64_only = true;
         if (d.flags & ST_ELEM_ORDER4) L.has_order4 = true;
         if (is_spin_type(d.type)) {
             max_slices = std::max(max_slices, (int)d.n_slices);

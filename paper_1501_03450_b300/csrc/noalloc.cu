@@ -143,7 +143,8 @@ extern "C" int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, c
         L.table_bytes = table_bytes;
         L.seq_offset = table_bytes;
         for (int u = 0; u < n_unique; ++u)
-            if ((table[u].flags & ST_ELEM_ORDER4) || table[u].type == ST_RBEND || table[u].type == ST_TEAPOT)
+            if ((table[u].flags & ST_ELEM_ORDER4) || table[u].type == ST_RBEND || table[u].type == ST_TEAPOT ||
+                table[u].type == ST_THIN_MULT)
                 L.has_ext = true;
         st_ctx ctx;
         ctx.lat = &lat;

@@ -35,6 +35,7 @@ static_assert(sizeof(DevElem) == 64, "DevElem must be 64 bytes");
 //   ST_SNAKE   : a0..a3 = unit quaternion (scalar first)
 //   ST_RBEND   : a0 = b1/(B rho), a1 = phi_entr, a2 = -phi_exit, a3 = X offset,
 //                a4 = arc length of the reference orbit
+//   ST_THIN_MULT: a0 = k1 L, a1 = k2 L (integrated), ds = 1/n_slices
 //   ST_TEAPOT  : a0 = h, a1 = eta; second-order slice: a2 = ds/2 (curved
 //                drifts), a4 = ds (kick); fourth-order: a2..a5 as ST_MULT's
 
@@ -122,7 +123,7 @@ struct LatticeImpl {
     int32_t max_slices;
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
     bool fp64_only = false;        // solenoids, fringe spin kicks or fourth-order maps: FP64 only
-    bool has_ext = false;          // fourth-order slice maps, rectangular or TEAPOT bends present
+    bool has_ext = false;          // fourth-order slice maps, rectangular or TEAPOT bends or thin lenses present
     bool has_order4 = false;       // fourth-order slice maps present
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]
     void* d_blob = nullptr;

@@ -500,9 +500,9 @@ __device__ __forceinline__ void store_particle(const Particle& p, double sx, dou
 }
 
 // EXT: compile the extended element set in (fourth-order slice maps,
-// rectangular and TEAPOT bends; a separate instantiation, chosen only for
-// lattices that use them, so that the common tracking loop keeps its register
-// budget).
+// rectangular and TEAPOT bends, thin lenses; a separate instantiation, chosen
+// only for lattices that use them, so that the common tracking loop keeps its
+// register budget).
 template <int K, bool SPIN = true, bool EXT = false>
 __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ table, const uint16_t* __restrict__ seq,
                                                     int n_seq, const RefConst& ref, double2* __restrict__ xpx,
@@ -761,6 +761,29 @@ __device__ __forceinline__ void fp64_track_particle(const DevElem* __restrict__ 
                 if constexpr (SPIN) q_x = qmul(quat_about_y(el.a[2]), q_x);
                 p.T += el.a[4] * ref.inv_beta0;
                 if (!ok) p.X = __longlong_as_double(0x7ff8000000000000LL);   // quiet NaN
+              } else if (type == ST_THIN_MULT) {
+                // Sec. 3.5: the multipole's slices without their drifts, in the
+                // unit kick parameter (ds = 1/N, integrated strengths a0, a1)
+                const double k1 = el.a[0], k2 = el.a[1];
+                double pp = p.Px * p.Px + p.Py * p.Py;
+                double ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                double Ps = (pc.P2 - pp) * ips;
+                if constexpr (SPIN) {
+                    precession(p, pc, k1 * p.Y + k2 * p.X * p.Y, k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y), 0.0,
+                               ips, Ps, ox, oy, os);
+                    lv.add_edge(0, N, ds, ox, oy, os);
+                }
+                for (int s = 1; s <= N; ++s) {
+                    mult_kick(p, k1, k2, ds);
+                    pp = p.Px * p.Px + p.Py * p.Py;
+                    ips = inv_sqrt_diff(pc.P2, pc.invP, pc.invP2, pp);
+                    Ps = (pc.P2 - pp) * ips;
+                    if constexpr (SPIN) {
+                        precession(p, pc, k1 * p.Y + k2 * p.X * p.Y, k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y),
+                                   0.0, ips, Ps, ox, oy, os);
+                        lv.add_edge(s, N, ds, ox, oy, os);
+                    }
+                }
               } else if (type == ST_TEAPOT) {
                 // Sec. 3.6: curved drift, kick, curved drift per slice (or
                 // Yoshida's composition D K D' K0 D' K D of it); Omega at the

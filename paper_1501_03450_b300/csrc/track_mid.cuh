@@ -45,7 +45,7 @@ __device__ __forceinline__ bool sbend_step(Particle& p, const PConst& pc, const 
 }
 
 // Precession vector at the current state of element el (Eq. (6b)): transverse
-// field of a multipole or quadrupole, vertical field eta h with curvature h in
+// field of a multipole, quadrupole or thin lens (per unit kick parameter), vertical field eta h with curvature h in
 // sector and TEAPOT bends, b1/(B rho) in a rectangular bend's straight frame.
 // Returns false if Ps^2 <= 0.
 __device__ __forceinline__ bool mid_omega(const DevElem& el, int type, const Particle& p, const PConst& pc,
@@ -61,7 +61,7 @@ __device__ __forceinline__ bool mid_omega(const DevElem& el, int type, const Par
     } else if (type == ST_RBEND) {
         by = el.a[0];
     } else {
-        const double k1 = el.a[0], k2 = type == ST_MULT ? el.a[1] : 0.0;
+        const double k1 = el.a[0], k2 = (type == ST_MULT || type == ST_THIN_MULT) ? el.a[1] : 0.0;
         bx = k1 * p.Y + k2 * p.X * p.Y;
         by = k1 * p.X + 0.5 * k2 * (p.X * p.X - p.Y * p.Y);
     }
@@ -205,6 +205,14 @@ __device__ __forceinline__ void fp64_track_particle_mid(const DevElem* __restric
                         ok = (pc.P2 - pp > 0.0) && ok;
                         if (!KICK || half == 1) dkd_drift(p, pc, ref, rsqrt(pc.P2 - pp), dl);
                     }
+                }
+            } else if (type == ST_THIN_MULT) {
+                // thin lens: half of the slice's partial kick on each side
+                for (int s = 0; s < N; ++s) {
+                    mult_kick(p, el.a[0], el.a[1], hd);
+                    ok = mid_omega(el, type, p, pc, ox, oy, os) && ok;
+                    qe = qmul(quat_from_rotvec(ds * ox, ds * oy, ds * os), qe);
+                    mult_kick(p, el.a[0], el.a[1], hd);
                 }
             } else if (type == ST_QUAD_MK) {
                 // KICK: L(ds/2) N(ds/2) | N(ds/2) L(ds/2); half-slices:

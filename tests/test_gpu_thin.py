@@ -1,0 +1,120 @@
+"""GPU parity of the thin lens (Sec. 3.5): the CUDA FP64 tracker through the C
+ABI against the CPU oracle on the same seeded inputs, every coordinate and
+spin component at 1e-11: single thin lenses at every Romberg order and both
+midpoint schemes, the RHIC-like ring with thin sextupoles, batched jobs and
+the allocation-free entry, lost particles, validation and the mixed
+tracker's refusal."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1501_03450_b300 as st
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+def compare(ring, z, S, turns, K, tol=TOL):
+    zg, Sg, lg = st.track(ring, z, S, turns, K)
+    zo, So, lo = oracle.track(ring, z, S, turns, K)
+    assert np.array_equal(lg, lo)
+    dz = np.abs(zg - zo).max(axis=1)
+    ds = np.abs(Sg - So).max()
+    assert dz.max() < tol and ds < tol, (dz, ds)
+    return zg, Sg, lg
+
+
+def toy_with_thin_lenses(gg):
+    """The toy ring with a thin sextupole-quadrupole lens in the middle of
+    every drift after a quadrupole."""
+    ring = W.toy_ring(gg)
+    els = []
+    for e in ring["elements"]:
+        if e["type"] == "drift" and els and els[-1]["type"] == "mult":
+            half = dict(e, L=0.5 * e["L"])
+            sgn = 1.0 if els[-1]["k1"] > 0 else -1.0
+            els += [half, W.element("thin_mult", n_slices=4, k1=0.002 * sgn, k2=0.3 * sgn), dict(half)]
+        else:
+            els.append(dict(e))
+    return dict(ring, elements=els, name="toy_thin_lenses")
+
+
+@pytest.mark.parametrize("gg", [45.5, 487.0])
+@pytest.mark.parametrize("K", [0, 1, 2, 3, st.ST_SPIN_MID_HALF, st.ST_SPIN_MID_KICK])
+def test_single_thin_lens(gg, K):
+    el = W.element("thin_mult", n_slices=8, k1=0.05, k2=2.0)
+    z, S = W.gaussian_particles(257, gg, seed=300 + K, sigmas=dict(x=3e-3, y=3e-3, px=3e-4, py=3e-4))
+    zg, Sg, _ = compare(W.single_element_ring(el, gg), z, S, 10, K)
+    assert np.array_equal(zg[[0, 2, 4, 5]], z[[0, 2, 4, 5]])        # positions, T, Pt untouched
+    assert np.abs(Sg - S).max() > 1e-6
+
+
+@pytest.mark.parametrize("K", [2, st.ST_SPIN_MID_KICK])
+def test_toy_ring_with_thin_lenses(K):
+    ring = toy_with_thin_lenses(45.5)
+    z, S = W.gaussian_particles(500, 45.5, seed=41)
+    compare(ring, z, S, 50, K)
+
+
+def test_rhic_like_ring_with_thin_sextupoles():
+    ring = W.with_spin_order(W.with_thin_sextupoles(W.rhic_like_ring(45.5)), 2)
+    z, S = W.gaussian_particles(200, 45.5, seed=42)
+    compare(ring, z, S, 3, 2)
+
+
+def test_thin_lenses_in_batched_jobs_and_the_allocation_free_entry():
+    import torch
+    rings = [toy_with_thin_lenses(45.5), W.with_thin_sextupoles(W.rhic_like_ring(300.0, n_cells=6))]
+    ns = [200, 90]
+    b = st.Batch(rings, ns, "fp64")
+    inputs = []
+    for k, (ring, n) in enumerate(zip(rings, ns)):
+        z, S = W.gaussian_particles(n, ring["Ggamma0"], seed=90 + k)
+        b.upload(k, z, S)
+        inputs.append((z, S))
+    b.track(4, 2)
+    for k, (ring, (z, S)) in enumerate(zip(rings, inputs)):
+        zb, Sb, lb = b.download(k)
+        zo, So, lo = oracle.track(ring, z, S, 4, 2)
+        assert np.array_equal(lb, lo)
+        assert np.abs(zb - zo).max() < TOL and np.abs(Sb - So).max() < TOL
+    b.close()
+    ring = rings[0]
+    z, S = inputs[0]
+    n = z.shape[1]
+    state = torch.from_numpy(st.pairs_from_soa(z, S)).to("cuda")
+    lost = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    st.st_track_fp64_noalloc(ring["elements"], ring["G"], ring["Ggamma0"], state.data_ptr(), lost.data_ptr(), n, 5,
+                             2, torch.cuda.current_stream().cuda_stream)
+    za, Sa = st.soa_from_pairs(state.cpu().numpy(), n)
+    zo, So, lo = oracle.track(ring, z, S, 5, 2)
+    assert np.array_equal(lost.cpu().numpy(), lo)
+    assert np.abs(za - zo).max() < TOL and np.abs(Sa - So).max() < TOL
+
+
+def test_lost_in_a_thin_lens_keeps_entrance_state():
+    gg = 45.5
+    ring = toy_with_thin_lenses(gg)
+    ring["elements"] = [e for e in ring["elements"] if e["type"] == "thin_mult"][:1] + ring["elements"]
+    z, S = W.gaussian_particles(40, gg, seed=5)
+    # at X = 2 m the lens kicks Px by about -0.6: from -0.9 past -1, so Ps
+    # turns imaginary inside the first thin lens
+    z[0, 11], z[1, 11], z[5, 11] = 2.0, -0.9, 0.0
+    zg, Sg, lg = compare(ring, z, S, 2, 2)
+    assert lg[11] == 1 and lg.sum() == 1
+    assert np.array_equal(zg[:, 11], z[:, 11]) and np.array_equal(Sg[:, 11], S[:, 11])
+
+
+def test_thin_lens_validation_and_mixed_rejection():
+    ring = toy_with_thin_lenses(45.5)
+    lat = st.Lattice(ring)
+    with pytest.raises(st.SpinTrackError):
+        st.Tracker(lat, 64, precision="mixed")
+    st.Tracker(lat, 64).close()
+    lat.close()
+    for bad in (dict(L=0.1), dict(fringe=1), dict(split_order=4)):
+        el = dict(W.element("thin_mult", n_slices=4, k2=1.0), **bad)
+        with pytest.raises(st.SpinTrackError):
+            st.Lattice(W.single_element_ring(el, 45.5))
