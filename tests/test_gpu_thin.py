@@ -66,7 +66,7 @@ def test_rhic_like_ring_with_thin_sextupoles():
 
 def test_thin_lenses_in_batched_jobs_and_the_allocation_free_entry():
     import torch
-    rings = [toy_with_thin_lenses(45.5), W.with_thin_sextupoles(W.rhic_like_ring(300.0, n_cells=6))]
+    rings = [toy_with_thin_lenses(45.5), W.with_spin_order(W.with_thin_sextupoles(W.rhic_like_ring(300.0, n_cells=6)), 2)]
     ns = [200, 90]
     b = st.Batch(rings, ns, "fp64")
     inputs = []
