@@ -327,6 +327,33 @@ int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, const st_ref
                           double* state, uint8_t* lost, int64_t n_particles, int32_t n_turns,
                           int32_t spin_order, void* cuda_stream);
 
+/* Slice-count tuner (Sec. 5.2.1, 5.3: the paper picks n_b and the Romberg
+ * order against a finely sliced reference).  For a sample ensemble (z_soa
+ * [6][n], spin_soa [3][n], host memory) every candidate discretisation --
+ * every spin-carrying element cut into n_b = 1, 2, 4, ..., ST_TUNE_MAX_SLICES
+ * slices, Romberg order K = 0 .. min(ST_TUNE_MAX_ORDER, log2 n_b) -- is
+ * tracked for one turn by the FP64 tracker from the same state, its one-turn
+ * Delta S of Sec. 5.3 (mean |S - S_ref| over the particles not lost) against
+ * the reference (n_b = ST_TUNE_REF_SLICES, K = ST_TUNE_REF_ORDER) is measured,
+ * and its turn is timed with CUDA events.  Returns the fastest candidate with
+ * Delta S <= spin_error_bound (the reference itself if none is).  Outputs:
+ * *n_slices_out, *spin_order_out (required); *dS_out, *ms_out,
+ * *n_candidates_out (may be NULL); table_out (may be NULL) receives one row
+ * (n_b, K, Delta S, ms) per candidate, at most ST_TUNE_MAX_CANDIDATES rows.
+ * The elements' own n_slices are ignored.  Creates and destroys its own
+ * lattices and contexts on the current device; synchronous.  Errors:
+ * ST_EINVAL (NULL, n < 1, bound <= 0, invalid element, a lattice that the
+ * FP64 tracker refuses), ST_ENOMEM, ST_ECUDA. */
+#define ST_TUNE_MAX_SLICES     64
+#define ST_TUNE_MAX_ORDER      3
+#define ST_TUNE_REF_SLICES     128
+#define ST_TUNE_REF_ORDER      3
+#define ST_TUNE_MAX_CANDIDATES 22
+int st_tune_slicing(const st_element* elems, int32_t n_elems, const st_reference* ref, const double* z_soa,
+                    const double* spin_soa, int64_t n_particles, double spin_error_bound, int32_t* n_slices_out,
+                    int32_t* spin_order_out, double* dS_out, float* ms_out, int32_t* n_candidates_out,
+                    double* table_out);
+
 /* BF16 tensor-core GEMM (tcgen05, TMA-fed, FP32 accumulation in tensor
  * memory): D[M][N] = A[M][K] . B[N][K]^T (+ bias[N] if bias != NULL).  All
  * pointers are device memory: A, B bf16 row-major, D and bias FP32; M a

@@ -69,6 +69,10 @@ SIGNATURES = {
     "st_measure_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "st_track_fp64_noalloc": ([ctypes.POINTER(StElement), ctypes.c_int32, ctypes.POINTER(StReference), _VP, _VP,
                                ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _VP], ctypes.c_int),
+    "st_tune_slicing": ([ctypes.POINTER(StElement), ctypes.c_int32, ctypes.POINTER(StReference), _VP, _VP,
+                         ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
+                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32), _VP], ctypes.c_int),
     "st_batch_create": ([ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.c_int32, _VP,
                          ctypes.POINTER(_VP)], ctypes.c_int),
     "st_batch_destroy": ([_VP], ctypes.c_int),
@@ -221,6 +225,26 @@ def st_track_fp64_noalloc(elements: List[Dict], G: float, Ggamma0: float, state_
     ref = StReference(G, Ggamma0)
     _check(load().st_track_fp64_noalloc(arr, len(elements), ctypes.byref(ref), state_ptr, lost_ptr,
                                         int(n_particles), int(n_turns), int(spin_order), stream))
+
+
+ST_TUNE_MAX_SLICES, ST_TUNE_MAX_ORDER, ST_TUNE_REF_SLICES, ST_TUNE_REF_ORDER, ST_TUNE_MAX_CANDIDATES = 64, 3, 128, 3, 22
+
+
+def st_tune_slicing(ring: Dict, z: np.ndarray, S: np.ndarray, spin_error_bound: float) -> Dict:
+    """Fastest (n_b, Romberg order) whose one-turn spin error on the sample
+    (z [6, n], S [3, n]) stays within the bound (see the header).  Returns
+    dict(n_slices, spin_order, dS, ms, table) with table rows (n_b, K, dS, ms)."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    arr = elements_array(ring["elements"])
+    ref = StReference(ring["G"], ring["Ggamma0"])
+    nb, K, nc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    dS, ms = ctypes.c_double(), ctypes.c_float()
+    table = np.zeros((ST_TUNE_MAX_CANDIDATES, 4), np.float64)
+    _check(load().st_tune_slicing(arr, len(ring["elements"]), ctypes.byref(ref), z.ctypes.data, S.ctypes.data,
+                                  z.shape[1], float(spin_error_bound), ctypes.byref(nb), ctypes.byref(K),
+                                  ctypes.byref(dS), ctypes.byref(ms), ctypes.byref(nc), table.ctypes.data))
+    return dict(n_slices=nb.value, spin_order=K.value, dS=dS.value, ms=ms.value, table=table[:nc.value])
 
 
 def st_batch_create(lattice_handles: List[int], n_particles: List[int], precision: int = ST_FP64,
