@@ -118,3 +118,30 @@ def test_thin_lens_validation_and_mixed_rejection():
         el = dict(W.element("thin_mult", n_slices=4, k2=1.0), **bad)
         with pytest.raises(st.SpinTrackError):
             st.Lattice(W.single_element_ring(el, 45.5))
+
+
+@pytest.mark.parametrize("K", [0, 4, st.ST_SPIN_MID_KICK])
+def test_extreme_slice_counts(K):
+    """One slice everywhere (midpoint and trapezoid) and the largest slice
+    count of the boundary (4096) on a thin lens, a TEAPOT bend and a
+    multipole.  The oracle's TEAPOT bend rounds X to about an ulp of 1/h in
+    each of its 8192 printed-form curved drifts (1.4e-11 from its long-double
+    build here), so that element is held to the long-double oracle as closely
+    as the FP64 oracle is."""
+    gg = 45.5
+    z, S = W.gaussian_particles(64, gg, seed=12)
+    if K in (0, st.ST_SPIN_MID_KICK):
+        ring = W.with_slices(toy_with_thin_lenses(gg), 1)
+        compare(ring, z, S, 5, K)
+        compare(W.with_slices(W.drift_kick_ring(W.toy_ring(gg)), 1), z, S, 3, K)
+    for el in (W.element("thin_mult", n_slices=4096, k1=0.02, k2=1.0),
+               W.element("mult", L=0.5, n_slices=4096, k1=0.1, k2=2.0)):
+        compare(W.single_element_ring(el, gg), z, S, 1, K)
+    ring = W.single_element_ring(W.element("teapot", L=3.0, n_slices=4096, angle=0.2), gg)
+    zg, Sg, lg = st.track(ring, z, S, 1, K)
+    zo, So, lo = oracle.track(ring, z, S, 1, K)
+    zx, Sx, lx = oracle.track(ring, z, S, 1, K, variant="f80")
+    zx, Sx = zx.astype(np.float64), Sx.astype(np.float64)
+    assert np.array_equal(lg, lx) and np.array_equal(lo, lx)
+    assert np.abs(zg - zx).max() < 2.0 * np.abs(zo - zx).max() + 1e-14
+    assert np.abs(Sg - Sx).max() < 2.0 * np.abs(So - Sx).max() + 1e-13
