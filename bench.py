@@ -90,7 +90,10 @@ def parse_args():
     ap.add_argument("--profile-train", type=int, default=0, metavar="STEPS",
                     help="profiling mode: only train the spin-map network for STEPS steps on 32768-row batches "
                          "(pairs from 4000 particles x 10 turns) and print the step time")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.precision == "mixed" and (args.ring != "rhic_like" or args.spin_order < 0):
+        ap.error("the mixed-precision tracker runs the bend-kick ring with a Romberg order only")
+    return args
 
 
 def profile_train(args):
