@@ -21,13 +21,13 @@ namespace st {
 // Exact sector-bend map over len (Eq. (10)) for the midpoint tracker, in the
 // rotation form of the Romberg tracker: (Px, A = Ps - eta (1 + hX)) turns by
 // h len (cb, sb = its cos, sin); X from Ps_f - A_f = eta (1 + h X_f).
-// Returns false if Ps^2 <= 0 at either end.
+// P_a^2 = P^2 - Py^2 is a constant of the bend (Eq. (8)), so Pa2 and 1/Pa2
+// come from the caller, and Ps (in: at the entrance, out: at the exit) is
+// carried from step to step.  Returns false if Ps^2 <= 0 at the exit.
 __device__ __forceinline__ bool sbend_step(Particle& p, const PConst& pc, const RefConst& ref, double h, double eta,
-                                           double ieh, double ieta, double cb, double sb, double len) {
-    const double Pa2 = pc.P2 - p.Py * p.Py;
-    const double qi = Pa2 - p.Px * p.Px;
-    if (!(qi > 0.0)) return false;
-    const double Psi = sqrt(qi);
+                                           double ieh, double ieta, double cb, double sb, double len, double Pa2,
+                                           double iPa2, double& Ps) {
+    const double Psi = Ps;
     const double A = Psi - eta * fma(h, p.X, 1.0);
     const double Pxi = p.Px;
     const double Pxf = Pxi * cb + A * sb;
@@ -35,12 +35,21 @@ __device__ __forceinline__ bool sbend_step(Particle& p, const PConst& pc, const 
     const double qf = Pa2 - Pxf * Pxf;
     if (!(qf > 0.0)) return false;
     const double Psf = sqrt(qf);
-    // asin(Px_i/P_a) - asin(Px_f/P_a) = asin((Px_i Ps_f - Px_f Ps_i)/P_a^2)
-    const double dpsi = asin((Pxi * Psf - Pxf * Psi) / Pa2);
+    // asin(Px_i/P_a) - asin(Px_f/P_a) = asin((Px_i Ps_f - Px_f Ps_i)/P_a^2),
+    // by its Taylor series when small (truncation < 1e-21 relative)
+    const double sd = (Pxi * Psf - Pxf * Psi) * iPa2;
+    double dpsi;
+    if ((__double2hiint(sd) & 0x7fffffff) < 0x3f847ae1) {   // |sd| < 1e-2, integer test
+        const double x2 = sd * sd;
+        dpsi = sd * fma(x2, fma(x2, fma(x2, fma(x2, 35.0 / 1152.0, 5.0 / 112.0), 3.0 / 40.0), 1.0 / 6.0), 1.0);
+    } else {
+        dpsi = asin(sd);
+    }
     p.X = (Psf - eta - Af) * ieh;
     p.Px = Pxf;
     p.Y += ieta * p.Py * len + ieh * p.Py * dpsi;
     p.T += -ieta * pc.Pt * len + (1.0 - ieta) * len * ref.inv_beta0 - ieh * pc.b0pt * dpsi;
+    Ps = Psf;
     return true;
 }
 
@@ -167,11 +176,16 @@ __device__ __forceinline__ void fp64_track_particle_mid(const DevElem* __restric
                 const double h = el.a[0], eta = el.a[1], ieh = el.a[4], ieta = el.a[5];
                 double sb, cb;
                 sincos(h * hd, &sb, &cb);
-                for (int s = 0; s < N; ++s) {
-                    ok = sbend_step(p, pc, ref, h, eta, ieh, ieta, cb, sb, hd) && ok;
-                    ok = mid_omega(el, type, p, pc, ox, oy, os) && ok;
+                const double Pa2 = pc.P2 - p.Py * p.Py, iPa2 = 1.0 / Pa2;
+                const double qi = Pa2 - p.Px * p.Px;
+                ok = qi > 0.0;
+                double Ps = sqrt(qi);
+                for (int s = 0; s < N && ok; ++s) {
+                    ok = sbend_step(p, pc, ref, h, eta, ieh, ieta, cb, sb, hd, Pa2, iPa2, Ps);
+                    // Omega (Eq. (6b)) with the bend's field and curvature
+                    precession(p, pc, 0.0, eta * h, h, 1.0 / Ps, Ps, ox, oy, os);
                     qe = qmul(quat_from_rotvec(ds * ox, ds * oy, ds * os), qe);
-                    ok = sbend_step(p, pc, ref, h, eta, ieh, ieta, cb, sb, hd) && ok;
+                    ok = ok && sbend_step(p, pc, ref, h, eta, ieh, ieta, cb, sb, hd, Pa2, iPa2, Ps);
                 }
             } else if (type == ST_TEAPOT) {
                 // KICK: D(ds/2) K(ds/2) | K(ds/2) D(ds/2); half-slices:
