@@ -14,7 +14,9 @@ def _mixed_ring():
     ring = W.with_fringes(W.with_split_order(W.with_spin_order(W.toy_ring(45.5, n_cells=2), 2), 4))
     ring["elements"] += [W.element("solenoid", L=2.0, n_slices=4, k1=0.05),
                          W.element("rbend", L=2.5, n_slices=4, angle=0.05, e1=0.01, fringe=1),
-                         W.element("snake", snake_phi=0.7, snake_mu=np.pi)]
+                         W.element("snake", snake_phi=0.7, snake_mu=np.pi),
+                         W.element("teapot", L=3.0, n_slices=4, angle=0.05, eta=0.99, split_order=4),
+                         W.element("thin_mult", n_slices=4, k1=0.01, k2=0.4)]
     return ring
 
 
