@@ -1,0 +1,77 @@
+"""The paper's statements about orbital errors (Sec. 5.1, Figs. oneTurnErrsX
+and xErrVsTurnNo) as checks on a tracker, `track(ring, z, S, n_turns,
+spin_order)` returning (z, S, lost): the oracle or the CUDA library.  The
+reference runs are the oracle's.  The ring is the RHIC-scale ring with thin
+sextupoles (Sec. 3.5), whose thin kicks are exact at any slicing, so the
+bend-kick / matrix-kick errors are those of the matrix-kick split alone;
+its drift-kick version has TEAPOT bends and drift-kick-drift quadrupoles."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+import workloads as W
+
+GG = 45.5
+
+
+def rings():
+    base = W.with_thin_sextupoles(W.rhic_like_ring(GG))
+    return base, W.drift_kick_ring(base)
+
+
+def relative_dX(zx, zref):
+    """Delta X of Sec. 5.1 (rms over the bunch of X - X_ref) relative to the
+    rms of X_ref."""
+    return float(np.sqrt(np.mean((zx[0] - zref[0]) ** 2)) / np.sqrt(np.mean(zref[0] ** 2)))
+
+
+def check_one_turn_errors(track, n_particles=64):
+    """Fig. oneTurnErrsX: one-turn Delta X(1; n_b) against bend-kick /
+    matrix-kick with n_b = 128.  Both integrators converge as n_b^-2; drift-kick
+    starts at a relative error of order one and reaches about a part in 1e4 at
+    n_b = 64; bend-kick / matrix-kick starts below a part in 1e6 and falls
+    below a part in 1e9."""
+    base, dk = rings()
+    z, S = W.gaussian_particles(n_particles, GG, seed=9)
+    zr, _, lr = oracle.track(W.with_slices(base, 128), z, S, 1, 0)
+    assert not lr.any()
+    err = {}
+    for name, ring in (("dk", dk), ("bk", base)):
+        for nb in (1, 2, 4, 8, 16, 32, 64):
+            z1, _, l1 = track(W.with_slices(ring, nb), z, S, 1, 0)
+            assert not l1.any()
+            err[(name, nb)] = relative_dX(z1, zr)
+    assert err[("dk", 1)] > 0.1
+    assert 0.5e-4 < err[("dk", 64)] < 5e-4
+    assert all(3.5 < err[("dk", nb)] / err[("dk", 2 * nb)] < 4.5 for nb in (4, 8, 16, 32))
+    assert err[("bk", 1)] < 1e-6
+    assert min(err[("bk", nb)] for nb in (32, 64)) < 1e-9
+    assert all(3.3 < err[("bk", nb)] / err[("bk", 2 * nb)] < 4.5 for nb in (2, 4, 8))
+    return err
+
+
+def check_errors_over_turns(track, turns=30, n_particles=64):
+    """Fig. xErrVsTurnNo, against bend-kick / matrix-kick with n_b = 16: at
+    every turn drift-kick with n_b = 8 (no tune fit) lies far above
+    bend-kick / matrix-kick with n_b = 1, which lies above n_b = 4; the
+    drift-kick error oscillates (it falls again at some turns) because of its
+    tune error."""
+    base, dk = rings()
+    z, S = W.gaussian_particles(n_particles, GG, seed=9)
+    ref = W.with_slices(base, 16)
+    runs = {"dk8": W.with_slices(dk, 8), "bk1": W.with_slices(base, 1), "bk4": W.with_slices(base, 4)}
+    state = {k: z for k in runs}
+    zr = z
+    hist = []
+    for _ in range(turns):
+        zr, _, _ = oracle.track(ref, zr, S, 1, 0)
+        row = {}
+        for k, ring in runs.items():
+            state[k], _, lk = track(ring, state[k], S, 1, 0)
+            assert not lk.any()
+            row[k] = relative_dX(state[k], zr)
+        assert row["dk8"] > 1e3 * row["bk1"] > 1e3 * row["bk4"], row
+        hist.append(row["dk8"])
+    assert any(hist[i + 1] < hist[i] for i in range(turns - 1))
+    return hist
