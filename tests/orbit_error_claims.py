@@ -75,3 +75,28 @@ def check_errors_over_turns(track, turns=30, n_particles=64):
         hist.append(row["dk8"])
     assert any(hist[i + 1] < hist[i] for i in range(turns - 1))
     return hist
+
+
+def check_amplitude_dependence(track, n_particles=400, bin_size=80):
+    """Fig. xErrVsAmp: one-turn errors in X binned by amplitude
+    (X^2 + (20 m Px)^2, bins of equal count) for drift-kick with n_b = 32
+    (upper curve) and bend-kick / matrix-kick with n_b = 1 (lower curve):
+    the drift-kick error lies more than 1e3 times above in every bin, and
+    the two have roughly the same amplitude dependence (their ratio varies
+    by less than a factor 5 across the bins)."""
+    base, dk = rings()
+    z, S = W.gaussian_particles(n_particles, GG, seed=13)
+    zr, _, _ = oracle.track(W.with_slices(base, 128), z, S, 1, 0)
+    zd, _, ld = track(W.with_slices(dk, 32), z, S, 1, 0)
+    zb, _, lb = track(W.with_slices(base, 1), z, S, 1, 0)
+    assert not ld.any() and not lb.any()
+    order = np.argsort(z[0] ** 2 + (20.0 * z[1]) ** 2)
+    ratios = []
+    for b in range(0, n_particles, bin_size):
+        idx = order[b:b + bin_size]
+        ed = np.sqrt(np.mean((zd[0, idx] - zr[0, idx]) ** 2))
+        eb = np.sqrt(np.mean((zb[0, idx] - zr[0, idx]) ** 2))
+        assert ed > 1e3 * eb, (b, ed, eb)
+        ratios.append(ed / eb)
+    assert max(ratios) < 5.0 * min(ratios), ratios
+    return ratios

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import paper_1501_03450_b300 as st
-from orbit_error_claims import check_errors_over_turns, check_one_turn_errors
+from orbit_error_claims import check_amplitude_dependence, check_errors_over_turns, check_one_turn_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -22,3 +22,7 @@ def test_one_turn_orbit_errors_on_the_gpu():
 
 def test_orbit_errors_over_turns_on_the_gpu():
     check_errors_over_turns(st.track)
+
+
+def test_orbit_error_amplitude_dependence_on_the_gpu():
+    check_amplitude_dependence(st.track)
