@@ -80,11 +80,16 @@ int build_mixed_tables(LatticeImpl& L) {
         double omr = 0.0;
         switch (d.type) {
         case ST_MULT:
+        case ST_THIN_MULT:
+            // a thin lens (Sec. 3.5) is the multipole without its drifts, in
+            // the unit kick parameter (ds = 1/N, integrated strengths)
+            m.type = ST_MULT;
             m.k1 = (float)d.a[0];
             m.k2 = (float)d.a[1];
             m.k1ds_ff = split(d.a[0] * d.ds);
             m.k2h_ff = split(0.5 * d.a[1] * d.ds);
             m.k2ds_ff = split(d.a[1] * d.ds);
+            m.dh_ff = split(d.type == ST_MULT ? 0.5 * d.ds : 0.0);
             break;
         case ST_QUAD_MK:
             m.k1 = (float)d.a[0];

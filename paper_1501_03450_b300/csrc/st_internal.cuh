@@ -99,6 +99,8 @@ struct __align__(16) MixElem {
     float2 cbm1_ff;                   // bend: cos(h ds) - 1 as (hi, lo)
     float2 dTeta_ff;                  // bend: (1 - 1/eta) ds / beta0 as (hi, lo)
     float2 rq[4];                     // reference rotation over the element (bends, snakes), (hi, lo) per component
+    float2 dh_ff;                     // multipole: half drift ds/2 as (hi, lo); thin lens: 0
+    float2 pad_;                      // keeps the size a multiple of 16 bytes
     MixWeight w[6];
 };
 static_assert(sizeof(MixElem) % 16 == 0, "MixElem must be a multiple of 16 bytes");

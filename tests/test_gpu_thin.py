@@ -2,8 +2,8 @@
 ABI against the CPU oracle on the same seeded inputs, every coordinate and
 spin component at 1e-11: single thin lenses at every Romberg order and both
 midpoint schemes, the RHIC-like ring with thin sextupoles, batched jobs and
-the allocation-free entry, lost particles, validation and the mixed
-tracker's refusal."""
+the allocation-free entry, lost particles, validation; and the mixed-precision
+tracker on thin lenses within its error budget."""
 import numpy as np
 import pytest
 
@@ -107,11 +107,45 @@ def test_lost_in_a_thin_lens_keeps_entrance_state():
     assert np.array_equal(zg[:, 11], z[:, 11]) and np.array_equal(Sg[:, 11], S[:, 11])
 
 
-def test_thin_lens_validation_and_mixed_rejection():
+def spin_err(Sa, Sb):
+    d = np.linalg.norm(Sa - Sb, axis=0)
+    return float(d.mean()), float(d.max())
+
+
+def test_mixed_tracker_with_thin_lenses_against_the_oracle():
+    """The mixed-precision tracker runs thin lenses as drift-less multipoles:
+    on the toy ring with thin lenses after 100 turns its spins stay within
+    1e-7 (mean) and 1e-6 (max) of the oracle, its transverse orbit within
+    1e-7, as on the toy ring without them."""
+    ring = toy_with_thin_lenses(45.5)
+    z, S = W.gaussian_particles(512, 45.5, seed=7)
+    zm, Sm, lm = st.track(ring, z, S, 100, 2, precision="mixed")
+    zo, So, lo = oracle.track(ring, z, S, 100, 2)
+    assert np.array_equal(lm, lo)
+    mean, mx = spin_err(Sm, So)
+    assert mean < 1e-7 and mx < 1e-6, (mean, mx)
+    assert np.abs(zm[:4] - zo[:4]).max() < 1e-7
+
+
+@pytest.mark.parametrize("gg", [45.5, 487.0])
+def test_mixed_tracker_thin_sextupole_ring_1000_turns(gg):
+    """The mixed tracker's error bound on the RHIC-like ring with thin
+    sextupoles: after 1000 turns the mean spin error over 1024 particles
+    against the FP64 tracker stays within 1e-6."""
+    ring = W.with_spin_order(W.with_thin_sextupoles(W.rhic_like_ring(gg)), 2)
+    z, S = W.gaussian_particles(1024, gg, seed=3451)
+    zm, Sm, lm = st.track(ring, z, S, 1000, 2, precision="mixed")
+    zf, Sf, lf = st.track(ring, z, S, 1000, 2, precision="fp64")
+    assert np.array_equal(lm, lf)
+    mean, mx = spin_err(Sm, Sf)
+    assert mean <= 1e-6, (mean, mx)
+    assert np.abs(zm[:4] - zf[:4]).max() < 1e-6
+
+
+def test_thin_lens_validation():
     ring = toy_with_thin_lenses(45.5)
     lat = st.Lattice(ring)
-    with pytest.raises(st.SpinTrackError):
-        st.Tracker(lat, 64, precision="mixed")
+    st.Tracker(lat, 64, precision="mixed").close()
     st.Tracker(lat, 64).close()
     lat.close()
     for bad in (dict(L=0.1), dict(fringe=1), dict(split_order=4)):
