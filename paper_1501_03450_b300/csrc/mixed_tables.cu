@@ -89,7 +89,7 @@ int build_mixed_tables(LatticeImpl& L) {
             m.k1ds_ff = split(d.a[0] * d.ds);
             m.k2h_ff = split(0.5 * d.a[1] * d.ds);
             m.k2ds_ff = split(d.a[1] * d.ds);
-            m.dh_ff = split(d.type == ST_MULT ? 0.5 * d.ds : 0.0);
+            if (d.type == ST_THIN_MULT) m.ds_ff = split(0.0);   // no drift
             break;
         case ST_QUAD_MK:
             m.k1 = (float)d.a[0];

@@ -81,7 +81,8 @@ struct __align__(16) MixElem {
     int32_t n_slices;
     float ds;                         // slice length (drift: full length)
     int32_t rho_off;                  // bends: offset (float2 units) of cos/sin(omr*i*ds), i = 0..N
-    float2 ds_ff;                     // ds as (hi, lo)
+    float2 ds_ff;                     // ds as (hi, lo); the drift length of a multipole's slice, 0 for a
+                                      // thin lens (its kicks and edge weights use ds and the *ds fields)
     float2 k1ds_ff;                   // multipole: k1 ds; matrix-kick quadrupole: |k1| (as (hi, lo))
     float k1, k2;                     // multipole / quadrupole strengths (quadrupole: k2 = |k1|)
     float cbm1, sb;                   // bend: cos(h ds) - 1, sin(h ds)
@@ -99,8 +100,6 @@ struct __align__(16) MixElem {
     float2 cbm1_ff;                   // bend: cos(h ds) - 1 as (hi, lo)
     float2 dTeta_ff;                  // bend: (1 - 1/eta) ds / beta0 as (hi, lo)
     float2 rq[4];                     // reference rotation over the element (bends, snakes), (hi, lo) per component
-    float2 dh_ff;                     // multipole: half drift ds/2 as (hi, lo); thin lens: 0
-    float2 pad_;                      // keeps the size a multiple of 16 bytes
     MixWeight w[6];
 };
 static_assert(sizeof(MixElem) % 16 == 0, "MixElem must be a multiple of 16 bytes");

@@ -580,7 +580,7 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 const float k1 = el.k1;
                 const float k2 = is_mult ? el.k2 : 0.0f;   // quadrupoles keep |k1| in el.k2
                 const FF dsff{el.ds_ff.x, el.ds_ff.y};
-                const FF half{el.dh_ff.x, el.dh_ff.y};   // half drift (0 for a thin lens)
+                const FF half{0.5f * el.ds_ff.x, 0.5f * el.ds_ff.y};   // half drift (0 for a thin lens)
                 const FF k1ds{el.k1ds_ff.x, el.k1ds_ff.y};   // quadrupoles: |k1|
                 const FF k2h{el.k2h_ff.x, el.k2h_ff.y};
                 const FF k2ds{el.k2ds_ff.x, el.k2ds_ff.y};
