@@ -179,3 +179,25 @@ def test_extreme_slice_counts(K):
     assert np.array_equal(lg, lx) and np.array_equal(lo, lx)
     assert np.abs(zg - zx).max() < 2.0 * np.abs(zo - zx).max() + 1e-14
     assert np.abs(Sg - Sx).max() < 2.0 * np.abs(So - Sx).max() + 1e-13
+
+
+def test_mixed_batch_with_thin_lenses():
+    """Thin-lens rings in one mixed-precision batch: each job within the
+    mixed tracker's budget of the oracle after 20 turns."""
+    rings = [toy_with_thin_lenses(45.5), W.with_spin_order(W.with_thin_sextupoles(W.rhic_like_ring(120.0, n_cells=6)), 2)]
+    ns = [256, 100]
+    b = st.Batch(rings, ns, "mixed")
+    inputs = []
+    for k, (ring, n) in enumerate(zip(rings, ns)):
+        z, S = W.gaussian_particles(n, ring["Ggamma0"], seed=95 + k)
+        b.upload(k, z, S)
+        inputs.append((z, S))
+    b.track(20, 2)
+    for k, (ring, (z, S)) in enumerate(zip(rings, inputs)):
+        zb, Sb, lb = b.download(k)
+        zo, So, lo = oracle.track(ring, z, S, 20, 2)
+        assert np.array_equal(lb, lo)
+        mean, mx = spin_err(Sb, So)
+        assert mean < 1e-7 and mx < 1e-6, (k, mean, mx)
+        assert np.abs(zb[:4] - zo[:4]).max() < 1e-7
+    b.close()
