@@ -142,8 +142,9 @@ typedef struct {
                         * + at the entrance, - at the exit, with b_1/(B rho) = eta h,
                         * b_2/(B rho) = k1, b_3/(B rho) = k2/2; orbit unchanged.  0: none.
                         * Solenoids always carry their Sec. 4.4 fringe kicks; drifts and
-                        * snakes must have 0 (ST_EINVAL otherwise).  FP64 contexts only
-                        * when 1. */
+                        * snakes must have 0 (ST_EINVAL otherwise).  The mixed-precision
+                        * tracker applies them on ST_MULT, ST_QUAD_MK and ST_SBEND; an
+                        * ST_RBEND or ST_TEAPOT is FP64 only anyway. */
     int32_t split_order; /* orbit slice map of an ST_MULT, ST_QUAD_MK or ST_TEAPOT: 0 or
                           * 2 = the symmetric second-order split of Eq. (27) (drift-kick-
                           * drift, matrix-kick, TEAPOT); 4 = Yoshida's fourth-order composition

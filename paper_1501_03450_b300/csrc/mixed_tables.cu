@@ -134,6 +134,10 @@ int build_mixed_tables(LatticeImpl& L) {
         default:
             break;
         }
+        if ((d.flags & ST_ELEM_FRINGE) && (d.type == ST_MULT || d.type == ST_QUAD_MK || d.type == ST_SBEND)) {
+            m.type |= ST_MIX_FRINGE;
+            L.mix_fringe = true;
+        }
         for (int j = 0; j < 6; ++j) {
             const double w = std::ldexp(d.ds, j) * 0.5;
             const double al = w * omr;

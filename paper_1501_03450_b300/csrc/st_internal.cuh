@@ -103,6 +103,10 @@ struct __align__(16) MixElem {
     MixWeight w[6];
 };
 static_assert(sizeof(MixElem) % 16 == 0, "MixElem must be a multiple of 16 bytes");
+// MixElem::type bit of an element with thin fringe spin kicks at both ends
+// (Sec. 4.5, Eq. (skfringe)); only the kernels instantiated for such lattices
+// read it (the element kind is the low byte).
+enum { ST_MIX_FRINGE = 0x100 };
 
 // Kernel status word values (written by bounded device waits).
 enum : int32_t { STATUS_OK = 0, STATUS_TMA_TIMEOUT = 1, STATUS_BOUNDS = 3 };
@@ -123,7 +127,8 @@ struct LatticeImpl {
     int32_t n_unique;
     int32_t max_slices;
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
-    bool fp64_only = false;        // solenoids, fringe spin kicks or fourth-order maps: FP64 only
+    bool fp64_only = false;        // solenoids, rectangular or TEAPOT bends, fourth-order maps: FP64 only
+    bool mix_fringe = false;       // mixed table entries carry ST_MIX_FRINGE (thin fringe spin kicks)
     bool has_ext = false;          // fourth-order slice maps, rectangular or TEAPOT bends or thin lenses present
     bool has_order4 = false;       // fourth-order slice maps present
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]

@@ -7,7 +7,7 @@ namespace st {
 
 // 2 blocks of 128 per SM (up to 255 registers): 13% faster than 3 blocks with a
 // 168-register cap on the RHIC-like ring (fewer warps, but no rematerialisation).
-template <int K, bool SPIN = true>
+template <int K, bool SPIN = true, bool FR = false>
 __global__ void __launch_bounds__(128, 2) track_mixed_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
                                                             uint32_t seq_offset, uint32_t rho_offset, int n_seq,
                                                             RefConst ref, double2* __restrict__ xpx,
@@ -31,19 +31,19 @@ __global__ void __launch_bounds__(128, 2) track_mixed_kernel(const void* __restr
         const int64_t i = wi * 32 + lane;
         if (i >= n || lost[i]) continue;
 
-        mixed_track_particle<K, SPIN>(table, seq, rho, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns,
-                                      status);
+        mixed_track_particle<K, SPIN, FR>(table, seq, rho, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns,
+                                          status);
     }
 }
 
-template <int K, bool SPIN = true>
-static int launch_mixed_k(st_ctx* ctx, int n_turns) {
+template <int K, bool SPIN, bool FR>
+static int launch_mixed_k_(st_ctx* ctx, int n_turns) {
     const LatticeImpl& L = ctx->lat->impl;
     const int threads = ctx->block_threads;
     const size_t smem = L.mix_bytes;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(track_mixed_kernel<K, SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(track_mixed_kernel<K, SPIN, FR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mixed tracker)");
         attr_set = true;
@@ -52,7 +52,7 @@ static int launch_mixed_k(st_ctx* ctx, int n_turns) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_mixed_kernel<K, SPIN>, threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_mixed_kernel<K, SPIN, FR>, threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "mixed tracker occupancy query");
     if (per_sm < 1) {
         set_error("mixed tracker: block of %d threads with %zu B shared memory does not fit on an SM", threads, smem);
@@ -64,13 +64,20 @@ static int launch_mixed_k(st_ctx* ctx, int n_turns) {
     const int tpl = ctx->turns_per_launch;
     for (int t = 0; t < n_turns; t += tpl) {
         int nt = n_turns - t < tpl ? n_turns - t : tpl;
-        track_mixed_kernel<K, SPIN><<<(unsigned)grid, threads, smem, ctx->stream>>>(
+        track_mixed_kernel<K, SPIN, FR><<<(unsigned)grid, threads, smem, ctx->stream>>>(
             L.d_mix, (uint32_t)L.mix_bytes, (uint32_t)L.mix_seq_offset, (uint32_t)L.mix_rho_offset, L.n_elements,
             L.ref, ctx->xpx, ctx->ypy, ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "mixed tracker launch");
     }
     return ST_OK;
+}
+
+// The instantiation that decodes fringe-kick entries only for lattices with them.
+template <int K, bool SPIN = true>
+static int launch_mixed_k(st_ctx* ctx, int n_turns) {
+    return ctx->lat->impl.mix_fringe ? launch_mixed_k_<K, SPIN, true>(ctx, n_turns)
+                                     : launch_mixed_k_<K, SPIN, false>(ctx, n_turns);
 }
 
 // Orbit only, in the mixed tracker's compensated arithmetic (spins untouched).

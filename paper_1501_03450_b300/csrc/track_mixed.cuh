@@ -372,7 +372,32 @@ struct MixLevels {
 
 // Track particle i for n_turns turns through the mixed-precision tables in
 // shared memory (table, seq, rho); state in the FP64 pair-SoA arrays.
-template <int K, bool SPIN = true>
+// Thin fringe spin kick of a multipole, quadrupole or sector bend (Sec. 4.5,
+// Eq. (skfringe)) as a near-identity quaternion about the longitudinal axis:
+// angle theta = -sign (1 + G) sum_m (b_m/(B rho)) Im (X + iY)^m / m with b_1 =
+// eta h, b_2 = k1, b_3 = k2/2 (the kick is below 1e-3 rad, so FP32 and the
+// series of cos(theta/2) - 1 and sin(theta/2) to theta^3 suffice).
+__device__ __forceinline__ CNQ mixed_fringe(const MixElem& el, int type, const MState& z, float sign, float onepG) {
+    const float X = z.X.hi, Y = z.Y.hi;
+    float sum;
+    if (type == ST_SBEND) {
+        sum = el.eta * el.h * Y;
+    } else {
+        sum = el.k1 * X * Y;
+        if (type == ST_MULT) sum += 0.5f * el.k2 * Y * (X * X - Y * Y * (1.0f / 3.0f));
+    }
+    const float th = -sign * onepG * sum;
+    CNQ q;
+    q.w = -0.125f * th * th;
+    q.x = FF{0.0f, 0.0f};
+    q.y = FF{0.0f, 0.0f};
+    q.z = FF{0.5f * th * (1.0f - th * th * (1.0f / 24.0f)), 0.0f};
+    return q;
+}
+
+// FR: the lattice's table entries may carry ST_MIX_FRINGE (a separate
+// instantiation, so that lattices without fringe kicks run the plain loop).
+template <int K, bool SPIN = true, bool FR = false>
 __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__ table,
                                                      const uint16_t* __restrict__ seq,
                                                      const float2* __restrict__ rho, int n_seq, const RefConst& ref,
@@ -450,7 +475,7 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 }
             }
             const MixElem& el = table[idx];
-            const int type = el.type;
+            const int type = FR ? (el.type & 0xff) : el.type;
             if (type == ST_SNAKE) {
                 if constexpr (SPIN) fq_premul_ref(qt, el.rq);
                 continue;
@@ -642,9 +667,13 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     is_lost = true;
                     break;
                 }
-                // element rotation R_L (1 + D) into the compensated turn quaternion
+                // element rotation R_L (1 + D) into the compensated turn quaternion,
+                // between the entrance and exit fringe kicks if the element has them
+                const bool fr = FR && (el.type & ST_MIX_FRINGE);
+                if (fr) fq_premul_cnq(qt, mixed_fringe(el, type, z0, 1.0f, 1.0f + (float)ref.G));
                 fq_premul_cnq(qt, dq);
                 if (type == ST_SBEND) fq_premul_ref(qt, el.rq);
+                if (fr) fq_premul_cnq(qt, mixed_fringe(el, type, z, -1.0f, 1.0f + (float)ref.G));
             } else {
                 if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi)) {
                     z = z0;
