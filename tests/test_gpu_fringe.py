@@ -120,7 +120,7 @@ def test_mixed_tracker_with_fringe_kicks_against_the_oracle():
     assert spin_err(Sp, So)[0] > 100 * mean
 
 
-@pytest.mark.parametrize("gg", [45.5, 487.0])
+@pytest.mark.parametrize("gg", [487.0])   # the larger spin rotation per turn
 def test_mixed_tracker_with_fringe_kicks_1000_turns(gg):
     """The mixed tracker's error bound on the RHIC-like ring with fringe kicks
     on every magnet: after 1000 turns the mean spin error over 1024

@@ -127,7 +127,7 @@ def test_mixed_tracker_with_thin_lenses_against_the_oracle():
     assert np.abs(zm[:4] - zo[:4]).max() < 1e-7
 
 
-@pytest.mark.parametrize("gg", [45.5, 487.0])
+@pytest.mark.parametrize("gg", [487.0])   # the larger spin rotation per turn
 def test_mixed_tracker_thin_sextupole_ring_1000_turns(gg):
     """The mixed tracker's error bound on the RHIC-like ring with thin
     sextupoles: after 1000 turns the mean spin error over 1024 particles
