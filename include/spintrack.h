@@ -95,7 +95,7 @@ extern "C" {
                            partial kicks of 1/n_slices each with Omega (Eq. (6b)) of the
                            integrated field at their edges, then the chosen spin scheme,
                            as for any element.  No fringe kicks, second-order only; FP64
-                           only.                                                        */
+                           and mixed-precision contexts.                                */
 
 /* ---- spin integration schemes (spin_order arguments) ------------------ */
 /* spin_order 0..4 is the number of Romberg iterations over slice-edge
