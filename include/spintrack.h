@@ -340,7 +340,8 @@ int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, const st_ref
  * Delta S <= spin_error_bound (the reference itself if none is).  Outputs:
  * *n_slices_out, *spin_order_out (required); *dS_out, *ms_out,
  * *n_candidates_out (may be NULL); table_out (may be NULL) receives one row
- * (n_b, K, Delta S, ms) per candidate, at most ST_TUNE_MAX_CANDIDATES rows.
+ * (n_b, K, Delta S, ms) per candidate, at most ST_TUNE_MAX_CANDIDATES rows
+ * (slicings that the lattice does not admit are skipped).
  * The elements' own n_slices are ignored.  Creates and destroys its own
  * lattices and contexts on the current device; synchronous.  Errors:
  * ST_EINVAL (NULL, n < 1, bound <= 0, invalid element, a lattice that the

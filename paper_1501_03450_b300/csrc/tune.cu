@@ -112,6 +112,8 @@ extern "C" int st_tune_slicing(const st_element* elems, int32_t n_elems, const s
         for (int K = 0; K <= ST_TUNE_MAX_ORDER && (1 << K) <= nb; ++K) {
             TuneRun run;
             rc = tune_run(base, ref, z_soa, spin_soa, n_particles, nb, K, run);
+            if (rc == ST_EINVAL) continue;   // a slicing the lattice does not admit (e.g. a TEAPOT
+                                             // bend of 1 rad or more in one slice): not a candidate
             if (rc != ST_OK) return rc;
             const double dS = mean_spin_distance(run, ref_run, n_particles);
             if (table_out) {
