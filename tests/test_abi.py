@@ -116,3 +116,27 @@ def test_teapot_validation_happens_on_host():
     assert lib.st_lattice_create(arr, 1, ctypes.byref(ref), ctypes.byref(out)) == st.ST_EINVAL
     assert b"split_order" in lib.st_last_error()
     assert out.value is None
+
+
+def test_tuner_and_midpoint_argument_checks_happen_on_host():
+    """st_tune_slicing rejects null outputs, empty input, a non-positive bound
+    and invalid elements before any device call."""
+    lib = st.load()
+    ref = st.StReference(1.7928, 45.5)
+    arr = st.elements_array([dict(type="mult", L=1.0, n_slices=4, k1=0.1, k2=0, angle=0, eta=1, snake_phi=0,
+                                  snake_mu=0)])
+    z = (ctypes.c_double * 6)()
+    s = (ctypes.c_double * 3)()
+    nb, K = ctypes.c_int32(), ctypes.c_int32()
+    args = lambda bound, n=1, nbp=ctypes.byref(nb): (arr, n, ctypes.byref(ref), z, s, 1, bound, nbp, ctypes.byref(K),
+                                                     None, None, None, None)
+    assert lib.st_tune_slicing(*args(0.0)) == st.ST_EINVAL
+    assert lib.st_tune_slicing(*args(1e-6, n=0)) == st.ST_EINVAL
+    assert lib.st_tune_slicing(*args(1e-6, nbp=None)) == st.ST_EINVAL
+    bad = st.elements_array([dict(type="thin_mult", L=0.5, n_slices=4, k1=0.1, k2=0, angle=0, eta=1, snake_phi=0,
+                                  snake_mu=0)])
+    assert lib.st_tune_slicing(bad, 1, ctypes.byref(ref), z, s, 1, 1e-6, ctypes.byref(nb), ctypes.byref(K),
+                               None, None, None, None) == st.ST_EINVAL
+    assert b"thin lens" in lib.st_last_error()
+    # the midpoint schemes on a null context are rejected like any order
+    assert lib.st_track(None, 1, st.ST_SPIN_MID_KICK) == st.ST_EINVAL
