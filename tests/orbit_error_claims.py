@@ -100,3 +100,27 @@ def check_amplitude_dependence(track, n_particles=400, bin_size=80):
         ratios.append(ed / eb)
     assert max(ratios) < 5.0 * min(ratios), ratios
     return ratios
+
+
+def linear_tunes(J):
+    """Fractional horizontal and vertical tunes from the 2x2 diagonal blocks of
+    a one-turn Jacobian (uncoupled, stable motion)."""
+    import math
+    return [math.acos(0.5 * np.trace(J[i:i + 2, i:i + 2])) / (2.0 * math.pi) for i in (0, 2)]
+
+
+def check_tunes(jacobian, tol_bk):
+    """Sec. 5.1 (orbital spectra and tunes; drift-kick needs a tune fit): on
+    the RHIC-scale ring with thin sextupoles and no snakes, the bend-kick /
+    matrix-kick one-turn linear map is exact at any slice count (exact
+    sector-bend map, exact linear quadrupole flow), so its tunes do not move
+    with n_b; the drift-kick tunes are off at few slices and converge to them
+    as n_b^-2.  jacobian(ring) returns the 6x6 one-turn Jacobian at z = 0."""
+    base = W.with_thin_sextupoles(W.rhic_like_ring(GG, snakes=False))
+    dk = W.drift_kick_ring(base)
+    bk = [linear_tunes(jacobian(W.with_slices(base, nb))) for nb in (1, 4, 16)]
+    for t in bk[1:]:
+        assert max(abs(a - b) for a, b in zip(t, bk[0])) < tol_bk, (bk, tol_bk)
+    d = [max(abs(a - b) for a, b in zip(linear_tunes(jacobian(W.with_slices(dk, nb))), bk[0])) for nb in (4, 16)]
+    assert d[0] > 1e-3 and 13.0 < d[0] / d[1] < 19.0, d
+    return bk[0], d

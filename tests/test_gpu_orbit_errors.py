@@ -8,7 +8,8 @@ import pytest
 
 import oracle
 import paper_1501_03450_b300 as st
-from orbit_error_claims import check_amplitude_dependence, check_errors_over_turns, check_one_turn_errors
+from orbit_error_claims import (check_amplitude_dependence, check_errors_over_turns, check_one_turn_errors,
+                               check_tunes)
 
 pytestmark = pytest.mark.gpu
 
@@ -26,3 +27,20 @@ def test_orbit_errors_over_turns_on_the_gpu():
 
 def test_orbit_error_amplitude_dependence_on_the_gpu():
     check_amplitude_dependence(st.track)
+
+
+def _gpu_jacobian(ring, h=1e-7):
+    """One-turn Jacobian at z = 0 by central differences of CUDA-tracked
+    orbits (12 particles, one turn)."""
+    n = 12
+    z = np.zeros((6, n))
+    for j in range(6):
+        z[j, 2 * j], z[j, 2 * j + 1] = h, -h
+    S = np.tile(np.array([[0.0], [1.0], [0.0]]), (1, n))
+    z1, _, lost = st.track(ring, z, S, 1, 0)
+    assert not lost.any()
+    return np.stack([(z1[:, 2 * j] - z1[:, 2 * j + 1]) / (2 * h) for j in range(6)], axis=1)
+
+
+def test_tunes_need_no_fit_with_bend_kick_matrix_kick_on_the_gpu():
+    check_tunes(_gpu_jacobian, 1e-7)
