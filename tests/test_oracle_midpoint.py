@@ -166,3 +166,26 @@ def test_midpoint_validation():
         ring = W.single_element_ring(W.element("quad_mk", L=1.0, n_slices=4, k1=0.1, split_order=4), 45.5)
         assert not oracle.check_lattice(ring, K)
     assert not oracle.check_lattice(W.toy_ring(45.5), -3)
+
+
+@pytest.mark.parametrize("el", [
+    W.element("solenoid", L=2.0, n_slices=1, k1=0.3),
+    W.element("rbend", L=3.0, n_slices=1, angle=0.1, e1=0.02, fringe=1),
+    W.element("thin_mult", n_slices=1, k1=0.2, k2=5.0),
+], ids=["solenoid", "rbend", "thin_lens"])
+@pytest.mark.parametrize("K", SCHEMES)
+def test_midpoint_converges_to_the_romberg_limit_on_every_element_kind(el, K):
+    """Both midpoint placements converge as N^-2 to the limit that three
+    Romberg iterations on 256 slices reach (the same integral of Eq. (37))
+    on the solenoid (with its fringe kicks), the rectangular bend (with its
+    rotations and fringe kicks) and the thin lens."""
+    gg = 45.5
+    z0 = np.array([2e-3, 3e-4, -2e-3, 2e-4, 0.0, float(W.delta_to_pt(np.array(1e-3), gg))])
+    _, Sref, _, _, rc = oracle.element_detail(dict(el, n_slices=256), G, gg, z0, S0, 3)
+    assert rc == 0
+    errs = []
+    for N in (8, 16, 32):
+        _, S, _, _, rc = oracle.element_detail(dict(el, n_slices=N), G, gg, z0, S0, K)
+        assert rc == 0
+        errs.append(np.linalg.norm(S - Sref))
+    assert all(3.6 < errs[i] / errs[i + 1] < 4.4 for i in range(2)), errs
