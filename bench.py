@@ -205,8 +205,11 @@ def run_reference(args):
     rank, local_rank, world = dist_env()
     if rank != 0:
         return 0
-    w = W.workload(WORKLOAD, spin_order=args.spin_order, Ggamma0=args.ggamma)
+    w = W.workload(WORKLOAD, spin_order=max(args.spin_order, 2) if args.spin_order < 0 else args.spin_order,
+                   Ggamma0=args.ggamma)
     ring = w["ring"]
+    if args.ring == "drift_kick":
+        ring = W.drift_kick_ring(ring)
     n_el = len(ring["elements"])
     npart = args.particles or w["n_particles"]
     z, S = W.gaussian_particles(npart, args.ggamma, seed=w["seed"])
