@@ -230,8 +230,11 @@ def run_reference(args):
         "unit": "passes/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: 108-cell RHIC-like ring, Ggamma={args.ggamma}, "
-                   f"Romberg order {args.spin_order}", "particles_per_gpu": npart,
+        "config": {"workload": f"{WORKLOAD}: 108-cell RHIC-like ring"
+                   + (", drift-kick version" if args.ring == "drift_kick" else "") + f", Ggamma={args.ggamma}, "
+                   + (f"Romberg order {args.spin_order}" if args.spin_order >= 0
+                      else ("half-slice" if args.spin_order == -1 else "split-kick") + " midpoint spin scheme"),
+                   "ring": args.ring, "spin_order": args.spin_order, "particles_per_gpu": npart,
                    "elements_per_turn": n_el, "precision": "fp64", "parallelism": f"replicas{args.gpus}"},
         "cpu_baseline": {"value": value, "unit": "passes/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "passes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
