@@ -311,10 +311,13 @@ int st_selftest_bounded_wait(double limit_s, double* elapsed_s);
  * one file-scope device array of about 64 KiB that every GPU loading the
  * library holds until the process exits.
  *   elems, n_elems, ref: the lattice as for st_lattice_create (host memory).
- *   state: device buffer of 9 n doubles, updated in place, laid out as the
+ *   state: device (or managed) buffer of 9 n doubles, 16-byte aligned (it
+ *          is read and written as pairs), updated in place, laid out as the
  *          tracker's native pairs: (X,Px)[n], (Y,Py)[n], (T,Pt)[n], (Sx,Sy)[n],
- *          then Sz[n];  lost: device buffer of n flags (0 = tracked; set to 1
- *          when a particle is lost; particles flagged on entry are skipped).
+ *          then Sz[n];  lost: device (or managed) buffer of n flags (0 =
+ *          tracked; set to 1 when a particle is lost; particles flagged on
+ *          entry are skipped).  A misaligned state or a host pointer is
+ *          refused with ST_EINVAL before anything is launched.
  *   n_turns >= 0, spin_order 0..4 (every spin-carrying element's n_slices a
  *   multiple of 2^spin_order) or a midpoint scheme (ST_SPIN_MID_HALF,
  *   ST_SPIN_MID_KICK; no fourth-order slice maps); cuda_stream may be NULL
@@ -322,8 +325,12 @@ int st_selftest_bounded_wait(double limit_s, double* elapsed_s);
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call shares the scratch and rewrites it;
- * calls that overlap on the GPU race.  The call synchronises the stream.
- * Errors: ST_EINVAL (arguments, lattice too large), ST_ECUDA, ST_ETIMEOUT. */
+ * calls that overlap on the GPU race.  On the host the lattice is packed
+ * into a static 96 KiB buffer of the library under a mutex (no heap use), so
+ * host threads calling at the same time take turns.  The call synchronises
+ * the stream.
+ * Errors: ST_EINVAL (arguments, alignment, non-device buffers, lattice too
+ * large), ST_ECUDA, ST_ETIMEOUT. */
 int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, const st_reference* ref,
                           double* state, uint8_t* lost, int64_t n_particles, int32_t n_turns,
                           int32_t spin_order, void* cuda_stream);

@@ -384,9 +384,9 @@ int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particle
         }
         b->cost_per_particle.push_back(c);
     }
-    if (total > ((int64_t)1 << 31)) {
+    if (total > ((int64_t)1 << 31) - 1) {   // the kernels index particles with int
         delete b;
-        set_error("st_batch_create: at most 2^31 particles in total");
+        set_error("st_batch_create: at most 2^31 - 1 particles in total");
         return ST_EINVAL;
     }
     b->uploaded.assign(n_jobs, 0);

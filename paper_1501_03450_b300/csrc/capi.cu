@@ -311,8 +311,8 @@ int st_ctx_create(const st_lattice* lat, int64_t n_particles, int32_t precision,
         set_error("st_ctx_create: precision must be ST_FP64 or ST_MIXED");
         return ST_EINVAL;
     }
-    if (n_particles > (int64_t)1 << 31) {
-        set_error("st_ctx_create: at most 2^31 particles");
+    if (n_particles > ((int64_t)1 << 31) - 1) {   // the kernels index particles with int
+        set_error("st_ctx_create: at most 2^31 - 1 particles");
         return ST_EINVAL;
     }
     if (precision == ST_MIXED && lat->impl.fp64_only) {

@@ -90,13 +90,15 @@ template <int BN, int ST>
 static int launch_gemm_bn(const void* A, const void* B, int M, int N, int K, const GemmEpi& epi, int32_t* status,
                           cudaStream_t stream, int splits) {
     using Cf = GemmCfg<BN, ST>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             Cf::SMEM_BYTES);
-        if (e != cudaSuccess) return cuda_fail(e, "gemm: cudaFuncSetAttribute");
-        attr = true;
-    }
+    static PerDeviceOnce attr;
+    int rc0 = once_per_device(
+        attr,
+        [] {
+            return cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        Cf::SMEM_BYTES);
+        },
+        "gemm: cudaFuncSetAttribute");
+    if (rc0) return rc0;
     CUtensorMap ta, tb;
     int rc = get_tmap(&ta, A, M, K, 128);
     if (rc == ST_OK) rc = get_tmap(&tb, B, N, K, BN);

@@ -11,9 +11,13 @@
 // The scratch array is shared by every call on a device and keeps the last
 // call's contents; calls that overlap on the GPU (different streams, or
 // different host threads) race on it.  It is held by every GPU that loads the
-// library until the process exits.
+// library until the process exits.  On the host the lattice is packed into
+// one static buffer (96 KiB, part of the library image, no heap) under a
+// mutex, so concurrent host threads serialise their packing and copy.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "st_internal.cuh"
 
@@ -47,6 +51,24 @@ static int scratch_address(void** out) {
     return ST_OK;
 }
 
+// True if p is memory the current device can address as device memory
+// (device or managed allocations); host pointers, registered or not, are
+// refused.  cudaPointerGetAttributes allocates nothing.
+static bool is_device_pointer(const void* p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();   // clear the non-sticky error of an unknown pointer
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Host packing buffers: one per process, guarded by g_pack_mutex.
+static unsigned char g_host_blob[kNoAllocBlobMax];
+static uint16_t g_host_seq[16384];
+static std::mutex g_pack_mutex;
+
 }  // namespace st
 
 using namespace st;
@@ -70,9 +92,19 @@ extern "C" int st_track_fp64_noalloc(const st_element* elems, int32_t n_elems, c
         set_error("st_track_fp64_noalloc: need G > 0 and Ggamma0 > G");
         return ST_EINVAL;
     }
-    // Pack the lattice into a host buffer of fixed size (no heap allocation).
-    static thread_local unsigned char host_blob[kNoAllocBlobMax];
-    static thread_local uint16_t seq[16384];
+    // The state is read and written as pairs of doubles (16-byte accesses).
+    if (((uintptr_t)state & 15) != 0) {
+        set_error("st_track_fp64_noalloc: state must be 16-byte aligned");
+        return ST_EINVAL;
+    }
+    if (!is_device_pointer(state) || !is_device_pointer(lost)) {
+        set_error("st_track_fp64_noalloc: state and lost must be device (or managed) memory");
+        return ST_EINVAL;
+    }
+    // Pack the lattice into the static host buffer (no heap allocation).
+    std::lock_guard<std::mutex> pack_lock(g_pack_mutex);
+    unsigned char* host_blob = g_host_blob;
+    uint16_t* seq = g_host_seq;
     DevElem* table = (DevElem*)host_blob;
     const int max_unique = 512;
     int n_unique = 0;

@@ -176,6 +176,26 @@ namespace st {
 
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
+
+// Function attributes (such as the dynamic shared-memory limit) apply per
+// device, so launchers keep one "already set" flag per device ordinal.
+constexpr int kMaxDeviceFlags = 64;
+struct PerDeviceOnce {
+    bool done[kMaxDeviceFlags] = {};
+};
+// Runs set() once per device for this flag set; returns ST_OK or an error
+// code (the message is set).
+template <class F>
+inline int once_per_device(PerDeviceOnce& once, F&& set, const char* what) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (dev >= 0 && dev < kMaxDeviceFlags && once.done[dev]) return ST_OK;
+    e = set();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (dev >= 0 && dev < kMaxDeviceFlags) once.done[dev] = true;
+    return ST_OK;
+}
 bool is_spin_type(int t);
 DevElem pack_element(const st_element& e);
 const char* element_error(const st_element& e);

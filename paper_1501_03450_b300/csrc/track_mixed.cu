@@ -41,13 +41,15 @@ static int launch_mixed_k_(st_ctx* ctx, int n_turns) {
     const LatticeImpl& L = ctx->lat->impl;
     const int threads = ctx->block_threads;
     const size_t smem = L.mix_bytes;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(track_mixed_kernel<K, SPIN, FR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mixed tracker)");
-        attr_set = true;
-    }
+    static PerDeviceOnce attr_set;
+    int rc0 = once_per_device(
+        attr_set,
+        [] {
+            return cudaFuncSetAttribute(track_mixed_kernel<K, SPIN, FR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024);
+        },
+        "cudaFuncSetAttribute(mixed tracker)");
+    if (rc0) return rc0;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -140,3 +140,22 @@ def test_tuner_and_midpoint_argument_checks_happen_on_host():
     assert b"thin lens" in lib.st_last_error()
     # the midpoint schemes on a null context are rejected like any order
     assert lib.st_track(None, 1, st.ST_SPIN_MID_KICK) == st.ST_EINVAL
+
+
+def test_particle_count_limit_is_checked_before_any_device_call():
+    """The kernels index particles with a 32-bit int, so a context holds at
+    most 2^31 - 1 particles; 2^31 is refused before the lattice handle is
+    touched or any memory is allocated (the handle here is a dummy that the
+    call must not dereference), and so is 2^31 for the allocation-free entry
+    point."""
+    lib = st.load()
+    dummy = ctypes.create_string_buffer(8)
+    out = ctypes.c_void_p()
+    assert lib.st_ctx_create(ctypes.addressof(dummy), 1 << 31, st.ST_FP64, None, ctypes.byref(out)) == st.ST_EINVAL
+    assert b"2^31 - 1" in lib.st_last_error()
+    assert out.value is None
+    ref = st.StReference(1.7928, 45.5)
+    arr = st.elements_array([dict(type="drift", L=1.0, n_slices=1, k1=0, k2=0, angle=0, eta=1, snake_phi=0,
+                                  snake_mu=0)])
+    assert lib.st_track_fp64_noalloc(arr, 1, ctypes.byref(ref), ctypes.addressof(dummy), ctypes.addressof(dummy),
+                                     1 << 31, 1, 0, None) == st.ST_EINVAL

@@ -454,6 +454,35 @@ def test_oracle_rounding_noise_against_extended_precision():
     assert np.abs(S64 - S80.astype(float)).max() < 1e-12
 
 
+@pytest.mark.parametrize("gg", [45.5, 487.0])
+@pytest.mark.parametrize("K", [2, 4])
+def test_oracle_rounding_noise_on_the_full_rhic_like_ring(gg, K):
+    """The FP64 oracle against its long-double build on the full 108-cell ring
+    (Sec. 5's ring with snakes), particles sampled across the 10^5-particle
+    bench ensemble.  After one turn the two agree to a few 1e-12.  After 100
+    turns they differ by up to 3e-10 m in X and T and 1e-8 in the spin: the
+    exact bend map of Eq. (10) forms X as (Ps - eta - A_f)/(eta h), with
+    1/(eta h) = 206 m amplifying every rounding of Ps ~ 1, and those errors
+    accumulate over the 1728 bend slices of each turn.  This is the rounding
+    floor under which no FP64 tracker can be held to the oracle on this ring
+    after 100 turns."""
+    w = W.workload("rhic_like_1e5", spin_order=K, Ggamma0=gg)
+    z, S = W.gaussian_particles(w["n_particles"], gg, seed=w["seed"])
+    idx = np.linspace(0, w["n_particles"] - 1, 16).astype(int)
+    z, S = z[:, idx], S[:, idx]
+    z64, S64, _ = oracle.track(w["ring"], z, S, 1, K)
+    z80, S80, _ = oracle.track(w["ring"], z, S, 1, K, variant="f80")
+    assert np.abs(z64 - z80.astype(float)).max() < 1e-11
+    assert np.abs(S64 - S80.astype(float)).max() < 1e-11
+    z64, S64, l64 = oracle.track(w["ring"], z64, S64, 99, K)
+    z80, S80, l80 = oracle.track(w["ring"], z80, S80, 99, K, variant="f80")
+    assert l64.sum() == 0 and l80.sum() == 0
+    dz = np.abs(z64 - z80.astype(float)).max(axis=1)
+    assert dz[0] < 1e-9 and dz[2] < 1e-10 and dz[4] < 2e-9, dz        # X, Y, T in m
+    assert dz[1] < 2e-11 and dz[3] < 2e-12 and dz[5] == 0.0, dz       # Px, Py; Pt is constant
+    assert np.abs(S64 - S80.astype(float)).max() < 3e-8
+
+
 def _thick_lens(el):
     """Textbook linear 4x4 transverse matrix (X, Px, Y, Py) of an element on
     momentum (P = 1): drifts, thick quadrupoles (cos/cosh), a sector dipole

@@ -93,3 +93,36 @@ def test_noalloc_midpoint_schemes_match_context_entry_point():
         st.st_track_fp64_noalloc(r4["elements"], r4["G"], r4["Ggamma0"], state.data_ptr(), lost.data_ptr(), n, 1,
                                  st.ST_SPIN_MID_KICK)
     assert e.value.code == st.ST_EINVAL
+
+
+def test_noalloc_refuses_misaligned_and_host_buffers_without_launching():
+    """The state is accessed as 16-byte pairs: an 8-byte-offset view is
+    refused with ST_EINVAL, and so are host buffers, before anything is
+    staged or launched (the buffers are unchanged and the context still
+    tracks correctly afterwards)."""
+    torch = pytest.importorskip("torch")
+    ring = W.with_spin_order(W.toy_ring(45.5), 2)
+    n = 64
+    z, S = W.gaussian_particles(n, 45.5, seed=105)
+    base = torch.from_numpy(np.concatenate([[0.0], st.pairs_from_soa(z, S)])).to("cuda")
+    lost = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    before = base.clone()
+    with pytest.raises(st.SpinTrackError) as e:
+        st.st_track_fp64_noalloc(ring["elements"], ring["G"], ring["Ggamma0"], base.data_ptr() + 8,
+                                 lost.data_ptr(), n, 1, 2)
+    assert e.value.code == st.ST_EINVAL and "aligned" in str(e.value)
+    host_state = np.ascontiguousarray(st.pairs_from_soa(z, S))
+    host_lost = np.zeros(n, np.uint8)
+    with pytest.raises(st.SpinTrackError) as e:
+        st.st_track_fp64_noalloc(ring["elements"], ring["G"], ring["Ggamma0"], host_state.ctypes.data,
+                                 lost.data_ptr(), n, 1, 2)
+    assert e.value.code == st.ST_EINVAL and "device" in str(e.value)
+    with pytest.raises(st.SpinTrackError) as e:
+        st.st_track_fp64_noalloc(ring["elements"], ring["G"], ring["Ggamma0"], base.data_ptr() + 8,
+                                 host_lost.ctypes.data, n, 1, 2)
+    assert e.value.code == st.ST_EINVAL
+    torch.cuda.synchronize()
+    assert torch.equal(base, before) and int(lost.sum()) == 0
+    a = _run_noalloc(torch, ring, z, S, 3, 2)
+    b = st.track(ring, z, S, 3, 2)
+    assert np.abs(a[0] - b[0]).max() < TOL and np.abs(a[1] - b[1]).max() < TOL
