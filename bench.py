@@ -201,6 +201,22 @@ def oracle_rate(ring, z, S, spin_order, seconds_target=10.0, threads=None):
     return n * n_el / dt, f"{n} particles x 1 turn of the {n_el}-element ring ({dt:.1f} s)", threads, n
 
 
+def bench_config(args, npart, n_el, world):
+    """The workload description both arms print (the GPU arm and the oracle
+    reference arm time the same ring, ensemble, spin scheme and steps)."""
+    K = args.spin_order
+    return {"workload": f"{WORKLOAD}: 108-cell RHIC-like ring ({n_el} elements/turn)"
+            + (", drift-kick version (TEAPOT bends, drift-kick-drift quadrupoles)" if args.ring == "drift_kick"
+               else "")
+            + f", {npart} Gaussian protons per GPU, Ggamma={args.ggamma}, "
+            + (f"Romberg order {K}" if K >= 0 else ("half-slice" if K == -1 else "split-kick")
+               + " midpoint spin scheme") + ", 1 turn per step",
+            "ring": args.ring,
+            "particles_per_gpu": npart, "elements_per_turn": n_el, "precision": args.precision,
+            "spin_order": K, "turns_per_step": 1, "parallelism": f"replicas{world}",
+            "l2": "GPU arm: flushed between steps (2x L2 buffer written outside the timed events)"}
+
+
 def run_reference(args):
     rank, local_rank, world = dist_env()
     if rank != 0:
@@ -230,12 +246,7 @@ def run_reference(args):
         "unit": "passes/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: 108-cell RHIC-like ring"
-                   + (", drift-kick version" if args.ring == "drift_kick" else "") + f", Ggamma={args.ggamma}, "
-                   + (f"Romberg order {args.spin_order}" if args.spin_order >= 0
-                      else ("half-slice" if args.spin_order == -1 else "split-kick") + " midpoint spin scheme"),
-                   "ring": args.ring, "spin_order": args.spin_order, "particles_per_gpu": npart,
-                   "elements_per_turn": n_el, "precision": "fp64", "parallelism": f"replicas{args.gpus}"},
+        "config": bench_config(args, npart, n_el, args.gpus),
         "cpu_baseline": {"value": value, "unit": "passes/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "passes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -714,16 +725,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: 108-cell RHIC-like ring (1514 elements/turn)"
-                   + (", drift-kick version (TEAPOT bends, drift-kick-drift quadrupoles)" if args.ring == "drift_kick"
-                      else "")
-                   + f", {npart} Gaussian protons per GPU, Ggamma={args.ggamma}, "
-                   + (f"Romberg order {K}" if K >= 0 else ("half-slice" if K == -1 else "split-kick")
-                      + " midpoint spin scheme") + ", 1 turn per step",
-                   "ring": args.ring,
-                   "particles_per_gpu": npart, "elements_per_turn": n_el, "precision": args.precision,
-                   "spin_order": K, "turns_per_step": 1, "parallelism": f"replicas{world}",
-                   "l2": "flushed between steps (2x L2 buffer written outside the timed events)"},
+        "config": bench_config(args, npart, n_el, world),
         "e2e": e2e,
         "gpu_launches": args.steps * launches_per_step,
         "roofline": roofline,

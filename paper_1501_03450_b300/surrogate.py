@@ -17,10 +17,8 @@ one-turn map does not depend on T.
 
 Every per-sample step runs in the CUDA library (pair tracking, the fit's
 moments, the residual targets, forward, backward, Adam, the surrogate turn
-loop).  The host does the bookkeeping: the 4x4 linear optics of the sampling
-domain from a handful of tracked particles, the input generator, the normal
-equations of the fit (inside the library), the batch schedule.  PyTorch
-provides device memory and the stream.
+loop).  The host does the bookkeeping: the initial weights, the batch and
+learning-rate schedule.  PyTorch provides device memory and the stream.
 """
 from __future__ import annotations
 
@@ -51,26 +49,6 @@ def init_params(seed: int, gain: float = 1.0, last_scale: float = 0.1) -> np.nda
     return np.concatenate(parts)
 
 
-def action_angle_points(n: int, seed: int, twiss_x: Dict, twiss_y: Dict, D: float, Dp: float,
-                        Jx_max: float, Jy_max: float, pt_max: float) -> np.ndarray:
-    """Orbits z [6, n] at s = 0 with betatron actions uniform in [0, J_max]
-    (uniform over the phase-space ellipse), uniform random phases, Pt uniform
-    in [-pt_max, pt_max], the dispersive offset (D, Dp) * Pt added, T = 0.
-    twiss_*: dict(beta, alpha); J = (gamma u^2 + 2 alpha u u' + beta u'^2) / 2."""
-    rng = np.random.default_rng(seed)
-    z = np.zeros((6, n))
-    pt = rng.uniform(-pt_max, pt_max, n)
-    for (i, tw, jm) in ((0, twiss_x, Jx_max), (2, twiss_y, Jy_max)):
-        J = jm * rng.uniform(0.0, 1.0, n)
-        ph = rng.uniform(0.0, 2.0 * math.pi, n)
-        z[i] = np.sqrt(2.0 * J * tw["beta"]) * np.cos(ph)
-        z[i + 1] = -np.sqrt(2.0 * J / tw["beta"]) * (np.sin(ph) + tw["alpha"] * np.cos(ph))
-    z[0] += D * pt
-    z[1] += Dp * pt
-    z[5] = pt
-    return z
-
-
 class SpinMapSurrogate:
     """Learned one-turn spin map of one ring at one reference energy."""
 
@@ -86,7 +64,6 @@ class SpinMapSurrogate:
         self.mlp = MLP(self.max_batch, self.sp)
         self.seed = int(seed)
         self.q0 = self.closed_orbit_quaternion()
-        self.optics = None
         self.in_scale = None
         self.coef = None
         self.degree = None
@@ -117,100 +94,7 @@ class SpinMapSurrogate:
         """q0: the one-turn quaternion of the on-axis particle (scalar part >= 0)."""
         return self.one_turn_maps(np.zeros((6, 1)), [1.0, 0.0, 0.0, 0.0])[:, 0].copy()
 
-    def linear_optics(self, eps=(1e-7, 1e-8, 1e-7, 1e-8, 0.0, 1e-7)) -> Dict:
-        """Twiss parameters and dispersion at s = 0 from the one-turn orbit map,
-        linearised by central differences of tracked orbits."""
-        cols = [j for j in range(6) if eps[j] > 0]
-        z = np.zeros((6, 2 * len(cols)))
-        for k, j in enumerate(cols):
-            z[j, 2 * k] = eps[j]
-            z[j, 2 * k + 1] = -eps[j]
-        tr = self._tracker(z.shape[1])
-        try:
-            tr.upload(z, np.tile([[0.0], [1.0], [0.0]], (1, z.shape[1])))
-            tr.track_orbit(1)
-            z1, _, lost = tr.download()
-        finally:
-            tr.close()
-        if lost.any():
-            raise RuntimeError("linear_optics: a probe particle was lost")
-        Mx = np.zeros((6, 6))
-        for k, j in enumerate(cols):
-            Mx[:, j] = (z1[:, 2 * k] - z1[:, 2 * k + 1]) / (2 * eps[j])
-        out = {}
-        for plane, (a, b) in (("x", (0, 1)), ("y", (2, 3))):
-            m = Mx[np.ix_([a, b], [a, b])]
-            c = 0.5 * (m[0, 0] + m[1, 1])
-            if not abs(c) < 1.0:
-                raise RuntimeError(f"linear_optics: plane {plane} is not stable (cos mu = {c})")
-            s = math.copysign(math.sqrt(1.0 - c * c), m[0, 1])
-            beta = m[0, 1] / s
-            alpha = (m[0, 0] - m[1, 1]) / (2 * s)
-            out[plane] = dict(beta=beta, alpha=alpha, gamma=(1 + alpha * alpha) / beta,
-                              tune=math.atan2(s, c) / (2 * math.pi) % 1.0)
-        # periodic dispersion per unit Pt: (I - M_xx) d = M_x,pt
-        m = Mx[np.ix_([0, 1], [0, 1])]
-        d = np.linalg.solve(np.eye(2) - m, Mx[[0, 1], 5])
-        out["D"], out["Dp"] = float(d[0]), float(d[1])
-        out["M"] = Mx
-        self.optics = out
-        return out
-
     # ------------------------------------------------------------ training set
-    def action_bounds(self, sigmas: Dict, cut: float, margin: float):
-        """Largest betatron action per plane of a particle whose coordinates lie
-        within cut sigma (each coordinate, as the truncated Gaussian use
-        distribution), and the Pt bound; margin scales the amplitudes.
-        sigmas: x, px, y, py and pt_max (the largest |Pt| of the use ensemble)."""
-        o = self.optics or self.linear_optics()
-        pt_max = float(sigmas["pt_max"])
-        bounds = {}
-        for plane, (su, sp) in (("x", (sigmas["x"], sigmas["px"])), ("y", (sigmas["y"], sigmas["py"]))):
-            t = o[plane]
-
-            def J(u, p):
-                return 0.5 * (t["gamma"] * u * u + 2 * t["alpha"] * u * p + t["beta"] * p * p)
-
-            jb = max(J(cut * su * a, cut * sp * b) for a in (-1, 1) for b in (-1, 1))
-            amp = math.sqrt(jb)
-            if plane == "x":   # the dispersive offset D Pt adds to the betatron amplitude
-                amp += pt_max * math.sqrt(J(o["D"], o["Dp"]))
-            bounds[plane] = (margin * amp) ** 2
-        return bounds, margin * pt_max
-
-    def training_points(self, n: int, sigmas: Dict, cut: float = 3.0, margin: float = 1.1, seed: int = None):
-        """Orbits at s = 0 uniform in betatron action up to the bounds of
-        action_bounds, with uniform random phases and uniform Pt."""
-        bounds, pt_max = self.action_bounds(sigmas, cut, margin)
-        o = self.optics
-        return action_angle_points(n, self.seed if seed is None else seed, o["x"], o["y"], o["D"], o["Dp"],
-                                   bounds["x"], bounds["y"], pt_max)
-
-    def make_pairs(self, n: int, sigmas: Dict, cut: float = 3.0, margin: float = 1.1, seed: int = None):
-        """Tracks the training orbits one turn (FP64, the surrogate's spin
-        order) and keeps the pairs on the device: z64 [6, n] (orbit at s = 0)
-        and q64 [4, n] (its one-turn quaternion in q0's hemisphere)."""
-        z = self.training_points(n, sigmas, cut, margin, seed)
-        tr = self._tracker(n)
-        try:
-            with torch.cuda.stream(self.stream):
-                z64 = torch.from_numpy(z).to("cuda")
-                q64 = torch.empty((4, n), dtype=torch.float64, device="cuda")
-                lost = torch.empty(n, dtype=torch.uint8, device="cuda")
-                s_out = torch.empty((3, n), dtype=torch.float64, device="cuda")
-            S = np.zeros((3, n))
-            S[1] = 1.0
-            tr.upload(z, S)
-            st_track_one_turn_map(tr.handle, self.spin_order, self.q0, _ptr(q64))
-            tr.download_device(_ptr(s_out), None, _ptr(lost))
-            self.stream.synchronize()
-        finally:
-            tr.close()
-        n_lost = int(lost.cpu().numpy().sum())
-        if n_lost:
-            raise RuntimeError(f"make_pairs: {n_lost} training orbits were lost in one turn")
-        return dict(z=z, z64=z64, q64=q64, lost=lost, n=n)
-
     def make_pairs_from_orbits(self, z0: np.ndarray, n_turns: int, S0: Optional[np.ndarray] = None):
         """Pairs along tracked orbits: the ensemble z0 [6, m] is tracked for
         n_turns (FP64) and every turn contributes (z at s = 0, one-turn
