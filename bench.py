@@ -318,53 +318,59 @@ def variant_mixed(st, torch, args, fp64_value, fp32_peak):
     return out
 
 
-def variant_batched(st, torch, args, turns=3):
+def variant_batched(st, torch, args, turns=50):
     """64 uneven jobs (8-108 cells, G*gamma0 in [45.5, 487], 10^3-10^5
-    particles) in one persistent launch per chunk of turns, against tracking
-    the same jobs one after another with the single-job entry point."""
+    particles) in one persistent launch per chunk of turns, replayed from a
+    CUDA graph, in the launch shape the library's autotuner picks for each
+    precision; CUDA events around `turns` of the configured 500 turns per job
+    (every turn does the same work, so the rate is that of the whole 500).
+    Against the same jobs tracked one after another on one stream with the
+    single-job entry point (each job's turn timed with CUDA events, summed)."""
     jobs = W.batched_jobs(n_jobs=64, seed=20240603)
     for j in jobs:
         j["ring"] = W.with_spin_order(j["ring"], args.spin_order)
     passes_per_turn = sum(len(j["ring"]["elements"]) * j["n_particles"] for j in jobs)
     inputs = [W.gaussian_particles(j["n_particles"], j["ring"]["Ggamma0"], seed=j["seed"]) for j in jobs]
-    out = {"config": {"workload": "64 seeded rings, 8-108 FODO cells, Ggamma U[45.5, 487], particles log-U[1e3, 1e5]",
+    out = {"config": {"workload": "64 seeded rings, 8-108 FODO cells, Ggamma U[45.5, 487], particles log-U[1e3, 1e5], "
+                                  "500 turns per job configured",
                       "jobs": len(jobs), "particles": sum(j["n_particles"] for j in jobs),
-                      "passes_per_turn": passes_per_turn, "turns_timed": turns}}
+                      "passes_per_turn": passes_per_turn, "turns_timed": turns,
+                      "timing": "CUDA events on the batch stream around one graph replay of the timed turns"}}
+    stream = torch.cuda.Stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) * 1e-3
+
     for prec in ("fp64", "mixed"):
-        b = st.Batch([j["ring"] for j in jobs], [j["n_particles"] for j in jobs], prec)
+        b = st.Batch([j["ring"] for j in jobs], [j["n_particles"] for j in jobs], prec, stream=stream.cuda_stream)
         for k in range(len(jobs)):
             b.upload(k, *inputs[k])
-        tuned = b.autotune(args.spin_order, trial_turns=1) if prec == "mixed" else None
+        tuned = b.autotune(args.spin_order, trial_turns=1)
         b.track(turns, args.spin_order)            # warm-up and graph capture
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        b.track(turns, args.spin_order)
-        b.download(0)                              # synchronises the batch stream
-        dt = time.perf_counter() - t0
+        dt = timed(lambda: b.track(turns, args.spin_order))
         b.close()
-        # the same jobs tracked one after another (single-job contexts)
-        lats, trs = [], []
+        # the same jobs one after another on one stream (single-job contexts),
+        # one turn per job after a warm-up turn
+        ds = 0.0
         for k, j in enumerate(jobs):
             lat = st.Lattice(j["ring"])
-            tr = st.Tracker(lat, j["n_particles"], prec)
-            tr.set_launch(128, turns)
+            tr = st.Tracker(lat, j["n_particles"], prec, stream=stream.cuda_stream)
+            tr.set_launch(128, 1)
             tr.upload(*inputs[k])
-            lats.append(lat)
-            trs.append(tr)
-        for tr in trs:
             tr.track(1, args.spin_order)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for tr in trs:
-            tr.track(turns, args.spin_order)
-        torch.cuda.synchronize()
-        ds = time.perf_counter() - t0
-        for tr, lat in zip(trs, lats):
+            ds += timed(lambda: tr.track(1, args.spin_order))
             tr.close()
             lat.close()
-        out[prec] = {"value": passes_per_turn * turns / dt, "unit": "passes/s",
-                     "sequential_single_job_value": passes_per_turn * turns / ds,
-                     "speedup_vs_sequential": ds / dt, "autotuned_shape": tuned}
+        value = passes_per_turn * turns / dt
+        out[prec] = {"value": value, "unit": "passes/s", "ms_per_turn": 1e3 * dt / turns,
+                     "sequential_single_job_value": passes_per_turn / ds,
+                     "speedup_vs_sequential": value / (passes_per_turn / ds), "autotuned_shape": tuned}
     return out
 
 
@@ -373,8 +379,11 @@ def variant_surrogate(st, torch, args, fp64_value, throughput_turns=30):
     FP64 polynomial head, network on its own tensor-core kernels), then used
     for stroboscopic spin tracking with the orbit tracked exactly.  Error
     against plain FP64 spin tracking on 1024 particles after --error-turns
-    turns; throughput on the 10^4-particle averaging ensemble against plain
-    FP64 tracking with the same stroboscopic sum."""
+    turns (mean, percentiles, maximum).  Throughput on the 10^4-particle
+    averaging ensemble and on 10^5 particles, each against the two trackers
+    without the network on the same ensemble with the same stroboscopic sum:
+    the mixed-precision tracker with its spin step (the fastest method without
+    the network) and the FP64 tracker."""
     from paper_1501_03450_b300.surrogate import train_spin_map
     w = W.workload("rhic_like_spin_map", spin_order=args.spin_order)
     ring = w["ring"]
@@ -382,7 +391,7 @@ def variant_surrogate(st, torch, args, fp64_value, throughput_turns=30):
     n_el = len(ring["elements"])
     z_train, _ = W.gaussian_particles(w["train_particles"], gg, seed=w["train_seed"], cut=w["cut"])
     sg = train_spin_map(ring, z_train, w["train_turns"], w["spin_order"], degree=w["degree"], steps=w["steps"],
-                        batch=w["batch"], lr=w["lr"])
+                        batch=w["batch"], lr=w["lr"], max_batch=100352)
     out = {"config": {"workload": f"108-cell RHIC-like ring, Ggamma={gg}, Romberg order {args.spin_order}; "
                       f"use: {w['n_particles']} Gaussian protons (cut {w['cut']} sigma), stroboscopic <S> at s=0",
                       "training": dict(sg.timings, degree=w["degree"], lr=w["lr"],
@@ -398,30 +407,46 @@ def variant_surrogate(st, torch, args, fp64_value, throughput_turns=30):
         zs, Ss, _, avs, _ = sg.track(z, S, T, orbit=orbit)
         dS = np.linalg.norm(Ss - Sp, axis=0)
         dA = np.linalg.norm(avs - avp, axis=0)
+        p50, p90, p99 = np.percentile(dS, [50, 90, 99])
         out["error_vs_fp64"][f"orbit_{orbit}"] = {
-            "turns": T, "particles": int(z.shape[1]), "dS_mean": float(dS.mean()), "dS_median": float(np.median(dS)),
-            "dS_max": float(dS.max()), "d_avgS_mean": float(dA.mean()), "d_avgS_max": float(dA.max()),
+            "turns": T, "particles": int(z.shape[1]), "dS_mean": float(dS.mean()), "dS_median": float(p50),
+            "dS_p90": float(p90), "dS_p99": float(p99), "dS_max": float(dS.max()),
+            "d_avgS_mean": float(dA.mean()), "d_avgS_max": float(dA.max()),
             "orbit_max_abs_diff": float(np.abs(zs[:4] - zp[:4]).max())}
+    zm, Sm, _, avm, _ = sg.track_plain(z, S, T, precision="mixed")
+    dm = np.linalg.norm(Sm - Sp, axis=0)
+    out["error_vs_fp64"]["mixed_tracker"] = {"dS_mean": float(dm.mean()), "dS_max": float(dm.max()),
+                                             "d_avgS_mean": float(np.linalg.norm(avm - avp, axis=0).mean())}
     p = sg.mlp.get_params()
     sg.mlp.set_params(np.zeros_like(p))
     _, Sl, _, _, _ = sg.track(z, S, T)
     sg.mlp.set_params(p)
     out["error_vs_fp64"]["polynomial_head_only_dS_mean"] = float(np.linalg.norm(Sl - Sp, axis=0).mean())
-    # throughput on the averaging ensemble (a bounded number of turns)
-    z, S = W.gaussian_particles(w["n_particles"], gg, seed=w["seed"] + 1, cut=w["cut"])
-    sg.track(z, S, 2, orbit="mixed")
-    _, _, _, _, ms_m = sg.track(z, S, throughput_turns, orbit="mixed")
-    _, _, _, _, ms_s = sg.track(z, S, throughput_turns)
-    _, _, _, _, ms_p = sg.track_plain(z, S, throughput_turns)
-    passes = w["n_particles"] * n_el * throughput_turns
-    out.update({"metric": "particle-element passes/s", "value": passes / (ms_m * 1e-3), "unit": "passes/s",
-                "orbit": "mixed (compensated FP32 maps)",
-                "speedup_vs_plain_fp64_same_ensemble": ms_p / ms_m,
-                "value_fp64_orbit": passes / (ms_s * 1e-3),
-                "speedup_vs_plain_fp64_same_ensemble_fp64_orbit": ms_p / ms_s,
-                "plain_fp64_same_ensemble": passes / (ms_p * 1e-3),
-                "speedup_vs_fp64_headline": passes / (ms_m * 1e-3) / fp64_value,
-                "turns_timed": throughput_turns, "ms_per_turn": ms_m / throughput_turns,
+    # throughput: the averaging ensemble (10^4) and 10^5 particles, every
+    # method with the stroboscopic sum, a bounded number of turns
+    out["same_ensemble"] = {}
+    for n in (w["n_particles"], 100000):
+        zz, SS = W.gaussian_particles(n, gg, seed=w["seed"] + 1, cut=w["cut"])
+        sg.track(zz, SS, 2, orbit="mixed")
+        ms = {}
+        _, _, _, _, ms["surrogate_mixed_orbit"] = sg.track(zz, SS, throughput_turns, orbit="mixed")
+        _, _, _, _, ms["surrogate_fp64_orbit"] = sg.track(zz, SS, throughput_turns)
+        _, _, _, _, ms["mixed_tracker"] = sg.track_plain(zz, SS, throughput_turns, precision="mixed")
+        _, _, _, _, ms["fp64_tracker"] = sg.track_plain(zz, SS, throughput_turns)
+        passes = n * n_el * throughput_turns
+        rates = {k: passes / (v * 1e-3) for k, v in ms.items()}
+        out["same_ensemble"][str(n)] = {
+            "passes_per_s": rates, "ms_per_turn": {k: v / throughput_turns for k, v in ms.items()},
+            "speedup_vs_mixed_same_ensemble": ms["mixed_tracker"] / ms["surrogate_mixed_orbit"],
+            "speedup_vs_fp64_same_ensemble": ms["fp64_tracker"] / ms["surrogate_mixed_orbit"],
+            "speedup_vs_fp64_same_ensemble_fp64_orbit": ms["fp64_tracker"] / ms["surrogate_fp64_orbit"]}
+    head = out["same_ensemble"][str(w["n_particles"])]
+    out.update({"metric": "particle-element passes/s", "value": head["passes_per_s"]["surrogate_mixed_orbit"],
+                "unit": "passes/s", "orbit": "mixed (compensated FP32 maps)",
+                "speedup_vs_mixed_same_ensemble": head["speedup_vs_mixed_same_ensemble"],
+                "speedup_vs_plain_fp64_same_ensemble": head["speedup_vs_fp64_same_ensemble"],
+                "speedup_vs_fp64_headline": head["passes_per_s"]["surrogate_mixed_orbit"] / fp64_value,
+                "turns_timed": throughput_turns,
                 "dtype": "f32 compensated orbit + bf16/fp32 network + f64 head and spin"})
     sg.close()
     return out
@@ -529,8 +554,8 @@ def variant_drift_kick(st, torch, npart, seed, fp64_peak, ggamma=45.5, dS_partic
                          "iterations"}
 
 
-def element_type_breakdown(st, torch, ring, npart, seed, K, ggamma, min_elements=200):
-    """Pass rate of the FP64 tracker per element type: for each type in the
+def element_type_breakdown(st, torch, ring, npart, seed, K, ggamma, min_elements=200, precision="fp64"):
+    """Pass rate of the tracker (FP64 or mixed) per element type: for each type in the
     ring, a ring made of that type's elements only (in ring order, repeated
     to at least min_elements) is tracked for one turn on the same ensemble
     size; its share of the full ring's time is count / rate normalised."""
@@ -543,7 +568,7 @@ def element_type_breakdown(st, torch, ring, npart, seed, K, ggamma, min_elements
         reps = -(-min_elements // len(els))
         sub = dict(ring, elements=els * reps, name=f"{t}_only")
         lat = st.Lattice(sub)
-        tr = st.Tracker(lat, npart, "fp64", stream=stream.cuda_stream)
+        tr = st.Tracker(lat, npart, precision, stream=stream.cuda_stream)
         tr.set_launch(block_threads=128, turns_per_launch=1)
         tr.upload(z, S)
         tr.track(1, K)
@@ -566,7 +591,7 @@ def element_type_breakdown(st, torch, ring, npart, seed, K, ggamma, min_elements
     total = sum(v["count_in_ring"] / v["passes_per_s"] for v in out.values())
     for v in out.values():
         v["time_share"] = v["count_in_ring"] / v["passes_per_s"] / total
-    return {"workload": f"one element type per ring, {npart} particles, order {K}, 1 turn",
+    return {"workload": f"one element type per ring, {npart} particles, {precision}, order {K}, 1 turn",
             "types": out, "predicted_ring_passes_per_s": len(ring["elements"]) / total}
 
 

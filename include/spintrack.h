@@ -219,8 +219,9 @@ int st_track_one_turn_map(st_ctx* ctx, int32_t spin_order, const double* q_ref, 
 /* Stroboscopic spin average: as st_track, and after every turn each
  * particle's spin at the start of the lattice (the fixed azimuth s = 0) is
  * added to spin_sum (device double [3][n], accumulated, not cleared), so that
- * spin_sum / n_turns is the turn-averaged spin <S>.  FP64 contexts only.
- * Asynchronous. */
+ * spin_sum / n_turns is the turn-averaged spin <S>.  FP64 contexts, and
+ * ST_MIXED contexts (the mixed-precision tracker, Romberg orders 0..4; the
+ * spin after each turn is its FP64 spin).  Asynchronous. */
 int st_track_average(st_ctx* ctx, int32_t n_turns, int32_t spin_order, double* spin_sum);
 
 /* Restore lost flags ([n] bytes, nonzero = lost; host or device memory as
@@ -276,7 +277,8 @@ int st_batch_download(st_batch* batch, int32_t job, double* spin_soa, double* z_
                       int32_t dst_is_device);
 /* Launch shape: threads per block (32..128, multiple of 32; 0 keeps), turns
  * per launch (0 keeps), CUDA graph on/off (-1 keeps), register-budget
- * variant 0 (larger budget, fewer resident blocks) or 1 (-1 keeps). */
+ * variant 0 (larger budget, fewer resident blocks; the default) or 1 (-1
+ * keeps).  Defaults: 128 threads, 5 turns per launch, graph on, variant 0. */
 int st_batch_set_launch(st_batch* batch, int32_t block_threads, int32_t turns_per_launch, int32_t use_graph,
                         int32_t variant);
 /* Autotuner: times block size {64, 96, 128} x turns per launch {1,

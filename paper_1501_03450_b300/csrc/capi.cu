@@ -525,12 +525,13 @@ int st_track_average(st_ctx* ctx, int32_t n_turns, int32_t spin_order, double* s
         set_error("st_track_average: no particles uploaded");
         return ST_ESTATE;
     }
-    if (ctx->precision != ST_FP64 || n_turns < 0) {
-        set_error("st_track_average: needs an FP64 context and n_turns >= 0");
+    if (n_turns < 0) {
+        set_error("st_track_average: needs n_turns >= 0");
         return ST_EINVAL;
     }
     if (!spin_scheme_ok(ctx, spin_order, "st_track_average")) return ST_EINVAL;
     if (n_turns == 0) return ST_OK;
+    if (ctx->precision == ST_MIXED) return launch_track_mixed(ctx, n_turns, spin_order, spin_sum);
     return launch_track_average(ctx, n_turns, spin_order, spin_sum);
 }
 

@@ -205,7 +205,7 @@ int launch_track_fp64(st_ctx* ctx, int n_turns, int spin_order);
 int launch_track_orbit(st_ctx* ctx, int n_turns);
 int launch_track_turn_map(st_ctx* ctx, int spin_order, double* q_out, const double* q_ref);
 int launch_track_average(st_ctx* ctx, int n_turns, int spin_order, double* spin_sum);
-int launch_track_mixed(st_ctx* ctx, int n_turns, int spin_order);
+int launch_track_mixed(st_ctx* ctx, int n_turns, int spin_order, double* spin_sum = nullptr);
 int launch_track_mixed_orbit(st_ctx* ctx, int n_turns);
 // mixed-precision table builder (mixed_tables.cu)
 int build_mixed_tables(LatticeImpl& L);

@@ -14,7 +14,8 @@ __global__ void __launch_bounds__(128, 2) track_mixed_kernel(const void* __restr
                                                             double2* __restrict__ ypy, double2* __restrict__ tpt,
                                                             double2* __restrict__ sxy, double* __restrict__ szp,
                                                             uint8_t* __restrict__ lost, int n, int n_turns,
-                                                            int32_t* __restrict__ status) {
+                                                            int32_t* __restrict__ status,
+                                                            double* __restrict__ spin_sum) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
     if (!stage_to_smem(smem, blob, blob_bytes, &bar, status)) return;
@@ -32,12 +33,12 @@ __global__ void __launch_bounds__(128, 2) track_mixed_kernel(const void* __restr
         if (i >= n || lost[i]) continue;
 
         mixed_track_particle<K, SPIN, FR>(table, seq, rho, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i, n_turns,
-                                          status);
+                                          status, spin_sum, n);
     }
 }
 
 template <int K, bool SPIN, bool FR>
-static int launch_mixed_k_(st_ctx* ctx, int n_turns) {
+static int launch_mixed_k_(st_ctx* ctx, int n_turns, double* spin_sum) {
     const LatticeImpl& L = ctx->lat->impl;
     const int threads = ctx->block_threads;
     const size_t smem = L.mix_bytes;
@@ -68,7 +69,8 @@ static int launch_mixed_k_(st_ctx* ctx, int n_turns) {
         int nt = n_turns - t < tpl ? n_turns - t : tpl;
         track_mixed_kernel<K, SPIN, FR><<<(unsigned)grid, threads, smem, ctx->stream>>>(
             L.d_mix, (uint32_t)L.mix_bytes, (uint32_t)L.mix_seq_offset, (uint32_t)L.mix_rho_offset, L.n_elements,
-            L.ref, ctx->xpx, ctx->ypy, ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status);
+            L.ref, ctx->xpx, ctx->ypy, ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status,
+            spin_sum);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "mixed tracker launch");
     }
@@ -77,9 +79,9 @@ static int launch_mixed_k_(st_ctx* ctx, int n_turns) {
 
 // The instantiation that decodes fringe-kick entries only for lattices with them.
 template <int K, bool SPIN = true>
-static int launch_mixed_k(st_ctx* ctx, int n_turns) {
-    return ctx->lat->impl.mix_fringe ? launch_mixed_k_<K, SPIN, true>(ctx, n_turns)
-                                     : launch_mixed_k_<K, SPIN, false>(ctx, n_turns);
+static int launch_mixed_k(st_ctx* ctx, int n_turns, double* spin_sum = nullptr) {
+    return ctx->lat->impl.mix_fringe ? launch_mixed_k_<K, SPIN, true>(ctx, n_turns, spin_sum)
+                                     : launch_mixed_k_<K, SPIN, false>(ctx, n_turns, spin_sum);
 }
 
 // Orbit only, in the mixed tracker's compensated arithmetic (spins untouched).
@@ -91,7 +93,7 @@ int launch_track_mixed_orbit(st_ctx* ctx, int n_turns) {
     return launch_mixed_k<0, false>(ctx, n_turns);
 }
 
-int launch_track_mixed(st_ctx* ctx, int n_turns, int spin_order) {
+int launch_track_mixed(st_ctx* ctx, int n_turns, int spin_order, double* spin_sum) {
     const LatticeImpl& L = ctx->lat->impl;
     if (!L.d_mix) {
         set_error("mixed tracker: lattice has no mixed-precision tables");
@@ -106,11 +108,11 @@ int launch_track_mixed(st_ctx* ctx, int n_turns, int spin_order) {
         return ST_EINVAL;
     }
     switch (spin_order) {
-    case 0: return launch_mixed_k<0>(ctx, n_turns);
-    case 1: return launch_mixed_k<1>(ctx, n_turns);
-    case 2: return launch_mixed_k<2>(ctx, n_turns);
-    case 3: return launch_mixed_k<3>(ctx, n_turns);
-    case 4: return launch_mixed_k<4>(ctx, n_turns);
+    case 0: return launch_mixed_k<0>(ctx, n_turns, spin_sum);
+    case 1: return launch_mixed_k<1>(ctx, n_turns, spin_sum);
+    case 2: return launch_mixed_k<2>(ctx, n_turns, spin_sum);
+    case 3: return launch_mixed_k<3>(ctx, n_turns, spin_sum);
+    case 4: return launch_mixed_k<4>(ctx, n_turns, spin_sum);
     }
     set_error("spin_order out of range");
     return ST_EINVAL;

@@ -370,8 +370,6 @@ struct MixLevels {
     }
 };
 
-// Track particle i for n_turns turns through the mixed-precision tables in
-// shared memory (table, seq, rho); state in the FP64 pair-SoA arrays.
 // Thin fringe spin kick of a multipole, quadrupole or sector bend (Sec. 4.5,
 // Eq. (skfringe)) as a near-identity quaternion about the longitudinal axis:
 // angle theta = -sign (1 + G) sum_m (b_m/(B rho)) Im (X + iY)^m / m with b_1 =
@@ -395,6 +393,9 @@ __device__ __forceinline__ CNQ mixed_fringe(const MixElem& el, int type, const M
     return q;
 }
 
+// Track particle i for n_turns turns through the mixed-precision tables in
+// shared memory (table, seq, rho); state in the FP64 pair-SoA arrays.  If
+// spin_sum ([3][n_all]) is given, the spin after every turn is added to it.
 // FR: the lattice's table entries may carry ST_MIX_FRINGE (a separate
 // instantiation, so that lattices without fringe kicks run the plain loop).
 template <int K, bool SPIN = true, bool FR = false>
@@ -404,7 +405,8 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                                                      double2* __restrict__ xpx, double2* __restrict__ ypy,
                                                      double2* __restrict__ tpt, double2* __restrict__ sxy,
                                                      double* __restrict__ szp, uint8_t* __restrict__ lost, int64_t i,
-                                                     int n_turns, int32_t* status = nullptr) {
+                                                     int n_turns, int32_t* status = nullptr,
+                                                     double* __restrict__ spin_sum = nullptr, int64_t n_all = 0) {
     // table entries below the sequence (both staged into shared memory back to back)
     const int n_table = (int)(((const char*)seq - (const char*)table) / sizeof(MixElem));
     // state and per-particle constants (FP64 -> compensated FP32)
@@ -688,6 +690,11 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
             Quat q64{ff_to_double(qt.w), ff_to_double(qt.x), ff_to_double(qt.y), ff_to_double(qt.z)};
             q64 = qnormalize(q64);
             rotate_vec(q64, sx, sy, sz);
+            if (spin_sum) {   // stroboscopic sum of the spin at the start of the lattice
+                spin_sum[i] += sx;
+                spin_sum[n_all + i] += sy;
+                spin_sum[2 * n_all + i] += sz;
+            }
         }
     }
     xpx[i] = make_double2(ff_to_double(z.X), ff_to_double(z.Px));

@@ -206,9 +206,11 @@ class SpinMapSurrogate:
         return _run(self, z, S, n_turns, average, timed, surrogate=True, orbit=orbit)
 
     def track_plain(self, z: np.ndarray, S: np.ndarray, n_turns: int, average: bool = True,
-                    timed: bool = False):
-        """The same with plain FP64 spin tracking (the reference for the map's error)."""
-        return _run(self, z, S, n_turns, average, timed, surrogate=False)
+                    timed: bool = False, precision: str = "fp64"):
+        """The same with plain spin tracking: precision "fp64" (the reference
+        for the map's error) or "mixed" (the mixed-precision tracker with its
+        spin step, the fastest method without the network)."""
+        return _run(self, z, S, n_turns, average, timed, surrogate=False, orbit=precision)
 
     def close(self):
         self.mlp.close()
@@ -219,7 +221,7 @@ def _run(sg: SpinMapSurrogate, z, S, n_turns, average, timed, surrogate, orbit="
     n = z.shape[1]
     if surrogate and n > sg.max_batch:
         raise ValueError("more particles than the network's max_batch")
-    tr = Tracker(sg.lattice, n, orbit, sg.sp) if surrogate else sg._tracker(n)
+    tr = Tracker(sg.lattice, n, orbit, sg.sp)
     try:
         with torch.cuda.stream(sg.stream):
             ssum = torch.zeros((3, n), dtype=torch.float64, device="cuda") if average else None

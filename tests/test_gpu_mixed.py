@@ -128,3 +128,41 @@ def test_mixed_orbit_only_tracks_the_mixed_orbit():
     # differently: agreement to the mixed orbit's own accuracy
     assert np.abs(zo[:4] - zm[:4]).max() < 1e-9
     assert np.abs(zo[:4] - zf[:4]).max() < 1e-9
+
+
+def test_mixed_stroboscopic_average_is_the_sum_of_the_turn_spins():
+    """st_track_average on a mixed-precision context: the accumulated spin is
+    the sum of the spins after each turn, bit for bit against tracking turn
+    by turn in the same launch shape, and close to the FP64 tracker's average."""
+    torch = pytest.importorskip("torch")
+    ring = W.with_spin_order(W.rhic_like_ring(487.0, n_cells=12), 2)
+    n, T = 333, 12
+    z, S = W.gaussian_particles(n, 487.0, seed=77)
+    lat = st.Lattice(ring)
+    acc = torch.zeros((3, n), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()                 # the tracker runs on its own stream
+    tr = st.Tracker(lat, n, "mixed")
+    tr.set_launch(block_threads=128, turns_per_launch=1)
+    tr.upload(z, S)
+    st.st_track_average(tr.handle, T, 2, acc.data_ptr())
+    zA, SA, _ = tr.download()
+    tr.upload(z, S)
+    manual = np.zeros((3, n))
+    for _ in range(T):
+        tr.track(1, 2)
+        _, Si, _ = tr.download()
+        manual += Si
+    zB, SB, _ = tr.download()
+    tr.close()
+    torch.cuda.synchronize()
+    assert np.array_equal(zA, zB) and np.array_equal(SA, SB)
+    assert np.array_equal(acc.cpu().numpy(), manual)
+    acc64 = torch.zeros((3, n), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    tr = st.Tracker(lat, n, "fp64")
+    tr.upload(z, S)
+    st.st_track_average(tr.handle, T, 2, acc64.data_ptr())
+    tr.download()                            # synchronises the tracker's stream
+    tr.close()
+    lat.close()
+    assert np.abs(acc.cpu().numpy() - acc64.cpu().numpy()).max() / T < 1e-6

@@ -6,7 +6,15 @@ with the map while the orbit is tracked exactly.  Compared with plain FP64
 spin tracking (the tracker that matches the oracle to 1e-11): the spin error
 after 1000 turns stays within 1e-4 (mean over 1024 particles, final spin and
 turn average), the trained network gains over the polynomial head alone,
-and the surrogate is faster than plain tracking."""
+the surrogate is faster than plain tracking, and faster than the fastest
+method without the network -- the mixed-precision tracker with its spin step
+-- on the same ensemble.
+
+The error tail is bounded too (99th percentile of the 1000-turn spin error).
+It does not sit at the edge of the training domain: the particles with the
+largest errors have ordinary one-turn map errors, which add up coherently
+over the turns (their final error is 0.06-0.25 of T times their mean one-turn
+error, against 0.003 for the median particle)."""
 import numpy as np
 import pytest
 
@@ -45,6 +53,7 @@ def test_spin_error_within_1e_4_after_1000_turns_and_faster(spin_map):
     dA = np.linalg.norm(avs - avp, axis=0)
     assert dS.mean() <= 1e-4, dS.mean()
     assert dA.mean() <= 1e-4, dA.mean()
+    assert np.percentile(dS, 99) <= 2e-3, np.percentile(dS, [50, 90, 99, 100])
     assert np.abs(np.linalg.norm(Ss, axis=0) - 1).max() < 1e-12
     assert ms_s < 0.5 * ms_p, (ms_s, ms_p)
     # what the network gains over the method without it: the polynomial head alone
@@ -70,3 +79,27 @@ def test_surrogate_with_the_mixed_orbit(spin_map):
     assert np.linalg.norm(Ss - Sp, axis=0).mean() <= 1e-4
     assert np.linalg.norm(avs - avp, axis=0).mean() <= 1e-4
     assert ms_s < 0.25 * ms_p, (ms_s, ms_p)
+
+
+def test_surrogate_beats_the_mixed_tracker_on_the_same_ensemble(spin_map):
+    """What the trained network gains over the method without it: on the
+    10^4-particle averaging ensemble, the surrogate (mixed-precision orbit,
+    network spin map, stroboscopic sum) against the mixed-precision tracker
+    with its own spin step and the same stroboscopic sum (the fastest tracker
+    without the network), and the surrogate with the FP64 orbit against the
+    FP64 tracker.  The averages of the two trackers agree (mixed against FP64
+    within the mixed tracker's own error)."""
+    w, sg = spin_map
+    gg = w["ring"]["Ggamma0"]
+    z, S = W.gaussian_particles(w["n_particles"], gg, seed=w["seed"] + 1, cut=w["cut"])
+    T = 20
+    sg.track(z, S, 2, orbit="mixed")
+    _, Ssm, _, avsm, ms_sm = sg.track(z, S, T, orbit="mixed")
+    _, _, _, _, ms_sf = sg.track(z, S, T)
+    _, Spm, lpm, avpm, ms_pm = sg.track_plain(z, S, T, precision="mixed")
+    _, Spf, lpf, avpf, ms_pf = sg.track_plain(z, S, T)
+    assert lpm.sum() == 0 and lpf.sum() == 0
+    assert np.linalg.norm(avpm - avpf, axis=0).max() < 1e-6
+    assert np.linalg.norm(Spm - Spf, axis=0).max() < 1e-6
+    assert ms_sm < 0.6 * ms_pm, (ms_sm, ms_pm)
+    assert ms_sf < 0.6 * ms_pf, (ms_sf, ms_pf)
