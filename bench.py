@@ -87,6 +87,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant report")
     ap.add_argument("--error-turns", type=int, default=1000, help="turns of the variants' error check")
+    ap.add_argument("--profile-surrogate", type=int, default=0, metavar="TURNS",
+                    help="run the learned map's turn loop for TURNS turns and exit (for ncu)")
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="TURNS",
+                    help="track the 64-job batch TURNS turns, one launch per turn, and exit (for ncu)")
     ap.add_argument("--profile-train", type=int, default=0, metavar="STEPS",
                     help="profiling mode: only train the spin-map network for STEPS steps on 32768-row batches "
                          "(pairs from 4000 particles x 10 turns) and print the step time")
@@ -117,6 +121,50 @@ def profile_train(args):
                       "ms_per_step": e0.elapsed_time(e1) / max(1, args.profile_train),
                       "library": st.LIB_PATH}))
     sg.close()
+
+
+def profile_surrogate(args):
+    """A short run of the learned map's turn loop on the 10^4-particle
+    averaging ensemble, with both orbit trackers (for ncu's launch list: the
+    split of one turn into orbit, pack, network layers and spin step).  The
+    network is untrained (its weights do not change the work)."""
+    import torch
+    import paper_1501_03450_b300 as st
+    from paper_1501_03450_b300.surrogate import SpinMapSurrogate
+    w = W.workload("rhic_like_spin_map", spin_order=args.spin_order)
+    gg = w["ring"]["Ggamma0"]
+    sg = SpinMapSurrogate(w["ring"], w["spin_order"], max_batch=w["n_particles"] + 128)
+    z0, _ = W.gaussian_particles(2000, gg, seed=w["train_seed"], cut=w["cut"])
+    pairs = sg.make_pairs_from_orbits(z0, 5)
+    sg.fit_head(pairs, w["degree"])
+    z, S = W.gaussian_particles(w["n_particles"], gg, seed=w["seed"] + 1, cut=w["cut"])
+    out = {"profile_surrogate_turns": args.profile_surrogate, "particles": w["n_particles"], "library": st.LIB_PATH}
+    for orbit in ("mixed", "fp64"):
+        sg.track(z, S, 1, orbit=orbit)
+        _, _, _, _, ms = sg.track(z, S, args.profile_surrogate, orbit=orbit)
+        out[f"ms_per_turn_{orbit}_orbit"] = ms / max(1, args.profile_surrogate)
+    print(json.dumps(out))
+    sg.close()
+
+
+def profile_batch(args):
+    """One turn of the 64-job batch in one persistent launch (no graph), at
+    --precision, in the default launch shape (for ncu: per-launch time and
+    the spread of SM busy cycles, i.e. the tail of the work queue)."""
+    import torch
+    import paper_1501_03450_b300 as st
+    jobs = W.batched_jobs(n_jobs=64, seed=20240603)
+    b = st.Batch([W.with_spin_order(j["ring"], args.spin_order) for j in jobs], [j["n_particles"] for j in jobs],
+                 args.precision)
+    for k, j in enumerate(jobs):
+        b.upload(k, *W.gaussian_particles(j["n_particles"], j["ring"]["Ggamma0"], seed=j["seed"]))
+    b.set_launch(128, 1, 0, -1)
+    for _ in range(args.profile_batch):
+        b.track(1, args.spin_order)
+    b.download(0)
+    print(json.dumps({"profile_batch_turns": args.profile_batch, "precision": args.precision,
+                      "library": st.LIB_PATH}))
+    b.close()
 
 
 def dist_env():
@@ -599,6 +647,10 @@ def main():
     args = parse_args()
     if args.profile_train:
         return profile_train(args)
+    if args.profile_surrogate:
+        return profile_surrogate(args)
+    if args.profile_batch:
+        return profile_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch
