@@ -8,6 +8,7 @@
 //     pairs, the reference rotation of each element as a (hi, lo) quaternion;
 //   - the element sequence (uint16) and, for bends, cos/sin of the reference
 //     rotation accumulated up to every slice edge.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -105,6 +106,7 @@ int build_mixed_tables(LatticeImpl& L) {
             m.eta = (float)eta;
             m.ieta = (float)(1.0 / eta);
             m.ieh = (float)(1.0 / (eta * h));
+            m.ieh_ff = split(1.0 / (eta * h));
             m.dT_eta = (float)((1.0 - 1.0 / eta) * d.ds / beta0);
             m.sbieh_ff = split(std::sin(h * d.ds) / (eta * h));
             m.ietads_ff = split(d.ds / eta);
@@ -163,7 +165,20 @@ int build_mixed_tables(LatticeImpl& L) {
             const double kq = ch * al * S[1] - sh * C[1];
             W.Ky = split(ch * S[0] + 2.0 * al * kq);
             W.Kq = (float)kq;
-            W.pad_ = 0.0f;
+            // short series: with |du| <= du3 the first neglected term (n = 3) is below
+            // 2^-27 of the leading one for both functions, and the later terms fall
+            // off faster (|dX[n+1] / dX[n]| du <= 1/4 there)
+            double du3 = 1e30;
+            for (const double* X : {C, S}) {
+                const double c0 = std::fabs(X[1]), c3 = std::fabs(X[4] / 24.0);
+                if (c3 > 0.0) du3 = std::min(du3, std::cbrt(std::ldexp(c0, -27) / c3));
+                for (int n = 3; n < MIX_TAYLOR - 1; ++n) {   // ratio test of the later terms
+                    const double a = std::fabs(X[n + 1]) / std::tgamma(n + 2.0);
+                    const double b = std::fabs(X[n + 2]) / std::tgamma(n + 3.0);
+                    if (b > 0.0) du3 = std::min(du3, 0.25 * a / b);
+                }
+            }
+            W.du3 = (float)du3;
         }
         for (int c = 0; c < 4; ++c) m.rq[c] = split(rq[c]);
         me[u] = m;

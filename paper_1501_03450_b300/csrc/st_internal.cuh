@@ -69,7 +69,7 @@ struct MixWeight {
     float dS[MIX_TAYLOR];   // S(u0 + du) - S(u0) = sum_n dS[n] du^(n+1)
     float2 Ky;        // d e_y / d b_y at b = 0 (first-order coefficient), as (hi, lo)
     float Kq;         // coefficient of du in e_y beyond Ky: ch alpha dS[0] - sh dC[0]
-    float pad_;
+    float du3;        // |du| below which the terms n >= 3 of dC, dS are below 2^-27 of the first
 };
 
 // Per unique element, constants of the mixed-precision kernel.  First-order
@@ -99,6 +99,8 @@ struct __align__(16) MixElem {
     float2 eh2_ff;                    // bend: eta h^2 as (hi, lo)
     float2 cbm1_ff;                   // bend: cos(h ds) - 1 as (hi, lo)
     float2 dTeta_ff;                  // bend: (1 - 1/eta) ds / beta0 as (hi, lo)
+    float2 ieh_ff;                    // bend: 1/(eta h) as (hi, lo)
+    float2 pad2_;
     float2 rq[4];                     // reference rotation over the element (bends, snakes), (hi, lo) per component
     MixWeight w[6];
 };

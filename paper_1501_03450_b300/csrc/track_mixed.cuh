@@ -159,16 +159,44 @@ struct FQ {
 
 // Q <- (1 + D) Q for a near-identity D with compensated vector part: the
 // first-order products D.v Q compensated, D.w Q (second order) in FP32
+// (the four components as two packed FP32x2 pairs, (w, x) and (y, z))
+__device__ __forceinline__ FF2 ff2_add_lazy(const FF2& a, const FF2& b) {
+    float2 s, e;
+    two_sum2(a.hi, b.hi, s, e);
+    return FF2{s, __fadd2_rn(e, __fadd2_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ FF2 ff2_neg(const FF2& a) { return FF2{f2_neg(a.hi), f2_neg(a.lo)}; }
 __device__ __forceinline__ void fq_premul_cnq(FQ& q, const CNQ& d) {
-    const float qw = q.w.hi, qx = q.x.hi, qy = q.y.hi, qz = q.z.hi;
-    const FF cw = ff_addlo(ff_neg(ff_add_lazy(ff_add_lazy(ff_mul(d.x, q.x), ff_mul(d.y, q.y)), ff_mul(d.z, q.z))), d.w * qw);
-    const FF cx = ff_addlo(ff_add_lazy(ff_add_lazy(ff_mul(d.x, q.w), ff_mul(d.y, q.z)), ff_neg(ff_mul(d.z, q.y))), d.w * qx);
-    const FF cy = ff_addlo(ff_add_lazy(ff_add_lazy(ff_mul(d.y, q.w), ff_mul(d.z, q.x)), ff_neg(ff_mul(d.x, q.z))), d.w * qy);
-    const FF cz = ff_addlo(ff_add_lazy(ff_add_lazy(ff_mul(d.z, q.w), ff_mul(d.x, q.y)), ff_neg(ff_mul(d.y, q.x))), d.w * qz);
-    q.w = ff_add(q.w, cw);
-    q.x = ff_add(q.x, cx);
-    q.y = ff_add(q.y, cy);
-    q.z = ff_add(q.z, cz);
+    const FF2 qwx = ff2_pack(q.w, q.x), qyz = ff2_pack(q.y, q.z);
+    const FF nx = ff_neg(d.x), ny = ff_neg(d.y), nz = ff_neg(d.z);
+    // c_w = -(dx qx + dy qy + dz qz),  c_x = dx qw + dy qz - dz qy
+    const FF2 cwx = ff2_add_lazy(ff2_add_lazy(ff2_mul(ff2_pack(nx, d.x), ff2_pack(q.x, q.w)),
+                                              ff2_mul(ff2_pack(ny, d.y), ff2_pack(q.y, q.z))),
+                                 ff2_mul(ff2_pack(nz, nz), ff2_pack(q.z, q.y)));
+    // c_y = dy qw + dz qx - dx qz,  c_z = dz qw + dx qy - dy qx
+    const FF2 cyz = ff2_add_lazy(ff2_add_lazy(ff2_mul(ff2_pack(d.y, d.z), ff2_pack(q.w, q.w)),
+                                              ff2_mul(ff2_pack(d.z, d.x), ff2_pack(q.x, q.y))),
+                                 ff2_mul(ff2_pack(nx, ny), ff2_pack(q.z, q.x)));
+    // plus the second-order d_w q in the compensation word
+    const FF2 awx{cwx.hi, __ffma2_rn(make_float2(d.w, d.w), qwx.hi, cwx.lo)};
+    const FF2 ayz{cyz.hi, __ffma2_rn(make_float2(d.w, d.w), qyz.hi, cyz.lo)};
+    const FF2 owx = ff2_add(qwx, awx), oyz = ff2_add(qyz, ayz);
+    q.w = ff2_first(owx);
+    q.x = ff2_second(owx);
+    q.y = ff2_first(oyz);
+    q.z = ff2_second(oyz);
+}
+
+// Q <- R Q for a compensated reference rotation R = (a0, 0, a2, 0) about y
+// (a sector bend's: the other two components vanish)
+__device__ __forceinline__ void fq_premul_about_y(FQ& q, const float2* rq) {
+    const FF a0{rq[0].x, rq[0].y}, a2{rq[2].x, rq[2].y};
+    FQ o;
+    o.w = ff_add(ff_mul(a0, q.w), ff_neg(ff_mul(a2, q.y)));
+    o.x = ff_add(ff_mul(a0, q.x), ff_mul(a2, q.z));
+    o.y = ff_add(ff_mul(a0, q.y), ff_mul(a2, q.w));
+    o.z = ff_add(ff_mul(a0, q.z), ff_neg(ff_mul(a2, q.x)));
+    q = o;
 }
 
 // Q <- R Q for a compensated reference rotation R
@@ -210,8 +238,10 @@ __device__ __forceinline__ FF inv_ps(const MConst& k, float px, float py, float&
 
 __device__ __forceinline__ void drift_inc(MState& z, const MConst& k, const FF& L, const FF& ips, float d) {
     const FF Lips = ff_mul(L, ips);
-    z.X = ff_add(z.X, ff_mul(Lips, z.Px));
-    z.Y = ff_add(z.Y, ff_mul(Lips, z.Py));
+    // (X, Y) += (L/Ps) (Px, Py), both planes in packed FP32x2 arithmetic
+    const FF2 U = ff2_add(ff2_pack(z.X, z.Y), ff2_mul(ff2_pack(z.Px, z.Py), ff2_pack(Lips, Lips)));
+    z.X = ff2_first(U);
+    z.Y = ff2_second(U);
     z.T = ff_add(z.T, ff_mul(L, ff_add_f(k.tau, -k.b0pt * d)));
 }
 
@@ -229,8 +259,14 @@ __device__ __forceinline__ void straight_edge(const MConst& k, const MState& z, 
     const float aPf = k.aP.hi;
     const float remx = -aPf * sx - d * k.a * fbx + ips * cu * px;
     const float remy = -aPf * sy - d * k.a * fby + ips * cu * py;
-    bx = ff_addn(ff_neg(ff_mul(Aw, z.Y)), w * remx);
-    by = ff_addn(ff_neg(ff_mul(Aw, z.X)), w * remy);
+    // (bx, by) = -Aw (Y, X) + w (remx, remy), renormalised; both in packed FP32x2
+    const FF2 p = ff2_mul(ff2_pack(z.Y, z.X), ff2_pack(Aw, Aw));
+    const float2 t = __ffma2_rn(make_float2(w, w), make_float2(remx, remy), f2_neg(p.lo));   // w rem - lo
+    const float2 h = f2_neg(p.hi);
+    float2 rh = __fadd2_rn(h, t);
+    float2 rl = f2_sub(t, f2_sub(rh, h));
+    bx = FF{rh.x, rl.x};
+    by = FF{rh.y, rl.y};
     bz = w * ips * cu * Ps;
 }
 
@@ -276,23 +312,38 @@ __device__ __forceinline__ void mquad_coeffs(MQuad& q, double invP, double absk,
 }
 
 // linear quadrupole flow H_qL over a half slice, Eq. (24), in increment form:
-// dU = U (C-1) + Pu (S/P),  dPu = Pu (C-1) -/+ k1 U S
-__device__ __forceinline__ void quad_linear_inc(MState& z, const MConst& k, const MQuad& q, float k1) {
-    const int px_ = k1 >= 0.0f ? 0 : 1, py_ = 1 - px_;
-    const float sgn = k1 >= 0.0f ? 1.0f : -1.0f;
+// dU = U (C-1) + Pu (S/P),  dPu = Pu (C-1) -/+ k1 U S.  PX is the coefficient
+// set of the x plane (0: the cos plane, k1 >= 0; 1: the cosh plane), a
+// compile-time index so that the coefficients stay in registers.
+template <int PX>
+__device__ __forceinline__ void quad_linear_inc_(MState& z, const MConst& k, const MQuad& q, float k1) {
+    constexpr int px_ = PX, py_ = 1 - PX;
+    constexpr float sgn = PX == 0 ? 1.0f : -1.0f;
     const float X = z.X.hi, Px = z.Px.hi, Y = z.Y.hi, Py = z.Py.hi;
     const float Pk = k.P * k1;
     const float tsum = Px * Px * q.al[px_] - k1 * X * Px * q.be[px_] + Pk * X * X * q.ga[px_] +
                        Py * Py * q.al[py_] + k1 * Y * Py * q.be[py_] - Pk * Y * Y * q.ga[py_];
-    const FF dX = ff_add(ff_mul(z.X, q.Cm1[px_]), ff_mul(z.Px, q.SP[px_]));
-    const FF dPx = ff_add(ff_mul(z.Px, q.Cm1[px_]), ff_neg(ff_mul_f(ff_mul(z.X, q.kS[px_]), sgn)));
-    const FF dY = ff_add(ff_mul(z.Y, q.Cm1[py_]), ff_mul(z.Py, q.SP[py_]));
-    const FF dPy = ff_add(ff_mul(z.Py, q.Cm1[py_]), ff_mul_f(ff_mul(z.Y, q.kS[py_]), sgn));
-    z.X = ff_add(z.X, dX);
-    z.Px = ff_add(z.Px, dPx);
-    z.Y = ff_add(z.Y, dY);
-    z.Py = ff_add(z.Py, dPy);
+    // both planes at once in packed FP32x2 arithmetic: (X, Y) and (Px, Py)
+    const FF2 U = ff2_pack(z.X, z.Y), PU = ff2_pack(z.Px, z.Py);
+    const FF2 Cm1 = ff2_pack(q.Cm1[px_], q.Cm1[py_]), SP = ff2_pack(q.SP[px_], q.SP[py_]);
+    const FF kSx = q.kS[px_], kSy = q.kS[py_];
+    const FF2 kS = ff2_pack(FF{-sgn * kSx.hi, -sgn * kSx.lo}, FF{sgn * kSy.hi, sgn * kSy.lo});   // exact sign flips
+    const FF2 dU = ff2_add(ff2_mul(U, Cm1), ff2_mul(PU, SP));
+    const FF2 dPU = ff2_add(ff2_mul(PU, Cm1), ff2_mul(U, kS));
+    const FF2 U1 = ff2_add(U, dU), PU1 = ff2_add(PU, dPU);
+    z.X = ff2_first(U1);
+    z.Y = ff2_second(U1);
+    z.Px = ff2_first(PU1);
+    z.Py = ff2_second(PU1);
     z.T = ff_add_f(z.T, -k.f3 * tsum);
+}
+
+// the sign of k1 is uniform per element, so the branch does not diverge
+__device__ __forceinline__ void quad_linear_inc(MState& z, const MConst& k, const MQuad& q, float k1) {
+    if (k1 >= 0.0f)
+        quad_linear_inc_<0>(z, k, q, k1);
+    else
+        quad_linear_inc_<1>(z, k, q, k1);
 }
 
 template <int K>
@@ -505,8 +556,10 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 float ps2 = Pa2 - px * px;
                 float ips = rsqrtf(ps2);
                 float Ps = ps2 * ips;
-                // Ps - 1 = (P - 1) + (Ps - P), the second term -p^2/(Ps + P) second order
-                FF PsM1 = ff_add_f(k.PM1, -(px * px + py * py) / (Ps + k.P));
+                // Ps - 1 = (P - 1) + (Ps - P), the second term dPsP = -p^2/(Ps + P) second
+                // order (about 1e-8), so a reciprocal good to 2 ulp is exact enough for it
+                float dPsP = -__fdividef(px * px + py * py, Ps + k.P);
+                FF PsM1 = ff_add_f(k.PM1, dPsP);
                 const float etah = eta * h;
                 const float cu = k.c * py * etah * k.invPf * k.invPf;     // G(gamma-1)(u.b)/P, u.b = Py eta h / P
                 const FF ietads{el.ietads_ff.x, el.ietads_ff.y};
@@ -515,6 +568,8 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 const FF cbmieh{el.cbmieh_ff.x, el.cbmieh_ff.y};
                 const FF etahff{el.etah_ff.x, el.etah_ff.y};
                 const FF omeff{el.ome_ff.x, el.ome_ff.y};
+                const bool eta1 = el.ome_ff.x == 0.0f;   // eta = 1: A needs no 1 - eta term
+                const FF iehff{el.ieh_ff.x, el.ieh_ff.y};
                 // T increment of the bend without the path term: (1 - 1/eta) ds/beta0 - Pt ds/eta
                 const FF dT0 = ff_add(FF{el.dTeta_ff.x, el.dTeta_ff.y}, ff_neg(ff_mul(k.Ptf, ietads)));
                 const FF cbm1ff{el.cbm1_ff.x, el.cbm1_ff.y};
@@ -531,13 +586,13 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 const FF B0 = ff_mul(etahff, k.c1P);
                 const FF B1 = ff_mul(FF{el.eh2_ff.x, el.eh2_ff.y}, k.a0P);
                 const float apda = k.a0 + k.da;
-                auto dev_omega = [&](const FF& Xf, float Pxv, float Psv, float ipsv, float& dx, FF& dy, float& dz) {
+                auto dev_omega = [&](const FF& Xf, float Pxv, float Psv, float ipsv, float dPsPv, float& dx, FF& dy,
+                                     float& dz) {
                     const float hX = h * Xf.hi;
                     const float g = (1.0f + hX) * ipsv;
-                    const float dPsP = -(Pxv * Pxv + py * py) / (Psv + k.P);   // Ps - P
-                    const float dd = -dPsP * k.invPf * ipsv;                  // 1/Ps - 1/P
-                    const float Nf = k.c1 + k.a0 * dPsP - hX * apda;
-                    const float rest = etah * ((k.a0 * dPsP - hX * k.da) * k.invPf + Nf * dd) + g * cu * py;
+                    const float dd = -dPsPv * k.invPf * ipsv;                 // 1/Ps - 1/P
+                    const float Nf = k.c1 + k.a0 * dPsPv - hX * apda;
+                    const float rest = etah * ((k.a0 * dPsPv - hX * k.da) * k.invPf + Nf * dd) + g * cu * py;
                     dy = ff_addn(ff_add(B0, ff_neg(ff_mul(B1, Xf))), rest);
                     dx = g * cu * Pxv;
                     dz = g * cu * Psv;
@@ -552,16 +607,19 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     // dX = (dPs - dA)/(eta h) with dA = A (cos - 1) - Px sin
                     // A = (Ps - 1) + (1 - eta) - eta h X, compensated (first order in the
                     // momentum deviation and in X)
-                    const FF Aff = ff_add(ff_add(PsM1, omeff), ff_neg(ff_mul(etahff, z.X)));
+                    FF PsE = PsM1;
+                    if (!eta1) PsE = ff_add(PsM1, omeff);
+                    const FF Aff = ff_add(PsE, ff_neg(ff_mul(etahff, z.X)));
                     const FF dPxff = ff_add(ff_mul(Aff, sbff), ff_mul(z.Px, cbm1ff));
                     // dPx / (eta h) = A sin(h ds)/(eta h) + Px (cos(h ds) - 1)/(eta h)
-                    const FF dPxieh = ff_add(ff_mul(Aff, sbieh), ff_mul(z.Px, cbmieh));
+                    const FF dPxieh = ff_mul(dPxff, iehff);
                     const float dPx = dPxff.hi;
                     const float pxf = px + dPx;
                     const float ps2f = Pa2 - pxf * pxf;
                     const float ipsf = rsqrtf(ps2f);
                     const float Psf = ps2f * ipsf;
-                    const FF PsfM1 = ff_add_f(k.PM1, -(pxf * pxf + py * py) / (Psf + k.P));
+                    const float dPsPf = -__fdividef(pxf * pxf + py * py, Psf + k.P);
+                    const FF PsfM1 = ff_add_f(k.PM1, dPsPf);
                     // The second-order terms below carry the factor 1/(eta h) (hundreds of
                     // metres in a large ring), so they are compensated as well.
                     // Q = (Ps_f - Ps)/(eta h) = -dPx/(eta h) (Px + Px_f) / (Ps + Ps_f), with
@@ -588,14 +646,17 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     z.Px = ff_add(z.Px, dPxff);
                     z.Y = ff_add(z.Y, dY);
                     z.T = ff_add(z.T, ff_add(dT0, ff_neg(ff_mul(k.b0ptf, dpsieh))));
-                    px = z.Px.hi;
-                    ps2 = Pa2 - px * px;
-                    ips = rsqrtf(ps2);
-                    Ps = ps2 * ips;
-                    PsM1 = ff_add_f(k.PM1, -(px * px + py * py) / (Ps + k.P));
+                    // the slice-end momentum quantities carry over (px_f differs from the
+                    // compensated Px's high part by at most an ulp: 1e-16 in Ps - P)
+                    px = pxf;
+                    ps2 = ps2f;
+                    ips = ipsf;
+                    Ps = Psf;
+                    dPsP = dPsPf;
+                    PsM1 = PsfM1;
                   }
                     if constexpr (SPIN) {
-                        dev_omega(z.X, px, Ps, ips, ox, oyf, os);
+                        dev_omega(z.X, px, Ps, ips, dPsP, ox, oyf, os);
                         const float2 r = rh[s];
                         lv.add_bend(s, N, el, r.x, r.y, ox, oyf, os);
                     }
@@ -629,11 +690,15 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                             drift_inc(z, k, half, ips_ff, d);
                             // kick of H_m over ds, compensated (the sextupole kick is first
                             // order in the betatron offset around a dispersive orbit)
-                            const FF x2my2 = ff_add(ff_mul(z.X, z.X), ff_neg(ff_mul(z.Y, z.Y)));
-                            const FF kx = ff_add(ff_mul(z.X, k1ds), ff_mul(x2my2, k2h));
-                            const FF ky = ff_add(ff_mul(z.Y, k1ds), ff_mul(ff_mul(z.X, z.Y), k2ds));
-                            z.Px = ff_add(z.Px, ff_neg(kx));
-                            z.Py = ff_add(z.Py, ky);
+                            // (X^2, XY) in one packed product, then X^2 - Y^2
+                            const FF2 xx = ff2_mul(ff2_pack(z.X, z.X), ff2_pack(z.X, z.Y));
+                            const FF x2my2 = ff_add(ff2_first(xx), ff_neg(ff_mul(z.Y, z.Y)));
+                            // (-kx, ky) = -(X, -Y) k1 ds - (x2my2 k2 ds/2, -XY k2 ds), packed
+                            const FF2 kk = ff2_add(ff2_mul(ff2_pack(ff_neg(z.X), z.Y), ff2_pack(k1ds, k1ds)),
+                                                   ff2_mul(ff2_pack(ff_neg(x2my2), ff2_second(xx)), ff2_pack(k2h, k2ds)));
+                            const FF2 PU = ff2_add(ff2_pack(z.Px, z.Py), kk);
+                            z.Px = ff2_first(PU);
+                            z.Py = ff2_second(PU);
                             ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                             ips = ips_ff.hi;
                             Ps = (k.P2 - pp) * ips;
@@ -643,8 +708,17 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                             inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                             // H_qNL over ds, Eq. (25), in increment form:
                             // dX = ds Px (1/Ps - 1/P); dT = ds [tau - (1/beta0+Pt)(d - p^2/(2P^3))]
-                            z.X = ff_add_f(z.X, ds * z.Px.hi * d);
-                            z.Y = ff_add_f(z.Y, ds * z.Py.hi * d);
+                            {   // (X, Y) += ds d (Px, Py): second order, added to the pair
+                                const float2 inc = __fmul2_rn(make_float2(z.Px.hi, z.Py.hi), make_float2(ds * d, ds * d));
+                                FF2 U = ff2_pack(z.X, z.Y);
+                                float2 sh, se;
+                                two_sum2(U.hi, inc, sh, se);
+                                se = __fadd2_rn(se, U.lo);
+                                U.hi = __fadd2_rn(sh, se);
+                                U.lo = f2_sub(se, f2_sub(U.hi, sh));
+                                z.X = ff2_first(U);
+                                z.Y = ff2_second(U);
+                            }
                             z.T = ff_add(z.T, ff_mul(dsff, ff_add_f(k.tau, -k.b0pt * (d - 0.5f * pp * k.invPf * k.invPf * k.invPf))));
                             quad_linear_inc(z, k, mq, k1);
                             ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
@@ -674,7 +748,7 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 const bool fr = FR && (el.type & ST_MIX_FRINGE);
                 if (fr) fq_premul_cnq(qt, mixed_fringe(el, type, z0, 1.0f, 1.0f + (float)ref.G));
                 fq_premul_cnq(qt, dq);
-                if (type == ST_SBEND) fq_premul_ref(qt, el.rq);
+                if (type == ST_SBEND) fq_premul_about_y(qt, el.rq);
                 if (fr) fq_premul_cnq(qt, mixed_fringe(el, type, z, -1.0f, 1.0f + (float)ref.G));
             } else {
                 if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi)) {
