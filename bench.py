@@ -307,10 +307,13 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 MIXED_WORKLOAD_PARTICLES = 1_000_000
-# FP32 floating-point operations the mixed tracker executes per pass on this
-# workload (2 per FFMA, 1 per FADD/FMUL), from one ncu capture
-# (profiles/track_mixed_rhic_like_ncu.md); None until measured.
-MIXED_FP32_FLOPS_PER_PASS = 2251.3
+# FMA-pipe instructions the mixed tracker executes per pass on this workload
+# (thread level: warp instructions x 32 / passes), from one ncu capture
+# (profiles/track_mixed_rhic_like_ncu.md).  Packed FP32x2 instructions count
+# once and the counters cannot tell them from scalar ones, so the executed
+# measure is the share of the FMA pipe's issue slots (128 lanes per SM per
+# clock), not a flop count.
+MIXED_FMA_PIPE_INSTR_PER_PASS = 1342.0
 
 
 def variant_mixed(st, torch, args, fp64_value, fp32_peak):
@@ -342,7 +345,10 @@ def variant_mixed(st, torch, args, fp64_value, fp32_peak):
     lat.close()
     algo = ALGO_FLOPS_PER_PASS.get(args.spin_order)
     achieved = algo * n * n_el / (t / steps) / 1e12 if algo else None
-    ex = MIXED_FP32_FLOPS_PER_PASS * n * n_el / (t / steps) / 1e12 if MIXED_FP32_FLOPS_PER_PASS else None
+    rate_now = n * n_el * steps / t
+    sm_hz = 2032.0e6
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fma_issue = MIXED_FMA_PIPE_INSTR_PER_PASS * rate_now / (128.0 * n_sm * sm_hz)
     out = {"metric": "particle-element passes/s", "value": value, "unit": "passes/s",
            "speedup_vs_fp64": value / fp64_value, "dtype": "f32 (compensated) + f64 per turn",
            "config": {"workload": f"108-cell RHIC-like ring, {n} Gaussian protons, Ggamma={args.ggamma}, "
@@ -350,8 +356,8 @@ def variant_mixed(st, torch, args, fp64_value, fp32_peak):
            "roofline": {"bound": "alu", "pipe": "fp32", "achieved": achieved, "peak": fp32_peak / 1e12,
                         "unit": "TFLOP/s", "frac": achieved / (fp32_peak / 1e12) if achieved else None,
                         "algorithmic_flops_per_pass": algo,
-                        "executed": {"fp32_flops_per_pass": MIXED_FP32_FLOPS_PER_PASS, "tflops": ex,
-                                     "frac_of_peak": ex / (fp32_peak / 1e12) if ex else None}},
+                        "executed": {"fma_pipe_instr_per_pass": MIXED_FMA_PIPE_INSTR_PER_PASS,
+                                     "fma_pipe_issue_frac_at_max_clock": fma_issue}},
            "error_vs_fp64": {}}
     # accuracy: 1024-particle subset, mixed vs the FP64 tracker (pinned to the oracle)
     for gg in sorted({args.ggamma, 45.5, 487.0}):
@@ -683,6 +689,7 @@ def main():
     tr.set_launch(block_threads=128, turns_per_launch=1)
     tr.upload(z, S)
     fp64_peak, fp32_peak = st.st_measure_peaks()
+    fp32x2_peak = st.st_measure_fp32x2_peak()
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     launches_per_step = 1
@@ -811,7 +818,8 @@ def main():
         "variants": variants,
         "clocks": clocks,
         "wall_s_timed": wall,
-        "peaks_measured": {"fp64_tflops": fp64_peak / 1e12, "fp32_tflops": fp32_peak / 1e12},
+        "peaks_measured": {"fp64_tflops": fp64_peak / 1e12, "fp32_tflops": fp32_peak / 1e12,
+                           "fp32x2_tflops": fp32x2_peak / 1e12},
     }
     print(json.dumps(out))
     tr.close()

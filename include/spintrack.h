@@ -294,6 +294,12 @@ int st_batch_autotune(st_batch* batch, int32_t spin_order, int32_t trial_turns, 
  * trackers' arithmetic roofline.  Errors: ST_EINVAL (NULL), ST_ECUDA. */
 int st_measure_peaks(double* fp64_flops, double* fp32_flops);
 
+/* The same FP32 measurement with Blackwell's packed FP32x2 fused
+ * multiply-add (two per instruction, independent chains): *fp32_flops in
+ * flop/s.  It shows whether the packed instructions raise the FP32 rate or
+ * only save issue slots.  About 0.1 s.  Errors: ST_EINVAL (NULL), ST_ECUDA. */
+int st_measure_fp32x2_peak(double* fp32_flops);
+
 /* Failure-path self-test of the device-side bounded waits: one block waits,
  * with the library's bounded mbarrier wait, on a barrier that nothing ever
  * completes (no copy is issued, so nothing is left in flight).  The wait

@@ -67,6 +67,7 @@ SIGNATURES = {
     "st_track_average": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP], ctypes.c_int),
     "st_ctx_set_launch": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "st_measure_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "st_measure_fp32x2_peak": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "st_track_fp64_noalloc": ([ctypes.POINTER(StElement), ctypes.c_int32, ctypes.POINTER(StReference), _VP, _VP,
                                ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _VP], ctypes.c_int),
     "st_tune_slicing": ([ctypes.POINTER(StElement), ctypes.c_int32, ctypes.POINTER(StReference), _VP, _VP,
@@ -215,6 +216,13 @@ def st_measure_peaks():
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load().st_measure_peaks(ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def st_measure_fp32x2_peak() -> float:
+    """FP32 flop/s of the current device with packed FP32x2 fused multiply-adds."""
+    a = ctypes.c_double()
+    _check(load().st_measure_fp32x2_peak(ctypes.byref(a)))
+    return a.value
 
 
 def st_track_fp64_noalloc(elements: List[Dict], G: float, Ggamma0: float, state_ptr: int, lost_ptr: int,
