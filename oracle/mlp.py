@@ -11,7 +11,9 @@ W1[256][6], b1, W2[256][256], b2, W3, b3, W4, b4, W5[4][256], b5.
 `bf16=True` rounds the weights and every hidden activation to bfloat16 (round
 to nearest even) and represents the scaled input as the two-term bf16 split of
 its float32 value, keeping FP64 arithmetic: the storage precision of the GPU
-kernels without their FP32 accumulation order.
+kernels without their FP32 accumulation order.  `bf16_grads=True` also stores
+the back-propagated dL/dy and every dL/dz in bfloat16, as the kernels do
+between their gradient GEMMs (the arithmetic stays FP64).
 """
 from __future__ import annotations
 
@@ -87,15 +89,18 @@ def network(p, a0, bf16=False):
     return y, dict(layers=layers, acts=acts, zs=zs, rd=rd)
 
 
-def backward(c, gy):
-    """Gradient (flattened, parameter order) from dL/dy [B, 4]."""
+def backward(c, gy, bf16_grads=False):
+    """Gradient (flattened, parameter order) from dL/dy [B, 4]; bf16_grads
+    stores dL/dy and each dL/dz in bfloat16 before it is used."""
     rd = c["rd"]
+    rg = round_bf16 if bf16_grads else (lambda a: a)
     grads = [None] * 5
     W5, _ = c["layers"][4]
+    gy = rg(gy)
     grads[4] = (gy.T @ c["acts"][4], gy.sum(axis=0))
     ga = gy @ rd(W5)
     for l in range(3, -1, -1):
-        gz = ga * dsilu(c["zs"][l])
+        gz = rg(ga * dsilu(c["zs"][l]))
         W, _ = c["layers"][l]
         grads[l] = (gz.T @ c["acts"][l], gz.sum(axis=0))
         ga = gz @ rd(W)
@@ -135,7 +140,7 @@ def forward(p, x, head, bf16=False):
     return q, c
 
 
-def loss_grad(p, x, qt, head, bf16=False):
+def loss_grad(p, x, qt, head, bf16=False, bf16_grads=False):
     """Loss mean_b |q_b - qt_b|^2 and its gradient (flattened, parameter order)."""
     q, c = forward(p, x, head, bf16)
     B = q.shape[0]
@@ -143,15 +148,15 @@ def loss_grad(p, x, qt, head, bf16=False):
     loss = float((d * d).sum() / B)
     gq = 2.0 * d / B
     gu = (gq - q * (q * gq).sum(axis=1, keepdims=True)) / c["nrm"]
-    return loss, backward(c, head["scale"] * gu)
+    return loss, backward(c, head["scale"] * gu, bf16_grads)
 
 
-def residual_loss_grad(p, x, r, in_scale, bf16=False):
+def residual_loss_grad(p, x, r, in_scale, bf16=False, bf16_grads=False):
     """Regression of the raw outputs: loss mean_b |y_b - r_b|^2 and its gradient."""
     y, c = network(p, scaled_input(x, in_scale, bf16), bf16)
     B = y.shape[0]
     d = y - r
-    return float((d * d).sum() / B), backward(c, 2.0 * d / B)
+    return float((d * d).sum() / B), backward(c, 2.0 * d / B, bf16_grads)
 
 
 def quat_from_images(ex, ey):

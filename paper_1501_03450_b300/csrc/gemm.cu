@@ -137,19 +137,39 @@ int gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const GemmEp
     return launch_gemm_bn<16, 4>(A, B, M, N, K, epi, status, stream, splits);
 }
 
-__global__ void split_reduce_kernel(const float4* __restrict__ ws, int splits, int64_t stride4, int64_t count4,
-                                    float4* __restrict__ out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count4) return;
-    float4 a = ws[i];
-    for (int z = 1; z < splits; ++z) {
-        const float4 b = ws[(int64_t)z * stride4 + i];
-        a.x += b.x;
-        a.y += b.y;
-        a.z += b.z;
-        a.w += b.w;
+// out[i] = sum_z ws[z][i] for float4 entries: each block handles 32 consecutive
+// entries (one per lane, coalesced 512-byte rows); its 8 warps take the splits
+// z = w, w + 8, ... and their partial sums are added in shared memory in a
+// fixed order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) split_reduce_kernel(const float4* __restrict__ ws, int splits, int64_t stride4,
+                                                           int64_t count4, float4* __restrict__ out) {
+    __shared__ float4 part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < count4) {
+#pragma unroll 4
+        for (int z = w; z < splits; z += 8) {
+            const float4 b = ws[(int64_t)z * stride4 + i];
+            a.x += b.x;
+            a.y += b.y;
+            a.z += b.z;
+            a.w += b.w;
+        }
     }
-    out[i] = a;
+    part[w][lane] = a;
+    __syncthreads();
+    if (w == 0 && i < count4) {
+        float4 r = part[0][lane];
+        for (int k = 1; k < 8; ++k) {
+            const float4 b = part[k][lane];
+            r.x += b.x;
+            r.y += b.y;
+            r.z += b.z;
+            r.w += b.w;
+        }
+        out[i] = r;
+    }
 }
 
 int gemm_split_reduce(const float* ws, int splits, int64_t stride, int64_t count, float* out, cudaStream_t stream) {
@@ -158,8 +178,8 @@ int gemm_split_reduce(const float* ws, int splits, int64_t stride, int64_t count
         return ST_EINVAL;
     }
     const int64_t c4 = count / 4;
-    split_reduce_kernel<<<(unsigned)((c4 + 255) / 256), 256, 0, stream>>>((const float4*)ws, splits, stride / 4, c4,
-                                                                          (float4*)out);
+    split_reduce_kernel<<<(unsigned)((c4 + 31) / 32), 256, 0, stream>>>((const float4*)ws, splits, stride / 4, c4,
+                                                                        (float4*)out);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ST_OK : cuda_fail(e, "gemm_split_reduce");
 }

@@ -267,14 +267,35 @@ __global__ void mlp_head_resid(const float* __restrict__ Y, const float* __restr
     block_loss_add(l / B, loss);
 }
 
-// row sums of a [rows][Bp] bf16 matrix (bias gradients), one warp per row
-__global__ void mlp_rowsum(const __nv_bfloat16* __restrict__ M, int rows, int Bp, float* __restrict__ out) {
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= rows) return;
+// row sums of a [rows][Bp] bf16 matrix (bias gradients): one block of 256
+// threads per row, 16-byte loads of 8 values (Bp is a multiple of 128, rows
+// 16-byte aligned), a fixed-order tree over the block
+constexpr int ROWSUM_THREADS = 256;
+__global__ void __launch_bounds__(ROWSUM_THREADS) mlp_rowsum(const __nv_bfloat16* __restrict__ M, int rows, int Bp,
+                                                            float* __restrict__ out) {
+    __shared__ float red[ROWSUM_THREADS / 32];
+    const int row = blockIdx.x;
+    const uint4* v = reinterpret_cast<const uint4*>(M + (size_t)row * Bp);
+    const int n8 = Bp / 8;
     float s = 0.0f;
-    for (int c = threadIdx.x & 31; c < Bp; c += 32) s += __bfloat162float(M[(size_t)row * Bp + c]);
+#pragma unroll 4
+    for (int c = threadIdx.x; c < n8; c += ROWSUM_THREADS) {
+        const uint4 q = v[c];
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __bfloat1622float2(h[k]);
+            s += f.x + f.y;
+        }
+    }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) out[row] = s;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int k = 0; k < ROWSUM_THREADS / 32; ++k) t += red[k];
+        if (row < rows) out[row] = t;
+    }
 }
 
 // dW1 [256][6] from dWtmp [256][64]: the hi and lo input columns share W1
@@ -530,7 +551,7 @@ static int mlp_backward(st_mlp* n, int Bp) {
     if (rc) return rc;
     GemmEpi ep;
     mlp_gather_w5<<<(MLP_OUT * MLP_H + 255) / 256, 256, 0, n->stream>>>(n->dWtmp, g + mlp_w_off(4));
-    mlp_rowsum<<<1, 128, 0, n->stream>>>(n->dYT, MLP_OUT, Bp, g + mlp_b_off(4));
+    mlp_rowsum<<<MLP_OUT, ROWSUM_THREADS, 0, n->stream>>>(n->dYT, MLP_OUT, Bp, g + mlp_b_off(4));
     ep = epi_base();
     ep.mode = EPI_DSILU;
     ep.n_valid = MLP_H;
@@ -549,7 +570,7 @@ static int mlp_backward(st_mlp* n, int Bp) {
         // dW_l = dZ_l^T . A_{l-1}  ->  [256 out][256 in], into the gradient buffer
         rc = wgrad_gemm(n, n->dZT[cur], n->AT[l - 1], MLP_H, MLP_H, Bp, g + mlp_w_off(l));
         if (rc) return rc;
-        mlp_rowsum<<<MLP_H / 4, 128, 0, n->stream>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(l));
+        mlp_rowsum<<<MLP_H, ROWSUM_THREADS, 0, n->stream>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(l));
         // dZ_{l-1} = (dZ_l W_l) * silu'(Z_{l-1})
         ep = epi_base();
         ep.mode = EPI_DSILU;
@@ -568,7 +589,7 @@ static int mlp_backward(st_mlp* n, int Bp) {
     rc = wgrad_gemm(n, n->dZT[cur], n->X0T, MLP_H, MLP_KIN, Bp, n->dWtmp);
     if (rc) return rc;
     mlp_gather_w1<<<(MLP_H * MLP_IN + 255) / 256, 256, 0, n->stream>>>(n->dWtmp, g + mlp_w_off(0));
-    mlp_rowsum<<<MLP_H / 4, 128, 0, n->stream>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(0));
+    mlp_rowsum<<<MLP_H, ROWSUM_THREADS, 0, n->stream>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(0));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "mlp: backward");
     n->have_grads = true;

@@ -98,11 +98,25 @@ def test_forward_matches_reference(B):
     net.close()
 
 
+# Gradient tolerance.  The reference emulates every bf16 store of the
+# kernels (weights, activations, dL/dy, dL/dz) and computes in FP64; what is
+# left is the kernels' FP32 accumulation: relative ~2^-24 sqrt(K) per sum (1e-5
+# for K = 32768), and the bf16 stores whose FP32 and FP64 values fall on
+# opposite sides of a rounding boundary.  Such a flip has probability
+# ~2^-24 sqrt(256) / 2^-8 = 2^-12 per stored value and changes it by 2^-8
+# relative, adding ~sqrt(2^-12) 2^-8 = 6e-5 to a block's relative L2 error
+# per stored stage; nine stages (four activations, dL/dy, four dL/dz) give
+# ~2e-4.  A bias gradient is a sum over the batch of values of both signs, so
+# its relative error is larger by the cancellation of that sum (measured: up
+# to 7.3e-4 for b1 at a batch of 1000, 3e-5 to 3e-4 elsewhere).  The bound
+# keeps a factor 3 over the largest measured block.
+GRAD_REL_TOL = 2e-3
+
+
 def test_loss_and_gradient_match_reference():
-    """Loss and all 200196 gradient entries against the reference (bf16
-    storage emulated, FP64 arithmetic).  The kernels also round the
-    back-propagated dL/dy and dL/dz to bf16 (relative 2^-9 each), so every
-    parameter block agrees to a relative L2 error of a few 1e-3."""
+    """Loss and all 200196 gradient entries against the reference with every
+    bf16 store emulated (weights, activations, dL/dy, dL/dz) and FP64
+    arithmetic: every parameter block to GRAD_REL_TOL in relative L2."""
     B = 1000
     p = random_params(7, last_scale=1.0)
     h = head_for(5)
@@ -115,15 +129,16 @@ def test_loss_and_gradient_match_reference():
     loss, g = net.loss_grad(xd.data_ptr(), qd.data_ptr(), B, want_grads=True)
     x32 = x.astype(np.float32).astype(np.float64)
     qt32 = qt.astype(np.float32).astype(np.float64)
-    lo, go = M.loss_grad(f32_params(p), x32, qt32, h, bf16=True)
+    lo, go = M.loss_grad(f32_params(p), x32, qt32, h, bf16=True, bf16_grads=True)
     assert loss == pytest.approx(lo, rel=2e-3)
     offs = np.cumsum([0] + [r * c + r for r, c in M.LAYERS])
+    rels = []
     for l, (r, c) in enumerate(M.LAYERS):
         for a, b in ((offs[l], offs[l] + r * c), (offs[l] + r * c, offs[l + 1])):
             gg, gr = g[a:b].astype(np.float64), go[a:b]
-            rel = np.linalg.norm(gg - gr) / np.linalg.norm(gr)
-            assert rel < 2e-2, (l, a, rel)
-            assert np.dot(gg, gr) / (np.linalg.norm(gg) * np.linalg.norm(gr)) > 0.9995
+            rels.append(np.linalg.norm(gg - gr) / np.linalg.norm(gr))
+    print("relative L2 error per block (W1, b1, ..., W5, b5):", ["%.1e" % v for v in rels])
+    assert max(rels) < GRAD_REL_TOL, rels
     net.close()
 
 
@@ -173,8 +188,8 @@ def test_training_reduces_loss_on_a_smooth_map():
 
 @pytest.mark.parametrize("B", [700, 8192])
 def test_residual_loss_and_gradient_match_reference(B):
-    """As the quaternion loss; B = 8192 runs the weight gradients as split-K
-    GEMMs (64 K pieces, reduced in a fixed order)."""
+    """As the quaternion loss, to GRAD_REL_TOL; B = 8192 runs the weight
+    gradients as split-K GEMMs (64 K pieces, reduced in a fixed order)."""
     p = random_params(8, last_scale=1.0)
     x = rand_x(B, 2)
     r = np.random.default_rng(4).standard_normal((B, 4))
@@ -183,12 +198,15 @@ def test_residual_loss_and_gradient_match_reference(B):
     loss, g = net.loss_grad_residual(xd.data_ptr(), rd.data_ptr(), B, want_grads=True)
     x32 = x.astype(np.float32).astype(np.float64)
     r32 = r.astype(np.float32).astype(np.float64)
-    lo, go = M.residual_loss_grad(f32_params(p), x32, r32, IN_SCALE, bf16=True)
+    lo, go = M.residual_loss_grad(f32_params(p), x32, r32, IN_SCALE, bf16=True, bf16_grads=True)
     assert loss == pytest.approx(lo, rel=2e-3)
     offs = np.cumsum([0] + [a * b + a for a, b in M.LAYERS])
+    rels = []
     for l, (a, b) in enumerate(M.LAYERS):
         gg, gr = g[offs[l]:offs[l + 1]].astype(np.float64), go[offs[l]:offs[l + 1]]
-        assert np.linalg.norm(gg - gr) / np.linalg.norm(gr) < 2e-2, l
+        rels.append(np.linalg.norm(gg - gr) / np.linalg.norm(gr))
+    print(f"B={B} relative L2 error per layer:", ["%.1e" % v for v in rels])
+    assert max(rels) < GRAD_REL_TOL, rels
     net.close()
 
 
