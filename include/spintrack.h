@@ -446,6 +446,18 @@ int st_mlp_loss_grad_residual(st_mlp* mlp, const float* x, const float* r_target
                               float* grads);
 /* One Adam update with the last gradients; refreshes the bf16 weights. */
 int st_mlp_adam_step(st_mlp* mlp, float lr, float beta1, float beta2, float eps);
+/* A training schedule in one call: for k = 0 .. steps-1, the residual loss
+ * and gradient (as st_mlp_loss_grad_residual) on the B rows starting at row
+ * row_start[k] of x_rows [n_rows][6] / r_rows [n_rows][4] (device memory,
+ * from st_mlp_make_targets), then one Adam update with learning rate lr[k]
+ * (as st_mlp_adam_step).  row_start, lr: host arrays of `steps` entries;
+ * loss_out: host double[steps] for every step's loss before its update, or
+ * NULL.  The steps are issued from the library without returning to the
+ * caller in between; synchronises at the end and reports a bounded-wait
+ * expiry of any step.  Errors: ST_EINVAL (arguments, a row range outside
+ * [0, n_rows), lr <= 0), ST_ECUDA, ST_ETIMEOUT. */
+int st_mlp_train(st_mlp* mlp, const float* x_rows, const float* r_rows, int64_t n_rows, int32_t B, int32_t steps,
+                 const int64_t* row_start, const float* lr, float beta1, float beta2, float eps, double* loss_out);
 /* Stroboscopic spin tracking with the learned map: per turn, the network
  * gives each particle's one-turn rotation from its FP64 orbit at s = 0 (head
  * in FP64), the spin is rotated by it (FP64), and the orbit is tracked

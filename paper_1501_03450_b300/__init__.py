@@ -99,6 +99,9 @@ SIGNATURES = {
     "st_mlp_loss_grad_residual": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), _VP],
                                   ctypes.c_int),
     "st_mlp_adam_step": ([_VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], ctypes.c_int),
+    "st_mlp_train": ([_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                      ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                      ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "st_track_surrogate": ([_VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
     "st_last_error": ([], ctypes.c_char_p),
     "st_version": ([], ctypes.c_char_p),
@@ -414,6 +417,23 @@ class MLP:
 
     def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
         _check(load().st_mlp_adam_step(self.handle, float(lr), float(beta1), float(beta2), float(eps)))
+
+    def train(self, x_ptr: int, r_ptr: int, n_rows: int, B: int, row_start, lr, beta1: float = 0.9,
+              beta2: float = 0.999, eps: float = 1e-8, want_loss: bool = False):
+        """A schedule of residual-loss Adam steps in one library call (see
+        st_mlp_train): row_start and lr give each step's first row and
+        learning rate.  Returns the per-step losses (or None)."""
+        rs = np.ascontiguousarray(row_start, dtype=np.int64)
+        lrs = np.ascontiguousarray(lr, dtype=np.float32)
+        if rs.shape != lrs.shape or rs.ndim != 1:
+            raise ValueError("row_start and lr must be 1-D arrays of equal length")
+        losses = np.zeros(len(rs)) if want_loss else None
+        _check(load().st_mlp_train(self.handle, x_ptr, r_ptr, int(n_rows), int(B), len(rs),
+                                   rs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   lrs.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), float(beta1), float(beta2),
+                                   float(eps),
+                                   losses.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_loss else None))
+        return losses
 
     def close(self):
         if self.handle:

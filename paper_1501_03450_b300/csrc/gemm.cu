@@ -123,9 +123,23 @@ int gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const GemmEp
         set_error("gemm: split-K needs the plain FP32 epilogue");
         return ST_EINVAL;
     }
-    // K blocks per CTA decide the pipeline depth; tiles of at most 128 columns
+    // K blocks per CTA decide the pipeline depth.  Short K: 128-wide tiles (3
+    // CTAs per SM), or 256-wide tiles (2 CTAs per SM: 97 KB of shared memory and
+    // 256 TMEM columns each) when those fit in one wave and the 128-wide ones
+    // would need a second, mostly empty one.
     const int kb = K / 64, per = (kb + splits - 1) / splits;
     if (per <= 4) {
+        if (N % 256 == 0 && splits == 1) {
+            static int sms_cache[kMaxDeviceFlags] = {0};
+            int dev = 0, sms = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDeviceFlags) {
+                if (!sms_cache[dev]) cudaDeviceGetAttribute(&sms_cache[dev], cudaDevAttrMultiProcessorCount, dev);
+                sms = sms_cache[dev];
+            }
+            const long tiles256 = (long)(M / 128) * (N / 256);
+            if (sms > 0 && tiles256 <= 2L * sms && 2 * tiles256 > 3L * sms)
+                return launch_gemm_bn<256, 2>(A, B, M, N, K, epi, status, stream, splits);
+        }
         if (N % 128 == 0) return launch_gemm_bn<128, 2>(A, B, M, N, K, epi, status, stream, splits);
         if (N % 64 == 0) return launch_gemm_bn<64, 2>(A, B, M, N, K, epi, status, stream, splits);
         if (N % 32 == 0) return launch_gemm_bn<32, 2>(A, B, M, N, K, epi, status, stream, splits);

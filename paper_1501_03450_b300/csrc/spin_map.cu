@@ -1015,6 +1015,46 @@ int st_mlp_adam_step(st_mlp* n, float lr, float beta1, float beta2, float eps) {
     return mlp_refresh_weights(n);
 }
 
+int st_mlp_train(st_mlp* n, const float* x_rows, const float* r_rows, int64_t n_rows, int32_t B, int32_t steps,
+                 const int64_t* row_start, const float* lr, float beta1, float beta2, float eps, double* loss_out) {
+    if (!n || !x_rows || !r_rows || !row_start || !lr || steps < 0 || B < 1 || B > n->max_batch) {
+        set_error("st_mlp_train: null pointer, steps < 0 or batch outside 1..max_batch");
+        return ST_EINVAL;
+    }
+    for (int k = 0; k < steps; ++k)
+        if (row_start[k] < 0 || row_start[k] + B > n_rows || !(lr[k] > 0.0f)) {
+            set_error("st_mlp_train: step %d: rows [%lld, %lld) outside the %lld rows, or lr <= 0", k,
+                      (long long)row_start[k], (long long)(row_start[k] + B), (long long)n_rows);
+            return ST_EINVAL;
+        }
+    if (steps == 0) return ST_OK;
+    double* d_loss = nullptr;
+    if (loss_out) {
+        cudaError_t e = cudaMallocAsync((void**)&d_loss, (size_t)steps * sizeof(double), n->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "st_mlp_train: loss buffer");
+    }
+    int rc = ST_OK;
+    for (int k = 0; k < steps && rc == ST_OK; ++k) {
+        rc = st_mlp_loss_grad_residual(n, x_rows + row_start[k] * MLP_IN, r_rows + row_start[k] * MLP_OUT, B, nullptr,
+                                       nullptr);
+        if (rc == ST_OK && d_loss) {
+            cudaError_t e = cudaMemcpyAsync(d_loss + k, n->loss, sizeof(double), cudaMemcpyDeviceToDevice, n->stream);
+            if (e != cudaSuccess) rc = cuda_fail(e, "st_mlp_train: loss copy");
+        }
+        if (rc == ST_OK) rc = st_mlp_adam_step(n, lr[k], beta1, beta2, eps);
+    }
+    if (d_loss) {
+        if (rc == ST_OK) {
+            cudaError_t e = cudaMemcpyAsync(loss_out, d_loss, (size_t)steps * sizeof(double), cudaMemcpyDeviceToHost,
+                                            n->stream);
+            if (e != cudaSuccess) rc = cuda_fail(e, "st_mlp_train: loss download");
+        }
+        cudaFreeAsync(d_loss, n->stream);
+    }
+    if (rc) return rc;
+    return check_status(n, "st_mlp_train");
+}
+
 int st_track_surrogate(st_ctx* ctx, st_mlp* n, int32_t n_turns, double* spin_sum) {
     if (!ctx || !n) {
         set_error("st_track_surrogate: null pointer");

@@ -253,6 +253,13 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_const
     } else {
         const int row = m0 + threadIdx.x;
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        // the bias is read as 16-byte vectors when it is 16-byte aligned (every
+        // column chunk starts at a multiple of 16), element by element otherwise
+        const bool bias_v4 = ((uintptr_t)epi.bias & 15) == 0;
+        auto bias4 = [&](int c) -> float4 {
+            if (bias_v4) return __ldg(reinterpret_cast<const float4*>(epi.bias + c));
+            return make_float4(epi.bias[c], epi.bias[c + 1], epi.bias[c + 2], epi.bias[c + 3]);
+        };
         constexpr int CH = BN < 32 ? BN : 32;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += CH) {
@@ -268,17 +275,24 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_const
                 for (int j = 0; j < CH; j += 4) {
                     float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                     if (epi.mode == EPI_BIAS_F32) {
-                        o.x += epi.bias[nb + j];
-                        o.y += epi.bias[nb + j + 1];
-                        o.z += epi.bias[nb + j + 2];
-                        o.w += epi.bias[nb + j + 3];
+                        const float4 bb = bias4(nb + j);
+                        o.x += bb.x;
+                        o.y += bb.y;
+                        o.z += bb.z;
+                        o.w += bb.w;
                     }
                     *reinterpret_cast<float4*>(dst + j) = o;
                 }
             } else {
                 if (epi.mode == EPI_BIAS_SILU) {
 #pragma unroll
-                    for (int j = 0; j < CH; ++j) v[j] += epi.bias[nb + j];
+                    for (int j = 0; j < CH; j += 4) {   // the bias as 16-byte loads (same address across the warp)
+                        const float4 bb = bias4(nb + j);
+                        v[j] += bb.x;
+                        v[j + 1] += bb.y;
+                        v[j + 2] += bb.z;
+                        v[j + 3] += bb.w;
+                    }
                     if (epi.z_out) {
                         float* zd = epi.z_out + (size_t)row * epi.ld_zo + nb;
 #pragma unroll
@@ -318,9 +332,30 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_const
                     }
                 }
                 if (epi.out_bf16_t) {
+                    if constexpr (CH == 32) {
+                        // transpose the warp's 32 x 32 block through shared memory (the
+                        // pipeline ring is idle once the MMAs are done): lane = row writes
+                        // column j of its row at [j][lane], then each lane reads 16 bytes
+                        // (8 consecutive rows of one column) and the warp stores 8
+                        // transposed rows of 64 bytes per instruction
+                        __nv_bfloat16* tb = reinterpret_cast<__nv_bfloat16*>(smem) + warp * (32 * 32);
+                        const int lane = threadIdx.x & 31;
+                        __syncwarp();
 #pragma unroll
-                    for (int j = 0; j < CH; ++j)
-                        epi.out_bf16_t[(size_t)(nb + j) * epi.ld_bf16_t + row] = __float2bfloat16_rn(v[j]);
+                        for (int j = 0; j < 32; ++j) tb[j * 32 + lane] = __float2bfloat16_rn(v[j]);
+                        __syncwarp();
+                        const int row0 = m0 + warp * 32;
+#pragma unroll
+                        for (int it = 0; it < 4; ++it) {
+                            const int j = it * 8 + (lane >> 2), seg = lane & 3;
+                            const uint4 q = *reinterpret_cast<const uint4*>(tb + j * 32 + seg * 8);
+                            *reinterpret_cast<uint4*>(epi.out_bf16_t + (size_t)(nb + j) * epi.ld_bf16_t + row0 + seg * 8) = q;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < CH; ++j)
+                            epi.out_bf16_t[(size_t)(nb + j) * epi.ld_bf16_t + row] = __float2bfloat16_rn(v[j]);
+                    }
                 }
             }
         }

@@ -164,26 +164,29 @@ class SpinMapSurrogate:
               lr_final: float = 1e-6, log_every: int = 500, init_seed: int = None, warmup: int = 200):
         """Adam on the residual regression mean |y - r|^2 over contiguous
         batches of the (randomly ordered) rows; the learning rate warms up
-        linearly and then decays as a cosine from lr to lr_final."""
+        linearly and then decays as a cosine from lr to lr_final.  The
+        schedule (each step's first row and learning rate) is computed here
+        and the steps run in one library call."""
         n = x.shape[0]
         batch = min(int(batch), self.max_batch, n)
         self.mlp.set_params(init_params(self.seed if init_seed is None else init_seed))
         rng = np.random.default_rng(self.seed + 1)
         start = int(rng.integers(0, n - batch + 1))
+        starts = np.empty(steps, dtype=np.int64)
+        lrs = np.empty(steps, dtype=np.float32)
         for k in range(steps):
             if start + batch > n:
                 start = int(rng.integers(0, batch)) if n >= 2 * batch else 0
-            xp = _ptr(x) + start * 6 * 4
-            rp = _ptr(r) + start * 4 * 4
+            starts[k] = start
             start += batch
-            log = bool(log_every) and (k % log_every == 0 or k == steps - 1)
-            loss, _ = self.mlp.loss_grad_residual(xp, rp, batch, want_loss=log)
-            if log:
-                self.history.append((k, loss))
             f = min(1.0, (k + 1) / warmup) if warmup else 1.0
             c = 0.5 * (1 + math.cos(math.pi * k / max(1, steps - 1)))
-            self.mlp.adam_step(f * (lr_final + (lr - lr_final) * c))
-        self.stream.synchronize()
+            lrs[k] = f * (lr_final + (lr - lr_final) * c)
+        losses = self.mlp.train(_ptr(x), _ptr(r), n, batch, starts, lrs, want_loss=bool(log_every))
+        if log_every:
+            for k in range(steps):
+                if k % log_every == 0 or k == steps - 1:
+                    self.history.append((k, float(losses[k])))
         return self.history
 
     def eval_loss(self, x: torch.Tensor, r: torch.Tensor) -> float:

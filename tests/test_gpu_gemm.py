@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (256, 256, 256), (384, 128, 192), (128, 16, 256),
-                                   (256, 64, 512), (128, 32, 64), (1024, 256, 1024)])
+                                   (256, 64, 512), (128, 32, 64), (1024, 256, 1024), (32768, 256, 256)])
 @pytest.mark.parametrize("with_bias", [False, True])
 def test_gemm_matches_fp64_reference(M, N, K, with_bias):
     torch = pytest.importorskip("torch")
@@ -33,6 +33,28 @@ def test_gemm_matches_fp64_reference(M, N, K, with_bias):
     scale = (A.double().abs() @ B.double().abs().T).max()
     assert torch.isfinite(Dh).all()
     assert (Dh - ref).abs().max() / scale < 2e-6 * np.sqrt(K) + 1e-7
+
+
+def test_gemm_with_a_bias_that_is_not_16_byte_aligned():
+    """The epilogue reads the bias as 16-byte vectors when it can and element
+    by element otherwise: a bias starting one float into its buffer gives
+    the same result."""
+    torch = pytest.importorskip("torch")
+    M, N, K = 256, 128, 128
+    g = torch.Generator().manual_seed(5)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    buf = torch.randn(N + 1, generator=g, dtype=torch.float32).cuda()
+    aligned = buf[1:].clone()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    D1 = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    D2 = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    st.st_gemm_bf16(A.data_ptr(), B.data_ptr(), D1.data_ptr(), M, N, K, buf.data_ptr() + 4, status.data_ptr(), s)
+    st.st_gemm_bf16(A.data_ptr(), B.data_ptr(), D2.data_ptr(), M, N, K, aligned.data_ptr(), status.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert torch.equal(D1, D2)
 
 
 def test_gemm_rejects_bad_shapes():
