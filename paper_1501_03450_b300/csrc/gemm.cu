@@ -106,7 +106,7 @@ static int launch_gemm_bn(const void* A, const void* B, int M, int N, int K, con
     const int kblocks = K / 64;
     const int per = (kblocks + splits - 1) / splits;
     dim3 grid(M / 128, N / BN, (kblocks + per - 1) / per);
-    gemm_bf16_tn_kernel<BN, ST><<<grid, 128, Cf::SMEM_BYTES, stream>>>(ta, tb, K, per, epi, status);
+    gemm_bf16_tn_kernel<BN, ST><<<grid, Cf::THREADS, Cf::SMEM_BYTES, stream>>>(ta, tb, K, per, epi, status);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ST_OK : cuda_fail(e, "gemm launch");
 }

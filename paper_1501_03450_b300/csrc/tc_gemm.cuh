@@ -3,14 +3,15 @@
 // A and B bf16 row-major (K contiguous, "K-major" for both operands), FP32
 // accumulation in tensor memory (TMEM).
 //
-// One CTA of 128 threads computes a 128 x BN tile:
+// One CTA of 256 threads computes a 128 x BN tile:
 //   thread 0   : TMA producer -- 2D tensor-map loads of 64-wide K blocks of A
 //                and B into a 2- or 4-stage shared-memory ring, 128-byte swizzle
 //                (the canonical K-major SW128 layout the MMA reads directly);
 //   thread 32  : MMA issuer -- 4 x tcgen05.mma (K = 16 each) per K block,
 //                tcgen05.commit to the stage's "empty" barrier, and to the
 //                "done" barrier after the last block;
-//   all 4 warps: epilogue -- tcgen05.ld of their 32 TMEM lanes (= rows),
+//   all 8 warps: epilogue -- tcgen05.ld of their 32 TMEM lanes (= rows; warps
+//                w and w + 4 share lanes and split the columns),
 //                bias / SiLU / SiLU-derivative, FP32 or BF16 stores (row-major
 //                and, for backward passes, transposed).
 // Every mbarrier wait is bounded (about one second); on expiry the CTA sets
@@ -150,9 +151,14 @@ __device__ __forceinline__ void tmem_load_cols<16>(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU and its derivative.  Their results are rounded to bf16 (8 bits) or
+// multiply a gradient that is, so the fast division (2 ulp of FP32) is exact
+// enough; for z < -87 the exponential overflows the fast division's range and
+// the limits (0) are returned directly.
+__device__ __forceinline__ float silu_f(float z) { return z < -87.0f ? 0.0f : __fdividef(z, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float dsilu_f(float z) {
-    const float s = 1.0f / (1.0f + __expf(-z));
+    if (z < -87.0f) return 0.0f;
+    const float s = __fdividef(1.0f, 1.0f + __expf(-z));
     return s * (1.0f + z * (1.0f - s));
 }
 
@@ -163,6 +169,11 @@ __device__ __forceinline__ float dsilu_f(float z) {
 template <int BN, int ST>
 struct GemmCfg {
     static constexpr int BM = 128, BK = 64, STAGES = ST;
+    // 8 warps: warps w and w + 4 read the same 32 TMEM lanes (rows) and split
+    // the tile's columns in the epilogue; threads 0 and 32 also run the TMA
+    // producer and the MMA issuer before it
+    static constexpr int THREADS = 256;
+    static constexpr int MIN_BLOCKS = BN >= 256 ? 2 : (ST == 2 ? 3 : 1);
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -171,7 +182,7 @@ struct GemmCfg {
 };
 
 template <int BN, int ST>
-__global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(GemmCfg<BN, ST>::THREADS, GemmCfg<BN, ST>::MIN_BLOCKS) gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB, int K,
                                                               int kb_per_split, GemmEpi epi, int32_t* status) {
     using C = GemmCfg<BN, ST>;
@@ -243,7 +254,7 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_const
         }
         tc_commit(&done_bar);
     }
-    // epilogue: every thread owns TMEM lane (= row) threadIdx.x
+    // epilogue: every thread owns one TMEM lane (= row) of its warp's quarter
     const bool done_ok = mbar_wait_bounded_parity(&done_bar, 0, limit);
     tc_fence_after();
     __syncthreads();
@@ -251,8 +262,13 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_const
         if (threadIdx.x == 0) atomicExch(status, STATUS_MMA_TIMEOUT);
         if (!done_ok) mbar_wait_bounded_parity(&done_bar, 0, limit);   // let work in flight drain
     } else {
-        const int row = m0 + threadIdx.x;
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const int quarter = warp & 3;                 // TMEM lane quarter this warp may read
+        const int row = m0 + quarter * 32 + (threadIdx.x & 31);
+        const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+        // column range of this warp: the first or second half of the tile
+        constexpr int NHALF = BN >= 64 ? BN / 2 : BN;
+        const int c_begin = BN >= 64 ? (warp >> 2) * NHALF : ((warp >> 2) ? BN : 0);
+        const int c_end = BN >= 64 ? c_begin + NHALF : ((warp >> 2) ? BN : BN);
         // the bias is read as 16-byte vectors when it is 16-byte aligned (every
         // column chunk starts at a multiple of 16), element by element otherwise
         const bool bias_v4 = ((uintptr_t)epi.bias & 15) == 0;
@@ -262,7 +278,7 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_const
         };
         constexpr int CH = BN < 32 ? BN : 32;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += CH) {
+        for (int c0 = c_begin; c0 < c_end; c0 += CH) {
             float v[CH];
             tmem_load_cols<CH>(lane_addr + c0, v);
             const int nb = n0 + c0;
@@ -344,7 +360,7 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(const __grid_const
 #pragma unroll
                         for (int j = 0; j < 32; ++j) tb[j * 32 + lane] = __float2bfloat16_rn(v[j]);
                         __syncwarp();
-                        const int row0 = m0 + warp * 32;
+                        const int row0 = m0 + quarter * 32;
 #pragma unroll
                         for (int it = 0; it < 4; ++it) {
                             const int j = it * 8 + (lane >> 2), seg = lane & 3;
