@@ -435,6 +435,12 @@ int st_mlp_make_targets(st_mlp* mlp, const double* z_soa, const double* q_soa, i
                         float* r_rows);
 /* Inference: q[B][4] unit quaternions for x[B][6].  Asynchronous. */
 int st_mlp_forward(st_mlp* mlp, const float* x, int32_t B, float* q_out);
+/* Inference path of st_mlp_forward and st_track_surrogate: on != 0 (the
+ * default) runs all five layers of each 128-row tile in one kernel, the
+ * activations kept in shared memory and the accumulators in tensor memory;
+ * 0 runs one GEMM per layer.  Both give the same results (same bf16
+ * operands, accumulation order and epilogue).  Errors: ST_EINVAL (NULL). */
+int st_mlp_set_fused_inference(st_mlp* mlp, int32_t on);
 /* Loss L = mean_b |q_b - q_target_b|^2 of the normalised head output and its
  * gradient with respect to all parameters (kept on the device for
  * st_mlp_adam_step).  If loss / grads (host, may be NULL) are given they are

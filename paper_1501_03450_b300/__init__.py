@@ -99,6 +99,7 @@ SIGNATURES = {
     "st_mlp_loss_grad_residual": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), _VP],
                                   ctypes.c_int),
     "st_mlp_adam_step": ([_VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], ctypes.c_int),
+    "st_mlp_set_fused_inference": ([_VP, ctypes.c_int32], ctypes.c_int),
     "st_mlp_train": ([_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                       ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float, ctypes.c_float,
                       ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -376,6 +377,9 @@ class MLP:
             lp = lin.ctypes.data
         self._head_keep = (q0, ins, lin)
         _check(load().st_mlp_set_head(self.handle, q0.ctypes.data, lp, float(out_scale), ins.ctypes.data))
+
+    def set_fused_inference(self, on: bool):
+        _check(load().st_mlp_set_fused_inference(self.handle, 1 if on else 0))
 
     def forward(self, x_ptr: int, B: int, q_ptr: int):
         _check(load().st_mlp_forward(self.handle, x_ptr, int(B), q_ptr))

@@ -6,8 +6,8 @@
 #include <cstring>
 #include <mutex>
 
+#include "mlp_fused.cuh"
 #include "st_internal.cuh"
-#include "tc_gemm.cuh"
 
 namespace st {
 
@@ -149,6 +149,44 @@ int gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const GemmEp
     if (N % 64 == 0) return launch_gemm_bn<64, 4>(A, B, M, N, K, epi, status, stream, splits);
     if (N % 32 == 0) return launch_gemm_bn<32, 4>(A, B, M, N, K, epi, status, stream, splits);
     return launch_gemm_bn<16, 4>(A, B, M, N, K, epi, status, stream, splits);
+}
+
+// Fused inference of the five layers (mlp_fused.cuh): X0 [Bp][64] and the
+// weights W1 [256][64], W2..W4 [256][256], W5 [16][256] bf16 K-major; bias
+// pointers 16-byte aligned (b1..b4); Y [Bp][16] FP32.
+int mlp_fused_forward(const void* X0, const void* const W[5], const float* const bias[5], float* Y, int Bp,
+                      int32_t* status, cudaStream_t stream) {
+    if (Bp <= 0 || Bp % 128) {
+        set_error("mlp_fused_forward: rows must be a positive multiple of 128");
+        return ST_EINVAL;
+    }
+    for (int l = 0; l < 4; ++l)
+        if ((uintptr_t)bias[l] & 15) {
+            set_error("mlp_fused_forward: hidden-layer biases must be 16-byte aligned");
+            return ST_EINVAL;
+        }
+    static PerDeviceOnce attr;
+    int rc = once_per_device(
+        attr,
+        [] {
+            return cudaFuncSetAttribute(mlp_fused_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        MLPF_SMEM_BYTES);
+        },
+        "mlp_fused_forward: cudaFuncSetAttribute");
+    if (rc) return rc;
+    CUtensorMap tx, tw[5];
+    rc = get_tmap(&tx, X0, Bp, MLP_KIN_FUSED, 128);
+    if (rc == ST_OK) rc = get_tmap(&tw[0], W[0], 256, MLP_KIN_FUSED, 256);
+    for (int l = 1; l < 4 && rc == ST_OK; ++l) rc = get_tmap(&tw[l], W[l], 256, 256, 256);
+    if (rc == ST_OK) rc = get_tmap(&tw[4], W[4], 16, 256, 16);
+    if (rc) return rc;
+    MlpFusedArgs a;
+    for (int l = 0; l < 5; ++l) a.bias[l] = bias[l];
+    a.Y = Y;
+    a.status = status;
+    mlp_fused_forward_kernel<<<Bp / 128, 256, MLPF_SMEM_BYTES, stream>>>(tx, tw[0], tw[1], tw[2], tw[3], tw[4], a);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ST_OK : cuda_fail(e, "mlp_fused_forward launch");
 }
 
 // out[i] = sum_z ws[z][i] for float4 entries: each block handles 32 consecutive

@@ -121,6 +121,7 @@ struct st_mlp {
     st::InScale in_scale;
     int64_t step = 0;
     bool have_grads = false;
+    bool fused_inference = true;   // inference through the fused five-layer kernel
 };
 
 namespace st {
@@ -491,6 +492,13 @@ static int upload_head(st_mlp* n) {
 // forward through the five layers from X0 (rows Bp); keep_t writes the
 // transposed activations and pre-activations for a following backward pass
 static int mlp_forward_layers(st_mlp* n, int Bp, bool keep_t) {
+    if (!keep_t && n->fused_inference) {
+        // inference: all five layers per 128-row tile in one kernel
+        const void* W[5] = {n->W1p, n->W2, n->W3, n->W4, n->W5p};
+        const float* b[5] = {n->p + mlp_b_off(0), n->p + mlp_b_off(1), n->p + mlp_b_off(2), n->p + mlp_b_off(3),
+                             n->b5p};
+        return mlp_fused_forward(n->X0, W, b, n->Y, Bp, n->status, n->stream);
+    }
     int rc;
     GemmEpi e = epi_base();
     const __nv_bfloat16* Win[4] = {n->W1p, n->W2, n->W3, n->W4};
@@ -1013,6 +1021,15 @@ int st_mlp_adam_step(st_mlp* n, float lr, float beta1, float beta2, float eps) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "st_mlp_adam_step");
     return mlp_refresh_weights(n);
+}
+
+int st_mlp_set_fused_inference(st_mlp* n, int32_t on) {
+    if (!n) {
+        set_error("st_mlp_set_fused_inference: null network");
+        return ST_EINVAL;
+    }
+    n->fused_inference = on != 0;
+    return ST_OK;
 }
 
 int st_mlp_train(st_mlp* n, const float* x_rows, const float* r_rows, int64_t n_rows, int32_t B, int32_t steps,

@@ -53,6 +53,12 @@ enum { STATUS_MMA_TIMEOUT = 2 };
 // and the caller reduces them (gemm_split_reduce).
 int gemm_bf16_tn(const void* A, const void* B, int M, int N, int K, const GemmEpi& epi, int32_t* status,
                  cudaStream_t stream, int splits = 1);
+// Fused inference of the network's five layers (gemm.cu, kernel in
+// mlp_fused.cuh): X0 [Bp][64] bf16 input rows, W1 [256][64], W2..W4
+// [256][256], W5 [16][256] bf16 K-major, biases b1..b4 [256] (16-byte
+// aligned) and b5 [16], Y [Bp][16] FP32; Bp % 128 == 0.
+int mlp_fused_forward(const void* X0, const void* const W[5], const float* const bias[5], float* Y, int Bp,
+                      int32_t* status, cudaStream_t stream);
 // out[i] = sum_z ws[z * stride + i], i < count
 int gemm_split_reduce(const float* ws, int splits, int64_t stride, int64_t count, float* out, cudaStream_t stream);
 // K blocks per split for a requested split count (every split gets >= 1 block)

@@ -113,6 +113,29 @@ def test_forward_matches_reference(B):
 GRAD_REL_TOL = 2e-3
 
 
+@pytest.mark.parametrize("B", [128, 1000, 10000])
+def test_fused_inference_equals_layer_by_layer(B):
+    """The fused five-layer inference kernel (activations in shared memory,
+    accumulators in tensor memory) and one GEMM per layer compute the same
+    bf16 operands, FP32 accumulation order and epilogue: identical outputs,
+    for a single tile, a ragged batch and the averaging ensemble's size."""
+    p = random_params(23, last_scale=1.0)
+    h = head_for(6)
+    x = rand_x(B, 24)
+    net = make_net(p, h, max_batch=max(B, 4096))
+    xd = dev(x, np.float32)
+    q_f = torch.empty((B, 4), dtype=torch.float32, device="cuda")
+    q_l = torch.empty((B, 4), dtype=torch.float32, device="cuda")
+    net.forward(xd.data_ptr(), B, q_f.data_ptr())
+    net.set_fused_inference(False)
+    net.forward(xd.data_ptr(), B, q_l.data_ptr())
+    net.set_fused_inference(True)
+    assert torch.equal(q_f, q_l)
+    qo, _ = M.forward(f32_params(p), x.astype(np.float32).astype(np.float64), h, bf16=True)
+    assert np.abs(q_f.cpu().numpy() - qo).max() < 1e-2 * h["scale"]
+    net.close()
+
+
 def test_loss_and_gradient_match_reference():
     """Loss and all 200196 gradient entries against the reference with every
     bf16 store emulated (weights, activations, dL/dy, dL/dz) and FP64
