@@ -307,6 +307,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 MIXED_WORKLOAD_PARTICLES = 1_000_000
+FP64_MIDPOINT_PARTICLES = 100_000   # the FP64 tracker is fully occupied at 10^5
 # FMA-pipe instructions the mixed tracker executes per pass on this workload
 # (thread level: warp instructions x 32 / passes), from one ncu capture
 # (profiles/track_mixed_rhic_like_ncu.md).  Packed FP32x2 instructions count
@@ -314,6 +315,33 @@ MIXED_WORKLOAD_PARTICLES = 1_000_000
 # measure is the share of the FMA pipe's issue slots (128 lanes per SM per
 # clock), not a flop count.
 MIXED_FMA_PIPE_INSTR_PER_PASS = 1342.0
+
+
+def _tracker_rate(st, torch, ring, z, S, precision, spin_order, steps=3):
+    """Passes/s of one tracker on a resident ensemble: CUDA events on the
+    tracker's stream around single turns, L2 flushed between turns."""
+    n = z.shape[1]
+    stream = torch.cuda.Stream()
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, n, precision, stream=stream.cuda_stream)
+    tr.set_launch(block_threads=128, turns_per_launch=1)
+    tr.upload(z, S)
+    for _ in range(2):
+        tr.track(1, spin_order)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            tr.track(1, spin_order)
+            b.record(stream)
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
+    tr.close()
+    lat.close()
+    return n * len(ring["elements"]) * steps / t
 
 
 def variant_mixed(st, torch, args, fp64_value, fp32_peak):
@@ -358,7 +386,15 @@ def variant_mixed(st, torch, args, fp64_value, fp32_peak):
                         "algorithmic_flops_per_pass": algo,
                         "executed": {"fma_pipe_instr_per_pass": MIXED_FMA_PIPE_INSTR_PER_PASS,
                                      "fma_pipe_issue_frac_at_max_clock": fma_issue}},
-           "error_vs_fp64": {}}
+           "error_vs_fp64": {}, "midpoint_schemes": {}}
+    # the midpoint spin placements (Sec. 4.1) in both trackers, on the same ring
+    # (order-2 slicing): mixed on the same 10^6 particles, FP64 on the headline 10^5
+    ring_mid = W.with_spin_order(W.rhic_like_ring(args.ggamma), 2)
+    for K, name in ((-1, "half_slice"), (-2, "split_kick")):
+        r_mixed = _tracker_rate(st, torch, ring_mid, z, S, "mixed", K)
+        r_fp64 = _tracker_rate(st, torch, ring_mid, z[:, :FP64_MIDPOINT_PARTICLES], S[:, :FP64_MIDPOINT_PARTICLES], "fp64", K)
+        out["midpoint_schemes"][name] = {"spin_order": K, "mixed_passes_per_s": r_mixed,
+                                         "fp64_passes_per_s": r_fp64, "speedup_vs_fp64": r_mixed / r_fp64}
     # accuracy: 1024-particle subset, mixed vs the FP64 tracker (pinned to the oracle)
     for gg in sorted({args.ggamma, 45.5, 487.0}):
         ring_g = W.with_spin_order(W.rhic_like_ring(gg), args.spin_order)

@@ -101,8 +101,10 @@ extern "C" {
 /* spin_order 0..4 is the number of Romberg iterations over slice-edge
  * samples.  Two negative values select the piece-wise constant rotation
  * R(ds Omega) per slice with Omega at the slice middle (Sec. 4.1, Eq. (37);
- * Sec. 5.3, Fig. oneTurnSpinErrs), FP64 contexts only, any n_slices, no
- * fourth-order slice maps (ST_EINVAL otherwise):                             */
+ * Sec. 5.3, Fig. oneTurnSpinErrs), on FP64 and mixed-precision contexts (the
+ * mixed tracker runs them on its element kinds in its compensated
+ * arithmetic), any n_slices, no fourth-order slice maps (ST_EINVAL
+ * otherwise):                                                               */
 #define ST_SPIN_MID_HALF  -1   /* each slice traversed as two half-slices of its own
                                   map, the rotation between them ("half-DKD, spin,
                                   half-DKD")                                        */
@@ -191,12 +193,12 @@ int st_particles_upload(st_ctx* ctx, const double* z_soa, const double* spin_soa
                         int32_t src_is_device);
 
 /* Track every particle for n_turns >= 0 turns with Romberg order spin_order
- * (0..4) or a midpoint scheme (ST_SPIN_MID_HALF, ST_SPIN_MID_KICK; FP64
- * contexts).  Asynchronous on the context stream.  Errors: ST_ESTATE before
- * the first upload, ST_EINVAL for n_turns < 0, spin_order outside -2..4, a
+ * (0..4) or a midpoint scheme (ST_SPIN_MID_HALF, ST_SPIN_MID_KICK).
+ * Asynchronous on the context stream.  Errors: ST_ESTATE before the first
+ * upload, ST_EINVAL for n_turns < 0, spin_order outside -2..4, a
  * spin-carrying element whose n_slices is not a multiple of 2^spin_order, a
- * midpoint scheme on a mixed-precision context or with fourth-order slice
- * maps, ST_ECUDA on a launch failure. */
+ * midpoint scheme with fourth-order slice maps, ST_ECUDA on a launch
+ * failure. */
 int st_track(st_ctx* ctx, int32_t n_turns, int32_t spin_order);
 
 /* Track the orbits only (the maps of st_track without the spin step; spins
@@ -219,8 +221,10 @@ int st_track_one_turn_map(st_ctx* ctx, int32_t spin_order, const double* q_ref, 
 /* Stroboscopic spin average: as st_track, and after every turn each
  * particle's spin at the start of the lattice (the fixed azimuth s = 0) is
  * added to spin_sum (device double [3][n], accumulated, not cleared), so that
- * spin_sum / n_turns is the turn-averaged spin <S>.  FP64 contexts, and
- * ST_MIXED contexts (the mixed-precision tracker, Romberg orders 0..4; the
+ * spin_sum / n_turns is the turn-averaged spin <S>.  A particle lost during
+ * a turn adds its spin for that turn (rotated up to the element that lost
+ * it) and nothing in later turns.  FP64 contexts, and ST_MIXED contexts (the
+ * mixed-precision tracker, Romberg orders 0..4 and the midpoint schemes; the
  * spin after each turn is its FP64 spin).  Asynchronous. */
 int st_track_average(st_ctx* ctx, int32_t n_turns, int32_t spin_order, double* spin_sum);
 

@@ -449,8 +449,8 @@ static bool spin_scheme_ok(const st_ctx* ctx, int spin_order, const char* who) {
         return false;
     }
     if (spin_order < 0) {
-        if (ctx->precision != ST_FP64 || L.has_order4) {
-            set_error("%s: the midpoint schemes need an FP64 context and second-order slice maps", who);
+        if (L.has_order4) {
+            set_error("%s: the midpoint schemes need second-order slice maps", who);
             return false;
         }
         return true;

@@ -117,6 +117,15 @@ int build_mixed_tables(LatticeImpl& L) {
             m.eh2_ff = split(eta * h * h);
             m.cbm1_ff = split(-2.0 * hs * hs);
             m.dTeta_ff = split((1.0 - 1.0 / eta) * d.ds / beta0);
+            {   // half slices (midpoint spin schemes)
+                const double hq = std::sin(0.25 * h * d.ds);
+                m.sbh_ff = split(std::sin(0.5 * h * d.ds));
+                m.sbiehh_ff = split(std::sin(0.5 * h * d.ds) / (eta * h));
+                m.cbm1h_ff = split(-2.0 * hq * hq);
+                m.cbmiehh_ff = split(-2.0 * hq * hq / (eta * h));
+                m.ietadsh_ff = split(0.5 * d.ds / eta);
+                m.dTetah_ff = split((1.0 - 1.0 / eta) * 0.5 * d.ds / beta0);
+            }
             // on-axis, on-momentum particle: Omega = (0, h - (1 + G gamma0) eta h, 0)
             omr = h - a0 * eta * h;
             m.omr = (float)omr;

@@ -101,6 +101,10 @@ struct __align__(16) MixElem {
     float2 dTeta_ff;                  // bend: (1 - 1/eta) ds / beta0 as (hi, lo)
     float2 ieh_ff;                    // bend: 1/(eta h) as (hi, lo)
     float2 pad2_;
+    // bend, half-slice constants of the midpoint spin schemes (as (hi, lo)):
+    // sin(h ds/2), sin(h ds/2)/(eta h), cos(h ds/2) - 1, (cos(h ds/2) - 1)/(eta h),
+    // ds/(2 eta), (1 - 1/eta) ds / (2 beta0)
+    float2 sbh_ff, sbiehh_ff, cbm1h_ff, cbmiehh_ff, ietadsh_ff, dTetah_ff;
     float2 rq[4];                     // reference rotation over the element (bends, snakes), (hi, lo) per component
     MixWeight w[6];
 };

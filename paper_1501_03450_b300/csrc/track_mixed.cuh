@@ -270,6 +270,44 @@ __device__ __forceinline__ void straight_edge(const MConst& k, const MState& z, 
     bz = w * ips * cu * Ps;
 }
 
+// Per-particle constants of the mixed-precision maps (FP64 -> compensated
+// FP32) for energy coordinate Pt: Eq. (2)'s P^2 = 1 + 2 Pt/beta0 + Pt^2 and
+// the particle's gamma for Eq. (6b); invP64 = 1/P in FP64.
+__device__ __forceinline__ void mixed_particle_consts(const RefConst& ref, double Pt, MConst& k, double& invP64) {
+    const double P2m1 = 2.0 * Pt * ref.inv_beta0 + Pt * Pt;
+    const double P2 = 1.0 + P2m1;
+    invP64 = rsqrt(P2);
+    const double P = P2 * invP64;
+    const double b0pt = ref.inv_beta0 + Pt;
+    const double gamma = ref.gamma0 * (1.0 + ref.beta0 * Pt);
+    k.invP = ff_make(invP64);
+    k.PM1 = ff_make(P2m1 / (P + 1.0));
+    // 1/beta0 - (1/beta0 + Pt)/P = ((P - 1) - beta0 Pt) / (beta0 P)
+    k.tau = ff_make((P2m1 / (P + 1.0) - ref.beta0 * Pt) * ref.inv_beta0 * invP64);
+    k.Pt = (float)Pt;
+    k.P2 = (float)P2;
+    k.P2m1 = (float)P2m1;
+    k.invPf = (float)invP64;
+    k.P = (float)P;
+    k.b0pt = (float)b0pt;
+    k.a = (float)(1.0 + ref.G * gamma);
+    k.c = (float)(ref.G * (gamma - 1.0));
+    k.da = (float)(ref.G * ref.gamma0 * ref.beta0 * Pt);
+    k.f3 = (float)(0.5 * b0pt * invP64 * invP64 * invP64);
+    k.a0 = (float)(1.0 + ref.G * ref.gamma0);
+    // a0 (P - 1) - da: the energy deviation's first-order terms of the bend's
+    // Omega_y, which cancel to O(Pt) for G gamma >> 1, combined in FP64
+    const double a0d = 1.0 + ref.G * ref.gamma0;
+    const double c1 = a0d * (P2m1 / (P + 1.0)) - ref.G * ref.gamma0 * ref.beta0 * Pt;
+    k.c1 = (float)c1;
+    k.aP = ff_make((1.0 + ref.G * gamma) * invP64);
+    k.a0P = ff_make(a0d * invP64);
+    k.c1P = ff_make(c1 * invP64);
+    k.invP2 = ff_make(1.0 / P2);
+    k.Ptf = ff_make(Pt);
+    k.b0ptf = ff_make(b0pt);
+}
+
 // cached matrix-kick coefficients of the half-slice linear flow (computed in
 // FP64 when the (|k1|, s) key changes): for the cos plane (1) and the cosh
 // plane (2): C - 1, S/P and |k1| S as compensated pairs, and the FP32 time
@@ -473,40 +511,7 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
     const double Pt = v.y;
     MConst k;
     double invP64;
-    {
-        const double P2m1 = 2.0 * Pt * ref.inv_beta0 + Pt * Pt;
-        const double P2 = 1.0 + P2m1;
-        invP64 = rsqrt(P2);
-        const double P = P2 * invP64;
-        const double b0pt = ref.inv_beta0 + Pt;
-        const double gamma = ref.gamma0 * (1.0 + ref.beta0 * Pt);
-        k.invP = ff_make(invP64);
-        k.PM1 = ff_make(P2m1 / (P + 1.0));
-        // 1/beta0 - (1/beta0 + Pt)/P = ((P - 1) - beta0 Pt) / (beta0 P)
-        k.tau = ff_make((P2m1 / (P + 1.0) - ref.beta0 * Pt) * ref.inv_beta0 * invP64);
-        k.Pt = (float)Pt;
-        k.P2 = (float)P2;
-        k.P2m1 = (float)P2m1;
-        k.invPf = (float)invP64;
-        k.P = (float)P;
-        k.b0pt = (float)b0pt;
-        k.a = (float)(1.0 + ref.G * gamma);
-        k.c = (float)(ref.G * (gamma - 1.0));
-        k.da = (float)(ref.G * ref.gamma0 * ref.beta0 * Pt);
-        k.f3 = (float)(0.5 * b0pt * invP64 * invP64 * invP64);
-        k.a0 = (float)(1.0 + ref.G * ref.gamma0);
-        // a0 (P - 1) - da: the energy deviation's first-order terms of the bend's
-        // Omega_y, which cancel to O(Pt) for G gamma >> 1, combined in FP64
-        const double a0d = 1.0 + ref.G * ref.gamma0;
-        const double c1 = a0d * (P2m1 / (P + 1.0)) - ref.G * ref.gamma0 * ref.beta0 * Pt;
-        k.c1 = (float)c1;
-        k.aP = ff_make((1.0 + ref.G * gamma) * invP64);
-        k.a0P = ff_make(a0d * invP64);
-        k.c1P = ff_make(c1 * invP64);
-        k.invP2 = ff_make(1.0 / P2);
-        k.Ptf = ff_make(Pt);
-        k.b0ptf = ff_make(b0pt);
-    }
+    mixed_particle_consts(ref, Pt, k, invP64);
     v = sxy[i];
     double sx = v.x, sy = v.y, sz = szp[i];
 

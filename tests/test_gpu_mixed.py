@@ -187,3 +187,89 @@ def test_mixed_against_the_oracle_on_the_configured_subset(gg):
           f"orbit max {np.abs(zm[:5] - zo[:5]).max(axis=1)}")
     assert mean <= 1e-6 and mx < 1e-4, (mean, mx)
     assert np.abs(zm[:4] - zo[:4]).max() < 1e-6
+
+
+MID = [st.ST_SPIN_MID_HALF, st.ST_SPIN_MID_KICK]
+
+
+@pytest.mark.parametrize("K", MID)
+@pytest.mark.parametrize("case", ["toy", "rhic_like_487", "thin_sextupoles", "fringes", "odd_slices"])
+def test_mixed_midpoint_schemes_against_the_oracle(case, K):
+    """The midpoint spin schemes (Sec. 4.1, Eq. (37)) in the mixed-precision
+    tracker against the oracle's, on rings of every element kind the mixed
+    tracker runs: the toy ring (drift-kick-drift quadrupoles, sector bends),
+    the RHIC-like ring at G*gamma0 = 487 (matrix-kick quadrupoles,
+    sextupoles, snakes), thin sextupoles, fringe spin kicks on every magnet,
+    and three slices per element (the midpoint schemes take any n_slices).
+    The same error budget as the mixed tracker's Romberg orders."""
+    if case == "toy":
+        ring, gg, turns = W.toy_ring(45.5), 45.5, 20
+    elif case == "rhic_like_487":
+        ring, gg, turns = W.with_spin_order(W.rhic_like_ring(487.0, n_cells=20), 2), 487.0, 10
+    elif case == "thin_sextupoles":
+        ring, gg, turns = W.with_thin_sextupoles(W.with_spin_order(W.rhic_like_ring(45.5, n_cells=12), 2)), 45.5, 10
+    elif case == "fringes":
+        ring, gg, turns = W.with_fringes(W.with_spin_order(W.rhic_like_ring(487.0, n_cells=12), 2)), 487.0, 10
+    else:
+        ring, gg, turns = W.with_slices(W.rhic_like_ring(45.5, n_cells=12), 3), 45.5, 10
+    z, S = W.gaussian_particles(200, gg, seed=61)
+    zm, Sm, lm = st.track(ring, z, S, turns, K, precision="mixed")
+    zo, So, lo = oracle.track(ring, z, S, turns, K)
+    assert np.array_equal(lm, lo)
+    mean, mx = spin_err(Sm, So)
+    assert mean < 1e-7 and mx < 1e-6, (case, K, mean, mx)
+    assert np.abs(zm[:4] - zo[:4]).max() < 1e-8
+
+
+@pytest.mark.parametrize("K", MID)
+def test_mixed_midpoint_1000_turns_within_1e_6(K):
+    """1000 turns of the RHIC-like ring at G*gamma0 = 487 with a midpoint
+    scheme: the mixed tracker against the FP64 tracker with the same scheme
+    (itself at parity with the oracle), mean Delta S within 1e-6."""
+    ring = W.with_spin_order(W.rhic_like_ring(487.0), 2)
+    z, S = W.gaussian_particles(1024, 487.0, seed=3451)
+    zm, Sm, lm = st.track(ring, z, S, 1000, K, precision="mixed")
+    zf, Sf, lf = st.track(ring, z, S, 1000, K)
+    assert np.array_equal(lm, lf)
+    mean, mx = spin_err(Sm, Sf)
+    print(f"midpoint scheme {K}: mixed vs FP64 after 1000 turns at 487: dS mean {mean:.3e} max {mx:.3e}")
+    assert mean <= 1e-6, (mean, mx)
+    assert np.abs(zm[:4] - zf[:4]).max() < 1e-6
+
+
+def test_mixed_midpoint_lost_particles_and_average():
+    """A particle lost in the first element is flagged as by the oracle; the
+    stroboscopic sum with a midpoint scheme is the sum of the turn spins (a
+    lost particle adds its spin of the turn that lost it, and nothing after)."""
+    torch = pytest.importorskip("torch")
+    ring = W.toy_ring(45.5)
+    z, S = W.gaussian_particles(40, 45.5, seed=62)
+    z[1, 9] = 1.5
+    zm, Sm, lm = st.track(ring, z, S, 3, st.ST_SPIN_MID_HALF, precision="mixed")
+    zo, So, lo = oracle.track(ring, z, S, 3, st.ST_SPIN_MID_HALF)
+    assert np.array_equal(lm, lo) and lm[9] == 1
+    assert spin_err(Sm, So)[1] < 1e-6
+    lat = st.Lattice(ring)
+    acc = torch.zeros((3, 40), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    tr = st.Tracker(lat, 40, "mixed")
+    tr.set_launch(block_threads=128, turns_per_launch=1)
+    tr.upload(z, S)
+    st.st_track_average(tr.handle, 5, st.ST_SPIN_MID_KICK, acc.data_ptr())
+    _, SA, _ = tr.download()
+    tr.upload(z, S)
+    manual = np.zeros((3, 40))
+    for turn in range(5):
+        tr.track(1, st.ST_SPIN_MID_KICK)
+        _, Si, li = tr.download()
+        manual += Si
+        if turn == 0:
+            S_first = Si.copy()
+    tr.close()
+    lat.close()
+    torch.cuda.synchronize()
+    got = acc.cpu().numpy()
+    alive = li == 0
+    assert li[9] == 1 and alive.sum() == 39
+    assert np.array_equal(got[:, alive], manual[:, alive])
+    assert np.array_equal(got[:, 9], S_first[:, 9])
