@@ -638,8 +638,16 @@ def variant_drift_kick(st, torch, npart, seed, fp64_peak, ggamma=45.5, dS_partic
         dS[f"n_b={nb}"] = row
     roof = {k: {"algorithmic_flops_per_pass": ALGO_FLOPS_COMPARISON[k],
                 "frac_of_fp64_peak": ALGO_FLOPS_COMPARISON[k] * v / fp64_peak} for k, v in rates.items()}
+    # the drift-kick ring in the mixed-precision tracker (TEAPOT bends in compensated
+    # FP32), on the mixed tracker's 10^6-particle ensemble
+    zm, Sm = W.gaussian_particles(MIXED_WORKLOAD_PARTICLES, ggamma, seed=seed)
+    mixed = {}
+    for name, K in (("drift_kick_romberg2", 2), ("drift_kick_mid_kick", st.ST_SPIN_MID_KICK)):
+        r = _tracker_rate(st, torch, dk, zm, Sm, "mixed", K)
+        mixed[name] = {"passes_per_s": r, "speedup_vs_fp64": r / rates[name]}
     return {"workload": f"108-cell RHIC-like ring at G gamma0 = {ggamma}, {npart} particles, 1 turn per launch",
             "passes_per_s": rates, "roofline": roof, "one_turn_dS": dS,
+            "mixed": dict(mixed, particles=MIXED_WORKLOAD_PARTICLES),
             "dS_sample": f"{dS_particles} particles, reference: bend-kick/matrix-kick, 256 slices, 3 Romberg "
                          "iterations"}
 

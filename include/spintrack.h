@@ -85,7 +85,9 @@ extern "C" {
                            -eta h (1 + hX), Eq. (sbendA)) and another curved drift;
                            split_order 4 composes it to fourth order.  eta = 0 is a
                            field-free curved frame.  The paper's comparison integrator:
-                           less accurate than ST_SBEND at any slice count.  FP64 only. */
+                           less accurate than ST_SBEND at any slice count.  FP64 and
+                           (second order) mixed-precision contexts; a mixed batch over a
+                           lattice with TEAPOT bends is rejected (ST_EINVAL).          */
 
 #define ST_THIN_MULT 8  /* thin lens, Sec. 3.5: the ST_MULT multipole in the limit of zero
                            length at fixed integrated strengths, k1 = integrated quadrupole
@@ -145,8 +147,8 @@ typedef struct {
                         * b_2/(B rho) = k1, b_3/(B rho) = k2/2; orbit unchanged.  0: none.
                         * Solenoids always carry their Sec. 4.4 fringe kicks; drifts and
                         * snakes must have 0 (ST_EINVAL otherwise).  The mixed-precision
-                        * tracker applies them on ST_MULT, ST_QUAD_MK and ST_SBEND; an
-                        * ST_RBEND or ST_TEAPOT is FP64 only anyway. */
+                        * tracker applies them on ST_MULT, ST_QUAD_MK, ST_SBEND and
+                        * ST_TEAPOT; an ST_RBEND is FP64 only anyway. */
     int32_t split_order; /* orbit slice map of an ST_MULT, ST_QUAD_MK or ST_TEAPOT: 0 or
                           * 2 = the symmetric second-order split of Eq. (27) (drift-kick-
                           * drift, matrix-kick, TEAPOT); 4 = Yoshida's fourth-order composition
@@ -175,7 +177,8 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
 int st_lattice_destroy(st_lattice* lat);
 
 /* Create a tracking context for n_particles >= 1 particles on the current
- * device.  precision is ST_FP64 or ST_MIXED.  cuda_stream is a cudaStream_t
+ * device.  precision is ST_FP64 or ST_MIXED (lattices with solenoids,
+ * rectangular bends or fourth-order maps: ST_FP64 only, ST_EINVAL otherwise).  cuda_stream is a cudaStream_t
  * (e.g. torch.cuda.current_stream().cuda_stream) or NULL for a stream owned by
  * the context.  Allocates the device state (orbit as (X,Px), (Y,Py), (T,Pt)
  * double2 arrays, spin, lost flags) and a staging buffer.  The lattice must
@@ -262,7 +265,9 @@ int st_ctx_set_launch(st_ctx* ctx, int32_t block_threads, int32_t turns_per_laun
 typedef struct st_batch st_batch;
 
 /* n_jobs >= 1 jobs: lattices[j] (must outlive the batch) and n_particles[j]
- * (1..2^30).  precision ST_FP64 or ST_MIXED; cuda_stream as st_ctx_create.
+ * (1..2^30).  precision ST_FP64 or ST_MIXED (a mixed batch takes neither the
+ * lattices an ST_MIXED context refuses nor TEAPOT bends); cuda_stream as
+ * st_ctx_create.
  * Errors: ST_EINVAL, ST_ENOMEM, ST_ECUDA. */
 int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particles, int32_t n_jobs,
                     int32_t precision, void* cuda_stream, st_batch** out);

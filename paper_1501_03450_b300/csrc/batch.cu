@@ -350,8 +350,9 @@ int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particle
     }
     if (precision == ST_MIXED)
         for (int j = 0; j < n_jobs; ++j)
-            if (lattices[j] && lattices[j]->impl.fp64_only) {
-                set_error("st_batch_create: solenoids and fringe spin kicks are tracked by the FP64 tracker only");
+            if (lattices[j] && (lattices[j]->impl.fp64_only || lattices[j]->impl.mix_ext)) {
+                set_error("st_batch_create: solenoids, rectangular bends, fourth-order maps and (in mixed batches) "
+                          "TEAPOT bends are tracked by FP64 batches only");
                 return ST_EINVAL;
             }
     st_batch* b = new (std::nothrow) st_batch();

@@ -97,27 +97,31 @@ int build_mixed_tables(LatticeImpl& L) {
             m.k2 = (float)d.a[1];          // |k1|
             m.k1ds_ff = split(d.a[1]);     // |k1| as (hi, lo): the matrix-kick coefficients need it exactly
             break;
-        case ST_SBEND: {
+        case ST_SBEND:
+        case ST_TEAPOT: {
             const double h = d.a[0], eta = d.a[1];
-            const double hs = std::sin(0.5 * h * d.ds);
-            m.cbm1 = (float)(-2.0 * hs * hs);
-            m.sb = (float)std::sin(h * d.ds);
+            // field and curvature: the spin constants are the same for both kinds
+            // (Omega at the same slice edges)
             m.h = (float)h;
             m.eta = (float)eta;
-            m.ieta = (float)(1.0 / eta);
-            m.ieh = (float)(1.0 / (eta * h));
-            m.ieh_ff = split(1.0 / (eta * h));
-            m.dT_eta = (float)((1.0 - 1.0 / eta) * d.ds / beta0);
-            m.sbieh_ff = split(std::sin(h * d.ds) / (eta * h));
-            m.ietads_ff = split(d.ds / eta);
-            m.sb_ff = split(std::sin(h * d.ds));
-            m.cbmieh_ff = split(-2.0 * hs * hs / (eta * h));
             m.etah_ff = split(eta * h);
-            m.ome_ff = split(1.0 - eta);
             m.eh2_ff = split(eta * h * h);
-            m.cbm1_ff = split(-2.0 * hs * hs);
-            m.dTeta_ff = split((1.0 - 1.0 / eta) * d.ds / beta0);
-            {   // half slices (midpoint spin schemes)
+            if (d.type == ST_SBEND) {
+                // exact bend over ds (Eq. (10)) and over ds/2 (midpoint schemes)
+                const double hs = std::sin(0.5 * h * d.ds);
+                m.cbm1 = (float)(-2.0 * hs * hs);
+                m.sb = (float)std::sin(h * d.ds);
+                m.ieta = (float)(1.0 / eta);
+                m.ieh = (float)(1.0 / (eta * h));
+                m.ieh_ff = split(1.0 / (eta * h));
+                m.dT_eta = (float)((1.0 - 1.0 / eta) * d.ds / beta0);
+                m.sbieh_ff = split(std::sin(h * d.ds) / (eta * h));
+                m.ietads_ff = split(d.ds / eta);
+                m.sb_ff = split(std::sin(h * d.ds));
+                m.cbmieh_ff = split(-2.0 * hs * hs / (eta * h));
+                m.ome_ff = split(1.0 - eta);
+                m.cbm1_ff = split(-2.0 * hs * hs);
+                m.dTeta_ff = split((1.0 - 1.0 / eta) * d.ds / beta0);
                 const double hq = std::sin(0.25 * h * d.ds);
                 m.sbh_ff = split(std::sin(0.5 * h * d.ds));
                 m.sbiehh_ff = split(std::sin(0.5 * h * d.ds) / (eta * h));
@@ -125,6 +129,30 @@ int build_mixed_tables(LatticeImpl& L) {
                 m.cbmiehh_ff = split(-2.0 * hq * hq / (eta * h));
                 m.ietadsh_ff = split(0.5 * d.ds / eta);
                 m.dTetah_ff = split((1.0 - 1.0 / eta) * 0.5 * d.ds / beta0);
+            } else {
+                // TEAPOT (Sec. 3.6): curved drifts of ds/2 and ds/4 and the kick
+                // of the bend's field over ds (eta = 0 is a field-free curved frame)
+                L.mix_ext = true;
+                for (int jj = 0; jj < 2; ++jj) {
+                    const double len = (jj == 0 ? 0.5 : 0.25) * d.ds;
+                    const double hs2 = std::sin(0.5 * h * len);
+                    const double omc = 2.0 * hs2 * hs2, sn = std::sin(h * len);
+                    MixCurvedDrift& c = m.td[jj];
+                    c.sn_ff = split(sn);
+                    c.A1_ff = split(omc / h);
+                    c.A2_ff = split(sn / h);
+                    c.omc_ff = split(omc);
+                    // len - sin(h len)/h, by its series when h len is small (len (h len)^2 / 6
+                    // to leading order)
+                    const double x = h * len, x2 = x * x;
+                    const double lms = std::fabs(x) < 1e-2
+                                           ? len * x2 / 6.0 * (1.0 - x2 / 20.0 * (1.0 - x2 / 42.0))
+                                           : len - sn / h;
+                    c.dT0_ff = split(lms / beta0);
+                    c.snb0_ff = split(sn / beta0);
+                }
+                m.ehl_ff = split(eta * h * d.ds);
+                m.ehlh_ff = split(eta * h * h * d.ds);
             }
             // on-axis, on-momentum particle: Omega = (0, h - (1 + G gamma0) eta h, 0)
             omr = h - a0 * eta * h;
@@ -145,7 +173,8 @@ int build_mixed_tables(LatticeImpl& L) {
         default:
             break;
         }
-        if ((d.flags & ST_ELEM_FRINGE) && (d.type == ST_MULT || d.type == ST_QUAD_MK || d.type == ST_SBEND)) {
+        if ((d.flags & ST_ELEM_FRINGE) &&
+            (d.type == ST_MULT || d.type == ST_QUAD_MK || d.type == ST_SBEND || d.type == ST_TEAPOT)) {
             m.type |= ST_MIX_FRINGE;
             L.mix_fringe = true;
         }

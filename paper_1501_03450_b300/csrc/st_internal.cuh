@@ -72,6 +72,13 @@ struct MixWeight {
     float du3;        // |du| below which the terms n >= 3 of dC, dS are below 2^-27 of the first
 };
 
+// Constants of a TEAPOT bend's curved drift over len (Sec. 3.6) for the
+// mixed-precision kernel: sin(h len), (1 - cos(h len))/h, sin(h len)/h,
+// 1 - cos(h len), (len - sin(h len)/h)/beta0 and sin(h len)/beta0, as (hi, lo).
+struct MixCurvedDrift {
+    float2 sn_ff, A1_ff, A2_ff, omc_ff, dT0_ff, snb0_ff;
+};
+
 // Per unique element, constants of the mixed-precision kernel.  First-order
 // (linear) map coefficients are kept as compensated (hi, lo) float pairs so
 // that no systematic FP32 rounding enters the linear optics; second-order
@@ -105,6 +112,11 @@ struct __align__(16) MixElem {
     // sin(h ds/2), sin(h ds/2)/(eta h), cos(h ds/2) - 1, (cos(h ds/2) - 1)/(eta h),
     // ds/(2 eta), (1 - 1/eta) ds / (2 beta0)
     float2 sbh_ff, sbiehh_ff, cbm1h_ff, cbmiehh_ff, ietadsh_ff, dTetah_ff;
+    // TEAPOT bend: curved drifts of ds/2 (the slice's) and ds/4 (half-slices of
+    // the midpoint scheme), and the kick of the bend's field over ds:
+    // eta h ds and eta h^2 ds, as (hi, lo)
+    MixCurvedDrift td[2];
+    float2 ehl_ff, ehlh_ff;
     float2 rq[4];                     // reference rotation over the element (bends, snakes), (hi, lo) per component
     MixWeight w[6];
 };
@@ -135,6 +147,7 @@ struct LatticeImpl {
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
     bool fp64_only = false;        // solenoids, rectangular or TEAPOT bends, fourth-order maps: FP64 only
     bool mix_fringe = false;       // mixed table entries carry ST_MIX_FRINGE (thin fringe spin kicks)
+    bool mix_ext = false;          // the lattice has TEAPOT bends (the mixed kernels' extended instantiation)
     bool has_ext = false;          // fourth-order slice maps, rectangular or TEAPOT bends or thin lenses present
     bool has_order4 = false;       // fourth-order slice maps present
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]

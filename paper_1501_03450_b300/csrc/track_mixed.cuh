@@ -215,6 +215,7 @@ struct MConst {
     FF invP, tau, PM1;                     // 1/P; 1/beta0 - (1/beta0 + Pt)/P; P - 1
     FF aP, a0P, c1P;                       // a/P, a0/P, c1/P (spin: first-order coefficients)
     FF invP2, Ptf, b0ptf;                  // 1/P^2, Pt, 1/beta0 + Pt
+    FF hiP3;                               // 1/(2 P^3) (TEAPOT bends only)
     float Pt, P2, P2m1, invPf, P, b0pt, a, c, da, f3, a0, c1;
 };
 
@@ -304,6 +305,7 @@ __device__ __forceinline__ void mixed_particle_consts(const RefConst& ref, doubl
     k.a0P = ff_make(a0d * invP64);
     k.c1P = ff_make(c1 * invP64);
     k.invP2 = ff_make(1.0 / P2);
+    k.hiP3 = ff_make(0.5 * invP64 * invP64 * invP64);
     k.Ptf = ff_make(Pt);
     k.b0ptf = ff_make(b0pt);
 }
@@ -459,7 +461,77 @@ struct MixLevels {
     }
 };
 
-// Thin fringe spin kick of a multipole, quadrupole or sector bend (Sec. 4.5,
+// ---- TEAPOT bend (Sec. 3.6) in increment form ---------------------------------
+// Curved drift over len: the flow of H_D = -(1 + hX) Ps + Pt/beta0 with the
+// reference time len/beta0 (Eq. (teapotD)), c = the drift's constants (sn =
+// sin(h len), omc = 1 - cos(h len), A1 = omc/h, A2 = sn/h).  With x' = Px/Ps,
+// y' = Py/Ps, eps = omc + x' sn (1 - eps is the cos - x' sin denominator) and
+// e1 = eps/(1 - eps):
+//   dX  = A1 + x' A2 + (X + A1 + x' A2) e1
+//   dY  = y' A2 (1 + g),  g = (1 + hX)(1 + e1) - 1
+//   dPx = sn + (Ps - 1) sn - Px omc
+//   dT  = (len - A2)/beta0 + A2 tau - A2 (1/beta0 + Pt) d - X sn/beta0
+//         - A2 [((1/beta0 + Pt) d - tau) hX + (1/beta0 + Pt) e1 (1 + hX)/Ps]
+// (tau = 1/beta0 - (1/beta0 + Pt)/P, d = 1/Ps - 1/P).  Unlike the exact bend,
+// the drift-kick split swings even the on-axis particle off the axis inside a
+// slice (Px by about sin(h ds/2), X by about (1 - cos)/h), so Px^2, Ps - P,
+// d, eps and e1 are not small there and are compensated too: with p^2 =
+// Px^2 + Py^2 and e = p^2/P^2,
+//   Ps - P = -(p^2/(2P)) (1 + e/4 + e^2/8 + 5e^3/64),
+//   d      =  (p^2/(2P^3)) (1 + 3e/4 + 5e^2/8 + 35e^3/64),
+// the leading terms compensated, the series factors in FP32 (FP32 throughout
+// for e >= 4e-3, far from the axis).  If the line does not meet the turned
+// frame (1 - eps <= 0) or Ps^2 <= 0, X becomes NaN: the particle is lost.
+__device__ __forceinline__ void mixed_curved_drift(MState& z, const MConst& k, const MixCurvedDrift& c, float h) {
+    const FF sn{c.sn_ff.x, c.sn_ff.y}, A1{c.A1_ff.x, c.A1_ff.y}, A2{c.A2_ff.x, c.A2_ff.y};
+    const FF omc{c.omc_ff.x, c.omc_ff.y};
+    const FF pp = ff_add(ff_mul(z.Px, z.Px), ff_mul(z.Py, z.Py));
+    const float e = pp.hi * k.invPf * k.invPf;
+    FF dPsP, d;   // Ps - P, 1/Ps - 1/P
+    if (e < 4e-3f) {
+        const FF u = ff_mul(pp, FF{0.5f * k.invP.hi, 0.5f * k.invP.lo});   // p^2/(2P)
+        dPsP = ff_addn(ff_neg(u), -u.hi * e * fmaf(e, fmaf(e, 5.0f / 64.0f, 0.125f), 0.25f));
+        const FF dd = ff_mul(pp, k.hiP3);                                  // p^2/(2P^3)
+        d = ff_addn(dd, dd.hi * e * fmaf(e, fmaf(e, 35.0f / 64.0f, 0.625f), 0.75f));
+    } else {   // far from the axis (the series would not converge fast): FP32
+        const float ipsf = rsqrtf(k.P2 - pp.hi);
+        const float Psf = (k.P2 - pp.hi) * ipsf;
+        d = FF{pp.hi * k.invPf * ipsf / (k.P + Psf), 0.0f};
+        dPsP = FF{-pp.hi / (Psf + k.P), 0.0f};
+    }
+    const FF ips = ff_add(k.invP, d);
+    // (x', y') and (x' A2, y' A2), both planes in packed FP32x2 arithmetic
+    const FF2 pr = ff2_mul(ff2_pack(z.Px, z.Py), ff2_pack(ips, ips));
+    const FF2 pA = ff2_mul(pr, ff2_pack(A2, A2));
+    const FF eps = ff_add(omc, ff_mul(ff2_first(pr), sn));
+    const float ome = 1.0f - eps.hi;
+    const FF e1 = ff_addn(eps, eps.hi * eps.hi * __frcp_rn(ome));   // eps + eps^2/(1 - eps)
+    const float hX = h * z.X.hi;
+    const FF xA = ff_add(A1, ff2_first(pA));
+    const FF dX = ff_add(xA, ff_mul(ff_add_lazy(z.X, xA), e1));
+    const FF yA = ff2_second(pA);
+    const FF dY = ff_add_f(yA, yA.hi * fmaf(e1.hi, 1.0f + hX, hX));
+    const FF PsM1 = ff_add(k.PM1, dPsP);
+    const FF dPx = ff_add(ff_add(sn, ff_mul(PsM1, sn)), ff_neg(ff_mul(z.Px, omc)));
+    const FF W = ff_mul(ff_mul(k.b0ptf, ips), ff_mul(A2, e1));        // (1/beta0 + Pt) e1 A2 / Ps
+    const float rem = fmaf(A2.hi * (k.b0pt * d.hi - k.tau.hi), hX, W.hi * hX);
+    const FF dT0 = ff_add(FF{c.dT0_ff.x, c.dT0_ff.y}, ff_mul(A2, k.tau));
+    const FF dT1 = ff_add(ff_mul(ff_mul(A2, d), k.b0ptf), ff_add_lazy(ff_mul(z.X, FF{c.snb0_ff.x, c.snb0_ff.y}), W));
+    const FF dT = ff_add_f(ff_add(dT0, ff_neg(dT1)), -rem);
+    z.X = ff_add(z.X, dX);
+    z.Y = ff_add(z.Y, dY);
+    z.Px = ff_add(z.Px, dPx);
+    z.T = ff_add(z.T, dT);
+    if (!(ome > 0.0f && k.P2 - pp.hi > 0.0f)) z.X.hi = __int_as_float(0x7fc00000);   // quiet NaN
+}
+
+// Kick of the bend's uniform field, dPx = -eta h len (1 + hX), from the
+// compensated eta h len and eta h^2 len.
+__device__ __forceinline__ void mixed_teapot_kick(MState& z, const FF& ehl, const FF& ehlh) {
+    z.Px = ff_add(z.Px, ff_neg(ff_add(ehl, ff_mul(z.X, ehlh))));
+}
+
+// Thin fringe spin kick of a multipole, quadrupole, sector or TEAPOT bend (Sec. 4.5,
 // Eq. (skfringe)) as a near-identity quaternion about the longitudinal axis:
 // angle theta = -sign (1 + G) sum_m (b_m/(B rho)) Im (X + iY)^m / m with b_1 =
 // eta h, b_2 = k1, b_3 = k2/2 (the kick is below 1e-3 rad, so FP32 and the
@@ -467,7 +539,7 @@ struct MixLevels {
 __device__ __forceinline__ CNQ mixed_fringe(const MixElem& el, int type, const MState& z, float sign, float onepG) {
     const float X = z.X.hi, Y = z.Y.hi;
     float sum;
-    if (type == ST_SBEND) {
+    if (type == ST_SBEND || type == ST_TEAPOT) {
         sum = el.eta * el.h * Y;
     } else {
         sum = el.k1 * X * Y;
@@ -487,7 +559,8 @@ __device__ __forceinline__ CNQ mixed_fringe(const MixElem& el, int type, const M
 // spin_sum ([3][n_all]) is given, the spin after every turn is added to it.
 // FR: the lattice's table entries may carry ST_MIX_FRINGE (a separate
 // instantiation, so that lattices without fringe kicks run the plain loop).
-template <int K, bool SPIN = true, bool FR = false>
+// EXT: the lattice may hold TEAPOT bends (an instantiation of its own too).
+template <int K, bool SPIN = true, bool FR = false, bool EXT = false>
 __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__ table,
                                                      const uint16_t* __restrict__ seq,
                                                      const float2* __restrict__ rho, int n_seq, const RefConst& ref,
@@ -553,7 +626,8 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
             const int N = el.n_slices;
             const float ds = el.ds;
             float ox, os;
-            if (type == ST_SBEND) {
+            const bool teapot = EXT && type == ST_TEAPOT;
+            if (type == ST_SBEND || teapot) {
                 const float h = el.h, eta = el.eta;
                 const float py = z.Py.hi;
                 const float Pa2 = k.P2 - py * py;
@@ -607,7 +681,19 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 // one loop over the slice edges (edge 0: no orbit step), so that the
                 // spin edge code exists once
                 for (int s = 0; s <= N; ++s) {
-                  if (s > 0) {
+                  if (s > 0 && teapot) {
+                    // TEAPOT slice (Sec. 3.6): curved drift, kick, curved drift; the
+                    // momentum quantities of the slice edge for Omega (Py is constant)
+                    const MixCurvedDrift& cd = el.td[0];
+                    mixed_curved_drift(z, k, cd, h);
+                    mixed_teapot_kick(z, FF{el.ehl_ff.x, el.ehl_ff.y}, FF{el.ehlh_ff.x, el.ehlh_ff.y});
+                    mixed_curved_drift(z, k, cd, h);
+                    px = z.Px.hi;
+                    ps2 = Pa2 - px * px;
+                    ips = rsqrtf(ps2);
+                    Ps = ps2 * ips;
+                    dPsP = -__fdividef(px * px + py * py, Ps + k.P);
+                  } else if (s > 0) {
                     // exact bend over ds, Eq. (10): (Px, A = Ps - eta(1+hX)) rotates by h ds;
                     // dX = (dPs - dA)/(eta h) with dA = A (cos - 1) - Px sin
                     // A = (Ps - 1) + (1 - eta) - eta h X, compensated (first order in the
@@ -753,7 +839,7 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 const bool fr = FR && (el.type & ST_MIX_FRINGE);
                 if (fr) fq_premul_cnq(qt, mixed_fringe(el, type, z0, 1.0f, 1.0f + (float)ref.G));
                 fq_premul_cnq(qt, dq);
-                if (type == ST_SBEND) fq_premul_about_y(qt, el.rq);
+                if (type == ST_SBEND || (EXT && type == ST_TEAPOT)) fq_premul_about_y(qt, el.rq);
                 if (fr) fq_premul_cnq(qt, mixed_fringe(el, type, z, -1.0f, 1.0f + (float)ref.G));
             } else {
                 if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi)) {

@@ -4,9 +4,10 @@
 // compensated FP32 arithmetic of track_mixed.cuh:
 //   KICK = false  each slice as two half-slices of its own map, the rotation
 //                 between them;
-//   KICK = true   drift-kick (multipole, thin lens) and matrix-kick slices keep
-//                 their map and rotate between the two halves of the central
-//                 kick; sector bends (exact maps) as for KICK = false.
+//   KICK = true   drift-kick (multipole, thin lens, TEAPOT bend) and
+//                 matrix-kick slices keep their map and rotate between the two
+//                 halves of the central kick; sector bends (exact maps) as for
+//                 KICK = false.
 // Element by element the same placements as the FP64 midpoint tracker
 // (track_mid.cuh) on the element kinds the mixed tracker runs.  The rotation
 // of a slice is split into the on-axis reference rotation (about y in bends,
@@ -104,7 +105,7 @@ __device__ __forceinline__ void mixed_quad_nonlinear(MState& z, const MConst& k,
     z.T = ff_add(z.T, ff_mul(lenff, ff_add_f(k.tau, -k.b0pt * (d - 0.5f * pp * k.invPf * k.invPf * k.invPf))));
 }
 
-template <bool KICK, bool FR = false>
+template <bool KICK, bool FR = false, bool EXT = false>
 __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restrict__ table,
                                                          const uint16_t* __restrict__ seq,
                                                          const float2* __restrict__ rho, int n_seq,
@@ -167,7 +168,8 @@ __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restri
             const float ds = el.ds;
             const FF dsff{el.ds_ff.x, el.ds_ff.y};   // the slice's drift length (0 for a thin lens)
             CNQ D = one;                              // product of the slices' deviations, later on the left
-            if (type == ST_SBEND) {
+            const bool teapot = EXT && type == ST_TEAPOT;
+            if (type == ST_SBEND || teapot) {
                 const float h = el.h, eta = el.eta, etah = eta * h;
                 const float py = z.Py.hi;
                 const float Pa2 = k.P2 - py * py;
@@ -197,9 +199,25 @@ __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restri
                 const FF B1 = ff_mul(FF{el.eh2_ff.x, el.eh2_ff.y}, k.a0P);
                 const float apda = k.a0 + k.da;
                 const float2* rh = rho + el.rho_off;
+                // TEAPOT: KICK: D(ds/2) K(ds/2) | K(ds/2) D(ds/2); half-slices:
+                // D(ds/4) K(ds/2) D(ds/4) | D(ds/4) K(ds/2) D(ds/4)
+                const MixCurvedDrift& cd = el.td[KICK ? 0 : 1];
+                const FF hehl{0.5f * el.ehl_ff.x, 0.5f * el.ehl_ff.y};
+                const FF hehlh{0.5f * el.ehlh_ff.x, 0.5f * el.ehlh_ff.y};
                 for (int s = 0; s < N; ++s) {
-                    mixed_bend_step(z, k, half, etah, eta1, omeff, etahff, iehff, iPa2ff, py, Pa2, px, ps2, ips, Ps,
-                                    dPsP, PsM1);
+                    if (teapot) {
+                        mixed_curved_drift(z, k, cd, h);
+                        mixed_teapot_kick(z, hehl, hehlh);
+                        if constexpr (!KICK) mixed_curved_drift(z, k, cd, h);
+                        px = z.Px.hi;
+                        ps2 = Pa2 - px * px;
+                        ips = rsqrtf(ps2);
+                        Ps = ps2 * ips;
+                        dPsP = -__fdividef(px * px + py * py, Ps + k.P);
+                    } else {
+                        mixed_bend_step(z, k, half, etah, eta1, omeff, etahff, iehff, iPa2ff, py, Pa2, px, ps2, ips,
+                                        Ps, dPsP, PsM1);
+                    }
                     // slice middle: ds (Omega - Omega_ref)
                     const float hX = h * z.X.hi;
                     const float g = (1.0f + hX) * ips;
@@ -216,8 +234,14 @@ __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restri
                     e.x = FF{ex, 0.0f};
                     e.z = FF{ez, 0.0f};
                     D = cnq_mul(e, D);
-                    mixed_bend_step(z, k, half, etah, eta1, omeff, etahff, iehff, iPa2ff, py, Pa2, px, ps2, ips, Ps,
-                                    dPsP, PsM1);
+                    if (teapot) {
+                        if constexpr (!KICK) mixed_curved_drift(z, k, cd, h);
+                        mixed_teapot_kick(z, hehl, hehlh);
+                        mixed_curved_drift(z, k, cd, h);
+                    } else {
+                        mixed_bend_step(z, k, half, etah, eta1, omeff, etahff, iehff, iPa2ff, py, Pa2, px, ps2, ips,
+                                        Ps, dPsP, PsM1);
+                    }
                 }
             } else {   // ST_MULT (drift-kick-drift; thin lenses too) or ST_QUAD_MK (matrix-kick)
                 const bool is_mult = type == ST_MULT;
@@ -284,7 +308,7 @@ __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restri
             const bool fr = FR && (el.type & ST_MIX_FRINGE);
             if (fr) fq_premul_cnq(qt, mixed_fringe(el, type, z0, 1.0f, 1.0f + (float)ref.G));
             fq_premul_cnq(qt, dq);
-            if (type == ST_SBEND) fq_premul_about_y(qt, el.rq);
+            if (type == ST_SBEND || (EXT && type == ST_TEAPOT)) fq_premul_about_y(qt, el.rq);
             if (fr) fq_premul_cnq(qt, mixed_fringe(el, type, z, -1.0f, 1.0f + (float)ref.G));
         }
         Quat q64{ff_to_double(qt.w), ff_to_double(qt.x), ff_to_double(qt.y), ff_to_double(qt.z)};

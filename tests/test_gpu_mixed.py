@@ -273,3 +273,110 @@ def test_mixed_midpoint_lost_particles_and_average():
     assert li[9] == 1 and alive.sum() == 39
     assert np.array_equal(got[:, alive], manual[:, alive])
     assert np.array_equal(got[:, 9], S_first[:, 9])
+
+
+# ---- TEAPOT bends (Sec. 3.6) in the mixed-precision tracker -------------------
+
+def mixed_vs_oracle(ring, z, S, turns, K, mean_tol=1e-7, max_tol=1e-6, orbit_tol=1e-8):
+    zm, Sm, lm = st.track(ring, z, S, turns, K, precision="mixed")
+    zo, So, lo = oracle.track(ring, z, S, turns, K)
+    assert np.array_equal(lm, lo)
+    alive = lo == 0
+    mean, mx = spin_err(Sm[:, alive], So[:, alive])
+    dz = np.abs(zm[:, alive] - zo[:, alive]).max(axis=1)
+    assert mean < mean_tol and mx < max_tol, (mean, mx)
+    assert dz[:4].max() < orbit_tol and dz[4] < 10 * orbit_tol, dz
+    return zm, Sm, lm
+
+
+TEAPOTS = [
+    dict(eta=1.0, fringe=0),
+    dict(eta=0.98, fringe=1),
+    dict(eta=0.0, fringe=0),
+]
+
+
+@pytest.mark.parametrize("kw", TEAPOTS, ids=["design", "field_error_kicks", "field_free"])
+@pytest.mark.parametrize("K", [0, 1, 2, 3, st.ST_SPIN_MID_HALF, st.ST_SPIN_MID_KICK])
+def test_mixed_single_teapot_bend(kw, K):
+    """One TEAPOT bend (design field, field error with fringe kicks, field-free
+    curved frame) with every Romberg order and both midpoint schemes, 10
+    turns, against the oracle.  In the field-free frame the particles leave
+    the axis (a straight line in a frame that turns 0.1 rad per pass: X of
+    order 0.1 m after one pass), outside the paraxial regime the mixed
+    tracker is built for, so that case runs one pass with an orbit bound of
+    1e-7 m."""
+    gg = 45.5
+    el = W.element("teapot", L=3.0, n_slices=8, angle=0.1, **kw)
+    ring = W.single_element_ring(el, gg)
+    z, S = W.gaussian_particles(257, gg, seed=300 + K, sigmas=dict(x=3e-3, y=3e-3, px=3e-4, py=3e-4))
+    if kw["eta"] == 0.0:
+        mixed_vs_oracle(ring, z, S, 1, K, orbit_tol=1e-7)
+    else:
+        mixed_vs_oracle(ring, z, S, 10, K)
+
+
+@pytest.mark.parametrize("K", [2, st.ST_SPIN_MID_HALF, st.ST_SPIN_MID_KICK])
+@pytest.mark.parametrize("gg", [45.5, 487.0])
+def test_mixed_drift_kick_ring_against_the_oracle(gg, K):
+    """The drift-kick RHIC-like ring (TEAPOT bends, drift-kick quadrupoles and
+    sextupoles, snakes), 10 turns, against the oracle."""
+    ring = W.with_spin_order(W.drift_kick_ring(W.rhic_like_ring(gg, n_cells=20)), 2)
+    z, S = W.gaussian_particles(200, gg, seed=63)
+    mixed_vs_oracle(ring, z, S, 10, K)
+
+
+def test_mixed_drift_kick_ring_with_fringes_and_odd_slices():
+    ring = W.with_slices(W.with_fringes(W.drift_kick_ring(W.rhic_like_ring(487.0, n_cells=12))), 3)
+    z, S = W.gaussian_particles(200, 487.0, seed=64)
+    mixed_vs_oracle(ring, z, S, 10, st.ST_SPIN_MID_KICK)
+    ring2 = W.with_spin_order(W.with_fringes(W.drift_kick_ring(W.rhic_like_ring(487.0, n_cells=12))), 2)
+    mixed_vs_oracle(ring2, z, S, 10, 2)
+
+
+@pytest.mark.parametrize("gg", [45.5, 487.0])
+def test_mixed_drift_kick_ring_1000_turns_within_1e_6(gg):
+    """1000 turns of the full drift-kick RHIC-like ring: the mixed tracker
+    against the FP64 tracker (itself at parity with the oracle), mean Delta S
+    within 1e-6, orbit within 1e-6."""
+    ring = W.with_spin_order(W.drift_kick_ring(W.rhic_like_ring(gg)), 2)
+    z, S = W.gaussian_particles(1024, gg, seed=3452)
+    zm, Sm, lm = st.track(ring, z, S, 1000, 2, precision="mixed")
+    zf, Sf, lf = st.track(ring, z, S, 1000, 2)
+    assert np.array_equal(lm, lf)
+    mean, mx = spin_err(Sm, Sf)
+    dz = np.abs(zm - zf).max(axis=1)
+    print(f"TEAPOT ring, G gamma0 = {gg}: mixed vs FP64 after 1000 turns: dS mean {mean:.3e} max {mx:.3e}, "
+          f"orbit {dz[:5]}")
+    assert mean <= 1e-6, (mean, mx)
+    assert dz[:4].max() < 1e-6
+
+
+def test_mixed_teapot_lost_particles_and_orbit_only():
+    """Particles lost in a TEAPOT bend (a line that never meets the turned
+    frame; an imaginary Ps) are flagged and keep their entrance state as in the
+    oracle; the orbit-only mode tracks the same orbit."""
+    gg = 45.5
+    ring = W.with_spin_order(W.drift_kick_ring(W.toy_ring(gg)), 2)
+    ring["elements"] = [e for e in ring["elements"] if e["type"] == "teapot"][:1] + ring["elements"]
+    z, S = W.gaussian_particles(40, gg, seed=4)
+    z[1, 5], z[3, 5], z[5, 5] = 0.9995, 0.0, 0.0
+    z[3, 21] = -1.2
+    zm, Sm, lm = mixed_vs_oracle(ring, z, S, 3, 2)
+    assert lm[5] == 1 and lm[21] == 1 and lm.sum() == 2
+    # the entrance state, to the 48 bits of the compensated pairs
+    assert np.abs(zm[:, 21] - z[:, 21]).max() <= 1e-14 * np.abs(z[:, 21]).max()
+    assert np.abs(zm[:, 5] - z[:, 5]).max() <= 1e-14 * np.abs(z[:, 5]).max()
+    assert np.array_equal(Sm[:, 5], S[:, 5]) and np.array_equal(Sm[:, 21], S[:, 21])
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, 40, "mixed")
+    tr.upload(z, S)
+    tr.track_orbit(3)
+    zo, So, lo = tr.download()
+    tr.close()
+    lat.close()
+    # the orbit-only kernel may contract FP32 operations differently
+    assert np.array_equal(lo, lm) and np.array_equal(So, S)
+    alive = lm == 0
+    assert np.abs(zo[:4, alive] - zm[:4, alive]).max() < 1e-9
+    assert np.array_equal(zo[:, ~alive], zm[:, ~alive])

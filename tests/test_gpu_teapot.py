@@ -112,13 +112,21 @@ def test_batched_jobs_with_teapot_bends():
 
 
 def test_teapot_validation_and_mixed_rejection():
+    """Second-order TEAPOT bends run in the mixed-precision tracker too; the
+    fourth-order composition, and TEAPOT bends in a mixed batch, are refused."""
     ring = W.with_spin_order(W.drift_kick_ring(W.toy_ring(45.5)), 2)
     lat = st.Lattice(ring)
-    with pytest.raises(st.SpinTrackError):
-        st.Tracker(lat, 64, precision="mixed")
+    t = st.Tracker(lat, 64, precision="mixed")
+    t.close()
     t = st.Tracker(lat, 64)
     t.close()
     lat.close()
+    with pytest.raises(st.SpinTrackError):
+        st.Batch([ring], [64], "mixed")
+    lat4 = st.Lattice(W.with_split_order(ring, 4))
+    with pytest.raises(st.SpinTrackError):
+        st.Tracker(lat4, 64, precision="mixed")
+    lat4.close()
     bad = W.single_element_ring(W.element("teapot", L=3.0, n_slices=4, angle=0.0), 45.5)
     with pytest.raises(st.SpinTrackError):
         st.Lattice(bad)
