@@ -63,7 +63,7 @@ extern "C" {
                            velocity taken along the kinetic momentum (Eq. (mgVSol)),
                            and thin-pancake fringes at both ends with the spin kicks of
                            Eq. (solFringe) (orbit unchanged across a fringe).  FP64
-                           only: a mixed-precision context or batch over a lattice
+                           and mixed-precision contexts; a mixed batch over a lattice
                            with solenoids is rejected (ST_EINVAL).                     */
 
 #define ST_RBEND    6   /* rectangular bend, Sec. 3.2: L = magnet length along its
@@ -177,8 +177,8 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
 int st_lattice_destroy(st_lattice* lat);
 
 /* Create a tracking context for n_particles >= 1 particles on the current
- * device.  precision is ST_FP64 or ST_MIXED (lattices with solenoids,
- * rectangular bends or fourth-order maps: ST_FP64 only, ST_EINVAL otherwise).  cuda_stream is a cudaStream_t
+ * device.  precision is ST_FP64 or ST_MIXED (lattices with rectangular bends
+ * or fourth-order maps: ST_FP64 only, ST_EINVAL otherwise).  cuda_stream is a cudaStream_t
  * (e.g. torch.cuda.current_stream().cuda_stream) or NULL for a stream owned by
  * the context.  Allocates the device state (orbit as (X,Px), (Y,Py), (T,Pt)
  * double2 arrays, spin, lost flags) and a staging buffer.  The lattice must
@@ -266,8 +266,8 @@ typedef struct st_batch st_batch;
 
 /* n_jobs >= 1 jobs: lattices[j] (must outlive the batch) and n_particles[j]
  * (1..2^30).  precision ST_FP64 or ST_MIXED (a mixed batch takes neither the
- * lattices an ST_MIXED context refuses nor TEAPOT bends); cuda_stream as
- * st_ctx_create.
+ * lattices an ST_MIXED context refuses nor TEAPOT bends or solenoids);
+ * cuda_stream as st_ctx_create.
  * Errors: ST_EINVAL, ST_ENOMEM, ST_ECUDA. */
 int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particles, int32_t n_jobs,
                     int32_t precision, void* cuda_stream, st_batch** out);

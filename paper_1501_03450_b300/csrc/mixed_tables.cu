@@ -167,6 +167,30 @@ int build_mixed_tables(LatticeImpl& L) {
             }
             break;
         }
+        case ST_SOLENOID: {
+            // Sec. 3.7: ks, eta = ks/2 (body), ks/4 (fringes); on-axis, on-momentum
+            // particle: Omega = -(1 + G) ks s^ (Eq. (6b) with the velocity along s),
+            // a rotation about s; the kernel evaluates the deviations in the
+            // relabelled frame (y, s, x), where this axis is the second one as in
+            // a bend, so the weights and the rho table below are the bend's
+            const double ks = d.a[0];
+            L.mix_ext = true;
+            m.ks_ff = split(ks);
+            m.seta_ff = split(d.a[1]);
+            m.setaf_ff = split(d.a[2]);
+            m.ks1G_ff = split(ks * (1.0 + G));
+            omr = -(1.0 + G) * ks;
+            m.omr = (float)omr;
+            const double phi = omr * d.ds * d.n_slices;
+            rq[0] = std::cos(0.5 * phi);
+            rq[3] = std::sin(0.5 * phi);
+            m.rho_off = (int)(rho.size() / 2);
+            for (int i = 0; i <= d.n_slices; ++i) {
+                rho.push_back((float)std::cos(omr * i * d.ds));
+                rho.push_back((float)std::sin(omr * i * d.ds));
+            }
+            break;
+        }
         case ST_SNAKE:
             for (int c = 0; c < 4; ++c) rq[c] = d.a[c];
             break;

@@ -117,6 +117,9 @@ struct __align__(16) MixElem {
     // eta h ds and eta h^2 ds, as (hi, lo)
     MixCurvedDrift td[2];
     float2 ehl_ff, ehlh_ff;
+    // solenoid (Sec. 3.7, 4.4): ks = b0/(B rho), eta = ks/2 of the body map, ks/4
+    // (the vector potential in the middle of a fringe), ks (1 + G), as (hi, lo)
+    float2 ks_ff, seta_ff, setaf_ff, ks1G_ff;
     float2 rq[4];                     // reference rotation over the element (bends, snakes), (hi, lo) per component
     MixWeight w[6];
 };
@@ -147,7 +150,8 @@ struct LatticeImpl {
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
     bool fp64_only = false;        // solenoids, rectangular or TEAPOT bends, fourth-order maps: FP64 only
     bool mix_fringe = false;       // mixed table entries carry ST_MIX_FRINGE (thin fringe spin kicks)
-    bool mix_ext = false;          // the lattice has TEAPOT bends (the mixed kernels' extended instantiation)
+    bool mix_ext = false;          // the lattice has TEAPOT bends or solenoids (the mixed kernels'
+                                   // extended instantiation)
     bool has_ext = false;          // fourth-order slice maps, rectangular or TEAPOT bends or thin lenses present
     bool has_order4 = false;       // fourth-order slice maps present
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]

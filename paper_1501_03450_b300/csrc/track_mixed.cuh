@@ -215,7 +215,8 @@ struct MConst {
     FF invP, tau, PM1;                     // 1/P; 1/beta0 - (1/beta0 + Pt)/P; P - 1
     FF aP, a0P, c1P;                       // a/P, a0/P, c1/P (spin: first-order coefficients)
     FF invP2, Ptf, b0ptf;                  // 1/P^2, Pt, 1/beta0 + Pt
-    FF hiP3;                               // 1/(2 P^3) (TEAPOT bends only)
+    FF hiP3;                               // 1/(2 P^3) (TEAPOT bends, solenoids)
+    FF cP2, PM1P;                          // G (gamma - 1)/P^2, (P - 1)/P (solenoids)
     float Pt, P2, P2m1, invPf, P, b0pt, a, c, da, f3, a0, c1;
 };
 
@@ -306,6 +307,8 @@ __device__ __forceinline__ void mixed_particle_consts(const RefConst& ref, doubl
     k.c1P = ff_make(c1 * invP64);
     k.invP2 = ff_make(1.0 / P2);
     k.hiP3 = ff_make(0.5 * invP64 * invP64 * invP64);
+    k.cP2 = ff_make(ref.G * (gamma - 1.0) / P2);
+    k.PM1P = ff_make(P2m1 / (P + 1.0) * invP64);
     k.Ptf = ff_make(Pt);
     k.b0ptf = ff_make(b0pt);
 }
@@ -482,23 +485,30 @@ struct MixLevels {
 // the leading terms compensated, the series factors in FP32 (FP32 throughout
 // for e >= 4e-3, far from the axis).  If the line does not meet the turned
 // frame (1 - eps <= 0) or Ps^2 <= 0, X becomes NaN: the particle is lost.
-__device__ __forceinline__ void mixed_curved_drift(MState& z, const MConst& k, const MixCurvedDrift& c, float h) {
-    const FF sn{c.sn_ff.x, c.sn_ff.y}, A1{c.A1_ff.x, c.A1_ff.y}, A2{c.A2_ff.x, c.A2_ff.y};
-    const FF omc{c.omc_ff.x, c.omc_ff.y};
-    const FF pp = ff_add(ff_mul(z.Px, z.Px), ff_mul(z.Py, z.Py));
+// Ps - P and d = 1/Ps - 1/P (compensated) for a transverse momentum (px, py)
+// with p^2 = px^2 + py^2 not small against the compensation's precision (see
+// below); NaN if Ps^2 <= 0.
+__device__ __forceinline__ void ps_deviations(const MConst& k, const FF& px, const FF& py, FF& dPsP, FF& d) {
+    const FF pp = ff_add(ff_mul(px, px), ff_mul(py, py));
     const float e = pp.hi * k.invPf * k.invPf;
-    FF dPsP, d;   // Ps - P, 1/Ps - 1/P
     if (e < 4e-3f) {
         const FF u = ff_mul(pp, FF{0.5f * k.invP.hi, 0.5f * k.invP.lo});   // p^2/(2P)
         dPsP = ff_addn(ff_neg(u), -u.hi * e * fmaf(e, fmaf(e, 5.0f / 64.0f, 0.125f), 0.25f));
         const FF dd = ff_mul(pp, k.hiP3);                                  // p^2/(2P^3)
         d = ff_addn(dd, dd.hi * e * fmaf(e, fmaf(e, 35.0f / 64.0f, 0.625f), 0.75f));
     } else {   // far from the axis (the series would not converge fast): FP32
-        const float ipsf = rsqrtf(k.P2 - pp.hi);
+        const float ipsf = rsqrtf(k.P2 - pp.hi);   // NaN for Ps^2 < 0
         const float Psf = (k.P2 - pp.hi) * ipsf;
         d = FF{pp.hi * k.invPf * ipsf / (k.P + Psf), 0.0f};
         dPsP = FF{-pp.hi / (Psf + k.P), 0.0f};
     }
+}
+
+__device__ __forceinline__ void mixed_curved_drift(MState& z, const MConst& k, const MixCurvedDrift& c, float h) {
+    const FF sn{c.sn_ff.x, c.sn_ff.y}, A1{c.A1_ff.x, c.A1_ff.y}, A2{c.A2_ff.x, c.A2_ff.y};
+    const FF omc{c.omc_ff.x, c.omc_ff.y};
+    FF dPsP, d;   // Ps - P, 1/Ps - 1/P
+    ps_deviations(k, z.Px, z.Py, dPsP, d);
     const FF ips = ff_add(k.invP, d);
     // (x', y') and (x' A2, y' A2), both planes in packed FP32x2 arithmetic
     const FF2 pr = ff2_mul(ff2_pack(z.Px, z.Py), ff2_pack(ips, ips));
@@ -522,13 +532,104 @@ __device__ __forceinline__ void mixed_curved_drift(MState& z, const MConst& k, c
     z.Y = ff_add(z.Y, dY);
     z.Px = ff_add(z.Px, dPx);
     z.T = ff_add(z.T, dT);
-    if (!(ome > 0.0f && k.P2 - pp.hi > 0.0f)) z.X.hi = __int_as_float(0x7fc00000);   // quiet NaN
+    if (!(ome > 0.0f && k.P + dPsP.hi > 0.0f)) z.X.hi = __int_as_float(0x7fc00000);   // quiet NaN
 }
 
 // Kick of the bend's uniform field, dPx = -eta h len (1 + hX), from the
 // compensated eta h len and eta h^2 len.
 __device__ __forceinline__ void mixed_teapot_kick(MState& z, const FF& ehl, const FF& ehlh) {
     z.Px = ff_add(z.Px, ff_neg(ff_add(ehl, ff_mul(z.X, ehlh))));
+}
+
+// ---- solenoid (Sec. 3.7, 4.4) ------------------------------------------------
+// In the body the kinetic momentum (Px + eta Y, Py - eta X), eta = ks/2, keeps
+// its Ps, and a slice of length len is the map of Eq. (solenoid) with
+// kappa = eta/Ps, theta = kappa len = theta0 + delta, theta0 = eta len/P (FP64
+// once per element and particle) and delta = eta len (1/Ps - 1/P) (of order
+// 1e-10 of theta0 near the axis):
+//   cos theta - 1 = (cos theta0 - 1) - sin theta0 delta,
+//   sin theta = sin theta0 + cos theta0 delta,
+//   sin theta / eta = sin theta0 / eta + cos theta0 len (1/Ps - 1/P),
+// compensated; d = 1/Ps - 1/P of the kinetic momentum.
+struct MSolSlice {
+    FF cm1, sn, a12, a21;
+};
+
+__device__ __forceinline__ MSolSlice mixed_solenoid_slice(const FF& eta, double len, double invP64, float d) {
+    const double eta64 = (double)eta.hi + (double)eta.lo;
+    const double th0 = eta64 * len * invP64;
+    double s2, c2;
+    sincos(0.5 * th0, &s2, &c2);
+    const double s0 = 2.0 * s2 * c2, c0m1 = -2.0 * s2 * s2;
+    // sin(theta0)/eta = (len/P) sin(theta0)/theta0
+    const double s0ieta = fabs(th0) > 1e-4 ? s0 / eta64 : len * invP64 * (1.0 - th0 * th0 * (1.0 / 6.0 - th0 * th0 / 120.0));
+    const float c0f = (float)(1.0 + c0m1);
+    const float delta = eta.hi * (float)len * d;
+    MSolSlice m;
+    m.cm1 = ff_add_f(ff_make(c0m1), -(float)s0 * delta);
+    m.sn = ff_add_f(ff_make(s0), c0f * delta);
+    m.a12 = ff_add_f(ff_make(s0ieta), c0f * (float)len * d);
+    m.a21 = ff_neg(ff_mul(eta, m.sn));
+    return m;
+}
+
+// One body slice, in increment form with both planes in packed FP32x2
+// arithmetic: (U, PU) <- (cos U + (sin/eta) PU, -eta sin U + cos PU), then the
+// (X, Y) and (Px, Py) planes rotated by -theta; T += len (tau - (1/beta0 + Pt) d).
+__device__ __forceinline__ void mixed_solenoid_map(MState& z, const MConst& k, const MSolSlice& m, const FF& lenff,
+                                                   float d) {
+    const FF2 cm1 = ff2_pack(m.cm1, m.cm1), a12 = ff2_pack(m.a12, m.a12), a21 = ff2_pack(m.a21, m.a21);
+    const FF2 rs = ff2_pack(m.sn, ff_neg(m.sn));
+    const FF2 U = ff2_pack(z.X, z.Y), PU = ff2_pack(z.Px, z.Py);
+    const FF2 U1 = ff2_add(U, ff2_add(ff2_mul(U, cm1), ff2_mul(PU, a12)));
+    const FF2 PU1 = ff2_add(PU, ff2_add(ff2_mul(U, a21), ff2_mul(PU, cm1)));
+    const FF2 U1s{make_float2(U1.hi.y, U1.hi.x), make_float2(U1.lo.y, U1.lo.x)};
+    const FF2 PU1s{make_float2(PU1.hi.y, PU1.hi.x), make_float2(PU1.lo.y, PU1.lo.x)};
+    const FF2 U2 = ff2_add(U1, ff2_add(ff2_mul(U1, cm1), ff2_mul(U1s, rs)));
+    const FF2 PU2 = ff2_add(PU1, ff2_add(ff2_mul(PU1, cm1), ff2_mul(PU1s, rs)));
+    z.X = ff2_first(U2);
+    z.Y = ff2_second(U2);
+    z.Px = ff2_first(PU2);
+    z.Py = ff2_second(PU2);
+    z.T = ff_add(z.T, ff_mul(lenff, ff_add_f(k.tau, -k.b0pt * d)));
+}
+
+// Deviation of Omega (Eq. (6b), velocity along the kinetic momentum) from the
+// on-axis reference -(1 + G) ks s^, in the relabelled frame (x~, y~, z~) =
+// (y, s, x) (a cyclic permutation, a proper rotation) where the reference axis
+// is y~ as in a sector bend: f = G (gamma - 1) ks/P^2,
+//   Omega_x = f kx, Omega_y = f ky (first order, rounded to FP32 once),
+//   Omega_s + (1 + G) ks = ks (1 + G)(P - 1)/P + f (Ps - P) - a ks d.
+__device__ __forceinline__ void solenoid_dev_omega(const MConst& k, const MState& z, const FF& eta, const FF& f,
+                                                   const FF& ks1G, float ks, float dPsP, float d, float& ox_t,
+                                                   FF& oy_t, float& oz_t) {
+    const FF kx = ff_add(z.Px, ff_mul(eta, z.Y)), ky = ff_add(z.Py, ff_neg(ff_mul(eta, z.X)));
+    const FF fx = ff_mul(f, kx), fy = ff_mul(f, ky);
+    ox_t = fy.hi + fy.lo;
+    oz_t = fx.hi + fx.lo;
+    oy_t = ff_addn(ff_mul(ks1G, k.PM1P), f.hi * dPsP - k.a * ks * d);
+}
+
+// Thin-pancake fringe spin kick of a solenoid, Eq. (solFringe):
+//   w = sign (ks/2)/Ps' [a (X, Y, 0) - G (gamma - 1)(X Px + Y Py)/P^2 (px', py', Ps')]
+// with (px', py') = (Px + (ks/4) Y, Py - (ks/4) X); the first-order part
+// sign (ks/2)(a/P)(X, Y) compensated, the rest in FP32; NaN if Ps'^2 <= 0.
+__device__ __forceinline__ CNQ mixed_solenoid_fringe(const MConst& k, const MState& z, const FF& ks, float etaf,
+                                                     float sign) {
+    const float pxk = z.Px.hi + etaf * z.Y.hi, pyk = z.Py.hi - etaf * z.X.hi;
+    float dk, ppk;
+    const FF ipsk = inv_ps(k, pxk, pyk, dk, ppk);
+    const float ipsf = ipsk.hi;
+    const float hks = 0.5f * sign * ks.hi;
+    const float pre = hks * ipsf;
+    const float xp = (z.X.hi * z.Px.hi + z.Y.hi * z.Py.hi) * k.invPf * k.invPf * k.c;
+    const FF c1 = ff_mul(k.aP, FF{0.5f * sign * ks.hi, 0.5f * sign * ks.lo});
+    const FF bx = ff_add_f(ff_mul(z.X, c1), hks * k.a * z.X.hi * dk - pre * xp * pxk);
+    const FF by = ff_add_f(ff_mul(z.Y, c1), hks * k.a * z.Y.hi * dk - pre * xp * pyk);
+    const float bz = -pre * xp * ((k.P2 - ppk) * ipsf);
+    CNQ q = cnq_from_rotvec(bx, by, bz);
+    if (!(k.P2 - ppk > 0.0f)) q.w = __int_as_float(0x7fc00000);   // quiet NaN: the particle is lost
+    return q;
 }
 
 // Thin fringe spin kick of a multipole, quadrupole, sector or TEAPOT bend (Sec. 4.5,
@@ -752,6 +853,28 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                         lv.add_bend(s, N, el, r.x, r.y, ox, oyf, os);
                     }
                 }
+            } else if (EXT && type == ST_SOLENOID) {
+                // Sec. 3.7: exact body map in N slices, Omega at the slice edges along
+                // the kinetic momentum, whose Ps the body conserves; the spin edges in
+                // the relabelled frame (y, s, x) with the bend's deviation code
+                const FF eta{el.seta_ff.x, el.seta_ff.y}, ks{el.ks_ff.x, el.ks_ff.y};
+                const FF kx = ff_add(z.Px, ff_mul(eta, z.Y)), ky = ff_add(z.Py, ff_neg(ff_mul(eta, z.X)));
+                FF dPsPk, dk;
+                ps_deviations(k, kx, ky, dPsPk, dk);
+                const MSolSlice m = mixed_solenoid_slice(eta, (double)el.ds_ff.x + (double)el.ds_ff.y, invP64, dk.hi);
+                const FF dsff{el.ds_ff.x, el.ds_ff.y};
+                const FF f = ff_mul(k.cP2, ks);
+                const FF ks1G{el.ks1G_ff.x, el.ks1G_ff.y};
+                const float2* rh = rho + el.rho_off;
+                for (int s = 0; s <= N; ++s) {
+                    if (s > 0) mixed_solenoid_map(z, k, m, dsff, dk.hi);
+                    if constexpr (SPIN) {
+                        FF oyt;
+                        solenoid_dev_omega(k, z, eta, f, ks1G, ks.hi, dPsPk.hi, dk.hi, ox, oyt, os);
+                        const float2 r = rh[s];
+                        lv.add_bend(s, N, el, r.x, r.y, ox, oyt, os);
+                    }
+                }
             } else {   // ST_MULT (drift-kick-drift; thin lenses too) or ST_QUAD_MK (matrix-kick)
                 // one loop over the slice edges for both straight element kinds (edge
                 // 0: no orbit step), so that the spin edge code exists once
@@ -828,7 +951,26 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 }
             }
             if constexpr (SPIN) {
-                const CNQ dq = lv.romberg();
+                CNQ dq = lv.romberg();
+                if (EXT && type == ST_SOLENOID) {
+                    // back from the relabelled frame; the fringe kicks of Sec. 4.4 at
+                    // the entrance (entry state) and the exit
+                    dq = CNQ{dq.w, dq.z, dq.x, dq.y};
+                    const FF ks{el.ks_ff.x, el.ks_ff.y};
+                    const CNQ fi = mixed_solenoid_fringe(k, z0, ks, el.setaf_ff.x, 1.0f);
+                    const CNQ fo = mixed_solenoid_fringe(k, z, ks, el.setaf_ff.x, -1.0f);
+                    if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi + dq.w + dq.x.hi + dq.y.hi +
+                                  dq.z.hi + fi.w + fi.x.hi + fi.y.hi + fi.z.hi + fo.w + fo.x.hi + fo.y.hi + fo.z.hi)) {
+                        z = z0;
+                        is_lost = true;
+                        break;
+                    }
+                    fq_premul_cnq(qt, fi);
+                    fq_premul_cnq(qt, dq);
+                    fq_premul_ref(qt, el.rq);
+                    fq_premul_cnq(qt, fo);
+                    continue;
+                }
                 if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi + dq.w + dq.x.hi + dq.y.hi + dq.z.hi)) {
                     z = z0;
                     is_lost = true;

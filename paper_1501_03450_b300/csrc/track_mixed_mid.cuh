@@ -243,6 +243,34 @@ __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restri
                                         Ps, dPsP, PsM1);
                     }
                 }
+            } else if (EXT && type == ST_SOLENOID) {
+                // exact body map over half-slices, Omega at the slice middle along the
+                // kinetic momentum (its Ps conserved in the body), the deviation in the
+                // relabelled frame (y, s, x) as in the Romberg kernel
+                const FF eta{el.seta_ff.x, el.seta_ff.y}, ks{el.ks_ff.x, el.ks_ff.y};
+                const FF kx = ff_add(z.Px, ff_mul(eta, z.Y)), ky = ff_add(z.Py, ff_neg(ff_mul(eta, z.X)));
+                FF dPsPk, dk;
+                ps_deviations(k, kx, ky, dPsPk, dk);
+                const MSolSlice m =
+                    mixed_solenoid_slice(eta, 0.5 * ((double)el.ds_ff.x + (double)el.ds_ff.y), invP64, dk.hi);
+                const FF hdff{0.5f * dsff.hi, 0.5f * dsff.lo};
+                const FF f = ff_mul(k.cP2, ks);
+                const FF ks1G{el.ks1G_ff.x, el.ks1G_ff.y};
+                const float2* rh = rho + el.rho_off;
+                for (int s = 0; s < N; ++s) {
+                    mixed_solenoid_map(z, k, m, hdff, dk.hi);
+                    float oxt, ozt;
+                    FF oyt;
+                    solenoid_dev_omega(k, z, eta, f, ks1G, ks.hi, dPsPk.hi, dk.hi, oxt, oyt, ozt);
+                    CNQ e = cnq_deviation(el.w[1], ds * oxt, ff_mul(dsff, oyt), ds * ozt);
+                    const float2 r = rh[s];
+                    const float ex = e.x.hi * r.x - e.z.hi * r.y;
+                    const float ez = e.x.hi * r.y + e.z.hi * r.x;
+                    e.x = FF{ex, 0.0f};
+                    e.z = FF{ez, 0.0f};
+                    D = cnq_mul(e, D);
+                    mixed_solenoid_map(z, k, m, hdff, dk.hi);
+                }
             } else {   // ST_MULT (drift-kick-drift; thin lenses too) or ST_QUAD_MK (matrix-kick)
                 const bool is_mult = type == ST_MULT;
                 const float k1 = el.k1;
@@ -299,7 +327,25 @@ __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restri
                     }
                 }
             }
-            const CNQ dq = cnq_normalize(D);
+            CNQ dq = cnq_normalize(D);
+            if (EXT && type == ST_SOLENOID) {
+                // back from the relabelled frame, between the fringe kicks of Sec. 4.4
+                dq = CNQ{dq.w, dq.z, dq.x, dq.y};
+                const FF ks{el.ks_ff.x, el.ks_ff.y};
+                const CNQ fi = mixed_solenoid_fringe(k, z0, ks, el.setaf_ff.x, 1.0f);
+                const CNQ fo = mixed_solenoid_fringe(k, z, ks, el.setaf_ff.x, -1.0f);
+                if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi + dq.w + dq.x.hi + dq.y.hi + dq.z.hi +
+                              fi.w + fi.x.hi + fi.y.hi + fi.z.hi + fo.w + fo.x.hi + fo.y.hi + fo.z.hi)) {
+                    z = z0;
+                    is_lost = true;
+                    break;
+                }
+                fq_premul_cnq(qt, fi);
+                fq_premul_cnq(qt, dq);
+                fq_premul_ref(qt, el.rq);
+                fq_premul_cnq(qt, fo);
+                continue;
+            }
             if (!isfinite(z.X.hi + z.Px.hi + z.Y.hi + z.Py.hi + z.T.hi + dq.w + dq.x.hi + dq.y.hi + dq.z.hi)) {
                 z = z0;
                 is_lost = true;

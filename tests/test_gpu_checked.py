@@ -39,6 +39,8 @@ out["mid_z"], out["mid_S"], out["mid_l"] = st.track(dk, z, S, 5, st.ST_SPIN_MID_
 dk2 = W.with_spin_order(dk, 2)
 out["mdk_z"], out["mdk_S"], out["mdk_l"] = st.track(dk2, z, S, 5, 2, precision="mixed")
 out["mdm_z"], out["mdm_S"], out["mdm_l"] = st.track(dk, z, S, 5, st.ST_SPIN_MID_HALF, precision="mixed")
+sol = W.with_spin_order(W.solenoid_ring(45.5), 2)
+out["msol_z"], out["msol_S"], out["msol_l"] = st.track(sol, z, S, 3, 2, precision="mixed")
 b = st.Batch([toy, W.with_spin_order(W.rhic_like_ring(300.0, n_cells=6), 2)], [300, 77], "mixed")
 b.upload(0, z, S)
 z2, S2 = W.gaussian_particles(77, 300.0, seed=6)
@@ -84,7 +86,8 @@ def test_checked_build_runs_clean_and_matches_the_oracle(tmp_path):
     assert np.array_equal(d["bat_l"], lo)
     assert np.abs(d["bat_S"] - So).max() < 1e-6
     # the mixed tracker's TEAPOT instantiation (Romberg and midpoint kernels)
-    for key, ring, K in (("mdk", W.with_spin_order(dk, 2), 2), ("mdm", dk, oracle.MID_HALF)):
-        zo, So, lo = oracle.track(ring, z, S, 5, K)
+    for key, ring, K in (("mdk", W.with_spin_order(dk, 2), 2), ("mdm", dk, oracle.MID_HALF),
+                         ("msol", W.with_spin_order(W.solenoid_ring(45.5), 2), 2)):
+        zo, So, lo = oracle.track(ring, z, S, 3 if key == "msol" else 5, K)
         assert np.array_equal(d[key + "_l"], lo)
         assert np.abs(d[key + "_S"] - So).max() < 1e-6
