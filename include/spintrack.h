@@ -63,8 +63,7 @@ extern "C" {
                            velocity taken along the kinetic momentum (Eq. (mgVSol)),
                            and thin-pancake fringes at both ends with the spin kicks of
                            Eq. (solFringe) (orbit unchanged across a fringe).  FP64
-                           and mixed-precision contexts; a mixed batch over a lattice
-                           with solenoids is rejected (ST_EINVAL).                     */
+                           and mixed precision, single contexts and batches.          */
 
 #define ST_RBEND    6   /* rectangular bend, Sec. 3.2: L = magnet length along its
                            Cartesian axis, angle = total bend, eta = field factor, e1 =
@@ -86,8 +85,8 @@ extern "C" {
                            split_order 4 composes it to fourth order.  eta = 0 is a
                            field-free curved frame.  The paper's comparison integrator:
                            less accurate than ST_SBEND at any slice count.  FP64 and
-                           (second order) mixed-precision contexts; a mixed batch over a
-                           lattice with TEAPOT bends is rejected (ST_EINVAL).          */
+                           (second order) mixed precision, single contexts and
+                           batches.                                                     */
 
 #define ST_THIN_MULT 8  /* thin lens, Sec. 3.5: the ST_MULT multipole in the limit of zero
                            length at fixed integrated strengths, k1 = integrated quadrupole
@@ -265,9 +264,8 @@ int st_ctx_set_launch(st_ctx* ctx, int32_t block_threads, int32_t turns_per_laun
 typedef struct st_batch st_batch;
 
 /* n_jobs >= 1 jobs: lattices[j] (must outlive the batch) and n_particles[j]
- * (1..2^30).  precision ST_FP64 or ST_MIXED (a mixed batch takes neither the
- * lattices an ST_MIXED context refuses nor TEAPOT bends or solenoids);
- * cuda_stream as st_ctx_create.
+ * (1..2^30).  precision ST_FP64 or ST_MIXED (a mixed batch takes the lattices
+ * an ST_MIXED context takes); cuda_stream as st_ctx_create.
  * Errors: ST_EINVAL, ST_ENOMEM, ST_ECUDA. */
 int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particles, int32_t n_jobs,
                     int32_t precision, void* cuda_stream, st_batch** out);

@@ -104,3 +104,33 @@ def test_batch_errors():
     with pytest.raises(st.SpinTrackError):
         b.set_launch(block_threads=256)
     b.close()
+
+
+def test_mixed_batch_with_teapot_bends_and_solenoids():
+    """A mixed batch whose jobs hold TEAPOT bends, solenoids, fringe kicks and
+    plain elements (the extended mixed instantiation for the whole batch):
+    every job against the oracle within the mixed tracker's budget, and
+    against the single-job mixed tracker."""
+    rings = [W.with_spin_order(W.drift_kick_ring(W.toy_ring(45.5)), 2),
+             W.with_spin_order(W.solenoid_ring(120.0, ks=0.05), 2),
+             W.with_spin_order(W.with_fringes(W.rhic_like_ring(300.0, n_cells=6)), 2),
+             W.with_spin_order(W.toy_ring(45.5), 2)]
+    ns = [300, 77, 150, 33]
+    b = st.Batch(rings, ns, "mixed")
+    inputs = []
+    for k, (ring, n) in enumerate(zip(rings, ns)):
+        z, S = W.gaussian_particles(n, ring["Ggamma0"], seed=90 + k)
+        b.upload(k, z, S)
+        inputs.append((z, S))
+    b.track(4, 2)
+    for k, (ring, (z, S)) in enumerate(zip(rings, inputs)):
+        zb, Sb, lb = b.download(k)
+        zo, So, lo = oracle.track(ring, z, S, 4, 2)
+        assert np.array_equal(lb, lo)
+        d = np.linalg.norm(Sb - So, axis=0)
+        assert d.mean() < 1e-7 and d.max() < 1e-6, (k, d.mean(), d.max())
+        assert np.abs(zb[:4] - zo[:4]).max() < 1e-8
+        zs, Ss, ls = st.track(ring, z, S, 4, 2, precision="mixed")
+        assert np.array_equal(lb, ls)
+        assert np.abs(Sb - Ss).max() < TOL_MIXED and np.abs(zb - zs).max() < TOL_MIXED
+    b.close()

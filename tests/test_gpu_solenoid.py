@@ -3,8 +3,7 @@ the CUDA FP64 tracker through the C ABI against the CPU oracle on the same
 seeded inputs, every coordinate and spin component at 1e-11, for a single
 solenoid at two energies and field strengths and every Romberg order, a ring
 with solenoids, lost particles, the zero-field limit, the batched entry point,
-and the mixed-precision tracker's solenoids within its error budget (mixed
-batches refuse them)."""
+and the mixed-precision tracker's solenoids within its error budget."""
 import math
 
 import numpy as np
@@ -125,14 +124,12 @@ def test_batched_jobs_with_solenoids_equal_single_job():
     b.close()
 
 
-def test_mixed_precision_solenoids_and_batch_refusal():
-    """A mixed-precision context takes solenoids; a mixed batch refuses them."""
+def test_mixed_precision_contexts_and_batches_take_solenoids():
     ring = W.with_spin_order(W.solenoid_ring(45.5), 2)
     lat = st.Lattice(ring)
     t = st.Tracker(lat, 64, precision="mixed")
     t.close()
-    with pytest.raises(st.SpinTrackError):
-        st.Batch([ring], [64], "mixed")
+    st.Batch([ring], [64], "mixed").close()
     t = st.Tracker(lat, 64)
     t.close()
     lat.close()

@@ -112,8 +112,8 @@ def test_batched_jobs_with_teapot_bends():
 
 
 def test_teapot_validation_and_mixed_rejection():
-    """Second-order TEAPOT bends run in the mixed-precision tracker too; the
-    fourth-order composition, and TEAPOT bends in a mixed batch, are refused."""
+    """Second-order TEAPOT bends run in the mixed-precision tracker and mixed
+    batches too; the fourth-order composition is refused there."""
     ring = W.with_spin_order(W.drift_kick_ring(W.toy_ring(45.5)), 2)
     lat = st.Lattice(ring)
     t = st.Tracker(lat, 64, precision="mixed")
@@ -121,8 +121,9 @@ def test_teapot_validation_and_mixed_rejection():
     t = st.Tracker(lat, 64)
     t.close()
     lat.close()
+    st.Batch([ring], [64], "mixed").close()
     with pytest.raises(st.SpinTrackError):
-        st.Batch([ring], [64], "mixed")
+        st.Batch([W.with_split_order(ring, 4)], [64], "mixed")
     lat4 = st.Lattice(W.with_split_order(ring, 4))
     with pytest.raises(st.SpinTrackError):
         st.Tracker(lat4, 64, precision="mixed")
