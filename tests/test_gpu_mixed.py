@@ -16,6 +16,12 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 
+# measured at G gamma0 = 487 (1024 particles, 1000 turns): p50 4.8e-8, p90 6.0e-7,
+# p99 2.5e-6, max 7.4e-6
+TAIL_P99_487 = 8e-6
+TAIL_MAX_487 = 2.5e-5
+
+
 def spin_err(Sa, Sb):
     d = np.linalg.norm(Sa - Sb, axis=0)
     return float(d.mean()), float(d.max())
@@ -103,8 +109,19 @@ def test_mixed_spin_error_1000_turns_within_1e_6(gg):
     zf, Sf, lf = st.track(ring, z, S, 1000, 2, precision="fp64")
     assert np.array_equal(lm, lf)
     mean, mx = spin_err(Sm, Sf)
+    d = np.linalg.norm(Sm - Sf, axis=0)
+    p50, p90, p99 = np.percentile(d, [50, 90, 99])
+    print(f"mixed vs FP64 after 1000 turns at {gg}: dS mean {mean:.3e} p50 {p50:.3e} p90 {p90:.3e} "
+          f"p99 {p99:.3e} max {mx:.3e}")
     assert mean <= 1e-6, (mean, mx)
     assert np.abs(zm[:4] - zf[:4]).max() < 1e-6
+    # the tail: every particle within 1e-6 at 45.5; at 487, where a 1e-12 change
+    # of Pt moves the FP64 tracker's own spins by 5e-7 on average, bounds with
+    # a margin of about 3 over the measured p99 and max
+    if gg < 100.0:
+        assert mx <= 1e-6, mx
+    else:
+        assert p99 <= TAIL_P99_487 and mx <= TAIL_MAX_487, (p99, mx)
 
 
 def test_mixed_orbit_only_tracks_the_mixed_orbit():
