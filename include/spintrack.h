@@ -154,7 +154,8 @@ typedef struct {
                           * S2(x1 ds) S2(x0 ds) S2(x1 ds), x1 = 1/(2 - 2^(1/3)),
                           * x0 = 1 - 2 x1 (Sec. 3.3's higher-order versions).  Spin is
                           * still sampled at the slice edges.  Other types: 0 or 2
-                          * (ST_EINVAL otherwise).  FP64 contexts only when 4. */
+                          * (ST_EINVAL otherwise).  With 4 the midpoint schemes are
+                          * refused (ST_EINVAL); FP64 and mixed precision. */
     double e1;           /* ST_RBEND only: face asymmetry (see ST_RBEND); ignored otherwise */
 } st_element;
 
@@ -176,8 +177,8 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
 int st_lattice_destroy(st_lattice* lat);
 
 /* Create a tracking context for n_particles >= 1 particles on the current
- * device.  precision is ST_FP64 or ST_MIXED (lattices with rectangular bends
- * or fourth-order maps: ST_FP64 only, ST_EINVAL otherwise).  cuda_stream is a cudaStream_t
+ * device.  precision is ST_FP64 or ST_MIXED (lattices with rectangular bends:
+ * ST_FP64 only, ST_EINVAL otherwise).  cuda_stream is a cudaStream_t
  * (e.g. torch.cuda.current_stream().cuda_stream) or NULL for a stream owned by
  * the context.  Allocates the device state (orbit as (X,Px), (Y,Py), (T,Pt)
  * double2 arrays, spin, lost flags) and a staging buffer.  The lattice must

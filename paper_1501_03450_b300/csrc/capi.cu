@@ -213,10 +213,9 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
             uniq.push_back(d);
         }
         seq[i] = (uint16_t)idx;
-        if (d.flags & ST_ELEM_ORDER4) L.fp64_only = true;
         if ((d.flags & ST_ELEM_ORDER4) || d.type == ST_RBEND || d.type == ST_TEAPOT || d.type == ST_THIN_MULT)
             L.has_ext = true;
-        if (d.type == ST_RBEND) L.fp64_only = true;   // TEAPOT bends of the second order run mixed too
+        if (d.type == ST_RBEND) L.fp64_only = true;   // rectangular bends: FP64 trackers only
         if (d.flags & ST_ELEM_ORDER4) L.has_order4 = true;
         if (is_spin_type(d.type)) {
             max_slices = std::max(max_slices, (int)d.n_slices);

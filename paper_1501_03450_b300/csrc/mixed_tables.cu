@@ -197,6 +197,41 @@ int build_mixed_tables(LatticeImpl& L) {
         default:
             break;
         }
+        if (d.flags & ST_ELEM_ORDER4) {
+            // fourth-order slice of a multipole, matrix-kick quadrupole or TEAPOT bend
+            // (the host packs the sub-step lengths into a[2..5])
+            m.type |= ST_MIX_ORDER4;
+            L.mix_ext = true;
+            for (int jj = 0; jj < 2; ++jj) {
+                const double dl = d.a[2 + jj], sl = d.a[4 + jj];
+                m.o4_d_ff[jj] = split(dl);
+                m.o4_s_ff[jj] = split(sl);
+                if (d.type == ST_MULT) {
+                    m.o4_k1_ff[jj] = split(d.a[0] * sl);
+                    m.o4_k2h_ff[jj] = split(0.5 * d.a[1] * sl);
+                    m.o4_k2_ff[jj] = split(d.a[1] * sl);
+                } else if (d.type == ST_TEAPOT) {
+                    const double h = d.a[0], eta = d.a[1];
+                    m.o4_k1_ff[jj] = split(eta * h * sl);
+                    m.o4_k2h_ff[jj] = split(eta * h * h * sl);
+                    // the curved drifts of the two lengths take the places of the
+                    // second-order ones (no midpoint scheme runs fourth-order maps)
+                    const double hs2 = std::sin(0.5 * h * dl);
+                    const double omc = 2.0 * hs2 * hs2, sn = std::sin(h * dl);
+                    MixCurvedDrift& c = m.td[jj];
+                    c.sn_ff = split(sn);
+                    c.A1_ff = split(omc / h);
+                    c.A2_ff = split(sn / h);
+                    c.omc_ff = split(omc);
+                    const double x = h * dl, x2 = x * x;
+                    const double lms = std::fabs(x) < 1e-2
+                                           ? dl * x2 / 6.0 * (1.0 - x2 / 20.0 * (1.0 - x2 / 42.0))
+                                           : dl - sn / h;
+                    c.dT0_ff = split(lms / beta0);
+                    c.snb0_ff = split(sn / beta0);
+                }
+            }
+        }
         if ((d.flags & ST_ELEM_FRINGE) &&
             (d.type == ST_MULT || d.type == ST_QUAD_MK || d.type == ST_SBEND || d.type == ST_TEAPOT)) {
             m.type |= ST_MIX_FRINGE;

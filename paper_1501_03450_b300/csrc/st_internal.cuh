@@ -120,6 +120,12 @@ struct __align__(16) MixElem {
     // solenoid (Sec. 3.7, 4.4): ks = b0/(B rho), eta = ks/2 of the body map, ks/4
     // (the vector potential in the middle of a fringe), ks (1 + G), as (hi, lo)
     float2 ks_ff, seta_ff, setaf_ff, ks1G_ff;
+    // fourth-order slice (Sec. 3.3, Yoshida's S2(x1 ds) S2(x0 ds) S2(x1 ds) with
+    // adjacent half steps merged), as (hi, lo): the drift / linear-flow /
+    // curved-drift lengths x1 ds/2 and (x1 + x0) ds/2, the kick / nonlinear-step
+    // lengths x1 ds and x0 ds, and the multipole kicks over those lengths (k1 l,
+    // k2 l/2, k2 l; a TEAPOT bend's eta h l and eta h^2 l in the first two)
+    float2 o4_d_ff[2], o4_s_ff[2], o4_k1_ff[2], o4_k2h_ff[2], o4_k2_ff[2];
     float2 rq[4];                     // reference rotation over the element (bends, snakes), (hi, lo) per component
     MixWeight w[6];
 };
@@ -128,6 +134,9 @@ static_assert(sizeof(MixElem) % 16 == 0, "MixElem must be a multiple of 16 bytes
 // (Sec. 4.5, Eq. (skfringe)); only the kernels instantiated for such lattices
 // read it (the element kind is the low byte).
 enum { ST_MIX_FRINGE = 0x100 };
+// MixElem::type bit of an element with the fourth-order slice map (read by the
+// extended instantiation only)
+enum { ST_MIX_ORDER4 = 0x200 };
 
 // Kernel status word values (written by bounded device waits).
 enum : int32_t { STATUS_OK = 0, STATUS_TMA_TIMEOUT = 1, STATUS_BOUNDS = 3 };
@@ -150,8 +159,8 @@ struct LatticeImpl {
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
     bool fp64_only = false;        // solenoids, rectangular or TEAPOT bends, fourth-order maps: FP64 only
     bool mix_fringe = false;       // mixed table entries carry ST_MIX_FRINGE (thin fringe spin kicks)
-    bool mix_ext = false;          // the lattice has TEAPOT bends or solenoids (the mixed kernels'
-                                   // extended instantiation)
+    bool mix_ext = false;          // the lattice has TEAPOT bends, solenoids or fourth-order maps (the
+                                   // mixed kernels' extended instantiation)
     bool has_ext = false;          // fourth-order slice maps, rectangular or TEAPOT bends or thin lenses present
     bool has_order4 = false;       // fourth-order slice maps present
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]

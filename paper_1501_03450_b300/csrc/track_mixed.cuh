@@ -655,6 +655,30 @@ __device__ __forceinline__ CNQ mixed_fringe(const MixElem& el, int type, const M
     return q;
 }
 
+// One multipole half step of the drift-kick-drift map: drift dl (compensated
+// length; 0 skips it), kick of k1, k2 over the compensated lengths k1l = k1 l,
+// k2hl = k2 l / 2, k2l = k2 l, drift dl2.  ips_ff, d, pp: 1/Ps and its
+// deviation at the current momenta (updated after the kick).
+__device__ __forceinline__ void mixed_mult_half(MState& z, const MConst& k, const FF& dl, const FF& dl2, const FF& k1l,
+                                                const FF& k2hl, const FF& k2l, FF& ips_ff, float& d, float& pp) {
+    if (dl.hi != 0.0f) drift_inc(z, k, dl, ips_ff, d);
+    const FF x2my2 = ff_add(ff_mul(z.X, z.X), ff_neg(ff_mul(z.Y, z.Y)));
+    const FF kx = ff_add(ff_mul(z.X, k1l), ff_mul(x2my2, k2hl));
+    const FF ky = ff_add(ff_mul(z.Y, k1l), ff_mul(ff_mul(z.X, z.Y), k2l));
+    z.Px = ff_add(z.Px, ff_neg(kx));
+    z.Py = ff_add(z.Py, ky);
+    ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
+    if (dl2.hi != 0.0f) drift_inc(z, k, dl2, ips_ff, d);
+}
+
+// H_qNL over len in increment form (Eq. (25)); d, pp at the current momenta
+__device__ __forceinline__ void mixed_quad_nonlinear(MState& z, const MConst& k, float len, const FF& lenff, float d,
+                                                     float pp) {
+    z.X = ff_add_f(z.X, len * z.Px.hi * d);
+    z.Y = ff_add_f(z.Y, len * z.Py.hi * d);
+    z.T = ff_add(z.T, ff_mul(lenff, ff_add_f(k.tau, -k.b0pt * (d - 0.5f * pp * k.invPf * k.invPf * k.invPf))));
+}
+
 // Track particle i for n_turns turns through the mixed-precision tables in
 // shared memory (table, seq, rho); state in the FP64 pair-SoA arrays.  If
 // spin_sum ([3][n_all]) is given, the spin after every turn is added to it.
@@ -689,9 +713,11 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
     v = sxy[i];
     double sx = v.x, sy = v.y, sz = szp[i];
 
-    MQuad mq;
+    MQuad mq, mq2;   // mq2: the second coefficient set of fourth-order matrix-kick slices
     mq.key_k = -1.0f;
     mq.key_s = 0.0f;
+    mq2.key_k = -1.0f;
+    mq2.key_s = 0.0f;
     MixLevels<K> lv;
     bool is_lost = false;
 
@@ -785,10 +811,23 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                   if (s > 0 && teapot) {
                     // TEAPOT slice (Sec. 3.6): curved drift, kick, curved drift; the
                     // momentum quantities of the slice edge for Omega (Py is constant)
-                    const MixCurvedDrift& cd = el.td[0];
-                    mixed_curved_drift(z, k, cd, h);
-                    mixed_teapot_kick(z, FF{el.ehl_ff.x, el.ehl_ff.y}, FF{el.ehlh_ff.x, el.ehlh_ff.y});
-                    mixed_curved_drift(z, k, cd, h);
+                    if (EXT && (el.type & ST_MIX_ORDER4)) {
+                        // fourth order: CD(x1 ds/2) K(x1 ds) CD((x1 + x0) ds/2) K(x0 ds) ... mirrored
+                        const FF ka{el.o4_k1_ff[0].x, el.o4_k1_ff[0].y}, kha{el.o4_k2h_ff[0].x, el.o4_k2h_ff[0].y};
+                        const FF kb{el.o4_k1_ff[1].x, el.o4_k1_ff[1].y}, khb{el.o4_k2h_ff[1].x, el.o4_k2h_ff[1].y};
+                        mixed_curved_drift(z, k, el.td[0], h);
+                        mixed_teapot_kick(z, ka, kha);
+                        mixed_curved_drift(z, k, el.td[1], h);
+                        mixed_teapot_kick(z, kb, khb);
+                        mixed_curved_drift(z, k, el.td[1], h);
+                        mixed_teapot_kick(z, ka, kha);
+                        mixed_curved_drift(z, k, el.td[0], h);
+                    } else {
+                        const MixCurvedDrift& cd = el.td[0];
+                        mixed_curved_drift(z, k, cd, h);
+                        mixed_teapot_kick(z, FF{el.ehl_ff.x, el.ehl_ff.y}, FF{el.ehlh_ff.x, el.ehlh_ff.y});
+                        mixed_curved_drift(z, k, cd, h);
+                    }
                     px = z.Px.hi;
                     ps2 = Pa2 - px * px;
                     ips = rsqrtf(ps2);
@@ -891,15 +930,52 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                     Aw = ff_mul(k.aP, k1ds);
                 } else {
                     const float absk = el.k2, hs = 0.5f * ds;
-                    if (mq.key_k != absk || mq.key_s != hs)
+                    // (fourth-order slices keep their own two coefficient sets)
+                    if (!(EXT && (el.type & ST_MIX_ORDER4)) && (mq.key_k != absk || mq.key_s != hs))
                         mquad_coeffs(mq, invP64, (double)el.k1ds_ff.x + (double)el.k1ds_ff.y,
                                      0.5 * ((double)el.ds_ff.x + (double)el.ds_ff.y), absk, hs);
                     Aw = ff_mul_f(ff_mul(ff_mul(k.aP, k1ds), dsff), k1 >= 0.0f ? 1.0f : -1.0f);
                 }
+                const bool o4 = EXT && (el.type & ST_MIX_ORDER4);
                 FF ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                 float ips = ips_ff.hi, Ps = (k.P2 - pp) * ips;
                 for (int s = 0; s <= N; ++s) {
-                    if (s > 0) {
+                    if (s > 0 && o4) {
+                        // fourth order (Sec. 3.3): Yoshida's S2(x1 ds) S2(x0 ds) S2(x1 ds) with
+                        // adjacent half steps merged: D K D' K0 D' K D or L N L' N0 L' N L
+                        const FF d1{el.o4_d_ff[0].x, el.o4_d_ff[0].y}, d2{el.o4_d_ff[1].x, el.o4_d_ff[1].y};
+                        if (is_mult) {
+                            const FF zero{0.0f, 0.0f};
+                            const FF k1a{el.o4_k1_ff[0].x, el.o4_k1_ff[0].y}, k1b{el.o4_k1_ff[1].x, el.o4_k1_ff[1].y};
+                            const FF k2ha{el.o4_k2h_ff[0].x, el.o4_k2h_ff[0].y};
+                            const FF k2hb{el.o4_k2h_ff[1].x, el.o4_k2h_ff[1].y};
+                            const FF k2a{el.o4_k2_ff[0].x, el.o4_k2_ff[0].y}, k2b{el.o4_k2_ff[1].x, el.o4_k2_ff[1].y};
+                            mixed_mult_half(z, k, d1, d2, k1a, k2ha, k2a, ips_ff, d, pp);
+                            mixed_mult_half(z, k, zero, d2, k1b, k2hb, k2b, ips_ff, d, pp);
+                            mixed_mult_half(z, k, zero, d1, k1a, k2ha, k2a, ips_ff, d, pp);
+                        } else {
+                            const float absk = el.k2, l1 = d1.hi, l2 = d2.hi;
+                            const double absk64 = (double)el.k1ds_ff.x + (double)el.k1ds_ff.y;
+                            if (mq.key_k != absk || mq.key_s != l1)
+                                mquad_coeffs(mq, invP64, absk64, (double)d1.hi + (double)d1.lo, absk, l1);
+                            if (mq2.key_k != absk || mq2.key_s != l2)
+                                mquad_coeffs(mq2, invP64, absk64, (double)d2.hi + (double)d2.lo, absk, l2);
+                            const FF sa{el.o4_s_ff[0].x, el.o4_s_ff[0].y}, sb{el.o4_s_ff[1].x, el.o4_s_ff[1].y};
+                            quad_linear_inc(z, k, mq, k1);
+                            inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
+                            mixed_quad_nonlinear(z, k, sa.hi, sa, d, pp);
+                            quad_linear_inc(z, k, mq2, k1);
+                            inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
+                            mixed_quad_nonlinear(z, k, sb.hi, sb, d, pp);
+                            quad_linear_inc(z, k, mq2, k1);
+                            inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
+                            mixed_quad_nonlinear(z, k, sa.hi, sa, d, pp);
+                            quad_linear_inc(z, k, mq, k1);
+                            ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
+                        }
+                        ips = ips_ff.hi;
+                        Ps = (k.P2 - pp) * ips;
+                    } else if (s > 0) {
                         if (is_mult) {
                             drift_inc(z, k, half, ips_ff, d);
                             // kick of H_m over ds, compensated (the sextupole kick is first

@@ -81,30 +81,6 @@ __device__ __forceinline__ void mixed_bend_step(MState& z, const MConst& k, cons
     PsM1 = PsfM1;
 }
 
-// One multipole half step of the drift-kick-drift map: drift dl (compensated
-// length; 0 skips it), kick of k1, k2 over the compensated lengths k1l = k1 l,
-// k2hl = k2 l / 2, k2l = k2 l, drift dl2.  ips_ff, d, pp: 1/Ps and its
-// deviation at the current momenta (updated after the kick).
-__device__ __forceinline__ void mixed_mult_half(MState& z, const MConst& k, const FF& dl, const FF& dl2, const FF& k1l,
-                                                const FF& k2hl, const FF& k2l, FF& ips_ff, float& d, float& pp) {
-    if (dl.hi != 0.0f) drift_inc(z, k, dl, ips_ff, d);
-    const FF x2my2 = ff_add(ff_mul(z.X, z.X), ff_neg(ff_mul(z.Y, z.Y)));
-    const FF kx = ff_add(ff_mul(z.X, k1l), ff_mul(x2my2, k2hl));
-    const FF ky = ff_add(ff_mul(z.Y, k1l), ff_mul(ff_mul(z.X, z.Y), k2l));
-    z.Px = ff_add(z.Px, ff_neg(kx));
-    z.Py = ff_add(z.Py, ky);
-    ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
-    if (dl2.hi != 0.0f) drift_inc(z, k, dl2, ips_ff, d);
-}
-
-// H_qNL over len in increment form (Eq. (25)); d, pp at the current momenta
-__device__ __forceinline__ void mixed_quad_nonlinear(MState& z, const MConst& k, float len, const FF& lenff, float d,
-                                                     float pp) {
-    z.X = ff_add_f(z.X, len * z.Px.hi * d);
-    z.Y = ff_add_f(z.Y, len * z.Py.hi * d);
-    z.T = ff_add(z.T, ff_mul(lenff, ff_add_f(k.tau, -k.b0pt * (d - 0.5f * pp * k.invPf * k.invPf * k.invPf))));
-}
-
 template <bool KICK, bool FR = false, bool EXT = false>
 __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restrict__ table,
                                                          const uint16_t* __restrict__ seq,
