@@ -202,6 +202,7 @@ int build_mixed_tables(LatticeImpl& L) {
             // (the host packs the sub-step lengths into a[2..5])
             m.type |= ST_MIX_ORDER4;
             L.mix_ext = true;
+            L.mix_o4 = true;
             for (int jj = 0; jj < 2; ++jj) {
                 const double dl = d.a[2 + jj], sl = d.a[4 + jj];
                 m.o4_d_ff[jj] = split(dl);

@@ -161,6 +161,7 @@ struct LatticeImpl {
     bool mix_fringe = false;       // mixed table entries carry ST_MIX_FRINGE (thin fringe spin kicks)
     bool mix_ext = false;          // the lattice has TEAPOT bends, solenoids or fourth-order maps (the
                                    // mixed kernels' extended instantiation)
+    bool mix_o4 = false;           // ... fourth-order maps (the extended instantiation with them)
     bool has_ext = false;          // fourth-order slice maps, rectangular or TEAPOT bends or thin lenses present
     bool has_order4 = false;       // fourth-order slice maps present
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]

@@ -684,8 +684,10 @@ __device__ __forceinline__ void mixed_quad_nonlinear(MState& z, const MConst& k,
 // spin_sum ([3][n_all]) is given, the spin after every turn is added to it.
 // FR: the lattice's table entries may carry ST_MIX_FRINGE (a separate
 // instantiation, so that lattices without fringe kicks run the plain loop).
-// EXT: the lattice may hold TEAPOT bends (an instantiation of its own too).
-template <int K, bool SPIN = true, bool FR = false, bool EXT = false>
+// EXT: the lattice may hold TEAPOT bends and solenoids, O4 (with EXT):
+// fourth-order slices (instantiations of their own too, so that each keeps
+// the register budget of what it runs).
+template <int K, bool SPIN = true, bool FR = false, bool EXT = false, bool O4 = false>
 __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__ table,
                                                      const uint16_t* __restrict__ seq,
                                                      const float2* __restrict__ rho, int n_seq, const RefConst& ref,
@@ -811,7 +813,7 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                   if (s > 0 && teapot) {
                     // TEAPOT slice (Sec. 3.6): curved drift, kick, curved drift; the
                     // momentum quantities of the slice edge for Omega (Py is constant)
-                    if (EXT && (el.type & ST_MIX_ORDER4)) {
+                    if (O4 && (el.type & ST_MIX_ORDER4)) {
                         // fourth order: CD(x1 ds/2) K(x1 ds) CD((x1 + x0) ds/2) K(x0 ds) ... mirrored
                         const FF ka{el.o4_k1_ff[0].x, el.o4_k1_ff[0].y}, kha{el.o4_k2h_ff[0].x, el.o4_k2h_ff[0].y};
                         const FF kb{el.o4_k1_ff[1].x, el.o4_k1_ff[1].y}, khb{el.o4_k2h_ff[1].x, el.o4_k2h_ff[1].y};
@@ -931,12 +933,12 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 } else {
                     const float absk = el.k2, hs = 0.5f * ds;
                     // (fourth-order slices keep their own two coefficient sets)
-                    if (!(EXT && (el.type & ST_MIX_ORDER4)) && (mq.key_k != absk || mq.key_s != hs))
+                    if (!(O4 && (el.type & ST_MIX_ORDER4)) && (mq.key_k != absk || mq.key_s != hs))
                         mquad_coeffs(mq, invP64, (double)el.k1ds_ff.x + (double)el.k1ds_ff.y,
                                      0.5 * ((double)el.ds_ff.x + (double)el.ds_ff.y), absk, hs);
                     Aw = ff_mul_f(ff_mul(ff_mul(k.aP, k1ds), dsff), k1 >= 0.0f ? 1.0f : -1.0f);
                 }
-                const bool o4 = EXT && (el.type & ST_MIX_ORDER4);
+                const bool o4 = O4 && (el.type & ST_MIX_ORDER4);
                 FF ips_ff = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);
                 float ips = ips_ff.hi, Ps = (k.P2 - pp) * ips;
                 for (int s = 0; s <= N; ++s) {
