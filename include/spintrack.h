@@ -74,7 +74,8 @@ extern "C" {
                            (Eq. (dipolefringe), symplectic form) at both faces, the
                            exact body map (Eq. (rbend)) in n_slices slices, the offsets
                            of Eqs. (Xoffset), (Toffset); fringe = 1 adds the spin kicks
-                           of Eq. (skfringeRB).  FP64 only.                           */
+                           of Eq. (skfringeRB).  FP64 and mixed-precision contexts and
+                           batches (the mixed kernels track it in FP64).               */
 
 #define ST_TEAPOT   7   /* sector bend (h = angle/L, field ratio eta as ST_SBEND) integrated
                            by the TEAPOT drift-kick split, Sec. 3.6, Eqs. (DKsplit),
@@ -145,9 +146,8 @@ typedef struct {
                         * + at the entrance, - at the exit, with b_1/(B rho) = eta h,
                         * b_2/(B rho) = k1, b_3/(B rho) = k2/2; orbit unchanged.  0: none.
                         * Solenoids always carry their Sec. 4.4 fringe kicks; drifts and
-                        * snakes must have 0 (ST_EINVAL otherwise).  The mixed-precision
-                        * tracker applies them on ST_MULT, ST_QUAD_MK, ST_SBEND and
-                        * ST_TEAPOT; an ST_RBEND is FP64 only anyway. */
+                        * snakes must have 0 (ST_EINVAL otherwise).  Both trackers apply
+                        * them (the mixed one on an ST_RBEND in its FP64 maps). */
     int32_t split_order; /* orbit slice map of an ST_MULT, ST_QUAD_MK or ST_TEAPOT: 0 or
                           * 2 = the symmetric second-order split of Eq. (27) (drift-kick-
                           * drift, matrix-kick, TEAPOT); 4 = Yoshida's fourth-order composition
@@ -177,8 +177,7 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
 int st_lattice_destroy(st_lattice* lat);
 
 /* Create a tracking context for n_particles >= 1 particles on the current
- * device.  precision is ST_FP64 or ST_MIXED (lattices with rectangular bends:
- * ST_FP64 only, ST_EINVAL otherwise).  cuda_stream is a cudaStream_t
+ * device.  precision is ST_FP64 or ST_MIXED (every element kind runs in both).  cuda_stream is a cudaStream_t
  * (e.g. torch.cuda.current_stream().cuda_stream) or NULL for a stream owned by
  * the context.  Allocates the device state (orbit as (X,Px), (Y,Py), (T,Pt)
  * double2 arrays, spin, lost flags) and a staging buffer.  The lattice must
@@ -265,8 +264,7 @@ int st_ctx_set_launch(st_ctx* ctx, int32_t block_threads, int32_t turns_per_laun
 typedef struct st_batch st_batch;
 
 /* n_jobs >= 1 jobs: lattices[j] (must outlive the batch) and n_particles[j]
- * (1..2^30).  precision ST_FP64 or ST_MIXED (a mixed batch takes the lattices
- * an ST_MIXED context takes); cuda_stream as st_ctx_create.
+ * (1..2^30).  precision ST_FP64 or ST_MIXED; cuda_stream as st_ctx_create.
  * Errors: ST_EINVAL, ST_ENOMEM, ST_ECUDA. */
 int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particles, int32_t n_jobs,
                     int32_t precision, void* cuda_stream, st_batch** out);

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(128, EXT ? (MINB > 2 ? MINB - 1 : MINB) : MINB
     });
 }
 
-template <int K, int MINB, bool FR = false, bool EXT = false, bool O4 = false>
+template <int K, int MINB, bool FR = false, bool EXT = false, bool O4 = false, bool RB = false>
 __global__ void __launch_bounds__(128, MINB) track_batch_mixed_kernel(const JobDesc* __restrict__ jobs,
                                                                        const WorkItem* __restrict__ items,
                                                                        int n_items, int32_t* queue, int n_turns,
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(128, MINB) track_batch_mixed_kernel(const JobD
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
     batch_loop(jobs, items, n_items, queue, status, smem, &bar, [&](const JobDesc& J, int64_t i) {
-        mixed_track_particle<K, true, FR, EXT, O4>((const MixElem*)smem, (const uint16_t*)(smem + J.seq_offset),
+        mixed_track_particle<K, true, FR, EXT, O4, RB>((const MixElem*)smem, (const uint16_t*)(smem + J.seq_offset),
                                 (const float2*)(smem + J.rho_offset), J.n_seq, J.ref, J.xpx, J.ypy, J.tpt, J.sxy,
                                 J.sz, J.lost, i, n_turns, status);
     });
@@ -138,8 +138,9 @@ typedef void (*BatchKernel)(const JobDesc*, const WorkItem*, int, int32_t*, int,
 // fr: the mixed instantiation that decodes fringe-kick table entries
 // mext: the mixed instantiation with TEAPOT bends and solenoids (and fringe
 // entries) compiled in, at the larger register budget for both variants;
-// mo4: the same with fourth-order slices
-static BatchKernel batch_kernel(int precision, int K, int variant, bool ext, bool fr, bool mext, bool mo4) {
+// mo4: the same with fourth-order slices; mrb: with rectangular bends too
+static BatchKernel batch_kernel(int precision, int K, int variant, bool ext, bool fr, bool mext, bool mo4,
+                                bool mrb) {
 #define ST_SEL(KK)                                                                                            \
     case KK:                                                                                                  \
         if (precision == ST_FP64) {                                                                           \
@@ -147,6 +148,7 @@ static BatchKernel batch_kernel(int precision, int K, int variant, bool ext, boo
                 return variant ? track_batch_fp64_kernel<KK, 3, true> : track_batch_fp64_kernel<KK, 2, true>; \
             return variant ? track_batch_fp64_kernel<KK, 3, false> : track_batch_fp64_kernel<KK, 2, false>;   \
         }                                                                                                     \
+        if (mrb) return track_batch_mixed_kernel<KK, 2, true, true, true, true>;                        \
         if (mo4) return track_batch_mixed_kernel<KK, 2, true, true, true>;                              \
         if (mext) return track_batch_mixed_kernel<KK, 2, true, true>;                                   \
         if (fr) return variant ? track_batch_mixed_kernel<KK, 3, true> : track_batch_mixed_kernel<KK, 2, true>; \
@@ -183,6 +185,7 @@ struct st_batch {
     bool mix_fringe = false;   // some job's mixed table has fringe-kick entries
     bool mix_ext = false;      // some job's lattice has TEAPOT bends, solenoids or fourth-order slices
     bool mix_o4 = false;       // some job's lattice has fourth-order slices
+    bool mix_rb = false;       // some job's lattice has rectangular bends
     std::vector<const st_lattice*> lats;
     std::vector<int64_t> n, offset;
     std::vector<double> cost_per_particle;
@@ -302,7 +305,7 @@ static int build_jobs(st_batch* b) {
 // Kernel and grid for the current launch shape (no stream work; safe before a capture).
 static int prepare_launch(st_batch* b, int K, BatchKernel* kern_out, int* grid_out) {
     BatchKernel kern =
-        batch_kernel(b->precision, K, b->variant, b->has_ext, b->mix_fringe, b->mix_ext, b->mix_o4);
+        batch_kernel(b->precision, K, b->variant, b->has_ext, b->mix_fringe, b->mix_ext, b->mix_o4, b->mix_rb);
     cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "batch: cudaFuncSetAttribute");
     int dev = 0, sms = 0, per_sm = 0;
@@ -356,12 +359,6 @@ int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particle
         set_error("st_batch_create: precision must be ST_FP64 or ST_MIXED");
         return ST_EINVAL;
     }
-    if (precision == ST_MIXED)
-        for (int j = 0; j < n_jobs; ++j)
-            if (lattices[j] && lattices[j]->impl.fp64_only) {
-                set_error("st_batch_create: rectangular bends and fourth-order maps are tracked by FP64 batches only");
-                return ST_EINVAL;
-            }
     st_batch* b = new (std::nothrow) st_batch();
     if (!b) {
         set_error("st_batch_create: host allocation failed");
@@ -381,6 +378,7 @@ int st_batch_create(const st_lattice* const* lattices, const int64_t* n_particle
         if (lattices[j]->impl.mix_fringe) b->mix_fringe = true;
         if (lattices[j]->impl.mix_ext) b->mix_ext = true;
         if (lattices[j]->impl.mix_o4) b->mix_o4 = true;
+        if (lattices[j]->impl.mix_rb) b->mix_rb = true;
         b->n.push_back(n_particles[j]);
         b->offset.push_back(total);
         total += n_particles[j];

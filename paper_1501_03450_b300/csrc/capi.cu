@@ -215,7 +215,6 @@ int st_lattice_create(const st_element* elems, int32_t n, const st_reference* re
         seq[i] = (uint16_t)idx;
         if ((d.flags & ST_ELEM_ORDER4) || d.type == ST_RBEND || d.type == ST_TEAPOT || d.type == ST_THIN_MULT)
             L.has_ext = true;
-        if (d.type == ST_RBEND) L.fp64_only = true;   // rectangular bends: FP64 trackers only
         if (d.flags & ST_ELEM_ORDER4) L.has_order4 = true;
         if (is_spin_type(d.type)) {
             max_slices = std::max(max_slices, (int)d.n_slices);
@@ -312,10 +311,6 @@ int st_ctx_create(const st_lattice* lat, int64_t n_particles, int32_t precision,
     }
     if (n_particles > ((int64_t)1 << 31) - 1) {   // the kernels index particles with int
         set_error("st_ctx_create: at most 2^31 - 1 particles");
-        return ST_EINVAL;
-    }
-    if (precision == ST_MIXED && lat->impl.fp64_only) {
-        set_error("st_ctx_create: solenoids and fringe spin kicks are tracked by the FP64 tracker only");
         return ST_EINVAL;
     }
     st_ctx* c = new (std::nothrow) st_ctx();

@@ -191,6 +191,14 @@ int build_mixed_tables(LatticeImpl& L) {
             }
             break;
         }
+        case ST_RBEND:
+            // Sec. 3.2: tracked in FP64 inside the mixed kernels (in the magnet's
+            // straight frame the on-axis particle's precession rate changes along
+            // the body, so the reference-and-deviation split does not apply)
+            m.d64 = d;
+            L.mix_ext = true;
+            L.mix_rb = true;
+            break;
         case ST_SNAKE:
             for (int c = 0; c < 4; ++c) rq[c] = d.a[c];
             break;

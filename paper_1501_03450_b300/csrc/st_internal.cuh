@@ -128,6 +128,9 @@ struct __align__(16) MixElem {
     float2 o4_d_ff[2], o4_s_ff[2], o4_k1_ff[2], o4_k2h_ff[2], o4_k2_ff[2];
     float2 rq[4];                     // reference rotation over the element (bends, snakes), (hi, lo) per component
     MixWeight w[6];
+    // rectangular bend (Sec. 3.2): the FP64 descriptor, tracked in FP64 inside the
+    // mixed kernels
+    DevElem d64;
 };
 static_assert(sizeof(MixElem) % 16 == 0, "MixElem must be a multiple of 16 bytes");
 // MixElem::type bit of an element with thin fringe spin kicks at both ends
@@ -157,11 +160,11 @@ struct LatticeImpl {
     int32_t n_unique;
     int32_t max_slices;
     int32_t min_spin_slices_pow2;  // largest k with every spin element divisible by 2^k
-    bool fp64_only = false;        // solenoids, rectangular or TEAPOT bends, fourth-order maps: FP64 only
     bool mix_fringe = false;       // mixed table entries carry ST_MIX_FRINGE (thin fringe spin kicks)
     bool mix_ext = false;          // the lattice has TEAPOT bends, solenoids or fourth-order maps (the
                                    // mixed kernels' extended instantiation)
     bool mix_o4 = false;           // ... fourth-order maps (the extended instantiation with them)
+    bool mix_rb = false;           // ... rectangular bends (the instantiation with their FP64 island)
     bool has_ext = false;          // fourth-order slice maps, rectangular or TEAPOT bends or thin lenses present
     bool has_order4 = false;       // fourth-order slice maps present
     // device copy: [DevElem table (n_unique)] [uint16 sequence (n_elements), padded]

@@ -7,7 +7,7 @@ namespace st {
 
 // 2 blocks of 128 per SM (up to 255 registers): 13% faster than 3 blocks with a
 // 168-register cap on the RHIC-like ring (fewer warps, but no rematerialisation).
-template <int K, bool SPIN = true, bool FR = false, bool EXT = false, bool O4 = false>
+template <int K, bool SPIN = true, bool FR = false, bool EXT = false, bool O4 = false, bool RB = false>
 __global__ void __launch_bounds__(128, 2) track_mixed_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
                                                             uint32_t seq_offset, uint32_t rho_offset, int n_seq,
                                                             RefConst ref, double2* __restrict__ xpx,
@@ -32,13 +32,13 @@ __global__ void __launch_bounds__(128, 2) track_mixed_kernel(const void* __restr
         const int64_t i = wi * 32 + lane;
         if (i >= n || lost[i]) continue;
 
-        mixed_track_particle<K, SPIN, FR, EXT, O4>(table, seq, rho, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i,
-                                                   n_turns, status, spin_sum, n);
+        mixed_track_particle<K, SPIN, FR, EXT, O4, RB>(table, seq, rho, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost,
+                                                       i, n_turns, status, spin_sum, n);
     }
 }
 
 // The midpoint spin schemes (KICK: split-kick placement), a separate kernel.
-template <bool KICK, bool FR, bool EXT>
+template <bool KICK, bool FR, bool EXT, bool RB = false>
 __global__ void __launch_bounds__(128, 2) track_mixed_mid_kernel(const void* __restrict__ blob, uint32_t blob_bytes,
                                                                 uint32_t seq_offset, uint32_t rho_offset, int n_seq,
                                                                 RefConst ref, double2* __restrict__ xpx,
@@ -61,12 +61,12 @@ __global__ void __launch_bounds__(128, 2) track_mixed_mid_kernel(const void* __r
     for (int64_t wi = w_begin + (threadIdx.x >> 5); wi < w_end; wi += wpb) {
         const int64_t i = wi * 32 + lane;
         if (i >= n || lost[i]) continue;
-        mixed_track_particle_mid<KICK, FR, EXT>(table, seq, rho, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i,
-                                                n_turns, status, spin_sum, n);
+        mixed_track_particle_mid<KICK, FR, EXT, RB>(table, seq, rho, n_seq, ref, xpx, ypy, tpt, sxy, szp, lost, i,
+                                                    n_turns, status, spin_sum, n);
     }
 }
 
-template <bool KICK, bool FR, bool EXT>
+template <bool KICK, bool FR, bool EXT, bool RB = false>
 static int launch_mixed_mid_(st_ctx* ctx, int n_turns, double* spin_sum) {
     const LatticeImpl& L = ctx->lat->impl;
     const int threads = ctx->block_threads;
@@ -75,7 +75,7 @@ static int launch_mixed_mid_(st_ctx* ctx, int n_turns, double* spin_sum) {
     int rc0 = once_per_device(
         attr_set,
         [] {
-            return cudaFuncSetAttribute(track_mixed_mid_kernel<KICK, FR, EXT>,
+            return cudaFuncSetAttribute(track_mixed_mid_kernel<KICK, FR, EXT, RB>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         },
         "cudaFuncSetAttribute(mixed midpoint tracker)");
@@ -84,7 +84,7 @@ static int launch_mixed_mid_(st_ctx* ctx, int n_turns, double* spin_sum) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_mixed_mid_kernel<KICK, FR, EXT>, threads,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_mixed_mid_kernel<KICK, FR, EXT, RB>, threads,
                                                           smem);
     if (e != cudaSuccess) return cuda_fail(e, "mixed midpoint tracker occupancy query");
     if (per_sm < 1) {
@@ -98,7 +98,7 @@ static int launch_mixed_mid_(st_ctx* ctx, int n_turns, double* spin_sum) {
     const int tpl = ctx->turns_per_launch;
     for (int t = 0; t < n_turns; t += tpl) {
         int nt = n_turns - t < tpl ? n_turns - t : tpl;
-        track_mixed_mid_kernel<KICK, FR, EXT><<<(unsigned)grid, threads, smem, ctx->stream>>>(
+        track_mixed_mid_kernel<KICK, FR, EXT, RB><<<(unsigned)grid, threads, smem, ctx->stream>>>(
             L.d_mix, (uint32_t)L.mix_bytes, (uint32_t)L.mix_seq_offset, (uint32_t)L.mix_rho_offset, L.n_elements,
             L.ref, ctx->xpx, ctx->ypy, ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status,
             spin_sum);
@@ -113,12 +113,13 @@ static int launch_mixed_mid_(st_ctx* ctx, int n_turns, double* spin_sum) {
 template <bool KICK>
 static int launch_mixed_mid(st_ctx* ctx, int n_turns, double* spin_sum) {
     const LatticeImpl& L = ctx->lat->impl;
+    if (L.mix_rb) return launch_mixed_mid_<KICK, true, true, true>(ctx, n_turns, spin_sum);
     if (L.mix_ext) return launch_mixed_mid_<KICK, true, true>(ctx, n_turns, spin_sum);
     return L.mix_fringe ? launch_mixed_mid_<KICK, true, false>(ctx, n_turns, spin_sum)
                         : launch_mixed_mid_<KICK, false, false>(ctx, n_turns, spin_sum);
 }
 
-template <int K, bool SPIN, bool FR, bool EXT, bool O4 = false>
+template <int K, bool SPIN, bool FR, bool EXT, bool O4 = false, bool RB = false>
 static int launch_mixed_k_(st_ctx* ctx, int n_turns, double* spin_sum) {
     const LatticeImpl& L = ctx->lat->impl;
     const int threads = ctx->block_threads;
@@ -127,7 +128,7 @@ static int launch_mixed_k_(st_ctx* ctx, int n_turns, double* spin_sum) {
     int rc0 = once_per_device(
         attr_set,
         [] {
-            return cudaFuncSetAttribute(track_mixed_kernel<K, SPIN, FR, EXT, O4>,
+            return cudaFuncSetAttribute(track_mixed_kernel<K, SPIN, FR, EXT, O4, RB>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         },
         "cudaFuncSetAttribute(mixed tracker)");
@@ -136,7 +137,7 @@ static int launch_mixed_k_(st_ctx* ctx, int n_turns, double* spin_sum) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_mixed_kernel<K, SPIN, FR, EXT, O4>, threads,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_mixed_kernel<K, SPIN, FR, EXT, O4, RB>, threads,
                                                           smem);
     if (e != cudaSuccess) return cuda_fail(e, "mixed tracker occupancy query");
     if (per_sm < 1) {
@@ -149,7 +150,7 @@ static int launch_mixed_k_(st_ctx* ctx, int n_turns, double* spin_sum) {
     const int tpl = ctx->turns_per_launch;
     for (int t = 0; t < n_turns; t += tpl) {
         int nt = n_turns - t < tpl ? n_turns - t : tpl;
-        track_mixed_kernel<K, SPIN, FR, EXT, O4><<<(unsigned)grid, threads, smem, ctx->stream>>>(
+        track_mixed_kernel<K, SPIN, FR, EXT, O4, RB><<<(unsigned)grid, threads, smem, ctx->stream>>>(
             L.d_mix, (uint32_t)L.mix_bytes, (uint32_t)L.mix_seq_offset, (uint32_t)L.mix_rho_offset, L.n_elements,
             L.ref, ctx->xpx, ctx->ypy, ctx->tpt, ctx->sxy, ctx->sz, ctx->lost, (int)ctx->n, nt, ctx->status,
             spin_sum);
@@ -161,10 +162,12 @@ static int launch_mixed_k_(st_ctx* ctx, int n_turns, double* spin_sum) {
 
 // The instantiation that decodes fringe-kick entries only for lattices with
 // them; lattices with TEAPOT bends or solenoids run the extended one (fringe
-// entries too), lattices with fourth-order slices the extended one with those.
+// entries too), lattices with fourth-order slices the extended one with those,
+// lattices with rectangular bends the one with everything.
 template <int K, bool SPIN = true>
 static int launch_mixed_k(st_ctx* ctx, int n_turns, double* spin_sum = nullptr) {
     const LatticeImpl& L = ctx->lat->impl;
+    if (L.mix_rb) return launch_mixed_k_<K, SPIN, true, true, true, true>(ctx, n_turns, spin_sum);
     if (L.mix_o4) return launch_mixed_k_<K, SPIN, true, true, true>(ctx, n_turns, spin_sum);
     if (L.mix_ext) return launch_mixed_k_<K, SPIN, true, true>(ctx, n_turns, spin_sum);
     return L.mix_fringe ? launch_mixed_k_<K, SPIN, true, false>(ctx, n_turns, spin_sum)

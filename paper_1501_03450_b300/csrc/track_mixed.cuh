@@ -32,6 +32,7 @@
 
 #include "device_common.cuh"
 #include "ff.cuh"
+#include "track_mid.cuh"   // the FP64 rectangular-bend maps (tracked in FP64 in the mixed kernels)
 
 namespace st {
 
@@ -679,15 +680,130 @@ __device__ __forceinline__ void mixed_quad_nonlinear(MState& z, const MConst& k,
     z.T = ff_add(z.T, ff_mul(lenff, ff_add_f(k.tau, -k.b0pt * (d - 0.5f * pp * k.invPf * k.invPf * k.invPf))));
 }
 
+// ---- rectangular bend (Sec. 3.2): an FP64 island ------------------------------
+// In the magnet's straight frame the on-axis particle's Px runs from
+// sin(phi_in) to sin(phi_out), so its precession rate (1 + G gamma) b/Ps
+// changes along the body and the levels of the Romberg table do not share one
+// reference rotation: the element is tracked in FP64 with the FP64 tracker's
+// maps (entrance rotation, fringe map, body slices, exit fringe, offset, exit
+// rotation, time offset; Omega at the slice edges and the Romberg table, or
+// Omega at the slice middles for the midpoint schemes), from the compensated
+// state converted exactly to FP64, and the element's normalised rotation is
+// composed into the compensated turn quaternion.  Returns false if the
+// particle is lost (state unchanged then).
+__device__ __forceinline__ void fq_premul_quat64(FQ& qt, const Quat& r) {
+    float2 rq[4];
+    const double c[4] = {r.w, r.x, r.y, r.z};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const FF f = ff_make(c[i]);
+        rq[i] = make_float2(f.hi, f.lo);
+    }
+    fq_premul_ref(qt, rq);
+}
+
+__device__ __forceinline__ void pconst_fp64(const RefConst& ref, double Pt, PConst& pc) {
+    pc.Pt = Pt;
+    pc.P2 = 1.0 + 2.0 * Pt * ref.inv_beta0 + Pt * Pt;
+    pc.invP = rsqrt(pc.P2);
+    pc.P = pc.P2 * pc.invP;
+    pc.invP2 = pc.invP * pc.invP;
+    pc.b0pt = ref.inv_beta0 + Pt;
+    const double gamma = ref.gamma0 * (1.0 + ref.beta0 * Pt);
+    pc.a = 1.0 + ref.G * gamma;
+    pc.c = ref.G * (gamma - 1.0);
+    pc.cP2 = pc.c * pc.invP2;
+    pc.hP3 = 0.5 * pc.invP * pc.invP2;
+}
+
+struct RbendOut {
+    MState z;
+    Quat r;   // the element's normalised rotation (identity without SPIN)
+    bool ok;
+};
+
+// MID: the midpoint placement (Omega at the slice middles, the body in
+// half-slices; both midpoint schemes place it so for exact maps); otherwise
+// Romberg order K.  Not inlined: the FP64 state and level products stay out
+// of the mixed kernel's register budget.
+template <int K, bool SPIN, bool MID>
+__device__ __noinline__ RbendOut mixed_rbend_fp64(MState z, RefConst ref, double Pt, const DevElem* elp) {
+    const DevElem& el = *elp;
+    RbendOut out;
+    out.z = z;
+    out.r = Quat{1.0, 0.0, 0.0, 0.0};
+    out.ok = false;
+    Particle p{ff_to_double(z.X), ff_to_double(z.Px), ff_to_double(z.Y), ff_to_double(z.Py), ff_to_double(z.T)};
+    PConst pc;
+    pconst_fp64(ref, Pt, pc);
+    const double onepG = 1.0 + ref.G;
+    const int N = el.n_slices;
+    const double ds = el.ds, b = el.a[0];
+    Quat q_in{1.0, 0.0, 0.0, 0.0}, q_x{1.0, 0.0, 0.0, 0.0}, qe{1.0, 0.0, 0.0, 0.0};
+    bool ok = rbend_rotation(p, pc, el.a[1]);
+    if constexpr (SPIN) {
+        q_in = quat_about_y(el.a[1]);
+        if (el.flags & ST_ELEM_FRINGE) q_in = qmul(rbend_fringe_quat(pc, onepG, p, b), q_in);
+    }
+    ok = ok && rbend_fringe_orbit(p, pc, b);
+    double ox, oy, os;
+    if constexpr (MID) {
+        const double hd = 0.5 * ds;
+        for (int s = 0; s < N; ++s) {
+            ok = ok && rbend_body(p, pc, b, hd);
+            if constexpr (SPIN) {
+                ok = ok && mid_omega(el, ST_RBEND, p, pc, ox, oy, os);
+                if (ok) qe = qmul(quat_from_rotvec(ds * ox, ds * oy, ds * os), qe);
+            }
+            ok = ok && rbend_body(p, pc, b, hd);
+        }
+    } else {
+        LevelProducts<K> lv;
+        if constexpr (SPIN) {
+            const double pp = p.Px * p.Px + p.Py * p.Py;
+            const double ips = rsqrt(pc.P2 - pp);
+            precession(p, pc, 0.0, b, 0.0, ips, (pc.P2 - pp) * ips, ox, oy, os);
+            lv.add_edge(0, N, ds, ox, oy, os);
+        }
+        for (int s = 1; s <= N; ++s) {
+            ok = ok && rbend_body(p, pc, b, ds);
+            if constexpr (SPIN) {
+                const double pp = p.Px * p.Px + p.Py * p.Py;
+                const double ips = rsqrt(pc.P2 - pp);
+                precession(p, pc, 0.0, b, 0.0, ips, (pc.P2 - pp) * ips, ox, oy, os);
+                lv.add_edge(s, N, ds, ox, oy, os);
+            }
+        }
+        if constexpr (SPIN) qe = lv.romberg();
+    }
+    if constexpr (SPIN) {
+        if (el.flags & ST_ELEM_FRINGE) q_x = rbend_fringe_quat(pc, onepG, p, -b);
+    }
+    ok = ok && rbend_fringe_orbit(p, pc, -b);
+    p.X -= el.a[3];
+    ok = ok && rbend_rotation(p, pc, el.a[2]);
+    if constexpr (SPIN) q_x = qmul(quat_about_y(el.a[2]), q_x);
+    p.T += el.a[4] * ref.inv_beta0;
+    if (!ok || !isfinite(p.X + p.Px + p.Y + p.Py + p.T + qe.w + qe.x + qe.y + qe.z)) return out;
+    if constexpr (SPIN) out.r = qnormalize(qmul(q_x, qmul(qe, q_in)));
+    out.z.X = ff_make(p.X);
+    out.z.Px = ff_make(p.Px);
+    out.z.Y = ff_make(p.Y);
+    out.z.Py = ff_make(p.Py);
+    out.z.T = ff_make(p.T);
+    out.ok = true;
+    return out;
+}
+
 // Track particle i for n_turns turns through the mixed-precision tables in
 // shared memory (table, seq, rho); state in the FP64 pair-SoA arrays.  If
 // spin_sum ([3][n_all]) is given, the spin after every turn is added to it.
 // FR: the lattice's table entries may carry ST_MIX_FRINGE (a separate
 // instantiation, so that lattices without fringe kicks run the plain loop).
 // EXT: the lattice may hold TEAPOT bends and solenoids, O4 (with EXT):
-// fourth-order slices (instantiations of their own too, so that each keeps
-// the register budget of what it runs).
-template <int K, bool SPIN = true, bool FR = false, bool EXT = false, bool O4 = false>
+// fourth-order slices, RB (with both): rectangular bends (instantiations of
+// their own too, so that each keeps the register budget of what it runs).
+template <int K, bool SPIN = true, bool FR = false, bool EXT = false, bool O4 = false, bool RB = false>
 __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__ table,
                                                      const uint16_t* __restrict__ seq,
                                                      const float2* __restrict__ rho, int n_seq, const RefConst& ref,
@@ -741,6 +857,18 @@ __device__ __forceinline__ void mixed_track_particle(const MixElem* __restrict__
                 continue;
             }
             const MState z0 = z;
+            if constexpr (RB) {
+                if (type == ST_RBEND) {
+                    const RbendOut o = mixed_rbend_fp64<K, SPIN, false>(z, ref, Pt, &el.d64);
+                    if (!o.ok) {
+                        is_lost = true;
+                        break;
+                    }
+                    z = o.z;
+                    if constexpr (SPIN) fq_premul_quat64(qt, o.r);
+                    continue;
+                }
+            }
             float d, pp;
             if (type == ST_DRIFT) {
                 const FF ips = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);

@@ -81,7 +81,7 @@ __device__ __forceinline__ void mixed_bend_step(MState& z, const MConst& k, cons
     PsM1 = PsfM1;
 }
 
-template <bool KICK, bool FR = false, bool EXT = false>
+template <bool KICK, bool FR = false, bool EXT = false, bool RB = false>
 __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restrict__ table,
                                                          const uint16_t* __restrict__ seq,
                                                          const float2* __restrict__ rho, int n_seq,
@@ -100,9 +100,10 @@ __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restri
     z.Py = ff_make(v.y);
     v = tpt[i];
     z.T = ff_make(v.x);
+    const double Pt = v.y;
     MConst k;
     double invP64;
-    mixed_particle_consts(ref, v.y, k, invP64);
+    mixed_particle_consts(ref, Pt, k, invP64);
     v = sxy[i];
     double sx = v.x, sy = v.y, sz = szp[i];
     MQuad mq;
@@ -129,6 +130,18 @@ __device__ __forceinline__ void mixed_track_particle_mid(const MixElem* __restri
                 continue;
             }
             const MState z0 = z;
+            if constexpr (RB) {
+                if (type == ST_RBEND) {   // in FP64, the body in half-slices (an exact map)
+                    const RbendOut o = mixed_rbend_fp64<0, true, true>(z, ref, Pt, &el.d64);
+                    if (!o.ok) {
+                        is_lost = true;
+                        break;
+                    }
+                    z = o.z;
+                    fq_premul_quat64(qt, o.r);
+                    continue;
+                }
+            }
             float d, pp;
             if (type == ST_DRIFT) {
                 const FF ips = inv_ps(k, z.Px.hi, z.Py.hi, d, pp);

@@ -4,8 +4,9 @@ orbit maps, exact body map, offsets; Sec. 4.5: fringe spin kicks of Eq.
 on the same seeded inputs, every coordinate and spin component at 1e-11, for
 single magnets at every Romberg order (symmetric and asymmetric faces, field
 errors, with and without fringe kicks), a ring of rectangular bends, the
-reference particle's closed form, lost particles, batched jobs, validation and
-the mixed tracker's refusal."""
+reference particle's closed form, lost particles, batched jobs and
+validation; and the mixed-precision tracker, which tracks rectangular bends in
+FP64 inside its kernels, against the same oracle."""
 import math
 
 import numpy as np
@@ -104,7 +105,7 @@ def test_batched_jobs_with_rectangular_bends():
     b.close()
 
 
-def test_rbend_validation_and_mixed_rejection():
+def test_rbend_validation():
     for el in (W.element("rbend", L=2.0, n_slices=4, angle=0.0),
                W.element("rbend", L=2.0, n_slices=4, angle=0.1, eta=0.0),
                W.element("rbend", L=2.0, n_slices=4, angle=0.1, e1=1.6)):
@@ -112,7 +113,103 @@ def test_rbend_validation_and_mixed_rejection():
             st.Lattice(W.single_element_ring(el, 45.5))
     ring = W.with_spin_order(W.rbend_ring(45.5), 2)
     lat = st.Lattice(ring)
-    with pytest.raises(st.SpinTrackError):
-        st.Tracker(lat, 64, precision="mixed")
+    st.Tracker(lat, 64, precision="mixed").close()
     st.Tracker(lat, 64).close()
     lat.close()
+
+
+# ---- the mixed-precision tracker (rectangular bends in FP64 inside it) -------
+
+def spin_err(Sa, Sb):
+    d = np.linalg.norm(Sa - Sb, axis=0)
+    return float(d.mean()), float(d.max())
+
+
+@pytest.mark.parametrize("kw", MAGNETS, ids=["symmetric", "asymmetric_kicks", "field_error"])
+@pytest.mark.parametrize("K", [0, 2, st.ST_SPIN_MID_HALF, st.ST_SPIN_MID_KICK])
+def test_mixed_single_rectangular_bend(kw, K):
+    """A single magnet in the mixed tracker: its maps run in FP64, so only the
+    conversions at the element's ends and the compensated turn quaternion
+    separate it from the oracle (10 passes: spin and orbit within 1e-12)."""
+    gg = 45.5
+    el = W.element("rbend", L=3.0, n_slices=8, angle=0.06, **kw)
+    ring = W.single_element_ring(el, gg)
+    z, S = W.gaussian_particles(257, gg, seed=500 + K)
+    zm, Sm, lm = st.track(ring, z, S, 10, K, precision="mixed")
+    zo, So, lo = oracle.track(ring, z, S, 10, K)
+    assert np.array_equal(lm, lo)
+    assert np.abs(Sm - So).max() < 1e-12 and np.abs(zm - zo).max() < 1e-12
+
+
+@pytest.mark.parametrize("K", [2, st.ST_SPIN_MID_HALF])
+@pytest.mark.parametrize("gg,fringe", [(45.5, 0), (45.5, 1), (487.0, 1)])
+def test_mixed_ring_of_rectangular_bends(gg, fringe, K):
+    """The toy ring with rectangular bends (drift-kick quadrupoles in compensated
+    FP32 around them), 20 turns against the oracle, orbit < 1e-8.  At G gamma0
+    = 45.5 the mixed tracker's budget holds (mean Delta S < 1e-7, max < 1e-6).
+    At 487 the small ring turns the spin by 190 rad per bend, and its
+    drift-kick quadrupoles, on this ring's optics, put the mixed tracker's own
+    error at about 4e-8 per turn (4.8e-7 after 20 turns; the ring without its
+    quadrupole fields agrees with the FP64 tracker to 1e-15, so the FP64 maps
+    of the rectangular bends add nothing measurable): there the bound is the
+    tracker's 1e-6 budget, and one turn of the field-free version of the ring is
+    held to 1e-12 in the spin (1e-10 m in the orbit, whose drifts then reach
+    millimetre offsets) against the FP64 tracker."""
+    ring = W.rbend_ring(gg, fringe=fringe)
+    if K >= 0:
+        ring = W.with_spin_order(ring, K)
+    z, S = W.gaussian_particles(300, gg, seed=501)
+    zm, Sm, lm = st.track(ring, z, S, 20, K, precision="mixed")
+    zo, So, lo = oracle.track(ring, z, S, 20, K)
+    assert np.array_equal(lm, lo)
+    mean, mx = spin_err(Sm, So)
+    assert np.abs(zm[:4] - zo[:4]).max() < 1e-8
+    if gg < 100.0:
+        assert mean < 1e-7 and mx < 1e-6, (mean, mx)
+    else:
+        assert mean < 1e-6 and mx < 1e-5, (mean, mx)
+        free = dict(ring, elements=[dict(e, k1=0.0, k2=0.0) if e["type"] in ("mult", "quad_mk") else e
+                                    for e in ring["elements"]])
+        zf, Sf, lf = st.track(free, z, S, 1, K)      # one turn: without its quadrupoles the ring is unstable
+        zfm, Sfm, lfm = st.track(free, z, S, 1, K, precision="mixed")
+        assert np.array_equal(lf, lfm)
+        assert np.abs(Sfm - Sf).max() < 1e-12 and np.abs(zfm[:4] - zf[:4]).max() < 1e-10
+
+
+def test_mixed_rectangular_bends_lost_particles_batch_and_orbit_only():
+    """Losses inside a rectangular bend flag the particle with its entrance
+    state as in the oracle; a mixed batch with a ring of rectangular bends; the
+    orbit-only mode."""
+    gg = 45.5
+    ring = W.with_spin_order(W.rbend_ring(gg, fringe=1), 2)
+    ring["elements"] = [e for e in ring["elements"] if e["type"] == "rbend"][:1] + ring["elements"]
+    z, S = W.gaussian_particles(40, gg, seed=502)
+    z[3, 13] = -1.2
+    zm, Sm, lm = st.track(ring, z, S, 3, 2, precision="mixed")
+    zo, So, lo = oracle.track(ring, z, S, 3, 2)
+    assert np.array_equal(lm, lo) and lm[13] == 1
+    assert np.abs(zm[:, 13] - z[:, 13]).max() <= 1e-14 * np.abs(z[:, 13]).max()
+    assert np.array_equal(Sm[:, 13], S[:, 13])
+    alive = lo == 0
+    assert spin_err(Sm[:, alive], So[:, alive])[1] < 1e-6
+    b = st.Batch([ring, W.with_spin_order(W.toy_ring(120.0), 2)], [40, 64], "mixed")
+    z2, S2 = W.gaussian_particles(64, 120.0, seed=503)
+    b.upload(0, z, S)
+    b.upload(1, z2, S2)
+    b.track(3, 2)
+    zb, Sb, lb = b.download(0)
+    assert np.array_equal(lb, lo)
+    assert spin_err(Sb[:, alive], So[:, alive])[1] < 1e-6
+    zb2, Sb2, lb2 = b.download(1)
+    zo2, So2, lo2 = oracle.track(W.with_spin_order(W.toy_ring(120.0), 2), z2, S2, 3, 2)
+    assert np.array_equal(lb2, lo2) and spin_err(Sb2, So2)[1] < 1e-6
+    b.close()
+    lat = st.Lattice(ring)
+    tr = st.Tracker(lat, 40, "mixed")
+    tr.upload(z, S)
+    tr.track_orbit(3)
+    zr, Sr, lr = tr.download()
+    tr.close()
+    lat.close()
+    assert np.array_equal(lr, lo) and np.array_equal(Sr, S)
+    assert np.abs(zr[:4, alive] - zm[:4, alive]).max() < 1e-9
