@@ -421,16 +421,31 @@ struct MixLevels {
     // rotation accumulated over the level's earlier edges (angle
     // omr i ds - alpha_m, the trapezoid end weight alpha_m = omr 2^m ds / 2);
     // the deviation of Omega is (dox, doy, dos) with doy compensated
+    // Each coarser level's weight at an edge is twice the finer one's, so its
+    // edge rotation is the square of the finer one: with r = q(alpha y^) the
+    // finer weight's reference rotation, (r e)^2 = r^2 (r^-1 e r) e, i.e. the
+    // coarser deviation is e conjugated by r, times e (no second series).
     __device__ __forceinline__ void add_bend(int i, int N, const MixElem& el, float rc, float rs, float dox,
                                              const FF& doy, float dos) {
+        CNQ ep;   // the previous (finer) level's deviation at this edge
 #pragma unroll
         for (int m = 0; m <= K; ++m) {
             if (m > 0 && (i & ((1 << m) - 1))) break;
             const int j = (i == 0 || i == N) ? m : m + 1;
-            const float p2 = (float)(1 << j) * 0.5f;   // 2^(j-1), exact
-            const float w = el.ds * p2;
-            const FF wf{el.ds_ff.x * p2, el.ds_ff.y * p2};
-            CNQ e = cnq_deviation(el.w[j], w * dox, ff_mul(wf, doy), w * dos);
+            CNQ e;
+            if (m == 0) {
+                const float p2 = (float)(1 << j) * 0.5f;   // 2^(j-1), exact
+                const float w = el.ds * p2;
+                const FF wf{el.ds_ff.x * p2, el.ds_ff.y * p2};
+                e = cnq_deviation(el.w[j], w * dox, ff_mul(wf, doy), w * dos);
+            } else {
+                const MixWeight& Wp = el.w[j - 1];
+                CNQ c = ep;
+                c.x = FF{ep.x.hi * Wp.cf - ep.z.hi * Wp.sf, 0.0f};
+                c.z = FF{ep.x.hi * Wp.sf + ep.z.hi * Wp.cf, 0.0f};
+                e = cnq_mul(c, ep);
+            }
+            ep = e;
             if (i == 0) {
                 q[K - m] = e;
                 continue;
