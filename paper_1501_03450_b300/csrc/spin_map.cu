@@ -167,10 +167,14 @@ __device__ __forceinline__ void write_input_row(const float* xs, int r, int Bp, 
             X0T[(size_t)c * Bp + r] = c < 16 ? row[c] : __float2bfloat16_rn(0.0f);
 }
 
+// rows, step (optional): the batch starts at row rows[*step] of x (a training
+// schedule replayed from a CUDA graph)
 __global__ void mlp_pack_x(const float* __restrict__ x, int B, int Bp, InScale is, __nv_bfloat16* __restrict__ X0,
-                           __nv_bfloat16* __restrict__ X0T) {
+                           __nv_bfloat16* __restrict__ X0T, const int64_t* __restrict__ rows = nullptr,
+                           const int32_t* __restrict__ step = nullptr) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= Bp) return;
+    if (rows) x += rows[*step] * MLP_IN;
     float xs[MLP_IN];
     for (int c = 0; c < MLP_IN; ++c) xs[c] = r < B ? x[(size_t)r * MLP_IN + c] * is.s[c] : 0.0f;
     write_input_row(xs, r, Bp, X0, X0T);
@@ -251,8 +255,10 @@ __global__ void mlp_head_quat(const float* __restrict__ Y, const float* __restri
 // Residual head: loss mean_b |y_b - r_b|^2, dL/dy = 2 (y - r) / B.
 __global__ void mlp_head_resid(const float* __restrict__ Y, const float* __restrict__ rt, int B, int Bp,
                                double* __restrict__ loss, __nv_bfloat16* __restrict__ dYp,
-                               __nv_bfloat16* __restrict__ dYT) {
+                               __nv_bfloat16* __restrict__ dYT, const int64_t* __restrict__ rows = nullptr,
+                               const int32_t* __restrict__ step = nullptr) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rows) rt += rows[*step] * MLP_OUT;
     double l = 0.0;
     if (r < Bp) {
         float gy[4] = {0, 0, 0, 0};
@@ -266,6 +272,12 @@ __global__ void mlp_head_resid(const float* __restrict__ Y, const float* __restr
         write_dy(gy, r, Bp, dYp, dYT);
     }
     block_loss_add(l / B, loss);
+}
+
+// end of a replayed training step: record its loss, advance the step counter
+__global__ void mlp_step_end(int32_t* __restrict__ step, const double* __restrict__ loss, double* __restrict__ losses) {
+    if (losses) losses[*step] = *loss;
+    *step += 1;
 }
 
 // row sums of a [rows][Bp] bf16 matrix (bias gradients): one block of 256
@@ -348,11 +360,18 @@ __global__ void mlp_cast_weights(const float* __restrict__ p, __nv_bfloat16* W1p
     }
 }
 
+// sched, step (optional): lr, c1, c2 of step *step from sched[3 step ...]
 __global__ void mlp_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
                          const float* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps, float c1,
-                         float c2) {
+                         float c2, const float* __restrict__ sched = nullptr, const int32_t* __restrict__ step = nullptr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (sched) {
+        const int s = *step;
+        lr = sched[3 * s];
+        c1 = sched[3 * s + 1];
+        c2 = sched[3 * s + 2];
+    }
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -533,7 +552,8 @@ static int mlp_forward_layers(st_mlp* n, int Bp, bool keep_t) {
 // Weight gradient out[M][N] = A . B^T with the batch as K (K = Bp): few
 // output tiles and a long K, so K is split across CTAs and the partial sums
 // reduced (deterministic order).
-static int wgrad_gemm(st_mlp* n, const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int Bp, float* out) {
+static int wgrad_gemm(st_mlp* n, const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int Bp, float* out,
+                      cudaStream_t stream) {
     GemmEpi ep = epi_base();
     ep.mode = EPI_F32;
     ep.n_valid = N;
@@ -541,26 +561,59 @@ static int wgrad_gemm(st_mlp* n, const __nv_bfloat16* A, const __nv_bfloat16* B,
     const int splits = gemm_split_count(Bp, WG_MAX_SPLITS);
     if (splits == 1) {
         ep.out_f32 = out;
-        return gemm_bf16_tn(A, B, M, N, Bp, ep, n->status, n->stream);
+        return gemm_bf16_tn(A, B, M, N, Bp, ep, n->status, stream);
     }
     ep.out_f32 = n->ws;
     ep.split_stride = (int64_t)M * N;
-    int rc = gemm_bf16_tn(A, B, M, N, Bp, ep, n->status, n->stream, splits);
+    int rc = gemm_bf16_tn(A, B, M, N, Bp, ep, n->status, stream, splits);
     if (rc) return rc;
-    return gemm_split_reduce(n->ws, splits, (int64_t)M * N, (int64_t)M * N, out, n->stream);
+    return gemm_split_reduce(n->ws, splits, (int64_t)M * N, (int64_t)M * N, out, stream);
 }
+
+// Streams of a backward pass: the data gradients (the chain to the next layer)
+// on `main`; the weight gradients of each layer, which only the optimiser
+// reads, on `side` and its bias gradients on `side2` when they are given (a
+// captured training step),
+// forked after the data gradient they read and joined back at the end.  The
+// data gradient of layer l - 1 overwrites the buffer that layer l + 1's weight
+// gradient reads, so it waits for that one.  The kernels and their order on
+// each stream are those of the single-stream pass, so the results are equal.
+struct BackwardStreams {
+    cudaStream_t main, side, side2;   // side2: the bias-gradient row sums
+    cudaEvent_t fork, done, join, done2, join2;
+};
+
+static int bw_event(cudaError_t e, const char* what) { return e == cudaSuccess ? ST_OK : cuda_fail(e, what); }
 
 // Backward pass from dL/dy (dYp, dYT written by a head kernel) into the
 // gradient buffer g, using the activations kept by the forward pass.
-static int mlp_backward(st_mlp* n, int Bp) {
+static int mlp_backward(st_mlp* n, int Bp, const BackwardStreams* bs = nullptr) {
     float* g = n->g;
+    const cudaStream_t ms = n->stream, ss = bs ? bs->side : n->stream, s2 = bs ? bs->side2 : n->stream;
+    auto fork = [&]() -> int {   // the side streams wait for the main stream's work so far
+        if (!bs) return ST_OK;
+        int rc = bw_event(cudaEventRecord(bs->fork, ms), "mlp: backward fork");
+        if (!rc) rc = bw_event(cudaStreamWaitEvent(ss, bs->fork, 0), "mlp: backward fork");
+        return rc ? rc : bw_event(cudaStreamWaitEvent(s2, bs->fork, 0), "mlp: backward fork");
+    };
+    auto side_done = [&]() -> int {
+        if (!bs) return ST_OK;
+        int rc = bw_event(cudaEventRecord(bs->done, ss), "mlp: backward side");
+        return rc ? rc : bw_event(cudaEventRecord(bs->done2, s2), "mlp: backward side");
+    };
+    auto wait_side = [&]() -> int {   // the main stream waits for the side work recorded last
+        if (!bs) return ST_OK;
+        int rc = bw_event(cudaStreamWaitEvent(ms, bs->done, 0), "mlp: backward wait");
+        return rc ? rc : bw_event(cudaStreamWaitEvent(ms, bs->done2, 0), "mlp: backward wait");
+    };
     // layer 5: dW5^T = A4^T . dY  (D'[256][16]), db5 = sum dY, dZ4 = (dY W5) * silu'(Z4)
-    int rc = wgrad_gemm(n, n->AT[3], n->dYT, MLP_H, MLP_NOUT, Bp, n->dWtmp);
+    int rc = fork();
+    if (!rc) rc = wgrad_gemm(n, n->AT[3], n->dYT, MLP_H, MLP_NOUT, Bp, n->dWtmp, ss);
     if (rc) return rc;
-    GemmEpi ep;
-    mlp_gather_w5<<<(MLP_OUT * MLP_H + 255) / 256, 256, 0, n->stream>>>(n->dWtmp, g + mlp_w_off(4));
-    mlp_rowsum<<<MLP_OUT, ROWSUM_THREADS, 0, n->stream>>>(n->dYT, MLP_OUT, Bp, g + mlp_b_off(4));
-    ep = epi_base();
+    mlp_gather_w5<<<(MLP_OUT * MLP_H + 255) / 256, 256, 0, ss>>>(n->dWtmp, g + mlp_w_off(4));
+    mlp_rowsum<<<MLP_OUT, ROWSUM_THREADS, 0, s2>>>(n->dYT, MLP_OUT, Bp, g + mlp_b_off(4));
+    if ((rc = side_done())) return rc;
+    GemmEpi ep = epi_base();
     ep.mode = EPI_DSILU;
     ep.n_valid = MLP_H;
     ep.z_in = n->Z[3];
@@ -569,16 +622,21 @@ static int mlp_backward(st_mlp* n, int Bp) {
     ep.ld_bf16 = MLP_H;
     ep.out_bf16_t = n->dZT[0];
     ep.ld_bf16_t = Bp;
-    rc = gemm_bf16_tn(n->dYp, n->W5Tp, Bp, MLP_H, MLP_KIN, ep, n->status, n->stream);
+    rc = gemm_bf16_tn(n->dYp, n->W5Tp, Bp, MLP_H, MLP_KIN, ep, n->status, ms);
     if (rc) return rc;
     // hidden layers l = 3, 2, 1 (0-based weights W[l], activations A[l-1])
     const __nv_bfloat16* WT[4] = {nullptr, n->W2T, n->W3T, n->W4T};
     int cur = 0;
     for (int l = 3; l >= 1; --l) {
         // dW_l = dZ_l^T . A_{l-1}  ->  [256 out][256 in], into the gradient buffer
-        rc = wgrad_gemm(n, n->dZT[cur], n->AT[l - 1], MLP_H, MLP_H, Bp, g + mlp_w_off(l));
+        if ((rc = fork())) return rc;
+        // (the main stream's next data gradient overwrites what the previous
+        // iteration's side work reads: wait for it first)
+        if (l < 3 && (rc = wait_side())) return rc;
+        rc = wgrad_gemm(n, n->dZT[cur], n->AT[l - 1], MLP_H, MLP_H, Bp, g + mlp_w_off(l), ss);
         if (rc) return rc;
-        mlp_rowsum<<<MLP_H, ROWSUM_THREADS, 0, n->stream>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(l));
+        mlp_rowsum<<<MLP_H, ROWSUM_THREADS, 0, s2>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(l));
+        if ((rc = side_done())) return rc;
         // dZ_{l-1} = (dZ_l W_l) * silu'(Z_{l-1})
         ep = epi_base();
         ep.mode = EPI_DSILU;
@@ -589,15 +647,22 @@ static int mlp_backward(st_mlp* n, int Bp) {
         ep.ld_bf16 = MLP_H;
         ep.out_bf16_t = n->dZT[1 - cur];
         ep.ld_bf16_t = Bp;
-        rc = gemm_bf16_tn(n->dZ[cur], WT[l], Bp, MLP_H, MLP_H, ep, n->status, n->stream);
+        rc = gemm_bf16_tn(n->dZ[cur], WT[l], Bp, MLP_H, MLP_H, ep, n->status, ms);
         if (rc) return rc;
         cur = 1 - cur;
     }
     // layer 1: dW1 = dZ1^T . X0 -> [256][64] -> [256][6] (hi + lo columns); db1
-    rc = wgrad_gemm(n, n->dZT[cur], n->X0T, MLP_H, MLP_KIN, Bp, n->dWtmp);
+    if ((rc = fork())) return rc;
+    rc = wgrad_gemm(n, n->dZT[cur], n->X0T, MLP_H, MLP_KIN, Bp, n->dWtmp, ss);
     if (rc) return rc;
-    mlp_gather_w1<<<(MLP_H * MLP_IN + 255) / 256, 256, 0, n->stream>>>(n->dWtmp, g + mlp_w_off(0));
-    mlp_rowsum<<<MLP_H, ROWSUM_THREADS, 0, n->stream>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(0));
+    mlp_gather_w1<<<(MLP_H * MLP_IN + 255) / 256, 256, 0, ss>>>(n->dWtmp, g + mlp_w_off(0));
+    mlp_rowsum<<<MLP_H, ROWSUM_THREADS, 0, s2>>>(n->dZT[cur], MLP_H, Bp, g + mlp_b_off(0));
+    if (bs) {   // join: the main stream continues after all the gradients
+        if ((rc = bw_event(cudaEventRecord(bs->join, ss), "mlp: backward join"))) return rc;
+        if ((rc = bw_event(cudaEventRecord(bs->join2, s2), "mlp: backward join"))) return rc;
+        if ((rc = bw_event(cudaStreamWaitEvent(ms, bs->join, 0), "mlp: backward join"))) return rc;
+        if ((rc = bw_event(cudaStreamWaitEvent(ms, bs->join2, 0), "mlp: backward join"))) return rc;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "mlp: backward");
     n->have_grads = true;
@@ -1032,6 +1097,111 @@ int st_mlp_set_fused_inference(st_mlp* n, int32_t on) {
     return ST_OK;
 }
 
+// Steps 1..steps-1 of a training schedule as one captured CUDA graph of a step
+// (pack, forward, head, backward, Adam, weight refresh, step end) replayed
+// once per step: the batch's rows and (lr, c1, c2) come from device arrays
+// indexed by a device step counter, so every replay is the same graph.  The
+// kernels and their arguments are those of the eager step, so the results
+// are identical to stepping eagerly.
+static int train_replayed(st_mlp* n, const float* x_rows, const float* r_rows, int32_t B, int32_t steps,
+                          const int64_t* row_start, const float* lr, float beta1, float beta2, float eps,
+                          double* d_loss) {
+    const int Bp = ((B + 127) / 128) * 128;
+    std::vector<float> sched(3 * (size_t)steps, 0.0f);
+    for (int k = 1; k < steps; ++k) {
+        // Adam's bias corrections at the optimiser step this schedule step makes
+        const float t = (float)(n->step + k);
+        sched[3 * k] = lr[k];
+        sched[3 * k + 1] = 1.0f / (1.0f - powf(beta1, t));
+        sched[3 * k + 2] = 1.0f / (1.0f - powf(beta2, t));
+    }
+    int64_t* d_rows = nullptr;
+    float* d_sched = nullptr;
+    int32_t* d_step = nullptr;
+    const int32_t first = 1;
+    cudaError_t e = cudaMallocAsync((void**)&d_rows, (size_t)steps * sizeof(int64_t), n->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_sched, sched.size() * sizeof(float), n->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_step, sizeof(int32_t), n->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_rows, row_start, (size_t)steps * sizeof(int64_t), cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_sched, sched.data(), sched.size() * sizeof(float), cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_step, &first, sizeof(int32_t), cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);   // the host arrays are transient
+    int rc = e == cudaSuccess ? ST_OK : cuda_fail(e, "st_mlp_train: schedule upload");
+    // capture and replay on a stream of our own (the caller's may be the legacy
+    // default stream, which cannot be captured), joined to the caller's by events
+    // (the weight gradients on a second stream, see mlp_backward)
+    cudaStream_t caller = n->stream, cs = nullptr, side = nullptr, side2 = nullptr;
+    cudaEvent_t ev = nullptr, evs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (rc == ST_OK) {
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&side2, cudaStreamNonBlocking);
+        for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&evs[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, caller);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "st_mlp_train: replay stream");
+    }
+    if (rc == ST_OK) n->stream = cs;   // the step's launches go to the capture stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (rc == ST_OK) {
+        e = cudaStreamBeginCapture(n->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) rc = cuda_fail(e, "st_mlp_train: capture");
+    }
+    if (rc == ST_OK) {
+        e = cudaMemsetAsync(n->loss, 0, sizeof(double), n->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "st_mlp_train: loss reset");
+        if (rc == ST_OK) {
+            mlp_pack_x<<<(Bp + 127) / 128, 128, 0, n->stream>>>(x_rows, B, Bp, n->in_scale, n->X0, n->X0T, d_rows,
+                                                                d_step);
+            rc = mlp_forward_layers(n, Bp, true);
+        }
+        if (rc == ST_OK) {
+            mlp_head_resid<<<(Bp + 127) / 128, 128, 0, n->stream>>>(n->Y, r_rows, B, Bp, n->loss, n->dYp, n->dYT,
+                                                                    d_rows, d_step);
+            const BackwardStreams bs{cs, side, side2, evs[0], evs[1], evs[2], evs[3], evs[4]};
+            rc = mlp_backward(n, Bp, &bs);
+        }
+        if (rc == ST_OK) {
+            const int64_t P = MLP_PARAMS;
+            mlp_adam<<<(unsigned)((P + 255) / 256), 256, 0, n->stream>>>(n->p, n->m, n->v, n->g, P, 0.0f, beta1,
+                                                                         beta2, eps, 0.0f, 0.0f, d_sched, d_step);
+            rc = mlp_refresh_weights(n);
+        }
+        if (rc == ST_OK) mlp_step_end<<<1, 1, 0, n->stream>>>(d_step, n->loss, d_loss);
+        const cudaError_t ec = cudaStreamEndCapture(n->stream, &graph);   // always end the capture
+        if (rc == ST_OK && ec != cudaSuccess) rc = cuda_fail(ec, "st_mlp_train: capture");
+    }
+    if (rc == ST_OK) {
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "st_mlp_train: graph instantiation");
+    }
+    for (int k = 1; k < steps && rc == ST_OK; ++k) {
+        e = cudaGraphLaunch(exec, n->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "st_mlp_train: graph launch");
+    }
+    if (rc == ST_OK) n->step += steps - 1;
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) {   // join the replays back into the caller's stream
+        n->stream = caller;
+        if (cudaEventRecord(ev, cs) == cudaSuccess) cudaStreamWaitEvent(caller, ev, 0);
+        cudaStreamDestroy(cs);   // released once its work is done
+    }
+    if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t x : evs)
+        if (x) cudaEventDestroy(x);
+    if (side) cudaStreamDestroy(side);
+    if (side2) cudaStreamDestroy(side2);
+    cudaFreeAsync(d_rows, caller);
+    cudaFreeAsync(d_sched, caller);
+    cudaFreeAsync(d_step, caller);
+    return rc;
+}
+
 int st_mlp_train(st_mlp* n, const float* x_rows, const float* r_rows, int64_t n_rows, int32_t B, int32_t steps,
                  const int64_t* row_start, const float* lr, float beta1, float beta2, float eps, double* loss_out) {
     if (!n || !x_rows || !r_rows || !row_start || !lr || steps < 0 || B < 1 || B > n->max_batch) {
@@ -1050,16 +1220,17 @@ int st_mlp_train(st_mlp* n, const float* x_rows, const float* r_rows, int64_t n_
         cudaError_t e = cudaMallocAsync((void**)&d_loss, (size_t)steps * sizeof(double), n->stream);
         if (e != cudaSuccess) return cuda_fail(e, "st_mlp_train: loss buffer");
     }
-    int rc = ST_OK;
-    for (int k = 0; k < steps && rc == ST_OK; ++k) {
-        rc = st_mlp_loss_grad_residual(n, x_rows + row_start[k] * MLP_IN, r_rows + row_start[k] * MLP_OUT, B, nullptr,
+    // the first step eagerly (it also sets the kernels' attributes and fills the
+    // tensor-map cache before the capture), the rest replayed from a graph
+    int rc = st_mlp_loss_grad_residual(n, x_rows + row_start[0] * MLP_IN, r_rows + row_start[0] * MLP_OUT, B, nullptr,
                                        nullptr);
-        if (rc == ST_OK && d_loss) {
-            cudaError_t e = cudaMemcpyAsync(d_loss + k, n->loss, sizeof(double), cudaMemcpyDeviceToDevice, n->stream);
-            if (e != cudaSuccess) rc = cuda_fail(e, "st_mlp_train: loss copy");
-        }
-        if (rc == ST_OK) rc = st_mlp_adam_step(n, lr[k], beta1, beta2, eps);
+    if (rc == ST_OK && d_loss) {
+        cudaError_t e = cudaMemcpyAsync(d_loss, n->loss, sizeof(double), cudaMemcpyDeviceToDevice, n->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "st_mlp_train: loss copy");
     }
+    if (rc == ST_OK) rc = st_mlp_adam_step(n, lr[0], beta1, beta2, eps);
+    if (rc == ST_OK && steps > 1)
+        rc = train_replayed(n, x_rows, r_rows, B, steps, row_start, lr, beta1, beta2, eps, d_loss);
     if (d_loss) {
         if (rc == ST_OK) {
             cudaError_t e = cudaMemcpyAsync(loss_out, d_loss, (size_t)steps * sizeof(double), cudaMemcpyDeviceToHost,

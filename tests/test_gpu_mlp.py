@@ -401,3 +401,30 @@ def test_surrogate_with_zero_network_is_the_closed_form():
     tr2.close()
     lat.close()
     net.close()
+
+
+def test_train_schedule_replayed_from_a_graph_equals_eager_steps():
+    """st_mlp_train runs its first step eagerly and replays the others from a
+    captured CUDA graph (the rows and the Adam schedule read on the device):
+    after a 7-step schedule the parameters and the per-step losses equal
+    those of 7 one-step calls, which all run eagerly, bit for bit."""
+    B, n_rows = 1000, 5000
+    rng = np.random.default_rng(77)
+    x = rand_x(n_rows, 40)
+    r = rng.standard_normal((n_rows, 4)) * 0.1
+    p = random_params(9, last_scale=1.0)
+    xd, rd = dev(x, np.float32), dev(r, np.float32)
+    rows = np.array([0, 1200, 4000, 300, 2500, 3999, 17], dtype=np.int64)
+    lrs = np.array([2e-3, 2e-3, 1e-3, 1e-3, 5e-4, 5e-4, 5e-4], dtype=np.float32)
+    a = make_net(p, head_for(1), max_batch=B)
+    la = a.train(xd.data_ptr(), rd.data_ptr(), n_rows, B, rows, lrs, want_loss=True)
+    pa = a.get_params()
+    b = make_net(p, head_for(1), max_batch=B)
+    lb = [b.train(xd.data_ptr(), rd.data_ptr(), n_rows, B, rows[k:k + 1], lrs[k:k + 1], want_loss=True)[0]
+          for k in range(len(rows))]
+    pb = b.get_params()
+    a.close()
+    b.close()
+    assert np.array_equal(pa, pb)
+    assert np.allclose(la, lb, rtol=1e-12, atol=0.0)   # the loss is an atomic sum: order may vary
+    assert not np.array_equal(pa, p.astype(np.float32))
