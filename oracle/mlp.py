@@ -12,8 +12,10 @@ W1[256][6], b1, W2[256][256], b2, W3, b3, W4, b4, W5[4][256], b5.
 to nearest even) and represents the scaled input as the two-term bf16 split of
 its float32 value, keeping FP64 arithmetic: the storage precision of the GPU
 kernels without their FP32 accumulation order.  `bf16_grads=True` also stores
-the back-propagated dL/dy and every dL/dz in bfloat16, as the kernels do
-between their gradient GEMMs (the arithmetic stays FP64).
+the back-propagated dL/dy, every dL/dz and every SiLU derivative SiLU'(z) in
+bfloat16, as the kernels do between their gradient GEMMs (the forward pass
+keeps SiLU'(z) in bf16, the activations' storage precision, for the
+backward pass; the arithmetic stays FP64).
 """
 from __future__ import annotations
 
@@ -91,7 +93,7 @@ def network(p, a0, bf16=False):
 
 def backward(c, gy, bf16_grads=False):
     """Gradient (flattened, parameter order) from dL/dy [B, 4]; bf16_grads
-    stores dL/dy and each dL/dz in bfloat16 before it is used."""
+    stores dL/dy, each SiLU'(z) and each dL/dz in bfloat16 before it is used."""
     rd = c["rd"]
     rg = round_bf16 if bf16_grads else (lambda a: a)
     grads = [None] * 5
@@ -100,7 +102,7 @@ def backward(c, gy, bf16_grads=False):
     grads[4] = (gy.T @ c["acts"][4], gy.sum(axis=0))
     ga = gy @ rd(W5)
     for l in range(3, -1, -1):
-        gz = rg(ga * dsilu(c["zs"][l]))
+        gz = rg(ga * rg(dsilu(c["zs"][l])))
         W, _ = c["layers"][l]
         grads[l] = (gz.T @ c["acts"][l], gz.sum(axis=0))
         ga = gz @ rd(W)

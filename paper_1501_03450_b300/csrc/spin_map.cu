@@ -102,7 +102,7 @@ struct st_mlp {
     __nv_bfloat16 *X0 = nullptr, *X0T = nullptr;            // [Bp][64] / [64][Bp]: hi, lo, zero
     __nv_bfloat16* A[4] = {nullptr, nullptr, nullptr, nullptr};
     __nv_bfloat16* AT[4] = {nullptr, nullptr, nullptr, nullptr};
-    float* Z[4] = {nullptr, nullptr, nullptr, nullptr};
+    __nv_bfloat16* DS[4] = {nullptr, nullptr, nullptr, nullptr};   // SiLU'(z) of the hidden layers, [Bp][256]
     float* Y = nullptr;                                     // [Bp][16]
     __nv_bfloat16 *dYp = nullptr, *dYT = nullptr;
     __nv_bfloat16* dZ[2] = {nullptr, nullptr};
@@ -509,7 +509,8 @@ static int upload_head(st_mlp* n) {
 }
 
 // forward through the five layers from X0 (rows Bp); keep_t writes the
-// transposed activations and pre-activations for a following backward pass
+// transposed activations and the SiLU derivatives (bf16) for a following
+// backward pass
 static int mlp_forward_layers(st_mlp* n, int Bp, bool keep_t) {
     if (!keep_t && n->fused_inference) {
         // inference: all five layers per 128-row tile in one kernel
@@ -532,8 +533,8 @@ static int mlp_forward_layers(st_mlp* n, int Bp, bool keep_t) {
         e.ld_bf16 = MLP_H;
         e.out_bf16_t = keep_t ? n->AT[l] : nullptr;
         e.ld_bf16_t = Bp;
-        e.z_out = keep_t ? n->Z[l] : nullptr;
-        e.ld_zo = MLP_H;
+        e.ds_out = keep_t ? n->DS[l] : nullptr;
+        e.ld_dso = MLP_H;
         rc = gemm_bf16_tn(in, Win[l], Bp, MLP_H, K, e, n->status, n->stream);
         if (rc) return rc;
         in = n->A[l];
@@ -616,8 +617,8 @@ static int mlp_backward(st_mlp* n, int Bp, const BackwardStreams* bs = nullptr) 
     GemmEpi ep = epi_base();
     ep.mode = EPI_DSILU;
     ep.n_valid = MLP_H;
-    ep.z_in = n->Z[3];
-    ep.ld_z = MLP_H;
+    ep.ds_in = n->DS[3];
+    ep.ld_ds = MLP_H;
     ep.out_bf16 = n->dZ[0];
     ep.ld_bf16 = MLP_H;
     ep.out_bf16_t = n->dZT[0];
@@ -641,8 +642,8 @@ static int mlp_backward(st_mlp* n, int Bp, const BackwardStreams* bs = nullptr) 
         ep = epi_base();
         ep.mode = EPI_DSILU;
         ep.n_valid = MLP_H;
-        ep.z_in = n->Z[l - 1];
-        ep.ld_z = MLP_H;
+        ep.ds_in = n->DS[l - 1];
+        ep.ld_ds = MLP_H;
         ep.out_bf16 = n->dZ[1 - cur];
         ep.ld_bf16 = MLP_H;
         ep.out_bf16_t = n->dZT[1 - cur];
@@ -722,7 +723,7 @@ int st_mlp_destroy(st_mlp* n) {
     for (int l = 0; l < 4; ++l) {
         cudaFree(n->A[l]);
         cudaFree(n->AT[l]);
-        cudaFree(n->Z[l]);
+        cudaFree(n->DS[l]);
     }
     for (int k = 0; k < 2; ++k) {
         cudaFree(n->dZ[k]);
@@ -783,7 +784,7 @@ int st_mlp_create(int32_t max_batch, void* cuda_stream, st_mlp** out) {
     for (int l = 0; l < 4; ++l) {
         ST_MALLOC(n->A[l], (size_t)Bp * MLP_H * bf);
         ST_MALLOC(n->AT[l], (size_t)Bp * MLP_H * bf);
-        ST_MALLOC(n->Z[l], (size_t)Bp * MLP_H * 4);
+        ST_MALLOC(n->DS[l], (size_t)Bp * MLP_H * 2);
     }
     ST_MALLOC(n->Y, (size_t)Bp * MLP_NOUT * 4);
     ST_MALLOC(n->dYp, (size_t)Bp * MLP_KIN * bf);

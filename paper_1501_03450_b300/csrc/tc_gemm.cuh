@@ -12,8 +12,9 @@
 //                "done" barrier after the last block;
 //   all 8 warps: epilogue -- tcgen05.ld of their 32 TMEM lanes (= rows; warps
 //                w and w + 4 share lanes and split the columns),
-//                bias / SiLU / SiLU-derivative, FP32 or BF16 stores (row-major
-//                and, for backward passes, transposed).
+//                bias / SiLU (and its derivative stored in bf16 for the
+//                backward pass) / times the stored SiLU derivative, FP32 or
+//                BF16 stores (row-major and, for backward passes, transposed).
 // Every mbarrier wait is bounded (about one second); on expiry the CTA sets
 // the status word, waits once more for work in flight, frees its TMEM and
 // returns.
@@ -38,10 +39,10 @@ struct GemmEpi {
     int32_t ld_bf16;
     __nv_bfloat16* out_bf16_t;       // [N][ld_bf16_t] (transposed)
     int32_t ld_bf16_t;
-    const float* z_in;               // [M][ld_z] pre-activations (EPI_DSILU)
-    int32_t ld_z;
-    float* z_out;                    // [M][ld_zo] pre-activations (EPI_BIAS_SILU)
-    int32_t ld_zo;
+    const __nv_bfloat16* ds_in;      // [M][ld_ds] SiLU derivatives at the pre-activations (EPI_DSILU)
+    int32_t ld_ds;
+    __nv_bfloat16* ds_out;           // [M][ld_dso] SiLU derivatives, written by EPI_BIAS_SILU
+    int32_t ld_dso;
     int64_t split_stride;            // split-K (EPI_F32): split z writes out_f32 + z * split_stride
 };
 
@@ -315,23 +316,36 @@ __global__ void __launch_bounds__(GemmCfg<BN, ST>::THREADS, GemmCfg<BN, ST>::MIN
                         v[j + 2] += bb.z;
                         v[j + 3] += bb.w;
                     }
-                    if (epi.z_out) {
-                        float* zd = epi.z_out + (size_t)row * epi.ld_zo + nb;
+                    if (epi.ds_out) {   // SiLU'(z) in bf16 for the backward pass
+                        __nv_bfloat16* dd = epi.ds_out + (size_t)row * epi.ld_dso + nb;
 #pragma unroll
-                        for (int j = 0; j < CH; j += 4)
-                            *reinterpret_cast<float4*>(zd + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                        for (int j = 0; j < CH; j += 8) {
+                            uint4 pk;
+                            __nv_bfloat162 h0 = __floats2bfloat162_rn(dsilu_f(v[j]), dsilu_f(v[j + 1]));
+                            __nv_bfloat162 h1 = __floats2bfloat162_rn(dsilu_f(v[j + 2]), dsilu_f(v[j + 3]));
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(dsilu_f(v[j + 4]), dsilu_f(v[j + 5]));
+                            __nv_bfloat162 h3 = __floats2bfloat162_rn(dsilu_f(v[j + 6]), dsilu_f(v[j + 7]));
+                            pk.x = *reinterpret_cast<uint32_t*>(&h0);
+                            pk.y = *reinterpret_cast<uint32_t*>(&h1);
+                            pk.z = *reinterpret_cast<uint32_t*>(&h2);
+                            pk.w = *reinterpret_cast<uint32_t*>(&h3);
+                            *reinterpret_cast<uint4*>(dd + j) = pk;
+                        }
                     }
 #pragma unroll
                     for (int j = 0; j < CH; ++j) v[j] = silu_f(v[j]);
-                } else {   // EPI_DSILU
-                    const float* zs = epi.z_in + (size_t)row * epi.ld_z + nb;
+                } else {   // EPI_DSILU: times the stored SiLU'(z)
+                    const __nv_bfloat16* ds = epi.ds_in + (size_t)row * epi.ld_ds + nb;
 #pragma unroll
-                    for (int j = 0; j < CH; j += 4) {
-                        const float4 zz = *reinterpret_cast<const float4*>(zs + j);
-                        v[j] *= dsilu_f(zz.x);
-                        v[j + 1] *= dsilu_f(zz.y);
-                        v[j + 2] *= dsilu_f(zz.z);
-                        v[j + 3] *= dsilu_f(zz.w);
+                    for (int j = 0; j < CH; j += 8) {
+                        const uint4 q = *reinterpret_cast<const uint4*>(ds + j);
+                        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float2 f = __bfloat1622float2(h[k]);
+                            v[j + 2 * k] *= f.x;
+                            v[j + 2 * k + 1] *= f.y;
+                        }
                     }
                 }
 #pragma unroll

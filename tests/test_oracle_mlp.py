@@ -178,11 +178,12 @@ def test_residual_gradient_central_differences():
 
 
 def test_bf16_gradient_storage_rounds_each_stage_once():
-    """bf16_grads stores dL/dy and every dL/dz in bfloat16 and changes nothing
-    else: the output layer's gradient is exactly the one computed from the
-    rounded dL/dy, every block moves by about the bf16 resolution (not more:
-    relative L2 change below 2^-6, not zero), and a dL/dy already in bf16 with
-    rounded dL/dz reproduces the stored values."""
+    """bf16_grads stores dL/dy, every SiLU'(z) and every dL/dz in bfloat16
+    and changes nothing else: the output layer's gradient is exactly the one
+    computed from the rounded dL/dy, the last hidden layer's exactly the one
+    from the rounded dL/dz = bf16(dL/da * bf16(SiLU'(z))), every block moves by
+    about the bf16 resolution (not more: relative L2 change below 2^-6, not
+    zero), and a dL/dy already in bf16 reproduces the stored values."""
     rng = np.random.default_rng(41)
     p = random_params(9)
     x, _ = _inputs(64, 42)
@@ -194,6 +195,11 @@ def test_bf16_gradient_storage_rounds_each_stage_once():
     offs = np.cumsum([0] + [a * b + a for a, b in M.LAYERS])
     gyr = M.round_bf16(gy)
     assert np.array_equal(g1[offs[4]:offs[5]], np.concatenate([(gyr.T @ c["acts"][4]).ravel(), gyr.sum(axis=0)]))
+    W5, _ = c["layers"][4]
+    z3 = c["zs"][3]
+    s3 = 1.0 / (1.0 + np.exp(-z3))
+    gz3 = M.round_bf16((gyr @ c["rd"](W5)) * M.round_bf16(s3 * (1.0 + z3 * (1.0 - s3))))
+    assert np.array_equal(g1[offs[3]:offs[4]], np.concatenate([(gz3.T @ c["acts"][3]).ravel(), gz3.sum(axis=0)]))
     for l in range(5):
         a, b = offs[l], offs[l + 1]
         rel = np.linalg.norm(g1[a:b] - g0[a:b]) / np.linalg.norm(g0[a:b])
