@@ -168,6 +168,12 @@ __device__ __forceinline__ float dsilu_f(float z) {
     const float s = __fdividef(1.0f, 1.0f + __expf(-z));
     return s * (1.0f + z * (1.0f - s));
 }
+// SiLU and its derivative from one sigmoid s (a = z s, d = s (1 + z (1 - s)))
+__device__ __forceinline__ void silu_dsilu_f(float z, float& a, float& d) {
+    const float s = z < -87.0f ? 0.0f : __fdividef(1.0f, 1.0f + __expf(-z));
+    a = z * s;
+    d = s * (1.0f + z * (1.0f - s));
+}
 
 // BN: tile width along N; ST: shared-memory pipeline stages (2 for the short
 // K = 64..256 of the network's layers, so that up to 3 CTAs share an SM and
@@ -316,24 +322,28 @@ __global__ void __launch_bounds__(GemmCfg<BN, ST>::THREADS, GemmCfg<BN, ST>::MIN
                         v[j + 2] += bb.z;
                         v[j + 3] += bb.w;
                     }
-                    if (epi.ds_out) {   // SiLU'(z) in bf16 for the backward pass
+                    if (epi.ds_out) {   // SiLU(z), and SiLU'(z) in bf16 for the backward pass
                         __nv_bfloat16* dd = epi.ds_out + (size_t)row * epi.ld_dso + nb;
 #pragma unroll
                         for (int j = 0; j < CH; j += 8) {
+                            float dv[8];
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) silu_dsilu_f(v[j + k], v[j + k], dv[k]);
                             uint4 pk;
-                            __nv_bfloat162 h0 = __floats2bfloat162_rn(dsilu_f(v[j]), dsilu_f(v[j + 1]));
-                            __nv_bfloat162 h1 = __floats2bfloat162_rn(dsilu_f(v[j + 2]), dsilu_f(v[j + 3]));
-                            __nv_bfloat162 h2 = __floats2bfloat162_rn(dsilu_f(v[j + 4]), dsilu_f(v[j + 5]));
-                            __nv_bfloat162 h3 = __floats2bfloat162_rn(dsilu_f(v[j + 6]), dsilu_f(v[j + 7]));
+                            __nv_bfloat162 h0 = __floats2bfloat162_rn(dv[0], dv[1]);
+                            __nv_bfloat162 h1 = __floats2bfloat162_rn(dv[2], dv[3]);
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(dv[4], dv[5]);
+                            __nv_bfloat162 h3 = __floats2bfloat162_rn(dv[6], dv[7]);
                             pk.x = *reinterpret_cast<uint32_t*>(&h0);
                             pk.y = *reinterpret_cast<uint32_t*>(&h1);
                             pk.z = *reinterpret_cast<uint32_t*>(&h2);
                             pk.w = *reinterpret_cast<uint32_t*>(&h3);
                             *reinterpret_cast<uint4*>(dd + j) = pk;
                         }
-                    }
+                    } else {
 #pragma unroll
-                    for (int j = 0; j < CH; ++j) v[j] = silu_f(v[j]);
+                        for (int j = 0; j < CH; ++j) v[j] = silu_f(v[j]);
+                    }
                 } else {   // EPI_DSILU: times the stored SiLU'(z)
                     const __nv_bfloat16* ds = epi.ds_in + (size_t)row * epi.ld_ds + nb;
 #pragma unroll
