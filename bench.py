@@ -314,7 +314,7 @@ FP64_MIDPOINT_PARTICLES = 100_000   # the FP64 tracker is fully occupied at 10^5
 # once and the counters cannot tell them from scalar ones, so the executed
 # measure is the share of the FMA pipe's issue slots (128 lanes per SM per
 # clock), not a flop count.
-MIXED_FMA_PIPE_INSTR_PER_PASS = 1342.0
+MIXED_FMA_PIPE_INSTR_PER_PASS = 1344.0
 
 
 def _tracker_rate(st, torch, ring, z, S, precision, spin_order, steps=3):
