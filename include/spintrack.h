@@ -464,10 +464,14 @@ int st_mlp_adam_step(st_mlp* mlp, float lr, float beta1, float beta2, float eps)
  * from st_mlp_make_targets), then one Adam update with learning rate lr[k]
  * (as st_mlp_adam_step).  row_start, lr: host arrays of `steps` entries;
  * loss_out: host double[steps] for every step's loss before its update, or
- * NULL.  The steps are issued from the library without returning to the
- * caller in between; synchronises at the end and reports a bounded-wait
- * expiry of any step.  Errors: ST_EINVAL (arguments, a row range outside
- * [0, n_rows), lr <= 0), ST_ECUDA, ST_ETIMEOUT. */
+ * NULL.  The first step runs on the network's stream; the others are
+ * replayed from one captured CUDA graph of a step (its rows and Adam schedule
+ * read from device copies of row_start and lr) on streams the library
+ * creates and joins back to the network's stream, with each layer's weight
+ * and bias gradients beside the next layer's data gradient; the results are
+ * those of stepping one step at a time.  Synchronises at the end and reports
+ * a bounded-wait expiry of any step.  Errors: ST_EINVAL (arguments, a row
+ * range outside [0, n_rows), lr <= 0), ST_ECUDA, ST_ETIMEOUT. */
 int st_mlp_train(st_mlp* mlp, const float* x_rows, const float* r_rows, int64_t n_rows, int32_t B, int32_t steps,
                  const int64_t* row_start, const float* lr, float beta1, float beta2, float eps, double* loss_out);
 /* Stroboscopic spin tracking with the learned map: per turn, the network
