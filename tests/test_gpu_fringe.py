@@ -3,8 +3,8 @@ Eq. (skfringe)): the CUDA FP64 tracker through the C ABI against the CPU
 oracle on the same seeded inputs, every coordinate and spin component at
 1e-11, for single elements with fringes at every Romberg order, RHIC-like
 rings with fringe kicks on every magnet, lost particles, the batched entry
-point, the flag's validation, and the rejection of the mixed-precision
-tracker (FP64 only)."""
+point and the flag's validation; and the mixed-precision tracker's kicks
+within its error budget."""
 import numpy as np
 import pytest
 
