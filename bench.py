@@ -94,10 +94,7 @@ def parse_args():
     ap.add_argument("--profile-train", type=int, default=0, metavar="STEPS",
                     help="profiling mode: only train the spin-map network for STEPS steps on 32768-row batches "
                          "(pairs from 4000 particles x 10 turns) and print the step time")
-    args = ap.parse_args()
-    if args.precision == "mixed" and (args.ring != "rhic_like" or args.spin_order < 0):
-        ap.error("the mixed-precision tracker runs the bend-kick ring with a Romberg order only")
-    return args
+    return ap.parse_args()
 
 
 def profile_train(args):
