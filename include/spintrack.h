@@ -274,9 +274,9 @@ int st_batch_destroy(st_batch* batch);
 int st_batch_upload(st_batch* batch, int32_t job, const double* z_soa, const double* spin_soa,
                     int32_t src_is_device);
 /* Track every job for n_turns with Romberg order spin_order, or with a
- * midpoint scheme (ST_SPIN_MID_HALF, ST_SPIN_MID_KICK; FP64 batches without
- * fourth-order slice maps), asynchronously.  Errors: ST_ESTATE if a job has
- * no particles, ST_EINVAL as st_track. */
+ * midpoint scheme (ST_SPIN_MID_HALF, ST_SPIN_MID_KICK; batches without
+ * fourth-order slice maps, FP64 or mixed precision), asynchronously.  Errors:
+ * ST_ESTATE if a job has no particles, ST_EINVAL as st_track. */
 int st_batch_track(st_batch* batch, int32_t n_turns, int32_t spin_order);
 /* Copy job `job`'s state out (as st_spins_download); synchronises. */
 int st_batch_download(st_batch* batch, int32_t job, double* spin_soa, double* z_soa, uint8_t* lost,

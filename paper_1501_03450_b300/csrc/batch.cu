@@ -18,7 +18,7 @@
 #include <vector>
 
 #include "track_mid.cuh"
-#include "track_mixed.cuh"
+#include "track_mixed_mid.cuh"
 
 namespace st {
 
@@ -131,7 +131,31 @@ __global__ void __launch_bounds__(128, MINB) track_batch_mixed_kernel(const JobD
     });
 }
 
+// The midpoint spin schemes in mixed precision (KICK: split-kick placement)
+template <bool KICK, bool FR = false, bool EXT = false, bool RB = false>
+__global__ void __launch_bounds__(128, 2) track_batch_mixed_mid_kernel(const JobDesc* __restrict__ jobs,
+                                                                      const WorkItem* __restrict__ items,
+                                                                      int n_items, int32_t* queue, int n_turns,
+                                                                      int32_t* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t bar;
+    batch_loop(jobs, items, n_items, queue, status, smem, &bar, [&](const JobDesc& J, int64_t i) {
+        mixed_track_particle_mid<KICK, FR, EXT, RB>((const MixElem*)smem, (const uint16_t*)(smem + J.seq_offset),
+                                                    (const float2*)(smem + J.rho_offset), J.n_seq, J.ref, J.xpx,
+                                                    J.ypy, J.tpt, J.sxy, J.sz, J.lost, i, n_turns, status, nullptr,
+                                                    0);
+    });
+}
+
 typedef void (*BatchKernel)(const JobDesc*, const WorkItem*, int, int32_t*, int, int32_t*);
+
+template <bool KICK>
+static BatchKernel batch_mixed_mid_kernel(bool fr, bool mext, bool mrb) {
+    if (mrb) return track_batch_mixed_mid_kernel<KICK, true, true, true>;
+    if (mext) return track_batch_mixed_mid_kernel<KICK, true, true>;
+    if (fr) return track_batch_mixed_mid_kernel<KICK, true>;
+    return track_batch_mixed_mid_kernel<KICK>;
+}
 
 // variant 0 / 1 = larger / smaller register budget (fewer / more resident blocks)
 // ext: the FP64 instantiation with the extended element set compiled in
@@ -155,11 +179,11 @@ static BatchKernel batch_kernel(int precision, int K, int variant, bool ext, boo
         return variant ? track_batch_mixed_kernel<KK, 3> : track_batch_mixed_kernel<KK, 2>;
     switch (K) {
     case ST_SPIN_MID_HALF:
-        if (precision != ST_FP64) return nullptr;
+        if (precision != ST_FP64) return batch_mixed_mid_kernel<false>(fr, mext, mrb);
         return variant ? track_batch_fp64_kernel<ST_SPIN_MID_HALF, 3, true>
                        : track_batch_fp64_kernel<ST_SPIN_MID_HALF, 2, true>;
     case ST_SPIN_MID_KICK:
-        if (precision != ST_FP64) return nullptr;
+        if (precision != ST_FP64) return batch_mixed_mid_kernel<true>(fr, mext, mrb);
         return variant ? track_batch_fp64_kernel<ST_SPIN_MID_KICK, 3, true>
                        : track_batch_fp64_kernel<ST_SPIN_MID_KICK, 2, true>;
         ST_SEL(0)
@@ -521,8 +545,8 @@ int st_batch_track(st_batch* b, int32_t n_turns, int32_t spin_order) {
     if (spin_order < 0) {
         bool order4 = false;
         for (int j = 0; j < b->n_jobs; ++j) order4 = order4 || b->lats[j]->impl.has_order4;
-        if (b->precision != ST_FP64 || order4) {
-            set_error("st_batch_track: the midpoint schemes need an FP64 batch and second-order slice maps");
+        if (order4) {
+            set_error("st_batch_track: the midpoint schemes need second-order slice maps");
             return ST_EINVAL;
         }
     }

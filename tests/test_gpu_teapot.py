@@ -261,8 +261,9 @@ def test_one_turn_errors_drift_kick_against_bend_kick_on_the_gpu():
 
 @pytest.mark.parametrize("K", MID)
 def test_batched_jobs_with_midpoint_schemes(K):
-    """Uneven jobs (drift-kick, bend-kick and solenoid rings) in one
-    persistent launch with a midpoint scheme, each job against the oracle."""
+    """Uneven jobs (drift-kick, bend-kick, solenoid and rectangular-bend rings)
+    in one persistent launch with a midpoint scheme, each job against the
+    oracle, in FP64 and in mixed precision."""
     rings = [W.drift_kick_ring(W.toy_ring(45.5)), W.with_fringes(W.toy_ring(120.0)),
              W.solenoid_ring(45.5, ks=0.05), W.with_slices(W.rbend_ring(45.5, fringe=1), 3)]
     ns = [300, 77, 150, 33]
@@ -279,12 +280,27 @@ def test_batched_jobs_with_midpoint_schemes(K):
         assert np.array_equal(lb, lo)
         assert np.abs(zb - zo).max() < TOL and np.abs(Sb - So).max() < TOL
     b.close()
-    bm = st.Batch([W.toy_ring(45.5)], [64], "mixed")
-    z, S = W.gaussian_particles(64, 45.5, seed=1)
-    bm.upload(0, z, S)
-    with pytest.raises(st.SpinTrackError):
-        bm.track(1, K)
+    # the same jobs in a mixed batch (the mixed tracker's midpoint kernels, the
+    # rectangular bends in FP64 inside them): the mixed tracker's budget
+    bm = st.Batch(rings, ns, "mixed")
+    for k in range(len(rings)):
+        bm.upload(k, *inputs[k])
+    bm.track(4, K)
+    for k, (ring, (z, S)) in enumerate(zip(rings, inputs)):
+        zb, Sb, lb = bm.download(k)
+        zo, So, lo = oracle.track(ring, z, S, 4, K)
+        assert np.array_equal(lb, lo)
+        d = np.linalg.norm(Sb - So, axis=0)
+        assert d.mean() < 1e-7 and d.max() < 1e-6, (k, d.mean(), d.max())
+        assert np.abs(zb[:4] - zo[:4]).max() < 1e-8
     bm.close()
+    # fourth-order slices are refused with a midpoint scheme
+    b4 = st.Batch([W.with_split_order(W.with_spin_order(W.toy_ring(45.5), 2), 4)], [64], "mixed")
+    z, S = W.gaussian_particles(64, 45.5, seed=1)
+    b4.upload(0, z, S)
+    with pytest.raises(st.SpinTrackError):
+        b4.track(1, K)
+    b4.close()
 
 
 def test_spin_errors_over_turns_order_on_the_gpu():
